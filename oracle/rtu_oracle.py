@@ -1,0 +1,550 @@
+"""FP64 CPU oracle for the RTU-grid lensing hot path (Enzi et al., "Gaussian
+processes on ray-guided transformed uniform grids").
+
+TEST INFRASTRUCTURE ONLY.  The tests, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may call this module; the product path (the
+CUDA library and its Python binding) never imports it and shares no code with
+it.
+
+Plain, slow, obviously correct: every step is written out in float64 with
+plain PyTorch CPU tensor ops in the paper's order and notation.  Library
+primitives used as steps: ``torch.sort`` (order statistics), ``torch.fft``
+(the FFT of Eq. 1), ``torch.linalg.solve`` (the polynomial fit) and
+``torch.autograd`` (the gradient of log L / ELBO is by definition the
+derivative of the forward model; autograd evaluates it exactly up to
+rounding).
+
+Passages followed (paper sections / equations):
+  * pixel grid and supersampling ............ Sec. 2.3, Sec. 3.1
+  * EPL convergence (Eq. A1) ................ App. A.1; deflection by the
+    Tessore & Metcalf (2015) hypergeometric series (the paper gives kappa only)
+  * external shear .......................... App. A.1
+  * NFW (Eq. A2-A3), truncated NFW .......... App. A.2; truncation after
+    Baltz, Marshall & Oguri (2009)
+  * arc-mask centre rays, standardisation ... App. C step i, Sec. 2.2 footnote
+  * marginal eCDFs / quantile function ...... Sec. 2.2, App. C step ii
+  * Chebyshev-node polynomial fit of the QF . App. C step iii (order 21)
+  * cubic Hermite spline inverse (the CDF) .. App. C step iv
+  * copula map y = g(x) (Eq. 5) ............. Sec. 2.2
+  * GP source f = F^-1(sqrt(P) xi) (Eq. 1) .. Sec. 2.1; Matern P(k) (Eq. 4)
+  * softplus positivity (Eq. 2-3) ........... Sec. 2.1
+  * bilinear interpolation, zero outside .... Sec. 2.1
+  * supersample average, PSF, Gaussian noise  Sec. 2.3, Sec. 3.1
+  * likelihood / chi^2 in the mask .......... Sec. 4
+  * SVI ELBO with a Normal guide ............ Sec. 4 (location and scale)
+
+Readings where the paper is silent or ambiguous are listed in the design doc
+("Readings of the paper").  Parity unpinned (no independent pin exists):
+the linear prior T(a, lo, hi) of Table A1, whose definition lives in a cited
+paper that is not reproduced here.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import torch
+
+DT = torch.float64
+S0 = 0.01  # softplus transition scale s_0 (Eq. 3)
+
+# lens-profile and family codes (shared *numbering* with the C ABI header;
+# the numbers are an interface, not code)
+PROFILE_SIE = 0
+PROFILE_EPL = 1
+SUB_NONE = 0
+SUB_NFW = 1
+SUB_TNFW = 2
+PS_POWER_LAW = 0    # P = A k^-beta, P(0) = 0             params (A, beta)
+PS_MATERN_LIKE = 1  # P = A / (1 + (k/k0)^2)^2             params (A, k0)
+PS_MATERN = 2       # Eq. 4                                 params (sigma, n, zeta)
+N_PS_PARAMS = {PS_POWER_LAW: 2, PS_MATERN_LIKE: 2, PS_MATERN: 3}
+N_LENS = 8          # theta_E, gamma, e1, e2, x0, y0, Gamma1, Gamma2
+N_SUB_PARAMS = 5    # kappa_s, r_s, tau, x_s, y_s
+
+FLAG_NONMONOTONE = 1
+
+
+# ---------------------------------------------------------------------------
+# image-plane rays (Sec. 2.3: s_super x s_super sub-rays per pixel)
+# ---------------------------------------------------------------------------
+def pixel_centres(n_img: int, pix: float):
+    """Pixel (i, j) -> theta = ((i-(N-1)/2) pix, (j-(N-1)/2) pix); row-major [j][i]."""
+    c = (torch.arange(n_img, dtype=DT) - (n_img - 1) / 2.0) * pix
+    yy, xx = torch.meshgrid(c, c, indexing="ij")
+    return xx.reshape(-1), yy.reshape(-1)
+
+
+def subray_positions(n_img: int, pix: float, s: int):
+    """Sub-ray (a, b) of a pixel sits at ((a+1/2)/s - 1/2) pix from its centre.
+
+    Returns x, y of shape [n_img*n_img, s*s]; sub-ray index b*s + a."""
+    xc, yc = pixel_centres(n_img, pix)
+    off = ((torch.arange(s, dtype=DT) + 0.5) / s - 0.5) * pix
+    oy, ox = torch.meshgrid(off, off, indexing="ij")
+    return xc[:, None] + ox.reshape(1, -1), yc[:, None] + oy.reshape(1, -1)
+
+
+# ---------------------------------------------------------------------------
+# deflections (App. A)
+# ---------------------------------------------------------------------------
+def ellipticity_to_q_phi(e1, e2):
+    """(e1, e2) = (1-q)/(1+q) (cos 2phi, sin 2phi); phi from +x, counter-clockwise."""
+    c = torch.sqrt(e1 * e1 + e2 * e2)
+    q = (1.0 - c) / (1.0 + c)
+    phi = 0.5 * torch.atan2(e2, e1)
+    return q, phi
+
+
+def deflection_epl(x, y, theta_E, gamma, e1, e2, x0, y0, rel_tol=1e-17, max_terms=4000):
+    """Deflection of kappa = (3-gamma)/2 (theta_E/rho)^(gamma-1), Eq. A1, with
+    rho^2 = q x'^2 + y'^2/q in the frame centred on (x0, y0) and rotated by phi.
+
+    Tessore & Metcalf (2015): with R^2 = q^2 x'^2 + y'^2 (= q rho^2),
+    b = theta_E sqrt(q), t = gamma - 1, f = (1-q)/(1+q) and e^{i vphi} =
+    (q x' + i y')/R, the complex deflection in the rotated frame is
+        alpha' = 2b/(1+q) (b/R)^(t-1) sum_n Omega_n,
+        Omega_0 = e^{i vphi},
+        Omega_n = -f (2n-(2-t))/(2n+(2-t)) e^{2 i vphi} Omega_{n-1},
+    the series of 2F1(1, t/2; 2-t/2; -f e^{2 i vphi}).  Summed until the term is
+    below rel_tol.  R is clamped at 1e-10 arcsec (the singular centre)."""
+    q, phi = ellipticity_to_q_phi(e1, e2)
+    cp, sp = torch.cos(phi), torch.sin(phi)
+    dx, dy = x - x0, y - y0
+    xr = cp * dx + sp * dy
+    yr = -sp * dx + cp * dy
+    t = gamma - 1.0
+    b = theta_E * torch.sqrt(q)
+    R = torch.sqrt(q * q * xr * xr + yr * yr).clamp_min(1e-10)
+    eiv = torch.complex(q * xr / R, yr / R)
+    e2iv = eiv * eiv
+    f = (1.0 - q) / (1.0 + q)
+    term = eiv
+    total = term
+    for n in range(1, max_terms):
+        term = term * e2iv * (-f * (2.0 * n - (2.0 - t)) / (2.0 * n + (2.0 - t)))
+        total = total + term
+        if float(term.detach().abs().max()) <= rel_tol:
+            break
+    pref = 2.0 * b / (1.0 + q) * torch.pow(b / R, t - 1.0)
+    axr = pref * total.real
+    ayr = pref * total.imag
+    return cp * axr - sp * ayr, sp * axr + cp * ayr
+
+
+def deflection_shear(x, y, g1, g2):
+    """External shear about the origin: potential psi = g1 (x^2-y^2)/2 + g2 x y."""
+    return g1 * x + g2 * y, g2 * x - g1 * y
+
+
+def _safe_F(x):
+    """F(x) of Eq. A3: atan(sqrt(x^2-1))/sqrt(x^2-1) (x>1), atanh(sqrt(1-x^2))/sqrt(1-x^2) (x<1).
+
+    Near x = 1 both branches equal the series sum_k w^k/(2k+1), w = 1-x^2."""
+    w = 1.0 - x * x
+    near = w.abs() < 1e-2
+    ws = torch.where(near, w, torch.zeros_like(w))
+    ser = torch.zeros_like(x)
+    p = torch.ones_like(x)
+    for k in range(0, 14):
+        ser = ser + p / (2 * k + 1)
+        p = p * ws
+    lo = (w > 0) & ~near
+    hi = (w < 0) & ~near
+    sl = torch.sqrt(torch.where(lo, w, torch.full_like(w, 0.5)))
+    sh = torch.sqrt(torch.where(hi, -w, torch.full_like(w, 0.5)))
+    f_lo = torch.atanh(sl) / sl
+    f_hi = torch.atan(sh) / sh
+    return torch.where(near, ser, torch.where(lo, f_lo, f_hi))
+
+
+def nfw_convergence(r, kappa_s, r_s):
+    """Eq. A3: kappa = 2 kappa_s (1 - F(x)) / (x^2 - 1), x = r / r_s."""
+    x = r / r_s
+    w = 1.0 - x * x
+    near = w.abs() < 1e-2
+    # (1-F)/(x^2-1) = (F-1)/w = sum_{k>=1} w^(k-1)/(2k+1) near x = 1
+    ws = torch.where(near, w, torch.zeros_like(w))
+    ser = torch.zeros_like(x)
+    p = torch.ones_like(x)
+    for k in range(1, 15):
+        ser = ser + p / (2 * k + 1)
+        p = p * ws
+    wsafe = torch.where(near, torch.ones_like(w), w)
+    far = (_safe_F(x) - 1.0) / wsafe
+    return 2.0 * kappa_s * torch.where(near, ser, far)
+
+
+def _nfw_mass_fn(x):
+    """h(x) = ln(x/2) + F(x): alpha(r) = 4 kappa_s r_s h(x)/x for Eq. A3."""
+    return torch.log(x / 2.0) + _safe_F(x)
+
+
+def _tnfw_mass_fn(x, tau):
+    """Projected-mass function of the tau-truncated NFW (Baltz, Marshall & Oguri
+    2009, rho = rho_NFW tau^2/(tau^2 + x^2)); tends to h(x) as tau -> infinity."""
+    t2 = tau * tau
+    sq = torch.sqrt(t2 + x * x)
+    L = torch.log(x / (sq + tau))
+    return t2 / (t2 + 1.0) ** 2 * (
+        (t2 + 1.0 + 2.0 * (x * x - 1.0)) * _safe_F(x)
+        + tau * math.pi
+        + (t2 - 1.0) * torch.log(tau)
+        + sq * (-math.pi + L * (t2 - 1.0) / tau)
+    )
+
+
+def deflection_nfw(x, y, kappa_s, r_s, tau, xs, ys, kind):
+    """Radial deflection of an (optionally truncated) NFW subhalo centred at (xs, ys)."""
+    dx, dy = x - xs, y - ys
+    r = torch.sqrt(dx * dx + dy * dy).clamp_min(1e-10)
+    xx = r / r_s
+    g = _nfw_mass_fn(xx) if kind == SUB_NFW else _tnfw_mass_fn(xx, tau)
+    a = 4.0 * kappa_s * r_s * g / xx / r
+    return a * dx, a * dy
+
+
+def trace(x, y, lens, profile, subs=None, sub_kind=SUB_NONE):
+    """Lens equation beta = theta - sum alpha (App. A); lens = [thE, gamma, e1, e2, x0, y0, G1, G2]."""
+    gamma = lens[1] if profile == PROFILE_EPL else torch.tensor(2.0, dtype=DT)
+    ax, ay = deflection_epl(x, y, lens[0], gamma, lens[2], lens[3], lens[4], lens[5])
+    sx, sy = deflection_shear(x, y, lens[6], lens[7])
+    ax, ay = ax + sx, ay + sy
+    if subs is not None and sub_kind != SUB_NONE:
+        for h in range(subs.shape[0]):
+            p = subs[h]
+            nx, ny = deflection_nfw(x, y, p[0], p[1], p[2], p[3], p[4], sub_kind)
+            ax, ay = ax + nx, ay + ny
+    return x - ax, y - ay
+
+
+# ---------------------------------------------------------------------------
+# the RTU transform (Sec. 2.2, App. C)
+# ---------------------------------------------------------------------------
+def chebyshev_nodes(m: int):
+    """u_j = (1 - cos((2j-1) pi / (2m)))/2, j = 1..m (ascending, inside (0, 1))."""
+    j = torch.arange(1, m + 1, dtype=DT)
+    return (1.0 - torch.cos((2.0 * j - 1.0) * math.pi / (2.0 * m))) / 2.0
+
+
+def chebyshev_T(t, degree):
+    """[len(t), degree+1] matrix of T_k(t) by the three-term recurrence."""
+    cols = [torch.ones_like(t), t]
+    for _ in range(2, degree + 1):
+        cols.append(2.0 * t * cols[-1] - cols[-2])
+    return torch.stack(cols[: degree + 1], dim=-1)
+
+
+def chebyshev_dT(t, degree):
+    """[len(t), degree+1] matrix of dT_k/dt = k U_{k-1}(t)."""
+    U = [torch.ones_like(t), 2.0 * t]
+    for _ in range(2, degree + 1):
+        U.append(2.0 * t * U[-1] - U[-2])
+    cols = [torch.zeros_like(t)] + [k * U[k - 1] for k in range(1, degree + 1)]
+    return torch.stack(cols, dim=-1)
+
+
+def quantile_type7(sorted_vals, u):
+    """Empirical quantile (linear interpolation of order statistics, h = u (N-1))."""
+    n = sorted_vals.shape[0]
+    h = u * (n - 1)
+    k = torch.floor(h).long().clamp(0, n - 1)
+    k1 = (k + 1).clamp(max=n - 1)
+    frac = h - k.to(DT)
+    return sorted_vals[k] + frac * (sorted_vals[k1] - sorted_vals[k])
+
+
+@dataclass
+class RTUTransform:
+    """Per-axis smoothed CDF: mu, sigma_min and the Hermite knots (z-space)."""
+    mu: torch.Tensor            # [2]
+    sigma: torch.Tensor         # scalar sigma_min
+    knots: torch.Tensor         # [2, M+2]  X_0 = p(0), X_j = p(u_j), X_{M+1} = p(1)
+    values: torch.Tensor        # [M+2]     0, u_1..u_M, 1
+    slopes: torch.Tensor        # [2, M+2]  dC/dz = 1 / p'(u)
+    coeffs: torch.Tensor        # [2, D+1]  Chebyshev coefficients of the QF
+    q_nodes: torch.Tensor       # [2, M]    empirical QF at the nodes
+    flags: int = 0
+    n_centre: int = 0
+    extra: dict = field(default_factory=dict)
+
+
+def standardise(bx, by):
+    """App. C step i: mean per axis and sigma_min = min(std_x, std_y) (ddof 0, tie -> x)."""
+    mu = torch.stack([bx.mean(), by.mean()])
+    sx = torch.sqrt(((bx - mu[0]) ** 2).mean())
+    sy = torch.sqrt(((by - mu[1]) ** 2).mean())
+    sigma = sx if float(sx.detach()) <= float(sy.detach()) else sy
+    return mu, sigma
+
+
+def fit_qf_polynomial(zs, u, degree):
+    """App. C step iii: Chebyshev coefficients c of p(u) = sum_k c_k T_k(2u-1) fitted to
+    the empirical QF at the nodes u; each node weighted by the eCDF slope there
+    (centred rank difference of half-width 1/(2M)).  With M = degree+1 nodes the
+    weighted fit is the interpolant and the weights drop out."""
+    m = u.shape[0]
+    V = chebyshev_T(2.0 * u - 1.0, degree)
+    Q = quantile_type7(zs, u)
+    if m == degree + 1:
+        return torch.linalg.solve(V, Q), Q
+    d = 0.5 / m
+    lo, hi = (u - d).clamp(0.0, 1.0), (u + d).clamp(0.0, 1.0)
+    wgt = (hi - lo) / (quantile_type7(zs, hi) - quantile_type7(zs, lo)).clamp_min(1e-300)
+    return torch.linalg.lstsq(wgt[:, None] * V, wgt * Q).solution, Q
+
+
+def hermite_knots(c, u, degree, guard_eps=1e-6):
+    """App. C step iv: knots X = p(0), p(u_1..u_M), p(1) and CDF slopes 1/p'(u) there.
+
+    Monotonicity guard: p' >= eps*span, X_{j+1} >= X_j + eps*span with
+    span = p(1) - p(0); returns (X, slopes, repaired?)."""
+    t = torch.cat([torch.tensor([-1.0], dtype=DT), 2.0 * u - 1.0, torch.tensor([1.0], dtype=DT)])
+    X = chebyshev_T(t, degree) @ c
+    dp = (chebyshev_dT(t, degree) * 2.0) @ c
+    repaired = False
+    span = X[-1] - X[0]
+    if float(span.detach()) <= 0.0:
+        repaired = True
+        span = span.abs() + 1e-300
+    floor_d = guard_eps * span
+    if bool((dp.detach() < floor_d.detach()).any()):
+        repaired = True
+    dp = torch.maximum(dp, floor_d)
+    Xr = [X[0]]
+    for j in range(1, X.shape[0]):
+        lim = Xr[-1] + floor_d
+        if float(X[j].detach()) < float(lim.detach()):
+            repaired = True
+        Xr.append(torch.maximum(X[j], lim))
+    return torch.stack(Xr), 1.0 / dp, repaired
+
+
+def fit_transform(bx, by, n_nodes=22, degree=21, guard_eps=1e-6):
+    """App. C steps i-iv from the traced centre rays (bx, by): standardise, sort each
+    marginal (the eCDF), fit the QF polynomial at the Chebyshev nodes, and build the
+    Hermite CDF (values u_j at knots p(u_j), slopes 1/p'(u_j), linear beyond the ends)."""
+    mu, sigma = standardise(bx, by)
+    u = chebyshev_nodes(n_nodes)
+    flags = 0
+    knots, slopes, coeffs, qn = [], [], [], []
+    for a, b in enumerate((bx, by)):
+        zs, _ = torch.sort((b - mu[a]) / sigma)
+        c, Q = fit_qf_polynomial(zs, u, degree)
+        X, d, rep = hermite_knots(c, u, degree, guard_eps)
+        if rep:
+            flags |= FLAG_NONMONOTONE
+        knots.append(X)
+        slopes.append(d)
+        coeffs.append(c)
+        qn.append(Q)
+    values = torch.cat([torch.zeros(1, dtype=DT), u, torch.ones(1, dtype=DT)])
+    return RTUTransform(mu=mu, sigma=sigma, knots=torch.stack(knots), values=values,
+                        slopes=torch.stack(slopes), coeffs=torch.stack(coeffs),
+                        q_nodes=torch.stack(qn), flags=flags, n_centre=bx.shape[0])
+
+
+def hermite_cdf(z, X, U, d):
+    """Cubic Hermite spline through (X_j, U_j) with slopes d_j; linear extrapolation
+    beyond the end knots (so C can leave [0, 1])."""
+    m = X.shape[0]
+    j = (torch.searchsorted(X.detach(), z.detach(), right=True) - 1).clamp(0, m - 2)
+    x0, x1 = X[j], X[j + 1]
+    h = x1 - x0
+    t = (z - x0) / h
+    t2, t3 = t * t, t * t * t
+    h00 = 2 * t3 - 3 * t2 + 1
+    h10 = t3 - 2 * t2 + t
+    h01 = -2 * t3 + 3 * t2
+    h11 = t3 - t2
+    inner = h00 * U[j] + h10 * h * d[j] + h01 * U[j + 1] + h11 * h * d[j + 1]
+    left = U[0] + d[0] * (z - X[0])
+    right = U[-1] + d[-1] * (z - X[-1])
+    return torch.where(z < X[0], left, torch.where(z >= X[-1], right, inner))
+
+
+def rtu_map(bx, by, T: RTUTransform):
+    """Eq. 5 coordinates: y = g(x) = (C_1(z_1), C_2(z_2)), z = (beta - mu)/sigma_min."""
+    zx = (bx - T.mu[0]) / T.sigma
+    zy = (by - T.mu[1]) / T.sigma
+    return (hermite_cdf(zx, T.knots[0], T.values, T.slopes[0]),
+            hermite_cdf(zy, T.knots[1], T.values, T.slopes[1]))
+
+
+# ---------------------------------------------------------------------------
+# the GP source (Sec. 2.1, Eq. 1-4)
+# ---------------------------------------------------------------------------
+def wavenumbers(n_src: int, pitch: float):
+    """k = 2 pi |(fx, fy)| / pitch with f = fftfreq(n_src) per axis (cycles per pixel)."""
+    f = torch.fft.fftfreq(n_src, dtype=DT)
+    fy, fx = torch.meshgrid(f, f, indexing="ij")
+    return 2.0 * math.pi * torch.sqrt(fx * fx + fy * fy) / pitch
+
+
+def power_spectrum(family: int, ps, k):
+    """P(k) of the chosen family; ps holds the family's parameters."""
+    if family == PS_POWER_LAW:
+        A, beta = ps[0], ps[1]
+        zero = k == 0
+        ks = torch.where(zero, torch.ones_like(k), k)
+        return torch.where(zero, torch.zeros_like(k), A * torch.pow(ks, -beta))
+    if family == PS_MATERN_LIKE:
+        A, k0 = ps[0], ps[1]
+        return A / (1.0 + (k / k0) ** 2) ** 2
+    if family == PS_MATERN:  # Eq. 4
+        sig, n, zeta = ps[0], ps[1], ps[2]
+        a = 2.0 * n / (zeta * zeta)
+        return sig * sig * 4.0 * math.pi * n * torch.pow(a, n) * torch.pow(a + k * k, -(n + 1.0))
+    raise ValueError(family)
+
+
+def gp_field(w, sqrtP):
+    """Eq. 1: f = F^-1(sqrt(P) . F(w)), unnormalised forward FFT, 1/N^2 inverse."""
+    return torch.fft.ifft2(sqrtP * torch.fft.fft2(w)).real
+
+
+def softplus(x):
+    """Eq. 2, phi_sp(x) = log(1 + exp(x)), in the overflow-free form max(x,0) + log1p(exp(-|x|))."""
+    return torch.clamp_min(x, 0.0) + torch.log1p(torch.exp(-x.abs()))
+
+
+def source_brightness(f, alpha_src):
+    """Eq. 3: s = (phi_sp(f/s0) s0)^alpha_src."""
+    return torch.pow(softplus(f / S0) * S0, alpha_src)
+
+
+def bilinear(grid, yx, yy):
+    """Bilinear interpolation of a vertex-centred grid on [0,1]^2 (node (i, j) at
+    (i/(N-1), j/(N-1)), grid[j][i]); zero outside the unit square (Sec. 2.1)."""
+    n = grid.shape[0]
+    inside = (yx >= 0) & (yx <= 1) & (yy >= 0) & (yy <= 1)
+    gx = yx.clamp(0.0, 1.0) * (n - 1)
+    gy = yy.clamp(0.0, 1.0) * (n - 1)
+    i0 = torch.floor(gx.detach()).long().clamp(0, n - 2)
+    j0 = torch.floor(gy.detach()).long().clamp(0, n - 2)
+    fx = gx - i0.to(DT)
+    fy = gy - j0.to(DT)
+    v = ((1 - fx) * (1 - fy) * grid[j0, i0] + fx * (1 - fy) * grid[j0, i0 + 1]
+         + (1 - fx) * fy * grid[j0 + 1, i0] + fx * fy * grid[j0 + 1, i0 + 1])
+    return torch.where(inside, v, torch.zeros_like(v))
+
+
+# ---------------------------------------------------------------------------
+# image formation and likelihood (Sec. 3.1, Sec. 4)
+# ---------------------------------------------------------------------------
+def psf_convolve(img, psf):
+    """'same' 2-D convolution with zero padding: m[j,i] = sum_{b,a} psf[b,a] img[j-(b-c), i-(a-c)]."""
+    n = img.shape[0]
+    K = psf.shape[0]
+    c = (K - 1) // 2
+    pad = torch.zeros((n + 2 * c, n + 2 * c), dtype=DT)
+    pad = pad.index_put((torch.arange(c, c + n)[:, None], torch.arange(c, c + n)[None, :]), img)
+    out = torch.zeros((n, n), dtype=DT)
+    for b in range(K):
+        for a in range(K):
+            # img[j - (b - c)] = pad[j - b + 2c]
+            out = out + psf[b, a] * pad[2 * c - b: 2 * c - b + n, 2 * c - a: 2 * c - a + n]
+    return out
+
+
+def log_likelihood(model, data, sigma, mask):
+    """Gaussian noise over all pixels (Sec. 2.2: light outside the mask is kept):
+    log L = -1/2 sum ((d-m)/sigma)^2 - N log(sigma sqrt(2 pi)); chi^2_img in the mask."""
+    r = (data - model) / sigma
+    r2 = r * r
+    n = data.numel()
+    logL = -0.5 * r2.sum() - n * math.log(sigma * math.sqrt(2.0 * math.pi))
+    nm = int(mask.sum())
+    chi2 = (r2 * mask.to(DT)).sum() / max(nm, 1)
+    return logL, chi2
+
+
+@dataclass
+class System:
+    """One lens system: observation (Sec. 3.1) plus the model's fixed choices."""
+    data: torch.Tensor          # [n_img, n_img] float64
+    mask: torch.Tensor          # [n_img, n_img] bool (arc mask)
+    psf: torch.Tensor           # [K, K]
+    sigma: float                # Gaussian noise rms
+    pix: float                  # arcsec per pixel
+    s_super: int
+    n_src: int
+    src_pitch: float            # source-grid pitch for k (arcsec)
+    profile: int = PROFILE_SIE
+    ps_family: int = PS_POWER_LAW
+    sub_kind: int = SUB_NONE
+    n_nodes: int = 22
+    degree: int = 21
+
+    @property
+    def n_img(self):
+        return self.data.shape[0]
+
+
+def build_grid(sys: System, lens, subs=None):
+    """rtu_build_grid: trace the masked pixel centres and fit the transform."""
+    xc, yc = pixel_centres(sys.n_img, sys.pix)
+    sel = sys.mask.reshape(-1)
+    bx, by = trace(xc[sel], yc[sel], lens, sys.profile, subs, sys.sub_kind)
+    return fit_transform(bx, by, sys.n_nodes, sys.degree)
+
+
+def gp_source(sys: System, latents, ps):
+    """Source grid s*(y) on the RTU grid; ps = [family params..., alpha_src]."""
+    k = wavenumbers(sys.n_src, sys.src_pitch)
+    npar = N_PS_PARAMS[sys.ps_family]
+    P = power_spectrum(sys.ps_family, ps[:npar], k)
+    f = gp_field(latents, torch.sqrt(P))
+    return source_brightness(f, ps[npar]), f
+
+
+def ray_hist(sys: System, lens, subs=None, T=None):
+    """Integer count of supersampled rays per RTU cell (cells (N-1)^2, row-major);
+    rays outside the unit square are not counted."""
+    if T is None:
+        T = build_grid(sys, lens, subs)
+    x, y = subray_positions(sys.n_img, sys.pix, sys.s_super)
+    bx, by = trace(x.reshape(-1), y.reshape(-1), lens, sys.profile, subs, sys.sub_kind)
+    yx, yy = rtu_map(bx, by, T)
+    n = sys.n_src
+    inside = (yx >= 0) & (yx <= 1) & (yy >= 0) & (yy <= 1)
+    i0 = torch.floor(yx.clamp(0, 1) * (n - 1)).long().clamp(0, n - 2)
+    j0 = torch.floor(yy.clamp(0, 1) * (n - 1)).long().clamp(0, n - 2)
+    cell = (j0 * (n - 1) + i0)[inside]
+    return torch.bincount(cell, minlength=(n - 1) * (n - 1)).to(torch.int64)
+
+
+def forward(sys: System, lens, latents, ps, subs=None):
+    """rtu_forward: RTU grid -> GP source -> ray-traced supersampled image -> PSF -> log L."""
+    T = build_grid(sys, lens, subs)
+    src, f = gp_source(sys, latents, ps)
+    x, y = subray_positions(sys.n_img, sys.pix, sys.s_super)
+    bx, by = trace(x.reshape(-1), y.reshape(-1), lens, sys.profile, subs, sys.sub_kind)
+    yx, yy = rtu_map(bx, by, T)
+    vals = bilinear(src, yx, yy).reshape(sys.n_img * sys.n_img, sys.s_super ** 2)
+    image = vals.mean(dim=1).reshape(sys.n_img, sys.n_img)
+    model = psf_convolve(image, sys.psf)
+    logL, chi2 = log_likelihood(model, sys.data, sys.sigma, sys.mask)
+    return dict(logL=logL, chi2=chi2, model=model, image=image, source=src, field=f, T=T)
+
+
+def forward_adjoint(sys: System, lens, latents, ps, subs=None):
+    """rtu_adjoint reference: log L and its gradient w.r.t. lens, latents, ps (and subhaloes)."""
+    lens = lens.detach().clone().requires_grad_(True)
+    latents = latents.detach().clone().requires_grad_(True)
+    ps = ps.detach().clone().requires_grad_(True)
+    inputs = [lens, latents, ps]
+    if subs is not None:
+        subs = subs.detach().clone().requires_grad_(True)
+        inputs.append(subs)
+    out = forward(sys, lens, latents, ps, subs)
+    grads = torch.autograd.grad(out["logL"], inputs, allow_unused=True)
+    grads = [torch.zeros_like(v) if g is None else g for g, v in zip(grads, inputs)]
+    res = dict(logL=out["logL"].detach(), chi2=out["chi2"].detach(), model=out["model"].detach(),
+               image=out["image"].detach(), g_lens=grads[0], g_latents=grads[1], g_ps=grads[2],
+               flags=out["T"].flags)
+    if subs is not None:
+        res["g_subs"] = grads[3]
+    if sys.profile == PROFILE_SIE:
+        res["g_lens"][1] = 0.0
+    return res
