@@ -1,0 +1,174 @@
+/*
+ * rtu.h -- C ABI of the B300 (sm_103a) hot path of the RTU-grid lensing method
+ * (Enzi, Krawczyk, Li & Collett, "Gaussian processes on ray-guided transformed
+ * uniform grids for ... adaptive source reconstruction in lens modelling").
+ *
+ * One evaluation = one lens system with one parameter set.  A call takes an
+ * array of systems and an array of per-evaluation bindings (rtu_eval) and
+ * launches each step once for the whole array, so a batch of many systems of
+ * uneven sizes fills the GPU; an array of one is the plain per-system path.
+ *
+ * Conventions common to every entry point
+ *  - Ownership: the caller owns every pointer.  Device pointers must stay valid
+ *    until the stream reaches the call.  The library allocates no device
+ *    memory: all scratch lives in the workspace the caller passes to
+ *    rtu_system_create (size from rtu_workspace_size).
+ *  - Asynchrony: compute calls are stream-ordered and return before the GPU
+ *    finishes; outputs are valid once `stream` has reached the call.
+ *  - Precision: desc.precision selects RTU_F64 (every buffer marked "real"
+ *    is double) or RTU_F32 (real = float; the centre-ray trace, the CDF
+ *    order statistics, the fit, all reductions and near-core deflections stay
+ *    in double).  Lens, subhalo and power-spectrum parameters, their
+ *    gradients and the scalar statistics are always double.
+ *  - Errors: argument, shape and CUDA launch errors are returned
+ *    synchronously as a negative rtu_status and described by rtu_last_error().
+ *    Conditions found on the device (a repaired non-monotone CDF fit, an
+ *    order-statistic selection that ran out of candidate space, a bounded wait
+ *    that gave up) are written as bits into stats[RTU_STAT_FLAGS].  Nothing
+ *    aborts, traps or exits.
+ *  - Thread safety: calls on distinct systems may run from distinct host
+ *    threads; a system (its workspace) must not be used by two calls at once.
+ *
+ * Layouts
+ *  - Images are row-major [n_img][n_img]; pixel (i, j), i = column = x, sits at
+ *    theta = ((i - (n_img-1)/2) pix, (j - (n_img-1)/2) pix) arcsec; its
+ *    s x s sub-rays at offsets ((a + 1/2)/s - 1/2) pix (Sec. 2.3, Sec. 3.1).
+ *  - Source grids are row-major [n_src][n_src] on the unit square of RTU
+ *    coordinates, node (i, j) at (i/(n_src-1), j/(n_src-1)) (Sec. 2.1-2.2).
+ *  - lens[8] = theta_E, gamma, e1, e2, x0, y0, Gamma1, Gamma2 (App. A.1), then
+ *    n_sub x {kappa_s, r_s, tau, x_s, y_s} (App. A.2).  (e1, e2) =
+ *    (1-q)/(1+q) (cos 2 phi, sin 2 phi).  For RTU_SIE gamma is ignored (= 2) and
+ *    its gradient is 0.
+ *  - ps = family parameters then alpha_src (Eq. 3-4):
+ *      RTU_PS_POWER_LAW   (A, beta):      P = A k^-beta, P(0) = 0
+ *      RTU_PS_MATERN_LIKE (A, k0):        P = A / (1 + (k/k0)^2)^2
+ *      RTU_PS_MATERN      (sigma, n, zeta): Eq. 4
+ *    with k = 2 pi |fftfreq| / src_pitch.
+ */
+#ifndef RTU_H
+#define RTU_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t rtu_status;
+
+/* return codes (negative = error, returned synchronously) */
+#define RTU_OK              0
+#define RTU_E_ARG          -1   /* bad argument or unsupported shape */
+#define RTU_E_CUDA         -2   /* a CUDA runtime call or launch failed */
+#define RTU_E_WORKSPACE    -3   /* workspace too small or misaligned */
+#define RTU_E_UNSUPPORTED  -4   /* a mode this build does not implement */
+
+/* device-side flag bits in stats[RTU_STAT_FLAGS] */
+#define RTU_W_NONMONOTONE   1   /* the CDF fit needed its monotonicity repair */
+#define RTU_W_SELECT        2   /* order-statistic selection ran out of space */
+#define RTU_W_TIMEOUT       4   /* a bounded wait on an async copy gave up */
+
+enum { RTU_F32 = 0, RTU_F64 = 1 };
+enum { RTU_SIE = 0, RTU_EPL = 1 };
+enum { RTU_SUB_NONE = 0, RTU_SUB_NFW = 1, RTU_SUB_TNFW = 2 };
+enum { RTU_PS_POWER_LAW = 0, RTU_PS_MATERN_LIKE = 1, RTU_PS_MATERN = 2 };
+
+/* stats[] written by rtu_forward (double[RTU_N_STATS]) */
+enum { RTU_STAT_LOGL = 0, RTU_STAT_CHI2_MASK = 1, RTU_STAT_N_MASK = 2, RTU_STAT_FLAGS = 3,
+       RTU_N_STATS = 4 };
+
+#define RTU_N_LENS 8
+#define RTU_N_SUB_PARAMS 5
+#define RTU_MAX_SUB 16
+#define RTU_MAX_NODES 64
+
+/* Static description of one lens system (Sec. 3.1 observation + model choices). */
+typedef struct {
+    int32_t n_img;       /* image side, pixels (>= 2) */
+    int32_t s_super;     /* sub-rays per pixel side (1..8) */
+    int32_t n_src;       /* source-grid side; 2^a 3^b, 4 <= n_src <= 256 */
+    int32_t psf_k;       /* odd PSF side, 1 <= psf_k <= 31 */
+    int32_t profile;     /* RTU_SIE | RTU_EPL */
+    int32_t sub_kind;    /* RTU_SUB_* */
+    int32_t n_sub;       /* 0..RTU_MAX_SUB subhaloes */
+    int32_t ps_family;   /* RTU_PS_* */
+    int32_t precision;   /* RTU_F32 | RTU_F64 */
+    int32_t n_nodes;     /* Chebyshev nodes M (App. C iii); must equal degree+1 */
+    int32_t degree;      /* polynomial degree D of the quantile fit (21 in the paper) */
+    int32_t n_slots;     /* concurrent evaluations of this system (e.g. ELBO samples) */
+    double pix;          /* arcsec per pixel */
+    double src_pitch;    /* source-grid pitch entering k (arcsec) */
+    double sigma;        /* Gaussian noise rms (Sec. 3.1) */
+    const void* data;    /* device, real [n_img*n_img] observed image */
+    const uint8_t* mask; /* device, u8 [n_img*n_img]; nonzero = in the arc mask (Sec. 2.2) */
+    const void* psf;     /* device, real [psf_k*psf_k], centre at (psf_k-1)/2 */
+} rtu_system_desc;
+
+typedef struct rtu_system rtu_system;
+
+/* Per-evaluation bindings; every pointer is a device pointer. */
+typedef struct {
+    int32_t slot;              /* workspace slot 0..n_slots-1 */
+    int32_t pad_;
+    const double* lens;        /* [8 + 5 n_sub] */
+    const void* latents;       /* real [n_src*n_src] white-noise latents (Eq. 1) */
+    const double* ps;          /* [n_family + 1] power spectrum params, alpha_src last */
+    const double* dlogL;       /* adjoint: upstream scale on d log L (nullable => 1) */
+    double* stats;             /* forward out: [RTU_N_STATS] (nullable) */
+    void* model;               /* forward out: real [n_img^2] PSF-convolved model (nullable) */
+    void* image;               /* forward out: real [n_img^2] unconvolved image (nullable) */
+    void* source;              /* forward out: real [n_src^2] source brightness s* (nullable) */
+    double* cdf;               /* build out: [3 + 4 (M+2)] mu_x, mu_y, sigma_min,
+                                  knots_x[M+2], knots_y[M+2], slopes_x[M+2], slopes_y[M+2]
+                                  (nullable) */
+    int32_t* ray_hist;         /* forward out: [(n_src-1)^2] supersampled rays per RTU cell
+                                  (nullable) */
+    void* g_latents;           /* adjoint out: real [n_src^2] */
+    double* g_lens;            /* adjoint out: [8 + 5 n_sub] */
+    double* g_ps;              /* adjoint out: [n_family + 1] */
+} rtu_eval;
+
+/* Bytes of device workspace one system needs (256-byte aligned base). 0 on bad desc. */
+size_t rtu_workspace_size(const rtu_system_desc* desc);
+
+/* Create a system over caller-owned workspace.  Synchronous: copies the mask to
+ * the host once to list the arc-mask pixels (Sec. 2.2 footnote: the CDF uses
+ * only observed-pixel centres inside the mask) and uploads small tables
+ * (FFT twiddles, digit reversal, Chebyshev nodes) into the workspace. */
+rtu_status rtu_system_create(const rtu_system_desc* desc, void* workspace, size_t ws_bytes,
+                             rtu_system** out);
+rtu_status rtu_system_destroy(rtu_system* sys);
+
+/* S1-S5 (App. C steps i-iv, Sec. 2.2): trace the arc-mask pixel centres through
+ * the lens (lens equation, App. A), standardise them, take the exact order
+ * statistics at the Chebyshev nodes with integer histograms and prefix scans,
+ * fit the degree-D quantile polynomial and build the Hermite CDF knots.
+ * Writes ev.cdf when non-null; the transform stays in the slot for rtu_forward. */
+rtu_status rtu_build_grid(rtu_system* const* sys, const rtu_eval* ev, int32_t n, void* stream);
+
+/* S1-S8 + S11: rtu_build_grid, then the GP source (Eq. 1-4: FFT filter of the
+ * latents by sqrt(P), softplus and alpha_src), the supersampled ray trace
+ * through the RTU map (Eq. 5) with bilinear interpolation (zero outside the
+ * grid), the supersample average, the PSF convolution and the Gaussian
+ * log-likelihood / chi^2 in the mask (Sec. 3.1, Sec. 4). */
+rtu_status rtu_forward(rtu_system* const* sys, const rtu_eval* ev, int32_t n, void* stream);
+
+/* S9: gradient of dlogL * log L with respect to latents, lens (and subhalo)
+ * parameters and power-spectrum parameters, through the PSF, the bilinear
+ * interpolation (atomic-free: rays counting-sorted by source cell, gathered per
+ * node), the Hermite CDF, the polynomial fit and the order statistics, the
+ * standardisation and the ray trace.  Ray positions are recomputed, not stored.
+ * Must follow rtu_forward on the same stream with the same bindings/slot. */
+rtu_status rtu_adjoint(rtu_system* const* sys, const rtu_eval* ev, int32_t n, void* stream);
+
+/* Human-readable description of the last error on this host thread. */
+const char* rtu_last_error(void);
+
+/* Library version string. */
+const char* rtu_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RTU_H */

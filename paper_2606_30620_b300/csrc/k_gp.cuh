@@ -1,0 +1,298 @@
+// k_gp.cuh -- the GP source on the uniform RTU grid (Sec. 2.1, Eq. 1-4) and
+// its adjoint.  One CTA per evaluation runs a mixed-radix (2, 3, 4)
+// decimation-in-time FFT in shared memory over chunks of rows, then chunks of
+// columns, of an n_src x n_src complex buffer that stays in L2.
+#pragma once
+#include "rtu_internal.cuh"
+
+namespace rtu {
+
+constexpr int GP_NT = 512;
+constexpr int GP_SMEM = 96 * 1024;   // bytes of dynamic shared memory for FFT chunks
+
+template <typename T> struct Cx { T x, y; };
+template <typename T> __device__ __forceinline__ Cx<T> cmul(Cx<T> a, Cx<T> b) {
+    return Cx<T>{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+template <typename T> __device__ __forceinline__ Cx<T> cadd(Cx<T> a, Cx<T> b) { return Cx<T>{a.x + b.x, a.y + b.y}; }
+template <typename T> __device__ __forceinline__ Cx<T> csub(Cx<T> a, Cx<T> b) { return Cx<T>{a.x - b.x, a.y - b.y}; }
+
+// twiddle exp(-+2 pi i m / n) from the table (conjugate for the inverse)
+template <typename T>
+__device__ __forceinline__ Cx<T> twid(const Cx<T>* tw, int m, bool inv) {
+    Cx<T> w = tw[m];
+    if (inv) w.y = -w.y;
+    return w;
+}
+
+// In-place DIT butterflies over `cnt` length-n sequences stored contiguously in
+// shared memory, input already in digit-reversed order.
+template <typename T>
+__device__ void fft_seq_smem(Cx<T>* buf, int cnt, int n, const int* rad, int nrad, const Cx<T>* tw,
+                             bool inv) {
+    int L = 1;
+    for (int s = 0; s < nrad; ++s) {
+        const int r = rad[s];
+        const int Ls = L * r;
+        const int nb = n / r;
+        const int step = n / Ls;
+        for (int w = threadIdx.x; w < cnt * nb; w += blockDim.x) {
+            const int row = w / nb, bi = w - row * nb;
+            const int blk = bi / L, k = bi - blk * L;
+            Cx<T>* p = buf + row * n + blk * Ls + k;
+            if (r == 2) {
+                Cx<T> y0 = p[0], y1 = cmul(p[L], twid(tw, k * step, inv));
+                p[0] = cadd(y0, y1);
+                p[L] = csub(y0, y1);
+            } else if (r == 4) {
+                Cx<T> y0 = p[0];
+                Cx<T> y1 = cmul(p[L], twid(tw, k * step, inv));
+                Cx<T> y2 = cmul(p[2 * L], twid(tw, 2 * k * step, inv));
+                Cx<T> y3 = cmul(p[3 * L], twid(tw, 3 * k * step, inv));
+                Cx<T> a0 = cadd(y0, y2), a1 = csub(y0, y2);
+                Cx<T> b0 = cadd(y1, y3), b1 = csub(y1, y3);
+                // -i (forward) / +i (inverse) times b1
+                Cx<T> jb1 = inv ? Cx<T>{-b1.y, b1.x} : Cx<T>{b1.y, -b1.x};
+                p[0] = cadd(a0, b0);
+                p[L] = cadd(a1, jb1);
+                p[2 * L] = csub(a0, b0);
+                p[3 * L] = csub(a1, jb1);
+            } else {  // r == 3
+                Cx<T> y0 = p[0];
+                Cx<T> y1 = cmul(p[L], twid(tw, k * step, inv));
+                Cx<T> y2 = cmul(p[2 * L], twid(tw, 2 * k * step, inv));
+                Cx<T> w3 = twid(tw, n / 3, inv);          // exp(-+2 pi i / 3)
+                Cx<T> w32 = Cx<T>{w3.x, -w3.y};           // its square = its conjugate
+                p[0] = cadd(y0, cadd(y1, y2));
+                p[L] = cadd(y0, cadd(cmul(y1, w3), cmul(y2, w32)));
+                p[2 * L] = cadd(y0, cadd(cmul(y1, w32), cmul(y2, w3)));
+            }
+        }
+        __syncthreads();
+        L = Ls;
+    }
+}
+
+// 2-D FFT of a global n x n complex buffer in place (rows then columns), or
+// one direction only (dir bit 1 = rows, bit 2 = columns).  `smem` holds a
+// chunk; `tw` and `rev` are in shared memory.
+template <typename T>
+__device__ void fft2_pass(Cx<T>* g, int n, const int* rad, int nrad, const Cx<T>* tw, const int* rev,
+                          Cx<T>* smem, int chunk, bool inv, bool cols) {
+    for (int c0 = 0; c0 < n; c0 += chunk) {
+        const int cnt = min(chunk, n - c0);
+        // load with digit reversal: seq q position p <- element rev[p]
+        for (int w = threadIdx.x; w < cnt * n; w += blockDim.x) {
+            if (!cols) {
+                const int q = w / n, p = w - q * n;
+                smem[q * n + p] = g[(c0 + q) * n + rev[p]];
+            } else {
+                const int p = w / cnt, q = w - p * cnt;
+                smem[q * n + p] = g[rev[p] * n + c0 + q];
+            }
+        }
+        __syncthreads();
+        fft_seq_smem<T>(smem, cnt, n, rad, nrad, tw, inv);
+        for (int w = threadIdx.x; w < cnt * n; w += blockDim.x) {
+            if (!cols) {
+                const int q = w / n, p = w - q * n;
+                g[(c0 + q) * n + p] = smem[q * n + p];
+            } else {
+                const int p = w / cnt, q = w - p * cnt;
+                g[p * n + c0 + q] = smem[q * n + p];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T>
+__device__ void fft2(Cx<T>* g, int n, const int* rad, int nrad, const Cx<T>* tw, const int* rev,
+                     Cx<T>* smem, int chunk, bool inv) {
+    fft2_pass<T>(g, n, rad, nrad, tw, rev, smem, chunk, inv, false);
+    fft2_pass<T>(g, n, rad, nrad, tw, rev, smem, chunk, inv, true);
+}
+
+// numpy fftfreq(n)[i] in cycles per pixel
+__device__ __forceinline__ double fftfreq(int i, int n) {
+    return (double)(i < (n + 1) / 2 ? i : i - n) / n;
+}
+
+// sqrt(P(k)) and d sqrt(P)/d theta for the family (Eq. 4 and its stand-ins)
+__device__ __forceinline__ double sqrtP_and_grad(int family, const double* ps, double k, double* g) {
+    if (family == 0) {            // A k^-beta, zero mode removed
+        if (k == 0.0) { g[0] = g[1] = 0.0; return 0.0; }
+        double A = ps[0], be = ps[1];
+        double sp = sqrt(A * pow(k, -be));
+        g[0] = sp / (2.0 * A);
+        g[1] = -0.5 * log(k) * sp;
+        return sp;
+    }
+    if (family == 1) {            // A / (1 + (k/k0)^2)^2
+        double A = ps[0], k0 = ps[1];
+        double u = 1.0 + (k / k0) * (k / k0);
+        double sp = sqrt(A) / u;
+        g[0] = sp / (2.0 * A);
+        g[1] = sqrt(A) * 2.0 * k * k / (k0 * k0 * k0) / (u * u);
+        return sp;
+    }
+    // Eq. 4: sigma^2 4 pi n (2n/zeta^2)^n (2n/zeta^2 + k^2)^-(n+1)
+    double sg = ps[0], nn = ps[1], ze = ps[2];
+    double a = 2.0 * nn / (ze * ze);
+    double logP = 2.0 * log(sg) + log(4.0 * 3.14159265358979323846 * nn) + nn * log(a)
+                  - (nn + 1.0) * log(a + k * k);
+    double sp = exp(0.5 * logP);
+    g[0] = sp / sg;
+    g[1] = 0.5 * sp * (1.0 / nn + log(a) + 1.0 - log(a + k * k) - (nn + 1.0) * a / (nn * (a + k * k)));
+    g[2] = 0.5 * sp * (-2.0 * nn / ze + 2.0 * (nn + 1.0) * a / (ze * (a + k * k)));
+    return sp;
+}
+
+__device__ __forceinline__ int n_family(int family) { return family == 2 ? 3 : 2; }
+
+// ln(phi_sp(x) s0) without underflow, and sigma(x)/phi_sp(x)
+template <typename T>
+__device__ __forceinline__ T log_sp_s0(T x) {
+    const T ls0 = T(-4.605170185988091);      // ln 0.01
+    if (x < T(-30)) return x + ls0;
+    T sp = (x > T(0) ? x : T(0)) + r_log1p(r_exp(-r_abs(x)));
+    return r_log(sp) + ls0;
+}
+template <typename T>
+__device__ __forceinline__ T sig_over_sp(T x) {
+    if (x < T(-30)) return T(1);
+    T e = r_exp(-r_abs(x));
+    T sgm = x >= T(0) ? T(1) / (T(1) + e) : e / (T(1) + e);
+    T sp = (x > T(0) ? x : T(0)) + r_log1p(e);
+    return sgm / sp;
+}
+
+struct GPShared {
+    int rad[MAX_RADIX];
+};
+
+template <typename T>
+__device__ __forceinline__ void gp_setup(const EvalArgs& E, Cx<T>* tw_s, int* rev_s, int* rad_s) {
+    const int n = E.n_src;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        tw_s[i] = Cx<T>{(T)E.tw[2 * i], (T)E.tw[2 * i + 1]};
+        rev_s[i] = E.digrev[i];
+    }
+    if (threadIdx.x < MAX_RADIX) rad_s[threadIdx.x] = E.rad[threadIdx.x];
+    __syncthreads();
+}
+
+// S6: f = Re F^-1(sqrt(P) F(w)) (1/N^2 on the inverse), s* = (phi_sp(f/s0) s0)^alpha
+template <typename T>
+__global__ void __launch_bounds__(GP_NT) k_gp_source(const __grid_constant__ Batch B) {
+    const EvalArgs& E = B.e[blockIdx.x];
+    const int n = E.n_src, n2 = n * n;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Cx<T>* sm = reinterpret_cast<Cx<T>*>(smem_raw);
+    __shared__ Cx<T> tw_s[256];
+    __shared__ int rev_s[256];
+    __shared__ int rad_s[MAX_RADIX];
+    gp_setup<T>(E, tw_s, rev_s, rad_s);
+    const int chunk = max(1, min(n, (int)(GP_SMEM / sizeof(Cx<T>)) / n));
+    Cx<T>* W = reinterpret_cast<Cx<T>*>(E.cbufA);
+    const T* w = reinterpret_cast<const T*>(E.latents);
+    for (int i = threadIdx.x; i < n2; i += blockDim.x) W[i] = Cx<T>{w[i], T(0)};
+    __syncthreads();
+    fft2<T>(W, n, rad_s, E.nrad, tw_s, rev_s, sm, chunk, false);
+    const int nf = n_family(E.family);
+    double psv[4];
+    for (int q = 0; q < nf; ++q) psv[q] = E.ps[q];
+    for (int i = threadIdx.x; i < n2; i += blockDim.x) {
+        const int ky = i / n, kx = i - ky * n;
+        const double fx = fftfreq(kx, n), fy = fftfreq(ky, n);
+        const double k = 2.0 * 3.14159265358979323846 * sqrt(fx * fx + fy * fy) / E.pitch;
+        double gdummy[3];
+        const T sp = (T)sqrtP_and_grad(E.family, psv, k, gdummy);
+        W[i] = Cx<T>{W[i].x * sp, W[i].y * sp};
+    }
+    __syncthreads();
+    fft2<T>(W, n, rad_s, E.nrad, tw_s, rev_s, sm, chunk, true);
+    const T alpha = (T)E.ps[nf];
+    const T inv_n2 = T(1) / T(n2);
+    T* fld = reinterpret_cast<T*>(E.fld);
+    T* src = reinterpret_cast<T*>(E.src);
+    T* so = reinterpret_cast<T*>(E.source_out);
+    for (int i = threadIdx.x; i < n2; i += blockDim.x) {
+        const T f = W[i].x * inv_n2;
+        const T s = r_exp(alpha * log_sp_s0<T>(f / T(0.01)));
+        fld[i] = f;
+        src[i] = s;
+        if (so) so[i] = s;
+    }
+}
+
+// S9 (source part): node gradients from the per-cell bilinear corner sums,
+// back through the softplus/alpha map and the FFT filter (self-adjoint) to the
+// latents; d log L / d sqrt(P_k) = Re(W_k conj(G_k)) / N^2 to the spectrum
+// parameters; d s*/d alpha to alpha_src.
+template <typename T>
+__global__ void __launch_bounds__(GP_NT) k_gp_adjoint(const __grid_constant__ Batch B) {
+    const EvalArgs& E = B.e[blockIdx.x];
+    const int n = E.n_src, n2 = n * n, nc = n - 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Cx<T>* sm = reinterpret_cast<Cx<T>*>(smem_raw);
+    __shared__ Cx<T> tw_s[256];
+    __shared__ int rev_s[256];
+    __shared__ int rad_s[MAX_RADIX];
+    __shared__ double red[GP_NT / 32];
+    gp_setup<T>(E, tw_s, rev_s, rad_s);
+    const int chunk = max(1, min(n, (int)(GP_SMEM / sizeof(Cx<T>)) / n));
+    Cx<T>* G = reinterpret_cast<Cx<T>*>(E.cbufA);
+    Cx<T>* W = reinterpret_cast<Cx<T>*>(E.cbufB);
+    const T* w = reinterpret_cast<const T*>(E.latents);
+    const T* fld = reinterpret_cast<const T*>(E.fld);
+    const T* src = reinterpret_cast<const T*>(E.src);
+    const int nf = n_family(E.family);
+    const T alpha = (T)E.ps[nf];
+    double ga = 0.0;
+    for (int i = threadIdx.x; i < n2; i += blockDim.x) {
+        const int j = i / n, ii = i - j * n;
+        double g = 0.0;
+        if (ii < nc && j < nc) g += E.corner[(j * nc + ii) * 4 + 0];
+        if (ii > 0 && j < nc) g += E.corner[(j * nc + ii - 1) * 4 + 1];
+        if (ii < nc && j > 0) g += E.corner[((j - 1) * nc + ii) * 4 + 2];
+        if (ii > 0 && j > 0) g += E.corner[((j - 1) * nc + ii - 1) * 4 + 3];
+        const T s = src[i];
+        const T x = fld[i] / T(0.01);
+        // d s / d f = alpha s (sigma(x)/phi_sp(x)) / s0
+        const T dsdf = alpha * s * sig_over_sp<T>(x) / T(0.01);
+        G[i] = Cx<T>{(T)g * dsdf, T(0)};
+        W[i] = Cx<T>{w[i], T(0)};
+        if (s > T(0)) ga += g * (double)s * (double)log_sp_s0<T>(x);
+    }
+    ga = block_sum<GP_NT>(ga, red);
+    __syncthreads();
+    fft2<T>(G, n, rad_s, E.nrad, tw_s, rev_s, sm, chunk, false);
+    fft2<T>(W, n, rad_s, E.nrad, tw_s, rev_s, sm, chunk, false);
+    double psv[4];
+    for (int q = 0; q < nf; ++q) psv[q] = E.ps[q];
+    double gp[3] = {0.0, 0.0, 0.0};
+    for (int i = threadIdx.x; i < n2; i += blockDim.x) {
+        const int ky = i / n, kx = i - ky * n;
+        const double fx = fftfreq(kx, n), fy = fftfreq(ky, n);
+        const double k = 2.0 * 3.14159265358979323846 * sqrt(fx * fx + fy * fy) / E.pitch;
+        double dsp[3] = {0.0, 0.0, 0.0};
+        const double sp = sqrtP_and_grad(E.family, psv, k, dsp);
+        const Cx<T> Gk = G[i], Wk = W[i];
+        const double d = ((double)Wk.x * (double)Gk.x + (double)Wk.y * (double)Gk.y) / (double)n2;
+        for (int q = 0; q < nf; ++q) gp[q] += d * dsp[q];
+        G[i] = Cx<T>{Gk.x * (T)sp, Gk.y * (T)sp};
+    }
+    for (int q = 0; q < nf; ++q) gp[q] = block_sum<GP_NT>(gp[q], red);
+    __syncthreads();
+    fft2<T>(G, n, rad_s, E.nrad, tw_s, rev_s, sm, chunk, true);
+    T* gl = reinterpret_cast<T*>(E.g_lat);
+    const T inv_n2 = T(1) / T(n2);
+    for (int i = threadIdx.x; i < n2; i += blockDim.x) gl[i] = G[i].x * inv_n2;
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < nf; ++q) E.g_ps[q] = gp[q];
+        E.g_ps[nf] = ga;
+    }
+}
+
+}  // namespace rtu

@@ -1,0 +1,122 @@
+// k_psf.cuh -- S8: PSF convolution ('same', zero padding) fused with the
+// Gaussian residual and the likelihood partial sums (Sec. 3.1, Sec. 4); its
+// adjoint (correlation with the PSF); the per-evaluation final reductions.
+#pragma once
+#include "rtu_internal.cuh"
+
+namespace rtu {
+
+constexpr int PSF_NT = PSF_T * PSF_T;
+constexpr int PSF_MAXK = 31;
+constexpr int PSF_IN = PSF_T + PSF_MAXK - 1;
+
+__device__ __forceinline__ void psf_tile_of(const EvalArgs& E, int tile, int& ti, int& tj) {
+    const int nt = (E.n_img + PSF_T - 1) / PSF_T;
+    tj = tile / nt;
+    ti = tile - tj * nt;
+}
+
+// m[j,i] = sum_{b,a} psf[b,a] img[j-(b-c), i-(a-c)];  resid = (d - m)/sigma^2;
+// per-CTA sums of r^2 (all pixels) and r^2 in the mask, r = (d - m)/sigma.
+template <typename T>
+__global__ void __launch_bounds__(PSF_NT) k_psf_like(const __grid_constant__ Batch B) {
+    const int ev = find_eval(B, blockIdx.x);
+    const EvalArgs& E = B.e[ev];
+    const int tile = blockIdx.x - B.tile0[ev];
+    __shared__ T in[PSF_IN][PSF_IN + 1];
+    __shared__ T kp[PSF_MAXK * PSF_MAXK];
+    __shared__ double red[2][PSF_NT / 32];
+    const int K = E.psf_k, c = (K - 1) / 2, n = E.n_img;
+    int ti, tj;
+    psf_tile_of(E, tile, ti, tj);
+    const int i0 = ti * PSF_T, j0 = tj * PSF_T;
+    const T* img = reinterpret_cast<const T*>(E.img);
+    const T* psf = reinterpret_cast<const T*>(E.psf);
+    for (int w = threadIdx.x; w < K * K; w += PSF_NT) kp[w] = psf[w];
+    const int W = PSF_T + 2 * c;
+    for (int w = threadIdx.x; w < W * W; w += PSF_NT) {
+        const int r = w / W, q = w - r * W;
+        const int gj = j0 - c + r, gi = i0 - c + q;
+        in[r][q] = (gj >= 0 && gj < n && gi >= 0 && gi < n) ? img[gj * n + gi] : T(0);
+    }
+    __syncthreads();
+    const int tx = threadIdx.x % PSF_T, ty = threadIdx.x / PSF_T;
+    const int i = i0 + tx, j = j0 + ty;
+    double r2 = 0.0, r2m = 0.0;
+    if (i < n && j < n) {
+        T m = T(0);
+        for (int b = 0; b < K; ++b)
+            for (int a = 0; a < K; ++a) m += kp[b * K + a] * in[ty - b + 2 * c][tx - a + 2 * c];
+        const T d = reinterpret_cast<const T*>(E.data)[j * n + i];
+        const T isg = T(1) / T(E.sigma);
+        const T r = (d - m) * isg;
+        reinterpret_cast<T*>(E.resid)[j * n + i] = r * isg;
+        if (E.model_out) reinterpret_cast<T*>(E.model_out)[j * n + i] = m;
+        r2 = (double)r * (double)r;
+        r2m = E.mask[j * n + i] ? r2 : 0.0;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        r2 += __shfl_down_sync(0xffffffffu, r2, o);
+        r2m += __shfl_down_sync(0xffffffffu, r2m, o);
+    }
+    if ((threadIdx.x & 31) == 0) { red[0][threadIdx.x >> 5] = r2; red[1][threadIdx.x >> 5] = r2m; }
+    __syncthreads();
+    if (threadIdx.x < 2) {
+        double s = 0.0;
+        for (int w = 0; w < PSF_NT / 32; ++w) s += red[threadIdx.x][w];
+        E.lpart[tile * 2 + threadIdx.x] = s;
+    }
+}
+
+// log L = -1/2 sum r^2 - N log(sigma sqrt(2 pi)); chi^2_img = sum_mask r^2 / N_mask
+__global__ void __launch_bounds__(256) k_like_final(const __grid_constant__ Batch B) {
+    const EvalArgs& E = B.e[blockIdx.x];
+    if (threadIdx.x == 0 && E.stats) {
+        double s = 0.0, sm = 0.0;
+        for (int t = 0; t < E.n_cta_p; ++t) { s += E.lpart[2 * t]; sm += E.lpart[2 * t + 1]; }
+        const double npx = (double)E.n_img * E.n_img;
+        E.stats[0] = -0.5 * s - npx * log(E.sigma * sqrt(2.0 * 3.14159265358979323846));
+        E.stats[1] = sm / (E.n_mask > 0 ? E.n_mask : 1);
+        E.stats[2] = E.n_mask;
+        E.stats[3] = (double)(*E.flags);
+    }
+    if (E.hist_out) {
+        const int nc = (E.n_src - 1) * (E.n_src - 1);
+        for (int i = threadIdx.x; i < nc; i += blockDim.x) E.hist_out[i] = E.ccount[i];
+    }
+}
+
+// d L / d img[p,q] = dlogL * sum_{b,a} psf[b,a] resid[p+b-c, q+a-c]
+template <typename T>
+__global__ void __launch_bounds__(PSF_NT) k_psf_adj(const __grid_constant__ Batch B) {
+    const int ev = find_eval(B, blockIdx.x);
+    const EvalArgs& E = B.e[ev];
+    const int tile = blockIdx.x - B.tile0[ev];
+    __shared__ T in[PSF_IN][PSF_IN + 1];
+    __shared__ T kp[PSF_MAXK * PSF_MAXK];
+    const int K = E.psf_k, c = (K - 1) / 2, n = E.n_img;
+    int ti, tj;
+    psf_tile_of(E, tile, ti, tj);
+    const int i0 = ti * PSF_T, j0 = tj * PSF_T;
+    const T* res = reinterpret_cast<const T*>(E.resid);
+    const T* psf = reinterpret_cast<const T*>(E.psf);
+    for (int w = threadIdx.x; w < K * K; w += PSF_NT) kp[w] = psf[w];
+    const int W = PSF_T + 2 * c;
+    for (int w = threadIdx.x; w < W * W; w += PSF_NT) {
+        const int r = w / W, q = w - r * W;
+        const int gj = j0 - c + r, gi = i0 - c + q;
+        in[r][q] = (gj >= 0 && gj < n && gi >= 0 && gi < n) ? res[gj * n + gi] : T(0);
+    }
+    __syncthreads();
+    const int tx = threadIdx.x % PSF_T, ty = threadIdx.x / PSF_T;
+    const int i = i0 + tx, j = j0 + ty;
+    if (i < n && j < n) {
+        T g = T(0);
+        for (int b = 0; b < K; ++b)
+            for (int a = 0; a < K; ++a) g += kp[b * K + a] * in[ty + b][tx + a];
+        const T sc = E.dlogL ? (T)(*E.dlogL) : T(1);
+        reinterpret_cast<T*>(E.gimg)[j * n + i] = g * sc;
+    }
+}
+
+}  // namespace rtu

@@ -1,0 +1,389 @@
+// rtu_host.cu -- the C ABI (include/rtu.h): workspace layout, system creation
+// and the per-step batched launches.  Host code allocates nothing on the
+// device; every buffer is carved out of the caller's workspace.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "rtu.h"
+#include "rtu_internal.cuh"
+#include "k_grid.cuh"
+#include "k_gp.cuh"
+#include "k_render.cuh"
+#include "k_psf.cuh"
+#include "k_adj.cuh"
+
+using namespace rtu;
+
+static_assert(sizeof(Batch) <= 32000, "batch descriptor must fit the kernel-parameter limit");
+
+namespace {
+
+thread_local std::string g_err;
+
+rtu_status fail(rtu_status code, const std::string& msg) {
+    g_err = msg;
+    return code;
+}
+
+size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
+
+bool factor_radices(int n, std::vector<int>& rad) {
+    rad.clear();
+    while (n % 4 == 0) { rad.push_back(4); n /= 4; }
+    while (n % 2 == 0) { rad.push_back(2); n /= 2; }
+    while (n % 3 == 0) { rad.push_back(3); n /= 3; }
+    return n == 1 && (int)rad.size() <= MAX_RADIX;
+}
+
+// position p holds input element rev(p) for the in-place DIT order used by
+// fft_seq_smem: p = sum_s j_s L_{s-1} -> rev = j_S + r_S j_{S-1} + r_S r_{S-1} j_{S-2} + ...
+std::vector<int> digit_reversal(int n, const std::vector<int>& rad) {
+    std::vector<int> rev(n);
+    const int S = (int)rad.size();
+    for (int p = 0; p < n; ++p) {
+        std::vector<int> js(S);
+        int q = p;
+        for (int s = 0; s < S; ++s) { js[s] = q % rad[s]; q /= rad[s]; }
+        int v = 0, w = 1;
+        for (int s = S - 1; s >= 0; --s) { v += js[s] * w; w *= rad[s]; }
+        rev[p] = v;
+    }
+    return rev;
+}
+
+struct Sizes {
+    int nm_max, n_cta_c_max, n_cta_r, n_cta_p, K, ncell, n_rays, nacc, nl, tb;
+};
+
+Sizes sizes_of(const rtu_system_desc& d) {
+    Sizes z;
+    z.nm_max = d.n_img * d.n_img;
+    z.n_cta_c_max = (z.nm_max + CTA_C - 1) / CTA_C;
+    z.n_cta_r = (d.n_img * d.n_img + CTA_R - 1) / CTA_R;
+    const int tiles = (d.n_img + PSF_T - 1) / PSF_T;
+    z.n_cta_p = tiles * tiles;
+    z.K = d.n_nodes + 2;
+    z.ncell = (d.n_src - 1) * (d.n_src - 1);
+    z.n_rays = d.n_img * d.n_img * d.s_super * d.s_super;
+    const int nsub = d.sub_kind ? d.n_sub : 0;
+    z.nacc = NACC_FIX + 4 * z.K + 5 * nsub;
+    z.nl = 8 + 5 * nsub;
+    z.tb = d.precision == RTU_F64 ? 8 : 4;
+    return z;
+}
+
+// per-slot layout; returns bytes.  If base != nullptr fills the slot pointers.
+size_t slot_layout(const rtu_system_desc& d, char* base, EvalArgs* e) {
+    const Sizes z = sizes_of(d);
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t at = o; o = align_up(o + bytes); return base ? base + at : nullptr; };
+    char* p;
+    p = take((size_t)2 * z.nm_max * 8);               if (e) e->beta = (double*)p;
+    p = take((size_t)z.n_cta_c_max * 8 * 8);          if (e) e->cpart = (double*)p;
+    p = take((size_t)z.n_cta_c_max * 2 * 8);          if (e) e->cpart2 = (double*)p;
+    p = take((size_t)z.n_cta_c_max * z.nl * 8);       if (e) e->cadj = (double*)p;
+    p = take((size_t)2 * HB * 4);                     if (e) e->hist = (int*)p;
+    p = take((size_t)tr_size(z.K) * 8);               if (e) e->trd = (double*)p;
+    p = take((size_t)tr_size(z.K) * 4);               if (e) e->trf = (float*)p;
+    p = take((size_t)4 * MAXM * 4);                   if (e) e->sel_idx = (int*)p;
+    p = take((size_t)4 * MAXM * 8);                   if (e) e->sel_val = (double*)p;
+    p = take((size_t)(TADJ_SEL + 4 * MAXM) * 8);      if (e) e->tadj = (double*)p;
+    const size_t n2 = (size_t)d.n_src * d.n_src;
+    p = take(n2 * 2 * z.tb);                          if (e) e->cbufA = p;
+    p = take(n2 * 2 * z.tb);                          if (e) e->cbufB = p;
+    p = take(n2 * z.tb);                              if (e) e->fld = p;
+    p = take(n2 * z.tb);                              if (e) e->src = p;
+    const size_t ni = (size_t)d.n_img * d.n_img;
+    p = take(ni * z.tb);                              if (e) e->img = p;
+    p = take(ni * z.tb);                              if (e) e->resid = p;
+    p = take(ni * z.tb);                              if (e) e->gimg = p;
+    p = take((size_t)z.n_cta_p * 2 * 8);              if (e) e->lpart = (double*)p;
+    p = take((size_t)z.n_rays * 4);                   if (e) e->cell = (int*)p;
+    p = take((size_t)(2 * z.ncell + 1) * 4);          if (e) e->ccount = (int*)p;
+    p = take((size_t)z.ncell * 4);                    if (e) e->cursor = (int*)p;
+    p = take((size_t)z.n_rays * 4 * z.tb);            if (e) e->rec = p;
+    p = take((size_t)z.ncell * 4 * 8);                if (e) e->corner = (double*)p;
+    p = take((size_t)z.n_cta_r * z.nacc * 8);         if (e) e->apart = (double*)p;
+    p = take(16);                                     if (e) e->flags = (int*)p;
+    return o;
+}
+
+size_t static_layout(const rtu_system_desc& d, char* base, int** cidx, double** tw, int** rev) {
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t at = o; o = align_up(o + bytes); return base ? base + at : nullptr; };
+    char* p = take((size_t)d.n_img * d.n_img * 4); if (cidx) *cidx = (int*)p;
+    p = take((size_t)2 * d.n_src * 8);             if (tw) *tw = (double*)p;
+    p = take((size_t)d.n_src * 4);                 if (rev) *rev = (int*)p;
+    return o;
+}
+
+const char* check_desc(const rtu_system_desc* d) {
+    if (!d) return "desc is null";
+    if (d->n_img < 2 || d->n_img > 4096) return "n_img must be in [2, 4096]";
+    if (d->s_super < 1 || d->s_super > 8) return "s_super must be in [1, 8]";
+    std::vector<int> rad;
+    if (d->n_src < 4 || d->n_src > 256 || !factor_radices(d->n_src, rad)) return "n_src must be 2^a 3^b in [4, 256]";
+    if (d->psf_k < 1 || d->psf_k > 31 || d->psf_k % 2 == 0) return "psf_k must be odd in [1, 31]";
+    if (d->profile != RTU_SIE && d->profile != RTU_EPL) return "profile must be RTU_SIE or RTU_EPL";
+    if (d->sub_kind < 0 || d->sub_kind > 2) return "bad sub_kind";
+    if (d->n_sub < 0 || d->n_sub > RTU_MAX_SUB) return "n_sub must be in [0, 16]";
+    if (d->ps_family < 0 || d->ps_family > 2) return "bad ps_family";
+    if (d->precision != RTU_F32 && d->precision != RTU_F64) return "precision must be RTU_F32 or RTU_F64";
+    if (d->n_nodes != d->degree + 1) return "this build supports n_nodes == degree + 1 (interpolating fit)";
+    if (d->n_nodes < 2 || d->n_nodes > MAXM) return "n_nodes must be in [2, 64]";
+    if (d->n_slots < 1) return "n_slots must be >= 1";
+    if (!(d->pix > 0) || !(d->src_pitch > 0) || !(d->sigma > 0)) return "pix, src_pitch, sigma must be > 0";
+    if (!d->data || !d->mask || !d->psf) return "data, mask and psf must be device pointers";
+    return nullptr;
+}
+
+std::once_flag g_attr_once;
+constexpr int SEL_SMEM = SEL_CAP * 12 + HB / 8;
+constexpr int MAX_DYN = 200 * 1024;
+
+void set_attributes() {
+    cudaFuncSetAttribute(k_select_fit, cudaFuncAttributeMaxDynamicSharedMemorySize, SEL_SMEM);
+    cudaFuncSetAttribute(k_gp_source<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, GP_SMEM);
+    cudaFuncSetAttribute(k_gp_source<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, GP_SMEM);
+    cudaFuncSetAttribute(k_gp_adjoint<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, GP_SMEM);
+    cudaFuncSetAttribute(k_gp_adjoint<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, GP_SMEM);
+    cudaFuncSetAttribute(k_render<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN);
+    cudaFuncSetAttribute(k_render<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN);
+    cudaFuncSetAttribute(k_render_adj<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN);
+    cudaFuncSetAttribute(k_render_adj<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN);
+}
+
+}  // namespace
+
+struct rtu_system {
+    rtu_system_desc d;
+    Sizes z;
+    int n_mask, n_cta_c, nrad;
+    int rad[MAX_RADIX];
+    int* cidx;
+    double* tw;
+    int* rev;
+    std::vector<EvalArgs> slot;   // workspace pointers of each slot
+};
+
+// ------------------------------------------------------------ zero kernel
+constexpr int ZERO_TILES = 16;
+__global__ void __launch_bounds__(256) k_zero(const __grid_constant__ Batch B, int with_cells) {
+    const int ev = find_eval(B, blockIdx.x);
+    const EvalArgs& E = B.e[ev];
+    const int tile = blockIdx.x - B.tile0[ev];
+    const int nh = 2 * HB;
+    const int ncell = (E.n_src - 1) * (E.n_src - 1);
+    const int tot = nh + (with_cells ? ncell : 0);
+    for (int i = tile * 256 + threadIdx.x; i < tot; i += ZERO_TILES * 256) {
+        if (i < nh) E.hist[i] = 0; else E.ccount[i - nh] = 0;
+    }
+    if (tile == 0 && threadIdx.x == 0) *E.flags = 0;
+}
+
+extern "C" {
+
+size_t rtu_workspace_size(const rtu_system_desc* d) {
+    if (check_desc(d)) return 0;
+    return static_layout(*d, nullptr, nullptr, nullptr, nullptr) + (size_t)d->n_slots * slot_layout(*d, nullptr, nullptr) + 256;
+}
+
+rtu_status rtu_system_create(const rtu_system_desc* d, void* ws, size_t ws_bytes, rtu_system** out) {
+    if (!out) return fail(RTU_E_ARG, "out is null");
+    *out = nullptr;
+    if (const char* m = check_desc(d)) return fail(RTU_E_ARG, m);
+    if (!ws) return fail(RTU_E_WORKSPACE, "workspace is null");
+    if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return fail(RTU_E_WORKSPACE, "workspace must be 256-byte aligned");
+    if (ws_bytes < rtu_workspace_size(d)) return fail(RTU_E_WORKSPACE, "workspace smaller than rtu_workspace_size()");
+    std::call_once(g_attr_once, set_attributes);
+    rtu_system* s = new rtu_system();
+    s->d = *d;
+    s->z = sizes_of(*d);
+    std::vector<int> rad;
+    factor_radices(d->n_src, rad);
+    s->nrad = (int)rad.size();
+    for (int i = 0; i < MAX_RADIX; ++i) s->rad[i] = i < s->nrad ? rad[i] : 1;
+    char* base = static_cast<char*>(ws);
+    const size_t st = static_layout(*d, base, &s->cidx, &s->tw, &s->rev);
+    // arc-mask pixel list (the CDF uses observed-pixel centres inside the mask)
+    const size_t npx = (size_t)d->n_img * d->n_img;
+    std::vector<uint8_t> mask(npx);
+    cudaError_t ce = cudaMemcpy(mask.data(), d->mask, npx, cudaMemcpyDeviceToHost);
+    if (ce != cudaSuccess) { delete s; return fail(RTU_E_CUDA, std::string("mask copy: ") + cudaGetErrorString(ce)); }
+    std::vector<int> idx;
+    for (size_t i = 0; i < npx; ++i) if (mask[i]) idx.push_back((int)i);
+    if (idx.size() < 2) { delete s; return fail(RTU_E_ARG, "the arc mask must hold at least 2 pixels"); }
+    s->n_mask = (int)idx.size();
+    s->n_cta_c = (s->n_mask + CTA_C - 1) / CTA_C;
+    std::vector<double> tw(2 * d->n_src);
+    for (int m = 0; m < d->n_src; ++m) {
+        const double ang = -2.0 * M_PI * m / d->n_src;
+        tw[2 * m] = std::cos(ang);
+        tw[2 * m + 1] = std::sin(ang);
+    }
+    std::vector<int> rev = digit_reversal(d->n_src, rad);
+    if ((ce = cudaMemcpy(s->cidx, idx.data(), idx.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (ce = cudaMemcpy(s->tw, tw.data(), tw.size() * 8, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (ce = cudaMemcpy(s->rev, rev.data(), rev.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess) {
+        delete s;
+        return fail(RTU_E_CUDA, std::string("table upload: ") + cudaGetErrorString(ce));
+    }
+    const size_t per = slot_layout(*d, nullptr, nullptr);
+    s->slot.resize(d->n_slots);
+    for (int k = 0; k < d->n_slots; ++k) {
+        EvalArgs e;
+        memset(&e, 0, sizeof(e));
+        slot_layout(*d, base + st + (size_t)k * per, &e);
+        s->slot[k] = e;
+    }
+    *out = s;
+    return RTU_OK;
+}
+
+rtu_status rtu_system_destroy(rtu_system* s) {
+    delete s;
+    return RTU_OK;
+}
+
+const char* rtu_last_error(void) { return g_err.c_str(); }
+const char* rtu_version(void) { return "rtu-b300 0.1 (sm_103a)"; }
+
+}  // extern "C"
+
+namespace {
+
+rtu_status fill_args(rtu_system* s, const rtu_eval& v, EvalArgs& e) {
+    if (v.slot < 0 || v.slot >= s->d.n_slots) return fail(RTU_E_ARG, "eval slot out of range");
+    if (!v.lens || !v.latents || !v.ps) return fail(RTU_E_ARG, "lens, latents and ps must be set");
+    e = s->slot[v.slot];
+    const rtu_system_desc& d = s->d;
+    e.n_img = d.n_img; e.s = d.s_super; e.n_src = d.n_src; e.psf_k = d.psf_k;
+    e.profile = d.profile; e.sub_kind = d.sub_kind; e.n_sub = d.n_sub; e.family = d.ps_family;
+    e.n_nodes = d.n_nodes; e.degree = d.degree; e.n_mask = s->n_mask; e.f64 = d.precision == RTU_F64;
+    e.nrad = s->nrad; e.n_cta_c = s->n_cta_c; e.n_cta_r = s->z.n_cta_r; e.n_cta_p = s->z.n_cta_p;
+    for (int i = 0; i < MAX_RADIX; ++i) e.rad[i] = s->rad[i];
+    e.pix = d.pix; e.pitch = d.src_pitch; e.sigma = d.sigma;
+    e.data = d.data; e.mask = d.mask; e.psf = d.psf;
+    e.centre_idx = s->cidx; e.tw = s->tw; e.digrev = s->rev;
+    e.lens = v.lens; e.latents = v.latents; e.ps = v.ps; e.dlogL = v.dlogL;
+    e.stats = v.stats; e.model_out = v.model; e.image_out = v.image; e.source_out = v.source;
+    e.cdf_out = v.cdf; e.hist_out = v.ray_hist;
+    e.g_lat = v.g_latents; e.g_lens = v.g_lens; e.g_ps = v.g_ps;
+    return RTU_OK;
+}
+
+typedef int (*TileFn)(const EvalArgs&);
+
+template <typename Kern, typename... Extra>
+rtu_status launch(Kern kern, Batch& B, TileFn tiles, int threads, size_t smem, cudaStream_t st,
+                  Extra... extra) {
+    int tot = 0;
+    for (int i = 0; i < B.n; ++i) { B.tile0[i] = tot; tot += tiles(B.e[i]); }
+    B.tile0[B.n] = tot;
+    if (tot == 0) return RTU_OK;
+    kern<<<tot, threads, smem, st>>>(B, extra...);
+    cudaError_t ce = cudaGetLastError();
+    if (ce != cudaSuccess) return fail(RTU_E_CUDA, std::string("launch: ") + cudaGetErrorString(ce));
+    return RTU_OK;
+}
+
+int t_one(const EvalArgs&) { return 1; }
+int t_zero(const EvalArgs&) { return ZERO_TILES; }
+int t_centre(const EvalArgs& e) { return e.n_cta_c; }
+int t_render(const EvalArgs& e) { return e.n_cta_r; }
+int t_psf(const EvalArgs& e) { return e.n_cta_p; }
+int t_cells(const EvalArgs& e) {
+    const int nc = (e.n_src - 1) * (e.n_src - 1);
+    return (nc + GATHER_NT / 32 - 1) / (GATHER_NT / 32);
+}
+
+enum Phase { PH_GRID = 1, PH_FORWARD = 2, PH_ADJOINT = 4 };
+
+template <typename T>
+rtu_status run_chunk(Batch& B, int phase, cudaStream_t st) {
+    rtu_status r;
+    int max_n2 = 0, max_s2 = 0, any_sub = 0, maxK = 0;
+    for (int i = 0; i < B.n; ++i) {
+        max_n2 = std::max(max_n2, B.e[i].n_src * B.e[i].n_src);
+        max_s2 = std::max(max_s2, B.e[i].s * B.e[i].s);
+        any_sub |= (B.e[i].sub_kind && B.e[i].n_sub > 0);
+        maxK = std::max(maxK, B.e[i].n_nodes + 2);
+    }
+    const size_t grid_bytes = align_up((size_t)max_n2 * sizeof(T), 128);
+    if (phase & (PH_GRID | PH_FORWARD)) {
+        if ((r = launch(k_zero, B, t_zero, 256, 0, st, (phase & PH_FORWARD) ? 1 : 0))) return r;
+        if ((r = launch(k_trace_centres, B, t_centre, CTA_C, 0, st))) return r;
+        if ((r = launch(k_centre_hist, B, t_centre, CTA_C, 0, st))) return r;
+        if ((r = launch(k_select_fit, B, t_one, SEL_NT, SEL_SMEM, st))) return r;
+    }
+    if (phase & PH_FORWARD) {
+        if ((r = launch(k_gp_source<T>, B, t_one, GP_NT, GP_SMEM, st))) return r;
+        if (grid_bytes > MAX_DYN) return fail(RTU_E_ARG, "source grid too large for shared memory");
+        if ((r = launch(k_render<T>, B, t_render, CTA_R, grid_bytes, st))) return r;
+        if ((r = launch(k_psf_like<T>, B, t_psf, PSF_NT, 0, st))) return r;
+        if ((r = launch(k_like_final, B, t_one, 256, 0, st))) return r;
+    }
+    if (phase & PH_ADJOINT) {
+        if ((r = launch(k_psf_adj<T>, B, t_psf, PSF_NT, 0, st))) return r;
+        if ((r = launch(k_scan_cells, B, t_one, SCAN_NT, 0, st))) return r;
+        size_t adj = grid_bytes + (size_t)(CTA_R / 32) * 4 * maxK * 8 +
+                     (any_sub ? (size_t)CTA_R * max_s2 * 2 * sizeof(T) : 0);
+        if (adj > MAX_DYN) return fail(RTU_E_ARG, "adjoint shared memory exceeds the limit");
+        if ((r = launch(k_render_adj<T>, B, t_render, CTA_R, adj, st))) return r;
+        if ((r = launch(k_cell_gather<T>, B, t_cells, GATHER_NT, 0, st))) return r;
+        if ((r = launch(k_cdf_adj, B, t_one, 256, 0, st))) return r;
+        if ((r = launch(k_centre_adj<T>, B, t_centre, CTA_C, 0, st))) return r;
+        if ((r = launch(k_gp_adjoint<T>, B, t_one, GP_NT, GP_SMEM, st))) return r;
+        if ((r = launch(k_grad_final, B, t_one, 64, 0, st))) return r;
+    }
+    return RTU_OK;
+}
+
+rtu_status run(rtu_system* const* sys, const rtu_eval* ev, int n, int phase, void* stream) {
+    if (n < 0 || (n > 0 && (!sys || !ev))) return fail(RTU_E_ARG, "bad system/eval arrays");
+    if (n == 0) return RTU_OK;
+    const int prec = sys[0] ? sys[0]->d.precision : 0;
+    for (int i = 0; i < n; ++i) {
+        if (!sys[i]) return fail(RTU_E_ARG, "null system in batch");
+        if (sys[i]->d.precision != prec) return fail(RTU_E_ARG, "all systems of one call must share the precision");
+        if ((phase & PH_ADJOINT) && (!ev[i].g_latents || !ev[i].g_lens || !ev[i].g_ps))
+            return fail(RTU_E_ARG, "adjoint outputs g_latents, g_lens, g_ps must be set");
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    static thread_local Batch B;
+    for (int c0 = 0; c0 < n; c0 += MAXB) {
+        B.n = std::min(MAXB, n - c0);
+        for (int i = 0; i < B.n; ++i) {
+            rtu_status r = fill_args(sys[c0 + i], ev[c0 + i], B.e[i]);
+            if (r) return r;
+        }
+        rtu_status r = prec == RTU_F64 ? run_chunk<double>(B, phase, st) : run_chunk<float>(B, phase, st);
+        if (r) return r;
+    }
+    return RTU_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+rtu_status rtu_build_grid(rtu_system* const* sys, const rtu_eval* ev, int32_t n, void* stream) {
+    return run(sys, ev, n, PH_GRID, stream);
+}
+
+rtu_status rtu_forward(rtu_system* const* sys, const rtu_eval* ev, int32_t n, void* stream) {
+    return run(sys, ev, n, PH_FORWARD, stream);
+}
+
+rtu_status rtu_adjoint(rtu_system* const* sys, const rtu_eval* ev, int32_t n, void* stream) {
+    return run(sys, ev, n, PH_ADJOINT, stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,244 @@
+"""ctypes binding of the C ABI in ``include/rtu.h`` (argument marshalling only).
+
+Every step of the hot path runs in the CUDA kernels of ``librtu.so``; PyTorch
+supplies device memory and streams.  Importing this module on a machine
+without the built library raises immediately: there is no fallback.
+
+Names follow the ABI: ``rtu_build_grid``, ``rtu_forward``, ``rtu_adjoint``
+(and the batched ``Batch`` helper, the ``RTUForward`` autograd Function).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "librtu.so")
+
+RTU_F32, RTU_F64 = 0, 1
+RTU_SIE, RTU_EPL = 0, 1
+RTU_SUB_NONE, RTU_SUB_NFW, RTU_SUB_TNFW = 0, 1, 2
+RTU_PS_POWER_LAW, RTU_PS_MATERN_LIKE, RTU_PS_MATERN = 0, 1, 2
+STAT_LOGL, STAT_CHI2, STAT_NMASK, STAT_FLAGS = 0, 1, 2, 3
+W_NONMONOTONE, W_SELECT, W_TIMEOUT = 1, 2, 4
+N_STATS = 4
+N_PS = {RTU_PS_POWER_LAW: 2, RTU_PS_MATERN_LIKE: 2, RTU_PS_MATERN: 3}
+
+
+class RTUError(RuntimeError):
+    pass
+
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"librtu.so is not built at {LIB_PATH}: run `python -m paper_2606_30620_b300.build`"
+                      " (the CUDA path has no fallback)")
+_lib = ctypes.CDLL(LIB_PATH)
+
+
+class SystemDesc(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int32) for n in (
+        "n_img", "s_super", "n_src", "psf_k", "profile", "sub_kind", "n_sub", "ps_family",
+        "precision", "n_nodes", "degree", "n_slots")] + [
+        ("pix", ctypes.c_double), ("src_pitch", ctypes.c_double), ("sigma", ctypes.c_double),
+        ("data", ctypes.c_void_p), ("mask", ctypes.c_void_p), ("psf", ctypes.c_void_p)]
+
+
+class Eval(ctypes.Structure):
+    _fields_ = [("slot", ctypes.c_int32), ("pad_", ctypes.c_int32)] + [(n, ctypes.c_void_p) for n in (
+        "lens", "latents", "ps", "dlogL", "stats", "model", "image", "source", "cdf", "ray_hist",
+        "g_latents", "g_lens", "g_ps")]
+
+
+_lib.rtu_workspace_size.argtypes = [ctypes.POINTER(SystemDesc)]
+_lib.rtu_workspace_size.restype = ctypes.c_size_t
+_lib.rtu_system_create.argtypes = [ctypes.POINTER(SystemDesc), ctypes.c_void_p, ctypes.c_size_t,
+                                   ctypes.POINTER(ctypes.c_void_p)]
+_lib.rtu_system_create.restype = ctypes.c_int32
+_lib.rtu_system_destroy.argtypes = [ctypes.c_void_p]
+_lib.rtu_system_destroy.restype = ctypes.c_int32
+for _name in ("rtu_build_grid", "rtu_forward", "rtu_adjoint"):
+    getattr(_lib, _name).argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(Eval), ctypes.c_int32,
+                                     ctypes.c_void_p]
+    getattr(_lib, _name).restype = ctypes.c_int32
+_lib.rtu_last_error.restype = ctypes.c_char_p
+_lib.rtu_version.restype = ctypes.c_char_p
+
+EXPORTED = ("rtu_workspace_size", "rtu_system_create", "rtu_system_destroy", "rtu_build_grid",
+            "rtu_forward", "rtu_adjoint", "rtu_last_error", "rtu_version")
+
+
+def _check(rc: int, what: str):
+    if rc < 0:
+        raise RTUError(f"{what} failed ({rc}): {_lib.rtu_last_error().decode()}")
+
+
+def version() -> str:
+    return _lib.rtu_version().decode()
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+class System:
+    """One lens system: the caller-owned observation tensors plus its workspace."""
+
+    def __init__(self, data, mask, psf, sigma, pix, s_super, n_src, src_pitch, profile=RTU_SIE,
+                 ps_family=RTU_PS_POWER_LAW, sub_kind=RTU_SUB_NONE, n_sub=0, precision=RTU_F32,
+                 n_nodes=22, degree=21, n_slots=1, device="cuda"):
+        self.dtype = torch.float64 if precision == RTU_F64 else torch.float32
+        self.device = torch.device(device)
+        self.data = torch.as_tensor(data, dtype=self.dtype, device=self.device).contiguous()
+        self.mask = torch.as_tensor(mask, dtype=torch.uint8, device=self.device).contiguous()
+        self.psf = torch.as_tensor(psf, dtype=self.dtype, device=self.device).contiguous()
+        self.n_img = int(self.data.shape[0])
+        self.n_src = int(n_src)
+        self.s_super = int(s_super)
+        self.profile = int(profile)
+        self.ps_family = int(ps_family)
+        self.sub_kind = int(sub_kind)
+        self.n_sub = int(n_sub) if sub_kind else 0
+        self.n_slots = int(n_slots)
+        self.precision = int(precision)
+        self.n_nodes = int(n_nodes)
+        self.desc = SystemDesc(self.n_img, self.s_super, self.n_src, int(self.psf.shape[0]), self.profile,
+                               self.sub_kind, self.n_sub, self.ps_family, self.precision, int(n_nodes),
+                               int(degree), self.n_slots, float(pix), float(src_pitch), float(sigma),
+                               self.data.data_ptr(), self.mask.data_ptr(), self.psf.data_ptr())
+        nbytes = _lib.rtu_workspace_size(ctypes.byref(self.desc))
+        if nbytes == 0:
+            raise RTUError("invalid system description (rtu_workspace_size returned 0)")
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        base = self.workspace.data_ptr()
+        off = (-base) % 256
+        h = ctypes.c_void_p()
+        _check(_lib.rtu_system_create(ctypes.byref(self.desc), ctypes.c_void_p(base + off), nbytes,
+                                      ctypes.byref(h)), "rtu_system_create")
+        self.handle = h
+        self.n_lens = 8 + 5 * self.n_sub
+        self.n_ps = N_PS[self.ps_family] + 1
+        self.n_knots = self.n_nodes + 2
+
+    @classmethod
+    def from_mock(cls, m, precision=RTU_F32, n_slots=1, device="cuda"):
+        return cls(m.data, m.mask, m.psf, m.sigma, m.pix, m.s_super, m.n_src, m.src_pitch, m.profile,
+                   m.ps_family, m.sub_kind, 0 if m.subs is None else m.subs.shape[0], precision,
+                   n_slots=n_slots, device=device)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            _lib.rtu_system_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Binding:
+    """Device buffers of one evaluation (inputs, and outputs allocated on demand)."""
+
+    def __init__(self, system: System, lens, latents, ps, slot=0, want_model=False, want_image=False,
+                 want_source=False, want_cdf=False, want_hist=False, grads=True, dlogL=None):
+        dev, dt = system.device, system.dtype
+        self.system = system
+        self.slot = slot
+        self.lens = torch.as_tensor(lens, dtype=torch.float64, device=dev).contiguous().reshape(-1)
+        self.latents = torch.as_tensor(latents, dtype=dt, device=dev).contiguous()
+        self.ps = torch.as_tensor(ps, dtype=torch.float64, device=dev).contiguous()
+        if self.lens.numel() != system.n_lens:
+            raise ValueError(f"lens must hold {system.n_lens} values")
+        if self.latents.numel() != system.n_src ** 2:
+            raise ValueError("latents must hold n_src^2 values")
+        if self.ps.numel() != system.n_ps:
+            raise ValueError(f"ps must hold {system.n_ps} values")
+        self.dlogL = None if dlogL is None else torch.as_tensor(dlogL, dtype=torch.float64, device=dev)
+        self.stats = torch.zeros(N_STATS, dtype=torch.float64, device=dev)
+        n_img, n_src = system.n_img, system.n_src
+        self.model = torch.empty(n_img, n_img, dtype=dt, device=dev) if want_model else None
+        self.image = torch.empty(n_img, n_img, dtype=dt, device=dev) if want_image else None
+        self.source = torch.empty(n_src, n_src, dtype=dt, device=dev) if want_source else None
+        self.cdf = torch.empty(3 + 4 * system.n_knots, dtype=torch.float64, device=dev) if want_cdf else None
+        self.ray_hist = torch.empty((n_src - 1) ** 2, dtype=torch.int32, device=dev) if want_hist else None
+        if grads:
+            self.g_latents = torch.empty(n_src, n_src, dtype=dt, device=dev)
+            self.g_lens = torch.empty(system.n_lens, dtype=torch.float64, device=dev)
+            self.g_ps = torch.empty(system.n_ps, dtype=torch.float64, device=dev)
+        else:
+            self.g_latents = self.g_lens = self.g_ps = None
+
+    def as_struct(self) -> Eval:
+        return Eval(self.slot, 0, *[None if t is None else t.data_ptr() for t in (
+            self.lens, self.latents, self.ps, self.dlogL, self.stats, self.model, self.image, self.source,
+            self.cdf, self.ray_hist, self.g_latents, self.g_lens, self.g_ps)])
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _arrays(bindings):
+    n = len(bindings)
+    sys_arr = (ctypes.c_void_p * n)(*[b.system.handle.value for b in bindings])
+    ev_arr = (Eval * n)(*[b.as_struct() for b in bindings])
+    return sys_arr, ev_arr, n
+
+
+class Batch:
+    """Pre-marshalled argument arrays for repeated calls over the same bindings."""
+
+    def __init__(self, bindings):
+        self.bindings = list(bindings)
+        self.sys_arr, self.ev_arr, self.n = _arrays(self.bindings)
+
+    def build_grid(self, stream=None):
+        _check(_lib.rtu_build_grid(self.sys_arr, self.ev_arr, self.n, _stream_ptr(stream)), "rtu_build_grid")
+
+    def forward(self, stream=None):
+        _check(_lib.rtu_forward(self.sys_arr, self.ev_arr, self.n, _stream_ptr(stream)), "rtu_forward")
+
+    def adjoint(self, stream=None):
+        _check(_lib.rtu_adjoint(self.sys_arr, self.ev_arr, self.n, _stream_ptr(stream)), "rtu_adjoint")
+
+
+def rtu_build_grid(bindings, stream=None):
+    Batch(bindings).build_grid(stream)
+
+
+def rtu_forward(bindings, stream=None):
+    Batch(bindings).forward(stream)
+
+
+def rtu_adjoint(bindings, stream=None):
+    Batch(bindings).adjoint(stream)
+
+
+class RTUForward(torch.autograd.Function):
+    """log L(lens, latents, ps) of one system; backward runs rtu_adjoint, which
+    recomputes the rays instead of saving them."""
+
+    @staticmethod
+    def forward(ctx, system: System, lens, latents, ps):
+        b = Binding(system, lens.detach(), latents.detach(), ps.detach(), grads=True,
+                    dlogL=torch.ones(1, dtype=torch.float64, device=system.device))
+        Batch([b]).forward()
+        ctx.binding = b
+        return b.stats[STAT_LOGL].clone()
+
+    @staticmethod
+    def backward(ctx, g):
+        b = ctx.binding
+        b.dlogL.copy_(g.reshape(1).to(torch.float64))
+        Batch([b]).adjoint()
+        return None, b.g_lens.clone(), b.g_latents.clone(), b.g_ps.clone()
+
+
+def log_likelihood(system: System, lens, latents, ps):
+    return RTUForward.apply(system, lens, latents, ps)

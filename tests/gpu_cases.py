@@ -1,0 +1,73 @@
+"""Run one seeded input through the CUDA path and through the oracle."""
+import numpy as np
+import torch
+
+from oracle import rtu_oracle as O
+from tests import oracle_io
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, dtype=np.float64).ravel()
+    b = np.asarray(b, dtype=np.float64).ravel()
+    den = np.linalg.norm(b)
+    return float(np.linalg.norm(a - b) / (den if den > 0 else 1.0))
+
+
+def run_gpu(m, precision, want_grads=True, n_slots=1):
+    from paper_2606_30620_b300 import rtu
+    sysm = rtu.System.from_mock(m, precision=precision, n_slots=n_slots)
+    lens = m.lens if m.subs is None else np.concatenate([m.lens, m.subs.ravel()])
+    b = rtu.Binding(sysm, lens, m.latents, m.ps, want_model=True, want_image=True, want_source=True,
+                    want_cdf=True, want_hist=True, grads=want_grads)
+    batch = rtu.Batch([b])
+    batch.forward()
+    if want_grads:
+        batch.adjoint()
+    torch.cuda.synchronize()
+    out = dict(stats=b.stats.cpu().numpy(), model=b.model.cpu().numpy(), image=b.image.cpu().numpy(),
+               source=b.source.cpu().numpy(), cdf=b.cdf.cpu().numpy(), hist=b.ray_hist.cpu().numpy())
+    if want_grads:
+        out.update(g_latents=b.g_latents.cpu().numpy(), g_lens=b.g_lens.cpu().numpy(),
+                   g_ps=b.g_ps.cpu().numpy())
+    return out, sysm, b
+
+
+def run_oracle(m, grads=True):
+    s = oracle_io.system(m)
+    lens, lat, ps, subs = oracle_io.params(m)
+    if grads:
+        r = O.forward_adjoint(s, lens, lat, ps, subs)
+    else:
+        f = O.forward(s, lens, lat, ps, subs)
+        r = dict(logL=f["logL"], chi2=f["chi2"], model=f["model"], image=f["image"], flags=f["T"].flags)
+    T = O.build_grid(s, lens, subs)
+    src, _ = O.gp_source(s, lat, ps)
+    hist = O.ray_hist(s, lens, subs, T)
+    cdf = np.concatenate([T.mu.detach().numpy(), [float(T.sigma)], T.knots.detach().numpy().ravel(),
+                          T.slopes.detach().numpy().ravel()])
+    out = dict(logL=float(r["logL"]), chi2=float(r["chi2"]), model=r["model"].detach().numpy(),
+               image=r["image"].detach().numpy(), source=src.detach().numpy(), cdf=cdf,
+               hist=hist.numpy(), flags=T.flags)
+    if grads:
+        g_lens = r["g_lens"].numpy()
+        if subs is not None:
+            g_lens = np.concatenate([g_lens, r["g_subs"].numpy().ravel()])
+        out.update(g_latents=r["g_latents"].numpy(), g_lens=g_lens, g_ps=r["g_ps"].numpy())
+    return out
+
+
+def compare(g, o):
+    res = dict(
+        logL=abs(g["stats"][0] - o["logL"]) / abs(o["logL"]),
+        chi2=abs(g["stats"][1] - o["chi2"]) / abs(o["chi2"]),
+        cdf=rel_l2(g["cdf"], o["cdf"]),
+        source=rel_l2(g["source"], o["source"]),
+        image=rel_l2(g["image"], o["image"]),
+        model=rel_l2(g["model"], o["model"]),
+        hist_diff=int(np.abs(g["hist"].astype(np.int64) - o["hist"]).sum()),
+        flags=(int(g["stats"][3]), o["flags"]),
+    )
+    if "g_latents" in g and "g_latents" in o:
+        res.update(g_latents=rel_l2(g["g_latents"], o["g_latents"]), g_lens=rel_l2(g["g_lens"], o["g_lens"]),
+                   g_ps=rel_l2(g["g_ps"], o["g_ps"]))
+    return res
