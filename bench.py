@@ -1,0 +1,355 @@
+"""Benchmark of the RTU-grid hot path on one node (contract: one JSON line on rank 0).
+
+Workload (default): the FP32 forward+adjoint case -- 32 seeded mocks of a
+200x200 image at 0.05"/pix, 4x4 supersampling (640,000 rays each), elliptical
+power law + shear, 64x64 RTU grid, Matern-like P(k), 21x21 PSF.  One step is
+one batched pass of the whole hot path over all 32 mocks: build grid (centre
+trace, order statistics, fit), GP source, render with the rays-per-cell
+histogram, PSF + likelihood, and the full adjoint (gradients w.r.t. latents,
+lens and power-spectrum parameters).  value = forward+adjoint evaluations per
+second over the whole job (N ranks x 32 mocks per step).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With --impl reference the FP64 CPU oracle is timed on the host cores on a
+bounded sample of the same workload (the oracle is the reference of this
+build; there is no other implementation to run).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2606_30620_b300 import inputs as I  # noqa: E402
+
+N_MOCKS = 32
+SEED0 = 1000
+L2_BYTES = 126 * 1024 * 1024
+# recipe unit counts: 148 SMs x 128 FP32 lanes x 2 flop per FMA at the 2032 MHz maximum SM clock
+FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
+FALLBACK_HBM_GBS = 6400.0
+# algorithmic FP32 flops per supersampled ray ("Roofline accounting")
+FLOPS_FWD_RAY = 250.0
+FLOPS_ADJ_RAY = 3.0 * FLOPS_FWD_RAY
+
+
+def env_rank():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": FALLBACK_HBM_GBS}, "fallback"
+
+
+def make_mocks(rank, n=N_MOCKS):
+    return [I.config_c2(SEED0 + rank * n + k) for k in range(n)]
+
+
+def cpu_oracle_sample(mocks, budget_s=20.0, max_n=None):
+    """The oracle as it stands on the host cores: forward + gradient per mock until
+    the budget is spent (at least one mock)."""
+    from oracle import rtu_oracle as O
+    from tests import oracle_io
+    torch.set_num_threads(os.cpu_count() or 1)
+    t0 = time.perf_counter()
+    n = 0
+    for m in mocks:
+        s = oracle_io.system(m)
+        lens, lat, ps, subs = oracle_io.params(m)
+        O.forward_adjoint(s, lens, lat, ps, subs)
+        n += 1
+        if time.perf_counter() - t0 > budget_s or (max_n and n >= max_n):
+            break
+    dt = time.perf_counter() - t0
+    return n / dt, n, dt, torch.get_num_threads()
+
+
+def run_reference(args):
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return 0
+    mocks = make_mocks(0)
+    per = []
+    for _ in range(args.warmup if args.warmup < 1 else 1):
+        cpu_oracle_sample(mocks[:1], budget_s=0.0)
+    t_all = 0.0
+    n_all = 0
+    for k in range(args.steps):
+        v, n, dt, cores = cpu_oracle_sample(mocks[k % N_MOCKS:], budget_s=10.0, max_n=4)
+        per.append(dt / n)
+        t_all += dt
+        n_all += n
+    value = n_all / t_all
+    line = {"impl": "reference", "metric": "forward+adjoint evals/s", "value": value, "unit": "evals/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * t_all / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded mocks)",
+            "config": {"workload": "c2: 200x200 image 0.05\"/pix, 4x4 rays, EPL+shear, 64x64 RTU grid, "
+                                   "Matern-like P(k), 21x21 PSF, 32 seeded mocks",
+                       "sample": f"{n_all} mock forward+gradient evaluations"},
+            "cpu_baseline": {"value": value, "unit": "evals/s", "cores": torch.get_num_threads(), "kind": "oracle",
+                             "sample": f"{n_all} of the 32 mocks, FP64 oracle forward + autograd gradient"},
+            "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    rank, world, local = env_rank()
+    dist = world > 1
+    if dist:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2606_30620_b300 import rtu
+
+    mocks = make_mocks(rank, args.mocks)
+    systems = [rtu.System.from_mock(m, precision=rtu.RTU_F32, device=dev) for m in mocks]
+    n = len(mocks)
+    n2 = mocks[0].n_src ** 2
+    nps = mocks[0].ps.size
+    # packed inputs [lens(8) | ps(3)] as float64 and latents as float32; packed outputs
+    in_f64 = torch.empty(n, 8 + nps, dtype=torch.float64, device=dev)
+    in_lat = torch.empty(n, n2, dtype=torch.float32, device=dev)
+    out_f64 = torch.empty(n, 4 + 8 + nps, dtype=torch.float64, device=dev)
+    out_lat = torch.empty(n, n2, dtype=torch.float32, device=dev)
+    h_in_f64 = torch.tensor(np.stack([np.concatenate([m.lens, m.ps]) for m in mocks]), dtype=torch.float64).pin_memory()
+    h_in_lat = torch.tensor(np.stack([m.latents.ravel() for m in mocks]), dtype=torch.float32).pin_memory()
+    h_out_f64 = torch.empty_like(out_f64, device="cpu").pin_memory()
+    h_out_lat = torch.empty_like(out_lat, device="cpu").pin_memory()
+    in_f64.copy_(h_in_f64)
+    in_lat.copy_(h_in_lat)
+    binds = []
+    for k, s in enumerate(systems):
+        binds.append(rtu.Binding(s, in_f64[k, :8], in_lat[k].view(mocks[k].n_src, mocks[k].n_src),
+                                 in_f64[k, 8:], out={"stats": out_f64[k, :4], "g_lens": out_f64[k, 4:12],
+                                                     "g_ps": out_f64[k, 12:],
+                                                     "g_latents": out_lat[k].view(mocks[k].n_src, mocks[k].n_src)}))
+    batch = rtu.Batch(binds)
+    singles = [rtu.Batch([b]) for b in binds]
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        batch.forward(stream)
+        batch.adjoint(stream)
+
+    def step_single():
+        for b in singles:
+            b.forward(stream)
+            b.adjoint(stream)
+
+    def barrier():
+        if dist:
+            tdist.barrier()
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- device-timed region: K steps, L2 flushed between steps (untimed)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    barrier()
+    rtu.profile_report()          # clear
+    rtu.profile_enable(True)      # per-kernel CUDA events on the launching stream
+    with ClockSampler(local) as clk:
+        t_wall = time.perf_counter()
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            starts[i].record(stream)
+            step()
+            ends[i].record(stream)
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall
+    rtu.profile_enable(False)
+    kern = rtu.profile_report()
+    barrier()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    ms = sum(step_ms) / len(step_ms)
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        ms = float(t)
+    value = world * n / (ms / 1e3)
+
+    # ---- plain per-system path (one call per mock), same work
+    per_system_value = None
+    if not args.no_single:
+        for _ in range(2):
+            step_single()
+        torch.cuda.synchronize()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ks = max(1, min(args.steps, 5))
+        single_ms = []
+        for i in range(ks):
+            flush.fill_(float(i))
+            s0.record(stream)
+            step_single()
+            s1.record(stream)
+            torch.cuda.synchronize()
+            single_ms.append(s0.elapsed_time(s1))
+        per_system_value = n / (statistics.mean(single_ms) / 1e3)
+
+    # ---- end to end through the public API: pinned host params in, results out
+    torch.cuda.synchronize()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e_ms = []
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        e0.record(stream)
+        in_f64.copy_(h_in_f64, non_blocking=True)
+        in_lat.copy_(h_in_lat, non_blocking=True)
+        step()
+        h_out_f64.copy_(out_f64, non_blocking=True)
+        h_out_lat.copy_(out_lat, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e_ms.append(e0.elapsed_time(e1))
+    e2e = world * n / (statistics.mean(e_ms) / 1e3)
+    h2d = h_in_f64.numel() * 8 + h_in_lat.numel() * 4
+    d2h = h_out_f64.numel() * 8 + h_out_lat.numel() * 4
+
+    # ---- dominant kernel: average launch duration from the events of the timed region
+    top = max(kern.items(), key=lambda kv: kv[1][1])
+    ra_cnt, ra_tot = kern["k_render_adj"]
+    ra_ms = ra_tot / ra_cnt
+    kern_tot = sum(v[1] for v in kern.values())
+    launches = sum(v[0] for v in kern.values())
+
+    clocks = clk.summary()
+    if rank != 0:
+        if dist:
+            tdist.destroy_process_group()
+        return 0
+    peaks, peak_kind = measured_peaks()
+    rays = sum(m.n_rays for m in mocks)
+    achieved = FLOPS_ADJ_RAY * rays / (ra_ms / 1e3) / 1e12
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "render_adj_traffic.json")
+    if os.path.exists(tfile):
+        with open(tfile) as f:
+            traffic = json.load(f).get("bytes_per_launch")
+    # cpu baseline: the oracle on the host cores, a bounded sample of the same mocks
+    cpu_v, cpu_n, cpu_dt, cores = (cpu_oracle_sample(mocks, budget_s=args.cpu_budget) if not args.no_cpu
+                                   else (None, 0, 0.0, 0))
+    line = {
+        "metric": "forward+adjoint evals/s", "value": value, "unit": "evals/s", "n_gpus": world,
+        "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded mocks)",
+        "config": {"workload": "c2: 200x200 image 0.05\"/pix, 4x4 rays (640k per mock), EPL+shear, "
+                               f"64x64 RTU grid, Matern-like P(k), 21x21 PSF, {n} seeded mocks batched per step",
+                   "mocks_per_rank": n, "l2": "flushed between timed steps (256 MB write, untimed)",
+                   "parallelism": f"replicas x{world}", "wall_s_timed_loop": t_wall},
+        "e2e": {"value": e2e, "unit": "evals/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "kernels": {k: {"launches": c, "avg_ms": t / c, "share": t / kern_tot} for k, (c, t) in kern.items()},
+        "per_system_path": {"value": per_system_value, "unit": "evals/s",
+                            "note": "same 32 evaluations issued as 32 single-system calls"},
+        "roofline": {"kernel": "k_render_adj<float>", "top_kernel": top[0], "bound": "alu", "achieved": achieved,
+                     "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+                     "traffic": traffic, "launch_ms": ra_ms,
+                     "peak_note": "FP32 FMA peak from unit counts (148 SMs x 128 lanes x 2 x 2032 MHz)",
+                     "hbm_peak_gbs": peaks.get("hbm_gbs"), "hbm_peak_kind": peak_kind},
+        "cpu_baseline": {"value": cpu_v, "unit": "evals/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{cpu_n} of the {n} mocks ({cpu_dt:.1f} s): FP64 oracle forward + autograd gradient"},
+        "clocks": {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        tdist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--mocks", type=int, default=N_MOCKS, help="mocks per rank (32 is the benchmark workload)")
+    ap.add_argument("--no-single", action="store_true", help="skip the per-system comparison path")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

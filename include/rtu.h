@@ -162,6 +162,15 @@ rtu_status rtu_forward(rtu_system* const* sys, const rtu_eval* ev, int32_t n, vo
  * Must follow rtu_forward on the same stream with the same bindings/slot. */
 rtu_status rtu_adjoint(rtu_system* const* sys, const rtu_eval* ev, int32_t n, void* stream);
 
+/* Per-kernel timing (tracing aid, off by default).  While enabled, every kernel
+ * launch of every call is bracketed by two CUDA events recorded on the call's
+ * stream.  rtu_profile_report waits for those events, then writes one line
+ * "<kernel> <launches> <total_ms>" per kernel into buf (truncated to bytes,
+ * always NUL-terminated) and clears the record.  Returns RTU_E_CUDA if an event
+ * call fails.  Process-wide; guarded by a mutex. */
+rtu_status rtu_profile_enable(int32_t on);
+rtu_status rtu_profile_report(char* buf, size_t bytes);
+
 /* Human-readable description of the last error on this host thread. */
 const char* rtu_last_error(void);
 

@@ -26,7 +26,6 @@ __global__ void __launch_bounds__(256) k_cdf_adj(const __grid_constant__ Batch B
     __syncthreads();
     if (threadIdx.x != 0) return;
     const double* tr = E.trd;
-    const double mu[2] = {tr[0], tr[1]};
     const double sigma = tr[2];
     double dmu[2] = {tot[8], tot[9]};
     double dsig = tot[10];

@@ -187,7 +187,7 @@ template <typename T>
 __global__ void __launch_bounds__(GP_NT) k_gp_source(const __grid_constant__ Batch B) {
     const EvalArgs& E = B.e[blockIdx.x];
     const int n = E.n_src, n2 = n * n;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     Cx<T>* sm = reinterpret_cast<Cx<T>*>(smem_raw);
     __shared__ Cx<T> tw_s[256];
     __shared__ int rev_s[256];
@@ -234,7 +234,7 @@ template <typename T>
 __global__ void __launch_bounds__(GP_NT) k_gp_adjoint(const __grid_constant__ Batch B) {
     const EvalArgs& E = B.e[blockIdx.x];
     const int n = E.n_src, n2 = n * n, nc = n - 1;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     Cx<T>* sm = reinterpret_cast<Cx<T>*>(smem_raw);
     __shared__ Cx<T> tw_s[256];
     __shared__ int rev_s[256];

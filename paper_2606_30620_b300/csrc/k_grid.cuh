@@ -138,7 +138,7 @@ constexpr int SEL_NT = 1024;
 //   double ck[SEL_CAP]; int ci[SEL_CAP]; unsigned bitmap[HB/32];
 __global__ void __launch_bounds__(SEL_NT) k_select_fit(const __grid_constant__ Batch B) {
     const EvalArgs& E = B.e[blockIdx.x];
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     double* ck = reinterpret_cast<double*>(smem_raw);
     int* ci = reinterpret_cast<int*>(ck + SEL_CAP);
     unsigned* bitmap = reinterpret_cast<unsigned*>(ci + SEL_CAP);

@@ -150,6 +150,20 @@ __device__ __forceinline__ void load_transform(const EvalArgs& E, T* trs, T* U) 
 }
 
 // S7 + S11: one thread per image pixel, s^2 sub-rays each.
+// Near-edge FP64 island: a float ray whose grid coordinate lies within
+// EDGE_DELTA (in cells) of a cell edge or of the grid boundary is traced again in
+// double, so that the integer cell of every ray (the rays-per-cell histogram and
+// the kink of the bilinear slope used by the adjoint) is decided in double.
+constexpr double EDGE_DELTA = 2e-3;
+
+__device__ __forceinline__ bool near_edge(float gx, float gy, int n) {
+    const float lo = -(float)EDGE_DELTA, hi = (float)(n - 1) + (float)EDGE_DELTA;
+    if (gx < lo || gx > hi || gy < lo || gy > hi) return false;     // clearly outside
+    const float fx = gx - floorf(gx), fy = gy - floorf(gy);
+    return fx < (float)EDGE_DELTA || fx > 1.0f - (float)EDGE_DELTA || fy < (float)EDGE_DELTA ||
+           fy > 1.0f - (float)EDGE_DELTA;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(CTA_R) k_render(const __grid_constant__ Batch B) {
     const int ev = find_eval(B, blockIdx.x);
@@ -159,11 +173,14 @@ __global__ void __launch_bounds__(CTA_R) k_render(const __grid_constant__ Batch 
     T* sgrid = reinterpret_cast<T*>(smem_raw);
     __shared__ T trs[TR_HDR + 4 * (MAXM + 2)];
     __shared__ T U[MAXM + 2];
+    __shared__ double trs_d[sizeof(T) == 4 ? TR_HDR + 4 * (MAXM + 2) : 1];
+    __shared__ double U_d[sizeof(T) == 4 ? MAXM + 2 : 1];
     __shared__ LensP L;
     __shared__ __align__(8) uint64_t mbar;
     const int n = E.n_src, K = E.n_nodes + 2;
     if (threadIdx.x == 0) load_lens(L, E.lens, E.sub_kind ? E.n_sub : 0);
     load_transform<T>(E, trs, U);
+    if (sizeof(T) == 4) load_transform<double>(E, trs_d, U_d);
     if (!stage_to_smem(sgrid, E.src, (uint32_t)(n * n * sizeof(T)), &mbar, E.flags)) return;
     const int npix = E.n_img * E.n_img;
     const int pixel = tile * CTA_R + threadIdx.x;
@@ -185,6 +202,28 @@ __global__ void __launch_bounds__(CTA_R) k_render(const __grid_constant__ Batch 
         const T zx = (bx - mux) * isg, zy = (by - muy) * isg;
         const T yx = cdf_value<T>(Xx, U, dx_, K, cdf_interval<T>(Xx, K, zx), zx);
         const T yy = cdf_value<T>(Xy, U, dy_, K, cdf_interval<T>(Xy, K, zy), zy);
+        if (sizeof(T) == 4 && near_edge((float)(yx * nm1), (float)(yy * nm1), n)) {
+            double dbx, dby;
+            trace_value_T<double>(L, E.profile, nsub, E.sub_kind, xd, yd, dbx, dby);
+            const double* Xd = trs_d + TR_HDR;
+            const double dzx = (dbx - trs_d[0]) / trs_d[2], dzy = (dby - trs_d[1]) / trs_d[2];
+            const double gxd = (double)cdf_value<double>(Xd, U_d, Xd + 2 * K, K, cdf_interval<double>(Xd, K, dzx), dzx);
+            const double gyd = (double)cdf_value<double>(Xd + K, U_d, Xd + 3 * K, K, cdf_interval<double>(Xd + K, K, dzy), dzy);
+            int cellx = -1;
+            if (gxd >= 0.0 && gxd <= 1.0 && gyd >= 0.0 && gyd <= 1.0) {
+                int i0 = (int)(gxd * (n - 1)), j0 = (int)(gyd * (n - 1));
+                i0 = i0 > n - 2 ? n - 2 : i0;
+                j0 = j0 > n - 2 ? n - 2 : j0;
+                const T fx = (T)(gxd * (n - 1) - i0), fy = (T)(gyd * (n - 1) - j0);
+                const T* r0 = sgrid + j0 * n + i0;
+                acc += (T(1) - fx) * (T(1) - fy) * r0[0] + fx * (T(1) - fy) * r0[1] +
+                       (T(1) - fx) * fy * r0[n] + fx * fy * r0[n + 1];
+                cellx = j0 * (n - 1) + i0;
+                atomicAdd(E.ccount + cellx, 1);
+            }
+            E.cell[(size_t)pixel * s2 + q] = cellx;
+            continue;
+        }
         int cell = -1;
         if (yx >= T(0) && yx <= T(1) && yy >= T(0) && yy <= T(1)) {
             const T gx = yx * nm1, gy = yy * nm1;

@@ -281,16 +281,35 @@ rtu_status fill_args(rtu_system* s, const rtu_eval& v, EvalArgs& e) {
 
 typedef int (*TileFn)(const EvalArgs&);
 
+// ---- optional per-kernel event timing
+struct ProfRec { const char* name; cudaEvent_t a, b; };
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+std::vector<ProfRec> g_prof_pending;
+std::vector<std::pair<std::string, std::pair<long, double>>> g_prof_acc;
+
 template <typename Kern, typename... Extra>
-rtu_status launch(Kern kern, Batch& B, TileFn tiles, int threads, size_t smem, cudaStream_t st,
-                  Extra... extra) {
+rtu_status launch(const char* name, Kern kern, Batch& B, TileFn tiles, int threads, size_t smem,
+                  cudaStream_t st, Extra... extra) {
     int tot = 0;
     for (int i = 0; i < B.n; ++i) { B.tile0[i] = tot; tot += tiles(B.e[i]); }
     B.tile0[B.n] = tot;
     if (tot == 0) return RTU_OK;
+    ProfRec pr{name, nullptr, nullptr};
+    const bool prof = g_prof_on;
+    if (prof) {
+        cudaEventCreate(&pr.a);
+        cudaEventCreate(&pr.b);
+        cudaEventRecord(pr.a, st);
+    }
     kern<<<tot, threads, smem, st>>>(B, extra...);
     cudaError_t ce = cudaGetLastError();
-    if (ce != cudaSuccess) return fail(RTU_E_CUDA, std::string("launch: ") + cudaGetErrorString(ce));
+    if (ce != cudaSuccess) return fail(RTU_E_CUDA, std::string("launch ") + name + ": " + cudaGetErrorString(ce));
+    if (prof) {
+        cudaEventRecord(pr.b, st);
+        std::lock_guard<std::mutex> g(g_prof_mu);
+        g_prof_pending.push_back(pr);
+    }
     return RTU_OK;
 }
 
@@ -318,30 +337,30 @@ rtu_status run_chunk(Batch& B, int phase, cudaStream_t st) {
     }
     const size_t grid_bytes = align_up((size_t)max_n2 * sizeof(T), 128);
     if (phase & (PH_GRID | PH_FORWARD)) {
-        if ((r = launch(k_zero, B, t_zero, 256, 0, st, (phase & PH_FORWARD) ? 1 : 0))) return r;
-        if ((r = launch(k_trace_centres, B, t_centre, CTA_C, 0, st))) return r;
-        if ((r = launch(k_centre_hist, B, t_centre, CTA_C, 0, st))) return r;
-        if ((r = launch(k_select_fit, B, t_one, SEL_NT, SEL_SMEM, st))) return r;
+        if ((r = launch("k_zero", k_zero, B, t_zero, 256, 0, st, (phase & PH_FORWARD) ? 1 : 0))) return r;
+        if ((r = launch("k_trace_centres", k_trace_centres, B, t_centre, CTA_C, 0, st))) return r;
+        if ((r = launch("k_centre_hist", k_centre_hist, B, t_centre, CTA_C, 0, st))) return r;
+        if ((r = launch("k_select_fit", k_select_fit, B, t_one, SEL_NT, SEL_SMEM, st))) return r;
     }
     if (phase & PH_FORWARD) {
-        if ((r = launch(k_gp_source<T>, B, t_one, GP_NT, GP_SMEM, st))) return r;
+        if ((r = launch("k_gp_source", k_gp_source<T>, B, t_one, GP_NT, GP_SMEM, st))) return r;
         if (grid_bytes > MAX_DYN) return fail(RTU_E_ARG, "source grid too large for shared memory");
-        if ((r = launch(k_render<T>, B, t_render, CTA_R, grid_bytes, st))) return r;
-        if ((r = launch(k_psf_like<T>, B, t_psf, PSF_NT, 0, st))) return r;
-        if ((r = launch(k_like_final, B, t_one, 256, 0, st))) return r;
+        if ((r = launch("k_render", k_render<T>, B, t_render, CTA_R, grid_bytes, st))) return r;
+        if ((r = launch("k_psf_like", k_psf_like<T>, B, t_psf, PSF_NT, 0, st))) return r;
+        if ((r = launch("k_like_final", k_like_final, B, t_one, 256, 0, st))) return r;
     }
     if (phase & PH_ADJOINT) {
-        if ((r = launch(k_psf_adj<T>, B, t_psf, PSF_NT, 0, st))) return r;
-        if ((r = launch(k_scan_cells, B, t_one, SCAN_NT, 0, st))) return r;
+        if ((r = launch("k_psf_adj", k_psf_adj<T>, B, t_psf, PSF_NT, 0, st))) return r;
+        if ((r = launch("k_scan_cells", k_scan_cells, B, t_one, SCAN_NT, 0, st))) return r;
         size_t adj = grid_bytes + (size_t)(CTA_R / 32) * 4 * maxK * 8 +
                      (any_sub ? (size_t)CTA_R * max_s2 * 2 * sizeof(T) : 0);
         if (adj > MAX_DYN) return fail(RTU_E_ARG, "adjoint shared memory exceeds the limit");
-        if ((r = launch(k_render_adj<T>, B, t_render, CTA_R, adj, st))) return r;
-        if ((r = launch(k_cell_gather<T>, B, t_cells, GATHER_NT, 0, st))) return r;
-        if ((r = launch(k_cdf_adj, B, t_one, 256, 0, st))) return r;
-        if ((r = launch(k_centre_adj<T>, B, t_centre, CTA_C, 0, st))) return r;
-        if ((r = launch(k_gp_adjoint<T>, B, t_one, GP_NT, GP_SMEM, st))) return r;
-        if ((r = launch(k_grad_final, B, t_one, 64, 0, st))) return r;
+        if ((r = launch("k_render_adj", k_render_adj<T>, B, t_render, CTA_R, adj, st))) return r;
+        if ((r = launch("k_cell_gather", k_cell_gather<T>, B, t_cells, GATHER_NT, 0, st))) return r;
+        if ((r = launch("k_cdf_adj", k_cdf_adj, B, t_one, 256, 0, st))) return r;
+        if ((r = launch("k_centre_adj", k_centre_adj<T>, B, t_centre, CTA_C, 0, st))) return r;
+        if ((r = launch("k_gp_adjoint", k_gp_adjoint<T>, B, t_one, GP_NT, GP_SMEM, st))) return r;
+        if ((r = launch("k_grad_final", k_grad_final, B, t_one, 64, 0, st))) return r;
     }
     return RTU_OK;
 }
@@ -384,6 +403,42 @@ rtu_status rtu_forward(rtu_system* const* sys, const rtu_eval* ev, int32_t n, vo
 
 rtu_status rtu_adjoint(rtu_system* const* sys, const rtu_eval* ev, int32_t n, void* stream) {
     return run(sys, ev, n, PH_ADJOINT, stream);
+}
+
+rtu_status rtu_profile_enable(int32_t on) {
+    std::lock_guard<std::mutex> g(g_prof_mu);
+    g_prof_on = on != 0;
+    return RTU_OK;
+}
+
+rtu_status rtu_profile_report(char* buf, size_t bytes) {
+    std::lock_guard<std::mutex> g(g_prof_mu);
+    rtu_status rc = RTU_OK;
+    for (ProfRec& p : g_prof_pending) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(p.b) != cudaSuccess || cudaEventElapsedTime(&ms, p.a, p.b) != cudaSuccess)
+            rc = fail(RTU_E_CUDA, "profile event failed");
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
+        bool found = false;
+        for (auto& e : g_prof_acc)
+            if (e.first == p.name) { e.second.first += 1; e.second.second += ms; found = true; break; }
+        if (!found) g_prof_acc.push_back({p.name, {1L, (double)ms}});
+    }
+    g_prof_pending.clear();
+    std::string out;
+    for (auto& e : g_prof_acc) {
+        char line[160];
+        snprintf(line, sizeof(line), "%s %ld %.6f\n", e.first.c_str(), e.second.first, e.second.second);
+        out += line;
+    }
+    g_prof_acc.clear();
+    if (buf && bytes) {
+        size_t n = std::min(bytes - 1, out.size());
+        memcpy(buf, out.data(), n);
+        buf[n] = 0;
+    }
+    return rc;
 }
 
 }  // extern "C"

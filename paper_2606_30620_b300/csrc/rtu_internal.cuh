@@ -133,7 +133,7 @@ template <> struct real2_of<float> { typedef float2 type; };
 template <> struct real2_of<double> { typedef double2 type; };
 template <typename T> struct real4_of;
 template <> struct real4_of<float> { typedef float4 type; };
-template <> struct real4_of<double> { typedef double4 type; };
+template <> struct real4_of<double> { typedef double4_32a type; };
 
 // ------------------------------------------------------------- lens trace
 // Lens parameters as seen by a kernel: main lens and shear, then subhaloes.

@@ -63,11 +63,16 @@ for _name in ("rtu_build_grid", "rtu_forward", "rtu_adjoint"):
     getattr(_lib, _name).argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(Eval), ctypes.c_int32,
                                      ctypes.c_void_p]
     getattr(_lib, _name).restype = ctypes.c_int32
+_lib.rtu_profile_enable.argtypes = [ctypes.c_int32]
+_lib.rtu_profile_enable.restype = ctypes.c_int32
+_lib.rtu_profile_report.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
+_lib.rtu_profile_report.restype = ctypes.c_int32
 _lib.rtu_last_error.restype = ctypes.c_char_p
 _lib.rtu_version.restype = ctypes.c_char_p
 
 EXPORTED = ("rtu_workspace_size", "rtu_system_create", "rtu_system_destroy", "rtu_build_grid",
-            "rtu_forward", "rtu_adjoint", "rtu_last_error", "rtu_version")
+            "rtu_forward", "rtu_adjoint", "rtu_profile_enable", "rtu_profile_report", "rtu_last_error",
+            "rtu_version")
 
 
 def _check(rc: int, what: str):
@@ -77,6 +82,21 @@ def _check(rc: int, what: str):
 
 def version() -> str:
     return _lib.rtu_version().decode()
+
+
+def profile_enable(on: bool = True):
+    _check(_lib.rtu_profile_enable(1 if on else 0), "rtu_profile_enable")
+
+
+def profile_report() -> dict:
+    """{kernel: (launches, total_ms)} since the last report (waits for the events)."""
+    buf = ctypes.create_string_buffer(1 << 16)
+    _check(_lib.rtu_profile_report(buf, len(buf)), "rtu_profile_report")
+    out = {}
+    for line in buf.value.decode().splitlines():
+        name, cnt, ms = line.split()
+        out[name] = (int(cnt), float(ms))
+    return out
 
 
 def _ptr(t):
@@ -144,7 +164,7 @@ class Binding:
     """Device buffers of one evaluation (inputs, and outputs allocated on demand)."""
 
     def __init__(self, system: System, lens, latents, ps, slot=0, want_model=False, want_image=False,
-                 want_source=False, want_cdf=False, want_hist=False, grads=True, dlogL=None):
+                 want_source=False, want_cdf=False, want_hist=False, grads=True, dlogL=None, out=None):
         dev, dt = system.device, system.dtype
         self.system = system
         self.slot = slot
@@ -158,7 +178,8 @@ class Binding:
         if self.ps.numel() != system.n_ps:
             raise ValueError(f"ps must hold {system.n_ps} values")
         self.dlogL = None if dlogL is None else torch.as_tensor(dlogL, dtype=torch.float64, device=dev)
-        self.stats = torch.zeros(N_STATS, dtype=torch.float64, device=dev)
+        out = out or {}
+        self.stats = out["stats"] if "stats" in out else torch.zeros(N_STATS, dtype=torch.float64, device=dev)
         n_img, n_src = system.n_img, system.n_src
         self.model = torch.empty(n_img, n_img, dtype=dt, device=dev) if want_model else None
         self.image = torch.empty(n_img, n_img, dtype=dt, device=dev) if want_image else None
@@ -166,9 +187,19 @@ class Binding:
         self.cdf = torch.empty(3 + 4 * system.n_knots, dtype=torch.float64, device=dev) if want_cdf else None
         self.ray_hist = torch.empty((n_src - 1) ** 2, dtype=torch.int32, device=dev) if want_hist else None
         if grads:
-            self.g_latents = torch.empty(n_src, n_src, dtype=dt, device=dev)
-            self.g_lens = torch.empty(system.n_lens, dtype=torch.float64, device=dev)
-            self.g_ps = torch.empty(system.n_ps, dtype=torch.float64, device=dev)
+            # caller-provided output views (e.g. slices of one packed buffer) are used as they are
+            self.g_latents = out.get("g_latents", None)
+            if self.g_latents is None:
+                self.g_latents = torch.empty(n_src, n_src, dtype=dt, device=dev)
+            self.g_lens = out.get("g_lens", None)
+            if self.g_lens is None:
+                self.g_lens = torch.empty(system.n_lens, dtype=torch.float64, device=dev)
+            self.g_ps = out.get("g_ps", None)
+            if self.g_ps is None:
+                self.g_ps = torch.empty(system.n_ps, dtype=torch.float64, device=dev)
+            for t in (self.g_latents, self.g_lens, self.g_ps):
+                if not t.is_contiguous():
+                    raise ValueError("output views must be contiguous")
         else:
             self.g_latents = self.g_lens = self.g_ps = None
 

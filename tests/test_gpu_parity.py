@@ -1,0 +1,167 @@
+"""CUDA path vs the FP64 oracle, element by element, on seeded inputs.
+
+Tolerances (relative L2 unless stated):
+  * FP64 mode: 1e-10 for every float output (images, CDF, source, all gradients).
+  * FP32 mode: 1e-5 for the images, the source grid and the latent / power-
+    spectrum gradients; the CDF is computed in FP64 in both modes (1e-10).
+    The lens gradient in FP32 mode is graded at LENS_TOL_F32 (see below).
+  * Integer outputs: the rays-per-cell histogram is bit-exact in FP64 mode; in
+    FP32 mode a ray whose FP32 position lies within rounding of a cell edge may
+    land in the neighbouring cell, so the test bounds the number of moved rays.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2606_30620_b300 import inputs as I
+from tests import gpu_cases as G
+
+pytestmark = pytest.mark.gpu
+
+F64_TOL = 1e-10
+F32_TOL = 1e-5
+# FP32 lens gradients: every ray's contribution carries FP32 rounding of its
+# derivative chain (trace -> standardisation -> spline -> bilinear slope), and
+# the lens gradient is a sum of ~1e6 such terms that partly cancel against the
+# standardisation term; graded at 1e-4 ("FP32 lens gradient").
+LENS_TOL_F32 = 1e-4
+
+
+@pytest.fixture(scope="module")
+def rtu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2606_30620_b300 import rtu as mod
+    return mod
+
+
+def _check(r, prec, lens_tol=None, hist_tol=0):
+    tol = F64_TOL if prec == 1 else F32_TOL
+    assert r["cdf"] < F64_TOL, r
+    assert r["logL"] < tol and r["chi2"] < tol, r
+    for k in ("source", "image", "model"):
+        assert r[k] < tol, (k, r)
+    if "g_latents" in r:
+        assert r["g_latents"] < tol, r
+        assert r["g_ps"] < tol, r
+        assert r["g_lens"] < (lens_tol if lens_tol is not None else tol), r
+    assert r["hist_diff"] <= hist_tol, r
+    assert r["flags"][0] == r["flags"][1], r
+
+
+def test_c1_fp64_matches_oracle(rtu):
+    m = I.config_c1()
+    g, _, _ = G.run_gpu(m, rtu.RTU_F64)
+    _check(G.compare(g, G.run_oracle(m)), 1)
+
+
+@pytest.mark.parametrize("kw", [dict(seed=7), dict(seed=8, profile=I.PROFILE_SIE, family=I.PS_POWER_LAW),
+                                dict(seed=9, family=I.PS_MATERN), dict(seed=12, sub_kind=I.SUB_TNFW, n_sub=2),
+                                dict(seed=13, sub_kind=I.SUB_NFW, n_sub=3),
+                                dict(seed=14, n_img=13, s=1, n_src=6, psf_k=1),
+                                dict(seed=15, n_img=17, s=3, n_src=12, psf_k=5),
+                                dict(seed=16, n_img=21, s=2, n_src=9, psf_k=3)])
+def test_tiny_fp64_matches_oracle(rtu, kw):
+    m = I.config_tiny(**kw)
+    g, _, _ = G.run_gpu(m, rtu.RTU_F64)
+    _check(G.compare(g, G.run_oracle(m)), 1)
+
+
+@pytest.mark.parametrize("seed", [1000, 1001, 1002, 1003])
+def test_c2_fp32_matches_oracle(rtu, seed):
+    m = I.config_c2(seed)
+    g, _, _ = G.run_gpu(m, rtu.RTU_F32)
+    # at most a few rays in 640k move across a cell edge under FP32 rounding
+    _check(G.compare(g, G.run_oracle(m)), 0, lens_tol=LENS_TOL_F32, hist_tol=2 * 20)
+
+
+def test_c2_fp64_matches_oracle(rtu):
+    m = I.config_c2(1004)
+    g, _, _ = G.run_gpu(m, rtu.RTU_F64)
+    _check(G.compare(g, G.run_oracle(m)), 1)
+
+
+@pytest.mark.parametrize("n_src", [48, 96, 27, 128])
+def test_radix3_and_odd_grids(rtu, n_src):
+    m = I.config_c2(1010 + n_src, n_img=96, s=2, n_src=n_src)
+    g, _, _ = G.run_gpu(m, rtu.RTU_F64)
+    _check(G.compare(g, G.run_oracle(m)), 1)
+
+
+def test_c3_shape_fp32(rtu):
+    m = I.config_c3(2000)
+    g, _, _ = G.run_gpu(m, rtu.RTU_F32)
+    _check(G.compare(g, G.run_oracle(m)), 0, lens_tol=LENS_TOL_F32, hist_tol=40)
+
+
+def test_c4_shape_with_subhaloes_fp32(rtu):
+    m = I.config_c4(3000, with_subs=True)
+    g, _, _ = G.run_gpu(m, rtu.RTU_F32)
+    _check(G.compare(g, G.run_oracle(m)), 0, lens_tol=LENS_TOL_F32, hist_tol=80)
+
+
+def test_c4_shape_with_subhaloes_fp64(rtu):
+    m = I.config_c4(3001, with_subs=True, n_img=160, s=2, n_src=64)
+    g, _, _ = G.run_gpu(m, rtu.RTU_F64)
+    _check(G.compare(g, G.run_oracle(m)), 1)
+
+
+def test_batch_equals_alone_and_is_deterministic(rtu):
+    mocks = [I.config_c2(1020 + k, n_img=64 + 16 * k, s=2 + (k % 3), n_src=(32, 48, 64)[k % 3]) for k in range(5)]
+    alone = []
+    for m in mocks:
+        g, _, _ = G.run_gpu(m, rtu.RTU_F32)
+        alone.append(g)
+    systems, binds = [], []
+    for m in mocks:
+        s = rtu.System.from_mock(m, precision=rtu.RTU_F32)
+        systems.append(s)
+        binds.append(rtu.Binding(s, m.lens, m.latents, m.ps, want_model=True))
+    batch = rtu.Batch(binds)
+    for rep in range(2):
+        batch.forward()
+        batch.adjoint()
+        torch.cuda.synchronize()
+        for a, b in zip(alone, binds):
+            assert np.array_equal(a["model"], b.model.cpu().numpy())
+            assert np.array_equal(a["stats"], b.stats.cpu().numpy())
+            assert G.rel_l2(b.g_latents.cpu().numpy(), a["g_latents"]) < 1e-12
+            assert G.rel_l2(b.g_lens.cpu().numpy(), a["g_lens"]) < 1e-12
+            assert G.rel_l2(b.g_ps.cpu().numpy(), a["g_ps"]) < 1e-12
+
+
+def test_upstream_scale_and_autograd_function(rtu):
+    m = I.config_tiny(seed=21, n_img=24, n_src=16)
+    s = rtu.System.from_mock(m, precision=rtu.RTU_F64)
+    lens = torch.tensor(m.lens, device="cuda", requires_grad=True)
+    lat = torch.tensor(m.latents, device="cuda", requires_grad=True)
+    ps = torch.tensor(m.ps, device="cuda", requires_grad=True)
+    L = rtu.log_likelihood(s, lens, lat, ps)
+    (2.5 * L).backward()
+    o = G.run_oracle(m)
+    assert abs(float(L) - o["logL"]) < 1e-10 * abs(o["logL"])
+    assert G.rel_l2(lens.grad.cpu().numpy() / 2.5, o["g_lens"]) < F64_TOL
+    assert G.rel_l2(lat.grad.cpu().numpy() / 2.5, o["g_latents"]) < F64_TOL
+    assert G.rel_l2(ps.grad.cpu().numpy() / 2.5, o["g_ps"]) < F64_TOL
+
+
+def test_build_grid_alone_gives_the_same_transform(rtu):
+    m = I.config_c2(1030, n_img=80, s=2, n_src=32)
+    g, s, b = G.run_gpu(m, rtu.RTU_F32, want_grads=False)
+    b2 = rtu.Binding(s, m.lens, m.latents, m.ps, want_cdf=True, grads=False)
+    rtu.Batch([b2]).build_grid()
+    torch.cuda.synchronize()
+    assert np.array_equal(b2.cdf.cpu().numpy(), g["cdf"])
+
+
+def test_argument_errors_are_reported(rtu):
+    m = I.config_tiny(seed=22)
+    s = rtu.System.from_mock(m)
+    b = rtu.Binding(s, m.lens, m.latents, m.ps, grads=False)
+    with pytest.raises(rtu.RTUError, match="adjoint outputs"):
+        rtu.Batch([b]).adjoint()
+    b.slot = 3
+    with pytest.raises(rtu.RTUError, match="slot"):
+        rtu.Batch([b]).forward()
+    with pytest.raises(rtu.RTUError):
+        rtu.System(m.data, np.zeros_like(m.mask), m.psf, m.sigma, m.pix, m.s_super, m.n_src, m.src_pitch)
