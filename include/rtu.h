@@ -162,6 +162,57 @@ rtu_status rtu_forward(rtu_system* const* sys, const rtu_eval* ev, int32_t n, vo
  * Must follow rtu_forward on the same stream with the same bindings/slot. */
 rtu_status rtu_adjoint(rtu_system* const* sys, const rtu_eval* ev, int32_t n, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * S10: stochastic variational inference (Sec. 4).  A mean-field Normal guide
+ * over unconstrained sites: the non-latent sites (n_sites of them: theta_E,
+ * gamma (RTU_EPL only), e1, e2, x0, y0, Gamma1, Gamma2; per subhalo kappa_s,
+ * r_s, x_s, y_s (tau held fixed); the power-spectrum parameters and alpha_src)
+ * then the n_src^2 latents (prior N(0, 1), Eq. 1).  Site i has prior priors[i]
+ * (Table A1 families) on its value v = support-map(u); its physical parameter is
+ * v (RTU_SPACE_LINEAR) or 10^v (RTU_SPACE_LOG10).  The guide is
+ * u = loc + softplus(rho) eps with eps drawn on the device by Philox4x32-10
+ * (Salmon et al. 2011; counter (e/2, sample, step, tag), key = seed) and
+ * Box-Muller.  All state lives in the system's workspace.
+ * ------------------------------------------------------------------------- */
+enum { RTU_PRIOR_NORMAL = 0,        /* a = mean, b = sd                       */
+       RTU_PRIOR_UNIFORM = 1,       /* on [a, b]                              */
+       RTU_PRIOR_TRUNC_NORMAL = 2,  /* mean a, sd b, truncated to [c, d]      */
+       RTU_PRIOR_LINEAR = 3 };      /* density prop. to 1 + a (v-c)/(d-c) on [c, d] */
+enum { RTU_SPACE_LINEAR = 0, RTU_SPACE_LOG10 = 1 };
+typedef struct {
+    int32_t kind;
+    int32_t space;
+    double a, b, c, d;
+} rtu_prior;
+
+/* Number of non-latent sites of a system (0 on a bad desc). */
+int32_t rtu_n_sites(const rtu_system_desc* desc);
+
+/* Set the guide of one system (synchronous host copies into the workspace):
+ * priors[n_sites]; fixed[8 + 5 n_sub + n_ps] physical values that supply the
+ * non-site entries (gamma of an SIE, tau of each subhalo); loc and rho
+ * [n_sites + n_src^2] unconstrained locations and softplus-scale parameters;
+ * tag = the system's random stream.  Resets Adam's moments and the step. */
+rtu_status rtu_elbo_init(rtu_system* sys, const rtu_prior* priors, const double* fixed,
+                         const double* loc, const double* rho, uint32_t tag);
+
+/* One optimiser step for each of n systems: n_samples (1..8, <= desc.n_slots)
+ * reparametrised guide samples, the batched rtu_forward + rtu_adjoint of every
+ * sample, the Monte-Carlo ELBO
+ *   (1/S) sum_s [log L(theta_s) + sum_sites (log p + log|dv/du|) + sum_latents log N(w)
+ *                - log q(u_s)],
+ * its gradient w.r.t. loc and rho, and an Adam ascent step (beta1 0.9, beta2
+ * 0.999, eps 1e-8, learning rate lr).  elbo_out (device double[n], nullable)
+ * receives each system's ELBO.  Stream-ordered. */
+rtu_status rtu_elbo_step(rtu_system* const* sys, int32_t n, int32_t n_samples, uint64_t seed,
+                         double lr, double* elbo_out, void* stream);
+
+/* Checkpoint / resume of the guide and optimiser state: bytes of the blob,
+ * export into / import from caller host memory (synchronous). */
+size_t rtu_elbo_state_bytes(const rtu_system* sys);
+rtu_status rtu_elbo_export(const rtu_system* sys, void* host, size_t bytes);
+rtu_status rtu_elbo_import(rtu_system* sys, const void* host, size_t bytes);
+
 /* Per-kernel timing (tracing aid, off by default).  While enabled, every kernel
  * launch of every call is bracketed by two CUDA events recorded on the call's
  * stream.  rtu_profile_report waits for those events, then writes one line

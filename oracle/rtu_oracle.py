@@ -548,3 +548,163 @@ def forward_adjoint(sys: System, lens, latents, ps, subs=None):
     if sys.profile == PROFILE_SIE:
         res["g_lens"][1] = 0.0
     return res
+
+
+# ---------------------------------------------------------------------------
+# Stochastic variational inference (Sec. 4): Normal guide in unconstrained space
+# ---------------------------------------------------------------------------
+# Counter-based generator for the guide's noise: Philox4x32-10 (Salmon, Moraes,
+# Dror & Shaw 2011), written from its published definition, and Box-Muller.
+PHILOX_M0, PHILOX_M1 = 0xD2511F53, 0xCD9E8D57
+PHILOX_W0, PHILOX_W1 = 0x9E3779B9, 0xBB67AE85
+MASK32 = 0xFFFFFFFF
+
+
+def philox4x32_10(ctr, key):
+    """Ten rounds of the Philox 4x32 bijection of counter `ctr` (4 words) under
+    `key` (2 words); the key is bumped by the Weyl constants between rounds."""
+    c0, c1, c2, c3 = [int(v) & MASK32 for v in ctr]
+    k0, k1 = [int(v) & MASK32 for v in key]
+    for r in range(10):
+        if r > 0:
+            k0 = (k0 + PHILOX_W0) & MASK32
+            k1 = (k1 + PHILOX_W1) & MASK32
+        p0 = PHILOX_M0 * c0
+        p1 = PHILOX_M1 * c2
+        hi0, lo0 = p0 >> 32, p0 & MASK32
+        hi1, lo1 = p1 >> 32, p1 & MASK32
+        c0, c1, c2, c3 = (hi1 ^ c1 ^ k0) & MASK32, lo1, (hi0 ^ c3 ^ k1) & MASK32, lo0
+    return c0, c1, c2, c3
+
+
+def guide_noise(seed: int, tag: int, step: int, sample: int, n: int):
+    """Standard normals e_0..e_{n-1} of one guide sample.  Element e takes the Philox
+    block with counter (e // 2, sample, step, tag) and key (seed lo, seed hi); words
+    (0, 1) for even e and (2, 3) for odd e give u1 = (w + 1/2)/2^32, u2 likewise, and
+    e = sqrt(-2 ln u1) cos(2 pi u2)."""
+    out = torch.empty(n, dtype=DT)
+    key = (seed & MASK32, (seed >> 32) & MASK32)
+    for e in range(n):
+        w = philox4x32_10((e >> 1, sample, step, tag), key)
+        a, b = (w[0], w[1]) if e % 2 == 0 else (w[2], w[3])
+        u1 = (a + 0.5) / 4294967296.0
+        u2 = (b + 0.5) / 4294967296.0
+        out[e] = math.sqrt(-2.0 * math.log(u1)) * math.cos(2.0 * math.pi * u2)
+    return out
+
+
+PRIOR_NORMAL, PRIOR_UNIFORM, PRIOR_TRUNC_NORMAL, PRIOR_LINEAR = 0, 1, 2, 3
+SPACE_LINEAR, SPACE_LOG10 = 0, 1
+
+
+def site_targets(profile: int, sub_kind: int, n_sub: int, family: int):
+    """Physical-parameter index of every non-latent site, in order: the lens
+    vector [8 + 5 n_sub] (gamma skipped for the SIE, tau of each subhalo held
+    fixed), then the power-spectrum vector [n_family + 1] offset by the lens size."""
+    nl = 8 + 5 * (n_sub if sub_kind else 0)
+    idx = [0] + ([1] if profile == PROFILE_EPL else []) + [2, 3, 4, 5, 6, 7]
+    for h in range(n_sub if sub_kind else 0):
+        idx += [8 + 5 * h + 0, 8 + 5 * h + 1, 8 + 5 * h + 3, 8 + 5 * h + 4]
+    idx += [nl + k for k in range(N_PS_PARAMS[family] + 1)]
+    return idx
+
+
+def _sigmoid(u):
+    return 1.0 / (1.0 + torch.exp(-u))
+
+
+def _log_sigmoid(u):
+    return -softplus(-u)
+
+
+def site_value_and_logdensity(u, prior):
+    """Support transform v(u) of one site and log p(v) + log |dv/du| under its prior
+    (Table A1 families: G normal, U uniform, truncated normal, T linear)."""
+    kind, _space, a, b, c, d = prior
+    if kind == PRIOR_NORMAL:
+        v = u
+        return v, -0.5 * ((v - a) / b) ** 2 - math.log(b) - 0.5 * math.log(2 * math.pi)
+    if kind == PRIOR_UNIFORM:
+        v = a + (b - a) * _sigmoid(u)
+        return v, _log_sigmoid(u) + _log_sigmoid(-u)
+    if kind == PRIOR_TRUNC_NORMAL:
+        lo, hi = c, d
+        v = lo + (hi - lo) * _sigmoid(u)
+        Z = 0.5 * (math.erf((hi - a) / (b * math.sqrt(2))) - math.erf((lo - a) / (b * math.sqrt(2))))
+        lp = -0.5 * ((v - a) / b) ** 2 - math.log(b) - 0.5 * math.log(2 * math.pi) - math.log(Z)
+        return v, lp + math.log(hi - lo) + _log_sigmoid(u) + _log_sigmoid(-u)
+    if kind == PRIOR_LINEAR:
+        # p(v) proportional to 1 + a (v - lo)/(hi - lo) on [lo, hi]  (parity unpinned reading)
+        lo, hi = c, d
+        sg = _sigmoid(u)
+        v = lo + (hi - lo) * sg
+        lp = torch.log(1.0 + a * sg) - math.log((hi - lo) * (1.0 + 0.5 * a))
+        return v, lp + math.log(hi - lo) + _log_sigmoid(u) + _log_sigmoid(-u)
+    raise ValueError(kind)
+
+
+@dataclass
+class GuideState:
+    """Mean-field Normal guide: location and softplus-parametrised scale per site,
+    for the n_sites physical sites and the n_src^2 latents, plus Adam moments."""
+    loc: torch.Tensor
+    rho: torch.Tensor
+    m: torch.Tensor
+    v: torch.Tensor
+    t: int = 0
+
+
+def elbo_estimate(sys: System, state: GuideState, priors, fixed_phys, n_samples: int, seed: int, tag: int,
+                  step: int, subs_kind_n=(SUB_NONE, 0)):
+    """Monte-Carlo ELBO of the Normal guide (reparametrised samples; Sec. 4):
+    ELBO = (1/S) sum_s [log L(theta_s) + sum_sites (log p + log|J|)
+                        + sum_latents log N(w; 0, 1) - log q(u_s)],
+    u_s = loc + softplus(rho) e_s.  `fixed_phys` is the physical vector
+    [lens (8 + 5 n_sub) | ps] that supplies the values of non-site entries
+    (gamma of an SIE, tau of each subhalo).  Returns the ELBO (with autograd graph)."""
+    sub_kind, n_sub = subs_kind_n
+    targets = site_targets(sys.profile, sub_kind, n_sub, sys.ps_family)
+    ns = len(targets)
+    nl = 8 + 5 * (n_sub if sub_kind else 0)
+    n_lat = sys.n_src * sys.n_src
+    scale = softplus(state.rho)
+    total = 0.0
+    for s in range(n_samples):
+        eps = guide_noise(seed, tag, step, s, ns + n_lat)
+        u = state.loc + scale * eps
+        phys = [torch.as_tensor(float(x), dtype=DT) for x in fixed_phys]
+        lpj = 0.0
+        for i, ti in enumerate(targets):
+            v, lp = site_value_and_logdensity(u[i], priors[i])
+            phys[ti] = torch.pow(10.0, v) if priors[i][1] == SPACE_LOG10 else v
+            lpj = lpj + lp
+        w = u[ns:].reshape(sys.n_src, sys.n_src)
+        lpj = lpj + (-0.5 * w * w - 0.5 * math.log(2 * math.pi)).sum()
+        lens = torch.stack(phys[:8])
+        subs = torch.stack(phys[8:nl]).reshape(-1, 5) if nl > 8 else None
+        ps = torch.stack(phys[nl:])
+        logL = forward(sys, lens, w, ps, subs)["logL"]
+        logq = (-0.5 * eps * eps - torch.log(scale) - 0.5 * math.log(2 * math.pi)).sum()
+        total = total + logL + lpj - logq
+    return total / n_samples
+
+
+def elbo_step(sys: System, state: GuideState, priors, fixed_phys, n_samples, seed, tag, lr=1e-3,
+              b1=0.9, b2=0.999, eps=1e-8, subs_kind_n=(SUB_NONE, 0)):
+    """One optimiser step: ELBO and its gradient w.r.t. (loc, rho) at the current
+    step's noise, then Adam ascent; returns (elbo, grad_loc, grad_rho, new state)."""
+    loc = state.loc.detach().clone().requires_grad_(True)
+    rho = state.rho.detach().clone().requires_grad_(True)
+    st = GuideState(loc=loc, rho=rho, m=state.m, v=state.v, t=state.t)
+    elbo = elbo_estimate(sys, st, priors, fixed_phys, n_samples, seed, tag, state.t, subs_kind_n)
+    gl, gr = torch.autograd.grad(elbo, [loc, rho])
+    g = torch.cat([gl, gr])
+    t = state.t + 1
+    m = b1 * state.m + (1 - b1) * g
+    v = b2 * state.v + (1 - b2) * g * g
+    mh = m / (1 - b1 ** t)
+    vh = v / (1 - b2 ** t)
+    p = torch.cat([state.loc, state.rho]) + lr * mh / (torch.sqrt(vh) + eps)
+    n = state.loc.numel()
+    new = GuideState(loc=p[:n].detach(), rho=p[n:].detach(), m=m.detach(), v=v.detach(), t=t)
+    return float(elbo), gl.detach(), gr.detach(), new

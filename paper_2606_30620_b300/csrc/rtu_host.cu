@@ -18,10 +18,13 @@
 #include "k_render.cuh"
 #include "k_psf.cuh"
 #include "k_adj.cuh"
+#include "k_elbo.cuh"
 
 using namespace rtu;
 
 static_assert(sizeof(Batch) <= 32000, "batch descriptor must fit the kernel-parameter limit");
+static_assert(sizeof(ElboBatch) <= 32000, "ELBO batch descriptor must fit the kernel-parameter limit");
+static_assert(sizeof(rtu_prior) == sizeof(PriorD), "prior layout");
 
 namespace {
 
@@ -60,6 +63,7 @@ std::vector<int> digit_reversal(int n, const std::vector<int>& rad) {
 
 struct Sizes {
     int nm_max, n_cta_c_max, n_cta_r, n_cta_p, K, ncell, n_rays, nacc, nl, tb;
+    int nps, n_sites, n_state, n_phys, n_cta_upd;
 };
 
 Sizes sizes_of(const rtu_system_desc& d) {
@@ -76,6 +80,11 @@ Sizes sizes_of(const rtu_system_desc& d) {
     z.nacc = NACC_FIX + 4 * z.K + 5 * nsub;
     z.nl = 8 + 5 * nsub;
     z.tb = d.precision == RTU_F64 ? 8 : 4;
+    z.nps = (d.ps_family == RTU_PS_MATERN ? 3 : 2) + 1;
+    z.n_sites = (d.profile == RTU_EPL ? 8 : 7) + 4 * nsub + z.nps;
+    z.n_state = z.n_sites + d.n_src * d.n_src;
+    z.n_phys = z.nl + z.nps;
+    z.n_cta_upd = (z.n_state + ELBO_NT - 1) / ELBO_NT;
     return z;
 }
 
@@ -112,6 +121,42 @@ size_t slot_layout(const rtu_system_desc& d, char* base, EvalArgs* e) {
     p = take((size_t)z.ncell * 4 * 8);                if (e) e->corner = (double*)p;
     p = take((size_t)z.n_cta_r * z.nacc * 8);         if (e) e->apart = (double*)p;
     p = take(16);                                     if (e) e->flags = (int*)p;
+    return o;
+}
+
+// per-slot buffers of one guide sample: parameters in, statistics and gradients out
+struct SampleBufs { double *lens, *ps, *stats, *glens, *gps; void *lat, *glat; };
+
+size_t sample_layout(const rtu_system_desc& d, char* base, SampleBufs* b) {
+    const Sizes z = sizes_of(d);
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t at = o; o = align_up(o + bytes); return base ? base + at : nullptr; };
+    const size_t n2 = (size_t)d.n_src * d.n_src;
+    char* p;
+    p = take((size_t)z.nl * 8);   if (b) b->lens = (double*)p;
+    p = take((size_t)z.nps * 8);  if (b) b->ps = (double*)p;
+    p = take(n2 * z.tb);          if (b) b->lat = p;
+    p = take(4 * 8);              if (b) b->stats = (double*)p;
+    p = take((size_t)z.nl * 8);   if (b) b->glens = (double*)p;
+    p = take((size_t)z.nps * 8);  if (b) b->gps = (double*)p;
+    p = take(n2 * z.tb);          if (b) b->glat = p;
+    return o;
+}
+
+size_t state_layout(const rtu_system_desc& d, char* base, ElboState* st) {
+    const Sizes z = sizes_of(d);
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t at = o; o = align_up(o + bytes); return base ? base + at : nullptr; };
+    char* p;
+    p = take((size_t)z.n_state * 8);      if (st) st->loc = (double*)p;
+    p = take((size_t)z.n_state * 8);      if (st) st->rho = (double*)p;
+    p = take((size_t)2 * z.n_state * 8);  if (st) st->m = (double*)p;
+    p = take((size_t)2 * z.n_state * 8);  if (st) st->v = (double*)p;
+    p = take((size_t)z.n_sites * sizeof(PriorD)); if (st) st->prior = (PriorD*)p;
+    p = take((size_t)z.n_phys * 8);       if (st) st->fixed = (double*)p;
+    p = take(8);                          if (st) st->t = (long long*)p;
+    p = take((size_t)z.n_cta_upd * 8);    if (st) st->part = (double*)p;
+    if (st) { st->n_sites = z.n_sites; st->n_state = z.n_state; st->n_phys = z.n_phys; st->tag = 0; }
     return o;
 }
 
@@ -171,6 +216,9 @@ struct rtu_system {
     double* tw;
     int* rev;
     std::vector<EvalArgs> slot;   // workspace pointers of each slot
+    std::vector<SampleBufs> sbuf; // guide-sample buffers of each slot
+    ElboState st;
+    bool elbo_ready = false;
 };
 
 // ------------------------------------------------------------ zero kernel
@@ -192,7 +240,9 @@ extern "C" {
 
 size_t rtu_workspace_size(const rtu_system_desc* d) {
     if (check_desc(d)) return 0;
-    return static_layout(*d, nullptr, nullptr, nullptr, nullptr) + (size_t)d->n_slots * slot_layout(*d, nullptr, nullptr) + 256;
+    return static_layout(*d, nullptr, nullptr, nullptr, nullptr) +
+           (size_t)d->n_slots * (slot_layout(*d, nullptr, nullptr) + sample_layout(*d, nullptr, nullptr)) +
+           state_layout(*d, nullptr, nullptr) + 256;
 }
 
 rtu_status rtu_system_create(const rtu_system_desc* d, void* ws, size_t ws_bytes, rtu_system** out) {
@@ -236,13 +286,18 @@ rtu_status rtu_system_create(const rtu_system_desc* d, void* ws, size_t ws_bytes
         return fail(RTU_E_CUDA, std::string("table upload: ") + cudaGetErrorString(ce));
     }
     const size_t per = slot_layout(*d, nullptr, nullptr);
+    const size_t sper = sample_layout(*d, nullptr, nullptr);
     s->slot.resize(d->n_slots);
+    s->sbuf.resize(d->n_slots);
     for (int k = 0; k < d->n_slots; ++k) {
         EvalArgs e;
         memset(&e, 0, sizeof(e));
-        slot_layout(*d, base + st + (size_t)k * per, &e);
+        slot_layout(*d, base + st + (size_t)k * (per + sper), &e);
         s->slot[k] = e;
+        sample_layout(*d, base + st + (size_t)k * (per + sper) + per, &s->sbuf[k]);
     }
+    memset(&s->st, 0, sizeof(s->st));
+    state_layout(*d, base + st + (size_t)d->n_slots * (per + sper), &s->st);
     *out = s;
     return RTU_OK;
 }
@@ -439,6 +494,156 @@ rtu_status rtu_profile_report(char* buf, size_t bytes) {
         buf[n] = 0;
     }
     return rc;
+}
+
+}  // extern "C"
+
+namespace {
+
+int t_elbo_sample(const ElboArgs& a) { return a.n_samples * ((a.st.n_state + ELBO_NT - 1) / ELBO_NT); }
+int t_elbo_update(const ElboArgs& a) { return a.n_cta_upd; }
+int t_elbo_one(const ElboArgs&) { return 1; }
+
+template <typename Kern>
+rtu_status launch_elbo(const char* name, Kern kern, ElboBatch& B, int (*tiles)(const ElboArgs&), int threads,
+                       cudaStream_t st) {
+    int tot = 0;
+    for (int i = 0; i < B.n; ++i) { B.tile0[i] = tot; tot += tiles(B.e[i]); }
+    B.tile0[B.n] = tot;
+    if (tot == 0) return RTU_OK;
+    kern<<<tot, threads, 0, st>>>(B);
+    cudaError_t ce = cudaGetLastError();
+    if (ce != cudaSuccess) return fail(RTU_E_CUDA, std::string("launch ") + name + ": " + cudaGetErrorString(ce));
+    return RTU_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t rtu_n_sites(const rtu_system_desc* d) {
+    if (check_desc(d)) return 0;
+    return sizes_of(*d).n_sites;
+}
+
+rtu_status rtu_elbo_init(rtu_system* s, const rtu_prior* priors, const double* fixed, const double* loc,
+                         const double* rho, uint32_t tag) {
+    if (!s || !priors || !fixed || !loc || !rho) return fail(RTU_E_ARG, "rtu_elbo_init: null argument");
+    const Sizes& z = s->z;
+    for (int i = 0; i < z.n_sites; ++i) {
+        const rtu_prior& p = priors[i];
+        if (p.kind < 0 || p.kind > 3 || p.space < 0 || p.space > 1) return fail(RTU_E_ARG, "bad prior kind/space");
+        if ((p.kind == RTU_PRIOR_NORMAL || p.kind == RTU_PRIOR_TRUNC_NORMAL) && !(p.b > 0))
+            return fail(RTU_E_ARG, "normal prior needs sd > 0");
+        if (p.kind == RTU_PRIOR_UNIFORM && !(p.b > p.a)) return fail(RTU_E_ARG, "uniform prior needs b > a");
+        if ((p.kind == RTU_PRIOR_TRUNC_NORMAL || p.kind == RTU_PRIOR_LINEAR) && !(p.d > p.c))
+            return fail(RTU_E_ARG, "bounded prior needs d > c");
+        if (p.kind == RTU_PRIOR_LINEAR && !(p.a >= -1.0)) return fail(RTU_E_ARG, "linear prior needs a >= -1");
+    }
+    std::vector<double> zero((size_t)2 * z.n_state, 0.0);
+    long long t0 = 0;
+    cudaError_t ce;
+    if ((ce = cudaMemcpy(s->st.prior, priors, (size_t)z.n_sites * sizeof(rtu_prior), cudaMemcpyHostToDevice)) ||
+        (ce = cudaMemcpy(s->st.fixed, fixed, (size_t)z.n_phys * 8, cudaMemcpyHostToDevice)) ||
+        (ce = cudaMemcpy(s->st.loc, loc, (size_t)z.n_state * 8, cudaMemcpyHostToDevice)) ||
+        (ce = cudaMemcpy(s->st.rho, rho, (size_t)z.n_state * 8, cudaMemcpyHostToDevice)) ||
+        (ce = cudaMemcpy(s->st.m, zero.data(), zero.size() * 8, cudaMemcpyHostToDevice)) ||
+        (ce = cudaMemcpy(s->st.v, zero.data(), zero.size() * 8, cudaMemcpyHostToDevice)) ||
+        (ce = cudaMemcpy(s->st.t, &t0, 8, cudaMemcpyHostToDevice)))
+        return fail(RTU_E_CUDA, std::string("rtu_elbo_init: ") + cudaGetErrorString(ce));
+    s->st.tag = tag;
+    s->elbo_ready = true;
+    return RTU_OK;
+}
+
+rtu_status rtu_elbo_step(rtu_system* const* sys, int32_t n, int32_t n_samples, uint64_t seed, double lr,
+                         double* elbo_out, void* stream) {
+    if (n < 0 || (n > 0 && !sys)) return fail(RTU_E_ARG, "bad system array");
+    if (n_samples < 1 || n_samples > MAXS) return fail(RTU_E_ARG, "n_samples must be in [1, 8]");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    for (int i = 0; i < n; ++i) {
+        if (!sys[i]) return fail(RTU_E_ARG, "null system");
+        if (!sys[i]->elbo_ready) return fail(RTU_E_ARG, "rtu_elbo_init was not called for a system");
+        if (sys[i]->d.n_slots < n_samples) return fail(RTU_E_ARG, "n_samples exceeds the system's n_slots");
+        for (int j = 0; j < i; ++j)
+            if (sys[j] == sys[i]) return fail(RTU_E_ARG, "a system appears twice in one ELBO step");
+    }
+    static thread_local ElboBatch B;
+    std::vector<rtu_system*> es;
+    std::vector<rtu_eval> ev;
+    for (int c0 = 0; c0 < n; c0 += ELBO_MAXB) {
+        B.n = std::min(ELBO_MAXB, n - c0);
+        es.clear();
+        ev.clear();
+        for (int i = 0; i < B.n; ++i) {
+            rtu_system* s = sys[c0 + i];
+            ElboArgs& a = B.e[i];
+            memset(&a, 0, sizeof(a));
+            a.st = s->st;
+            a.profile = s->d.profile;
+            a.nsub = s->d.sub_kind ? s->d.n_sub : 0;
+            a.nl = s->z.nl;
+            a.n_src = s->d.n_src;
+            a.f64 = s->d.precision == RTU_F64;
+            a.n_samples = n_samples;
+            a.seed = seed;
+            a.lr = lr;
+            a.n_cta_upd = s->z.n_cta_upd;
+            a.elbo_out = elbo_out ? elbo_out + c0 + i : nullptr;
+            for (int k = 0; k < n_samples; ++k) {
+                const SampleBufs& b = s->sbuf[k];
+                a.lens[k] = b.lens; a.ps[k] = b.ps; a.lat[k] = b.lat; a.stats[k] = b.stats;
+                a.glens[k] = b.glens; a.gps[k] = b.gps; a.glat[k] = b.glat;
+                rtu_eval e;
+                memset(&e, 0, sizeof(e));
+                e.slot = k;
+                e.lens = b.lens; e.latents = b.lat; e.ps = b.ps; e.stats = b.stats;
+                e.g_latents = b.glat; e.g_lens = b.glens; e.g_ps = b.gps;
+                es.push_back(s);
+                ev.push_back(e);
+            }
+        }
+        rtu_status r;
+        if ((r = launch_elbo("k_elbo_sample", k_elbo_sample, B, t_elbo_sample, ELBO_NT, st))) return r;
+        if ((r = run(es.data(), ev.data(), (int)es.size(), PH_FORWARD | PH_ADJOINT, stream))) return r;
+        if ((r = launch_elbo("k_elbo_update", k_elbo_update, B, t_elbo_update, ELBO_NT, st))) return r;
+        if ((r = launch_elbo("k_elbo_final", k_elbo_final, B, t_elbo_one, 32, st))) return r;
+    }
+    return RTU_OK;
+}
+
+size_t rtu_elbo_state_bytes(const rtu_system* s) {
+    if (!s) return 0;
+    return (size_t)6 * s->z.n_state * 8 + 8;
+}
+
+rtu_status rtu_elbo_export(const rtu_system* s, void* host, size_t bytes) {
+    if (!s || !host || bytes < rtu_elbo_state_bytes(s)) return fail(RTU_E_ARG, "rtu_elbo_export: bad buffer");
+    const size_t n = (size_t)s->z.n_state * 8;
+    char* h = static_cast<char*>(host);
+    cudaError_t ce;
+    if ((ce = cudaMemcpy(h, s->st.loc, n, cudaMemcpyDeviceToHost)) ||
+        (ce = cudaMemcpy(h + n, s->st.rho, n, cudaMemcpyDeviceToHost)) ||
+        (ce = cudaMemcpy(h + 2 * n, s->st.m, 2 * n, cudaMemcpyDeviceToHost)) ||
+        (ce = cudaMemcpy(h + 4 * n, s->st.v, 2 * n, cudaMemcpyDeviceToHost)) ||
+        (ce = cudaMemcpy(h + 6 * n, s->st.t, 8, cudaMemcpyDeviceToHost)))
+        return fail(RTU_E_CUDA, std::string("rtu_elbo_export: ") + cudaGetErrorString(ce));
+    return RTU_OK;
+}
+
+rtu_status rtu_elbo_import(rtu_system* s, const void* host, size_t bytes) {
+    if (!s || !host || bytes < rtu_elbo_state_bytes(s)) return fail(RTU_E_ARG, "rtu_elbo_import: bad buffer");
+    if (!s->elbo_ready) return fail(RTU_E_ARG, "rtu_elbo_import: call rtu_elbo_init first (priors, fixed values)");
+    const size_t n = (size_t)s->z.n_state * 8;
+    const char* h = static_cast<const char*>(host);
+    cudaError_t ce;
+    if ((ce = cudaMemcpy(s->st.loc, h, n, cudaMemcpyHostToDevice)) ||
+        (ce = cudaMemcpy(s->st.rho, h + n, n, cudaMemcpyHostToDevice)) ||
+        (ce = cudaMemcpy(s->st.m, h + 2 * n, 2 * n, cudaMemcpyHostToDevice)) ||
+        (ce = cudaMemcpy(s->st.v, h + 4 * n, 2 * n, cudaMemcpyHostToDevice)) ||
+        (ce = cudaMemcpy(s->st.t, h + 6 * n, 8, cudaMemcpyHostToDevice)))
+        return fail(RTU_E_CUDA, std::string("rtu_elbo_import: ") + cudaGetErrorString(ce));
+    return RTU_OK;
 }
 
 }  // extern "C"

@@ -100,7 +100,8 @@ struct Batch {
 constexpr int TR_HDR = 8;
 __host__ __device__ constexpr int tr_size(int K) { return TR_HDR + 8 * K + 4 * MAXM; }
 
-__device__ __forceinline__ int find_eval(const Batch& B, int bid) {
+template <typename BatchT>
+__device__ __forceinline__ int find_eval(const BatchT& B, int bid) {
     int lo = 0, hi = B.n - 1;
     while (lo < hi) {
         int mid = (lo + hi + 1) >> 1;

@@ -245,3 +245,53 @@ def poisson_arrivals(n: int, rate_hz: float, seed: int) -> np.ndarray:
     """Arrival times (s) of a Poisson stream: cumulative exponential gaps."""
     rng = np.random.default_rng(seed)
     return np.cumsum(rng.exponential(1.0 / rate_hz, size=n))
+
+
+# ---------------------------------------------------------------------------
+# priors of the variational fit (Table A1) -- inputs to both sides
+# ---------------------------------------------------------------------------
+PRIOR_NORMAL, PRIOR_UNIFORM, PRIOR_TRUNC_NORMAL, PRIOR_LINEAR = 0, 1, 2, 3
+SPACE_LINEAR, SPACE_LOG10 = 0, 1
+
+
+def default_priors(profile, sub_kind, n_sub, family, subs=None):
+    """Prior (kind, space, a, b, c, d) of each non-latent site, in the site order
+    theta_E, [gamma], e1, e2, x0, y0, Gamma1, Gamma2, per subhalo (log10 kappa_s,
+    log10 r_s, x_s, y_s), power-spectrum parameters, log10 alpha_src.
+
+    Table A1: theta_E U(-10,15); gamma G(2, 0.2) on [1, 3]; e G(0, 0.1); centre
+    G(0, 0.5); shear U(-0.2, 0.2); log10 kappa_s U(-10, 4); log10 r_s U(-4, 4);
+    subhalo position G(guess, 0.05); n_src T(-1, 0.1, 10); zeta 10^G(2.1, 1.1);
+    sigma_src 10^U(-5, 2); alpha_src 10^U(-1, 1).  The power-law and Matern-like
+    spectra are not in the paper: A 10^U(-6, 6), beta U(1, 5), k0 10^G(0.3, 1)."""
+    U, G, TG, T = PRIOR_UNIFORM, PRIOR_NORMAL, PRIOR_TRUNC_NORMAL, PRIOR_LINEAR
+    L, LG = SPACE_LINEAR, SPACE_LOG10
+    p = [(U, L, -10.0, 15.0, 0.0, 0.0)]
+    if profile == PROFILE_EPL:
+        p.append((TG, L, 2.0, 0.2, 1.0, 3.0))
+    p += [(G, L, 0.0, 0.1, 0, 0), (G, L, 0.0, 0.1, 0, 0), (G, L, 0.0, 0.5, 0, 0), (G, L, 0.0, 0.5, 0, 0),
+          (U, L, -0.2, 0.2, 0, 0), (U, L, -0.2, 0.2, 0, 0)]
+    for h in range(n_sub if sub_kind else 0):
+        gx, gy = (0.0, 0.0) if subs is None else (float(subs[h][3]), float(subs[h][4]))
+        p += [(U, LG, -10.0, 4.0, 0, 0), (U, LG, -4.0, 4.0, 0, 0), (G, L, gx, 0.05, 0, 0), (G, L, gy, 0.05, 0, 0)]
+    if family == PS_POWER_LAW:
+        p += [(U, LG, -6.0, 6.0, 0, 0), (U, L, 1.0, 5.0, 0, 0)]
+    elif family == PS_MATERN_LIKE:
+        p += [(U, LG, -6.0, 6.0, 0, 0), (G, LG, 0.3, 1.0, 0, 0)]
+    else:
+        p += [(U, LG, -5.0, 2.0, 0, 0), (T, L, -1.0, 0.0, 0.1, 10.0), (G, LG, 2.1, 1.1, 0, 0)]
+    p.append((U, LG, -1.0, 1.0, 0, 0))
+    return p
+
+
+def unconstrain(v, prior):
+    """Unconstrained start value u of a site whose constrained value is v (the
+    inverse of the site's support map): identity for normal priors, the logit of
+    the position inside the interval otherwise."""
+    kind, _space, a, b, c, d = prior
+    if kind == PRIOR_NORMAL:
+        return float(v)
+    lo, hi = (a, b) if kind == PRIOR_UNIFORM else (c, d)
+    t = (v - lo) / (hi - lo)
+    t = min(max(t, 1e-12), 1 - 1e-12)
+    return math.log(t / (1.0 - t))

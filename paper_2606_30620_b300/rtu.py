@@ -52,6 +52,11 @@ class Eval(ctypes.Structure):
         "g_latents", "g_lens", "g_ps")]
 
 
+class Prior(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("space", ctypes.c_int32), ("a", ctypes.c_double),
+                ("b", ctypes.c_double), ("c", ctypes.c_double), ("d", ctypes.c_double)]
+
+
 _lib.rtu_workspace_size.argtypes = [ctypes.POINTER(SystemDesc)]
 _lib.rtu_workspace_size.restype = ctypes.c_size_t
 _lib.rtu_system_create.argtypes = [ctypes.POINTER(SystemDesc), ctypes.c_void_p, ctypes.c_size_t,
@@ -63,6 +68,20 @@ for _name in ("rtu_build_grid", "rtu_forward", "rtu_adjoint"):
     getattr(_lib, _name).argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(Eval), ctypes.c_int32,
                                      ctypes.c_void_p]
     getattr(_lib, _name).restype = ctypes.c_int32
+_lib.rtu_n_sites.argtypes = [ctypes.POINTER(SystemDesc)]
+_lib.rtu_n_sites.restype = ctypes.c_int32
+_lib.rtu_elbo_init.argtypes = [ctypes.c_void_p, ctypes.POINTER(Prior), ctypes.POINTER(ctypes.c_double),
+                               ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), ctypes.c_uint32]
+_lib.rtu_elbo_init.restype = ctypes.c_int32
+_lib.rtu_elbo_step.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64,
+                               ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p]
+_lib.rtu_elbo_step.restype = ctypes.c_int32
+_lib.rtu_elbo_state_bytes.argtypes = [ctypes.c_void_p]
+_lib.rtu_elbo_state_bytes.restype = ctypes.c_size_t
+_lib.rtu_elbo_export.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]
+_lib.rtu_elbo_export.restype = ctypes.c_int32
+_lib.rtu_elbo_import.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]
+_lib.rtu_elbo_import.restype = ctypes.c_int32
 _lib.rtu_profile_enable.argtypes = [ctypes.c_int32]
 _lib.rtu_profile_enable.restype = ctypes.c_int32
 _lib.rtu_profile_report.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
@@ -71,8 +90,9 @@ _lib.rtu_last_error.restype = ctypes.c_char_p
 _lib.rtu_version.restype = ctypes.c_char_p
 
 EXPORTED = ("rtu_workspace_size", "rtu_system_create", "rtu_system_destroy", "rtu_build_grid",
-            "rtu_forward", "rtu_adjoint", "rtu_profile_enable", "rtu_profile_report", "rtu_last_error",
-            "rtu_version")
+            "rtu_forward", "rtu_adjoint", "rtu_n_sites", "rtu_elbo_init", "rtu_elbo_step",
+            "rtu_elbo_state_bytes", "rtu_elbo_export", "rtu_elbo_import", "rtu_profile_enable",
+            "rtu_profile_report", "rtu_last_error", "rtu_version")
 
 
 def _check(rc: int, what: str):
@@ -147,6 +167,41 @@ class System:
         return cls(m.data, m.mask, m.psf, m.sigma, m.pix, m.s_super, m.n_src, m.src_pitch, m.profile,
                    m.ps_family, m.sub_kind, 0 if m.subs is None else m.subs.shape[0], precision,
                    n_slots=n_slots, device=device)
+
+    @property
+    def n_sites(self) -> int:
+        return int(_lib.rtu_n_sites(ctypes.byref(self.desc)))
+
+    def elbo_init(self, priors, fixed, loc, rho, tag: int):
+        """Set the guide: priors[n_sites] as (kind, space, a, b, c, d), the physical
+        values of the non-site entries, loc/rho over n_sites + n_src^2, stream tag."""
+        ns = self.n_sites
+        if len(priors) != ns:
+            raise ValueError(f"{ns} priors expected")
+        arr = (Prior * ns)(*[Prior(int(p[0]), int(p[1]), *[float(x) for x in p[2:6]]) for p in priors])
+        fixed = np.ascontiguousarray(fixed, dtype=np.float64)
+        loc = np.ascontiguousarray(loc, dtype=np.float64)
+        rho = np.ascontiguousarray(rho, dtype=np.float64)
+        if fixed.size != self.n_lens + self.n_ps or loc.size != ns + self.n_src ** 2 or rho.size != loc.size:
+            raise ValueError("fixed / loc / rho sizes do not match the system")
+        dp = ctypes.POINTER(ctypes.c_double)
+        _check(_lib.rtu_elbo_init(self.handle, arr, fixed.ctypes.data_as(dp), loc.ctypes.data_as(dp),
+                                  rho.ctypes.data_as(dp), int(tag) & 0xFFFFFFFF), "rtu_elbo_init")
+
+    def elbo_export(self) -> bytes:
+        n = _lib.rtu_elbo_state_bytes(self.handle)
+        buf = ctypes.create_string_buffer(n)
+        _check(_lib.rtu_elbo_export(self.handle, buf, n), "rtu_elbo_export")
+        return buf.raw
+
+    def elbo_import(self, blob: bytes):
+        _check(_lib.rtu_elbo_import(self.handle, blob, len(blob)), "rtu_elbo_import")
+
+    def elbo_state(self):
+        """(loc, rho, step) of the guide as numpy arrays (a synchronous copy)."""
+        raw = np.frombuffer(self.elbo_export(), dtype=np.float64)
+        n = self.n_sites + self.n_src ** 2
+        return raw[:n].copy(), raw[n:2 * n].copy(), int(np.frombuffer(raw[6 * n:6 * n + 1].tobytes(), np.int64)[0])
 
     def close(self):
         if getattr(self, "handle", None) is not None and self.handle.value:
@@ -249,6 +304,15 @@ def rtu_forward(bindings, stream=None):
 
 def rtu_adjoint(bindings, stream=None):
     Batch(bindings).adjoint(stream)
+
+
+def rtu_elbo_step(systems, n_samples: int, seed: int, lr: float, elbo_out=None, stream=None):
+    """One SVI step for each system (batched); elbo_out: device float64 [len(systems)]."""
+    n = len(systems)
+    arr = (ctypes.c_void_p * n)(*[s.handle.value for s in systems])
+    out = None if elbo_out is None else ctypes.c_void_p(elbo_out.data_ptr())
+    _check(_lib.rtu_elbo_step(arr, n, int(n_samples), int(seed) & 0xFFFFFFFFFFFFFFFF, float(lr), out,
+                              _stream_ptr(stream)), "rtu_elbo_step")
 
 
 class RTUForward(torch.autograd.Function):

@@ -1,0 +1,260 @@
+"""Continuous-batching server of ELBO-step requests for many lens systems.
+
+Each request asks for optimiser steps of one lens system (its observation
+and starting guide).  The server keeps every admitted system's workspace,
+latents and Adam state on the device, admits new systems while their
+workspace fits an HBM budget, and batches the ready requests of systems of
+uneven image and grid sizes into one ``rtu_elbo_step`` call (one launch per
+step of the hot path for the whole batch).  Up to ``n_streams`` batches are in
+flight on separate CUDA streams, so requests that arrive while others run
+are admitted as memory and stream slots free up and their work overlaps on
+the device.  A request completes when the CUDA event recorded after its
+batch has been reached; its latency is completion minus arrival time.
+"""
+from __future__ import annotations
+
+import math
+import time
+from collections import deque
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+from . import inputs as I
+from . import rtu
+
+
+@dataclass
+class Request:
+    rid: int
+    system_id: int
+    mock: I.Mock
+    arrival: float                  # seconds after the stream starts
+    n_steps: int = 1
+    done_steps: int = 0
+    finish: float | None = None
+    elbo: float | None = None
+
+
+@dataclass
+class Resident:
+    system: rtu.System
+    nbytes: int
+    last_used: float
+    pending: int = 0
+
+
+def guide_start(m: I.Mock, rho0: float = -3.0):
+    """Priors (Table A1), fixed physical values and the starting guide of a mock:
+    loc at the mock's own parameters, softplus(rho0) scale."""
+    n_sub = 0 if m.subs is None else m.subs.shape[0]
+    priors = I.default_priors(m.profile, m.sub_kind, n_sub, m.ps_family, m.subs)
+    phys = list(m.lens) + ([] if m.subs is None else list(m.subs.ravel())) + list(m.ps)
+    targets = _targets(m.profile, m.sub_kind, n_sub, len(m.ps))
+    loc = [I.unconstrain(math.log10(phys[t]) if p[1] == I.SPACE_LOG10 else phys[t], p)
+           for t, p in zip(targets, priors)]
+    loc = np.array(loc + list(m.latents.ravel()))
+    rho = np.full(loc.size, rho0)
+    return priors, np.array(phys), loc, rho
+
+
+def _targets(profile, sub_kind, n_sub, nps):
+    # site order of the ABI: theta_E, [gamma], e1, e2, x0, y0, G1, G2, per subhalo
+    # (kappa_s, r_s, x_s, y_s), then the nps power-spectrum entries (alpha_src last)
+    idx = [0] + ([1] if profile == I.PROFILE_EPL else []) + [2, 3, 4, 5, 6, 7]
+    ns = n_sub if sub_kind else 0
+    for h in range(ns):
+        idx += [8 + 5 * h, 8 + 5 * h + 1, 8 + 5 * h + 3, 8 + 5 * h + 4]
+    nl = 8 + 5 * ns
+    return idx + [nl + k for k in range(nps)]
+
+
+def workspace_bytes(m: I.Mock, precision: int, n_samples: int) -> int:
+    """Device bytes a system occupies while resident (its workspace + observation)."""
+    d = rtu.SystemDesc(m.n_img, m.s_super, m.n_src, m.psf.shape[0], m.profile, m.sub_kind,
+                       0 if m.subs is None else m.subs.shape[0], m.ps_family, precision, 22, 21, n_samples,
+                       m.pix, m.src_pitch, m.sigma, 1 << 20, 1 << 20, 1 << 20)
+    import ctypes
+    ws = rtu._lib.rtu_workspace_size(ctypes.byref(d))
+    tb = 8 if precision == rtu.RTU_F64 else 4
+    return int(ws) + m.n_img * m.n_img * (tb + 1) + m.psf.size * tb + 4096
+
+
+class Server:
+    def __init__(self, budget_bytes: int, max_batch: int = 32, n_samples: int = 1, lr: float = 1e-3,
+                 seed: int = 0, precision: int = rtu.RTU_F32, n_streams: int = 2, device: str = "cuda",
+                 keep_resident: bool = False):
+        self.budget = int(budget_bytes)
+        self.max_batch = max_batch
+        self.n_samples = n_samples
+        self.lr = lr
+        self.seed = seed
+        self.precision = precision
+        self.device = torch.device(device)
+        self.streams = [torch.cuda.Stream(device=self.device) for _ in range(n_streams)]
+        self.admit_stream = torch.cuda.Stream(device=self.device)
+        self.keep_resident = keep_resident
+        self.resident: dict[int, Resident] = {}
+        self.used = 0
+        self.peak_used = 0
+        self.inflight = []        # (event, stream index, [requests], elbo tensor)
+        self.batches = 0
+        self.batch_sizes = []
+
+    # ---------------------------------------------------------------- admission
+    def _admit(self, req: Request, now: float) -> bool:
+        r = self.resident.get(req.system_id)
+        if r is not None:
+            r.last_used = now
+            return True
+        need = workspace_bytes(req.mock, self.precision, self.n_samples)
+        if need > self.budget:
+            raise ValueError(f"system {req.system_id} needs {need} bytes, above the budget")
+        if self.used + need > self.budget:
+            self._evict(need)
+            if self.used + need > self.budget:
+                return False
+        with torch.cuda.stream(self.admit_stream):
+            s = rtu.System.from_mock(req.mock, precision=self.precision, n_slots=self.n_samples,
+                                     device=self.device)
+            pr, ph, loc, rho = guide_start(req.mock)
+            s.elbo_init(pr, ph, loc, rho, tag=req.system_id)
+        self.admit_stream.synchronize()
+        self.resident[req.system_id] = Resident(s, need, now)
+        self.used += need
+        self.peak_used = max(self.peak_used, self.used)
+        return True
+
+    def _evict(self, need: int):
+        # idle residents (no queued or running request), least recently used first
+        idle = sorted((r.last_used, sid) for sid, r in self.resident.items() if r.pending == 0)
+        for _, sid in idle:
+            if self.used + need <= self.budget:
+                break
+            self._release(sid)
+
+    def _release(self, sid: int):
+        r = self.resident.pop(sid)
+        r.system.close()
+        self.used -= r.nbytes
+
+    # ----------------------------------------------------------------- batching
+    def _launch(self, reqs, k):
+        st = self.streams[k]
+        out = torch.empty(len(reqs), dtype=torch.float64, device=self.device)
+        systems = [self.resident[r.system_id].system for r in reqs]
+        st.wait_stream(self.admit_stream)
+        rtu.rtu_elbo_step(systems, self.n_samples, self.seed, self.lr, out, stream=st)
+        ev = torch.cuda.Event()
+        ev.record(st)
+        self.inflight.append((ev, k, reqs, out))
+        self.batches += 1
+        self.batch_sizes.append(len(reqs))
+
+    def _poll(self, now_fn, wait=False):
+        done_any = False
+        keep = []
+        for item in self.inflight:
+            ev, k, reqs, out = item
+            if wait or ev.query():
+                ev.synchronize()
+                t = now_fn()
+                vals = out.cpu().numpy()
+                for r, v in zip(reqs, vals):
+                    r.done_steps += 1
+                    r.elbo = float(v)
+                    res = self.resident[r.system_id]
+                    res.pending -= 1
+                    if r.done_steps >= r.n_steps:
+                        r.finish = t
+                done_any = True
+            else:
+                keep.append(item)
+        self.inflight = keep
+        return done_any
+
+    def run(self, requests, realtime: bool = True):
+        """Serve a list of requests; with realtime=False all arrive at t = 0
+        (saturation).  Returns the latency/throughput summary."""
+        reqs = sorted(requests, key=lambda r: r.arrival)
+        arrivals = deque(reqs)
+        ready = deque()
+        t0 = time.perf_counter()
+        now = (lambda: time.perf_counter() - t0)
+        while arrivals or ready or self.inflight:
+            tn = now()
+            while arrivals and (not realtime or arrivals[0].arrival <= tn):
+                r = arrivals.popleft()
+                if not realtime:
+                    r.arrival = 0.0
+                ready.append(r)
+            self._poll(now)
+            busy = {k for _, k, _, _ in self.inflight}
+            free = [k for k in range(len(self.streams)) if k not in busy]
+            if ready and free:
+                batch, skipped, ids = [], deque(), set()
+                while ready and len(batch) < self.max_batch:
+                    r = ready.popleft()
+                    if r.system_id in ids or (r.system_id in self.resident
+                                              and self.resident[r.system_id].pending > 0):
+                        skipped.append(r)          # one step per system per batch
+                        continue
+                    if not self._admit(r, tn):
+                        skipped.append(r)
+                        break
+                    self.resident[r.system_id].pending += 1
+                    ids.add(r.system_id)
+                    batch.append(r)
+                ready.extendleft(reversed(skipped))
+                if batch:
+                    self._launch(batch, free[0])
+                    continue
+            # release systems whose requests are all complete
+            if not self.keep_resident:
+                for sid in [sid for sid, r in self.resident.items() if r.pending == 0]:
+                    if not any(q.system_id == sid for q in ready):
+                        self._release(sid)
+            if self.inflight and not (ready and free):
+                # nothing to launch: wait for the oldest batch or the next arrival
+                if not arrivals or arrivals[0].arrival > now() + 1e-4:
+                    self.inflight[0][0].synchronize()
+            elif not self.inflight and arrivals and realtime:
+                time.sleep(max(0.0, min(1e-3, arrivals[0].arrival - now())))
+            # requests with more steps go back to the ready queue
+            for r in reqs:
+                if r.finish is None and r.done_steps > 0 and r.done_steps < r.n_steps and r not in ready \
+                        and self.resident.get(r.system_id) and self.resident[r.system_id].pending == 0:
+                    ready.append(r)
+        wall = now()
+        lat = np.array([r.finish - r.arrival for r in reqs])
+        return {"systems": len(reqs), "wall_s": wall, "systems_per_s": len(reqs) / wall,
+                "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                "mean_batch": float(np.mean(self.batch_sizes)) if self.batch_sizes else 0.0,
+                "batches": self.batches, "peak_bytes": self.peak_used}
+
+
+def serve_plain(requests, n_samples=1, lr=1e-3, seed=0, precision=rtu.RTU_F32, device="cuda"):
+    """The plain per-system path: each request alone, one call per system, in order."""
+    t0 = time.perf_counter()
+    lat = []
+    for r in sorted(requests, key=lambda q: q.arrival):
+        s = rtu.System.from_mock(r.mock, precision=precision, n_slots=n_samples, device=device)
+        pr, ph, loc, rho = guide_start(r.mock)
+        s.elbo_init(pr, ph, loc, rho, tag=r.system_id)
+        out = torch.empty(1, dtype=torch.float64, device=device)
+        for _ in range(r.n_steps):
+            rtu.rtu_elbo_step([s], n_samples, seed, lr, out)
+        r.elbo = float(out.cpu()[0])
+        r.finish = time.perf_counter() - t0
+        lat.append(r.finish - 0.0)
+        s.close()
+    wall = time.perf_counter() - t0
+    return {"systems": len(requests), "wall_s": wall, "systems_per_s": len(requests) / wall}
+
+
+def make_stream(n: int, rate_hz: float, seed: int = 5000):
+    """The serving workload: n systems, Poisson arrivals, mixed sizes and profiles."""
+    times = I.poisson_arrivals(n, rate_hz, seed)
+    return [Request(rid=k, system_id=k, mock=I.config_serving_system(seed + 1 + k), arrival=float(times[k]))
+            for k in range(n)]
