@@ -12,24 +12,30 @@ namespace rtu {
 //              [8 + a*2MAXM + t]  d logL / d beta of the ray selected at (axis a, target t)
 constexpr int TADJ_SEL = 8;
 
-__global__ void __launch_bounds__(256) k_cdf_adj(const __grid_constant__ Batch B) {
+constexpr int CDF_NT = 1024;
+__global__ void __launch_bounds__(CDF_NT) k_cdf_adj(const __grid_constant__ Batch B) {
     const EvalArgs& E = B.e[blockIdx.x];
     const int M = E.n_nodes, D = E.degree, K = M + 2, N = E.n_mask;
     const int nacc = NACC_FIX + 4 * K + 5 * (E.sub_kind ? E.n_sub : 0);
+    const int ncol = NACC_FIX + 4 * K;
     __shared__ double tot[NACC_FIX + 4 * (MAXM + 2)];
-    // column sums over the render-adjoint CTAs in fixed order
-    for (int col = threadIdx.x; col < NACC_FIX + 4 * K; col += blockDim.x) {
+    __shared__ double gXr[2][MAXM + 2], gpr[2][MAXM + 2], gc[2][MAXM], gQ[2][MAXM];
+    __shared__ double gfl_s[2];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    // column sums over the render-adjoint CTAs: one warp per column, fixed lane
+    // stride and a fixed shuffle tree
+    for (int col = wid; col < ncol; col += CDF_NT / 32) {
         double s = 0.0;
-        for (int t = 0; t < E.n_cta_r; ++t) s += E.apart[(size_t)t * nacc + col];
-        tot[col] = s;
+        for (int t = lane; t < E.n_cta_r; t += 32) s += E.apart[(size_t)t * nacc + col];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) tot[col] = s;
     }
     __syncthreads();
-    if (threadIdx.x != 0) return;
     const double* tr = E.trd;
     const double sigma = tr[2];
-    double dmu[2] = {tot[8], tot[9]};
-    double dsig = tot[10];
-    for (int a = 0; a < 2; ++a) {
+    // back through the guard (sequential in the knots; one thread per axis)
+    if (threadIdx.x < 2) {
+        const int a = threadIdx.x;
         const double* Xf = tr + TR_HDR + a * K;          // guarded knots
         const double* Xr = tr + TR_HDR + (6 + a) * K;    // raw knots
         const double* pr = tr + TR_HDR + (4 + a) * K;    // raw p'
@@ -41,59 +47,59 @@ __global__ void __launch_bounds__(256) k_cdf_adj(const __grid_constant__ Batch B
         if (!span_ok) span = fabs(span) + 1e-300;
         const double floor_d = 1e-6 * span;
         double gfl = 0.0;
-        double gpr[MAXM + 2], gXr[MAXM + 2], gXf[MAXM + 2];
+        double gXf[MAXM + 2];
         for (int j = 0; j < K; ++j) {
-            // slope d = 1/p'  ->  d L/d p' = -gd d^2
-            const double gp = -gd[j] * sl[j] * sl[j];
-            if (pr[j] < floor_d) { gpr[j] = 0.0; gfl += gp; } else gpr[j] = gp;
+            const double gp = -gd[j] * sl[j] * sl[j];        // slope d = 1/p'
+            if (pr[j] < floor_d) { gpr[a][j] = 0.0; gfl += gp; } else gpr[a][j] = gp;
             gXf[j] = gX[j];
         }
         for (int j = K - 1; j >= 1; --j) {
-            if (Xf[j] != Xr[j]) { gXf[j - 1] += gXf[j]; gfl += gXf[j]; gXr[j] = 0.0; }
-            else gXr[j] = gXf[j];
+            if (Xf[j] != Xr[j]) { gXf[j - 1] += gXf[j]; gfl += gXf[j]; gXr[a][j] = 0.0; }
+            else gXr[a][j] = gXf[j];
         }
-        gXr[0] = gXf[0];
-        if (span_ok) { gXr[K - 1] += 1e-6 * gfl; gXr[0] -= 1e-6 * gfl; }
-        // X(t) = sum c_k T_k(t), p'(u) = 2 sum c_k T_k'(t), t = -1, t_j, +1
-        double gc[MAXM];
-        for (int k = 0; k <= D; ++k) gc[k] = 0.0;
-        for (int j = 0; j < K; ++j) {
-            const double t = j == 0 ? -1.0 : (j == K - 1 ? 1.0 : 2.0 * cheb_node(j, M) - 1.0);
-            double T0 = 1.0, T1 = t, U0 = 1.0, U1 = 2.0 * t;
-            gc[0] += gXr[j];
-            if (D >= 1) gc[1] += gXr[j] * t + gpr[j] * 2.0 * 1.0 * U0;
-            for (int k = 2; k <= D; ++k) {
-                const double T2 = 2.0 * t * T1 - T0;
-                gc[k] += gXr[j] * T2 + gpr[j] * 2.0 * k * U1;
-                const double U2 = 2.0 * t * U1 - U0;
-                T0 = T1; T1 = T2; U0 = U1; U1 = U2;
-            }
-        }
-        // c_k = (2/M) sum_i Q_i T_k(t_i)  (halved for k = 0)
-        const double* Q = tr + TR_HDR + 8 * K + 2 * MAXM + a * MAXM;
-        for (int i = 0; i < M; ++i) {
-            const double ti = 2.0 * cheb_node(i + 1, M) - 1.0;
-            double T0 = 1.0, T1 = ti, g = 0.5 * gc[0];
-            if (D >= 1) g += gc[1] * ti;
-            for (int k = 2; k <= D; ++k) {
-                const double T2 = 2.0 * ti * T1 - T0;
-                g += gc[k] * T2;
-                T0 = T1; T1 = T2;
-            }
-            const double gQ = g * 2.0 / M;
-            // Q_i = z_lo + frac (z_hi - z_lo), z = (beta - mu)/sigma
-            const double h = cheb_node(i + 1, M) * (N - 1);
-            const double frac = h - floor(h);
-            E.tadj[TADJ_SEL + a * 2 * MAXM + 2 * i] = gQ * (1.0 - frac) / sigma;
-            E.tadj[TADJ_SEL + a * 2 * MAXM + 2 * i + 1] = gQ * frac / sigma;
-            dmu[a] -= gQ / sigma;
-            dsig -= gQ * Q[i] / sigma;
-        }
+        gXr[a][0] = gXf[0];
+        if (span_ok) { gXr[a][K - 1] += 1e-6 * gfl; gXr[a][0] -= 1e-6 * gfl; }
     }
-    E.tadj[0] = dmu[0] / N;
-    E.tadj[1] = dmu[1] / N;
-    E.tadj[2] = dsig / (N * sigma);
-    E.tadj[3] = tr[3];
+    __syncthreads();
+    // knots X = V c and slopes p' = dV c  ->  gc = V^T gX + dV^T gp'
+    const double* Vt = E.cheb + cheb_V(M, D);
+    const double* dVt = E.cheb + cheb_dV(M, D);
+    for (int w = threadIdx.x; w < 2 * (D + 1); w += CDF_NT) {
+        const int a = w / (D + 1), k = w % (D + 1);
+        double g = 0.0;
+        for (int j = 0; j < K; ++j) g += Vt[j * (D + 1) + k] * gXr[a][j] + dVt[j * (D + 1) + k] * gpr[a][j];
+        gc[a][k] = g;
+    }
+    __syncthreads();
+    // c = C Q  ->  gQ = C^T gc; Q = z_lo + frac (z_hi - z_lo), z = (beta - mu)/sigma
+    const double* Ct = E.cheb + cheb_C(M, D);
+    for (int w = threadIdx.x; w < 2 * M; w += CDF_NT) {
+        const int a = w / M, i = w % M;
+        double g = 0.0;
+        for (int k = 0; k <= D; ++k) g += Ct[k * M + i] * gc[a][k];
+        gQ[a][i] = g;
+        const double h = E.cheb[cheb_u(M, D) + i] * (N - 1);
+        const double frac = h - floor(h);
+        E.tadj[TADJ_SEL + a * 2 * MAXM + 2 * i] = g * (1.0 - frac) / sigma;
+        E.tadj[TADJ_SEL + a * 2 * MAXM + 2 * i + 1] = g * frac / sigma;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double dmu[2] = {tot[8], tot[9]};
+        double dsig = tot[10];
+        for (int a = 0; a < 2; ++a) {
+            const double* Q = tr + TR_HDR + 8 * K + 2 * MAXM + a * MAXM;
+            for (int i = 0; i < M; ++i) {
+                dmu[a] -= gQ[a][i] / sigma;
+                dsig -= gQ[a][i] * Q[i] / sigma;
+            }
+        }
+        E.tadj[0] = dmu[0] / N;
+        E.tadj[1] = dmu[1] / N;
+        E.tadj[2] = dsig / (N * sigma);
+        E.tadj[3] = tr[3];
+    }
+    (void)gfl_s;
 }
 
 // centre rays: d logL / d beta_i = selected-rank terms + dmu/N
@@ -106,12 +112,14 @@ __global__ void __launch_bounds__(CTA_C) k_centre_adj(const __grid_constant__ Ba
     const int M = E.n_nodes, N = E.n_mask;
     const int nsub = E.sub_kind ? E.n_sub : 0;
     const int nl = 8 + 5 * nsub;
-    __shared__ LensP L;
+    __shared__ LensK<T> L;
+    __shared__ LensK<double> Ld;
     __shared__ int sidx[2][2 * MAXM];
     __shared__ double sg[2][2 * MAXM];
     __shared__ double hdr[4], mu[2];
     __shared__ double red[CTA_C / 32][8];
-    if (threadIdx.x == 0) load_lens(L, E.lens, nsub);
+    load_lensk(L, lensk_src<T>(E.lensk));
+    if (sizeof(T) == 4) load_lensk(Ld, E.lensk);
     for (int i = threadIdx.x; i < 2 * 2 * MAXM; i += blockDim.x) {
         const int a = i / (2 * MAXM), t = i - a * 2 * MAXM;
         const bool on = t < 2 * M;
@@ -139,18 +147,24 @@ __global__ void __launch_bounds__(CTA_C) k_centre_adj(const __grid_constant__ Ba
     T acc[8];
     for (int p = 0; p < 8; ++p) acc[p] = T(0);
     if (k < N) {
-        Dual<T, 6> bx, by;
-        trace_dual<T>(L, E.profile, nsub, E.sub_kind, xd, yd, bx, by);
-        const T g0 = (T)gb[0], g1 = (T)gb[1];
-        for (int p = 0; p < 6; ++p) acc[p] = g0 * bx.d[p] + g1 * by.d[p];
-        acc[6] = -g0 * T(xd) + g1 * T(yd);
-        acc[7] = -g0 * T(yd) - g1 * T(xd);
+        const T x = (T)xd, y = (T)yd;
+        if (sizeof(T) == 4 && lens_near_core(L, x, y)) {
+            EplJ<double> J;
+            double bx, by, o8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            lens_beta_eval(Ld, xd, yd, J, bx, by);
+            lens_beta_vjp(Ld, J, xd, yd, gb[0], gb[1], o8);
+            for (int p = 0; p < 8; ++p) acc[p] = (T)o8[p];
+        } else {
+            EplJ<T> J;
+            T bx, by;
+            lens_beta_eval(L, x, y, J, bx, by);
+            lens_beta_vjp(L, J, x, y, (T)gb[0], (T)gb[1], acc);
+        }
     }
     double* out = E.cadj + (size_t)tile * nl;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int p = 0; p < 8; ++p) {
-        double v = (double)acc[p];
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        const double v = warp_sum(acc[p]);
         if (lane == 0) red[wid][p] = v;
     }
     __syncthreads();
@@ -162,14 +176,9 @@ __global__ void __launch_bounds__(CTA_C) k_centre_adj(const __grid_constant__ Ba
     for (int h = 0; h < nsub; ++h) {
         __syncthreads();
         T a5[5] = {T(0), T(0), T(0), T(0), T(0)};
-        if (k < N) {
-            Dual<T, 5> ax, ay;
-            sub_dual<T>(L, h, E.sub_kind, xd, yd, ax, ay);
-            for (int c = 0; c < 5; ++c) a5[c] = -((T)gb[0] * ax.d[c] + (T)gb[1] * ay.d[c]);
-        }
+        if (k < N) sub_vjp<T>(L, h, (T)xd, (T)yd, (T)gb[0], (T)gb[1], a5);
         for (int c = 0; c < 5; ++c) {
-            double v = (double)a5[c];
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            const double v = warp_sum(a5[c]);
             if (lane == 0) red[wid][c] = v;
         }
         __syncthreads();

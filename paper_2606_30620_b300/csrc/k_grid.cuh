@@ -24,9 +24,9 @@ __global__ void __launch_bounds__(CTA_C) k_trace_centres(const __grid_constant__
     const int ev = find_eval(B, blockIdx.x);
     const EvalArgs& E = B.e[ev];
     const int tile = blockIdx.x - B.tile0[ev];
-    __shared__ LensP L;
+    __shared__ LensK<double> L;
     __shared__ double red[6][CTA_C / 32];
-    if (threadIdx.x == 0) load_lens(L, E.lens, E.sub_kind ? E.n_sub : 0);
+    load_lensk(L, E.lensk);
     __syncthreads();
     const int k = tile * CTA_C + threadIdx.x;
     double bx = 0.0, by = 0.0;
@@ -34,7 +34,7 @@ __global__ void __launch_bounds__(CTA_C) k_trace_centres(const __grid_constant__
     if (k < E.n_mask) {
         double x, y;
         ray_pos(E.n_img, E.pix, 1, E.centre_idx[k], 0, x, y);
-        trace_value_T<double>(L, E.profile, E.sub_kind ? E.n_sub : 0, E.sub_kind, x, y, bx, by);
+        lens_beta(L, x, y, bx, by);
         E.beta[k] = bx;
         E.beta[E.n_mask + k] = by;
         v[0] = bx; v[1] = by; v[2] = bx; v[3] = bx; v[4] = by; v[5] = by;
@@ -112,26 +112,6 @@ __global__ void __launch_bounds__(CTA_C) k_centre_hist(const __grid_constant__ B
     }
 }
 
-// Chebyshev node u_j (j = 1..M) and its rank position h = u (N-1)
-__device__ __forceinline__ double cheb_node(int j, int M) {
-    return (1.0 - cos((2.0 * j - 1.0) * 3.14159265358979323846 / (2.0 * M))) / 2.0;
-}
-
-// T_k(t), dT_k/dt for k = 0..D at one point
-__device__ __forceinline__ void cheb_eval(double t, int D, const double* c, double& p, double& dp) {
-    double T0 = 1.0, T1 = t, U0 = 1.0, U1 = 2.0 * t;
-    p = c[0] * T0;
-    dp = 0.0;
-    if (D >= 1) { p += c[1] * T1; dp += c[1] * 1.0 * U0; }
-    for (int k = 2; k <= D; ++k) {
-        double T2 = 2.0 * t * T1 - T0;
-        p += c[k] * T2;
-        dp += c[k] * k * U1;           // dT_k/dt = k U_{k-1}
-        double U2 = 2.0 * t * U1 - U0;
-        T0 = T1; T1 = T2; U0 = U1; U1 = U2;
-    }
-}
-
 constexpr int SEL_NT = 1024;
 
 // One CTA per evaluation.  Dynamic shared memory:
@@ -197,7 +177,7 @@ __global__ void __launch_bounds__(SEL_NT) k_select_fit(const __grid_constant__ B
         // target ranks: node j -> floor(u_j (N-1)) and the next one
         const int nt = 2 * M;
         for (int t = tid; t < nt; t += SEL_NT) {
-            double h = cheb_node(t / 2 + 1, M) * (N - 1);
+            double h = E.cheb[cheb_u(M, D) + t / 2] * (N - 1);
             int k = (int)floor(h);
             k = k < 0 ? 0 : (k > N - 1 ? N - 1 : k);
             if (t & 1) k = k + 1 > N - 1 ? N - 1 : k + 1;
@@ -272,7 +252,7 @@ __global__ void __launch_bounds__(SEL_NT) k_select_fit(const __grid_constant__ B
         __syncthreads();
         // empirical QF at the nodes in standardized coordinates (type-7 interpolation)
         for (int j = tid; j < M; j += SEL_NT) {
-            double h = cheb_node(j + 1, M) * (N - 1);
+            double h = E.cheb[cheb_u(M, D) + j] * (N - 1);
             double frac = h - floor(h);
             double zl = (E.sel_val[a * 2 * MAXM + 2 * j] - mom[a]) / sigma;
             double zh = (E.sel_val[a * 2 * MAXM + 2 * j + 1] - mom[a]) / sigma;
@@ -282,35 +262,38 @@ __global__ void __launch_bounds__(SEL_NT) k_select_fit(const __grid_constant__ B
     }
 
     // App. C iii: Chebyshev coefficients of the QF from M = D+1 nodes by the
-    // discrete orthogonality of T_k on the nodes: c_k = (2/M) sum_j Q_j T_k(t_j)
+    // discrete orthogonality of T_k on the nodes: c = C Q (one thread per coefficient)
+    const double* Ct = E.cheb + cheb_C(M, D);
     for (int w = tid; w < 2 * (D + 1); w += SEL_NT) {
         const int a = w / (D + 1), k = w % (D + 1);
-        double s = 0.0;
-        for (int j = 0; j < M; ++j) {
-            double tj = 2.0 * cheb_node(j + 1, M) - 1.0;
-            double T0 = 1.0, T1 = tj, Tk = k == 0 ? 1.0 : tj;
-            for (int q = 2; q <= k; ++q) { Tk = 2.0 * tj * T1 - T0; T0 = T1; T1 = Tk; }
-            s += Qs[a][j] * Tk;
-        }
-        s *= 2.0 / M;
-        if (k == 0) s *= 0.5;
-        coef[a][k] = s;
+        double sacc = 0.0;
+        for (int j = 0; j < M; ++j) sacc += Ct[k * M + j] * Qs[a][j];
+        coef[a][k] = sacc;
     }
     __syncthreads();
-    // App. C iv: knots p(0), p(u_j), p(1) and slopes 1/p'(u); monotonicity guard
+    // App. C iv: knots p(0), p(u_j), p(1) and p'(u) there (one thread per point)
     double* tr = E.trd;
+    __shared__ double Xs[2][MAXM + 2], Ps[2][MAXM + 2];
+    const double* Vt = E.cheb + cheb_V(M, D);
+    const double* dVt = E.cheb + cheb_dV(M, D);
+    for (int w = tid; w < 2 * K; w += SEL_NT) {
+        const int a = w / K, j = w % K;
+        double p = 0.0, d = 0.0;
+        for (int k = 0; k <= D; ++k) {
+            p += Vt[j * (D + 1) + k] * coef[a][k];
+            d += dVt[j * (D + 1) + k] * coef[a][k];
+        }
+        Xs[a][j] = p;
+        Ps[a][j] = d;
+        tr[TR_HDR + (6 + a) * K + j] = p;       // raw knots
+        tr[TR_HDR + (4 + a) * K + j] = d;       // raw p'
+    }
+    __syncthreads();
+    // monotonicity guard, sequential in the knots (one thread per axis)
     if (tid < 2) {
         const int a = tid;
-        double X[MAXM + 2], dp[MAXM + 2];
-        for (int j = 0; j < K; ++j) {
-            double t = j == 0 ? -1.0 : (j == K - 1 ? 1.0 : 2.0 * cheb_node(j, M) - 1.0);
-            double p, d;
-            cheb_eval(t, D, coef[a], p, d);
-            X[j] = p;
-            dp[j] = 2.0 * d;
-            tr[TR_HDR + (6 + a) * K + j] = p;       // raw knots
-            tr[TR_HDR + (4 + a) * K + j] = 2.0 * d; // raw p'
-        }
+        double* X = Xs[a];
+        double* dp = Ps[a];
         int fl = 0;
         double span = X[K - 1] - X[0];
         if (!(span > 0.0)) { fl |= F_NONMONO; span = fabs(span) + 1e-300; }

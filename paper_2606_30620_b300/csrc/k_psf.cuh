@@ -6,7 +6,7 @@
 
 namespace rtu {
 
-constexpr int PSF_NT = PSF_T * PSF_T;
+constexpr int PSF_NT = PSF_T * PSF_T / 4;   // each thread: 4 horizontally adjacent outputs
 constexpr int PSF_MAXK = 31;
 constexpr int PSF_IN = PSF_T + PSF_MAXK - 1;
 
@@ -18,6 +18,8 @@ __device__ __forceinline__ void psf_tile_of(const EvalArgs& E, int tile, int& ti
 
 // m[j,i] = sum_{b,a} psf[b,a] img[j-(b-c), i-(a-c)];  resid = (d - m)/sigma^2;
 // per-CTA sums of r^2 (all pixels) and r^2 in the mask, r = (d - m)/sigma.
+// Each thread computes 4 adjacent outputs with a sliding register window over a
+// shared-memory input tile (K + 3 shared loads per 4 K fused multiply-adds).
 template <typename T>
 __global__ void __launch_bounds__(PSF_NT) k_psf_like(const __grid_constant__ Batch B) {
     const int ev = find_eval(B, blockIdx.x);
@@ -40,20 +42,35 @@ __global__ void __launch_bounds__(PSF_NT) k_psf_like(const __grid_constant__ Bat
         in[r][q] = (gj >= 0 && gj < n && gi >= 0 && gi < n) ? img[gj * n + gi] : T(0);
     }
     __syncthreads();
-    const int tx = threadIdx.x % PSF_T, ty = threadIdx.x / PSF_T;
-    const int i = i0 + tx, j = j0 + ty;
+    const int tx0 = 4 * (threadIdx.x % (PSF_T / 4)), ty = threadIdx.x / (PSF_T / 4);
+    T acc[4] = {T(0), T(0), T(0), T(0)};
+    for (int b = 0; b < K; ++b) {
+        const T* row = in[ty - b + 2 * c] + tx0 + 2 * c;     // row[u - a] for output u, tap a
+        T v0 = row[0], v1 = row[1], v2 = row[2], v3 = row[3];
+        const T* kr = kp + b * K;
+        for (int a = 0; a < K; ++a) {
+            const T w = kr[a];
+            acc[0] += w * v0; acc[1] += w * v1; acc[2] += w * v2; acc[3] += w * v3;
+            v3 = v2; v2 = v1; v1 = v0;
+            v0 = a + 1 < K ? row[-(a + 1)] : T(0);
+        }
+    }
+    const T isg = T(1) / T(E.sigma);
     double r2 = 0.0, r2m = 0.0;
-    if (i < n && j < n) {
-        T m = T(0);
-        for (int b = 0; b < K; ++b)
-            for (int a = 0; a < K; ++a) m += kp[b * K + a] * in[ty - b + 2 * c][tx - a + 2 * c];
-        const T d = reinterpret_cast<const T*>(E.data)[j * n + i];
-        const T isg = T(1) / T(E.sigma);
-        const T r = (d - m) * isg;
-        reinterpret_cast<T*>(E.resid)[j * n + i] = r * isg;
-        if (E.model_out) reinterpret_cast<T*>(E.model_out)[j * n + i] = m;
-        r2 = (double)r * (double)r;
-        r2m = E.mask[j * n + i] ? r2 : 0.0;
+    const int j = j0 + ty;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int i = i0 + tx0 + u;
+        if (i < n && j < n) {
+            const T m = acc[u];
+            const T d = reinterpret_cast<const T*>(E.data)[j * n + i];
+            const T r = (d - m) * isg;
+            reinterpret_cast<T*>(E.resid)[j * n + i] = r * isg;
+            if (E.model_out) reinterpret_cast<T*>(E.model_out)[j * n + i] = m;
+            const double rr = (double)r * (double)r;
+            r2 += rr;
+            if (E.mask[j * n + i]) r2m += rr;
+        }
     }
     for (int o = 16; o > 0; o >>= 1) {
         r2 += __shfl_down_sync(0xffffffffu, r2, o);
@@ -62,9 +79,9 @@ __global__ void __launch_bounds__(PSF_NT) k_psf_like(const __grid_constant__ Bat
     if ((threadIdx.x & 31) == 0) { red[0][threadIdx.x >> 5] = r2; red[1][threadIdx.x >> 5] = r2m; }
     __syncthreads();
     if (threadIdx.x < 2) {
-        double s = 0.0;
-        for (int w = 0; w < PSF_NT / 32; ++w) s += red[threadIdx.x][w];
-        E.lpart[tile * 2 + threadIdx.x] = s;
+        double sacc = 0.0;
+        for (int w = 0; w < PSF_NT / 32; ++w) sacc += red[threadIdx.x][w];
+        E.lpart[tile * 2 + threadIdx.x] = sacc;
     }
 }
 
@@ -108,14 +125,25 @@ __global__ void __launch_bounds__(PSF_NT) k_psf_adj(const __grid_constant__ Batc
         in[r][q] = (gj >= 0 && gj < n && gi >= 0 && gi < n) ? res[gj * n + gi] : T(0);
     }
     __syncthreads();
-    const int tx = threadIdx.x % PSF_T, ty = threadIdx.x / PSF_T;
-    const int i = i0 + tx, j = j0 + ty;
-    if (i < n && j < n) {
-        T g = T(0);
-        for (int b = 0; b < K; ++b)
-            for (int a = 0; a < K; ++a) g += kp[b * K + a] * in[ty + b][tx + a];
-        const T sc = E.dlogL ? (T)(*E.dlogL) : T(1);
-        reinterpret_cast<T*>(E.gimg)[j * n + i] = g * sc;
+    const int tx0 = 4 * (threadIdx.x % (PSF_T / 4)), ty = threadIdx.x / (PSF_T / 4);
+    T acc[4] = {T(0), T(0), T(0), T(0)};
+    for (int b = 0; b < K; ++b) {
+        const T* row = in[ty + b] + tx0;                    // row[u + a] for output u, tap a
+        T v0 = row[0], v1 = row[1], v2 = row[2], v3 = row[3];
+        const T* kr = kp + b * K;
+        for (int a = 0; a < K; ++a) {
+            const T w = kr[a];
+            acc[0] += w * v0; acc[1] += w * v1; acc[2] += w * v2; acc[3] += w * v3;
+            v0 = v1; v1 = v2; v2 = v3;
+            v3 = a + 1 < K ? row[a + 4] : T(0);
+        }
+    }
+    const T sc = E.dlogL ? (T)(*E.dlogL) : T(1);
+    const int j = j0 + ty;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int i = i0 + tx0 + u;
+        if (i < n && j < n) reinterpret_cast<T*>(E.gimg)[j * n + i] = acc[u] * sc;
     }
 }
 

@@ -141,29 +141,83 @@ __device__ __forceinline__ void load_transform(const EvalArgs& E, T* trs, T* U) 
     const int nt = TR_HDR + 4 * K;
     for (int i = threadIdx.x; i < nt; i += blockDim.x)
         trs[i] = sizeof(T) == 4 ? (T)E.trf[i] : (T)E.trd[i];
-    for (int j = threadIdx.x; j < K; j += blockDim.x) {
-        double u = j == 0 ? 0.0
-                 : (j == K - 1 ? 1.0
-                               : (1.0 - cos((2.0 * j - 1.0) * 3.14159265358979323846 / (2.0 * E.n_nodes))) / 2.0);
-        U[j] = (T)u;
-    }
+    for (int j = threadIdx.x; j < K; j += blockDim.x)
+        U[j] = (T)(j == 0 ? 0.0 : (j == K - 1 ? 1.0 : E.cheb[cheb_u(E.n_nodes, E.degree) + j - 1]));
 }
 
 // S7 + S11: one thread per image pixel, s^2 sub-rays each.
-// Near-edge FP64 island: a float ray whose grid coordinate lies within
-// EDGE_DELTA (in cells) of a cell edge or of the grid boundary is traced again in
-// double, so that the integer cell of every ray (the rays-per-cell histogram and
-// the kink of the bilinear slope used by the adjoint) is decided in double.
-constexpr double EDGE_DELTA = 2e-3;
+// Near-edge FP64 island (float mode): a ray whose grid coordinate lies within
+// EDGE_DELTA cells of a cell edge or of the grid boundary is not decided in
+// float.  The render kernel appends it to a per-evaluation list; k_render_edge
+// traces the listed rays in double (no warp divergence in the float kernel), and
+// k_render_fix completes the affected pixels in a fixed order.  So the integer
+// cell of every ray -- the rays-per-cell histogram and the kink of the bilinear
+// slope the adjoint differentiates -- is the double-precision decision.
+constexpr float EDGE_DELTA = 2e-3f;
 
 __device__ __forceinline__ bool near_edge(float gx, float gy, int n) {
-    const float lo = -(float)EDGE_DELTA, hi = (float)(n - 1) + (float)EDGE_DELTA;
+    const float lo = -EDGE_DELTA, hi = (float)(n - 1) + EDGE_DELTA;
     if (gx < lo || gx > hi || gy < lo || gy > hi) return false;     // clearly outside
     const float fx = gx - floorf(gx), fy = gy - floorf(gy);
-    return fx < (float)EDGE_DELTA || fx > 1.0f - (float)EDGE_DELTA || fy < (float)EDGE_DELTA ||
-           fy > 1.0f - (float)EDGE_DELTA;
+    return fx < EDGE_DELTA || fx > 1.0f - EDGE_DELTA || fy < EDGE_DELTA || fy > 1.0f - EDGE_DELTA;
 }
 
+// bilinear value at grid coordinate (gx, gy) with the cell decided by the caller
+template <typename T, typename G>
+__device__ __forceinline__ T bilinear_at(const G* grid, int n, int i0, int j0, T fx, T fy) {
+    const G* r0 = grid + j0 * n + i0;
+    return (T(1) - fx) * (T(1) - fy) * (T)r0[0] + fx * (T(1) - fy) * (T)r0[1] + (T(1) - fx) * fy * (T)r0[n] +
+           fx * fy * (T)r0[n + 1];
+}
+
+// cell of a grid coordinate inside [0, n-1]^2 (else -1), and the offsets in it
+template <typename T>
+__device__ __forceinline__ int cell_of(T yx, T yy, int n, T& fx, T& fy, int& i0, int& j0) {
+    if (!(yx >= T(0) && yx <= T(1) && yy >= T(0) && yy <= T(1))) return -1;
+    const T gx = yx * T(n - 1), gy = yy * T(n - 1);
+    i0 = (int)gx;
+    j0 = (int)gy;
+    i0 = i0 > n - 2 ? n - 2 : i0;
+    j0 = j0 > n - 2 ? n - 2 : j0;
+    fx = gx - T(i0);
+    fy = gy - T(j0);
+    return j0 * (n - 1) + i0;
+}
+
+// double-precision RTU coordinates of a ray from the double lens block
+__device__ __forceinline__ void rtu_coords_d(const LensK<double>& Kd, const double* trd, const double* U, int K,
+                                             double x, double y, double& yx, double& yy) {
+    double bx, by;
+    lens_beta(Kd, x, y, bx, by);
+    const double* X = trd + TR_HDR;
+    const double zx = (bx - trd[0]) / trd[2], zy = (by - trd[1]) / trd[2];
+    yx = cdf_value<double>(X, U, X + 2 * K, K, cdf_interval<double>(X, K, zx), zx);
+    yy = cdf_value<double>(X + K, U, X + 3 * K, K, cdf_interval<double>(X + K, K, zy), zy);
+}
+
+template <typename T>
+struct RenderShared {
+    LensK<T> K;
+    LensK<double> Kd;          // the FP64 islands of the float path
+    T trs[TR_HDR + 4 * (MAXM + 2)];
+    T U[MAXM + 2];
+    double trd[TR_HDR + 4 * (MAXM + 2)];
+    double Ud[MAXM + 2];
+    T offx[8];                 // sub-ray offsets ((a + 1/2)/s - 1/2) pix
+};
+
+template <typename T>
+__device__ __forceinline__ void render_setup(const EvalArgs& E, RenderShared<T>& sh) {
+    load_lensk(sh.K, lensk_src<T>(E.lensk));
+    if (sizeof(T) == 4) {
+        load_lensk(sh.Kd, E.lensk);
+        load_transform<double>(E, sh.trd, sh.Ud);
+    }
+    load_transform<T>(E, sh.trs, sh.U);
+    if (threadIdx.x < E.s) sh.offx[threadIdx.x] = (T)(((threadIdx.x + 0.5) / E.s - 0.5) * E.pix);
+}
+
+// S7 + S11: one thread per image pixel, s^2 sub-rays each.
 template <typename T>
 __global__ void __launch_bounds__(CTA_R) k_render(const __grid_constant__ Batch B) {
     const int ev = find_eval(B, blockIdx.x);
@@ -171,78 +225,129 @@ __global__ void __launch_bounds__(CTA_R) k_render(const __grid_constant__ Batch 
     const int tile = blockIdx.x - B.tile0[ev];
     extern __shared__ __align__(128) unsigned char smem_raw[];
     T* sgrid = reinterpret_cast<T*>(smem_raw);
-    __shared__ T trs[TR_HDR + 4 * (MAXM + 2)];
-    __shared__ T U[MAXM + 2];
-    __shared__ double trs_d[sizeof(T) == 4 ? TR_HDR + 4 * (MAXM + 2) : 1];
-    __shared__ double U_d[sizeof(T) == 4 ? MAXM + 2 : 1];
-    __shared__ LensP L;
+    __shared__ RenderShared<T> sh;
     __shared__ __align__(8) uint64_t mbar;
     const int n = E.n_src, K = E.n_nodes + 2;
-    if (threadIdx.x == 0) load_lens(L, E.lens, E.sub_kind ? E.n_sub : 0);
-    load_transform<T>(E, trs, U);
-    if (sizeof(T) == 4) load_transform<double>(E, trs_d, U_d);
+    render_setup<T>(E, sh);
     if (!stage_to_smem(sgrid, E.src, (uint32_t)(n * n * sizeof(T)), &mbar, E.flags)) return;
     const int npix = E.n_img * E.n_img;
     const int pixel = tile * CTA_R + threadIdx.x;
     if (pixel >= npix) return;
-    const T mux = trs[0], muy = trs[1], isg = T(1) / trs[2];
-    const T* Xx = trs + TR_HDR;
+    const T mux = sh.trs[0], muy = sh.trs[1], isg = T(1) / sh.trs[2];
+    const T* Xx = sh.trs + TR_HDR;
     const T* Xy = Xx + K;
     const T* dx_ = Xx + 2 * K;
     const T* dy_ = Xx + 3 * K;
     const int s = E.s, s2 = s * s;
-    const int nsub = E.sub_kind ? E.n_sub : 0;
-    const T nm1 = T(n - 1);
+    const int pi = pixel % E.n_img, pj = pixel / E.n_img;
+    const T cx = (T)((pi - 0.5 * (E.n_img - 1)) * E.pix), cy = (T)((pj - 0.5 * (E.n_img - 1)) * E.pix);
     T acc = T(0);
+    unsigned long long deferred = 0ull;      // bit q: sub-ray q went to the double pass
     for (int q = 0; q < s2; ++q) {
-        double xd, yd;
-        ray_pos(E.n_img, E.pix, s, pixel, q, xd, yd);
-        T bx, by;
-        trace_value<T>(L, E.profile, nsub, E.sub_kind, xd, yd, bx, by);
-        const T zx = (bx - mux) * isg, zy = (by - muy) * isg;
-        const T yx = cdf_value<T>(Xx, U, dx_, K, cdf_interval<T>(Xx, K, zx), zx);
-        const T yy = cdf_value<T>(Xy, U, dy_, K, cdf_interval<T>(Xy, K, zy), zy);
-        if (sizeof(T) == 4 && near_edge((float)(yx * nm1), (float)(yy * nm1), n)) {
-            double dbx, dby;
-            trace_value_T<double>(L, E.profile, nsub, E.sub_kind, xd, yd, dbx, dby);
-            const double* Xd = trs_d + TR_HDR;
-            const double dzx = (dbx - trs_d[0]) / trs_d[2], dzy = (dby - trs_d[1]) / trs_d[2];
-            const double gxd = (double)cdf_value<double>(Xd, U_d, Xd + 2 * K, K, cdf_interval<double>(Xd, K, dzx), dzx);
-            const double gyd = (double)cdf_value<double>(Xd + K, U_d, Xd + 3 * K, K, cdf_interval<double>(Xd + K, K, dzy), dzy);
-            int cellx = -1;
-            if (gxd >= 0.0 && gxd <= 1.0 && gyd >= 0.0 && gyd <= 1.0) {
-                int i0 = (int)(gxd * (n - 1)), j0 = (int)(gyd * (n - 1));
-                i0 = i0 > n - 2 ? n - 2 : i0;
-                j0 = j0 > n - 2 ? n - 2 : j0;
-                const T fx = (T)(gxd * (n - 1) - i0), fy = (T)(gyd * (n - 1) - j0);
-                const T* r0 = sgrid + j0 * n + i0;
-                acc += (T(1) - fx) * (T(1) - fy) * r0[0] + fx * (T(1) - fy) * r0[1] +
-                       (T(1) - fx) * fy * r0[n] + fx * fy * r0[n + 1];
-                cellx = j0 * (n - 1) + i0;
-                atomicAdd(E.ccount + cellx, 1);
+        const int qa = q % s, qb = q / s;
+        const T x = cx + sh.offx[qa], y = cy + sh.offx[qb];
+        T yx, yy;
+        if (sizeof(T) == 4 && lens_near_core(sh.K, x, y)) {
+            double xd, yd, ydx, ydy;
+            ray_pos(E.n_img, E.pix, s, pixel, q, xd, yd);
+            rtu_coords_d(sh.Kd, sh.trd, sh.Ud, K, xd, yd, ydx, ydy);
+            yx = (T)ydx;
+            yy = (T)ydy;
+            if (near_edge((float)(ydx * (n - 1)), (float)(ydy * (n - 1)), n)) {
+                // decide in double right here (rare: near-core and near-edge)
+                double fxd, fyd;
+                int i0, j0;
+                const int cell = cell_of<double>(ydx, ydy, n, fxd, fyd, i0, j0);
+                if (cell >= 0) {
+                    acc += bilinear_at<T, T>(sgrid, n, i0, j0, (T)fxd, (T)fyd);
+                    atomicAdd(E.ccount + cell, 1);
+                }
+                E.cell[(size_t)pixel * s2 + q] = cell;
+                continue;
             }
-            E.cell[(size_t)pixel * s2 + q] = cellx;
-            continue;
+        } else {
+            T bx, by;
+            lens_beta(sh.K, x, y, bx, by);
+            const T zx = (bx - mux) * isg, zy = (by - muy) * isg;
+            yx = cdf_value<T>(Xx, sh.U, dx_, K, cdf_interval<T>(Xx, K, zx), zx);
+            yy = cdf_value<T>(Xy, sh.U, dy_, K, cdf_interval<T>(Xy, K, zy), zy);
+            if (sizeof(T) == 4 && near_edge((float)(yx * T(n - 1)), (float)(yy * T(n - 1)), n)) {
+                const int at = atomicAdd(E.ecount, 1);
+                reinterpret_cast<int*>(E.rec)[at] = pixel * s2 + q;
+                E.cell[(size_t)pixel * s2 + q] = -1;
+                deferred |= 1ull << q;
+                continue;
+            }
         }
-        int cell = -1;
-        if (yx >= T(0) && yx <= T(1) && yy >= T(0) && yy <= T(1)) {
-            const T gx = yx * nm1, gy = yy * nm1;
-            int i0 = (int)gx, j0 = (int)gy;
-            i0 = i0 > n - 2 ? n - 2 : i0;
-            j0 = j0 > n - 2 ? n - 2 : j0;
-            const T fx = gx - T(i0), fy = gy - T(j0);
-            const T* r0 = sgrid + j0 * n + i0;
-            const T v = (T(1) - fx) * (T(1) - fy) * r0[0] + fx * (T(1) - fy) * r0[1] +
-                        (T(1) - fx) * fy * r0[n] + fx * fy * r0[n + 1];
-            acc += v;
-            cell = j0 * (n - 1) + i0;
+        T fx, fy;
+        int i0, j0;
+        const int cell = cell_of<T>(yx, yy, n, fx, fy, i0, j0);
+        if (cell >= 0) {
+            acc += bilinear_at<T, T>(sgrid, n, i0, j0, fx, fy);
             atomicAdd(E.ccount + cell, 1);
         }
         E.cell[(size_t)pixel * s2 + q] = cell;
     }
-    const T val = acc / T(s2);
+    if (sizeof(T) == 4) E.pdef[pixel] = deferred;
+    // pixels with deferred rays keep the partial sum; k_render_fix completes them
+    const T val = deferred ? acc : acc / T(s2);
     reinterpret_cast<T*>(E.img)[pixel] = val;
-    if (E.image_out) reinterpret_cast<T*>(E.image_out)[pixel] = val;
+    if (E.image_out && !deferred) reinterpret_cast<T*>(E.image_out)[pixel] = val;
+}
+
+// the deferred near-edge rays of the float path, traced and decided in double
+constexpr int EDGE_NT = 128;
+constexpr int EDGE_CTAS = 16;
+__global__ void __launch_bounds__(EDGE_NT) k_render_edge(const __grid_constant__ Batch B) {
+    const int ev = find_eval(B, blockIdx.x);
+    const EvalArgs& E = B.e[ev];
+    const int tile = blockIdx.x - B.tile0[ev];
+    __shared__ LensK<double> Kd;
+    __shared__ double trd[TR_HDR + 4 * (MAXM + 2)];
+    __shared__ double Ud[MAXM + 2];
+    load_lensk(Kd, E.lensk);
+    load_transform<double>(E, trd, Ud);
+    __syncthreads();
+    const int n = E.n_src, K = E.n_nodes + 2, s2 = E.s * E.s;
+    const int cnt = min(*E.ecount, E.n_img * E.n_img * s2);
+    const float* grid = reinterpret_cast<const float*>(E.src);
+    for (int k = tile * EDGE_NT + threadIdx.x; k < cnt; k += EDGE_CTAS * EDGE_NT) {
+        const int ray = reinterpret_cast<const int*>(E.rec)[k];
+        const int pixel = ray / s2, q = ray - pixel * s2;
+        double xd, yd, yx, yy;
+        ray_pos(E.n_img, E.pix, E.s, pixel, q, xd, yd);
+        rtu_coords_d(Kd, trd, Ud, K, xd, yd, yx, yy);
+        double fx, fy;
+        int i0, j0;
+        const int cell = cell_of<double>(yx, yy, n, fx, fy, i0, j0);
+        float v = 0.0f;
+        if (cell >= 0) {
+            v = bilinear_at<float, float>(grid, n, i0, j0, (float)fx, (float)fy);
+            atomicAdd(E.ccount + cell, 1);
+        }
+        E.cell[ray] = cell;
+        E.rval[ray] = v;
+    }
+}
+
+// pixels with deferred rays: partial + deferred values in sub-ray order, / s^2
+__global__ void __launch_bounds__(256) k_render_fix(const __grid_constant__ Batch B) {
+    const int ev = find_eval(B, blockIdx.x);
+    const EvalArgs& E = B.e[ev];
+    const int tile = blockIdx.x - B.tile0[ev];
+    const int pixel = tile * 256 + threadIdx.x;
+    const int npix = E.n_img * E.n_img, s2 = E.s * E.s;
+    if (pixel >= npix) return;
+    float* img = reinterpret_cast<float*>(E.img);
+    float val = img[pixel];
+    const unsigned long long mask = E.pdef[pixel];
+    if (mask) {
+        for (int q = 0; q < s2; ++q)
+            if (mask >> q & 1ull) val += E.rval[(size_t)pixel * s2 + q];
+        val = val / (float)s2;
+        img[pixel] = val;
+    }
+    if (E.image_out) reinterpret_cast<float*>(E.image_out)[pixel] = val;
 }
 
 // exclusive scan of the per-cell ray counts into offsets; cursors zeroed
@@ -279,10 +384,11 @@ __global__ void __launch_bounds__(SCAN_NT) k_scan_cells(const __grid_constant__ 
     if (tid == SCAN_NT - 1) off[nc] = base;
 }
 
-// S9 (image -> source/transform/lens part).  One thread per pixel, rays
-// recomputed with forward-mode derivatives of the main lens.  Writes one
-// counting-sorted record per in-grid ray and fixed-order per-CTA partial sums
-// of the lens, standardisation and spline-knot gradients.
+// S9 (image -> source/transform/lens part).  One thread per pixel; each ray is
+// recomputed (value + the EPL series sums) and differentiated analytically;
+// the cell comes from the forward pass.  Writes one counting-sorted record per
+// in-grid ray and fixed-order per-CTA partial sums of the lens, standardisation
+// and spline-knot gradients.
 template <typename T>
 __global__ void __launch_bounds__(CTA_R) k_render_adj(const __grid_constant__ Batch B) {
     typedef typename real4_of<T>::type R4;
@@ -296,15 +402,12 @@ __global__ void __launch_bounds__(CTA_R) k_render_adj(const __grid_constant__ Ba
     double* tab = reinterpret_cast<double*>(smem_raw + gbytes);           // [NW][2 axes][2][K]
     constexpr int NW = CTA_R / 32;
     T* gbs = reinterpret_cast<T*>(tab + NW * 4 * K);                      // [CTA_R][s2][2]
-    __shared__ T trs[TR_HDR + 4 * (MAXM + 2)];
-    __shared__ T U[MAXM + 2];
-    __shared__ LensP L;
+    __shared__ RenderShared<T> sh;
     __shared__ double wacc[NW][NACC_FIX];
     __shared__ double wsub[NW][5];
     __shared__ __align__(8) uint64_t mbar;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (threadIdx.x == 0) load_lens(L, E.lens, E.sub_kind ? E.n_sub : 0);
-    load_transform<T>(E, trs, U);
+    render_setup<T>(E, sh);
     for (int i = threadIdx.x; i < NW * 4 * K; i += blockDim.x) tab[i] = 0.0;
     const bool staged = stage_to_smem(sgrid, E.src, (uint32_t)(n * n * sizeof(T)), &mbar, E.flags);
     const int nacc = NACC_FIX + 4 * K + 5 * (E.sub_kind ? E.n_sub : 0);
@@ -317,14 +420,16 @@ __global__ void __launch_bounds__(CTA_R) k_render_adj(const __grid_constant__ Ba
     const int pixel = tile * CTA_R + threadIdx.x;
     const bool valid = pixel < npix;
     const int s = E.s, s2 = s * s;
-    const int nsub = E.sub_kind ? E.n_sub : 0;
-    const T mux = trs[0], muy = trs[1], sg = trs[2], isg = T(1) / sg;
-    const T* Xa[2] = {trs + TR_HDR, trs + TR_HDR + K};
-    const T* Da[2] = {trs + TR_HDR + 2 * K, trs + TR_HDR + 3 * K};
+    const int nsub = sh.K.nsub;
+    const T mux = sh.trs[0], muy = sh.trs[1], sg = sh.trs[2], isg = T(1) / sg;
+    const T* Xa[2] = {sh.trs + TR_HDR, sh.trs + TR_HDR + K};
+    const T* Da[2] = {sh.trs + TR_HDR + 2 * K, sh.trs + TR_HDR + 3 * K};
     const T nm1 = T(n - 1);
     const T gpix = valid ? reinterpret_cast<const T*>(E.gimg)[pixel] / T(s2) : T(0);
     const int* off = E.ccount + nc * nc;
     R4* rec = reinterpret_cast<R4*>(E.rec);
+    const int pi = valid ? pixel % E.n_img : 0, pj = valid ? pixel / E.n_img : 0;
+    const T cx = (T)((pi - 0.5 * (E.n_img - 1)) * E.pix), cy = (T)((pj - 0.5 * (E.n_img - 1)) * E.pix);
 
     T acc[NACC_FIX];
 #pragma unroll
@@ -352,28 +457,39 @@ __global__ void __launch_bounds__(CTA_R) k_render_adj(const __grid_constant__ Ba
 
     for (int q = 0; q < s2; ++q) {
         int cell = -1;
-        double xd = 0.0, yd = 0.0;
         T gb0 = T(0), gb1 = T(0);
         int jn[2] = {cj[0], cj[1]};
         T pn[2][4];
         bool have = false;
+        const T x = cx + sh.offx[q % s], y = cy + sh.offx[q / s];
         if (valid) {
-            ray_pos(E.n_img, E.pix, s, pixel, q, xd, yd);
             cell = E.cell[(size_t)pixel * s2 + q];
             if (cell >= nc * nc) cell = -1;     // only a forward pass on this slot writes cells
         }
         if (cell >= 0) {
-            Dual<T, 6> bx, by;
-            trace_dual<T>(L, E.profile, nsub, E.sub_kind, xd, yd, bx, by);
-            const T z[2] = {(bx.v - mux) * isg, (by.v - muy) * isg};
-            T y[2], dz[2];
+            const bool near = sizeof(T) == 4 && lens_near_core(sh.K, x, y);
+            EplJ<T> J;
+            EplJ<double> Jd;
+            double xd = 0.0, yd = 0.0;
+            T bx, by;
+            if (near) {
+                ray_pos(E.n_img, E.pix, s, pixel, q, xd, yd);
+                double bxd, byd;
+                lens_beta_eval(sh.Kd, xd, yd, Jd, bxd, byd);
+                bx = (T)bxd;
+                by = (T)byd;
+            } else {
+                lens_beta_eval(sh.K, x, y, J, bx, by);
+            }
+            const T z[2] = {(bx - mux) * isg, (by - muy) * isg};
+            T yv[2], dz[2];
             for (int a = 0; a < 2; ++a) {
                 jn[a] = cdf_interval<T>(Xa[a], K, z[a]);
-                y[a] = cdf_grad<T>(Xa[a], U, Da[a], K, jn[a], z[a], dz[a], pn[a][0], pn[a][1], pn[a][2],
-                                   pn[a][3]);
+                yv[a] = cdf_grad<T>(Xa[a], sh.U, Da[a], K, jn[a], z[a], dz[a], pn[a][0], pn[a][1], pn[a][2],
+                                    pn[a][3]);
             }
             const int i0 = cell % nc, j0 = cell / nc;
-            const T fx = y[0] * nm1 - T(i0), fy = y[1] * nm1 - T(j0);
+            const T fx = yv[0] * nm1 - T(i0), fy = yv[1] * nm1 - T(j0);
             const T* r0 = sgrid + j0 * n + i0;
             const T dsdx = nm1 * ((T(1) - fy) * (r0[1] - r0[0]) + fy * (r0[n + 1] - r0[n]));
             const T dsdy = nm1 * ((T(1) - fx) * (r0[n] - r0[0]) + fx * (r0[n + 1] - r0[1]));
@@ -384,11 +500,14 @@ __global__ void __launch_bounds__(CTA_R) k_render_adj(const __grid_constant__ Ba
             acc[8] -= gb0;
             acc[9] -= gb1;
             acc[10] -= (gz0 * z[0] + gz1 * z[1]) * isg;
+            if (near) {
+                double o8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+                lens_beta_vjp(sh.Kd, Jd, xd, yd, (double)gb0, (double)gb1, o8);
 #pragma unroll
-            for (int p = 0; p < 6; ++p) acc[p] += gb0 * bx.d[p] + gb1 * by.d[p];
-            const T xf = T(xd), yf = T(yd);
-            acc[6] += -gb0 * xf + gb1 * yf;
-            acc[7] += -gb0 * yf - gb1 * xf;
+                for (int p = 0; p < 8; ++p) acc[p] += (T)o8[p];
+            } else {
+                lens_beta_vjp(sh.K, J, x, y, gb0, gb1, acc);
+            }
             for (int a = 0; a < 2; ++a)
                 for (int c = 0; c < 4; ++c) pn[a][c] *= gy[a];
             have = true;
@@ -416,8 +535,7 @@ __global__ void __launch_bounds__(CTA_R) k_render_adj(const __grid_constant__ Ba
     // fixed-order reductions: warp tree -> per-warp slots -> warps in order
 #pragma unroll
     for (int i = 0; i < NACC_FIX; ++i) {
-        double v = (double)acc[i];
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        const double v = warp_sum(acc[i]);
         if (lane == 0) wacc[wid][i] = v;
     }
     __syncthreads();
@@ -438,18 +556,12 @@ __global__ void __launch_bounds__(CTA_R) k_render_adj(const __grid_constant__ Ba
             for (int q = 0; q < s2; ++q) {
                 const T g0 = gbs[(threadIdx.x * s2 + q) * 2], g1 = gbs[(threadIdx.x * s2 + q) * 2 + 1];
                 if (g0 == T(0) && g1 == T(0)) continue;
-                double xd, yd;
-                ray_pos(E.n_img, E.pix, s, pixel, q, xd, yd);
-                Dual<T, 5> ax, ay;
-                sub_dual<T>(L, h, E.sub_kind, xd, yd, ax, ay);
-#pragma unroll
-                for (int c = 0; c < 5; ++c) a5[c] -= g0 * ax.d[c] + g1 * ay.d[c];
+                sub_vjp<T>(sh.K, h, cx + sh.offx[q % s], cy + sh.offx[q / s], g0, g1, a5);
             }
         }
 #pragma unroll
         for (int c = 0; c < 5; ++c) {
-            double v = (double)a5[c];
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            const double v = warp_sum(a5[c]);
             if (lane == 0) wsub[wid][c] = v;
         }
         __syncthreads();
@@ -477,23 +589,20 @@ __global__ void __launch_bounds__(GATHER_NT) k_cell_gather(const __grid_constant
     if (cell >= ncell) return;
     const int* off = E.ccount + ncell;
     const R4* rec = reinterpret_cast<const R4*>(E.rec);
-    double c0 = 0.0, c1 = 0.0, c2 = 0.0, c3 = 0.0;
+    // lane sums in the record type (a few records each), the warp tree in double
+    T l0 = T(0), l1 = T(0), l2 = T(0), l3 = T(0);
     const int n_rays = E.n_img * E.n_img * E.s * E.s;
     const int lo = max(0, off[cell]), hi = min(off[cell + 1], n_rays);
     for (int i = lo + lane; i < hi; i += 32) {
         const R4 r = rec[i];
-        const double fx = r.x, fy = r.y, g = r.z;
-        c0 += (1.0 - fx) * (1.0 - fy) * g;
-        c1 += fx * (1.0 - fy) * g;
-        c2 += (1.0 - fx) * fy * g;
-        c3 += fx * fy * g;
+        const T fx = r.x, fy = r.y, g = r.z;
+        const T gy0 = (T(1) - fy) * g, gy1 = fy * g;
+        l0 += (T(1) - fx) * gy0;
+        l1 += fx * gy0;
+        l2 += (T(1) - fx) * gy1;
+        l3 += fx * gy1;
     }
-    for (int o = 16; o > 0; o >>= 1) {
-        c0 += __shfl_down_sync(0xffffffffu, c0, o);
-        c1 += __shfl_down_sync(0xffffffffu, c1, o);
-        c2 += __shfl_down_sync(0xffffffffu, c2, o);
-        c3 += __shfl_down_sync(0xffffffffu, c3, o);
-    }
+    const double c0 = warp_sum(l0), c1 = warp_sum(l1), c2 = warp_sum(l2), c3 = warp_sum(l3);
     if (lane == 0) {
         double* c = E.corner + (size_t)cell * 4;
         c[0] = c0; c[1] = c1; c[2] = c2; c[3] = c3;

@@ -121,6 +121,10 @@ size_t slot_layout(const rtu_system_desc& d, char* base, EvalArgs* e) {
     p = take((size_t)z.ncell * 4 * 8);                if (e) e->corner = (double*)p;
     p = take((size_t)z.n_cta_r * z.nacc * 8);         if (e) e->apart = (double*)p;
     p = take(16);                                     if (e) e->flags = (int*)p;
+    p = take(LENSK_BYTES);                            if (e) e->lensk = p;
+    p = take(16);                                     if (e) e->ecount = (int*)p;
+    p = take(ni * 8);                                 if (e) e->pdef = (unsigned long long*)p;
+    p = take((size_t)z.n_rays * 4);                   if (e) e->rval = (float*)p;
     return o;
 }
 
@@ -160,13 +164,51 @@ size_t state_layout(const rtu_system_desc& d, char* base, ElboState* st) {
     return o;
 }
 
-size_t static_layout(const rtu_system_desc& d, char* base, int** cidx, double** tw, int** rev) {
+size_t static_layout(const rtu_system_desc& d, char* base, int** cidx, double** tw, int** rev, double** cheb) {
     size_t o = 0;
     auto take = [&](size_t bytes) { size_t at = o; o = align_up(o + bytes); return base ? base + at : nullptr; };
     char* p = take((size_t)d.n_img * d.n_img * 4); if (cidx) *cidx = (int*)p;
     p = take((size_t)2 * d.n_src * 8);             if (tw) *tw = (double*)p;
     p = take((size_t)d.n_src * 4);                 if (rev) *rev = (int*)p;
+    p = take((size_t)cheb_size(d.n_nodes, d.degree) * 8); if (cheb) *cheb = (double*)p;
     return o;
+}
+
+// Chebyshev nodes and the matrices of the interpolating fit (App. C iii-iv), by
+// the three-term recurrences in double
+std::vector<double> chebyshev_tables(int M, int D) {
+    const int K = M + 2;
+    std::vector<double> t(cheb_size(M, D), 0.0);
+    std::vector<double> u(M), tk(K);
+    for (int j = 1; j <= M; ++j) u[j - 1] = (1.0 - std::cos((2.0 * j - 1.0) * M_PI / (2.0 * M))) / 2.0;
+    for (int j = 0; j < M; ++j) t[cheb_u(M, D) + j] = u[j];
+    for (int j = 0; j < K; ++j) tk[j] = j == 0 ? -1.0 : (j == K - 1 ? 1.0 : 2.0 * u[j - 1] - 1.0);
+    for (int j = 0; j < K; ++j) {
+        double T0 = 1.0, T1 = tk[j], U0 = 1.0, U1 = 2.0 * tk[j];
+        for (int k = 0; k <= D; ++k) {
+            double Tk, dTk;
+            if (k == 0) { Tk = 1.0; dTk = 0.0; }
+            else if (k == 1) { Tk = T1; dTk = U0; }
+            else {
+                Tk = 2.0 * tk[j] * T1 - T0; dTk = k * U1;
+                T0 = T1; T1 = Tk;
+                const double U2 = 2.0 * tk[j] * U1 - U0;
+                U0 = U1; U1 = U2;
+            }
+            t[cheb_V(M, D) + j * (D + 1) + k] = Tk;
+            t[cheb_dV(M, D) + j * (D + 1) + k] = 2.0 * dTk;     // d/du = 2 d/dt
+        }
+    }
+    for (int j = 0; j < M; ++j) {
+        const double tj = 2.0 * u[j] - 1.0;
+        double T0 = 1.0, T1 = tj;
+        for (int k = 0; k <= D; ++k) {
+            double Tk = k == 0 ? 1.0 : (k == 1 ? tj : 2.0 * tj * T1 - T0);
+            if (k >= 2) { T0 = T1; T1 = Tk; }
+            t[cheb_C(M, D) + k * M + j] = (2.0 / M) * Tk * (k == 0 ? 0.5 : 1.0);
+        }
+    }
+    return t;
 }
 
 const char* check_desc(const rtu_system_desc* d) {
@@ -215,6 +257,7 @@ struct rtu_system {
     int* cidx;
     double* tw;
     int* rev;
+    double* cheb;
     std::vector<EvalArgs> slot;   // workspace pointers of each slot
     std::vector<SampleBufs> sbuf; // guide-sample buffers of each slot
     ElboState st;
@@ -233,14 +276,20 @@ __global__ void __launch_bounds__(256) k_zero(const __grid_constant__ Batch B, i
     for (int i = tile * 256 + threadIdx.x; i < tot; i += ZERO_TILES * 256) {
         if (i < nh) E.hist[i] = 0; else E.ccount[i - nh] = 0;
     }
-    if (tile == 0 && threadIdx.x == 0) *E.flags = 0;
+    if (tile == 0) {
+        if (threadIdx.x == 0) { *E.flags = 0; *E.ecount = 0; }
+        const int nsub = E.sub_kind ? E.n_sub : 0;
+        lens_setup_par(reinterpret_cast<LensK<double>*>(E.lensk),
+                       reinterpret_cast<LensK<float>*>(static_cast<char*>(E.lensk) + LENSK_D_BYTES), E.lens,
+                       E.profile, E.sub_kind, nsub);
+    }
 }
 
 extern "C" {
 
 size_t rtu_workspace_size(const rtu_system_desc* d) {
     if (check_desc(d)) return 0;
-    return static_layout(*d, nullptr, nullptr, nullptr, nullptr) +
+    return static_layout(*d, nullptr, nullptr, nullptr, nullptr, nullptr) +
            (size_t)d->n_slots * (slot_layout(*d, nullptr, nullptr) + sample_layout(*d, nullptr, nullptr)) +
            state_layout(*d, nullptr, nullptr) + 256;
 }
@@ -261,7 +310,7 @@ rtu_status rtu_system_create(const rtu_system_desc* d, void* ws, size_t ws_bytes
     s->nrad = (int)rad.size();
     for (int i = 0; i < MAX_RADIX; ++i) s->rad[i] = i < s->nrad ? rad[i] : 1;
     char* base = static_cast<char*>(ws);
-    const size_t st = static_layout(*d, base, &s->cidx, &s->tw, &s->rev);
+    const size_t st = static_layout(*d, base, &s->cidx, &s->tw, &s->rev, &s->cheb);
     // arc-mask pixel list (the CDF uses observed-pixel centres inside the mask)
     const size_t npx = (size_t)d->n_img * d->n_img;
     std::vector<uint8_t> mask(npx);
@@ -279,7 +328,9 @@ rtu_status rtu_system_create(const rtu_system_desc* d, void* ws, size_t ws_bytes
         tw[2 * m + 1] = std::sin(ang);
     }
     std::vector<int> rev = digit_reversal(d->n_src, rad);
+    std::vector<double> cheb = chebyshev_tables(d->n_nodes, d->degree);
     if ((ce = cudaMemcpy(s->cidx, idx.data(), idx.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (ce = cudaMemcpy(s->cheb, cheb.data(), cheb.size() * 8, cudaMemcpyHostToDevice)) != cudaSuccess ||
         (ce = cudaMemcpy(s->tw, tw.data(), tw.size() * 8, cudaMemcpyHostToDevice)) != cudaSuccess ||
         (ce = cudaMemcpy(s->rev, rev.data(), rev.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess) {
         delete s;
@@ -326,7 +377,7 @@ rtu_status fill_args(rtu_system* s, const rtu_eval& v, EvalArgs& e) {
     for (int i = 0; i < MAX_RADIX; ++i) e.rad[i] = s->rad[i];
     e.pix = d.pix; e.pitch = d.src_pitch; e.sigma = d.sigma;
     e.data = d.data; e.mask = d.mask; e.psf = d.psf;
-    e.centre_idx = s->cidx; e.tw = s->tw; e.digrev = s->rev;
+    e.centre_idx = s->cidx; e.tw = s->tw; e.digrev = s->rev; e.cheb = s->cheb;
     e.lens = v.lens; e.latents = v.latents; e.ps = v.ps; e.dlogL = v.dlogL;
     e.stats = v.stats; e.model_out = v.model; e.image_out = v.image; e.source_out = v.source;
     e.cdf_out = v.cdf; e.hist_out = v.ray_hist;
@@ -373,6 +424,8 @@ int t_zero(const EvalArgs&) { return ZERO_TILES; }
 int t_centre(const EvalArgs& e) { return e.n_cta_c; }
 int t_render(const EvalArgs& e) { return e.n_cta_r; }
 int t_psf(const EvalArgs& e) { return e.n_cta_p; }
+int t_edge(const EvalArgs&) { return EDGE_CTAS; }
+int t_fix(const EvalArgs& e) { return (e.n_img * e.n_img + 255) / 256; }
 int t_cells(const EvalArgs& e) {
     const int nc = (e.n_src - 1) * (e.n_src - 1);
     return (nc + GATHER_NT / 32 - 1) / (GATHER_NT / 32);
@@ -401,6 +454,10 @@ rtu_status run_chunk(Batch& B, int phase, cudaStream_t st) {
         if ((r = launch("k_gp_source", k_gp_source<T>, B, t_one, GP_NT, GP_SMEM, st))) return r;
         if (grid_bytes > MAX_DYN) return fail(RTU_E_ARG, "source grid too large for shared memory");
         if ((r = launch("k_render", k_render<T>, B, t_render, CTA_R, grid_bytes, st))) return r;
+        if (sizeof(T) == 4) {
+            if ((r = launch("k_render_edge", k_render_edge, B, t_edge, EDGE_NT, 0, st))) return r;
+            if ((r = launch("k_render_fix", k_render_fix, B, t_fix, 256, 0, st))) return r;
+        }
         if ((r = launch("k_psf_like", k_psf_like<T>, B, t_psf, PSF_NT, 0, st))) return r;
         if ((r = launch("k_like_final", k_like_final, B, t_one, 256, 0, st))) return r;
     }
@@ -412,7 +469,7 @@ rtu_status run_chunk(Batch& B, int phase, cudaStream_t st) {
         if (adj > MAX_DYN) return fail(RTU_E_ARG, "adjoint shared memory exceeds the limit");
         if ((r = launch("k_render_adj", k_render_adj<T>, B, t_render, CTA_R, adj, st))) return r;
         if ((r = launch("k_cell_gather", k_cell_gather<T>, B, t_cells, GATHER_NT, 0, st))) return r;
-        if ((r = launch("k_cdf_adj", k_cdf_adj, B, t_one, 256, 0, st))) return r;
+        if ((r = launch("k_cdf_adj", k_cdf_adj, B, t_one, CDF_NT, 0, st))) return r;
         if ((r = launch("k_centre_adj", k_centre_adj<T>, B, t_centre, CTA_C, 0, st))) return r;
         if ((r = launch("k_gp_adjoint", k_gp_adjoint<T>, B, t_one, GP_NT, GP_SMEM, st))) return r;
         if ((r = launch("k_grad_final", k_grad_final, B, t_one, 64, 0, st))) return r;

@@ -19,7 +19,7 @@ constexpr int MAXM = 64;          // max Chebyshev nodes
 constexpr int MAX_RADIX = 12;     // max FFT stages
 constexpr int CTA_C = 256;        // centre-ray kernels: rays per CTA
 constexpr int CTA_R = 128;        // render kernels: pixels per CTA (one thread each)
-constexpr int PSF_T = 16;         // PSF kernels: 16 x 16 output tile per CTA
+constexpr int PSF_T = 32;         // PSF kernels: 32 x 32 output tile per CTA (4 outputs per thread)
 constexpr int NACC_FIX = 11;      // render-adjoint partials: 8 lens + mu_x, mu_y, sigma
 
 // flag bits (mirror rtu.h)
@@ -39,6 +39,7 @@ struct EvalArgs {
     const int* centre_idx;      // [n_mask] pixel index of each arc-mask pixel
     const double* tw;           // [2 n_src] exp(-2 pi i m / n_src)
     const int* digrev;          // [n_src] mixed-radix digit reversal
+    const double* cheb;         // Chebyshev tables (layout: cheb_* helpers)
     // dynamic, from the rtu_eval binding
     const double* lens;
     const void* latents;
@@ -79,6 +80,10 @@ struct EvalArgs {
     double* corner;    // [n_cells][4] per-cell bilinear corner sums
     double* apart;     // [n_cta_r][nacc] render-adjoint partials
     int* flags;        // device flag word
+    void* lensk;       // LensK<T> then LensK<double> of the evaluation
+    int* ecount;       // number of deferred near-edge rays (float mode)
+    unsigned long long* pdef;  // [n_img^2] bit q: sub-ray q deferred to the double pass (float mode)
+    float* rval;       // [n_rays] values of deferred rays (float mode)
 };
 
 struct Batch {
@@ -99,6 +104,18 @@ struct Batch {
 //   [8+8K+2MAXM ..)   Q at nodes x, y (M each, MAXM stride)
 constexpr int TR_HDR = 8;
 __host__ __device__ constexpr int tr_size(int K) { return TR_HDR + 8 * K + 4 * MAXM; }
+
+// Chebyshev tables of a system (M nodes, degree D, K = M + 2 knot points
+// t = -1, t_1..t_M, +1), computed on the host at creation:
+//   u[M]             the nodes u_j = (1 - cos((2j-1) pi / (2M))) / 2
+//   V[K][D+1]        T_k(t) at the knot points
+//   dV[K][D+1]       dp/du per coefficient: 2 T_k'(t)
+//   C[D+1][M]        interpolating coefficients c = C Q  (2/M T_k(t_j), halved for k = 0)
+__host__ __device__ constexpr int cheb_u(int, int) { return 0; }
+__host__ __device__ constexpr int cheb_V(int M, int) { return M; }
+__host__ __device__ constexpr int cheb_dV(int M, int D) { return M + (M + 2) * (D + 1); }
+__host__ __device__ constexpr int cheb_C(int M, int D) { return M + 2 * (M + 2) * (D + 1); }
+__host__ __device__ constexpr int cheb_size(int M, int D) { return M + 2 * (M + 2) * (D + 1) + (D + 1) * M; }
 
 template <typename BatchT>
 __device__ __forceinline__ int find_eval(const BatchT& B, int bid) {
@@ -129,6 +146,32 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
     return r;
 }
 
+// Warp sum of one value per lane with a fixed shuffle tree, returned in lane 0
+// as double.  Float lanes use compensated summation (TwoSum at each level,
+// Knuth 1969), so the result carries about twice the float precision without
+// FP64 arithmetic in the tree; double lanes add in double.
+__device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ double warp_sum(float v) {
+    float hi = v, lo = 0.0f;
+    for (int o = 16; o > 0; o >>= 1) {
+        const float h2 = __shfl_down_sync(0xffffffffu, hi, o);
+        const float l2 = __shfl_down_sync(0xffffffffu, lo, o);
+        float sum, err;
+        two_sum_f(hi, h2, sum, err);
+        hi = sum;
+        lo = lo + l2 + err;
+    }
+    return (double)hi + (double)lo;
+}
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
 template <typename T> struct real2_of;
 template <> struct real2_of<float> { typedef float2 type; };
 template <> struct real2_of<double> { typedef double2 type; };
@@ -137,45 +180,105 @@ template <> struct real4_of<float> { typedef float4 type; };
 template <> struct real4_of<double> { typedef double4_32a type; };
 
 // ------------------------------------------------------------- lens trace
-// Lens parameters as seen by a kernel: main lens and shear, then subhaloes.
-struct LensP {
-    double p[8];
-    double sub[16][5];
+// Lens parameters as a kernel sees them: the EPL's per-system constants, the
+// shear, the subhaloes, in the kernel's real type.  Built once per evaluation
+// (k_zero) into the workspace and copied to shared memory by every CTA.
+constexpr int MAX_SUB = 16;
+
+template <typename T>
+struct LensK {
+    EplC<T> C;
+    T g1, g2, rc2;           // shear; squared radius of the near-core FP64 island
+    T sub[MAX_SUB][5];       // kappa_s, r_s, tau, x_s, y_s
+    int nsub, kind, epl, pad_;
 };
 
 template <typename T>
 __device__ __forceinline__ T epl_tol() { return sizeof(T) == 4 ? T(1e-9) : T(1e-17); }
 
-// Plain-value lens equation beta = theta - alpha(theta) (App. A).  In float
-// mode, rays close to the EPL centre or to a subhalo's centre / scale radius
-// are traced in double (the near-core FP64 island).
 template <typename T>
-__device__ __forceinline__ bool near_core(const LensP& L, int n_sub, int sub_kind, double x, double y) {
-    double dx = x - L.p[4], dy = y - L.p[5];
-    if (dx * dx + dy * dy < 0.0025 * L.p[0] * L.p[0] * 4.0) return true;  // |theta - c| < 0.1 theta_E
-    if (sub_kind != 0) {
-        for (int h = 0; h < n_sub; ++h) {
-            double sx = x - L.sub[h][3], sy = y - L.sub[h][4];
-            double r = sqrt(sx * sx + sy * sy) / L.sub[h][1];
-            if (r < 1e-2 || fabs(r - 1.0) < 1e-2) return true;
+__device__ void lens_rest(LensK<T>& K, const double* lens, int profile, int sub_kind, int n_sub) {
+    K.g1 = (T)lens[6];
+    K.g2 = (T)lens[7];
+    K.rc2 = (T)(1e-4 * lens[0] * lens[0]);          // |theta - centre| < 0.01 theta_E
+    K.nsub = sub_kind ? n_sub : 0;
+    K.kind = sub_kind;
+    K.epl = profile == 1;
+    for (int h = 0; h < K.nsub; ++h)
+        for (int k = 0; k < 5; ++k) K.sub[h][k] = (T)lens[8 + 5 * h + k];
+}
+
+// Both lens blocks of an evaluation, built by one CTA: the series coefficients
+// c_n, c_n/f and the per-term t-derivative of log|c_n| in parallel (one thread
+// per term), the running products and sums, and the stopping index of each
+// precision (1e-17 for double, 1e-9 for float), by one thread.
+__device__ void lens_setup_par(LensK<double>* Kd, LensK<float>* Kf, const double* lens, int profile, int sub_kind,
+                               int n_sub) {
+    __shared__ double sc[EPL_MAXT], sg[EPL_MAXT], sdl[EPL_MAXT], sconst[4];
+    if (threadIdx.x == 0) {
+        const double cc = sqrt(fmax(lens[2] * lens[2] + lens[3] * lens[3], 1e-30));
+        const double q = (1.0 - cc) / (1.0 + cc);
+        sconst[0] = (1.0 - q) / (1.0 + q);
+        sconst[1] = (profile == 1 ? lens[1] : 2.0) - 1.0;
+    }
+    __syncthreads();
+    const double f = sconst[0], t = sconst[1];
+    for (int n = threadIdx.x + 1; n <= EPL_MAXT; n += blockDim.x) {
+        const double g = -(2.0 * n - 2.0 + t) / (2.0 * n + 2.0 - t);
+        sg[n - 1] = g;
+        sc[n - 1] = f * g;
+        sdl[n - 1] = 1.0 / (2.0 * n - 2.0 + t) + 1.0 / (2.0 * n + 2.0 - t);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 || threadIdx.x == 32) {
+        const bool dbl = threadIdx.x == 0;
+        const double p[6] = {lens[0], lens[1], lens[2], lens[3], lens[4], lens[5]};
+        const double tol = dbl ? 1e-17 : 1e-9;
+        // scalars through the shared definition, then the coefficient tables
+        double a = 1.0, D = 0.0;
+        int nt = EPL_MAXT;
+        for (int n = 1; n <= EPL_MAXT; ++n) {
+            a *= sc[n - 1];
+            D += sdl[n - 1];
+            if (dbl) { Kd->C.cn[n - 1] = sc[n - 1]; Kd->C.gn[n - 1] = sg[n - 1]; Kd->C.Dn[n - 1] = D; }
+            else { Kf->C.cn[n - 1] = (float)sc[n - 1]; Kf->C.gn[n - 1] = (float)sg[n - 1]; Kf->C.Dn[n - 1] = (float)D; }
+            if (fabs(a) <= tol) { nt = n; break; }
         }
+        if (dbl) {
+            epl_scalars(Kd->C, p, profile == 1);
+            Kd->C.nterm = nt;
+            lens_rest(*Kd, lens, profile, sub_kind, n_sub);
+        } else {
+            epl_scalars(Kf->C, p, profile == 1);
+            Kf->C.nterm = nt;
+            lens_rest(*Kf, lens, profile, sub_kind, n_sub);
+        }
+    }
+}
+
+// rays near the EPL centre or a subhalo's centre / scale radius take the FP64 island
+template <typename T>
+__device__ __forceinline__ bool lens_near_core(const LensK<T>& K, T x, T y) {
+    const T dx = x - K.C.x0, dy = y - K.C.y0;
+    if (dx * dx + dy * dy < K.rc2) return true;
+    for (int h = 0; h < K.nsub; ++h) {
+        const T sx = x - K.sub[h][3], sy = y - K.sub[h][4];
+        const T r = r_sqrt(sx * sx + sy * sy) / K.sub[h][1];
+        if (r < T(1e-2) || r_abs(r - T(1)) < T(1e-2)) return true;
     }
     return false;
 }
 
+// lens equation beta = theta - alpha(theta) (App. A): EPL + shear + subhaloes
 template <typename T>
-__device__ __forceinline__ void trace_value_T(const LensP& L, int profile, int n_sub, int sub_kind,
-                                              T x, T y, T& bx, T& by) {
-    T gam = profile == 1 ? T(L.p[1]) : T(2);
+__device__ __forceinline__ void lens_beta(const LensK<T>& K, T x, T y, T& bx, T& by) {
     T ax, ay;
-    epl_deflect<T>(x, y, T(L.p[0]), gam, T(L.p[2]), T(L.p[3]), T(L.p[4]), T(L.p[5]), ax, ay,
-                   epl_tol<T>(), 200);
-    ax += T(L.p[6]) * x + T(L.p[7]) * y;
-    ay += T(L.p[7]) * x - T(L.p[6]) * y;
-    for (int h = 0; h < n_sub; ++h) {
+    epl_alpha(K.C, x, y, ax, ay);
+    ax += K.g1 * x + K.g2 * y;
+    ay += K.g2 * x - K.g1 * y;
+    for (int h = 0; h < K.nsub; ++h) {
         T nx, ny;
-        nfw_deflect<T>(x, y, T(L.sub[h][0]), T(L.sub[h][1]), T(L.sub[h][2]), T(L.sub[h][3]),
-                       T(L.sub[h][4]), sub_kind, nx, ny);
+        nfw_deflect<T>(x, y, K.sub[h][0], K.sub[h][1], K.sub[h][2], K.sub[h][3], K.sub[h][4], K.kind, nx, ny);
         ax += nx;
         ay += ny;
     }
@@ -183,76 +286,63 @@ __device__ __forceinline__ void trace_value_T(const LensP& L, int profile, int n
     by = y - ay;
 }
 
+// the same, keeping the EPL intermediates for a later vector-Jacobian product
 template <typename T>
-__device__ __forceinline__ void trace_value(const LensP& L, int profile, int n_sub, int sub_kind,
-                                            double xd, double yd, T& bx, T& by) {
-    if (sizeof(T) == 4 && near_core<T>(L, n_sub, sub_kind, xd, yd)) {
-        double dbx, dby;
-        trace_value_T<double>(L, profile, n_sub, sub_kind, xd, yd, dbx, dby);
-        bx = T(dbx);
-        by = T(dby);
-    } else {
-        trace_value_T<T>(L, profile, n_sub, sub_kind, T(xd), T(yd), bx, by);
-    }
-}
-
-// Main lens with derivatives: returns beta and d beta / d(theta_E, gamma, e1, e2, x0, y0)
-// (shear derivatives are analytic: d beta_x/d G1 = -x, d beta_x/d G2 = -y,
-//  d beta_y/d G1 = +y, d beta_y/d G2 = -x).  Subhaloes contribute values only.
-template <typename T>
-__device__ __forceinline__ void trace_dual_T(const LensP& L, int profile, int n_sub, int sub_kind,
-                                             T x, T y, Dual<T, 6>& bx, Dual<T, 6>& by) {
-    typedef Dual<T, 6> D;
-    D thE = D::seed(T(L.p[0]), 0);
-    D gam = profile == 1 ? D::seed(T(L.p[1]), 1) : D(T(2));
-    D e1 = D::seed(T(L.p[2]), 2), e2 = D::seed(T(L.p[3]), 3);
-    D x0 = D::seed(T(L.p[4]), 4), y0 = D::seed(T(L.p[5]), 5);
-    D ax, ay;
-    epl_deflect<D>(D(x), D(y), thE, gam, e1, e2, x0, y0, ax, ay, epl_tol<T>(), 200);
-    T sx = T(L.p[6]) * x + T(L.p[7]) * y;
-    T sy = T(L.p[7]) * x - T(L.p[6]) * y;
-    for (int h = 0; h < n_sub; ++h) {
+__device__ __forceinline__ void lens_beta_eval(const LensK<T>& K, T x, T y, EplJ<T>& J, T& bx, T& by) {
+    epl_eval(K.C, K.epl != 0, x, y, J);
+    T ax = J.ax + K.g1 * x + K.g2 * y;
+    T ay = J.ay + K.g2 * x - K.g1 * y;
+    for (int h = 0; h < K.nsub; ++h) {
         T nx, ny;
-        nfw_deflect<T>(x, y, T(L.sub[h][0]), T(L.sub[h][1]), T(L.sub[h][2]), T(L.sub[h][3]),
-                       T(L.sub[h][4]), sub_kind, nx, ny);
-        sx += nx;
-        sy += ny;
+        nfw_deflect<T>(x, y, K.sub[h][0], K.sub[h][1], K.sub[h][2], K.sub[h][3], K.sub[h][4], K.kind, nx, ny);
+        ax += nx;
+        ay += ny;
     }
-    bx = T(0) - (ax + sx) + x;
-    by = T(0) - (ay + sy) + y;
+    bx = x - ax;
+    by = y - ay;
 }
 
+// out[0..7] += dL/d(theta_E, gamma, e1, e2, x0, y0, Gamma1, Gamma2) given dL/dbeta = (gbx, gby)
 template <typename T>
-__device__ __forceinline__ void trace_dual(const LensP& L, int profile, int n_sub, int sub_kind,
-                                           double xd, double yd, Dual<T, 6>& bx, Dual<T, 6>& by) {
-    if (sizeof(T) == 4 && near_core<T>(L, n_sub, sub_kind, xd, yd)) {
-        Dual<double, 6> dbx, dby;
-        trace_dual_T<double>(L, profile, n_sub, sub_kind, xd, yd, dbx, dby);
-        bx = cast<Dual<T, 6>>(dbx);
-        by = cast<Dual<T, 6>>(dby);
-    } else {
-        trace_dual_T<T>(L, profile, n_sub, sub_kind, T(xd), T(yd), bx, by);
-    }
+__device__ __forceinline__ void lens_beta_vjp(const LensK<T>& K, const EplJ<T>& J, T x, T y, T gbx, T gby,
+                                              T* out) {
+    epl_vjp(K.C, J, K.epl != 0, -gbx, -gby, out);
+    out[6] += -gbx * x + gby * y;      // d beta / d Gamma1 = (-x, +y)
+    out[7] += -gbx * y - gby * x;      // d beta / d Gamma2 = (-y, -x)
 }
 
-// Subhalo h with derivatives w.r.t. (kappa_s, r_s, tau, x_s, y_s): d alpha.
+// subhalo h: out[0..4] += dL/d(kappa_s, r_s, tau, x_s, y_s) given dL/dbeta (forward-mode duals)
 template <typename T>
-__device__ __forceinline__ void sub_dual(const LensP& L, int h, int sub_kind, double xd, double yd,
-                                         Dual<T, 5>& ax, Dual<T, 5>& ay) {
+__device__ __forceinline__ void sub_vjp(const LensK<T>& K, int h, T x, T y, T gbx, T gby, T* out) {
     typedef Dual<T, 5> D;
-    D ks = D::seed(T(L.sub[h][0]), 0), rs = D::seed(T(L.sub[h][1]), 1);
-    D tau = sub_kind == 2 ? D::seed(T(L.sub[h][2]), 2) : D(T(L.sub[h][2]));
-    D xs = D::seed(T(L.sub[h][3]), 3), ys = D::seed(T(L.sub[h][4]), 4);
-    nfw_deflect<D>(D(T(xd)), D(T(yd)), ks, rs, tau, xs, ys, sub_kind, ax, ay);
+    D ks = D::seed(K.sub[h][0], 0), rs = D::seed(K.sub[h][1], 1);
+    D tau = K.kind == 2 ? D::seed(K.sub[h][2], 2) : D(K.sub[h][2]);
+    D xs = D::seed(K.sub[h][3], 3), ys = D::seed(K.sub[h][4], 4);
+    D ax, ay;
+    nfw_deflect<D>(D(x), D(y), ks, rs, tau, xs, ys, K.kind, ax, ay);
+#pragma unroll
+    for (int c = 0; c < 5; ++c) out[c] -= gbx * ax.d[c] + gby * ay.d[c];
 }
 
-__device__ __forceinline__ void load_lens(LensP& L, const double* lens, int n_sub) {
-    for (int i = 0; i < 8; ++i) L.p[i] = lens[i];
-    for (int h = 0; h < n_sub; ++h)
-        for (int k = 0; k < 5; ++k) L.sub[h][k] = lens[8 + 5 * h + k];
+// the evaluation's lens blocks: LensK<double> first, then LensK<float>
+constexpr size_t LENSK_D_BYTES = (sizeof(LensK<double>) + 255) / 256 * 256;
+constexpr size_t LENSK_BYTES = LENSK_D_BYTES + (sizeof(LensK<float>) + 255) / 256 * 256;
+
+// copy a lens block from global memory into shared memory (all threads)
+template <typename T>
+__device__ __forceinline__ void load_lensk(LensK<T>& dst, const void* src) {
+    const int n = (int)(sizeof(LensK<T>) / 4);
+    const int* s = reinterpret_cast<const int*>(src);
+    int* d = reinterpret_cast<int*>(&dst);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) d[i] = s[i];
 }
 
-// pixel centre and sub-ray positions (Sec. 2.3)
+template <typename T>
+__device__ __forceinline__ const void* lensk_src(const void* base) {
+    return sizeof(T) == 8 ? base : static_cast<const char*>(base) + LENSK_D_BYTES;
+}
+
+// pixel centre and sub-ray positions (Sec. 2.3) in double
 __device__ __forceinline__ void ray_pos(int n_img, double pix, int s, int pixel, int sub,
                                         double& x, double& y) {
     int i = pixel % n_img, j = pixel / n_img;

@@ -6,29 +6,33 @@
 #include <math.h>
 #include <stdint.h>
 
+#ifndef RTU_HD
+#define RTU_HD __host__ __device__ __forceinline__
+#endif
+
 namespace rtu {
 
 // ---------------------------------------------------------------- scalars
-__device__ __forceinline__ float  r_sqrt(float x)  { return sqrtf(x); }
-__device__ __forceinline__ double r_sqrt(double x) { return sqrt(x); }
-__device__ __forceinline__ float  r_exp(float x)   { return expf(x); }
-__device__ __forceinline__ double r_exp(double x)  { return exp(x); }
-__device__ __forceinline__ float  r_log(float x)   { return logf(x); }
-__device__ __forceinline__ double r_log(double x)  { return log(x); }
-__device__ __forceinline__ float  r_log1p(float x) { return log1pf(x); }
-__device__ __forceinline__ double r_log1p(double x){ return log1p(x); }
-__device__ __forceinline__ float  r_cos(float x)   { return cosf(x); }
-__device__ __forceinline__ double r_cos(double x)  { return cos(x); }
-__device__ __forceinline__ float  r_sin(float x)   { return sinf(x); }
-__device__ __forceinline__ double r_sin(double x)  { return sin(x); }
-__device__ __forceinline__ float  r_atan2(float y, float x)   { return atan2f(y, x); }
-__device__ __forceinline__ double r_atan2(double y, double x) { return atan2(y, x); }
-__device__ __forceinline__ float  r_atan(float x)  { return atanf(x); }
-__device__ __forceinline__ double r_atan(double x) { return atan(x); }
-__device__ __forceinline__ float  r_atanh(float x) { return atanhf(x); }
-__device__ __forceinline__ double r_atanh(double x){ return atanh(x); }
-__device__ __forceinline__ float  r_abs(float x)   { return fabsf(x); }
-__device__ __forceinline__ double r_abs(double x)  { return fabs(x); }
+RTU_HD float  r_sqrt(float x)  { return sqrtf(x); }
+RTU_HD double r_sqrt(double x) { return sqrt(x); }
+RTU_HD float  r_exp(float x)   { return expf(x); }
+RTU_HD double r_exp(double x)  { return exp(x); }
+RTU_HD float  r_log(float x)   { return logf(x); }
+RTU_HD double r_log(double x)  { return log(x); }
+RTU_HD float  r_log1p(float x) { return log1pf(x); }
+RTU_HD double r_log1p(double x){ return log1p(x); }
+RTU_HD float  r_cos(float x)   { return cosf(x); }
+RTU_HD double r_cos(double x)  { return cos(x); }
+RTU_HD float  r_sin(float x)   { return sinf(x); }
+RTU_HD double r_sin(double x)  { return sin(x); }
+RTU_HD float  r_atan2(float y, float x)   { return atan2f(y, x); }
+RTU_HD double r_atan2(double y, double x) { return atan2(y, x); }
+RTU_HD float  r_atan(float x)  { return atanf(x); }
+RTU_HD double r_atan(double x) { return atan(x); }
+RTU_HD float  r_atanh(float x) { return atanhf(x); }
+RTU_HD double r_atanh(double x){ return atanh(x); }
+RTU_HD float  r_abs(float x)   { return fabsf(x); }
+RTU_HD double r_abs(double x)  { return fabs(x); }
 
 // ------------------------------------------------------------ dual numbers
 // v + sum_i d[i] eps_i, eps_i eps_j = 0: forward-mode derivatives w.r.t. N seeds.
@@ -36,12 +40,12 @@ template <typename T, int N>
 struct Dual {
     T v;
     T d[N];
-    __device__ __forceinline__ Dual() {}
-    __device__ __forceinline__ Dual(T x) : v(x) {
+    RTU_HD Dual() {}
+    RTU_HD Dual(T x) : v(x) {
 #pragma unroll
         for (int i = 0; i < N; ++i) d[i] = T(0);
     }
-    __device__ __forceinline__ static Dual seed(T x, int k) {
+    RTU_HD static Dual seed(T x, int k) {
         Dual r(x);
         r.d[k] = T(1);
         return r;
@@ -51,83 +55,83 @@ struct Dual {
 template <typename T> struct base_of { typedef T type; };
 template <typename T, int N> struct base_of<Dual<T, N>> { typedef T type; };
 
-template <typename T> __device__ __forceinline__ T val(T x) { return x; }
-template <typename T, int N> __device__ __forceinline__ T val(const Dual<T, N>& x) { return x.v; }
+template <typename T> RTU_HD T val(T x) { return x; }
+template <typename T, int N> RTU_HD T val(const Dual<T, N>& x) { return x.v; }
 
 #define RTU_DUAL_LOOP _Pragma("unroll") for (int i = 0; i < N; ++i)
 
 template <typename T, int N>
-__device__ __forceinline__ Dual<T, N> operator+(const Dual<T, N>& a, const Dual<T, N>& b) {
+RTU_HD Dual<T, N> operator+(const Dual<T, N>& a, const Dual<T, N>& b) {
     Dual<T, N> r; r.v = a.v + b.v; RTU_DUAL_LOOP r.d[i] = a.d[i] + b.d[i]; return r;
 }
 template <typename T, int N>
-__device__ __forceinline__ Dual<T, N> operator-(const Dual<T, N>& a, const Dual<T, N>& b) {
+RTU_HD Dual<T, N> operator-(const Dual<T, N>& a, const Dual<T, N>& b) {
     Dual<T, N> r; r.v = a.v - b.v; RTU_DUAL_LOOP r.d[i] = a.d[i] - b.d[i]; return r;
 }
 template <typename T, int N>
-__device__ __forceinline__ Dual<T, N> operator-(const Dual<T, N>& a) {
+RTU_HD Dual<T, N> operator-(const Dual<T, N>& a) {
     Dual<T, N> r; r.v = -a.v; RTU_DUAL_LOOP r.d[i] = -a.d[i]; return r;
 }
 template <typename T, int N>
-__device__ __forceinline__ Dual<T, N> operator*(const Dual<T, N>& a, const Dual<T, N>& b) {
+RTU_HD Dual<T, N> operator*(const Dual<T, N>& a, const Dual<T, N>& b) {
     Dual<T, N> r; r.v = a.v * b.v; RTU_DUAL_LOOP r.d[i] = a.v * b.d[i] + a.d[i] * b.v; return r;
 }
 template <typename T, int N>
-__device__ __forceinline__ Dual<T, N> operator/(const Dual<T, N>& a, const Dual<T, N>& b) {
+RTU_HD Dual<T, N> operator/(const Dual<T, N>& a, const Dual<T, N>& b) {
     Dual<T, N> r; r.v = a.v / b.v; T ib = T(1) / b.v;
     RTU_DUAL_LOOP r.d[i] = (a.d[i] - r.v * b.d[i]) * ib; return r;
 }
 // mixed with the base scalar
 template <typename T, int N>
-__device__ __forceinline__ Dual<T, N> operator+(const Dual<T, N>& a, T b) { Dual<T, N> r = a; r.v += b; return r; }
+RTU_HD Dual<T, N> operator+(const Dual<T, N>& a, T b) { Dual<T, N> r = a; r.v += b; return r; }
 template <typename T, int N>
-__device__ __forceinline__ Dual<T, N> operator+(T b, const Dual<T, N>& a) { Dual<T, N> r = a; r.v += b; return r; }
+RTU_HD Dual<T, N> operator+(T b, const Dual<T, N>& a) { Dual<T, N> r = a; r.v += b; return r; }
 template <typename T, int N>
-__device__ __forceinline__ Dual<T, N> operator-(const Dual<T, N>& a, T b) { Dual<T, N> r = a; r.v -= b; return r; }
+RTU_HD Dual<T, N> operator-(const Dual<T, N>& a, T b) { Dual<T, N> r = a; r.v -= b; return r; }
 template <typename T, int N>
-__device__ __forceinline__ Dual<T, N> operator-(T b, const Dual<T, N>& a) {
+RTU_HD Dual<T, N> operator-(T b, const Dual<T, N>& a) {
     Dual<T, N> r; r.v = b - a.v; RTU_DUAL_LOOP r.d[i] = -a.d[i]; return r;
 }
 template <typename T, int N>
-__device__ __forceinline__ Dual<T, N> operator*(const Dual<T, N>& a, T b) {
+RTU_HD Dual<T, N> operator*(const Dual<T, N>& a, T b) {
     Dual<T, N> r; r.v = a.v * b; RTU_DUAL_LOOP r.d[i] = a.d[i] * b; return r;
 }
 template <typename T, int N>
-__device__ __forceinline__ Dual<T, N> operator*(T b, const Dual<T, N>& a) { return a * b; }
+RTU_HD Dual<T, N> operator*(T b, const Dual<T, N>& a) { return a * b; }
 template <typename T, int N>
-__device__ __forceinline__ Dual<T, N> operator/(const Dual<T, N>& a, T b) { return a * (T(1) / b); }
+RTU_HD Dual<T, N> operator/(const Dual<T, N>& a, T b) { return a * (T(1) / b); }
 template <typename T, int N>
-__device__ __forceinline__ Dual<T, N> operator/(T a, const Dual<T, N>& b) {
+RTU_HD Dual<T, N> operator/(T a, const Dual<T, N>& b) {
     Dual<T, N> r; r.v = a / b.v; T s = -r.v / b.v; RTU_DUAL_LOOP r.d[i] = s * b.d[i]; return r;
 }
 
 template <typename T, int N>
-__device__ __forceinline__ Dual<T, N> chain(const Dual<T, N>& a, T fv, T dfdv) {
+RTU_HD Dual<T, N> chain(const Dual<T, N>& a, T fv, T dfdv) {
     Dual<T, N> r; r.v = fv; RTU_DUAL_LOOP r.d[i] = dfdv * a.d[i]; return r;
 }
-template <typename T, int N> __device__ __forceinline__ Dual<T, N> r_sqrt(const Dual<T, N>& a) {
+template <typename T, int N> RTU_HD Dual<T, N> r_sqrt(const Dual<T, N>& a) {
     T s = r_sqrt(a.v); return chain(a, s, T(0.5) / s);
 }
-template <typename T, int N> __device__ __forceinline__ Dual<T, N> r_exp(const Dual<T, N>& a) {
+template <typename T, int N> RTU_HD Dual<T, N> r_exp(const Dual<T, N>& a) {
     T e = r_exp(a.v); return chain(a, e, e);
 }
-template <typename T, int N> __device__ __forceinline__ Dual<T, N> r_log(const Dual<T, N>& a) {
+template <typename T, int N> RTU_HD Dual<T, N> r_log(const Dual<T, N>& a) {
     return chain(a, r_log(a.v), T(1) / a.v);
 }
-template <typename T, int N> __device__ __forceinline__ Dual<T, N> r_cos(const Dual<T, N>& a) {
+template <typename T, int N> RTU_HD Dual<T, N> r_cos(const Dual<T, N>& a) {
     return chain(a, r_cos(a.v), -r_sin(a.v));
 }
-template <typename T, int N> __device__ __forceinline__ Dual<T, N> r_sin(const Dual<T, N>& a) {
+template <typename T, int N> RTU_HD Dual<T, N> r_sin(const Dual<T, N>& a) {
     return chain(a, r_sin(a.v), r_cos(a.v));
 }
-template <typename T, int N> __device__ __forceinline__ Dual<T, N> r_atan(const Dual<T, N>& a) {
+template <typename T, int N> RTU_HD Dual<T, N> r_atan(const Dual<T, N>& a) {
     return chain(a, r_atan(a.v), T(1) / (T(1) + a.v * a.v));
 }
-template <typename T, int N> __device__ __forceinline__ Dual<T, N> r_atanh(const Dual<T, N>& a) {
+template <typename T, int N> RTU_HD Dual<T, N> r_atanh(const Dual<T, N>& a) {
     return chain(a, r_atanh(a.v), T(1) / (T(1) - a.v * a.v));
 }
 template <typename T, int N>
-__device__ __forceinline__ Dual<T, N> r_atan2(const Dual<T, N>& y, const Dual<T, N>& x) {
+RTU_HD Dual<T, N> r_atan2(const Dual<T, N>& y, const Dual<T, N>& x) {
     Dual<T, N> r; r.v = r_atan2(y.v, x.v);
     T den = x.v * x.v + y.v * y.v;
     T ax = (den > T(0)) ? x.v / den : T(0), ay = (den > T(0)) ? y.v / den : T(0);
@@ -135,24 +139,24 @@ __device__ __forceinline__ Dual<T, N> r_atan2(const Dual<T, N>& y, const Dual<T,
     return r;
 }
 template <typename T, int N>
-__device__ __forceinline__ Dual<T, N> r_max(const Dual<T, N>& a, T lo) {
+RTU_HD Dual<T, N> r_max(const Dual<T, N>& a, T lo) {
     return a.v >= lo ? a : Dual<T, N>(lo);
 }
-template <typename T> __device__ __forceinline__ T r_max(T a, T lo) { return a >= lo ? a : lo; }
+template <typename T> RTU_HD T r_max(T a, T lo) { return a >= lo ? a : lo; }
 
 // cast between base types (value and derivatives)
 template <typename To, typename From> struct caster {
-    __device__ __forceinline__ static To go(const From& x) { return To(x); }
+    RTU_HD static To go(const From& x) { return To(x); }
 };
 template <typename To, typename From, int N> struct caster<Dual<To, N>, Dual<From, N>> {
-    __device__ __forceinline__ static Dual<To, N> go(const Dual<From, N>& x) {
+    RTU_HD static Dual<To, N> go(const Dual<From, N>& x) {
         Dual<To, N> r; r.v = To(x.v);
 #pragma unroll
         for (int i = 0; i < N; ++i) r.d[i] = To(x.d[i]);
         return r;
     }
 };
-template <typename To, typename From> __device__ __forceinline__ To cast(const From& x) {
+template <typename To, typename From> RTU_HD To cast(const From& x) {
     return caster<To, From>::go(x);
 }
 
@@ -165,7 +169,7 @@ template <typename To, typename From> __device__ __forceinline__ To cast(const F
 // stopping index is uniform across a warp.  `tol` is the absolute term size at
 // which the sum stops.
 template <typename S>
-__device__ __forceinline__ void epl_deflect(const S& x, const S& y, const S& thE, const S& gam,
+RTU_HD void epl_deflect(const S& x, const S& y, const S& thE, const S& gam,
                                             const S& e1, const S& e2, const S& x0, const S& y0,
                                             S& ax, S& ay,
                                             typename base_of<S>::type tol, int max_terms) {
@@ -207,7 +211,7 @@ __device__ __forceinline__ void epl_deflect(const S& x, const S& y, const S& thE
 
 // F(x) of Eq. A3 with the series sum_k w^k/(2k+1), w = 1 - x^2, near x = 1.
 template <typename S>
-__device__ __forceinline__ S nfw_F(const S& x) {
+RTU_HD S nfw_F(const S& x) {
     typedef typename base_of<S>::type T;
     S w = T(1) - x * x;
     T wv = val(w);
@@ -233,7 +237,7 @@ __device__ __forceinline__ S nfw_F(const S& x) {
 // NFW: g = ln(x/2) + F(x).  Truncated NFW (Baltz, Marshall & Oguri 2009, density
 // times tau^2/(tau^2 + x^2)).
 template <typename S>
-__device__ __forceinline__ S nfw_g(const S& x, const S& tau, int kind) {
+RTU_HD S nfw_g(const S& x, const S& tau, int kind) {
     typedef typename base_of<S>::type T;
     S F = nfw_F(x);
     if (kind == 1) return r_log(x * T(0.5)) + F;
@@ -248,7 +252,7 @@ __device__ __forceinline__ S nfw_g(const S& x, const S& tau, int kind) {
 }
 
 template <typename S>
-__device__ __forceinline__ void nfw_deflect(const S& x, const S& y, const S& ks, const S& rs,
+RTU_HD void nfw_deflect(const S& x, const S& y, const S& ks, const S& rs,
                                             const S& tau, const S& xs, const S& ys, int kind,
                                             S& ax, S& ay) {
     typedef typename base_of<S>::type T;
@@ -258,6 +262,168 @@ __device__ __forceinline__ void nfw_deflect(const S& x, const S& y, const S& ks,
     S a = T(4) * ks * rs * nfw_g(xx, tau, kind) / xx / r;
     ax = a * dx;
     ay = a * dy;
+}
+
+// ------------------------------------------------ EPL with per-system constants
+// The Tessore & Metcalf series of the deflection of Eq. A1 split into what
+// depends on the lens only (computed once per system in double) and the per-ray
+// part, plus its analytic vector-Jacobian product with respect to
+// (theta_E, gamma, e1, e2, x0, y0).
+constexpr int EPL_MAXT = 96;
+
+template <typename T>
+struct EplC {
+    T x0, y0, cp, sp, q, cc, e1, e2, thE, sq, b, t, pref0, lnb, opq;
+    int nterm;
+    T cn[EPL_MAXT];   // c_n = -f (2n - 2 + t) / (2n + 2 - t), n = 1..nterm
+    T gn[EPL_MAXT];   // c_n / f
+    T Dn[EPL_MAXT];   // D_n = sum_{k <= n} d log|c_k| / dt
+};
+
+// the lens-only scalars of the series (everything but the term tables)
+template <typename T>
+RTU_HD void epl_scalars(EplC<T>& C, const double* p, bool epl) {
+    const double e1 = p[2], e2 = p[3];
+    const double cc = sqrt(fmax(e1 * e1 + e2 * e2, 1e-30));
+    const double q = (1.0 - cc) / (1.0 + cc);
+    const double phi = 0.5 * atan2(e2, e1);
+    const double t = (epl ? p[1] : 2.0) - 1.0;
+    const double sq = sqrt(q);
+    const double b = p[0] * sq;
+    C.x0 = (T)p[4]; C.y0 = (T)p[5]; C.cp = (T)cos(phi); C.sp = (T)sin(phi); C.q = (T)q; C.cc = (T)cc;
+    C.e1 = (T)e1; C.e2 = (T)e2; C.thE = (T)p[0]; C.sq = (T)sq; C.b = (T)b; C.t = (T)t;
+    C.pref0 = (T)(2.0 * b / (1.0 + q)); C.lnb = (T)log(b); C.opq = (T)(1.0 + q);
+}
+
+// p = theta_E, gamma, e1, e2, x0, y0 (gamma ignored unless epl); tol = size of the
+// last summed term relative to the leading one
+template <typename T>
+RTU_HD void epl_setup(EplC<T>& C, const double* p, bool epl, double tol) {
+    const double e1 = p[2], e2 = p[3];
+    const double cc = sqrt(fmax(e1 * e1 + e2 * e2, 1e-30));
+    const double q = (1.0 - cc) / (1.0 + cc);
+    const double phi = 0.5 * atan2(e2, e1);
+    const double t = (epl ? p[1] : 2.0) - 1.0;
+    const double f = (1.0 - q) / (1.0 + q);
+    const double sq = sqrt(q);
+    const double b = p[0] * sq;
+    C.x0 = (T)p[4]; C.y0 = (T)p[5]; C.cp = (T)cos(phi); C.sp = (T)sin(phi); C.q = (T)q; C.cc = (T)cc;
+    C.e1 = (T)e1; C.e2 = (T)e2; C.thE = (T)p[0]; C.sq = (T)sq; C.b = (T)b; C.t = (T)t;
+    C.pref0 = (T)(2.0 * b / (1.0 + q)); C.lnb = (T)log(b); C.opq = (T)(1.0 + q);
+    double a = 1.0, D = 0.0;
+    int n = 1;
+    for (; n <= EPL_MAXT; ++n) {
+        const double g = -(2.0 * n - 2.0 + t) / (2.0 * n + 2.0 - t);
+        const double c = f * g;
+        D += 1.0 / (2.0 * n - 2.0 + t) + 1.0 / (2.0 * n + 2.0 - t);
+        a *= c;
+        C.cn[n - 1] = (T)c; C.gn[n - 1] = (T)g; C.Dn[n - 1] = (T)D;
+        if (fabs(a) <= tol) break;
+    }
+    C.nterm = n > EPL_MAXT ? EPL_MAXT : n;
+}
+
+template <typename T>
+RTU_HD void epl_alpha(const EplC<T>& C, T x, T y, T& ax, T& ay) {
+    const T dx = x - C.x0, dy = y - C.y0;
+    const T xr = C.cp * dx + C.sp * dy, yr = C.cp * dy - C.sp * dx;
+    const T R2 = r_max(C.q * C.q * xr * xr + yr * yr, T(1e-20));
+    const T R = r_sqrt(R2), iR = T(1) / R;
+    const T cre = C.q * xr * iR, cim = yr * iR;
+    const T wre = cre * cre - cim * cim, wim = T(2) * cre * cim;
+    T tre = cre, tim = cim, sre = cre, sim = cim;
+    for (int n = 0; n < C.nterm; ++n) {
+        const T nre = tre * wre - tim * wim, nim = tre * wim + tim * wre;
+        tre = C.cn[n] * nre;
+        tim = C.cn[n] * nim;
+        sre += tre;
+        sim += tim;
+    }
+    const T P = C.pref0 * r_exp((C.t - T(1)) * (C.lnb - r_log(R)));
+    const T axr = P * sre, ayr = P * sim;
+    ax = C.cp * axr - C.sp * ayr;
+    ay = C.sp * axr + C.cp * ayr;
+}
+
+// Per-ray intermediates of the EPL deflection kept for the vector-Jacobian product.
+template <typename T>
+struct EplJ {
+    T xr, yr, iR, P, lbR, are, aim, ax, ay, hre, him, ure, uim, fre, fim;
+};
+
+// deflection alpha = (ax, ay) plus the series sums needed for its derivatives
+template <typename T>
+RTU_HD void epl_eval(const EplC<T>& C, bool want_t, T x, T y, EplJ<T>& J) {
+    const T dx = x - C.x0, dy = y - C.y0;
+    const T xr = C.cp * dx + C.sp * dy, yr = C.cp * dy - C.sp * dx;
+    const T q = C.q;
+    const T R2 = r_max(q * q * xr * xr + yr * yr, T(1e-20));
+    const T R = r_sqrt(R2), iR = T(1) / R;
+    const T cre = q * xr * iR, cim = yr * iR;
+    const T wre = cre * cre - cim * cim, wim = T(2) * cre * cim;
+    T tre = cre, tim = cim;
+    T sre = cre, sim = cim;            // S = sum Omega_n
+    T hre = cre, him = cim;            // sum (2n+1) Omega_n
+    T ure = T(0), uim = T(0);          // sum D_n Omega_n
+    T fre = T(0), fim = T(0);          // sum n g_n Omega_{n-1} w
+    for (int n = 0; n < C.nterm; ++n) {
+        const T nre = tre * wre - tim * wim, nim = tre * wim + tim * wre;
+        const T k = T(n + 1);
+        fre += k * C.gn[n] * nre;
+        fim += k * C.gn[n] * nim;
+        tre = C.cn[n] * nre;
+        tim = C.cn[n] * nim;
+        sre += tre; sim += tim;
+        const T w2 = T(2 * n + 3);
+        hre += w2 * tre; him += w2 * tim;
+        if (want_t) { ure += C.Dn[n] * tre; uim += C.Dn[n] * tim; }
+    }
+    const T lbR = C.lnb - r_log(R);
+    const T P = C.pref0 * r_exp((C.t - T(1)) * lbR);
+    J.xr = xr; J.yr = yr; J.iR = iR; J.P = P; J.lbR = lbR;
+    J.are = P * sre; J.aim = P * sim;
+    J.ax = C.cp * J.are - C.sp * J.aim;
+    J.ay = C.sp * J.are + C.cp * J.aim;
+    J.hre = hre; J.him = him; J.ure = ure; J.uim = uim; J.fre = fre; J.fim = fim;
+}
+
+// out[k] += Re(conj(G) d alpha / d p_k), G = (gx, gy) = dL/d alpha,
+// p = (theta_E, gamma, e1, e2, x0, y0); gamma only when want_t
+template <typename T>
+RTU_HD void epl_vjp(const EplC<T>& C, const EplJ<T>& J, bool want_t, T gx, T gy, T* out) {
+    const T q = C.q, t = C.t, xr = J.xr, yr = J.yr, iR = J.iR, P = J.P;
+    const T sthr = -J.him, sthi = J.hre;                 // S_theta = i sum (2n+1) Omega_n
+    const T iR2 = iR * iR;
+    const T th_xr = -yr * q * iR2, th_yr = q * xr * iR2, th_q = -yr * xr * iR2;
+    const T R_xr = q * q * xr * iR, R_yr = yr * iR, R_q = q * xr * xr * iR;
+    const T f_q = T(-2) / (C.opq * C.opq);
+    const T b_q = C.thE / (T(2) * C.sq);
+    const T tb = t / C.b, tm1R = (t - T(1)) * iR;
+    const T gxr = C.cp * gx + C.sp * gy, gyr = C.cp * gy - C.sp * gx;   // G in the lens frame
+    const T Pd_th = P * (gxr * sthr + gyr * sthi);
+    const T Pd_f = P * (gxr * J.fre + gyr * J.fim);
+    const T ad = gxr * J.are + gyr * J.aim;
+    const T d_xr = Pd_th * th_xr - ad * tm1R * R_xr;
+    const T d_yr = Pd_th * th_yr - ad * tm1R * R_yr;
+    const T d_q = Pd_th * th_q + Pd_f * f_q + ad * (tb * b_q - tm1R * R_q - T(1) / C.opq);
+    out[0] += ad * tb * C.sq;
+    if (want_t) out[1] += P * (gxr * J.ure + gyr * J.uim) + ad * J.lbR;
+    const T d_phi = d_xr * yr - d_yr * xr + (gy * J.ax - gx * J.ay);
+    const T icc2 = T(1) / (C.cc * C.cc);
+    const T q_c = T(-2) / ((T(1) + C.cc) * (T(1) + C.cc));
+    out[2] += d_q * q_c * C.e1 / C.cc - d_phi * T(0.5) * C.e2 * icc2;
+    out[3] += d_q * q_c * C.e2 / C.cc + d_phi * T(0.5) * C.e1 * icc2;
+    out[4] += -C.cp * d_xr + C.sp * d_yr;
+    out[5] += -C.sp * d_xr - C.cp * d_yr;
+}
+
+template <typename T>
+RTU_HD void epl_alpha_vjp(const EplC<T>& C, bool want_t, T x, T y, T gx, T gy, T& ax, T& ay, T* out) {
+    EplJ<T> J;
+    epl_eval(C, want_t, x, y, J);
+    ax = J.ax;
+    ay = J.ay;
+    epl_vjp(C, J, want_t, gx, gy, out);
 }
 
 }  // namespace rtu

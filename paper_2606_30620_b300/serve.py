@@ -152,80 +152,74 @@ class Server:
         self.batches += 1
         self.batch_sizes.append(len(reqs))
 
-    def _poll(self, now_fn, wait=False):
-        done_any = False
+    def _complete(self, t, ready):
+        """Retire the batches whose event has been reached; re-queue requests with
+        steps left, release finished systems unless they are kept resident."""
         keep = []
         for item in self.inflight:
             ev, k, reqs, out = item
-            if wait or ev.query():
-                ev.synchronize()
-                t = now_fn()
-                vals = out.cpu().numpy()
-                for r, v in zip(reqs, vals):
-                    r.done_steps += 1
-                    r.elbo = float(v)
-                    res = self.resident[r.system_id]
-                    res.pending -= 1
-                    if r.done_steps >= r.n_steps:
-                        r.finish = t
-                done_any = True
-            else:
+            if not ev.query():
                 keep.append(item)
+                continue
+            vals = out.cpu().numpy()
+            for r, v in zip(reqs, vals):
+                r.done_steps += 1
+                r.elbo = float(v)
+                res = self.resident[r.system_id]
+                res.pending -= 1
+                res.last_used = t
+                if r.done_steps < r.n_steps:
+                    ready.append(r)
+                else:
+                    r.finish = t
+                    if not self.keep_resident and res.pending == 0:
+                        self._release(r.system_id)
         self.inflight = keep
-        return done_any
 
     def run(self, requests, realtime: bool = True):
         """Serve a list of requests; with realtime=False all arrive at t = 0
         (saturation).  Returns the latency/throughput summary."""
         reqs = sorted(requests, key=lambda r: r.arrival)
+        for r in reqs:
+            r.done_steps, r.finish = 0, None
+            if not realtime:
+                r.arrival = 0.0
         arrivals = deque(reqs)
         ready = deque()
         t0 = time.perf_counter()
-        now = (lambda: time.perf_counter() - t0)
+
+        def now():
+            return time.perf_counter() - t0
+
         while arrivals or ready or self.inflight:
-            tn = now()
-            while arrivals and (not realtime or arrivals[0].arrival <= tn):
-                r = arrivals.popleft()
-                if not realtime:
-                    r.arrival = 0.0
-                ready.append(r)
-            self._poll(now)
+            t = now()
+            while arrivals and arrivals[0].arrival <= t:
+                ready.append(arrivals.popleft())
+            self._complete(t, ready)
             busy = {k for _, k, _, _ in self.inflight}
             free = [k for k in range(len(self.streams)) if k not in busy]
             if ready and free:
-                batch, skipped, ids = [], deque(), set()
+                batch, defer, ids = [], [], set()
                 while ready and len(batch) < self.max_batch:
                     r = ready.popleft()
-                    if r.system_id in ids or (r.system_id in self.resident
-                                              and self.resident[r.system_id].pending > 0):
-                        skipped.append(r)          # one step per system per batch
+                    if r.system_id in ids:
+                        defer.append(r)
                         continue
-                    if not self._admit(r, tn):
-                        skipped.append(r)
+                    if not self._admit(r, t):
+                        defer.append(r)          # budget full: wait for completions
                         break
                     self.resident[r.system_id].pending += 1
                     ids.add(r.system_id)
                     batch.append(r)
-                ready.extendleft(reversed(skipped))
+                ready.extendleft(reversed(defer))
                 if batch:
                     self._launch(batch, free[0])
                     continue
-            # release systems whose requests are all complete
-            if not self.keep_resident:
-                for sid in [sid for sid, r in self.resident.items() if r.pending == 0]:
-                    if not any(q.system_id == sid for q in ready):
-                        self._release(sid)
-            if self.inflight and not (ready and free):
-                # nothing to launch: wait for the oldest batch or the next arrival
-                if not arrivals or arrivals[0].arrival > now() + 1e-4:
+            if self.inflight:
+                if not arrivals or arrivals[0].arrival > now():
                     self.inflight[0][0].synchronize()
-            elif not self.inflight and arrivals and realtime:
-                time.sleep(max(0.0, min(1e-3, arrivals[0].arrival - now())))
-            # requests with more steps go back to the ready queue
-            for r in reqs:
-                if r.finish is None and r.done_steps > 0 and r.done_steps < r.n_steps and r not in ready \
-                        and self.resident.get(r.system_id) and self.resident[r.system_id].pending == 0:
-                    ready.append(r)
+            elif arrivals:
+                time.sleep(max(0.0, min(2e-3, arrivals[0].arrival - now())))
         wall = now()
         lat = np.array([r.finish - r.arrival for r in reqs])
         return {"systems": len(reqs), "wall_s": wall, "systems_per_s": len(reqs) / wall,
