@@ -222,6 +222,27 @@ rtu_status rtu_elbo_import(rtu_system* sys, const void* host, size_t bytes);
 rtu_status rtu_profile_enable(int32_t on);
 rtu_status rtu_profile_report(char* buf, size_t bytes);
 
+/* ---------------------------------------------------------------------------
+ * Allocation-free variant of the GP source step (the paper has no counterpart).
+ * For callers that cannot allocate device memory: an application that hands
+ * this library no workspace because its device memory is planned up front, or
+ * a process that must not call cudaMalloc after start-up.  It computes the
+ * source s* of rtu_forward's S6 (Eq. 1-3, FP32) from device pointers:
+ * latents [n_src*n_src] floats, ps [n_family + 1] doubles (alpha_src last) ->
+ * source [n_src*n_src] floats; k = 2 pi |fftfreq| / src_pitch.
+ * Its FFT scratch is one static device array of RTU_STATIC_MAX_NSRC^2 complex
+ * floats (128 KiB) that every GPU loading the library holds until exit; n_src
+ * above RTU_STATIC_MAX_NSRC (or not 2^a 3^b, or below 4) returns RTU_E_ARG.
+ * The first call on a device (with that device current) looks up the array's
+ * device address; make that first call before any stream capture.  The call
+ * allocates nothing (no cudaMalloc, cudaFree or allocating library routine).
+ * All calls share the array and it keeps the last call's contents (each call
+ * overwrites all it reads), so calls that overlap on the GPU -- e.g. on two
+ * streams at once -- race; serialise them. */
+#define RTU_STATIC_MAX_NSRC 128
+rtu_status rtu_gp_source_static(int32_t n_src, double src_pitch, int32_t ps_family, const float* latents,
+                                const double* ps, float* source, void* stream);
+
 /* Human-readable description of the last error on this host thread. */
 const char* rtu_last_error(void);
 

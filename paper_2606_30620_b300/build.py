@@ -1,8 +1,8 @@
 """Build the sm_103a CUDA library ``librtu.so`` in-tree with nvcc.
 
 ``python -m paper_2606_30620_b300.build`` (or ``build()``) compiles
-``csrc/rtu_host.cu`` (which includes every kernel header) into a shared
-library next to this file.  The C ABI is declared in ``include/rtu.h``.
+``csrc/rtu_host.cu`` (which includes every kernel header) and
+``csrc/rtu_static.cu`` into a shared library next to this file.  The C ABI is declared in ``include/rtu.h``.
 """
 from __future__ import annotations
 
@@ -42,7 +42,8 @@ def build(force: bool = False, verbose_ptxas: bool = False) -> str:
         return LIB
     cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC",
            "-I", os.path.join(ROOT, "include"), "-I", os.path.join(HERE, "csrc"),
-           os.path.join(HERE, "csrc", "rtu_host.cu"), "-o", LIB + ".tmp", "-lcudart"]
+           os.path.join(HERE, "csrc", "rtu_host.cu"), os.path.join(HERE, "csrc", "rtu_static.cu"),
+           "-o", LIB + ".tmp", "-lcudart"]
     if verbose_ptxas:
         cmd[1:1] = ["-Xptxas", "-v"]
     res = subprocess.run(cmd, capture_output=True, text=True)

@@ -20,7 +20,6 @@ __global__ void __launch_bounds__(CDF_NT) k_cdf_adj(const __grid_constant__ Batc
     const int ncol = NACC_FIX + 4 * K;
     __shared__ double tot[NACC_FIX + 4 * (MAXM + 2)];
     __shared__ double gXr[2][MAXM + 2], gpr[2][MAXM + 2], gc[2][MAXM], gQ[2][MAXM];
-    __shared__ double gfl_s[2];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     // column sums over the render-adjoint CTAs: one warp per column, fixed lane
     // stride and a fixed shuffle tree
@@ -99,7 +98,6 @@ __global__ void __launch_bounds__(CDF_NT) k_cdf_adj(const __grid_constant__ Batc
         E.tadj[2] = dsig / (N * sigma);
         E.tadj[3] = tr[3];
     }
-    (void)gfl_s;
 }
 
 // centre rays: d logL / d beta_i = selected-rank terms + dmu/N

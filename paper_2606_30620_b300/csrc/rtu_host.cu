@@ -35,6 +35,14 @@ rtu_status fail(rtu_status code, const std::string& msg) {
     return code;
 }
 
+}  // namespace
+
+__attribute__((visibility("hidden"))) rtu_status rtu_fail_internal(rtu_status code, const char* msg) {
+    return fail(code, msg);
+}
+
+namespace {
+
 size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
 
 bool factor_radices(int n, std::vector<int>& rad) {

@@ -197,7 +197,7 @@ template <typename T>
 __device__ __forceinline__ T epl_tol() { return sizeof(T) == 4 ? T(1e-9) : T(1e-17); }
 
 template <typename T>
-__device__ void lens_rest(LensK<T>& K, const double* lens, int profile, int sub_kind, int n_sub) {
+__device__ inline void lens_rest(LensK<T>& K, const double* lens, int profile, int sub_kind, int n_sub) {
     K.g1 = (T)lens[6];
     K.g2 = (T)lens[7];
     K.rc2 = (T)(1e-4 * lens[0] * lens[0]);          // |theta - centre| < 0.01 theta_E
@@ -212,7 +212,7 @@ __device__ void lens_rest(LensK<T>& K, const double* lens, int profile, int sub_
 // c_n, c_n/f and the per-term t-derivative of log|c_n| in parallel (one thread
 // per term), the running products and sums, and the stopping index of each
 // precision (1e-17 for double, 1e-9 for float), by one thread.
-__device__ void lens_setup_par(LensK<double>* Kd, LensK<float>* Kf, const double* lens, int profile, int sub_kind,
+__device__ inline void lens_setup_par(LensK<double>* Kd, LensK<float>* Kf, const double* lens, int profile, int sub_kind,
                                int n_sub) {
     __shared__ double sc[EPL_MAXT], sg[EPL_MAXT], sdl[EPL_MAXT], sconst[4];
     if (threadIdx.x == 0) {

@@ -82,6 +82,9 @@ _lib.rtu_elbo_export.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size
 _lib.rtu_elbo_export.restype = ctypes.c_int32
 _lib.rtu_elbo_import.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]
 _lib.rtu_elbo_import.restype = ctypes.c_int32
+_lib.rtu_gp_source_static.argtypes = [ctypes.c_int32, ctypes.c_double, ctypes.c_int32, ctypes.c_void_p,
+                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+_lib.rtu_gp_source_static.restype = ctypes.c_int32
 _lib.rtu_profile_enable.argtypes = [ctypes.c_int32]
 _lib.rtu_profile_enable.restype = ctypes.c_int32
 _lib.rtu_profile_report.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
@@ -91,7 +94,8 @@ _lib.rtu_version.restype = ctypes.c_char_p
 
 EXPORTED = ("rtu_workspace_size", "rtu_system_create", "rtu_system_destroy", "rtu_build_grid",
             "rtu_forward", "rtu_adjoint", "rtu_n_sites", "rtu_elbo_init", "rtu_elbo_step",
-            "rtu_elbo_state_bytes", "rtu_elbo_export", "rtu_elbo_import", "rtu_profile_enable",
+            "rtu_elbo_state_bytes", "rtu_elbo_export", "rtu_elbo_import", "rtu_gp_source_static",
+            "rtu_profile_enable",
             "rtu_profile_report", "rtu_last_error", "rtu_version")
 
 
@@ -313,6 +317,21 @@ def rtu_elbo_step(systems, n_samples: int, seed: int, lr: float, elbo_out=None, 
     out = None if elbo_out is None else ctypes.c_void_p(elbo_out.data_ptr())
     _check(_lib.rtu_elbo_step(arr, n, int(n_samples), int(seed) & 0xFFFFFFFFFFFFFFFF, float(lr), out,
                               _stream_ptr(stream)), "rtu_elbo_step")
+
+
+STATIC_MAX_NSRC = 128
+
+
+def rtu_gp_source_static(n_src: int, src_pitch: float, ps_family: int, latents, ps, source, stream=None):
+    """GP source (Eq. 1-3, FP32) without a workspace: latents / source are float32
+    CUDA tensors [n_src, n_src], ps a float64 CUDA tensor.  Allocates no device memory;
+    calls share one static scratch array, so do not overlap them on the GPU."""
+    for t, dt in ((latents, torch.float32), (source, torch.float32), (ps, torch.float64)):
+        if t.dtype != dt or not t.is_cuda or not t.is_contiguous():
+            raise ValueError("latents/source must be contiguous float32 CUDA tensors, ps float64")
+    _check(_lib.rtu_gp_source_static(int(n_src), float(src_pitch), int(ps_family), latents.data_ptr(),
+                                     ps.data_ptr(), source.data_ptr(), _stream_ptr(stream)),
+           "rtu_gp_source_static")
 
 
 class RTUForward(torch.autograd.Function):
