@@ -41,9 +41,10 @@ L2_BYTES = 126 * 1024 * 1024
 # recipe unit counts: 148 SMs x 128 FP32 lanes x 2 flop per FMA at the 2032 MHz maximum SM clock
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
 FALLBACK_HBM_GBS = 6400.0
-# algorithmic FP32 flops per supersampled ray ("Roofline accounting")
-FLOPS_FWD_RAY = 250.0
-FLOPS_ADJ_RAY = 3.0 * FLOPS_FWD_RAY
+# algorithmic FP32 flops per supersampled ray: the EPL trace + map + interpolation of
+# one ray (about 190), its adjoint about 2.5x that ("Roofline accounting")
+FLOPS_FWD_RAY = 190.0
+FLOPS_ADJ_RAY = 2.5 * FLOPS_FWD_RAY
 
 
 def env_rank():
@@ -60,14 +61,18 @@ class ClockSampler:
         self.gpu = gpu_index
         self.proc = None
         self.lines = []
+        self.first = threading.Event()
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.th = threading.Thread(target=self._read, daemon=True)
             self.th.start()
+            # nvidia-smi takes a moment to start: the timed region begins after its first sample
+            self.first.wait(timeout=10.0)
+            self.lines.clear()
         except OSError:
             self.proc = None
         return self
@@ -75,9 +80,14 @@ class ClockSampler:
     def _read(self):
         for line in self.proc.stdout:
             self.lines.append(line.strip())
+            self.first.set()
 
     def __exit__(self, *a):
         if self.proc is not None:
+            # at least one sample taken after the region's start
+            t0 = time.perf_counter()
+            while not self.lines and time.perf_counter() - t0 < 2.0:
+                time.sleep(0.02)
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
@@ -183,7 +193,8 @@ def run_ours(args):
     # packed inputs [lens(8) | ps(3)] as float64 and latents as float32; packed outputs
     in_f64 = torch.empty(n, 8 + nps, dtype=torch.float64, device=dev)
     in_lat = torch.empty(n, n2, dtype=torch.float32, device=dev)
-    out_f64 = torch.empty(n, 4 + 8 + nps, dtype=torch.float64, device=dev)
+    NS = rtu.N_STATS
+    out_f64 = torch.empty(n, NS + 8 + nps, dtype=torch.float64, device=dev)
     out_lat = torch.empty(n, n2, dtype=torch.float32, device=dev)
     h_in_f64 = torch.tensor(np.stack([np.concatenate([m.lens, m.ps]) for m in mocks]), dtype=torch.float64).pin_memory()
     h_in_lat = torch.tensor(np.stack([m.latents.ravel() for m in mocks]), dtype=torch.float32).pin_memory()
@@ -194,8 +205,8 @@ def run_ours(args):
     binds = []
     for k, s in enumerate(systems):
         binds.append(rtu.Binding(s, in_f64[k, :8], in_lat[k].view(mocks[k].n_src, mocks[k].n_src),
-                                 in_f64[k, 8:], out={"stats": out_f64[k, :4], "g_lens": out_f64[k, 4:12],
-                                                     "g_ps": out_f64[k, 12:],
+                                 in_f64[k, 8:], out={"stats": out_f64[k, :NS], "g_lens": out_f64[k, NS:NS + 8],
+                                                     "g_ps": out_f64[k, NS + 8:],
                                                      "g_latents": out_lat[k].view(mocks[k].n_src, mocks[k].n_src)}))
     batch = rtu.Batch(binds)
     singles = [rtu.Batch([b]) for b in binds]
@@ -292,13 +303,16 @@ def run_ours(args):
     launches = sum(v[0] for v in kern.values())
 
     clocks = clk.summary()
+    serving = run_serving(args, dev) if args.serve_n > 0 else None
     if rank != 0:
         if dist:
             tdist.destroy_process_group()
         return 0
     peaks, peak_kind = measured_peaks()
+    # the adjoint differentiates the rays inside the RTU grid (zero gradient elsewhere)
+    rays_in = float(out_f64[:, rtu.STAT_N_IN_GRID].sum())
     rays = sum(m.n_rays for m in mocks)
-    achieved = FLOPS_ADJ_RAY * rays / (ra_ms / 1e3) / 1e12
+    achieved = FLOPS_ADJ_RAY * rays_in / (ra_ms / 1e3) / 1e12
     traffic = None
     tfile = os.path.join(ROOT, "profiles", "render_adj_traffic.json")
     if os.path.exists(tfile):
@@ -322,12 +336,15 @@ def run_ours(args):
                             "note": "same 32 evaluations issued as 32 single-system calls"},
         "roofline": {"kernel": "k_render_adj<float>", "top_kernel": top[0], "bound": "alu", "achieved": achieved,
                      "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
-                     "traffic": traffic, "launch_ms": ra_ms,
+                     "traffic": traffic, "launch_ms": ra_ms, "units": "in-grid rays",
+                     "units_per_launch": rays_in, "rays_per_launch": rays,
+                     "flops_per_unit": FLOPS_ADJ_RAY,
                      "peak_note": "FP32 FMA peak from unit counts (148 SMs x 128 lanes x 2 x 2032 MHz)",
                      "hbm_peak_gbs": peaks.get("hbm_gbs"), "hbm_peak_kind": peak_kind},
         "cpu_baseline": {"value": cpu_v, "unit": "evals/s", "cores": cores, "kind": "oracle",
                          "sample": f"{cpu_n} of the {n} mocks ({cpu_dt:.1f} s): FP64 oracle forward + autograd gradient"},
         "clocks": {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
+        "serving": serving,
     }
     print(json.dumps(line), flush=True)
     if dist:
@@ -335,16 +352,41 @@ def run_ours(args):
     return 0
 
 
+def run_serving(args, dev):
+    """The serving workload: a stream of lens systems (image 64-256^2, grid 32-128^2,
+    2-4x rays, SIE or EPL + shear) arriving Poisson at 2000/s, one ELBO step each with
+    the state kept on the device, 120 GB admission budget.  Measured three ways on the
+    same systems: the continuous-batching server in real time (latency), the server with
+    every request queued at t = 0 (saturation throughput), and the plain per-system path."""
+    from paper_2606_30620_b300 import serve
+    import copy
+    base = serve.make_stream(args.serve_n, 2000.0, seed=5000)
+
+    def fresh():
+        return [serve.Request(rid=r.rid, system_id=r.system_id, mock=r.mock, arrival=r.arrival) for r in base]
+
+    torch.cuda.synchronize()
+    live = serve.Server(budget_bytes=120 << 30, max_batch=32, n_samples=1, device=dev).run(fresh(), realtime=True)
+    sat = serve.Server(budget_bytes=120 << 30, max_batch=32, n_samples=1, device=dev).run(fresh(), realtime=False)
+    plain = serve.serve_plain(fresh(), n_samples=1, device=dev)
+    keep = ("systems", "wall_s", "systems_per_s", "p50_ms", "p99_ms", "mean_batch")
+    return {"stream": f"{args.serve_n} systems, Poisson 2000/s, one ELBO step (S=1) each, 120 GB budget",
+            "open_loop": {k: live[k] for k in keep},
+            "saturation": {k: sat[k] for k in keep},
+            "plain_per_system": {k: plain[k] for k in ("systems", "wall_s", "systems_per_s")}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--mocks", type=int, default=N_MOCKS, help="mocks per rank (32 is the benchmark workload)")
     ap.add_argument("--no-single", action="store_true", help="skip the per-system comparison path")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--serve-n", type=int, default=4096, help="systems in the serving stream (0 = skip)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -73,10 +73,15 @@ enum { RTU_F32 = 0, RTU_F64 = 1 };
 enum { RTU_SIE = 0, RTU_EPL = 1 };
 enum { RTU_SUB_NONE = 0, RTU_SUB_NFW = 1, RTU_SUB_TNFW = 2 };
 enum { RTU_PS_POWER_LAW = 0, RTU_PS_MATERN_LIKE = 1, RTU_PS_MATERN = 2 };
+/* Source-grid coordinates: the ray-guided transformed uniform grid (smoothed
+ * marginal CDFs, Sec. 2.2, App. C) or the uniform grid over the smallest square
+ * box containing the masked rays (Sec. 2.1), mapped affinely onto [0, 1]^2. */
+enum { RTU_TRANSFORM_RTU = 0, RTU_TRANSFORM_UNIFORM = 1 };
 
-/* stats[] written by rtu_forward (double[RTU_N_STATS]) */
+/* stats[] written by rtu_forward (double[RTU_N_STATS]); N_IN_GRID = supersampled
+ * rays that land inside the RTU grid (the rays the adjoint differentiates) */
 enum { RTU_STAT_LOGL = 0, RTU_STAT_CHI2_MASK = 1, RTU_STAT_N_MASK = 2, RTU_STAT_FLAGS = 3,
-       RTU_N_STATS = 4 };
+       RTU_STAT_N_IN_GRID = 4, RTU_N_STATS = 5 };
 
 #define RTU_N_LENS 8
 #define RTU_N_SUB_PARAMS 5
@@ -97,6 +102,8 @@ typedef struct {
     int32_t n_nodes;     /* Chebyshev nodes M (App. C iii); must equal degree+1 */
     int32_t degree;      /* polynomial degree D of the quantile fit (21 in the paper) */
     int32_t n_slots;     /* concurrent evaluations of this system (e.g. ELBO samples) */
+    int32_t transform;   /* RTU_TRANSFORM_RTU (Sec. 2.2) | RTU_TRANSFORM_UNIFORM (Sec. 2.1 box) */
+    int32_t reserved_;   /* 0 */
     double pix;          /* arcsec per pixel */
     double src_pitch;    /* source-grid pitch entering k (arcsec) */
     double sigma;        /* Gaussian noise rms (Sec. 3.1) */

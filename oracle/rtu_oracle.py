@@ -63,6 +63,8 @@ N_LENS = 8          # theta_E, gamma, e1, e2, x0, y0, Gamma1, Gamma2
 N_SUB_PARAMS = 5    # kappa_s, r_s, tau, x_s, y_s
 
 FLAG_NONMONOTONE = 1
+TRANSFORM_RTU = 0       # the ray-guided transformed uniform grid (Sec. 2.2)
+TRANSFORM_UNIFORM = 1   # the uniform grid over the masked rays' square box (Sec. 2.1)
 
 
 # ---------------------------------------------------------------------------
@@ -363,8 +365,32 @@ def hermite_cdf(z, X, U, d):
     return torch.where(z < X[0], left, torch.where(z >= X[-1], right, inner))
 
 
-def rtu_map(bx, by, T: RTUTransform):
-    """Eq. 5 coordinates: y = g(x) = (C_1(z_1), C_2(z_2)), z = (beta - mu)/sigma_min."""
+@dataclass
+class BoxTransform:
+    """The old approach's uniform grid (Sec. 2.1): the smallest square box that
+    contains every masked ray, mapped affinely onto the unit square."""
+    lo: torch.Tensor        # [2] lower corner
+    side: torch.Tensor      # box side
+    flags: int = 0
+
+
+def uniform_box(bx, by):
+    """Square box around the masked centre rays: centred on each axis's range, side =
+    the larger range (tie -> x)."""
+    mins = torch.stack([bx.min(), by.min()])
+    maxs = torch.stack([bx.max(), by.max()])
+    rng = maxs - mins
+    side = rng[0] if float(rng[0].detach()) >= float(rng[1].detach()) else rng[1]
+    centre = 0.5 * (mins + maxs)
+    return BoxTransform(lo=centre - 0.5 * side, side=side)
+
+
+def rtu_map(bx, by, T):
+    """Source-grid coordinates of source-plane positions: for the RTU grid Eq. 5,
+    y = g(x) = (C_1(z_1), C_2(z_2)) with z = (beta - mu)/sigma_min; for the uniform
+    grid the affine box map y = (beta - lo)/side."""
+    if isinstance(T, BoxTransform):
+        return (bx - T.lo[0]) / T.side, (by - T.lo[1]) / T.side
     zx = (bx - T.mu[0]) / T.sigma
     zy = (by - T.mu[1]) / T.sigma
     return (hermite_cdf(zx, T.knots[0], T.values, T.slopes[0]),
@@ -475,6 +501,7 @@ class System:
     sub_kind: int = SUB_NONE
     n_nodes: int = 22
     degree: int = 21
+    transform: int = TRANSFORM_RTU
 
     @property
     def n_img(self):
@@ -486,6 +513,8 @@ def build_grid(sys: System, lens, subs=None):
     xc, yc = pixel_centres(sys.n_img, sys.pix)
     sel = sys.mask.reshape(-1)
     bx, by = trace(xc[sel], yc[sel], lens, sys.profile, subs, sys.sub_kind)
+    if sys.transform == TRANSFORM_UNIFORM:
+        return uniform_box(bx, by)
     return fit_transform(bx, by, sys.n_nodes, sys.degree)
 
 

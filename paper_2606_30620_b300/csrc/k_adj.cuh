@@ -25,13 +25,45 @@ __global__ void __launch_bounds__(CDF_NT) k_cdf_adj(const __grid_constant__ Batc
     // stride and a fixed shuffle tree
     for (int col = wid; col < ncol; col += CDF_NT / 32) {
         double s = 0.0;
-        for (int t = lane; t < E.n_cta_r; t += 32) s += E.apart[(size_t)t * nacc + col];
+        for (int t = lane; t < E.n_cta_adj; t += 32) s += E.apart[(size_t)t * nacc + col];
         for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
         if (lane == 0) tot[col] = s;
     }
     __syncthreads();
     const double* tr = E.trd;
     const double sigma = tr[2];
+    if (E.transform) {
+        // uniform grid: X_j = (lo_a + U_j L - mu_a)/sigma, slopes sigma/L, with
+        // lo_a = (min_a + max_a)/2 - L/2 and L the larger range (axis amax)
+        if (threadIdx.x == 0) {
+            const int amax = tr[5] > 0.5 ? 1 : 0;
+            const double L = tr[6];
+            double dmu[2] = {tot[8], tot[9]}, dsig = tot[10], dL = 0.0, dc[2] = {0.0, 0.0};
+            for (int a = 0; a < 2; ++a) {
+                const double* X = tr + TR_HDR + a * K;
+                for (int j = 0; j < K; ++j) {
+                    const double U = j == 0 ? 0.0 : (j == K - 1 ? 1.0 : E.cheb[cheb_u(M, D) + j - 1]);
+                    const double gX = tot[NACC_FIX + a * K + j], gd = tot[NACC_FIX + 2 * K + a * K + j];
+                    dc[a] += gX / sigma;
+                    dL += gX * (U - 0.5) / sigma - gd * sigma / (L * L);
+                    dmu[a] -= gX / sigma;
+                    dsig += -gX * X[j] / sigma + gd / L;
+                }
+            }
+            for (int a = 0; a < 2; ++a) {
+                double gmin = 0.5 * dc[a], gmax = 0.5 * dc[a];
+                if (a == amax) { gmax += dL; gmin -= dL; }
+                E.tadj[TADJ_SEL + a * 2 * MAXM + 0] = gmin;
+                E.tadj[TADJ_SEL + a * 2 * MAXM + 1] = gmax;
+                for (int t = 2; t < 2 * MAXM; ++t) E.tadj[TADJ_SEL + a * 2 * MAXM + t] = 0.0;
+            }
+            E.tadj[0] = dmu[0] / N;
+            E.tadj[1] = dmu[1] / N;
+            E.tadj[2] = dsig / (N * sigma);
+            E.tadj[3] = tr[3];
+        }
+        return;
+    }
     // back through the guard (sequential in the knots; one thread per axis)
     if (threadIdx.x < 2) {
         const int a = threadIdx.x;
@@ -120,7 +152,7 @@ __global__ void __launch_bounds__(CTA_C) k_centre_adj(const __grid_constant__ Ba
     if (sizeof(T) == 4) load_lensk(Ld, E.lensk);
     for (int i = threadIdx.x; i < 2 * 2 * MAXM; i += blockDim.x) {
         const int a = i / (2 * MAXM), t = i - a * 2 * MAXM;
-        const bool on = t < 2 * M;
+        const bool on = t < 2 * M && E.sel_idx[a * 2 * MAXM + t] >= 0;
         sidx[a][t] = on ? E.sel_idx[a * 2 * MAXM + t] : -1;
         sg[a][t] = on ? E.tadj[TADJ_SEL + a * 2 * MAXM + t] : 0.0;
     }
@@ -198,7 +230,7 @@ __global__ void __launch_bounds__(64) k_grad_final(const __grid_constant__ Batch
     for (int p = threadIdx.x; p < nl; p += blockDim.x) {
         const int col = p < 8 ? p : NACC_FIX + 4 * K + (p - 8);
         double s = 0.0;
-        for (int t = 0; t < E.n_cta_r; ++t) s += E.apart[(size_t)t * nacc + col];
+        for (int t = 0; t < E.n_cta_adj; ++t) s += E.apart[(size_t)t * nacc + col];
         double c = 0.0;
         for (int t = 0; t < E.n_cta_c; ++t) c += E.cadj[(size_t)t * nl + p];
         double g = s + c;

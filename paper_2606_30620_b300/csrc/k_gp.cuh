@@ -118,33 +118,39 @@ __device__ __forceinline__ double fftfreq(int i, int n) {
     return (double)(i < (n + 1) / 2 ? i : i - n) / n;
 }
 
-// sqrt(P(k)) and d sqrt(P)/d theta for the family (Eq. 4 and its stand-ins)
-__device__ __forceinline__ double sqrtP_and_grad(int family, const double* ps, double k, double* g) {
+// sqrt(P(k)) and d sqrt(P)/d theta for the family (Eq. 4 and its stand-ins), in
+// the type R (double in FP64 mode, float in FP32 mode)
+template <typename R>
+__device__ __forceinline__ R sqrtP_and_grad(int family, const R* ps, R k, R* g) {
     if (family == 0) {            // A k^-beta, zero mode removed
-        if (k == 0.0) { g[0] = g[1] = 0.0; return 0.0; }
-        double A = ps[0], be = ps[1];
-        double sp = sqrt(A * pow(k, -be));
-        g[0] = sp / (2.0 * A);
-        g[1] = -0.5 * log(k) * sp;
+        if (k == R(0)) { g[0] = g[1] = R(0); return R(0); }
+        const R A = ps[0], be = ps[1];
+        const R lk = r_log(k);
+        const R sp = r_sqrt(A) * r_exp(R(-0.5) * be * lk);
+        g[0] = sp / (R(2) * A);
+        g[1] = R(-0.5) * lk * sp;
         return sp;
     }
     if (family == 1) {            // A / (1 + (k/k0)^2)^2
-        double A = ps[0], k0 = ps[1];
-        double u = 1.0 + (k / k0) * (k / k0);
-        double sp = sqrt(A) / u;
-        g[0] = sp / (2.0 * A);
-        g[1] = sqrt(A) * 2.0 * k * k / (k0 * k0 * k0) / (u * u);
+        const R A = ps[0], k0 = ps[1];
+        const R kk = k / k0;
+        const R u = R(1) + kk * kk;
+        const R sA = r_sqrt(A);
+        const R sp = sA / u;
+        g[0] = sp / (R(2) * A);
+        g[1] = sA * R(2) * kk * kk / (k0 * u * u);
         return sp;
     }
     // Eq. 4: sigma^2 4 pi n (2n/zeta^2)^n (2n/zeta^2 + k^2)^-(n+1)
-    double sg = ps[0], nn = ps[1], ze = ps[2];
-    double a = 2.0 * nn / (ze * ze);
-    double logP = 2.0 * log(sg) + log(4.0 * 3.14159265358979323846 * nn) + nn * log(a)
-                  - (nn + 1.0) * log(a + k * k);
-    double sp = exp(0.5 * logP);
+    const R sg = ps[0], nn = ps[1], ze = ps[2];
+    const R a = R(2) * nn / (ze * ze);
+    const R lak = r_log(a + k * k);
+    const R logP = R(2) * r_log(sg) + r_log(R(4.0 * 3.14159265358979323846) * nn) + nn * r_log(a)
+                   - (nn + R(1)) * lak;
+    const R sp = r_exp(R(0.5) * logP);
     g[0] = sp / sg;
-    g[1] = 0.5 * sp * (1.0 / nn + log(a) + 1.0 - log(a + k * k) - (nn + 1.0) * a / (nn * (a + k * k)));
-    g[2] = 0.5 * sp * (-2.0 * nn / ze + 2.0 * (nn + 1.0) * a / (ze * (a + k * k)));
+    g[1] = R(0.5) * sp * (R(1) / nn + r_log(a) + R(1) - lak - (nn + R(1)) * a / (nn * (a + k * k)));
+    g[2] = R(0.5) * sp * (R(-2) * nn / ze + R(2) * (nn + R(1)) * a / (ze * (a + k * k)));
     return sp;
 }
 
@@ -200,14 +206,15 @@ __global__ void __launch_bounds__(GP_NT) k_gp_source(const __grid_constant__ Bat
     __syncthreads();
     fft2<T>(W, n, rad_s, E.nrad, tw_s, rev_s, sm, chunk, false);
     const int nf = n_family(E.family);
-    double psv[4];
-    for (int q = 0; q < nf; ++q) psv[q] = E.ps[q];
+    T psv[4];
+    for (int q = 0; q < nf; ++q) psv[q] = (T)E.ps[q];
+    const T kscale = (T)(2.0 * 3.14159265358979323846 / E.pitch);
     for (int i = threadIdx.x; i < n2; i += blockDim.x) {
         const int ky = i / n, kx = i - ky * n;
-        const double fx = fftfreq(kx, n), fy = fftfreq(ky, n);
-        const double k = 2.0 * 3.14159265358979323846 * sqrt(fx * fx + fy * fy) / E.pitch;
-        double gdummy[3];
-        const T sp = (T)sqrtP_and_grad(E.family, psv, k, gdummy);
+        const T fx = (T)fftfreq(kx, n), fy = (T)fftfreq(ky, n);
+        const T k = kscale * r_sqrt(fx * fx + fy * fy);
+        T gdummy[3];
+        const T sp = sqrtP_and_grad<T>(E.family, psv, k, gdummy);
         W[i] = Cx<T>{W[i].x * sp, W[i].y * sp};
     }
     __syncthreads();
@@ -249,48 +256,53 @@ __global__ void __launch_bounds__(GP_NT) k_gp_adjoint(const __grid_constant__ Ba
     const T* src = reinterpret_cast<const T*>(E.src);
     const int nf = n_family(E.family);
     const T alpha = (T)E.ps[nf];
-    double ga = 0.0;
+    T ga_t = T(0);
     for (int i = threadIdx.x; i < n2; i += blockDim.x) {
         const int j = i / n, ii = i - j * n;
-        double g = 0.0;
-        if (ii < nc && j < nc) g += E.corner[(j * nc + ii) * 4 + 0];
-        if (ii > 0 && j < nc) g += E.corner[(j * nc + ii - 1) * 4 + 1];
-        if (ii < nc && j > 0) g += E.corner[((j - 1) * nc + ii) * 4 + 2];
-        if (ii > 0 && j > 0) g += E.corner[((j - 1) * nc + ii - 1) * 4 + 3];
+        typedef typename real2_of<T>::type TP;
+        const TP* cor = reinterpret_cast<const TP*>(E.corner);
+        T g = T(0);
+        if (ii < nc && j < nc) { const TP c = cor[(j * nc + ii) * 4 + 0]; g += c.x + c.y; }
+        if (ii > 0 && j < nc) { const TP c = cor[(j * nc + ii - 1) * 4 + 1]; g += c.x + c.y; }
+        if (ii < nc && j > 0) { const TP c = cor[((j - 1) * nc + ii) * 4 + 2]; g += c.x + c.y; }
+        if (ii > 0 && j > 0) { const TP c = cor[((j - 1) * nc + ii - 1) * 4 + 3]; g += c.x + c.y; }
         const T s = src[i];
         const T x = fld[i] / T(0.01);
         // d s / d f = alpha s (sigma(x)/phi_sp(x)) / s0
         const T dsdf = alpha * s * sig_over_sp<T>(x) / T(0.01);
-        G[i] = Cx<T>{(T)g * dsdf, T(0)};
+        G[i] = Cx<T>{g * dsdf, T(0)};
         W[i] = Cx<T>{w[i], T(0)};
-        if (s > T(0)) ga += g * (double)s * (double)log_sp_s0<T>(x);
+        if (s > T(0)) ga_t += g * s * log_sp_s0<T>(x);
     }
-    ga = block_sum<GP_NT>(ga, red);
+    const double ga = block_sum_t<GP_NT>(ga_t, red);
     __syncthreads();
     fft2<T>(G, n, rad_s, E.nrad, tw_s, rev_s, sm, chunk, false);
     fft2<T>(W, n, rad_s, E.nrad, tw_s, rev_s, sm, chunk, false);
-    double psv[4];
-    for (int q = 0; q < nf; ++q) psv[q] = E.ps[q];
-    double gp[3] = {0.0, 0.0, 0.0};
+    T psv[4];
+    for (int q = 0; q < nf; ++q) psv[q] = (T)E.ps[q];
+    const T kscale = (T)(2.0 * 3.14159265358979323846 / E.pitch);
+    const T inv_n2s = T(1) / T(n2);
+    T gp[3] = {T(0), T(0), T(0)};
     for (int i = threadIdx.x; i < n2; i += blockDim.x) {
         const int ky = i / n, kx = i - ky * n;
-        const double fx = fftfreq(kx, n), fy = fftfreq(ky, n);
-        const double k = 2.0 * 3.14159265358979323846 * sqrt(fx * fx + fy * fy) / E.pitch;
-        double dsp[3] = {0.0, 0.0, 0.0};
-        const double sp = sqrtP_and_grad(E.family, psv, k, dsp);
+        const T fx = (T)fftfreq(kx, n), fy = (T)fftfreq(ky, n);
+        const T k = kscale * r_sqrt(fx * fx + fy * fy);
+        T dsp[3] = {T(0), T(0), T(0)};
+        const T sp = sqrtP_and_grad<T>(E.family, psv, k, dsp);
         const Cx<T> Gk = G[i], Wk = W[i];
-        const double d = ((double)Wk.x * (double)Gk.x + (double)Wk.y * (double)Gk.y) / (double)n2;
+        const T d = (Wk.x * Gk.x + Wk.y * Gk.y) * inv_n2s;
         for (int q = 0; q < nf; ++q) gp[q] += d * dsp[q];
-        G[i] = Cx<T>{Gk.x * (T)sp, Gk.y * (T)sp};
+        G[i] = Cx<T>{Gk.x * sp, Gk.y * sp};
     }
-    for (int q = 0; q < nf; ++q) gp[q] = block_sum<GP_NT>(gp[q], red);
+    double gpd[3] = {0.0, 0.0, 0.0};
+    for (int q = 0; q < nf; ++q) gpd[q] = block_sum_t<GP_NT>(gp[q], red);
     __syncthreads();
     fft2<T>(G, n, rad_s, E.nrad, tw_s, rev_s, sm, chunk, true);
     T* gl = reinterpret_cast<T*>(E.g_lat);
     const T inv_n2 = T(1) / T(n2);
     for (int i = threadIdx.x; i < n2; i += blockDim.x) gl[i] = G[i].x * inv_n2;
     if (threadIdx.x == 0) {
-        for (int q = 0; q < nf; ++q) E.g_ps[q] = gp[q];
+        for (int q = 0; q < nf; ++q) E.g_ps[q] = gpd[q];
         E.g_ps[nf] = ga;
     }
 }

@@ -174,15 +174,22 @@ __global__ void __launch_bounds__(SEL_NT) k_select_fit(const __grid_constant__ B
         __syncthreads();
         chunk_off[tid] = wtot[tid >> 5] + incl - own;
         __syncthreads();
-        // target ranks: node j -> floor(u_j (N-1)) and the next one
-        const int nt = 2 * M;
+        // target ranks: node j -> floor(u_j (N-1)) and the next one (RTU grid); the
+        // smallest and largest ray (uniform grid: the square box, Sec. 2.1)
+        const int nt = E.transform ? 2 : 2 * M;
         for (int t = tid; t < nt; t += SEL_NT) {
-            double h = E.cheb[cheb_u(M, D) + t / 2] * (N - 1);
-            int k = (int)floor(h);
-            k = k < 0 ? 0 : (k > N - 1 ? N - 1 : k);
-            if (t & 1) k = k + 1 > N - 1 ? N - 1 : k + 1;
+            int k;
+            if (E.transform) {
+                k = t == 0 ? 0 : N - 1;
+            } else {
+                double h = E.cheb[cheb_u(M, D) + t / 2] * (N - 1);
+                k = (int)floor(h);
+                k = k < 0 ? 0 : (k > N - 1 ? N - 1 : k);
+                if (t & 1) k = k + 1 > N - 1 ? N - 1 : k + 1;
+            }
             t_rank[t] = k;
         }
+        for (int t = nt + tid; t < 2 * MAXM; t += SEL_NT) E.sel_idx[a * 2 * MAXM + t] = -1;
         for (int t = tid; t < nt; t += SEL_NT) { t_bin[t] = 0; t_below[t] = 0; }
         __syncthreads();
         for (int t = 0; t < nt; ++t) {
@@ -251,7 +258,7 @@ __global__ void __launch_bounds__(SEL_NT) k_select_fit(const __grid_constant__ B
         }
         __syncthreads();
         // empirical QF at the nodes in standardized coordinates (type-7 interpolation)
-        for (int j = tid; j < M; j += SEL_NT) {
+        for (int j = tid; j < M && !E.transform; j += SEL_NT) {
             double h = E.cheb[cheb_u(M, D) + j] * (N - 1);
             double frac = h - floor(h);
             double zl = (E.sel_val[a * 2 * MAXM + 2 * j] - mom[a]) / sigma;
@@ -261,6 +268,41 @@ __global__ void __launch_bounds__(SEL_NT) k_select_fit(const __grid_constant__ B
         __syncthreads();
     }
 
+    double* tr = E.trd;
+    if (E.transform) {
+        // uniform grid: the smallest square box around the masked rays, centred on
+        // each axis's range, mapped affinely onto [0, 1]^2 -- written as Hermite
+        // knots X_j = (lo + U_j L - mu)/sigma with equal slopes sigma/L (linear)
+        if (tid < 2) {
+            const int a = tid;
+            const double mn0 = E.sel_val[0], mx0 = E.sel_val[1];
+            const double mn1 = E.sel_val[2 * MAXM], mx1 = E.sel_val[2 * MAXM + 1];
+            const double r0 = mx0 - mn0, r1 = mx1 - mn1;
+            const double L = r0 >= r1 ? r0 : r1;
+            const double mn = a == 0 ? mn0 : mn1, mx = a == 0 ? mx0 : mx1;
+            const double lo = 0.5 * (mn + mx) - 0.5 * L;
+            for (int j = 0; j < K; ++j) {
+                const double U = j == 0 ? 0.0 : (j == K - 1 ? 1.0 : E.cheb[cheb_u(M, D) + j - 1]);
+                const double X = (lo + U * L - mom[a]) / sigma;
+                tr[TR_HDR + a * K + j] = X;
+                tr[TR_HDR + (6 + a) * K + j] = X;
+                tr[TR_HDR + (2 + a) * K + j] = sigma / L;
+                tr[TR_HDR + (4 + a) * K + j] = L / sigma;
+            }
+            if (a == 0) { tr[5] = r0 >= r1 ? 0.0 : 1.0; tr[6] = L; }
+        }
+        if (tid == 0) {
+            tr[0] = mom[0]; tr[1] = mom[1]; tr[2] = sigma; tr[3] = sig[1]; tr[4] = K;
+        }
+        __syncthreads();
+        for (int i = tid; i < TR_HDR + 4 * K; i += SEL_NT) E.trf[i] = (float)tr[i];
+        if (E.cdf_out) {
+            for (int i = tid; i < 3; i += SEL_NT) E.cdf_out[i] = tr[i];
+            for (int i = tid; i < 4 * K; i += SEL_NT) E.cdf_out[3 + i] = tr[TR_HDR + i];
+        }
+        if (tid == 0 && flag_sh) atomicOr(E.flags, flag_sh);
+        return;
+    }
     // App. C iii: Chebyshev coefficients of the QF from M = D+1 nodes by the
     // discrete orthogonality of T_k on the nodes: c = C Q (one thread per coefficient)
     const double* Ct = E.cheb + cheb_C(M, D);
@@ -272,7 +314,6 @@ __global__ void __launch_bounds__(SEL_NT) k_select_fit(const __grid_constant__ B
     }
     __syncthreads();
     // App. C iv: knots p(0), p(u_j), p(1) and p'(u) there (one thread per point)
-    double* tr = E.trd;
     __shared__ double Xs[2][MAXM + 2], Ps[2][MAXM + 2];
     const double* Vt = E.cheb + cheb_V(M, D);
     const double* dVt = E.cheb + cheb_dV(M, D);

@@ -88,7 +88,16 @@ __global__ void __launch_bounds__(PSF_NT) k_psf_like(const __grid_constant__ Bat
 // log L = -1/2 sum r^2 - N log(sigma sqrt(2 pi)); chi^2_img = sum_mask r^2 / N_mask
 __global__ void __launch_bounds__(256) k_like_final(const __grid_constant__ Batch B) {
     const EvalArgs& E = B.e[blockIdx.x];
+    __shared__ int red_i[256 / 32];
+    int cnt = 0;
+    for (int t = threadIdx.x; t < E.n_cta_r; t += blockDim.x) cnt += E.cta_cnt[t];
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, o);
+    if ((threadIdx.x & 31) == 0) red_i[threadIdx.x >> 5] = cnt;
+    __syncthreads();
     if (threadIdx.x == 0 && E.stats) {
+        int tot = 0;
+        for (int w = 0; w < 256 / 32; ++w) tot += red_i[w];
+        E.stats[4] = tot;
         double s = 0.0, sm = 0.0;
         for (int t = 0; t < E.n_cta_p; ++t) { s += E.lpart[2 * t]; sm += E.lpart[2 * t + 1]; }
         const double npx = (double)E.n_img * E.n_img;

@@ -229,22 +229,36 @@ __global__ void __launch_bounds__(CTA_R) k_render(const __grid_constant__ Batch 
     __shared__ __align__(8) uint64_t mbar;
     const int n = E.n_src, K = E.n_nodes + 2;
     render_setup<T>(E, sh);
+    __shared__ int cnt_sh;
+    if (threadIdx.x == 0) cnt_sh = 0;
     if (!stage_to_smem(sgrid, E.src, (uint32_t)(n * n * sizeof(T)), &mbar, E.flags)) return;
     const int npix = E.n_img * E.n_img;
     const int pixel = tile * CTA_R + threadIdx.x;
-    if (pixel >= npix) return;
+    const bool valid = pixel < npix;
+    int nin = 0;                 // in-grid (or deferred) sub-rays of this pixel
     const T mux = sh.trs[0], muy = sh.trs[1], isg = T(1) / sh.trs[2];
     const T* Xx = sh.trs + TR_HDR;
     const T* Xy = Xx + K;
     const T* dx_ = Xx + 2 * K;
     const T* dy_ = Xx + 3 * K;
-    const int s = E.s, s2 = s * s;
-    const int pi = pixel % E.n_img, pj = pixel / E.n_img;
-    const T cx = (T)((pi - 0.5 * (E.n_img - 1)) * E.pix), cy = (T)((pj - 0.5 * (E.n_img - 1)) * E.pix);
+    // z range whose image under the CDF reaches within the near-edge margin of
+    // [0, 1] (the CDF is linear beyond its end knots with slopes d_0, d_{K-1})
+    T zlo[2], zhi[2];
+    for (int a = 0; a < 2; ++a) {
+        const T* X = Xx + a * K;
+        const T* d = dx_ + a * K;
+        const T m = T(4) * T(EDGE_DELTA) / T(n - 1);
+        zlo[a] = X[0] - m / d[0];
+        zhi[a] = X[K - 1] + m / d[K - 1];
+    }
+    const int s = E.s, s2 = valid ? E.s * E.s : 0;
+    const int pj = pixel / E.n_img, pi = pixel - pj * E.n_img;
+    const T pixT = (T)E.pix, cT = (T)(0.5 * (E.n_img - 1) * E.pix);
+    const T cx = T(pi) * pixT - cT, cy = T(pj) * pixT - cT;
     T acc = T(0);
     unsigned long long deferred = 0ull;      // bit q: sub-ray q went to the double pass
     for (int q = 0; q < s2; ++q) {
-        const int qa = q % s, qb = q / s;
+        const int qb = q / s, qa = q - qb * s;
         const T x = cx + sh.offx[qa], y = cy + sh.offx[qb];
         T yx, yy;
         if (sizeof(T) == 4 && lens_near_core(sh.K, x, y)) {
@@ -261,6 +275,7 @@ __global__ void __launch_bounds__(CTA_R) k_render(const __grid_constant__ Batch 
                 if (cell >= 0) {
                     acc += bilinear_at<T, T>(sgrid, n, i0, j0, (T)fxd, (T)fyd);
                     atomicAdd(E.ccount + cell, 1);
+                    ++nin;
                 }
                 E.cell[(size_t)pixel * s2 + q] = cell;
                 continue;
@@ -269,6 +284,11 @@ __global__ void __launch_bounds__(CTA_R) k_render(const __grid_constant__ Batch 
             T bx, by;
             lens_beta(sh.K, x, y, bx, by);
             const T zx = (bx - mux) * isg, zy = (by - muy) * isg;
+            if (zx < zlo[0] || zx > zhi[0] || zy < zlo[1] || zy > zhi[1]) {
+                // far outside the grid (beyond the near-edge margin): no cell, zero source
+                E.cell[(size_t)pixel * s2 + q] = -1;
+                continue;
+            }
             yx = cdf_value<T>(Xx, sh.U, dx_, K, cdf_interval<T>(Xx, K, zx), zx);
             yy = cdf_value<T>(Xy, sh.U, dy_, K, cdf_interval<T>(Xy, K, zy), zy);
             if (sizeof(T) == 4 && near_edge((float)(yx * T(n - 1)), (float)(yy * T(n - 1)), n)) {
@@ -276,6 +296,7 @@ __global__ void __launch_bounds__(CTA_R) k_render(const __grid_constant__ Batch 
                 reinterpret_cast<int*>(E.rec)[at] = pixel * s2 + q;
                 E.cell[(size_t)pixel * s2 + q] = -1;
                 deferred |= 1ull << q;
+                ++nin;               // may turn out in-grid: the compaction checks the cell
                 continue;
             }
         }
@@ -285,9 +306,16 @@ __global__ void __launch_bounds__(CTA_R) k_render(const __grid_constant__ Batch 
         if (cell >= 0) {
             acc += bilinear_at<T, T>(sgrid, n, i0, j0, fx, fy);
             atomicAdd(E.ccount + cell, 1);
+            ++nin;
         }
         E.cell[(size_t)pixel * s2 + q] = cell;
     }
+    // in-grid rays of the CTA (deferred rays counted; k_render_edge takes back the
+    // ones that end outside), for the compaction of the adjoint's rays
+    atomicAdd(&cnt_sh, nin);
+    __syncthreads();
+    if (threadIdx.x == 0) E.cta_cnt[tile] = cnt_sh;
+    if (!valid) return;
     if (sizeof(T) == 4) E.pdef[pixel] = deferred;
     // pixels with deferred rays keep the partial sum; k_render_fix completes them
     const T val = deferred ? acc : acc / T(s2);
@@ -324,6 +352,8 @@ __global__ void __launch_bounds__(EDGE_NT) k_render_edge(const __grid_constant__
         if (cell >= 0) {
             v = bilinear_at<float, float>(grid, n, i0, j0, (float)fx, (float)fy);
             atomicAdd(E.ccount + cell, 1);
+        } else {
+            atomicSub(E.cta_cnt + pixel / CTA_R, 1);
         }
         E.cell[ray] = cell;
         E.rval[ray] = v;
@@ -352,6 +382,37 @@ __global__ void __launch_bounds__(256) k_render_fix(const __grid_constant__ Batc
 
 // exclusive scan of the per-cell ray counts into offsets; cursors zeroed
 constexpr int SCAN_NT = 1024;
+
+// in-place exclusive scan of a[0..n) by one CTA of SCAN_NT threads, total in a[n]
+__device__ __forceinline__ void block_exclusive_scan(int* a, int n, int* wtot) {
+    const int tid = threadIdx.x;
+    const int per = (n + SCAN_NT - 1) / SCAN_NT;
+    int own = 0;
+    for (int i = 0; i < per; ++i) {
+        const int c = tid * per + i;
+        if (c < n) own += a[c];
+    }
+    int incl = own;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if ((tid & 31) >= o) incl += y;
+    }
+    __syncthreads();
+    if ((tid & 31) == 31) wtot[tid >> 5] = incl;
+    __syncthreads();
+    if (tid == 0) {
+        int acc = 0;
+        for (int w = 0; w < SCAN_NT / 32; ++w) { const int t = wtot[w]; wtot[w] = acc; acc += t; }
+    }
+    __syncthreads();
+    int base = wtot[tid >> 5] + incl - own;
+    for (int i = 0; i < per; ++i) {
+        const int c = tid * per + i;
+        if (c < n) { const int v = a[c]; a[c] = base; base += v; }
+    }
+    if (tid == SCAN_NT - 1) a[n] = base;
+    __syncthreads();
+}
 __global__ void __launch_bounds__(SCAN_NT) k_scan_cells(const __grid_constant__ Batch B) {
     const EvalArgs& E = B.e[blockIdx.x];
     const int nc = (E.n_src - 1) * (E.n_src - 1);
@@ -382,16 +443,63 @@ __global__ void __launch_bounds__(SCAN_NT) k_scan_cells(const __grid_constant__ 
         if (c < nc) { off[c] = base; base += E.ccount[c]; E.cursor[c] = 0; }
     }
     if (tid == SCAN_NT - 1) off[nc] = base;
+    // exclusive scan of the per-render-CTA in-grid counts
+    __syncthreads();
+    block_exclusive_scan(E.cta_cnt, E.n_cta_r, wtot);
 }
 
-// S9 (image -> source/transform/lens part).  One thread per pixel; each ray is
-// recomputed (value + the EPL series sums) and differentiated analytically;
-// the cell comes from the forward pass.  Writes one counting-sorted record per
-// in-grid ray and fixed-order per-CTA partial sums of the lens, standardisation
-// and spline-knot gradients.
+// compaction of the in-grid rays in ray order: one CTA per render tile; the
+// tile's rays are taken CTA_R at a time (coalesced loads), ranked by a ballot
+// scan and appended in order
+__global__ void __launch_bounds__(CTA_R) k_compact(const __grid_constant__ Batch B) {
+    const int ev = find_eval(B, blockIdx.x);
+    const EvalArgs& E = B.e[ev];
+    const int tile = blockIdx.x - B.tile0[ev];
+    const int npix = E.n_img * E.n_img, s2 = E.s * E.s;
+    const int ncell = (E.n_src - 1) * (E.n_src - 1);
+    const int* off = E.ccount + ncell;
+    const int r0 = tile * CTA_R * s2;
+    const int r1 = min(npix, (tile + 1) * CTA_R) * s2;
+    __shared__ int wcnt[CTA_R / 32];
+    __shared__ int run;
+    if (threadIdx.x == 0) run = E.cta_cnt[tile];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int base = r0; base < r1; base += CTA_R) {
+        const int ray = base + threadIdx.x;
+        const int c = ray < r1 ? E.cell[ray] : -1;
+        const bool in = c >= 0;
+        const unsigned m = __ballot_sync(0xffffffffu, in);
+        if (lane == 0) wcnt[wid] = __popc(m);
+        __syncthreads();
+        int pos = run;
+        for (int w = 0; w < wid; ++w) pos += wcnt[w];
+        pos += __popc(m & ((1u << lane) - 1u));
+        if (in) {
+            E.ids[pos] = ray;
+            E.kcell[pos] = c;
+            // the ray's record slot in the counting sort by cell (integer cursor)
+            E.kslot[pos] = c < ncell ? off[c] + atomicAdd(E.cursor + c, 1) : -1;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int t = 0;
+            for (int w = 0; w < CTA_R / 32; ++w) t += wcnt[w];
+            run += t;
+        }
+        __syncthreads();
+    }
+}
+
+// S9 (image -> source/transform/lens part) over the compacted in-grid rays (ray
+// order): a grid-stride loop gives every CTA a fixed set of chunks, each thread
+// ADJ_RPT consecutive rays per chunk.  Each ray is recomputed (value + the EPL
+// series sums) and differentiated analytically; its cell comes from the forward
+// pass.  Writes one counting-sorted record per ray and fixed-order per-CTA
+// partial sums of the lens, standardisation and spline-knot gradients.
 template <typename T>
-__global__ void __launch_bounds__(CTA_R) k_render_adj(const __grid_constant__ Batch B) {
+__global__ void __launch_bounds__(CTA_R, 4) k_render_adj(const __grid_constant__ Batch B) {
     typedef typename real4_of<T>::type R4;
+    typedef typename real2_of<T>::type R2;
     const int ev = find_eval(B, blockIdx.x);
     const EvalArgs& E = B.e[ev];
     const int tile = blockIdx.x - B.tile0[ev];
@@ -399,55 +507,55 @@ __global__ void __launch_bounds__(CTA_R) k_render_adj(const __grid_constant__ Ba
     extern __shared__ __align__(128) unsigned char smem_raw[];
     T* sgrid = reinterpret_cast<T*>(smem_raw);
     const size_t gbytes = ((size_t)n * n * sizeof(T) + 127) & ~(size_t)127;
-    double* tab = reinterpret_cast<double*>(smem_raw + gbytes);           // [NW][2 axes][2][K]
+    // per-warp spline-knot tables [NW][2 axes][2][K]: (hi, lo) pairs of T
+    typedef typename real2_of<T>::type TP;
+    TP* tab = reinterpret_cast<TP*>(smem_raw + gbytes);
     constexpr int NW = CTA_R / 32;
-    T* gbs = reinterpret_cast<T*>(tab + NW * 4 * K);                      // [CTA_R][s2][2]
     __shared__ RenderShared<T> sh;
-    __shared__ double wacc[NW][NACC_FIX];
-    __shared__ double wsub[NW][5];
+    __shared__ TP wacc[NW][NACC_FIX];
     __shared__ __align__(8) uint64_t mbar;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     render_setup<T>(E, sh);
-    for (int i = threadIdx.x; i < NW * 4 * K; i += blockDim.x) tab[i] = 0.0;
+    for (int i = threadIdx.x; i < NW * 4 * K; i += blockDim.x) { tab[i].x = T(0); tab[i].y = T(0); }
     const bool staged = stage_to_smem(sgrid, E.src, (uint32_t)(n * n * sizeof(T)), &mbar, E.flags);
     const int nacc = NACC_FIX + 4 * K + 5 * (E.sub_kind ? E.n_sub : 0);
     double* out = E.apart + (size_t)tile * nacc;
     if (!staged) {
-        for (int i = threadIdx.x; i < nacc; i += blockDim.x) out[i] = 0.0;
+        for (int i = threadIdx.x; i < NACC_FIX + 4 * K; i += blockDim.x) out[i] = 0.0;
         return;
     }
-    const int npix = E.n_img * E.n_img;
-    const int pixel = tile * CTA_R + threadIdx.x;
-    const bool valid = pixel < npix;
     const int s = E.s, s2 = s * s;
     const int nsub = sh.K.nsub;
-    const T mux = sh.trs[0], muy = sh.trs[1], sg = sh.trs[2], isg = T(1) / sg;
+    const int total = E.cta_cnt[E.n_cta_r];
+    const T mux = sh.trs[0], muy = sh.trs[1], isg = T(1) / sh.trs[2];
     const T* Xa[2] = {sh.trs + TR_HDR, sh.trs + TR_HDR + K};
     const T* Da[2] = {sh.trs + TR_HDR + 2 * K, sh.trs + TR_HDR + 3 * K};
     const T nm1 = T(n - 1);
-    const T gpix = valid ? reinterpret_cast<const T*>(E.gimg)[pixel] / T(s2) : T(0);
     const int* off = E.ccount + nc * nc;
     R4* rec = reinterpret_cast<R4*>(E.rec);
-    const int pi = valid ? pixel % E.n_img : 0, pj = valid ? pixel / E.n_img : 0;
-    const T cx = (T)((pi - 0.5 * (E.n_img - 1)) * E.pix), cy = (T)((pj - 0.5 * (E.n_img - 1)) * E.pix);
+    R2* gbuf = reinterpret_cast<R2*>(E.gbuf);
+    const T* gimg = reinterpret_cast<const T*>(E.gimg);
+    // pixel centre x = i pix - c, c = (n_img - 1)/2 pix, in the kernel's type
+    const T pixT = (T)E.pix, cT = (T)(0.5 * (E.n_img - 1) * E.pix);
+    const T inv_s2 = T(1) / T(s2);
 
     T acc[NACC_FIX];
 #pragma unroll
     for (int i = 0; i < NACC_FIX; ++i) acc[i] = T(0);
     int cj[2] = {-2, -2};
     T ca[2][4] = {{T(0), T(0), T(0), T(0)}, {T(0), T(0), T(0), T(0)}};
-    double* mytab = tab + wid * 4 * K;
+    TP* mytab = tab + wid * 4 * K;
 
     auto flush = [&](int a, bool need) {
         unsigned m = __ballot_sync(0xffffffffu, need);
         while (m) {
             const int l = __ffs(m) - 1;
             if (lane == l) {
-                double* tX = mytab + a * K;
-                double* tD = mytab + 2 * K + a * K;
+                TP* tX = mytab + a * K;
+                TP* tD = mytab + 2 * K + a * K;
                 const int j = cj[a];
-                if (j >= 0) { tX[j] += (double)ca[a][0]; tD[j] += (double)ca[a][2]; }
-                if (j + 1 <= K - 1) { tX[j + 1] += (double)ca[a][1]; tD[j + 1] += (double)ca[a][3]; }
+                if (j >= 0) { pair_add(tX[j], ca[a][0]); pair_add(tD[j], ca[a][2]); }
+                if (j + 1 <= K - 1) { pair_add(tX[j + 1], ca[a][1]); pair_add(tD[j + 1], ca[a][3]); }
             }
             __syncwarp();
             m &= m - 1;
@@ -455,108 +563,152 @@ __global__ void __launch_bounds__(CTA_R) k_render_adj(const __grid_constant__ Ba
         if (need) { ca[a][0] = ca[a][1] = ca[a][2] = ca[a][3] = T(0); }
     };
 
-    for (int q = 0; q < s2; ++q) {
-        int cell = -1;
-        T gb0 = T(0), gb1 = T(0);
-        int jn[2] = {cj[0], cj[1]};
-        T pn[2][4];
-        bool have = false;
-        const T x = cx + sh.offx[q % s], y = cy + sh.offx[q / s];
-        if (valid) {
-            cell = E.cell[(size_t)pixel * s2 + q];
-            if (cell >= nc * nc) cell = -1;     // only a forward pass on this slot writes cells
-        }
-        if (cell >= 0) {
-            const bool near = sizeof(T) == 4 && lens_near_core(sh.K, x, y);
-            EplJ<T> J;
-            EplJ<double> Jd;
-            double xd = 0.0, yd = 0.0;
-            T bx, by;
-            if (near) {
-                ray_pos(E.n_img, E.pix, s, pixel, q, xd, yd);
-                double bxd, byd;
-                lens_beta_eval(sh.Kd, xd, yd, Jd, bxd, byd);
-                bx = (T)bxd;
-                by = (T)byd;
-            } else {
-                lens_beta_eval(sh.K, x, y, J, bx, by);
+    const int chunk = CTA_R * ADJ_RPT;
+    for (int base = tile * chunk; base < total; base += E.n_cta_adj * chunk) {
+        for (int r = 0; r < ADJ_RPT; ++r) {
+            const int k = base + threadIdx.x * ADJ_RPT + r;
+            int jn[2] = {cj[0], cj[1]};
+            T pn[2][4];
+            bool have = false;
+            int cell = -1, ray = 0;
+            int slot = -1;
+            if (k < total) {
+                ray = E.ids[k];
+                cell = E.kcell[k];
+                slot = E.kslot[k];
+                if (cell >= nc * nc) cell = -1;      // only a forward pass on this slot writes cells
             }
-            const T z[2] = {(bx - mux) * isg, (by - muy) * isg};
-            T yv[2], dz[2];
-            for (int a = 0; a < 2; ++a) {
-                jn[a] = cdf_interval<T>(Xa[a], K, z[a]);
-                yv[a] = cdf_grad<T>(Xa[a], sh.U, Da[a], K, jn[a], z[a], dz[a], pn[a][0], pn[a][1], pn[a][2],
-                                    pn[a][3]);
-            }
-            const int i0 = cell % nc, j0 = cell / nc;
-            const T fx = yv[0] * nm1 - T(i0), fy = yv[1] * nm1 - T(j0);
-            const T* r0 = sgrid + j0 * n + i0;
-            const T dsdx = nm1 * ((T(1) - fy) * (r0[1] - r0[0]) + fy * (r0[n + 1] - r0[n]));
-            const T dsdy = nm1 * ((T(1) - fx) * (r0[n] - r0[0]) + fx * (r0[n + 1] - r0[1]));
-            const T gy[2] = {gpix * dsdx, gpix * dsdy};
-            const T gz0 = gy[0] * dz[0], gz1 = gy[1] * dz[1];
-            gb0 = gz0 * isg;
-            gb1 = gz1 * isg;
-            acc[8] -= gb0;
-            acc[9] -= gb1;
-            acc[10] -= (gz0 * z[0] + gz1 * z[1]) * isg;
-            if (near) {
-                double o8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-                lens_beta_vjp(sh.Kd, Jd, xd, yd, (double)gb0, (double)gb1, o8);
+            T gb0 = T(0), gb1 = T(0);
+            if (cell >= 0) {
+                const int pixel = ray / s2, q = ray - pixel * s2;
+                const int pj = pixel / E.n_img, pi = pixel - pj * E.n_img;
+                const int qb = q / s, qa = q - qb * s;
+                const T x = (T(pi) * pixT - cT) + sh.offx[qa];
+                const T y = (T(pj) * pixT - cT) + sh.offx[qb];
+                const T gpix = gimg[pixel] * inv_s2;
+                const bool near = sizeof(T) == 4 && lens_near_core(sh.K, x, y);
+                EplJ<T> J;
+                EplJ<double> Jd;
+                double xd = 0.0, yd = 0.0;
+                T bx, by;
+                if (near) {
+                    ray_pos(E.n_img, E.pix, s, pixel, q, xd, yd);
+                    double bxd, byd;
+                    lens_beta_eval(sh.Kd, xd, yd, Jd, bxd, byd);
+                    bx = (T)bxd;
+                    by = (T)byd;
+                } else {
+                    lens_beta_eval(sh.K, x, y, J, bx, by);
+                }
+                const T z[2] = {(bx - mux) * isg, (by - muy) * isg};
+                T yv[2], dz[2];
+                for (int a = 0; a < 2; ++a) {
+                    jn[a] = cdf_interval<T>(Xa[a], K, z[a]);
+                    yv[a] = cdf_grad<T>(Xa[a], sh.U, Da[a], K, jn[a], z[a], dz[a], pn[a][0], pn[a][1], pn[a][2],
+                                        pn[a][3]);
+                }
+                const int i0 = cell % nc, j0 = cell / nc;
+                const T fx = yv[0] * nm1 - T(i0), fy = yv[1] * nm1 - T(j0);
+                const T* r0 = sgrid + j0 * n + i0;
+                const T dsdx = nm1 * ((T(1) - fy) * (r0[1] - r0[0]) + fy * (r0[n + 1] - r0[n]));
+                const T dsdy = nm1 * ((T(1) - fx) * (r0[n] - r0[0]) + fx * (r0[n + 1] - r0[1]));
+                const T gy[2] = {gpix * dsdx, gpix * dsdy};
+                const T gz0 = gy[0] * dz[0], gz1 = gy[1] * dz[1];
+                gb0 = gz0 * isg;
+                gb1 = gz1 * isg;
+                acc[8] -= gb0;
+                acc[9] -= gb1;
+                acc[10] -= (gz0 * z[0] + gz1 * z[1]) * isg;
+                if (near) {
+                    double o8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+                    lens_beta_vjp(sh.Kd, Jd, xd, yd, (double)gb0, (double)gb1, o8);
 #pragma unroll
-                for (int p = 0; p < 8; ++p) acc[p] += (T)o8[p];
-            } else {
-                lens_beta_vjp(sh.K, J, x, y, gb0, gb1, acc);
+                    for (int p = 0; p < 8; ++p) acc[p] += (T)o8[p];
+                } else {
+                    lens_beta_vjp(sh.K, J, x, y, gb0, gb1, acc);
+                }
+                for (int a = 0; a < 2; ++a)
+                    for (int c = 0; c < 4; ++c) pn[a][c] *= gy[a];
+                have = true;
+                if (slot >= 0 && slot < off[cell + 1] && slot < E.n_img * E.n_img * s2) {
+                    R4 rr;
+                    rr.x = fx; rr.y = fy; rr.z = gpix; rr.w = T(0);
+                    rec[slot] = rr;
+                }
             }
-            for (int a = 0; a < 2; ++a)
-                for (int c = 0; c < 4; ++c) pn[a][c] *= gy[a];
-            have = true;
-            const int slot = off[cell] + atomicAdd(E.cursor + cell, 1);
-            if (slot >= 0 && slot < off[cell + 1] && slot < npix * s2) {
-                R4 r;
-                r.x = fx; r.y = fy; r.z = gpix; r.w = T(0);
-                rec[slot] = r;
+            if (nsub && k < total) {
+                R2 g;
+                g.x = gb0; g.y = gb1;
+                gbuf[k] = g;
             }
-        }
-        for (int a = 0; a < 2; ++a) {
-            const bool need = have && jn[a] != cj[a] && cj[a] != -2;
-            flush(a, need);
-            if (have) {
-                cj[a] = jn[a];
-                for (int c = 0; c < 4; ++c) ca[a][c] += pn[a][c];
+            for (int a = 0; a < 2; ++a) {
+                const bool need = have && jn[a] != cj[a] && cj[a] != -2;
+                flush(a, need);
+                if (have) {
+                    cj[a] = jn[a];
+                    for (int c = 0; c < 4; ++c) ca[a][c] += pn[a][c];
+                }
             }
-        }
-        if (nsub) {
-            gbs[(threadIdx.x * s2 + q) * 2] = gb0;
-            gbs[(threadIdx.x * s2 + q) * 2 + 1] = gb1;
         }
     }
     for (int a = 0; a < 2; ++a) flush(a, cj[a] != -2);
     // fixed-order reductions: warp tree -> per-warp slots -> warps in order
 #pragma unroll
     for (int i = 0; i < NACC_FIX; ++i) {
-        const double v = warp_sum(acc[i]);
+        const TP v = warp_pair_sum(acc[i]);
         if (lane == 0) wacc[wid][i] = v;
     }
     __syncthreads();
     for (int i = threadIdx.x; i < NACC_FIX + 4 * K; i += blockDim.x) {
-        double r = 0.0;
+        TP r;
+        r.x = T(0); r.y = T(0);
         if (i < NACC_FIX) {
-            for (int w = 0; w < NW; ++w) r += wacc[w][i];
+            for (int w = 0; w < NW; ++w) pair_add(r, wacc[w][i]);
         } else {
-            const int k = i - NACC_FIX;     // [0, 2K) knots X (axis-major), [2K, 4K) slopes d
-            for (int w = 0; w < NW; ++w) r += tab[w * 4 * K + k];
+            const int kk = i - NACC_FIX;    // [0, 2K) knots X (axis-major), [2K, 4K) slopes d
+            for (int w = 0; w < NW; ++w) pair_add(r, tab[w * 4 * K + kk]);
         }
-        out[i] = r;
+        out[i] = (double)r.x + (double)r.y;
     }
-    // subhalo parameters: one pass per subhalo over the stored d logL / d beta
-    for (int h = 0; h < nsub; ++h) {
+}
+
+// subhalo parameters: d logL / d(kappa_s, r_s, tau, x_s, y_s) over the compacted rays
+// with the stored d logL / d beta, same CTA tiling (and partial rows) as k_render_adj
+template <typename T>
+__global__ void __launch_bounds__(CTA_R) k_sub_adj(const __grid_constant__ Batch B) {
+    typedef typename real2_of<T>::type R2;
+    const int ev = find_eval(B, blockIdx.x);
+    const EvalArgs& E = B.e[ev];
+    const int tile = blockIdx.x - B.tile0[ev];
+    __shared__ LensK<T> K;
+    __shared__ T offx[8];
+    __shared__ double wsub[CTA_R / 32][5];
+    load_lensk(K, lensk_src<T>(E.lensk));
+    if (threadIdx.x < E.s) offx[threadIdx.x] = (T)(((threadIdx.x + 0.5) / E.s - 0.5) * E.pix);
+    __syncthreads();
+    const int Kn = E.n_nodes + 2;
+    const int nacc = NACC_FIX + 4 * Kn + 5 * K.nsub;
+    double* out = E.apart + (size_t)tile * nacc;
+    const int total = E.cta_cnt[E.n_cta_r];
+    const int s = E.s, s2 = s * s;
+    const T pixT = (T)E.pix, cT = (T)(0.5 * (E.n_img - 1) * E.pix);
+    const R2* gbuf = reinterpret_cast<const R2*>(E.gbuf);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int chunk = CTA_R * ADJ_RPT;
+    for (int h = 0; h < K.nsub; ++h) {
         T a5[5] = {T(0), T(0), T(0), T(0), T(0)};
-        if (valid) {
-            for (int q = 0; q < s2; ++q) {
-                const T g0 = gbs[(threadIdx.x * s2 + q) * 2], g1 = gbs[(threadIdx.x * s2 + q) * 2 + 1];
-                if (g0 == T(0) && g1 == T(0)) continue;
-                sub_vjp<T>(sh.K, h, cx + sh.offx[q % s], cy + sh.offx[q / s], g0, g1, a5);
+        for (int base = tile * chunk; base < total; base += E.n_cta_adj * chunk) {
+            for (int r = 0; r < ADJ_RPT; ++r) {
+                const int k = base + threadIdx.x * ADJ_RPT + r;
+                if (k >= total) continue;
+                const R2 g = gbuf[k];
+                if (g.x == T(0) && g.y == T(0)) continue;
+                const int ray = E.ids[k];
+                const int pixel = ray / s2, q = ray - pixel * s2;
+                const int pj = pixel / E.n_img, pi = pixel - pj * E.n_img;
+                const T x = (T(pi) * pixT - cT) + offx[q % s];
+                const T y = (T(pj) * pixT - cT) + offx[q / s];
+                sub_vjp<T>(K, h, x, y, g.x, g.y, a5);
             }
         }
 #pragma unroll
@@ -567,8 +719,8 @@ __global__ void __launch_bounds__(CTA_R) k_render_adj(const __grid_constant__ Ba
         __syncthreads();
         if (threadIdx.x < 5) {
             double r = 0.0;
-            for (int w = 0; w < NW; ++w) r += wsub[w][threadIdx.x];
-            out[NACC_FIX + 4 * K + 5 * h + threadIdx.x] = r;
+            for (int w = 0; w < CTA_R / 32; ++w) r += wsub[w][threadIdx.x];
+            out[NACC_FIX + 4 * Kn + 5 * h + threadIdx.x] = r;
         }
         __syncthreads();
     }
@@ -602,9 +754,10 @@ __global__ void __launch_bounds__(GATHER_NT) k_cell_gather(const __grid_constant
         l2 += (T(1) - fx) * gy1;
         l3 += fx * gy1;
     }
-    const double c0 = warp_sum(l0), c1 = warp_sum(l1), c2 = warp_sum(l2), c3 = warp_sum(l3);
+    typedef typename real2_of<T>::type TP;
+    const TP c0 = warp_pair_sum(l0), c1 = warp_pair_sum(l1), c2 = warp_pair_sum(l2), c3 = warp_pair_sum(l3);
     if (lane == 0) {
-        double* c = E.corner + (size_t)cell * 4;
+        TP* c = reinterpret_cast<TP*>(E.corner) + (size_t)cell * 4;
         c[0] = c0; c[1] = c1; c[2] = c2; c[3] = c3;
     }
 }

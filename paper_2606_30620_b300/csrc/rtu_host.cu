@@ -70,7 +70,7 @@ std::vector<int> digit_reversal(int n, const std::vector<int>& rad) {
 }
 
 struct Sizes {
-    int nm_max, n_cta_c_max, n_cta_r, n_cta_p, K, ncell, n_rays, nacc, nl, tb;
+    int nm_max, n_cta_c_max, n_cta_r, n_cta_p, K, ncell, n_rays, nacc, nl, tb, n_cta_adj;
     int nps, n_sites, n_state, n_phys, n_cta_upd;
 };
 
@@ -84,6 +84,8 @@ Sizes sizes_of(const rtu_system_desc& d) {
     z.K = d.n_nodes + 2;
     z.ncell = (d.n_src - 1) * (d.n_src - 1);
     z.n_rays = d.n_img * d.n_img * d.s_super * d.s_super;
+    // the adjoint's grid-stride CTAs: one chunk each when a sixteenth of the rays is in the grid
+    z.n_cta_adj = std::max(1, (z.n_rays + 16 * CTA_R * ADJ_RPT - 1) / (16 * CTA_R * ADJ_RPT));
     const int nsub = d.sub_kind ? d.n_sub : 0;
     z.nacc = NACC_FIX + 4 * z.K + 5 * nsub;
     z.nl = 8 + 5 * nsub;
@@ -126,13 +128,18 @@ size_t slot_layout(const rtu_system_desc& d, char* base, EvalArgs* e) {
     p = take((size_t)(2 * z.ncell + 1) * 4);          if (e) e->ccount = (int*)p;
     p = take((size_t)z.ncell * 4);                    if (e) e->cursor = (int*)p;
     p = take((size_t)z.n_rays * 4 * z.tb);            if (e) e->rec = p;
-    p = take((size_t)z.ncell * 4 * 8);                if (e) e->corner = (double*)p;
-    p = take((size_t)z.n_cta_r * z.nacc * 8);         if (e) e->apart = (double*)p;
+    p = take((size_t)z.ncell * 4 * 2 * z.tb);         if (e) e->corner = p;
+    p = take((size_t)std::max(z.n_cta_r, z.n_cta_adj) * z.nacc * 8); if (e) e->apart = (double*)p;
     p = take(16);                                     if (e) e->flags = (int*)p;
     p = take(LENSK_BYTES);                            if (e) e->lensk = p;
     p = take(16);                                     if (e) e->ecount = (int*)p;
     p = take(ni * 8);                                 if (e) e->pdef = (unsigned long long*)p;
     p = take((size_t)z.n_rays * 4);                   if (e) e->rval = (float*)p;
+    p = take((size_t)(z.n_cta_r + 1) * 4);            if (e) e->cta_cnt = (int*)p;
+    p = take((size_t)z.n_rays * 4);                   if (e) e->ids = (int*)p;
+    p = take((size_t)z.n_rays * 4);                   if (e) e->kcell = (int*)p;
+    p = take((size_t)z.n_rays * 4);                   if (e) e->kslot = (int*)p;
+    p = take((size_t)z.n_rays * 2 * z.tb);            if (e) e->gbuf = p;
     return o;
 }
 
@@ -148,7 +155,7 @@ size_t sample_layout(const rtu_system_desc& d, char* base, SampleBufs* b) {
     p = take((size_t)z.nl * 8);   if (b) b->lens = (double*)p;
     p = take((size_t)z.nps * 8);  if (b) b->ps = (double*)p;
     p = take(n2 * z.tb);          if (b) b->lat = p;
-    p = take(4 * 8);              if (b) b->stats = (double*)p;
+    p = take(8 * 8);              if (b) b->stats = (double*)p;
     p = take((size_t)z.nl * 8);   if (b) b->glens = (double*)p;
     p = take((size_t)z.nps * 8);  if (b) b->gps = (double*)p;
     p = take(n2 * z.tb);          if (b) b->glat = p;
@@ -234,6 +241,7 @@ const char* check_desc(const rtu_system_desc* d) {
     if (d->n_nodes != d->degree + 1) return "this build supports n_nodes == degree + 1 (interpolating fit)";
     if (d->n_nodes < 2 || d->n_nodes > MAXM) return "n_nodes must be in [2, 64]";
     if (d->n_slots < 1) return "n_slots must be >= 1";
+    if (d->transform != RTU_TRANSFORM_RTU && d->transform != RTU_TRANSFORM_UNIFORM) return "bad transform";
     if (!(d->pix > 0) || !(d->src_pitch > 0) || !(d->sigma > 0)) return "pix, src_pitch, sigma must be > 0";
     if (!d->data || !d->mask || !d->psf) return "data, mask and psf must be device pointers";
     return nullptr;
@@ -381,7 +389,9 @@ rtu_status fill_args(rtu_system* s, const rtu_eval& v, EvalArgs& e) {
     e.n_img = d.n_img; e.s = d.s_super; e.n_src = d.n_src; e.psf_k = d.psf_k;
     e.profile = d.profile; e.sub_kind = d.sub_kind; e.n_sub = d.n_sub; e.family = d.ps_family;
     e.n_nodes = d.n_nodes; e.degree = d.degree; e.n_mask = s->n_mask; e.f64 = d.precision == RTU_F64;
+    e.transform = d.transform;
     e.nrad = s->nrad; e.n_cta_c = s->n_cta_c; e.n_cta_r = s->z.n_cta_r; e.n_cta_p = s->z.n_cta_p;
+    e.n_cta_adj = s->z.n_cta_adj;
     for (int i = 0; i < MAX_RADIX; ++i) e.rad[i] = s->rad[i];
     e.pix = d.pix; e.pitch = d.src_pitch; e.sigma = d.sigma;
     e.data = d.data; e.mask = d.mask; e.psf = d.psf;
@@ -431,6 +441,7 @@ int t_one(const EvalArgs&) { return 1; }
 int t_zero(const EvalArgs&) { return ZERO_TILES; }
 int t_centre(const EvalArgs& e) { return e.n_cta_c; }
 int t_render(const EvalArgs& e) { return e.n_cta_r; }
+int t_adj(const EvalArgs& e) { return e.n_cta_adj; }
 int t_psf(const EvalArgs& e) { return e.n_cta_p; }
 int t_edge(const EvalArgs&) { return EDGE_CTAS; }
 int t_fix(const EvalArgs& e) { return (e.n_img * e.n_img + 255) / 256; }
@@ -472,10 +483,11 @@ rtu_status run_chunk(Batch& B, int phase, cudaStream_t st) {
     if (phase & PH_ADJOINT) {
         if ((r = launch("k_psf_adj", k_psf_adj<T>, B, t_psf, PSF_NT, 0, st))) return r;
         if ((r = launch("k_scan_cells", k_scan_cells, B, t_one, SCAN_NT, 0, st))) return r;
-        size_t adj = grid_bytes + (size_t)(CTA_R / 32) * 4 * maxK * 8 +
-                     (any_sub ? (size_t)CTA_R * max_s2 * 2 * sizeof(T) : 0);
+        const size_t adj = grid_bytes + (size_t)(CTA_R / 32) * 4 * maxK * 2 * sizeof(T);
         if (adj > MAX_DYN) return fail(RTU_E_ARG, "adjoint shared memory exceeds the limit");
-        if ((r = launch("k_render_adj", k_render_adj<T>, B, t_render, CTA_R, adj, st))) return r;
+        if ((r = launch("k_compact", k_compact, B, t_render, CTA_R, 0, st))) return r;
+        if ((r = launch("k_render_adj", k_render_adj<T>, B, t_adj, CTA_R, adj, st))) return r;
+        if (any_sub && (r = launch("k_sub_adj", k_sub_adj<T>, B, t_adj, CTA_R, 0, st))) return r;
         if ((r = launch("k_cell_gather", k_cell_gather<T>, B, t_cells, GATHER_NT, 0, st))) return r;
         if ((r = launch("k_cdf_adj", k_cdf_adj, B, t_one, CDF_NT, 0, st))) return r;
         if ((r = launch("k_centre_adj", k_centre_adj<T>, B, t_centre, CTA_C, 0, st))) return r;

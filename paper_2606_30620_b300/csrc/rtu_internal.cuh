@@ -19,6 +19,7 @@ constexpr int MAXM = 64;          // max Chebyshev nodes
 constexpr int MAX_RADIX = 12;     // max FFT stages
 constexpr int CTA_C = 256;        // centre-ray kernels: rays per CTA
 constexpr int CTA_R = 128;        // render kernels: pixels per CTA (one thread each)
+constexpr int ADJ_RPT = 4;        // render adjoint: compacted rays per thread per chunk
 constexpr int PSF_T = 32;         // PSF kernels: 32 x 32 output tile per CTA (4 outputs per thread)
 constexpr int NACC_FIX = 11;      // render-adjoint partials: 8 lens + mu_x, mu_y, sigma
 
@@ -31,6 +32,7 @@ struct EvalArgs {
     int profile, sub_kind, n_sub, family;
     int n_nodes, degree, n_mask, f64;
     int nrad, n_cta_c, n_cta_r, n_cta_p;
+    int transform, pad2_;
     int rad[MAX_RADIX];
     double pix, pitch, sigma, pad_;
     const void* data;
@@ -77,13 +79,19 @@ struct EvalArgs {
     int* ccount;       // [n_cells] ray counts, then [n_cells + 1] exclusive offsets
     int* cursor;       // [n_cells]
     void* rec;         // real4 [n_rays] counting-sorted (fx, fy, g, -) records
-    double* corner;    // [n_cells][4] per-cell bilinear corner sums
+    void* corner;      // real2 [n_cells][4] per-cell bilinear corner sums (float: hi + lo pairs)
     double* apart;     // [n_cta_r][nacc] render-adjoint partials
     int* flags;        // device flag word
     void* lensk;       // LensK<T> then LensK<double> of the evaluation
     int* ecount;       // number of deferred near-edge rays (float mode)
     unsigned long long* pdef;  // [n_img^2] bit q: sub-ray q deferred to the double pass (float mode)
     float* rval;       // [n_rays] values of deferred rays (float mode)
+    int* cta_cnt;      // [n_cta_r + 1] in-grid rays per render CTA, then exclusive offsets
+    int* ids;          // [n_rays] in-grid ray ids in ray order (compacted)
+    int* kcell;        // [n_rays] cell of each compacted ray
+    int* kslot;        // [n_rays] counting-sorted record slot of each compacted ray
+    void* gbuf;        // real2 [n_rays] d logL / d beta of each compacted ray (subhalo pass)
+    int n_cta_adj;     // CTAs of the render adjoint (grid-stride over the compacted rays)
 };
 
 struct Batch {
@@ -155,26 +163,81 @@ __device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) 
     const float bb = s - a;
     e = (a - (s - bb)) + (b - bb);
 }
-__device__ __forceinline__ double warp_sum(float v) {
-    float hi = v, lo = 0.0f;
+// compensated float pair (hi + lo) and its exact-error addition
+struct F2 { float hi, lo; };
+__device__ __forceinline__ F2 f2_add(F2 a, F2 b) {
+    float s, e;
+    two_sum_f(a.hi, b.hi, s, e);
+    return F2{s, a.lo + b.lo + e};
+}
+__device__ __forceinline__ F2 f2_add(F2 a, float b) {
+    float s, e;
+    two_sum_f(a.hi, b, s, e);
+    return F2{s, a.lo + e};
+}
+// the warp sum as a compensated pair (valid in lane 0); no FP64 arithmetic
+__device__ __forceinline__ F2 warp_sum2(float v) {
+    F2 a{v, 0.0f};
     for (int o = 16; o > 0; o >>= 1) {
-        const float h2 = __shfl_down_sync(0xffffffffu, hi, o);
-        const float l2 = __shfl_down_sync(0xffffffffu, lo, o);
-        float sum, err;
-        two_sum_f(hi, h2, sum, err);
-        hi = sum;
-        lo = lo + l2 + err;
+        const F2 b{__shfl_down_sync(0xffffffffu, a.hi, o), __shfl_down_sync(0xffffffffu, a.lo, o)};
+        a = f2_add(a, b);
     }
-    return (double)hi + (double)lo;
+    return a;
+}
+__device__ __forceinline__ double warp_sum(float v) {
+    const F2 a = warp_sum2(v);
+    return (double)a.hi + (double)a.lo;
 }
 __device__ __forceinline__ double warp_sum(double v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     return v;
 }
 
+// deterministic block reduction of one value per thread in its own type: a
+// (compensated, for float) warp tree, then warps in order in double
+template <int NT, typename T>
+__device__ __forceinline__ double block_sum_t(T v, double* sh) {
+    const double w = warp_sum(v);
+    const int wid = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) sh[wid] = w;
+    __syncthreads();
+    double r = 0.0;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < NT / 32; ++i) r += sh[i];
+        sh[0] = r;
+    }
+    __syncthreads();
+    r = sh[0];
+    __syncthreads();
+    return r;
+}
+
 template <typename T> struct real2_of;
 template <> struct real2_of<float> { typedef float2 type; };
 template <> struct real2_of<double> { typedef double2 type; };
+
+// running sums kept as (hi, lo) pairs of the kernel's type: compensated for
+// float (no FP64 instruction), plain (lo = 0) for double
+__device__ __forceinline__ void pair_add(float2& a, float b) {
+    float s, e;
+    two_sum_f(a.x, b, s, e);
+    a.x = s;
+    a.y += e;
+}
+__device__ __forceinline__ void pair_add(float2& a, float2 b) {
+    float s, e;
+    two_sum_f(a.x, b.x, s, e);
+    a.x = s;
+    a.y += b.y + e;
+}
+__device__ __forceinline__ void pair_add(double2& a, double b) { a.x += b; }
+__device__ __forceinline__ void pair_add(double2& a, double2 b) { a.x += b.x + b.y; }
+__device__ __forceinline__ float2 warp_pair_sum(float v) {
+    const F2 a = warp_sum2(v);
+    return make_float2(a.hi, a.lo);
+}
+__device__ __forceinline__ double2 warp_pair_sum(double v) { return make_double2(warp_sum(v), 0.0); }
 template <typename T> struct real4_of;
 template <> struct real4_of<float> { typedef float4 type; };
 template <> struct real4_of<double> { typedef double4_32a type; };

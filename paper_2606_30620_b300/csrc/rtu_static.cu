@@ -72,14 +72,15 @@ __global__ void __launch_bounds__(GP_NT) k_gp_source_static(int n, double pitch,
     __syncthreads();
     fft2<float>(W, n, rad_s, S, tw_s, rev_s, sm, chunk, false);
     const int nf = n_family(family);
-    double psv[4];
-    for (int q = 0; q < nf; ++q) psv[q] = ps[q];
+    float psv[4];
+    for (int q = 0; q < nf; ++q) psv[q] = (float)ps[q];
+    const float kscale = (float)(2.0 * 3.14159265358979323846 / pitch);
     for (int i = threadIdx.x; i < n2; i += blockDim.x) {
         const int ky = i / n, kx = i - ky * n;
-        const double fx = fftfreq(kx, n), fy = fftfreq(ky, n);
-        const double k = 2.0 * 3.14159265358979323846 * sqrt(fx * fx + fy * fy) / pitch;
-        double gdummy[3];
-        const float sp = (float)sqrtP_and_grad(family, psv, k, gdummy);
+        const float fx = (float)fftfreq(kx, n), fy = (float)fftfreq(ky, n);
+        const float k = kscale * sqrtf(fx * fx + fy * fy);
+        float gdummy[3];
+        const float sp = sqrtP_and_grad<float>(family, psv, k, gdummy);
         W[i] = Cx<float>{W[i].x * sp, W[i].y * sp};
     }
     __syncthreads();

@@ -22,9 +22,10 @@ RTU_F32, RTU_F64 = 0, 1
 RTU_SIE, RTU_EPL = 0, 1
 RTU_SUB_NONE, RTU_SUB_NFW, RTU_SUB_TNFW = 0, 1, 2
 RTU_PS_POWER_LAW, RTU_PS_MATERN_LIKE, RTU_PS_MATERN = 0, 1, 2
-STAT_LOGL, STAT_CHI2, STAT_NMASK, STAT_FLAGS = 0, 1, 2, 3
+RTU_TRANSFORM_RTU, RTU_TRANSFORM_UNIFORM = 0, 1
+STAT_LOGL, STAT_CHI2, STAT_NMASK, STAT_FLAGS, STAT_N_IN_GRID = 0, 1, 2, 3, 4
 W_NONMONOTONE, W_SELECT, W_TIMEOUT = 1, 2, 4
-N_STATS = 4
+N_STATS = 5
 N_PS = {RTU_PS_POWER_LAW: 2, RTU_PS_MATERN_LIKE: 2, RTU_PS_MATERN: 3}
 
 
@@ -41,7 +42,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 class SystemDesc(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int32) for n in (
         "n_img", "s_super", "n_src", "psf_k", "profile", "sub_kind", "n_sub", "ps_family",
-        "precision", "n_nodes", "degree", "n_slots")] + [
+        "precision", "n_nodes", "degree", "n_slots", "transform", "reserved_")] + [
         ("pix", ctypes.c_double), ("src_pitch", ctypes.c_double), ("sigma", ctypes.c_double),
         ("data", ctypes.c_void_p), ("mask", ctypes.c_void_p), ("psf", ctypes.c_void_p)]
 
@@ -132,7 +133,7 @@ class System:
 
     def __init__(self, data, mask, psf, sigma, pix, s_super, n_src, src_pitch, profile=RTU_SIE,
                  ps_family=RTU_PS_POWER_LAW, sub_kind=RTU_SUB_NONE, n_sub=0, precision=RTU_F32,
-                 n_nodes=22, degree=21, n_slots=1, device="cuda"):
+                 n_nodes=22, degree=21, n_slots=1, device="cuda", transform=RTU_TRANSFORM_RTU):
         self.dtype = torch.float64 if precision == RTU_F64 else torch.float32
         self.device = torch.device(device)
         self.data = torch.as_tensor(data, dtype=self.dtype, device=self.device).contiguous()
@@ -150,7 +151,8 @@ class System:
         self.n_nodes = int(n_nodes)
         self.desc = SystemDesc(self.n_img, self.s_super, self.n_src, int(self.psf.shape[0]), self.profile,
                                self.sub_kind, self.n_sub, self.ps_family, self.precision, int(n_nodes),
-                               int(degree), self.n_slots, float(pix), float(src_pitch), float(sigma),
+                               int(degree), self.n_slots, int(transform), 0, float(pix), float(src_pitch),
+                               float(sigma),
                                self.data.data_ptr(), self.mask.data_ptr(), self.psf.data_ptr())
         nbytes = _lib.rtu_workspace_size(ctypes.byref(self.desc))
         if nbytes == 0:
@@ -167,10 +169,10 @@ class System:
         self.n_knots = self.n_nodes + 2
 
     @classmethod
-    def from_mock(cls, m, precision=RTU_F32, n_slots=1, device="cuda"):
+    def from_mock(cls, m, precision=RTU_F32, n_slots=1, device="cuda", transform=RTU_TRANSFORM_RTU):
         return cls(m.data, m.mask, m.psf, m.sigma, m.pix, m.s_super, m.n_src, m.src_pitch, m.profile,
                    m.ps_family, m.sub_kind, 0 if m.subs is None else m.subs.shape[0], precision,
-                   n_slots=n_slots, device=device)
+                   n_slots=n_slots, device=device, transform=transform)
 
     @property
     def n_sites(self) -> int:

@@ -13,9 +13,9 @@ def rel_l2(a, b):
     return float(np.linalg.norm(a - b) / (den if den > 0 else 1.0))
 
 
-def run_gpu(m, precision, want_grads=True, n_slots=1):
+def run_gpu(m, precision, want_grads=True, n_slots=1, transform=0):
     from paper_2606_30620_b300 import rtu
-    sysm = rtu.System.from_mock(m, precision=precision, n_slots=n_slots)
+    sysm = rtu.System.from_mock(m, precision=precision, n_slots=n_slots, transform=transform)
     lens = m.lens if m.subs is None else np.concatenate([m.lens, m.subs.ravel()])
     b = rtu.Binding(sysm, lens, m.latents, m.ps, want_model=True, want_image=True, want_source=True,
                     want_cdf=True, want_hist=True, grads=want_grads)
@@ -32,8 +32,9 @@ def run_gpu(m, precision, want_grads=True, n_slots=1):
     return out, sysm, b
 
 
-def run_oracle(m, grads=True):
+def run_oracle(m, grads=True, transform=0):
     s = oracle_io.system(m)
+    s.transform = transform
     lens, lat, ps, subs = oracle_io.params(m)
     if grads:
         r = O.forward_adjoint(s, lens, lat, ps, subs)
@@ -43,8 +44,11 @@ def run_oracle(m, grads=True):
     T = O.build_grid(s, lens, subs)
     src, _ = O.gp_source(s, lat, ps)
     hist = O.ray_hist(s, lens, subs, T)
-    cdf = np.concatenate([T.mu.detach().numpy(), [float(T.sigma)], T.knots.detach().numpy().ravel(),
-                          T.slopes.detach().numpy().ravel()])
+    if isinstance(T, O.BoxTransform):
+        cdf = None          # the box map has no knots of its own to compare
+    else:
+        cdf = np.concatenate([T.mu.detach().numpy(), [float(T.sigma)], T.knots.detach().numpy().ravel(),
+                              T.slopes.detach().numpy().ravel()])
     out = dict(logL=float(r["logL"]), chi2=float(r["chi2"]), model=r["model"].detach().numpy(),
                image=r["image"].detach().numpy(), source=src.detach().numpy(), cdf=cdf,
                hist=hist.numpy(), flags=T.flags)
@@ -60,7 +64,7 @@ def compare(g, o):
     res = dict(
         logL=abs(g["stats"][0] - o["logL"]) / abs(o["logL"]),
         chi2=abs(g["stats"][1] - o["chi2"]) / abs(o["chi2"]),
-        cdf=rel_l2(g["cdf"], o["cdf"]),
+        cdf=rel_l2(g["cdf"], o["cdf"]) if o["cdf"] is not None else 0.0,
         source=rel_l2(g["source"], o["source"]),
         image=rel_l2(g["image"], o["image"]),
         model=rel_l2(g["model"], o["model"]),

@@ -56,7 +56,8 @@ int main(void) {
 def _desc(**kw):
     from paper_2606_30620_b300 import rtu
     d = dict(n_img=64, s_super=2, n_src=32, psf_k=9, profile=0, sub_kind=0, n_sub=0, ps_family=0,
-             precision=0, n_nodes=22, degree=21, n_slots=1, pix=0.05, src_pitch=0.1, sigma=0.02,
+             precision=0, n_nodes=22, degree=21, n_slots=1, transform=0, reserved_=0, pix=0.05,
+             src_pitch=0.1, sigma=0.02,
              data=1 << 20, mask=1 << 21, psf=1 << 22)
     d.update(kw)
     return rtu.SystemDesc(**d)
@@ -70,7 +71,7 @@ def test_workspace_size_validates_the_description():
     two = lib.rtu_workspace_size(ctypes.byref(_desc(n_slots=2)))
     assert two > ok
     for bad in (dict(n_src=50), dict(n_src=512), dict(psf_k=4), dict(n_nodes=30), dict(s_super=0),
-                dict(precision=3), dict(sigma=0.0), dict(n_sub=17), dict(data=0)):
+                dict(precision=3), dict(sigma=0.0), dict(n_sub=17), dict(data=0), dict(transform=2)):
         assert lib.rtu_workspace_size(ctypes.byref(_desc(**bad))) == 0, bad
 
 

@@ -422,3 +422,43 @@ def test_subhalo_gradient_matches_central_differences():
           - float(O.forward(s, lens, lat, ps, subs - h * v)["logL"])) / (2 * h)
     an = float((g["g_subs"] * v).sum())
     assert abs(fd - an) < 1e-5 * max(1.0, abs(an))
+
+
+# ------------------------------------------------------- uniform-grid baseline
+def test_uniform_box_is_the_smallest_square_around_the_masked_rays():
+    # Sec. 2.1: the grid spans the smallest square box containing every masked ray
+    m = I.config_c2(1040, n_img=64, s=2, n_src=32)
+    s = oracle_io.system(m)
+    s.transform = O.TRANSFORM_UNIFORM
+    lens, _, _, _ = oracle_io.params(m)
+    T = O.build_grid(s, lens)
+    xc, yc = O.pixel_centres(s.n_img, s.pix)
+    sel = s.mask.reshape(-1)
+    bx, by = O.trace(xc[sel], yc[sel], lens, s.profile)
+    yx, yy = O.rtu_map(bx, by, T)
+    lo = torch.stack([yx.min(), yy.min()])
+    hi = torch.stack([yx.max(), yy.max()])
+    assert float(lo.min()) >= -1e-12 and float(hi.max()) <= 1 + 1e-12
+    wide = int(torch.argmax(hi - lo))
+    assert abs(float(lo[wide])) < 1e-12 and abs(float(hi[wide]) - 1) < 1e-12     # tight on the wider axis
+    assert abs(float(0.5 * (lo[1 - wide] + hi[1 - wide])) - 0.5) < 1e-12           # centred on the other
+
+
+def test_uniform_grid_gradient_matches_central_differences():
+    m = I.config_tiny(seed=17)
+    s = oracle_io.system(m)
+    s.transform = O.TRANSFORM_UNIFORM
+    lens, lat, ps, _ = oracle_io.params(m)
+    g = O.forward_adjoint(s, lens, lat, ps)
+    rng = np.random.default_rng(17)
+    for which, key in ((0, "g_lens"), (1, "g_latents"), (2, "g_ps")):
+        base = [lens, lat, ps]
+        v = t(rng.standard_normal(base[which].shape))
+        h = 1e-7
+        p = [b.clone() for b in base]
+        q = [b.clone() for b in base]
+        p[which] = p[which] + h * v
+        q[which] = q[which] - h * v
+        fd = (float(O.forward(s, *p)["logL"]) - float(O.forward(s, *q)["logL"])) / (2 * h)
+        an = float((g[key] * v).sum())
+        assert abs(fd - an) < 1e-5 * max(1.0, abs(an)), (key, fd, an)
