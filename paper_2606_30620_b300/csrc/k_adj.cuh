@@ -8,46 +8,57 @@
 
 namespace rtu {
 
-// tadj layout: [0] dmu_x/N  [1] dmu_y/N  [2] dsigma/(N sigma)  [3] amin
+// tadj layout: [0] dmu_x/N  [1] dmu_y/N  [3] amin  [4], [5] the x and y parts of
+//              dsigma (their sum / (N sigma) multiplies beta - mu on the amin axis)
 //              [8 + a*2MAXM + t]  d logL / d beta of the ray selected at (axis a, target t)
 constexpr int TADJ_SEL = 8;
 
-constexpr int CDF_NT = 1024;
+// one warp: column sums over the render-adjoint CTAs, fixed lane stride and a
+// fixed shuffle tree (lane 0 returns the sum)
+__device__ __forceinline__ double apart_col(const EvalArgs& E, int nacc, int col) {
+    const int lane = threadIdx.x & 31;
+    double s = 0.0;
+    for (int t = lane; t < E.n_cta_adj; t += 32) s += E.apart[(size_t)t * nacc + col];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    return s;
+}
+
+// One CTA per (evaluation, axis); the uniform-grid transform couples the axes
+// (one box side) and is done by the axis-0 CTA alone.
+constexpr int CDF_NT = 256;
 __global__ void __launch_bounds__(CDF_NT) k_cdf_adj(const __grid_constant__ Batch B) {
-    const EvalArgs& E = B.e[blockIdx.x];
+    const int ev = find_eval(B, blockIdx.x);
+    const EvalArgs& E = B.e[ev];
+    const int ax = blockIdx.x - B.tile0[ev];
     const int M = E.n_nodes, D = E.degree, K = M + 2, N = E.n_mask;
     const int nacc = NACC_FIX + 4 * K + 5 * (E.sub_kind ? E.n_sub : 0);
-    const int ncol = NACC_FIX + 4 * K;
     __shared__ double tot[NACC_FIX + 4 * (MAXM + 2)];
-    __shared__ double gXr[2][MAXM + 2], gpr[2][MAXM + 2], gc[2][MAXM], gQ[2][MAXM];
+    __shared__ double gXr[MAXM + 2], gpr[MAXM + 2], gc[MAXM], gQ[MAXM];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    // column sums over the render-adjoint CTAs: one warp per column, fixed lane
-    // stride and a fixed shuffle tree
-    for (int col = wid; col < ncol; col += CDF_NT / 32) {
-        double s = 0.0;
-        for (int t = lane; t < E.n_cta_adj; t += 32) s += E.apart[(size_t)t * nacc + col];
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-        if (lane == 0) tot[col] = s;
-    }
-    __syncthreads();
     const double* tr = E.trd;
-    const double sigma = tr[2];
+    const double sigma = tr[2], isig = 1.0 / sigma;
     if (E.transform) {
+        if (ax != 0) return;
+        for (int col = wid; col < NACC_FIX + 4 * K; col += CDF_NT / 32) {
+            const double v = apart_col(E, nacc, col);
+            if (lane == 0) tot[col] = v;
+        }
+        __syncthreads();
         // uniform grid: X_j = (lo_a + U_j L - mu_a)/sigma, slopes sigma/L, with
         // lo_a = (min_a + max_a)/2 - L/2 and L the larger range (axis amax)
         if (threadIdx.x == 0) {
             const int amax = tr[5] > 0.5 ? 1 : 0;
-            const double L = tr[6];
+            const double L = tr[6], iL = 1.0 / L;
             double dmu[2] = {tot[8], tot[9]}, dsig = tot[10], dL = 0.0, dc[2] = {0.0, 0.0};
             for (int a = 0; a < 2; ++a) {
                 const double* X = tr + TR_HDR + a * K;
                 for (int j = 0; j < K; ++j) {
                     const double U = j == 0 ? 0.0 : (j == K - 1 ? 1.0 : E.cheb[cheb_u(M, D) + j - 1]);
                     const double gX = tot[NACC_FIX + a * K + j], gd = tot[NACC_FIX + 2 * K + a * K + j];
-                    dc[a] += gX / sigma;
-                    dL += gX * (U - 0.5) / sigma - gd * sigma / (L * L);
-                    dmu[a] -= gX / sigma;
-                    dsig += -gX * X[j] / sigma + gd / L;
+                    dc[a] += gX * isig;
+                    dL += gX * (U - 0.5) * isig - gd * sigma * iL * iL;
+                    dmu[a] -= gX * isig;
+                    dsig += -gX * X[j] * isig + gd * iL;
                 }
             }
             for (int a = 0; a < 2; ++a) {
@@ -59,76 +70,86 @@ __global__ void __launch_bounds__(CDF_NT) k_cdf_adj(const __grid_constant__ Batc
             }
             E.tadj[0] = dmu[0] / N;
             E.tadj[1] = dmu[1] / N;
-            E.tadj[2] = dsig / (N * sigma);
             E.tadj[3] = tr[3];
+            E.tadj[4] = dsig;
+            E.tadj[5] = 0.0;
         }
         return;
     }
-    // back through the guard (sequential in the knots; one thread per axis)
-    if (threadIdx.x < 2) {
-        const int a = threadIdx.x;
-        const double* Xf = tr + TR_HDR + a * K;          // guarded knots
-        const double* Xr = tr + TR_HDR + (6 + a) * K;    // raw knots
-        const double* pr = tr + TR_HDR + (4 + a) * K;    // raw p'
-        const double* sl = tr + TR_HDR + (2 + a) * K;    // slopes 1/p'
-        const double* gX = tot + NACC_FIX + a * K;
-        const double* gd = tot + NACC_FIX + 2 * K + a * K;
-        double span = Xr[K - 1] - Xr[0];
-        const bool span_ok = span > 0.0;
-        if (!span_ok) span = fabs(span) + 1e-300;
-        const double floor_d = 1e-6 * span;
+    // this axis's columns: dmu_a, dsigma (axis 0), knots X and slopes d
+    const int ncol = 2 + 2 * K;
+    for (int w = wid; w < ncol; w += CDF_NT / 32) {
+        const int col = w == 0 ? 8 + ax : (w == 1 ? 10 : (w < 2 + K ? NACC_FIX + ax * K + (w - 2)
+                                                                   : NACC_FIX + 2 * K + ax * K + (w - 2 - K)));
+        const double v = apart_col(E, nacc, col);
+        if (lane == 0) tot[col] = v;
+    }
+    __syncthreads();
+    const double* gX = tot + NACC_FIX + ax * K;
+    const double* gd = tot + NACC_FIX + 2 * K + ax * K;
+    const double* Xf = tr + TR_HDR + ax * K;          // guarded knots
+    const double* Xr = tr + TR_HDR + (6 + ax) * K;    // raw knots
+    const double* pr = tr + TR_HDR + (4 + ax) * K;    // raw p'
+    const double* sl = tr + TR_HDR + (2 + ax) * K;    // slopes 1/p'
+    double span = Xr[K - 1] - Xr[0];
+    const bool span_ok = span > 0.0;
+    if (!span_ok) span = fabs(span) + 1e-300;
+    const double floor_d = 1e-6 * span;
+    // back through the slope floor (per point) ...
+    for (int j = threadIdx.x; j < K; j += CDF_NT) {
+        const double gp = -gd[j] * sl[j] * sl[j];    // slope d = 1/p'
+        gpr[j] = pr[j] < floor_d ? 0.0 : gp;
+        gXr[j] = gX[j];
+    }
+    __syncthreads();
+    // ... and the knot floor (sequential in the knots; the floor's span terms)
+    if (threadIdx.x == 0) {
         double gfl = 0.0;
-        double gXf[MAXM + 2];
-        for (int j = 0; j < K; ++j) {
-            const double gp = -gd[j] * sl[j] * sl[j];        // slope d = 1/p'
-            if (pr[j] < floor_d) { gpr[a][j] = 0.0; gfl += gp; } else gpr[a][j] = gp;
-            gXf[j] = gX[j];
-        }
-        for (int j = K - 1; j >= 1; --j) {
-            if (Xf[j] != Xr[j]) { gXf[j - 1] += gXf[j]; gfl += gXf[j]; gXr[a][j] = 0.0; }
-            else gXr[a][j] = gXf[j];
-        }
-        gXr[a][0] = gXf[0];
-        if (span_ok) { gXr[a][K - 1] += 1e-6 * gfl; gXr[a][0] -= 1e-6 * gfl; }
+        for (int j = 0; j < K; ++j)
+            if (pr[j] < floor_d) gfl += -gd[j] * sl[j] * sl[j];
+        for (int j = K - 1; j >= 1; --j)
+            if (Xf[j] != Xr[j]) { gXr[j - 1] += gXr[j]; gfl += gXr[j]; gXr[j] = 0.0; }
+        if (span_ok) { gXr[K - 1] += 1e-6 * gfl; gXr[0] -= 1e-6 * gfl; }
     }
     __syncthreads();
     // knots X = V c and slopes p' = dV c  ->  gc = V^T gX + dV^T gp'
     const double* Vt = E.cheb + cheb_V(M, D);
     const double* dVt = E.cheb + cheb_dV(M, D);
-    for (int w = threadIdx.x; w < 2 * (D + 1); w += CDF_NT) {
-        const int a = w / (D + 1), k = w % (D + 1);
+    for (int k = threadIdx.x; k <= D; k += CDF_NT) {
         double g = 0.0;
-        for (int j = 0; j < K; ++j) g += Vt[j * (D + 1) + k] * gXr[a][j] + dVt[j * (D + 1) + k] * gpr[a][j];
-        gc[a][k] = g;
+        for (int j = 0; j < K; ++j) g += Vt[j * (D + 1) + k] * gXr[j] + dVt[j * (D + 1) + k] * gpr[j];
+        gc[k] = g;
     }
     __syncthreads();
     // c = C Q  ->  gQ = C^T gc; Q = z_lo + frac (z_hi - z_lo), z = (beta - mu)/sigma
     const double* Ct = E.cheb + cheb_C(M, D);
-    for (int w = threadIdx.x; w < 2 * M; w += CDF_NT) {
-        const int a = w / M, i = w % M;
+    for (int i = threadIdx.x; i < M; i += CDF_NT) {
         double g = 0.0;
-        for (int k = 0; k <= D; ++k) g += Ct[k * M + i] * gc[a][k];
-        gQ[a][i] = g;
+        for (int k = 0; k <= D; ++k) g += Ct[k * M + i] * gc[k];
+        gQ[i] = g;
         const double h = E.cheb[cheb_u(M, D) + i] * (N - 1);
         const double frac = h - floor(h);
-        E.tadj[TADJ_SEL + a * 2 * MAXM + 2 * i] = g * (1.0 - frac) / sigma;
-        E.tadj[TADJ_SEL + a * 2 * MAXM + 2 * i + 1] = g * frac / sigma;
+        E.tadj[TADJ_SEL + ax * 2 * MAXM + 2 * i] = g * (1.0 - frac) * isig;
+        E.tadj[TADJ_SEL + ax * 2 * MAXM + 2 * i + 1] = g * frac * isig;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double dmu[2] = {tot[8], tot[9]};
-        double dsig = tot[10];
-        for (int a = 0; a < 2; ++a) {
-            const double* Q = tr + TR_HDR + 8 * K + 2 * MAXM + a * MAXM;
-            for (int i = 0; i < M; ++i) {
-                dmu[a] -= gQ[a][i] / sigma;
-                dsig -= gQ[a][i] * Q[i] / sigma;
-            }
+    // mu and sigma parts: fixed lane stride over the nodes, fixed tree
+    if (wid == 0) {
+        const double* Q = tr + TR_HDR + 8 * K + 2 * MAXM + ax * MAXM;
+        double sq = 0.0, sqq = 0.0;
+        for (int i = lane; i < M; i += 32) {
+            sq += gQ[i];
+            sqq += gQ[i] * Q[i];
         }
-        E.tadj[0] = dmu[0] / N;
-        E.tadj[1] = dmu[1] / N;
-        E.tadj[2] = dsig / (N * sigma);
-        E.tadj[3] = tr[3];
+        for (int o = 16; o > 0; o >>= 1) {
+            sq += __shfl_down_sync(0xffffffffu, sq, o);
+            sqq += __shfl_down_sync(0xffffffffu, sqq, o);
+        }
+        if (lane == 0) {
+            E.tadj[ax] = (tot[8 + ax] - sq * isig) / N;
+            E.tadj[4 + ax] = (ax == 0 ? tot[10] : 0.0) - sqq * isig;
+            if (ax == 0) E.tadj[3] = tr[3];
+        }
     }
 }
 
@@ -147,6 +168,7 @@ __global__ void __launch_bounds__(CTA_C) k_centre_adj(const __grid_constant__ Ba
     __shared__ int sidx[2][2 * MAXM];
     __shared__ double sg[2][2 * MAXM];
     __shared__ double hdr[4], mu[2];
+    __shared__ double gsel[2][CTA_C];        // selected-rank terms of this CTA's rays
     __shared__ double red[CTA_C / 32][8];
     load_lensk(L, lensk_src<T>(E.lensk));
     if (sizeof(T) == 4) load_lensk(Ld, E.lensk);
@@ -157,9 +179,22 @@ __global__ void __launch_bounds__(CTA_C) k_centre_adj(const __grid_constant__ Ba
         sg[a][t] = on ? E.tadj[TADJ_SEL + a * 2 * MAXM + t] : 0.0;
     }
     if (threadIdx.x < 4) hdr[threadIdx.x] = E.tadj[threadIdx.x];
+    if (threadIdx.x == 2) hdr[2] = (E.tadj[4] + E.tadj[5]) / (N * E.trd[2]);
     if (threadIdx.x < 2) mu[threadIdx.x] = E.trd[threadIdx.x];
+    gsel[0][threadIdx.x] = 0.0;
+    gsel[1][threadIdx.x] = 0.0;
     __syncthreads();
-    const int k = tile * CTA_C + threadIdx.x;
+    const int k0 = tile * CTA_C;
+    if (threadIdx.x < 2) {
+        // the selected rays among this CTA's: their rank terms, in target order
+        const int a = threadIdx.x;
+        for (int t = 0; t < 2 * M; ++t) {
+            const int i = sidx[a][t] - k0;
+            if (i >= 0 && i < CTA_C) gsel[a][i] += sg[a][t];
+        }
+    }
+    __syncthreads();
+    const int k = k0 + threadIdx.x;
     double gb[2] = {0.0, 0.0};
     double xd = 0.0, yd = 0.0;
     if (k < N) {
@@ -168,11 +203,14 @@ __global__ void __launch_bounds__(CTA_C) k_centre_adj(const __grid_constant__ Ba
         for (int a = 0; a < 2; ++a) {
             double g = hdr[a];
             if (a == amin) g += hdr[2] * (b[a] - mu[a]);
-            for (int t = 0; t < 2 * M; ++t)
-                if (sidx[a][t] == k) g += sg[a][t];
-            gb[a] = g;
+            gb[a] = g + gsel[a][threadIdx.x];
         }
-        ray_pos(E.n_img, E.pix, 1, E.centre_idx[k], 0, xd, yd);
+        // the pixel centre (sub-ray offset 0 at s = 1)
+        const int pix = E.centre_idx[k];
+        const int pj = pix / E.n_img, pi = pix - pj * E.n_img;
+        const double c = 0.5 * (E.n_img - 1);
+        xd = (pi - c) * E.pix;
+        yd = (pj - c) * E.pix;
     }
     T acc[8];
     for (int p = 0; p < 8; ++p) acc[p] = T(0);

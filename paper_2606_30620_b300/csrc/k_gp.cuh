@@ -113,9 +113,11 @@ __device__ void fft2(Cx<T>* g, int n, const int* rad, int nrad, const Cx<T>* tw,
     fft2_pass<T>(g, n, rad, nrad, tw, rev, smem, chunk, inv, true);
 }
 
-// numpy fftfreq(n)[i] in cycles per pixel
-__device__ __forceinline__ double fftfreq(int i, int n) {
-    return (double)(i < (n + 1) / 2 ? i : i - n) / n;
+// numpy fftfreq(n)[i] in cycles per pixel, in the kernel's type (no FP64
+// instruction in float mode)
+template <typename T>
+__device__ __forceinline__ T fftfreq(int i, int n) {
+    return T(i < (n + 1) / 2 ? i : i - n) / T(n);
 }
 
 // sqrt(P(k)) and d sqrt(P)/d theta for the family (Eq. 4 and its stand-ins), in
@@ -211,7 +213,7 @@ __global__ void __launch_bounds__(GP_NT) k_gp_source(const __grid_constant__ Bat
     const T kscale = (T)(2.0 * 3.14159265358979323846 / E.pitch);
     for (int i = threadIdx.x; i < n2; i += blockDim.x) {
         const int ky = i / n, kx = i - ky * n;
-        const T fx = (T)fftfreq(kx, n), fy = (T)fftfreq(ky, n);
+        const T fx = fftfreq<T>(kx, n), fy = fftfreq<T>(ky, n);
         const T k = kscale * r_sqrt(fx * fx + fy * fy);
         T gdummy[3];
         const T sp = sqrtP_and_grad<T>(E.family, psv, k, gdummy);
@@ -285,7 +287,7 @@ __global__ void __launch_bounds__(GP_NT) k_gp_adjoint(const __grid_constant__ Ba
     T gp[3] = {T(0), T(0), T(0)};
     for (int i = threadIdx.x; i < n2; i += blockDim.x) {
         const int ky = i / n, kx = i - ky * n;
-        const T fx = (T)fftfreq(kx, n), fy = (T)fftfreq(ky, n);
+        const T fx = fftfreq<T>(kx, n), fy = fftfreq<T>(ky, n);
         const T k = kscale * r_sqrt(fx * fx + fy * fy);
         T dsp[3] = {T(0), T(0), T(0)};
         const T sp = sqrtP_and_grad<T>(E.family, psv, k, dsp);

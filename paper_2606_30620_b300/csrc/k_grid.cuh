@@ -65,17 +65,30 @@ __global__ void __launch_bounds__(CTA_C) k_trace_centres(const __grid_constant__
     }
 }
 
-// reduce the per-CTA centre sums: mean and range per axis (same order everywhere)
+// reduce the per-CTA centre sums: mean and range per axis.  Called by one whole
+// warp; lane l takes the CTAs t = l mod 32 in order, then a fixed shuffle tree, so
+// every kernel that calls it gets the same bits.  Lane 0 writes out6.
 __device__ __forceinline__ void centre_moments(const EvalArgs& E, double* out6) {
+    const int lane = threadIdx.x & 31;
     double s0 = 0.0, s1 = 0.0, lo0 = 1e300, hi0 = -1e300, lo1 = 1e300, hi1 = -1e300;
-    for (int t = 0; t < E.n_cta_c; ++t) {
+    for (int t = lane; t < E.n_cta_c; t += 32) {
         const double* c = E.cpart + t * 8;
         s0 += c[0]; s1 += c[1];
         lo0 = fmin(lo0, c[2]); hi0 = fmax(hi0, c[3]);
         lo1 = fmin(lo1, c[4]); hi1 = fmax(hi1, c[5]);
     }
-    out6[0] = s0 / E.n_mask; out6[1] = s1 / E.n_mask;
-    out6[2] = lo0; out6[3] = hi0; out6[4] = lo1; out6[5] = hi1;
+    for (int o = 16; o > 0; o >>= 1) {
+        s0 += __shfl_down_sync(0xffffffffu, s0, o);
+        s1 += __shfl_down_sync(0xffffffffu, s1, o);
+        lo0 = fmin(lo0, __shfl_down_sync(0xffffffffu, lo0, o));
+        hi0 = fmax(hi0, __shfl_down_sync(0xffffffffu, hi0, o));
+        lo1 = fmin(lo1, __shfl_down_sync(0xffffffffu, lo1, o));
+        hi1 = fmax(hi1, __shfl_down_sync(0xffffffffu, hi1, o));
+    }
+    if (lane == 0) {
+        out6[0] = s0 / E.n_mask; out6[1] = s1 / E.n_mask;
+        out6[2] = lo0; out6[3] = hi0; out6[4] = lo1; out6[5] = hi1;
+    }
 }
 
 __device__ __forceinline__ double bin_scale(double lo, double hi) {
@@ -88,7 +101,7 @@ __global__ void __launch_bounds__(CTA_C) k_centre_hist(const __grid_constant__ B
     const int tile = blockIdx.x - B.tile0[ev];
     __shared__ double m[6];
     __shared__ double red[2][CTA_C / 32];
-    if (threadIdx.x == 0) centre_moments(E, m);
+    if (threadIdx.x < 32) centre_moments(E, m);
     __syncthreads();
     const int k = tile * CTA_C + threadIdx.x;
     double d0 = 0.0, d1 = 0.0;
@@ -113,255 +126,293 @@ __global__ void __launch_bounds__(CTA_C) k_centre_hist(const __grid_constant__ B
 }
 
 constexpr int SEL_NT = 1024;
+constexpr int SEL_ROWS = HB / 32;      // the histogram as rows of 32 bins (one per lane)
 
-// One CTA per evaluation.  Dynamic shared memory:
+// One CTA per (evaluation, axis).  Dynamic shared memory:
 //   double ck[SEL_CAP]; int ci[SEL_CAP]; unsigned bitmap[HB/32];
 __global__ void __launch_bounds__(SEL_NT) k_select_fit(const __grid_constant__ Batch B) {
-    const EvalArgs& E = B.e[blockIdx.x];
+    const int ev = find_eval(B, blockIdx.x);
+    const EvalArgs& E = B.e[ev];
+    const int a = blockIdx.x - B.tile0[ev];          // axis
     extern __shared__ __align__(128) unsigned char smem_raw[];
     double* ck = reinterpret_cast<double*>(smem_raw);
     int* ci = reinterpret_cast<int*>(ck + SEL_CAP);
     unsigned* bitmap = reinterpret_cast<unsigned*>(ci + SEL_CAP);
     __shared__ double mom[6];
     __shared__ double sig[3];
-    __shared__ int chunk_off[SEL_NT + 1];
-    __shared__ int t_bin[2 * MAXM], t_below[2 * MAXM], t_rank[2 * MAXM], t_slot[2 * MAXM];
+    __shared__ int rowoff[SEL_ROWS + 1];
+    __shared__ int wtot[SEL_NT / 32];
+    __shared__ int t_bin[2 * MAXM], t_below[2 * MAXM], t_rank[2 * MAXM], t_slot[2 * MAXM], t_cnt[2 * MAXM];
     __shared__ int d_bin[2 * MAXM], d_off[2 * MAXM + 1], d_fill[2 * MAXM];
     __shared__ int n_d;
-    __shared__ double Qs[2][MAXM];
-    __shared__ double coef[2][MAXM];
+    __shared__ double Qs[MAXM];
+    __shared__ double coef[MAXM];
+    __shared__ double Xs[MAXM + 2], Ps[MAXM + 2];
+    __shared__ double selv[2 * MAXM];        // the selected order statistics
     __shared__ int flag_sh;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int N = E.n_mask, M = E.n_nodes, D = E.degree, K = M + 2;
 
-    if (tid == 0) {
+    if (wid == 0) {
         centre_moments(E, mom);
+        // sums of squared deviations: lanes over CTAs, fixed tree
         double v0 = 0.0, v1 = 0.0;
-        for (int t = 0; t < E.n_cta_c; ++t) { v0 += E.cpart2[2 * t]; v1 += E.cpart2[2 * t + 1]; }
-        double sx = sqrt(v0 / N), sy = sqrt(v1 / N);
-        sig[0] = sx <= sy ? sx : sy;            // sigma_min, tie -> x (App. C i)
-        sig[1] = sx <= sy ? 0.0 : 1.0;
-        flag_sh = 0;
+        for (int t = lane; t < E.n_cta_c; t += 32) { v0 += E.cpart2[2 * t]; v1 += E.cpart2[2 * t + 1]; }
+        for (int o = 16; o > 0; o >>= 1) {
+            v0 += __shfl_down_sync(0xffffffffu, v0, o);
+            v1 += __shfl_down_sync(0xffffffffu, v1, o);
+        }
+        if (lane == 0) {
+            double sx = sqrt(v0 / N), sy = sqrt(v1 / N);
+            sig[0] = sx <= sy ? sx : sy;            // sigma_min, tie -> x (App. C i)
+            sig[1] = sx <= sy ? 0.0 : 1.0;
+            sig[2] = 1.0 / sig[0];
+            flag_sh = 0;
+        }
     }
     __syncthreads();
-    const double sigma = sig[0];
-
-    for (int a = 0; a < 2; ++a) {
-        const int* hist = E.hist + a * HB;
-        const double* beta = E.beta + a * N;
-        const double lo = mom[2 + 2 * a], hi = mom[3 + 2 * a];
-        const double scale = bin_scale(lo, hi);
-        // exclusive scan of HB bins: 64 consecutive bins per thread
-        constexpr int PER = HB / SEL_NT;
-        int own = 0;
-        for (int i = 0; i < PER; ++i) own += hist[tid * PER + i];
-        // block scan (warp inclusive scans, then warp totals)
-        int incl = own;
-        for (int o = 1; o < 32; o <<= 1) {
-            int y = __shfl_up_sync(0xffffffffu, incl, o);
-            if ((tid & 31) >= o) incl += y;
-        }
-        __shared__ int wtot[SEL_NT / 32];
-        if ((tid & 31) == 31) wtot[tid >> 5] = incl;
-        for (int i = tid; i < 2 * MAXM; i += SEL_NT) d_fill[i] = 0;
-        for (int i = tid; i < HB / 32; i += SEL_NT) bitmap[i] = 0u;
-        __syncthreads();
-        if (tid == 0) {
-            int acc = 0;
-            for (int w = 0; w < SEL_NT / 32; ++w) { int t = wtot[w]; wtot[w] = acc; acc += t; }
-            chunk_off[SEL_NT] = acc;
-        }
-        __syncthreads();
-        chunk_off[tid] = wtot[tid >> 5] + incl - own;
-        __syncthreads();
-        // target ranks: node j -> floor(u_j (N-1)) and the next one (RTU grid); the
-        // smallest and largest ray (uniform grid: the square box, Sec. 2.1)
-        const int nt = E.transform ? 2 : 2 * M;
-        for (int t = tid; t < nt; t += SEL_NT) {
-            int k;
-            if (E.transform) {
-                k = t == 0 ? 0 : N - 1;
-            } else {
-                double h = E.cheb[cheb_u(M, D) + t / 2] * (N - 1);
-                k = (int)floor(h);
-                k = k < 0 ? 0 : (k > N - 1 ? N - 1 : k);
-                if (t & 1) k = k + 1 > N - 1 ? N - 1 : k + 1;
-            }
-            t_rank[t] = k;
-        }
-        for (int t = nt + tid; t < 2 * MAXM; t += SEL_NT) E.sel_idx[a * 2 * MAXM + t] = -1;
-        for (int t = tid; t < nt; t += SEL_NT) { t_bin[t] = 0; t_below[t] = 0; }
-        __syncthreads();
-        for (int t = 0; t < nt; ++t) {
-            const int r = t_rank[t];
-            if (chunk_off[tid] <= r && r < chunk_off[tid + 1]) {
-                int c = chunk_off[tid];
-                for (int i = 0; i < PER; ++i) {
-                    int h = hist[tid * PER + i];
-                    if (r < c + h) { t_bin[t] = tid * PER + i; t_below[t] = c; break; }
-                    c += h;
-                }
-            }
-        }
-        __syncthreads();
-        if (tid == 0) {
-            // distinct target bins (ranks are non-decreasing, so are their bins)
-            int nd = 0, off = 0;
-            for (int t = 0; t < nt; ++t) {
-                if (nd == 0 || d_bin[nd - 1] != t_bin[t]) {
-                    d_bin[nd] = t_bin[t];
-                    d_off[nd] = off;
-                    int cnt = hist[t_bin[t]];
-                    off += cnt;
-                    bitmap[t_bin[t] >> 5] |= 1u << (t_bin[t] & 31);
-                    ++nd;
-                }
-                t_slot[t] = nd - 1;
-            }
-            d_off[nd] = off;
-            n_d = nd;
-            if (off > SEL_CAP) flag_sh |= F_SELECT;
-        }
-        __syncthreads();
-        const int nd = n_d;
-        // gather the candidates of the target bins
-        for (int k = tid; k < N; k += SEL_NT) {
-            const double b = beta[k];
-            const int bn = beta_bin(b, lo, scale);
-            if (bitmap[bn >> 5] & (1u << (bn & 31))) {
-                int d = 0;
-                while (d < nd - 1 && d_bin[d] != bn) ++d;
-                const int pos = atomicAdd(&d_fill[d], 1);
-                const int at = d_off[d] + pos;
-                if (at < SEL_CAP && pos < d_off[d + 1] - d_off[d]) { ck[at] = b; ci[at] = k; }
-            }
-        }
-        __syncthreads();
-        // the element of rank (r - below) inside its bin, ties ordered by index
-        for (int t = 0; t < nt; ++t) {
-            const int d = t_slot[t];
-            const int o = d_off[d], cnt = min(d_off[d + 1], SEL_CAP) - o;
-            const int want = t_rank[t] - t_below[t];
-            for (int c = tid; c < cnt; c += SEL_NT) {
-                const double kc = ck[o + c];
-                const int ic = ci[o + c];
-                int rank = 0;
-                for (int c2 = 0; c2 < cnt; ++c2) {
-                    const double k2 = ck[o + c2];
-                    rank += (k2 < kc) || (k2 == kc && ci[o + c2] < ic);
-                }
-                if (rank == want) {
-                    E.sel_val[a * 2 * MAXM + t] = kc;
-                    E.sel_idx[a * 2 * MAXM + t] = ic;
-                }
-            }
-        }
-        __syncthreads();
-        // empirical QF at the nodes in standardized coordinates (type-7 interpolation)
-        for (int j = tid; j < M && !E.transform; j += SEL_NT) {
-            double h = E.cheb[cheb_u(M, D) + j] * (N - 1);
-            double frac = h - floor(h);
-            double zl = (E.sel_val[a * 2 * MAXM + 2 * j] - mom[a]) / sigma;
-            double zh = (E.sel_val[a * 2 * MAXM + 2 * j + 1] - mom[a]) / sigma;
-            Qs[a][j] = zl + frac * (zh - zl);
-        }
-        __syncthreads();
-    }
-
+    const double sigma = sig[0], isig = sig[2];
     double* tr = E.trd;
+    const int* hist = E.hist + a * HB;
+    const double* beta = E.beta + a * N;
+    const double lo = mom[2 + 2 * a], hi = mom[3 + 2 * a];
+    const double scale = bin_scale(lo, hi);
+    // row sums: warp w reads its 64 rows of 32 bins coalesced
+    constexpr int RPW = SEL_ROWS / (SEL_NT / 32);
+    for (int i = 0; i < RPW; ++i) {
+        const int row = wid * RPW + i;
+        const int sum = __reduce_add_sync(0xffffffffu, hist[row * 32 + lane]);
+        if (lane == 0) rowoff[row] = sum;
+    }
+    for (int i = tid; i < 2 * MAXM; i += SEL_NT) d_fill[i] = 0;
+    for (int i = tid; i < HB / 32; i += SEL_NT) bitmap[i] = 0u;
+    __syncthreads();
+    // exclusive scan of the row sums: two rows per thread, warp scans, warp totals
+    const int r0 = rowoff[2 * tid], r1 = rowoff[2 * tid + 1];
+    const int own = r0 + r1;
+    int incl = own;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) wtot[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        const int v = wtot[lane];
+        int wi = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += y;
+        }
+        wtot[lane] = wi - v;
+        if (lane == 31) rowoff[SEL_ROWS] = wi;
+    }
+    __syncthreads();
+    {
+        const int ex = wtot[wid] + incl - own;
+        rowoff[2 * tid] = ex;
+        rowoff[2 * tid + 1] = ex + r0;
+    }
+    // target ranks: node j -> floor(u_j (N-1)) and the next one (RTU grid); the
+    // smallest and largest ray (uniform grid: the square box, Sec. 2.1)
+    const int nt = E.transform ? 2 : 2 * M;
+    for (int t = tid; t < nt; t += SEL_NT) {
+        int k;
+        if (E.transform) {
+            k = t == 0 ? 0 : N - 1;
+        } else {
+            double h = E.cheb[cheb_u(M, D) + t / 2] * (N - 1);
+            k = (int)floor(h);
+            k = k < 0 ? 0 : (k > N - 1 ? N - 1 : k);
+            if (t & 1) k = k + 1 > N - 1 ? N - 1 : k + 1;
+        }
+        t_rank[t] = k;
+    }
+    for (int t = nt + tid; t < 2 * MAXM; t += SEL_NT) E.sel_idx[a * 2 * MAXM + t] = -1;
+    __syncthreads();
+    // the bin of each target rank: one warp per target -- the 64-row section, the
+    // row, then the bin inside the row by a warp scan of its 32 counts
+    for (int t = wid; t < nt; t += SEL_NT / 32) {
+        const int r = t_rank[t];
+        constexpr int SEC = SEL_ROWS / 32;
+        const unsigned m1 = __ballot_sync(0xffffffffu, rowoff[lane * SEC] <= r && r < rowoff[lane * SEC + SEC]);
+        const int sec = __ffs(m1) - 1;
+        const int ra = sec * SEC + 2 * lane;
+        const unsigned m2 = __ballot_sync(0xffffffffu, rowoff[ra] <= r && r < rowoff[ra + 2]);
+        const int rr = sec * SEC + 2 * (__ffs(m2) - 1);
+        const int row = r < rowoff[rr + 1] ? rr : rr + 1;
+        const int v = hist[row * 32 + lane];
+        int inc = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        const int ex = rowoff[row] + inc - v;
+        const unsigned m3 = __ballot_sync(0xffffffffu, ex <= r && r < ex + v);
+        if (lane == __ffs(m3) - 1) {
+            t_bin[t] = row * 32 + lane;
+            t_below[t] = ex;
+            t_cnt[t] = v;
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        // distinct target bins (ranks are non-decreasing, so are their bins)
+        int nd = 0, off = 0;
+        for (int t = 0; t < nt; ++t) {
+            if (nd == 0 || d_bin[nd - 1] != t_bin[t]) {
+                d_bin[nd] = t_bin[t];
+                d_off[nd] = off;
+                off += t_cnt[t];
+                bitmap[t_bin[t] >> 5] |= 1u << (t_bin[t] & 31);
+                ++nd;
+            }
+            t_slot[t] = nd - 1;
+        }
+        d_off[nd] = off;
+        n_d = nd;
+        if (off > SEL_CAP) flag_sh |= F_SELECT;
+    }
+    for (int t = tid; t < nt; t += SEL_NT) selv[t] = lo;     // overwritten by the selection
+    __syncthreads();
+    const int nd = n_d;
+    // gather the candidates of the target bins
+    for (int k = tid; k < N; k += SEL_NT) {
+        const double b = beta[k];
+        const int bn = beta_bin(b, lo, scale);
+        if (bitmap[bn >> 5] & (1u << (bn & 31))) {
+            int d = 0;
+            while (d < nd - 1 && d_bin[d] != bn) ++d;
+            const int pos = atomicAdd(&d_fill[d], 1);
+            const int at = d_off[d] + pos;
+            if (at < SEL_CAP && pos < d_off[d + 1] - d_off[d]) { ck[at] = b; ci[at] = k; }
+        }
+    }
+    __syncthreads();
+    // the element of rank (r - below) inside its bin, ties ordered by index
+    for (int t = 0; t < nt; ++t) {
+        const int d = t_slot[t];
+        const int o = d_off[d], cnt = min(d_off[d + 1], SEL_CAP) - o;
+        const int want = t_rank[t] - t_below[t];
+        for (int c = tid; c < cnt; c += SEL_NT) {
+            const double kc = ck[o + c];
+            const int ic = ci[o + c];
+            int rank = 0;
+            for (int c2 = 0; c2 < cnt; ++c2) {
+                const double k2 = ck[o + c2];
+                rank += (k2 < kc) || (k2 == kc && ci[o + c2] < ic);
+            }
+            if (rank == want) {
+                E.sel_idx[a * 2 * MAXM + t] = ic;
+                selv[t] = kc;
+            }
+        }
+    }
+    __syncthreads();
+
     if (E.transform) {
         // uniform grid: the smallest square box around the masked rays, centred on
         // each axis's range, mapped affinely onto [0, 1]^2 -- written as Hermite
-        // knots X_j = (lo + U_j L - mu)/sigma with equal slopes sigma/L (linear)
-        if (tid < 2) {
-            const int a = tid;
-            const double mn0 = E.sel_val[0], mx0 = E.sel_val[1];
-            const double mn1 = E.sel_val[2 * MAXM], mx1 = E.sel_val[2 * MAXM + 1];
-            const double r0 = mx0 - mn0, r1 = mx1 - mn1;
-            const double L = r0 >= r1 ? r0 : r1;
-            const double mn = a == 0 ? mn0 : mn1, mx = a == 0 ? mx0 : mx1;
-            const double lo = 0.5 * (mn + mx) - 0.5 * L;
-            for (int j = 0; j < K; ++j) {
-                const double U = j == 0 ? 0.0 : (j == K - 1 ? 1.0 : E.cheb[cheb_u(M, D) + j - 1]);
-                const double X = (lo + U * L - mom[a]) / sigma;
-                tr[TR_HDR + a * K + j] = X;
-                tr[TR_HDR + (6 + a) * K + j] = X;
-                tr[TR_HDR + (2 + a) * K + j] = sigma / L;
-                tr[TR_HDR + (4 + a) * K + j] = L / sigma;
-            }
-            if (a == 0) { tr[5] = r0 >= r1 ? 0.0 : 1.0; tr[6] = L; }
+        // knots X_j = (lo + U_j L - mu)/sigma with equal slopes sigma/L (linear).
+        // The ranges are the order statistics of ranks 0 and N-1 (= min, max).
+        const double r0x = mom[3] - mom[2], r1y = mom[5] - mom[4];
+        const double L = r0x >= r1y ? r0x : r1y;
+        const double mn = mom[2 + 2 * a], mx = mom[3 + 2 * a];
+        const double lo_a = 0.5 * (mn + mx) - 0.5 * L;
+        for (int j = tid; j < K; j += SEL_NT) {
+            const double U = j == 0 ? 0.0 : (j == K - 1 ? 1.0 : E.cheb[cheb_u(M, D) + j - 1]);
+            const double X = (lo_a + U * L - mom[a]) * isig;
+            tr[TR_HDR + a * K + j] = X;
+            tr[TR_HDR + (6 + a) * K + j] = X;
+            tr[TR_HDR + (2 + a) * K + j] = sigma / L;
+            tr[TR_HDR + (4 + a) * K + j] = L * isig;
         }
-        if (tid == 0) {
+        if (a == 0 && tid == 0) {
             tr[0] = mom[0]; tr[1] = mom[1]; tr[2] = sigma; tr[3] = sig[1]; tr[4] = K;
+            tr[5] = r0x >= r1y ? 0.0 : 1.0; tr[6] = L;
+        }
+    } else {
+        // empirical QF at the nodes in standardized coordinates (type-7 interpolation)
+        for (int j = tid; j < M; j += SEL_NT) {
+            const double h = E.cheb[cheb_u(M, D) + j] * (N - 1);
+            const double frac = h - floor(h);
+            const double zl = (selv[2 * j] - mom[a]) * isig;
+            const double zh = (selv[2 * j + 1] - mom[a]) * isig;
+            Qs[j] = zl + frac * (zh - zl);
         }
         __syncthreads();
-        for (int i = tid; i < TR_HDR + 4 * K; i += SEL_NT) E.trf[i] = (float)tr[i];
-        if (E.cdf_out) {
-            for (int i = tid; i < 3; i += SEL_NT) E.cdf_out[i] = tr[i];
-            for (int i = tid; i < 4 * K; i += SEL_NT) E.cdf_out[3 + i] = tr[TR_HDR + i];
+        // App. C iii: Chebyshev coefficients of the QF from M = D+1 nodes by the
+        // discrete orthogonality of T_k on the nodes: c = C Q (one thread per coefficient)
+        const double* Ct = E.cheb + cheb_C(M, D);
+        for (int k = tid; k <= D; k += SEL_NT) {
+            double sacc = 0.0;
+            for (int j = 0; j < M; ++j) sacc += Ct[k * M + j] * Qs[j];
+            coef[k] = sacc;
         }
-        if (tid == 0 && flag_sh) atomicOr(E.flags, flag_sh);
-        return;
-    }
-    // App. C iii: Chebyshev coefficients of the QF from M = D+1 nodes by the
-    // discrete orthogonality of T_k on the nodes: c = C Q (one thread per coefficient)
-    const double* Ct = E.cheb + cheb_C(M, D);
-    for (int w = tid; w < 2 * (D + 1); w += SEL_NT) {
-        const int a = w / (D + 1), k = w % (D + 1);
-        double sacc = 0.0;
-        for (int j = 0; j < M; ++j) sacc += Ct[k * M + j] * Qs[a][j];
-        coef[a][k] = sacc;
-    }
-    __syncthreads();
-    // App. C iv: knots p(0), p(u_j), p(1) and p'(u) there (one thread per point)
-    __shared__ double Xs[2][MAXM + 2], Ps[2][MAXM + 2];
-    const double* Vt = E.cheb + cheb_V(M, D);
-    const double* dVt = E.cheb + cheb_dV(M, D);
-    for (int w = tid; w < 2 * K; w += SEL_NT) {
-        const int a = w / K, j = w % K;
-        double p = 0.0, d = 0.0;
-        for (int k = 0; k <= D; ++k) {
-            p += Vt[j * (D + 1) + k] * coef[a][k];
-            d += dVt[j * (D + 1) + k] * coef[a][k];
+        __syncthreads();
+        // App. C iv: knots p(0), p(u_j), p(1) and p'(u) there (one thread per point),
+        // the slope floor of the guard and the slopes 1/p' (per point)
+        const double* Vt = E.cheb + cheb_V(M, D);
+        const double* dVt = E.cheb + cheb_dV(M, D);
+        for (int j = tid; j < K; j += SEL_NT) {
+            double p = 0.0, d = 0.0;
+            for (int k = 0; k <= D; ++k) {
+                p += Vt[j * (D + 1) + k] * coef[k];
+                d += dVt[j * (D + 1) + k] * coef[k];
+            }
+            Xs[j] = p;
+            Ps[j] = d;
+            tr[TR_HDR + (6 + a) * K + j] = p;       // raw knots
+            tr[TR_HDR + (4 + a) * K + j] = d;       // raw p'
         }
-        Xs[a][j] = p;
-        Ps[a][j] = d;
-        tr[TR_HDR + (6 + a) * K + j] = p;       // raw knots
-        tr[TR_HDR + (4 + a) * K + j] = d;       // raw p'
-    }
-    __syncthreads();
-    // monotonicity guard, sequential in the knots (one thread per axis)
-    if (tid < 2) {
-        const int a = tid;
-        double* X = Xs[a];
-        double* dp = Ps[a];
-        int fl = 0;
-        double span = X[K - 1] - X[0];
-        if (!(span > 0.0)) { fl |= F_NONMONO; span = fabs(span) + 1e-300; }
+        __syncthreads();
+        // monotonicity guard (App. C iv): p' >= 1e-6 span per point (in parallel),
+        // strictly increasing knots (sequential in the knots, one thread)
+        double span = Xs[K - 1] - Xs[0];
+        const bool span_ok = span > 0.0;
+        if (!span_ok) span = fabs(span) + 1e-300;
         const double floor_d = 1e-6 * span;
-        for (int j = 0; j < K; ++j)
-            if (dp[j] < floor_d) { dp[j] = floor_d; fl |= F_NONMONO; }
-        for (int j = 1; j < K; ++j) {
-            double lim = X[j - 1] + floor_d;
-            if (X[j] < lim) { X[j] = lim; fl |= F_NONMONO; }
+        if (!span_ok && tid == 0) flag_sh |= F_NONMONO;
+        for (int j = tid; j < K; j += SEL_NT) {
+            double dp = Ps[j];
+            if (dp < floor_d) { dp = floor_d; atomicOr(&flag_sh, F_NONMONO); }
+            tr[TR_HDR + (2 + a) * K + j] = 1.0 / dp;
         }
-        for (int j = 0; j < K; ++j) {
-            tr[TR_HDR + a * K + j] = X[j];
-            tr[TR_HDR + (2 + a) * K + j] = 1.0 / dp[j];
+        if (tid == 0) {
+            int fl = 0;
+            double prev = Xs[0];
+            tr[TR_HDR + a * K] = prev;
+            for (int j = 1; j < K; ++j) {
+                double x = Xs[j];
+                const double lim = prev + floor_d;
+                if (x < lim) { x = lim; fl |= F_NONMONO; }
+                tr[TR_HDR + a * K + j] = x;
+                prev = x;
+            }
+            if (fl) atomicOr(&flag_sh, fl);
         }
-        for (int k = 0; k <= D; ++k) tr[TR_HDR + 8 * K + a * MAXM + k] = coef[a][k];
-        for (int j = 0; j < M; ++j) tr[TR_HDR + 8 * K + 2 * MAXM + a * MAXM + j] = Qs[a][j];
-        if (fl) atomicOr(&flag_sh, fl);
-    }
-    if (tid == 0) {
-        tr[0] = mom[0]; tr[1] = mom[1]; tr[2] = sigma; tr[3] = sig[1]; tr[4] = K;
+        for (int k = tid; k <= D; k += SEL_NT) tr[TR_HDR + 8 * K + a * MAXM + k] = coef[k];
+        for (int j = tid; j < M; j += SEL_NT) tr[TR_HDR + 8 * K + 2 * MAXM + a * MAXM + j] = Qs[j];
+        if (a == 0 && tid == 0) {
+            tr[0] = mom[0]; tr[1] = mom[1]; tr[2] = sigma; tr[3] = sig[1]; tr[4] = K;
+        }
     }
     __syncthreads();
-    // float copy for the float render path, the optional CDF output, flags
-    for (int i = tid; i < TR_HDR + 4 * K; i += SEL_NT) E.trf[i] = (float)tr[i];
+    // float copy of this axis's knots and slopes (and the header) for the float
+    // render path, the optional CDF output, flags
+    for (int j = tid; j < K; j += SEL_NT) {
+        E.trf[TR_HDR + a * K + j] = (float)tr[TR_HDR + a * K + j];
+        E.trf[TR_HDR + (2 + a) * K + j] = (float)tr[TR_HDR + (2 + a) * K + j];
+    }
+    if (a == 0)
+        for (int i = tid; i < TR_HDR; i += SEL_NT) E.trf[i] = (float)tr[i];
     if (E.cdf_out) {
-        for (int i = tid; i < 3; i += SEL_NT) E.cdf_out[i] = tr[i];
-        for (int i = tid; i < 4 * K; i += SEL_NT) E.cdf_out[3 + i] = tr[TR_HDR + i];
+        if (a == 0)
+            for (int i = tid; i < 3; i += SEL_NT) E.cdf_out[i] = tr[i];
+        for (int j = tid; j < K; j += SEL_NT) {
+            E.cdf_out[3 + a * K + j] = tr[TR_HDR + a * K + j];
+            E.cdf_out[3 + (2 + a) * K + j] = tr[TR_HDR + (2 + a) * K + j];
+        }
     }
     if (tid == 0 && flag_sh) atomicOr(E.flags, flag_sh);
 }

@@ -85,6 +85,144 @@ __global__ void __launch_bounds__(PSF_NT) k_psf_like(const __grid_constant__ Bat
     }
 }
 
+// ---- float path with a compile-time tap count KT (9 or 21): a PSF of K <= KT
+// taps is zero-padded to KT.  128 threads per 32 x 32 output tile, 8
+// horizontally adjacent outputs per thread; for every PSF row the thread loads
+// 8 + KT - 1 inputs and the KT weights with 16-byte shared loads and does
+// 8 KT fused multiply-adds from registers.
+constexpr int PSFT_NT = 128;
+template <int KT> struct PsfT {
+    static constexpr int C = (KT - 1) / 2;
+    static constexpr int W = PSF_T + KT - 1;          // input tile side
+    static constexpr int V = 8 + KT - 1;              // inputs per thread per row
+    static constexpr int VP = (V + 3) / 4 * 4;
+    // row pitch >= W with P = 4 (mod 8): 16-byte aligned rows, and the two rows
+    // read in one 8-thread phase of a 16-byte load fall in disjoint banks
+    static constexpr int P = (W + 3) / 8 * 8 + 4;
+    static constexpr int KP = (KT + 3) / 4 * 4;       // weight row pitch
+};
+
+// weights of an eval's K x K PSF centred in the KT x KT table (zeros around it),
+// psf[b][a] at [b][a]; the convolution flips by indexing the input
+template <int KT>
+__device__ __forceinline__ void psf_weights_t(const EvalArgs& E, float* kw) {
+    const int K = E.psf_k, o = (KT - K) / 2;
+    const float* psf = reinterpret_cast<const float*>(E.psf);
+    for (int w = threadIdx.x; w < KT * PsfT<KT>::KP; w += blockDim.x) {
+        const int b = w / PsfT<KT>::KP, a = w - b * PsfT<KT>::KP;
+        const int bb = b - o, aa = a - o;
+        kw[w] = (a < KT && bb >= 0 && bb < K && aa >= 0 && aa < K) ? psf[bb * K + aa] : 0.0f;
+    }
+}
+
+template <int KT>
+__device__ __forceinline__ void psf_stage_t(const float* src, int n, int i0, int j0, float (*in)[PsfT<KT>::P]) {
+    constexpr int W = PsfT<KT>::W, C = PsfT<KT>::C;
+    for (int w = threadIdx.x; w < W * PsfT<KT>::P; w += PSFT_NT) {
+        const int r = w / PsfT<KT>::P, q = w - r * PsfT<KT>::P;
+        const int gj = j0 - C + r, gi = i0 - C + q;
+        in[r][q] = (q < W && gj >= 0 && gj < n && gi >= 0 && gi < n) ? src[gj * n + gi] : 0.0f;
+    }
+}
+
+// acc[u] += sum_a kw_row[a] v[u + off(a)], off(a) = KT - 1 - a (convolution) or a
+// (correlation), v = the thread's inputs of one row
+template <int KT, bool CONV>
+__device__ __forceinline__ void psf_row_t(const float* in_row, const float* kw_row, float* acc) {
+    constexpr int VP = PsfT<KT>::VP, KP = PsfT<KT>::KP;
+    float v[VP], w[KP];
+#pragma unroll
+    for (int i = 0; i < VP / 4; ++i) {
+        const float4 t = reinterpret_cast<const float4*>(in_row)[i];
+        v[4 * i] = t.x; v[4 * i + 1] = t.y; v[4 * i + 2] = t.z; v[4 * i + 3] = t.w;
+    }
+#pragma unroll
+    for (int i = 0; i < KP / 4; ++i) {
+        const float4 t = reinterpret_cast<const float4*>(kw_row)[i];
+        w[4 * i] = t.x; w[4 * i + 1] = t.y; w[4 * i + 2] = t.z; w[4 * i + 3] = t.w;
+    }
+#pragma unroll
+    for (int a = 0; a < KT; ++a)
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc[u] += w[a] * v[u + (CONV ? KT - 1 - a : a)];
+}
+
+template <int KT>
+__global__ void __launch_bounds__(PSFT_NT) k_psf_like_t(const __grid_constant__ Batch B) {
+    const int ev = find_eval(B, blockIdx.x);
+    const EvalArgs& E = B.e[ev];
+    const int tile = blockIdx.x - B.tile0[ev];
+    __shared__ __align__(16) float in[PsfT<KT>::W][PsfT<KT>::P];
+    __shared__ __align__(16) float kw[KT * PsfT<KT>::KP];
+    __shared__ double red[2][PSFT_NT / 32];
+    const int n = E.n_img;
+    int ti, tj;
+    psf_tile_of(E, tile, ti, tj);
+    const int i0 = ti * PSF_T, j0 = tj * PSF_T;
+    psf_weights_t<KT>(E, kw);
+    psf_stage_t<KT>(reinterpret_cast<const float*>(E.img), n, i0, j0, in);
+    __syncthreads();
+    const int tx0 = 8 * (threadIdx.x & 3), ty = threadIdx.x >> 2;
+    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    // m[j, i] = sum_{b,a} psf[b][a] in[ty + 2C - b][x + 2C - a]
+#pragma unroll 1
+    for (int b = 0; b < KT; ++b)
+        psf_row_t<KT, true>(&in[ty + KT - 1 - b][tx0], kw + b * PsfT<KT>::KP, acc);
+    const float isg = 1.0f / (float)E.sigma;
+    float r2f = 0.f, r2mf = 0.f;
+    const int j = j0 + ty;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        const int i = i0 + tx0 + u;
+        if (i < n && j < n) {
+            const float m = acc[u];
+            const float d = reinterpret_cast<const float*>(E.data)[j * n + i];
+            const float r = (d - m) * isg;
+            reinterpret_cast<float*>(E.resid)[j * n + i] = r * isg;
+            if (E.model_out) reinterpret_cast<float*>(E.model_out)[j * n + i] = m;
+            r2f += r * r;
+            if (E.mask[j * n + i]) r2mf += r * r;
+        }
+    }
+    // per-thread float partials of 8 pixels, then double across threads
+    double r2 = warp_sum((double)r2f), r2m = warp_sum((double)r2mf);
+    if ((threadIdx.x & 31) == 0) { red[0][threadIdx.x >> 5] = r2; red[1][threadIdx.x >> 5] = r2m; }
+    __syncthreads();
+    if (threadIdx.x < 2) {
+        double sacc = 0.0;
+        for (int w = 0; w < PSFT_NT / 32; ++w) sacc += red[threadIdx.x][w];
+        E.lpart[tile * 2 + threadIdx.x] = sacc;
+    }
+}
+
+// d L / d img[p, q] = dlogL sum_{b,a} psf[b][a] resid[p + b - C, q + a - C]
+template <int KT>
+__global__ void __launch_bounds__(PSFT_NT) k_psf_adj_t(const __grid_constant__ Batch B) {
+    const int ev = find_eval(B, blockIdx.x);
+    const EvalArgs& E = B.e[ev];
+    const int tile = blockIdx.x - B.tile0[ev];
+    __shared__ __align__(16) float in[PsfT<KT>::W][PsfT<KT>::P];
+    __shared__ __align__(16) float kw[KT * PsfT<KT>::KP];
+    const int n = E.n_img;
+    int ti, tj;
+    psf_tile_of(E, tile, ti, tj);
+    const int i0 = ti * PSF_T, j0 = tj * PSF_T;
+    psf_weights_t<KT>(E, kw);
+    psf_stage_t<KT>(reinterpret_cast<const float*>(E.resid), n, i0, j0, in);
+    __syncthreads();
+    const int tx0 = 8 * (threadIdx.x & 3), ty = threadIdx.x >> 2;
+    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll 1
+    for (int b = 0; b < KT; ++b) psf_row_t<KT, false>(&in[ty + b][tx0], kw + b * PsfT<KT>::KP, acc);
+    const float sc = E.dlogL ? (float)(*E.dlogL) : 1.0f;
+    const int j = j0 + ty;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        const int i = i0 + tx0 + u;
+        if (i < n && j < n) reinterpret_cast<float*>(E.gimg)[j * n + i] = acc[u] * sc;
+    }
+}
+
 // log L = -1/2 sum r^2 - N log(sigma sqrt(2 pi)); chi^2_img = sum_mask r^2 / N_mask
 __global__ void __launch_bounds__(256) k_like_final(const __grid_constant__ Batch B) {
     const EvalArgs& E = B.e[blockIdx.x];

@@ -204,6 +204,7 @@ struct RenderShared {
     double trd[TR_HDR + 4 * (MAXM + 2)];
     double Ud[MAXM + 2];
     T offx[8];                 // sub-ray offsets ((a + 1/2)/s - 1/2) pix
+    UDiv dv_s2, dv_n, dv_s, dv_nc;   // dividers by s^2, n_img, s, n_src - 1
 };
 
 template <typename T>
@@ -215,6 +216,12 @@ __device__ __forceinline__ void render_setup(const EvalArgs& E, RenderShared<T>&
     }
     load_transform<T>(E, sh.trs, sh.U);
     if (threadIdx.x < E.s) sh.offx[threadIdx.x] = (T)(((threadIdx.x + 0.5) / E.s - 0.5) * E.pix);
+    if (threadIdx.x == 0) {
+        sh.dv_s2 = udiv_make((uint32_t)(E.s * E.s));
+        sh.dv_n = udiv_make((uint32_t)E.n_img);
+        sh.dv_s = udiv_make((uint32_t)E.s);
+        sh.dv_nc = udiv_make((uint32_t)(E.n_src - 1));
+    }
 }
 
 // S7 + S11: one thread per image pixel, s^2 sub-rays each.
@@ -231,10 +238,16 @@ __global__ void __launch_bounds__(CTA_R) k_render(const __grid_constant__ Batch 
     render_setup<T>(E, sh);
     __shared__ int cnt_sh;
     if (threadIdx.x == 0) cnt_sh = 0;
-    if (!stage_to_smem(sgrid, E.src, (uint32_t)(n * n * sizeof(T)), &mbar, E.flags)) return;
+    if (!stage_to_smem(sgrid, E.src, (uint32_t)(n * n * sizeof(T)), &mbar, E.flags)) {
+        // the copy timed out (flagged): this tile stages nothing
+        if (threadIdx.x < CTA_R / 32) E.useg[tile * (CTA_R / 32) + threadIdx.x] = 0;
+        if (threadIdx.x == 0) E.cta_cnt[tile] = 0;
+        return;
+    }
     const int npix = E.n_img * E.n_img;
     const int pixel = tile * CTA_R + threadIdx.x;
     const bool valid = pixel < npix;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     int nin = 0;                 // in-grid (or deferred) sub-rays of this pixel
     const T mux = sh.trs[0], muy = sh.trs[1], isg = T(1) / sh.trs[2];
     const T* Xx = sh.trs + TR_HDR;
@@ -251,14 +264,19 @@ __global__ void __launch_bounds__(CTA_R) k_render(const __grid_constant__ Batch 
         zlo[a] = X[0] - m / d[0];
         zhi[a] = X[K - 1] + m / d[K - 1];
     }
-    const int s = E.s, s2 = valid ? E.s * E.s : 0;
-    const int pj = pixel / E.n_img, pi = pixel - pj * E.n_img;
+    const int s = E.s, s2 = E.s * E.s;
+    const int pj = (int)udiv((uint32_t)pixel, sh.dv_n), pi = pixel - pj * E.n_img;
     const T pixT = (T)E.pix, cT = (T)(0.5 * (E.n_img - 1) * E.pix);
     const T cx = T(pi) * pixT - cT, cy = T(pj) * pixT - cT;
     T acc = T(0);
     unsigned long long deferred = 0ull;      // bit q: sub-ray q went to the double pass
-    for (int q = 0; q < s2; ++q) {
-        const int qb = q / s, qa = q - qb * s;
+    // this warp's staging segment: in-grid and deferred rays appended in (q, lane) order
+    const size_t ubase = ((size_t)tile * (CTA_R / 32) + wid) * 32 * s2;
+    int* stg = E.cell + ubase;
+    int wpos = 0;
+    // code of a sub-ray: -1 no cell, 0 deferred to the double pass, c + 1 in cell c
+    auto trace = [&](int q) -> int {
+        const int qb = (int)udiv((uint32_t)q, sh.dv_s), qa = q - qb * s;
         const T x = cx + sh.offx[qa], y = cy + sh.offx[qb];
         T yx, yy;
         if (sizeof(T) == 4 && lens_near_core(sh.K, x, y)) {
@@ -272,46 +290,52 @@ __global__ void __launch_bounds__(CTA_R) k_render(const __grid_constant__ Batch 
                 double fxd, fyd;
                 int i0, j0;
                 const int cell = cell_of<double>(ydx, ydy, n, fxd, fyd, i0, j0);
-                if (cell >= 0) {
-                    acc += bilinear_at<T, T>(sgrid, n, i0, j0, (T)fxd, (T)fyd);
-                    atomicAdd(E.ccount + cell, 1);
-                    ++nin;
-                }
-                E.cell[(size_t)pixel * s2 + q] = cell;
-                continue;
+                if (cell < 0) return -1;
+                acc += bilinear_at<T, T>(sgrid, n, i0, j0, (T)fxd, (T)fyd);
+                atomicAdd(E.ccount + cell, 1);
+                ++nin;
+                return cell + 1;
             }
         } else {
             T bx, by;
             lens_beta(sh.K, x, y, bx, by);
             const T zx = (bx - mux) * isg, zy = (by - muy) * isg;
-            if (zx < zlo[0] || zx > zhi[0] || zy < zlo[1] || zy > zhi[1]) {
-                // far outside the grid (beyond the near-edge margin): no cell, zero source
-                E.cell[(size_t)pixel * s2 + q] = -1;
-                continue;
-            }
+            // far outside the grid (beyond the near-edge margin): no cell, zero source
+            if (zx < zlo[0] || zx > zhi[0] || zy < zlo[1] || zy > zhi[1]) return -1;
             yx = cdf_value<T>(Xx, sh.U, dx_, K, cdf_interval<T>(Xx, K, zx), zx);
             yy = cdf_value<T>(Xy, sh.U, dy_, K, cdf_interval<T>(Xy, K, zy), zy);
             if (sizeof(T) == 4 && near_edge((float)(yx * T(n - 1)), (float)(yy * T(n - 1)), n)) {
-                const int at = atomicAdd(E.ecount, 1);
-                reinterpret_cast<int*>(E.rec)[at] = pixel * s2 + q;
-                E.cell[(size_t)pixel * s2 + q] = -1;
                 deferred |= 1ull << q;
-                ++nin;               // may turn out in-grid: the compaction checks the cell
-                continue;
+                ++nin;               // may turn out outside: k_render_edge takes it back
+                return 0;
             }
         }
         T fx, fy;
         int i0, j0;
         const int cell = cell_of<T>(yx, yy, n, fx, fy, i0, j0);
-        if (cell >= 0) {
-            acc += bilinear_at<T, T>(sgrid, n, i0, j0, fx, fy);
-            atomicAdd(E.ccount + cell, 1);
-            ++nin;
+        if (cell < 0) return -1;
+        acc += bilinear_at<T, T>(sgrid, n, i0, j0, fx, fy);
+        atomicAdd(E.ccount + cell, 1);
+        ++nin;
+        return cell + 1;
+    };
+    for (int q = 0; q < s2; ++q) {
+        const int code = valid ? trace(q) : -1;
+        const unsigned m = __ballot_sync(0xffffffffu, code >= 0);
+        if (code >= 0) {
+            const int pos = wpos + __popc(m & ((1u << lane) - 1u));
+            stg[pos] = (lane * s2 + q) | (code << STG_SHIFT);
+            if (code == 0) {
+                // the double pass finds the ray through its staging position
+                const int at = atomicAdd(E.ecount, 1);
+                reinterpret_cast<int*>(E.rec)[at] = (int)(ubase + pos);
+            }
         }
-        E.cell[(size_t)pixel * s2 + q] = cell;
+        wpos += __popc(m);
     }
+    if (lane == 0) E.useg[tile * (CTA_R / 32) + wid] = wpos;
     // in-grid rays of the CTA (deferred rays counted; k_render_edge takes back the
-    // ones that end outside), for the compaction of the adjoint's rays
+    // ones that end outside): the N_IN_GRID statistic
     atomicAdd(&cnt_sh, nin);
     __syncthreads();
     if (threadIdx.x == 0) E.cta_cnt[tile] = cnt_sh;
@@ -339,8 +363,11 @@ __global__ void __launch_bounds__(EDGE_NT) k_render_edge(const __grid_constant__
     const int n = E.n_src, K = E.n_nodes + 2, s2 = E.s * E.s;
     const int cnt = min(*E.ecount, E.n_img * E.n_img * s2);
     const float* grid = reinterpret_cast<const float*>(E.src);
+    const int cap = 32 * s2;                 // staged entries per render warp
     for (int k = tile * EDGE_NT + threadIdx.x; k < cnt; k += EDGE_CTAS * EDGE_NT) {
-        const int ray = reinterpret_cast<const int*>(E.rec)[k];
+        const int at = reinterpret_cast<const int*>(E.rec)[k];     // staging position
+        const int local = E.cell[at] & ((1 << STG_SHIFT) - 1);
+        const int ray = (at / cap) * cap + local;
         const int pixel = ray / s2, q = ray - pixel * s2;
         double xd, yd, yx, yy;
         ray_pos(E.n_img, E.pix, E.s, pixel, q, xd, yd);
@@ -352,10 +379,10 @@ __global__ void __launch_bounds__(EDGE_NT) k_render_edge(const __grid_constant__
         if (cell >= 0) {
             v = bilinear_at<float, float>(grid, n, i0, j0, (float)fx, (float)fy);
             atomicAdd(E.ccount + cell, 1);
+            E.cell[at] = local | ((cell + 1) << STG_SHIFT);
         } else {
             atomicSub(E.cta_cnt + pixel / CTA_R, 1);
         }
-        E.cell[ray] = cell;
         E.rval[ray] = v;
     }
 }
@@ -443,56 +470,42 @@ __global__ void __launch_bounds__(SCAN_NT) k_scan_cells(const __grid_constant__ 
         if (c < nc) { off[c] = base; base += E.ccount[c]; E.cursor[c] = 0; }
     }
     if (tid == SCAN_NT - 1) off[nc] = base;
-    // exclusive scan of the per-render-CTA in-grid counts
+    // exclusive scan of the per-render-warp staged counts
     __syncthreads();
-    block_exclusive_scan(E.cta_cnt, E.n_cta_r, wtot);
+    block_exclusive_scan(E.useg, E.n_cta_r * (CTA_R / 32), wtot);
 }
 
-// compaction of the in-grid rays in ray order: one CTA per render tile; the
-// tile's rays are taken CTA_R at a time (coalesced loads), ranked by a ballot
-// scan and appended in order
-__global__ void __launch_bounds__(CTA_R) k_compact(const __grid_constant__ Batch B) {
-    const int ev = find_eval(B, blockIdx.x);
-    const EvalArgs& E = B.e[ev];
-    const int tile = blockIdx.x - B.tile0[ev];
-    const int npix = E.n_img * E.n_img, s2 = E.s * E.s;
-    const int ncell = (E.n_src - 1) * (E.n_src - 1);
-    const int* off = E.ccount + ncell;
-    const int r0 = tile * CTA_R * s2;
-    const int r1 = min(npix, (tile + 1) * CTA_R) * s2;
-    __shared__ int wcnt[CTA_R / 32];
-    __shared__ int run;
-    if (threadIdx.x == 0) run = E.cta_cnt[tile];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int base = r0; base < r1; base += CTA_R) {
-        const int ray = base + threadIdx.x;
-        const int c = ray < r1 ? E.cell[ray] : -1;
-        const bool in = c >= 0;
-        const unsigned m = __ballot_sync(0xffffffffu, in);
-        if (lane == 0) wcnt[wid] = __popc(m);
-        __syncthreads();
-        int pos = run;
-        for (int w = 0; w < wid; ++w) pos += wcnt[w];
-        pos += __popc(m & ((1u << lane) - 1u));
-        if (in) {
-            E.ids[pos] = ray;
-            E.kcell[pos] = c;
-            // the ray's record slot in the counting sort by cell (integer cursor)
-            E.kslot[pos] = c < ncell ? off[c] + atomicAdd(E.cursor + c, 1) : -1;
+// The adjoint's rays: the staged rays of all render warps, numbered in warp order
+// (k = useg[u] + position in warp u).  Finds the warp u of ray k -- advancing
+// from a previous u of a smaller k when u >= 0, else by bisection -- and decodes
+// the ray id and its cell (-1: a deferred ray that ended outside).
+__device__ __forceinline__ void staged_ray(const EvalArgs& E, int nu, int cap, int k, int& u, int& ray,
+                                           int& cell) {
+    const int* us = E.useg;
+    if (u < 0) {
+        int lo = 0, hi = nu;                 // us[lo] <= k < us[hi]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (us[mid] <= k) lo = mid; else hi = mid;
         }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            int t = 0;
-            for (int w = 0; w < CTA_R / 32; ++w) t += wcnt[w];
-            run += t;
-        }
-        __syncthreads();
+        u = lo;
+    } else {
+        while (us[u + 1] <= k) ++u;
     }
+    const int pos = k - us[u];
+    if (pos < 0 || pos >= cap) {             // offsets not from a forward pass on this slot
+        ray = 0;
+        cell = -1;
+        return;
+    }
+    const int e = E.cell[(size_t)u * cap + pos];
+    ray = u * cap + min(e & ((1 << STG_SHIFT) - 1), cap - 1);
+    cell = (e >> STG_SHIFT) - 1;
 }
 
-// S9 (image -> source/transform/lens part) over the compacted in-grid rays (ray
-// order): a grid-stride loop gives every CTA a fixed set of chunks, each thread
-// ADJ_RPT consecutive rays per chunk.  Each ray is recomputed (value + the EPL
+// S9 (image -> source/transform/lens part) over the staged in-grid rays (render
+// warp order): a grid-stride loop gives every CTA a fixed set of chunks of
+// CTA_R x ADJ_RPT rays, thread t taking rays t, t + CTA_R, ... of a chunk.  Each ray is recomputed (value + the EPL
 // series sums) and differentiated analytically; its cell comes from the forward
 // pass.  Writes one counting-sorted record per ray and fixed-order per-CTA
 // partial sums of the lens, standardisation and spline-knot gradients.
@@ -526,7 +539,9 @@ __global__ void __launch_bounds__(CTA_R, 4) k_render_adj(const __grid_constant__
     }
     const int s = E.s, s2 = s * s;
     const int nsub = sh.K.nsub;
-    const int total = E.cta_cnt[E.n_cta_r];
+    const int nu = E.n_cta_r * (CTA_R / 32), cap = 32 * E.s * E.s;
+    const int total = min(E.useg[nu], min(nu * cap, E.n_img * E.n_img * E.s * E.s));
+    const int ncell = nc * nc;
     const T mux = sh.trs[0], muy = sh.trs[1], isg = T(1) / sh.trs[2];
     const T* Xa[2] = {sh.trs + TR_HDR, sh.trs + TR_HDR + K};
     const T* Da[2] = {sh.trs + TR_HDR + 2 * K, sh.trs + TR_HDR + 3 * K};
@@ -546,43 +561,54 @@ __global__ void __launch_bounds__(CTA_R, 4) k_render_adj(const __grid_constant__
     T ca[2][4] = {{T(0), T(0), T(0), T(0)}, {T(0), T(0), T(0), T(0)}};
     TP* mytab = tab + wid * 4 * K;
 
+    // merge the running knot partials of the lanes that leave their interval:
+    // one fixed-order warp sum per distinct interval among those lanes
     auto flush = [&](int a, bool need) {
         unsigned m = __ballot_sync(0xffffffffu, need);
         while (m) {
-            const int l = __ffs(m) - 1;
-            if (lane == l) {
+            const int key = __shfl_sync(0xffffffffu, cj[a], __ffs(m) - 1);
+            const bool in = need && cj[a] == key;
+            m &= ~__ballot_sync(0xffffffffu, in);
+            T v0 = in ? ca[a][0] : T(0), v1 = in ? ca[a][1] : T(0);
+            T v2 = in ? ca[a][2] : T(0), v3 = in ? ca[a][3] : T(0);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                v0 += __shfl_down_sync(0xffffffffu, v0, o);
+                v1 += __shfl_down_sync(0xffffffffu, v1, o);
+                v2 += __shfl_down_sync(0xffffffffu, v2, o);
+                v3 += __shfl_down_sync(0xffffffffu, v3, o);
+            }
+            if (lane == 0) {
                 TP* tX = mytab + a * K;
                 TP* tD = mytab + 2 * K + a * K;
-                const int j = cj[a];
-                if (j >= 0) { pair_add(tX[j], ca[a][0]); pair_add(tD[j], ca[a][2]); }
-                if (j + 1 <= K - 1) { pair_add(tX[j + 1], ca[a][1]); pair_add(tD[j + 1], ca[a][3]); }
+                if (key >= 0) { pair_add(tX[key], v0); pair_add(tD[key], v2); }
+                if (key + 1 <= K - 1) { pair_add(tX[key + 1], v1); pair_add(tD[key + 1], v3); }
             }
-            __syncwarp();
-            m &= m - 1;
         }
+        __syncwarp();
         if (need) { ca[a][0] = ca[a][1] = ca[a][2] = ca[a][3] = T(0); }
     };
 
     const int chunk = CTA_R * ADJ_RPT;
     for (int base = tile * chunk; base < total; base += E.n_cta_adj * chunk) {
+        int u = -1;
         for (int r = 0; r < ADJ_RPT; ++r) {
-            const int k = base + threadIdx.x * ADJ_RPT + r;
+            // coalesced: the CTA's threads take consecutive rays; a thread's rays
+            // are CTA_R apart, i.e. from nearby pixels (mostly the same intervals)
+            const int k = base + r * CTA_R + threadIdx.x;
             int jn[2] = {cj[0], cj[1]};
             T pn[2][4];
             bool have = false;
             int cell = -1, ray = 0;
-            int slot = -1;
             if (k < total) {
-                ray = E.ids[k];
-                cell = E.kcell[k];
-                slot = E.kslot[k];
-                if (cell >= nc * nc) cell = -1;      // only a forward pass on this slot writes cells
+                staged_ray(E, nu, cap, k, u, ray, cell);
+                if (cell >= ncell) cell = -1;        // only a forward pass on this slot stages rays
             }
             T gb0 = T(0), gb1 = T(0);
             if (cell >= 0) {
-                const int pixel = ray / s2, q = ray - pixel * s2;
-                const int pj = pixel / E.n_img, pi = pixel - pj * E.n_img;
-                const int qb = q / s, qa = q - qb * s;
+                const int pixel = (int)udiv((uint32_t)ray, sh.dv_s2), q = ray - pixel * s2;
+                const int pj = (int)udiv((uint32_t)pixel, sh.dv_n), pi = pixel - pj * E.n_img;
+                const int qb = (int)udiv((uint32_t)q, sh.dv_s), qa = q - qb * s;
                 const T x = (T(pi) * pixT - cT) + sh.offx[qa];
                 const T y = (T(pj) * pixT - cT) + sh.offx[qb];
                 const T gpix = gimg[pixel] * inv_s2;
@@ -607,7 +633,7 @@ __global__ void __launch_bounds__(CTA_R, 4) k_render_adj(const __grid_constant__
                     yv[a] = cdf_grad<T>(Xa[a], sh.U, Da[a], K, jn[a], z[a], dz[a], pn[a][0], pn[a][1], pn[a][2],
                                         pn[a][3]);
                 }
-                const int i0 = cell % nc, j0 = cell / nc;
+                const int j0 = (int)udiv((uint32_t)cell, sh.dv_nc), i0 = cell - j0 * nc;
                 const T fx = yv[0] * nm1 - T(i0), fy = yv[1] * nm1 - T(j0);
                 const T* r0 = sgrid + j0 * n + i0;
                 const T dsdx = nm1 * ((T(1) - fy) * (r0[1] - r0[0]) + fy * (r0[n + 1] - r0[n]));
@@ -630,7 +656,9 @@ __global__ void __launch_bounds__(CTA_R, 4) k_render_adj(const __grid_constant__
                 for (int a = 0; a < 2; ++a)
                     for (int c = 0; c < 4; ++c) pn[a][c] *= gy[a];
                 have = true;
-                if (slot >= 0 && slot < off[cell + 1] && slot < E.n_img * E.n_img * s2) {
+                // the ray's record slot in the counting sort by cell (integer cursor)
+                const int slot = off[cell] + atomicAdd(E.cursor + cell, 1);
+                if (slot < off[cell + 1]) {
                     R4 rr;
                     rr.x = fx; rr.y = fy; rr.z = gpix; rr.w = T(0);
                     rec[slot] = rr;
@@ -689,7 +717,8 @@ __global__ void __launch_bounds__(CTA_R) k_sub_adj(const __grid_constant__ Batch
     const int Kn = E.n_nodes + 2;
     const int nacc = NACC_FIX + 4 * Kn + 5 * K.nsub;
     double* out = E.apart + (size_t)tile * nacc;
-    const int total = E.cta_cnt[E.n_cta_r];
+    const int nu = E.n_cta_r * (CTA_R / 32), cap = 32 * E.s * E.s;
+    const int total = min(E.useg[nu], min(nu * cap, E.n_img * E.n_img * E.s * E.s));
     const int s = E.s, s2 = s * s;
     const T pixT = (T)E.pix, cT = (T)(0.5 * (E.n_img - 1) * E.pix);
     const R2* gbuf = reinterpret_cast<const R2*>(E.gbuf);
@@ -698,12 +727,14 @@ __global__ void __launch_bounds__(CTA_R) k_sub_adj(const __grid_constant__ Batch
     for (int h = 0; h < K.nsub; ++h) {
         T a5[5] = {T(0), T(0), T(0), T(0), T(0)};
         for (int base = tile * chunk; base < total; base += E.n_cta_adj * chunk) {
+            int u = -1;
             for (int r = 0; r < ADJ_RPT; ++r) {
-                const int k = base + threadIdx.x * ADJ_RPT + r;
+                const int k = base + r * CTA_R + threadIdx.x;
                 if (k >= total) continue;
                 const R2 g = gbuf[k];
                 if (g.x == T(0) && g.y == T(0)) continue;
-                const int ray = E.ids[k];
+                int ray, cell;
+                staged_ray(E, nu, cap, k, u, ray, cell);
                 const int pixel = ray / s2, q = ray - pixel * s2;
                 const int pj = pixel / E.n_img, pi = pixel - pj * E.n_img;
                 const T x = (T(pi) * pixT - cT) + offx[q % s];

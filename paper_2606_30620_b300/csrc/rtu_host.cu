@@ -84,8 +84,8 @@ Sizes sizes_of(const rtu_system_desc& d) {
     z.K = d.n_nodes + 2;
     z.ncell = (d.n_src - 1) * (d.n_src - 1);
     z.n_rays = d.n_img * d.n_img * d.s_super * d.s_super;
-    // the adjoint's grid-stride CTAs: one chunk each when a sixteenth of the rays is in the grid
-    z.n_cta_adj = std::max(1, (z.n_rays + 16 * CTA_R * ADJ_RPT - 1) / (16 * CTA_R * ADJ_RPT));
+    // the adjoint's grid-stride CTAs: one chunk each when an eighth of the rays is in the grid
+    z.n_cta_adj = std::max(1, (z.n_rays + 8 * CTA_R * ADJ_RPT - 1) / (8 * CTA_R * ADJ_RPT));
     const int nsub = d.sub_kind ? d.n_sub : 0;
     z.nacc = NACC_FIX + 4 * z.K + 5 * nsub;
     z.nl = 8 + 5 * nsub;
@@ -112,7 +112,6 @@ size_t slot_layout(const rtu_system_desc& d, char* base, EvalArgs* e) {
     p = take((size_t)tr_size(z.K) * 8);               if (e) e->trd = (double*)p;
     p = take((size_t)tr_size(z.K) * 4);               if (e) e->trf = (float*)p;
     p = take((size_t)4 * MAXM * 4);                   if (e) e->sel_idx = (int*)p;
-    p = take((size_t)4 * MAXM * 8);                   if (e) e->sel_val = (double*)p;
     p = take((size_t)(TADJ_SEL + 4 * MAXM) * 8);      if (e) e->tadj = (double*)p;
     const size_t n2 = (size_t)d.n_src * d.n_src;
     p = take(n2 * 2 * z.tb);                          if (e) e->cbufA = p;
@@ -124,7 +123,7 @@ size_t slot_layout(const rtu_system_desc& d, char* base, EvalArgs* e) {
     p = take(ni * z.tb);                              if (e) e->resid = p;
     p = take(ni * z.tb);                              if (e) e->gimg = p;
     p = take((size_t)z.n_cta_p * 2 * 8);              if (e) e->lpart = (double*)p;
-    p = take((size_t)z.n_rays * 4);                   if (e) e->cell = (int*)p;
+    p = take((size_t)z.n_cta_r * CTA_R * d.s_super * d.s_super * 4); if (e) e->cell = (int*)p;
     p = take((size_t)(2 * z.ncell + 1) * 4);          if (e) e->ccount = (int*)p;
     p = take((size_t)z.ncell * 4);                    if (e) e->cursor = (int*)p;
     p = take((size_t)z.n_rays * 4 * z.tb);            if (e) e->rec = p;
@@ -136,9 +135,7 @@ size_t slot_layout(const rtu_system_desc& d, char* base, EvalArgs* e) {
     p = take(ni * 8);                                 if (e) e->pdef = (unsigned long long*)p;
     p = take((size_t)z.n_rays * 4);                   if (e) e->rval = (float*)p;
     p = take((size_t)(z.n_cta_r + 1) * 4);            if (e) e->cta_cnt = (int*)p;
-    p = take((size_t)z.n_rays * 4);                   if (e) e->ids = (int*)p;
-    p = take((size_t)z.n_rays * 4);                   if (e) e->kcell = (int*)p;
-    p = take((size_t)z.n_rays * 4);                   if (e) e->kslot = (int*)p;
+    p = take((size_t)(z.n_cta_r * (CTA_R / 32) + 1) * 4); if (e) e->useg = (int*)p;
     p = take((size_t)z.n_rays * 2 * z.tb);            if (e) e->gbuf = p;
     return o;
 }
@@ -438,6 +435,7 @@ rtu_status launch(const char* name, Kern kern, Batch& B, TileFn tiles, int threa
 }
 
 int t_one(const EvalArgs&) { return 1; }
+int t_two(const EvalArgs&) { return 2; }
 int t_zero(const EvalArgs&) { return ZERO_TILES; }
 int t_centre(const EvalArgs& e) { return e.n_cta_c; }
 int t_render(const EvalArgs& e) { return e.n_cta_r; }
@@ -452,46 +450,97 @@ int t_cells(const EvalArgs& e) {
 
 enum Phase { PH_GRID = 1, PH_FORWARD = 2, PH_ADJOINT = 4 };
 
+// A second stream per (host thread, device) for the steps that do not depend on
+// the main chain: the GP source beside the grid build, the transform/centre-ray
+// adjoint beside the cell gather and GP adjoint.  Fork and join are event waits,
+// so a call still orders everything after the work already on the caller's
+// stream and leaves nothing pending on the side stream when it returns (and the
+// pattern is legal inside CUDA graph capture).  Created at the first call on a
+// device and kept for the life of the thread.
+struct SideStream {
+    cudaStream_t s = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+};
+constexpr int MAX_DEV = 64;
+
+rtu_status side_stream(SideStream*& out) {
+    static thread_local SideStream tab[MAX_DEV];
+    int dev = 0;
+    cudaError_t ce = cudaGetDevice(&dev);
+    if (ce != cudaSuccess) return fail(RTU_E_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(ce));
+    if (dev < 0 || dev >= MAX_DEV) return fail(RTU_E_ARG, "device index too large");
+    SideStream& ss = tab[dev];
+    if (!ss.s) {
+        if ((ce = cudaStreamCreateWithFlags(&ss.s, cudaStreamNonBlocking)) != cudaSuccess ||
+            (ce = cudaEventCreateWithFlags(&ss.fork, cudaEventDisableTiming)) != cudaSuccess ||
+            (ce = cudaEventCreateWithFlags(&ss.join, cudaEventDisableTiming)) != cudaSuccess)
+            return fail(RTU_E_CUDA, std::string("side stream: ") + cudaGetErrorString(ce));
+    }
+    out = &ss;
+    return RTU_OK;
+}
+
+// after: `to` runs behind everything enqueued so far on `from`
+rtu_status stream_after(cudaStream_t to, cudaStream_t from, cudaEvent_t ev) {
+    cudaError_t ce = cudaEventRecord(ev, from);
+    if (ce == cudaSuccess) ce = cudaStreamWaitEvent(to, ev, 0);
+    return ce == cudaSuccess ? RTU_OK : fail(RTU_E_CUDA, std::string("stream order: ") + cudaGetErrorString(ce));
+}
+
 template <typename T>
-rtu_status run_chunk(Batch& B, int phase, cudaStream_t st) {
+rtu_status run_chunk(Batch& B, int phase, cudaStream_t st, const SideStream& ss) {
     rtu_status r;
-    int max_n2 = 0, max_s2 = 0, any_sub = 0, maxK = 0;
+    int max_n2 = 0, max_s2 = 0, any_sub = 0, maxK = 0, maxPsf = 0;
     for (int i = 0; i < B.n; ++i) {
+        maxPsf = std::max(maxPsf, B.e[i].psf_k);
         max_n2 = std::max(max_n2, B.e[i].n_src * B.e[i].n_src);
         max_s2 = std::max(max_s2, B.e[i].s * B.e[i].s);
         any_sub |= (B.e[i].sub_kind && B.e[i].n_sub > 0);
         maxK = std::max(maxK, B.e[i].n_nodes + 2);
     }
     const size_t grid_bytes = align_up((size_t)max_n2 * sizeof(T), 128);
+    if (phase & PH_FORWARD) {
+        // S6 only needs the latents and spectrum parameters: beside S1-S5
+        if ((r = stream_after(ss.s, st, ss.fork))) return r;
+        if ((r = launch("k_gp_source", k_gp_source<T>, B, t_one, GP_NT, GP_SMEM, ss.s))) return r;
+    }
     if (phase & (PH_GRID | PH_FORWARD)) {
         if ((r = launch("k_zero", k_zero, B, t_zero, 256, 0, st, (phase & PH_FORWARD) ? 1 : 0))) return r;
         if ((r = launch("k_trace_centres", k_trace_centres, B, t_centre, CTA_C, 0, st))) return r;
         if ((r = launch("k_centre_hist", k_centre_hist, B, t_centre, CTA_C, 0, st))) return r;
-        if ((r = launch("k_select_fit", k_select_fit, B, t_one, SEL_NT, SEL_SMEM, st))) return r;
+        if ((r = launch("k_select_fit", k_select_fit, B, t_two, SEL_NT, SEL_SMEM, st))) return r;
     }
     if (phase & PH_FORWARD) {
-        if ((r = launch("k_gp_source", k_gp_source<T>, B, t_one, GP_NT, GP_SMEM, st))) return r;
+        if ((r = stream_after(st, ss.s, ss.join))) return r;
         if (grid_bytes > MAX_DYN) return fail(RTU_E_ARG, "source grid too large for shared memory");
         if ((r = launch("k_render", k_render<T>, B, t_render, CTA_R, grid_bytes, st))) return r;
         if (sizeof(T) == 4) {
             if ((r = launch("k_render_edge", k_render_edge, B, t_edge, EDGE_NT, 0, st))) return r;
             if ((r = launch("k_render_fix", k_render_fix, B, t_fix, 256, 0, st))) return r;
         }
-        if ((r = launch("k_psf_like", k_psf_like<T>, B, t_psf, PSF_NT, 0, st))) return r;
+        if (sizeof(T) == 4 && maxPsf <= 9) r = launch("k_psf_like", k_psf_like_t<9>, B, t_psf, PSFT_NT, 0, st);
+        else if (sizeof(T) == 4 && maxPsf <= 21) r = launch("k_psf_like", k_psf_like_t<21>, B, t_psf, PSFT_NT, 0, st);
+        else r = launch("k_psf_like", k_psf_like<T>, B, t_psf, PSF_NT, 0, st);
+        if (r) return r;
         if ((r = launch("k_like_final", k_like_final, B, t_one, 256, 0, st))) return r;
     }
     if (phase & PH_ADJOINT) {
-        if ((r = launch("k_psf_adj", k_psf_adj<T>, B, t_psf, PSF_NT, 0, st))) return r;
+        if (sizeof(T) == 4 && maxPsf <= 9) r = launch("k_psf_adj", k_psf_adj_t<9>, B, t_psf, PSFT_NT, 0, st);
+        else if (sizeof(T) == 4 && maxPsf <= 21) r = launch("k_psf_adj", k_psf_adj_t<21>, B, t_psf, PSFT_NT, 0, st);
+        else r = launch("k_psf_adj", k_psf_adj<T>, B, t_psf, PSF_NT, 0, st);
+        if (r) return r;
         if ((r = launch("k_scan_cells", k_scan_cells, B, t_one, SCAN_NT, 0, st))) return r;
         const size_t adj = grid_bytes + (size_t)(CTA_R / 32) * 4 * maxK * 2 * sizeof(T);
         if (adj > MAX_DYN) return fail(RTU_E_ARG, "adjoint shared memory exceeds the limit");
-        if ((r = launch("k_compact", k_compact, B, t_render, CTA_R, 0, st))) return r;
         if ((r = launch("k_render_adj", k_render_adj<T>, B, t_adj, CTA_R, adj, st))) return r;
         if (any_sub && (r = launch("k_sub_adj", k_sub_adj<T>, B, t_adj, CTA_R, 0, st))) return r;
+        // transform and centre-ray adjoint (side) beside the cell gather and GP adjoint (main)
+        if ((r = stream_after(ss.s, st, ss.fork))) return r;
+        if ((r = launch("k_cdf_adj", k_cdf_adj, B, t_two, CDF_NT, 0, ss.s))) return r;
+        if ((r = launch("k_centre_adj", k_centre_adj<T>, B, t_centre, CTA_C, 0, ss.s))) return r;
         if ((r = launch("k_cell_gather", k_cell_gather<T>, B, t_cells, GATHER_NT, 0, st))) return r;
-        if ((r = launch("k_cdf_adj", k_cdf_adj, B, t_one, CDF_NT, 0, st))) return r;
-        if ((r = launch("k_centre_adj", k_centre_adj<T>, B, t_centre, CTA_C, 0, st))) return r;
         if ((r = launch("k_gp_adjoint", k_gp_adjoint<T>, B, t_one, GP_NT, GP_SMEM, st))) return r;
+        if ((r = stream_after(st, ss.s, ss.join))) return r;
         if ((r = launch("k_grad_final", k_grad_final, B, t_one, 64, 0, st))) return r;
     }
     return RTU_OK;
@@ -508,6 +557,8 @@ rtu_status run(rtu_system* const* sys, const rtu_eval* ev, int n, int phase, voi
             return fail(RTU_E_ARG, "adjoint outputs g_latents, g_lens, g_ps must be set");
     }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    SideStream* ss = nullptr;
+    if (rtu_status r = side_stream(ss)) return r;
     static thread_local Batch B;
     for (int c0 = 0; c0 < n; c0 += MAXB) {
         B.n = std::min(MAXB, n - c0);
@@ -515,7 +566,7 @@ rtu_status run(rtu_system* const* sys, const rtu_eval* ev, int n, int phase, voi
             rtu_status r = fill_args(sys[c0 + i], ev[c0 + i], B.e[i]);
             if (r) return r;
         }
-        rtu_status r = prec == RTU_F64 ? run_chunk<double>(B, phase, st) : run_chunk<float>(B, phase, st);
+        rtu_status r = prec == RTU_F64 ? run_chunk<double>(B, phase, st, *ss) : run_chunk<float>(B, phase, st, *ss);
         if (r) return r;
     }
     return RTU_OK;

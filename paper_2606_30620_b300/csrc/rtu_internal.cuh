@@ -19,7 +19,8 @@ constexpr int MAXM = 64;          // max Chebyshev nodes
 constexpr int MAX_RADIX = 12;     // max FFT stages
 constexpr int CTA_C = 256;        // centre-ray kernels: rays per CTA
 constexpr int CTA_R = 128;        // render kernels: pixels per CTA (one thread each)
-constexpr int ADJ_RPT = 4;        // render adjoint: compacted rays per thread per chunk
+constexpr int STG_SHIFT = 11;      // staged entry: low bits the ray within its render warp (< 32 * 64)
+constexpr int ADJ_RPT = 16;        // render adjoint: compacted rays per thread per chunk
 constexpr int PSF_T = 32;         // PSF kernels: 32 x 32 output tile per CTA (4 outputs per thread)
 constexpr int NACC_FIX = 11;      // render-adjoint partials: 8 lens + mu_x, mu_y, sigma
 
@@ -65,7 +66,6 @@ struct EvalArgs {
     double* trd;       // transform, double (layout in tr_* helpers)
     float* trf;        // transform, float copy
     int* sel_idx;      // [2][2 MAXM] centre-ray index at each selected rank
-    double* sel_val;   // [2][2 MAXM]
     double* tadj;      // transform adjoint block
     void* cbufA;       // complex real2 [n_src^2]
     void* cbufB;       // complex real2 [n_src^2]
@@ -75,7 +75,9 @@ struct EvalArgs {
     void* resid;       // real [n_img^2] (d - m)/sigma^2
     void* gimg;        // real [n_img^2] d L / d image
     double* lpart;     // [n_cta_p][2]
-    int* cell;         // [n_rays] RTU cell of every supersampled ray (-1 outside)
+    int* cell;         // staged in-grid rays: render warp u owns [u*32*s^2, (u+1)*32*s^2), entries
+                       // (lane*s^2 + q) | (cell + 1) << STG_SHIFT in append order; cell + 1 = 0
+                       // while a deferred ray is undecided, and after it ended outside
     int* ccount;       // [n_cells] ray counts, then [n_cells + 1] exclusive offsets
     int* cursor;       // [n_cells]
     void* rec;         // real4 [n_rays] counting-sorted (fx, fy, g, -) records
@@ -86,11 +88,9 @@ struct EvalArgs {
     int* ecount;       // number of deferred near-edge rays (float mode)
     unsigned long long* pdef;  // [n_img^2] bit q: sub-ray q deferred to the double pass (float mode)
     float* rval;       // [n_rays] values of deferred rays (float mode)
-    int* cta_cnt;      // [n_cta_r + 1] in-grid rays per render CTA, then exclusive offsets
-    int* ids;          // [n_rays] in-grid ray ids in ray order (compacted)
-    int* kcell;        // [n_rays] cell of each compacted ray
-    int* kslot;        // [n_rays] counting-sorted record slot of each compacted ray
-    void* gbuf;        // real2 [n_rays] d logL / d beta of each compacted ray (subhalo pass)
+    int* cta_cnt;      // [n_cta_r] in-grid rays per render CTA (the N_IN_GRID statistic)
+    int* useg;         // [n_cta_r * CTA_R/32 + 1] staged rays per render warp, then exclusive offsets
+    void* gbuf;        // real2 [n_rays] d logL / d beta of each staged ray (subhalo pass)
     int n_cta_adj;     // CTAs of the render adjoint (grid-stride over the compacted rays)
 };
 
@@ -303,8 +303,13 @@ __device__ inline void lens_setup_par(LensK<double>* Kd, LensK<float>* Kf, const
         for (int n = 1; n <= EPL_MAXT; ++n) {
             a *= sc[n - 1];
             D += sdl[n - 1];
-            if (dbl) { Kd->C.cn[n - 1] = sc[n - 1]; Kd->C.gn[n - 1] = sg[n - 1]; Kd->C.Dn[n - 1] = D; }
-            else { Kf->C.cn[n - 1] = (float)sc[n - 1]; Kf->C.gn[n - 1] = (float)sg[n - 1]; Kf->C.Dn[n - 1] = (float)D; }
+            if (dbl) {
+                EplTerm<double>& tm = Kd->C.term[n - 1];
+                tm.c = sc[n - 1]; tm.ng = n * sg[n - 1]; tm.D = D; tm.pad_ = 0.0;
+            } else {
+                EplTerm<float>& tm = Kf->C.term[n - 1];
+                tm.c = (float)sc[n - 1]; tm.ng = (float)(n * sg[n - 1]); tm.D = (float)D; tm.pad_ = 0.0f;
+            }
             if (fabs(a) <= tol) { nt = n; break; }
         }
         if (dbl) {

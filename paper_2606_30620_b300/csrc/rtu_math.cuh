@@ -34,6 +34,32 @@ RTU_HD double r_atanh(double x){ return atanh(x); }
 RTU_HD float  r_abs(float x)   { return fabsf(x); }
 RTU_HD double r_abs(double x)  { return fabs(x); }
 
+// Unsigned division by a run-time invariant d (1 <= d < 2^32) as a multiply-high
+// and two shifts, exact for every 32-bit numerator: the round-up method of
+// Granlund & Montgomery, "Division by invariant integers using
+// multiplication" (PLDI 1994), Sec. 4 / Fig. 4.1, with N = 32.
+struct UDiv {
+    uint32_t m, s1, s2;
+};
+RTU_HD UDiv udiv_make(uint32_t d) {
+    uint32_t l = 0;
+    while (l < 32 && (1ull << l) < d) ++l;                 // l = ceil(log2 d)
+    const uint64_t mm = ((1ull << 32) * ((1ull << l) - d)) / d + 1;
+    UDiv u;
+    u.m = (uint32_t)mm;
+    u.s1 = l < 1 ? l : 1;
+    u.s2 = l > 1 ? l - 1 : 0;
+    return u;
+}
+RTU_HD uint32_t udiv(uint32_t n, const UDiv& u) {
+#ifdef __CUDA_ARCH__
+    const uint32_t t1 = __umulhi(u.m, n);
+#else
+    const uint32_t t1 = (uint32_t)(((uint64_t)u.m * n) >> 32);
+#endif
+    return (t1 + ((n - t1) >> u.s1)) >> u.s2;
+}
+
 // ------------------------------------------------------------ dual numbers
 // v + sum_i d[i] eps_i, eps_i eps_j = 0: forward-mode derivatives w.r.t. N seeds.
 template <typename T, int N>
@@ -271,13 +297,24 @@ RTU_HD void nfw_deflect(const S& x, const S& y, const S& ks, const S& rs,
 // (theta_E, gamma, e1, e2, x0, y0).
 constexpr int EPL_MAXT = 96;
 
+// one term of the series: c_n, n g_n (g_n = c_n / f), D_n; one 16-byte (float)
+// or two 16-byte (double) shared-memory loads per term
+template <typename T>
+struct __align__(16) EplTerm {
+    T c;      // c_n = -f (2n - 2 + t) / (2n + 2 - t), n = 1..nterm
+    T ng;     // n c_n / f
+    T D;      // D_n = sum_{k <= n} d log|c_k| / dt
+    T pad_;
+};
+
 template <typename T>
 struct EplC {
     T x0, y0, cp, sp, q, cc, e1, e2, thE, sq, b, t, pref0, lnb, opq;
+    // lens-only factors of the vector-Jacobian product: dF/dq through f,
+    // (t/b) db/dq, (t/b) db/dtheta_E, 1/(1+q), the (e1, e2) chain factors
+    T f_q, tb_bq, tb_sq, iopq, qe1, qe2, pe1, pe2;
     int nterm;
-    T cn[EPL_MAXT];   // c_n = -f (2n - 2 + t) / (2n + 2 - t), n = 1..nterm
-    T gn[EPL_MAXT];   // c_n / f
-    T Dn[EPL_MAXT];   // D_n = sum_{k <= n} d log|c_k| / dt
+    EplTerm<T> term[EPL_MAXT];
 };
 
 // the lens-only scalars of the series (everything but the term tables)
@@ -293,23 +330,27 @@ RTU_HD void epl_scalars(EplC<T>& C, const double* p, bool epl) {
     C.x0 = (T)p[4]; C.y0 = (T)p[5]; C.cp = (T)cos(phi); C.sp = (T)sin(phi); C.q = (T)q; C.cc = (T)cc;
     C.e1 = (T)e1; C.e2 = (T)e2; C.thE = (T)p[0]; C.sq = (T)sq; C.b = (T)b; C.t = (T)t;
     C.pref0 = (T)(2.0 * b / (1.0 + q)); C.lnb = (T)log(b); C.opq = (T)(1.0 + q);
+    const double opq = 1.0 + q, opc = 1.0 + cc;
+    const double q_c = -2.0 / (opc * opc);          // dq/dcc
+    C.f_q = (T)(-2.0 / (opq * opq));
+    C.tb_bq = (T)(t / b * p[0] / (2.0 * sq));
+    C.tb_sq = (T)(t / b * sq);
+    C.iopq = (T)(1.0 / opq);
+    C.qe1 = (T)(q_c * e1 / cc);
+    C.qe2 = (T)(q_c * e2 / cc);
+    C.pe1 = (T)(0.5 * e1 / (cc * cc));
+    C.pe2 = (T)(0.5 * e2 / (cc * cc));
 }
 
 // p = theta_E, gamma, e1, e2, x0, y0 (gamma ignored unless epl); tol = size of the
 // last summed term relative to the leading one
 template <typename T>
 RTU_HD void epl_setup(EplC<T>& C, const double* p, bool epl, double tol) {
-    const double e1 = p[2], e2 = p[3];
-    const double cc = sqrt(fmax(e1 * e1 + e2 * e2, 1e-30));
+    epl_scalars(C, p, epl);
+    const double cc = sqrt(fmax(p[2] * p[2] + p[3] * p[3], 1e-30));
     const double q = (1.0 - cc) / (1.0 + cc);
-    const double phi = 0.5 * atan2(e2, e1);
     const double t = (epl ? p[1] : 2.0) - 1.0;
     const double f = (1.0 - q) / (1.0 + q);
-    const double sq = sqrt(q);
-    const double b = p[0] * sq;
-    C.x0 = (T)p[4]; C.y0 = (T)p[5]; C.cp = (T)cos(phi); C.sp = (T)sin(phi); C.q = (T)q; C.cc = (T)cc;
-    C.e1 = (T)e1; C.e2 = (T)e2; C.thE = (T)p[0]; C.sq = (T)sq; C.b = (T)b; C.t = (T)t;
-    C.pref0 = (T)(2.0 * b / (1.0 + q)); C.lnb = (T)log(b); C.opq = (T)(1.0 + q);
     double a = 1.0, D = 0.0;
     int n = 1;
     for (; n <= EPL_MAXT; ++n) {
@@ -317,7 +358,7 @@ RTU_HD void epl_setup(EplC<T>& C, const double* p, bool epl, double tol) {
         const double c = f * g;
         D += 1.0 / (2.0 * n - 2.0 + t) + 1.0 / (2.0 * n + 2.0 - t);
         a *= c;
-        C.cn[n - 1] = (T)c; C.gn[n - 1] = (T)g; C.Dn[n - 1] = (T)D;
+        C.term[n - 1].c = (T)c; C.term[n - 1].ng = (T)(n * g); C.term[n - 1].D = (T)D; C.term[n - 1].pad_ = T(0);
         if (fabs(a) <= tol) break;
     }
     C.nterm = n > EPL_MAXT ? EPL_MAXT : n;
@@ -333,9 +374,10 @@ RTU_HD void epl_alpha(const EplC<T>& C, T x, T y, T& ax, T& ay) {
     const T wre = cre * cre - cim * cim, wim = T(2) * cre * cim;
     T tre = cre, tim = cim, sre = cre, sim = cim;
     for (int n = 0; n < C.nterm; ++n) {
+        const T c = C.term[n].c;
         const T nre = tre * wre - tim * wim, nim = tre * wim + tim * wre;
-        tre = C.cn[n] * nre;
-        tim = C.cn[n] * nim;
+        tre = c * nre;
+        tim = c * nim;
         sre += tre;
         sim += tim;
     }
@@ -366,17 +408,18 @@ RTU_HD void epl_eval(const EplC<T>& C, bool want_t, T x, T y, EplJ<T>& J) {
     T hre = cre, him = cim;            // sum (2n+1) Omega_n
     T ure = T(0), uim = T(0);          // sum D_n Omega_n
     T fre = T(0), fim = T(0);          // sum n g_n Omega_{n-1} w
+    T w2 = T(3);                       // 2n + 1 for the term n = 1, 2, ...
     for (int n = 0; n < C.nterm; ++n) {
+        const EplTerm<T> tm = C.term[n];
         const T nre = tre * wre - tim * wim, nim = tre * wim + tim * wre;
-        const T k = T(n + 1);
-        fre += k * C.gn[n] * nre;
-        fim += k * C.gn[n] * nim;
-        tre = C.cn[n] * nre;
-        tim = C.cn[n] * nim;
+        fre += tm.ng * nre;
+        fim += tm.ng * nim;
+        tre = tm.c * nre;
+        tim = tm.c * nim;
         sre += tre; sim += tim;
-        const T w2 = T(2 * n + 3);
         hre += w2 * tre; him += w2 * tim;
-        if (want_t) { ure += C.Dn[n] * tre; uim += C.Dn[n] * tim; }
+        w2 += T(2);
+        if (want_t) { ure += tm.D * tre; uim += tm.D * tim; }
     }
     const T lbR = C.lnb - r_log(R);
     const T P = C.pref0 * r_exp((C.t - T(1)) * lbR);
@@ -396,23 +439,19 @@ RTU_HD void epl_vjp(const EplC<T>& C, const EplJ<T>& J, bool want_t, T gx, T gy,
     const T iR2 = iR * iR;
     const T th_xr = -yr * q * iR2, th_yr = q * xr * iR2, th_q = -yr * xr * iR2;
     const T R_xr = q * q * xr * iR, R_yr = yr * iR, R_q = q * xr * xr * iR;
-    const T f_q = T(-2) / (C.opq * C.opq);
-    const T b_q = C.thE / (T(2) * C.sq);
-    const T tb = t / C.b, tm1R = (t - T(1)) * iR;
+    const T tm1R = (t - T(1)) * iR;
     const T gxr = C.cp * gx + C.sp * gy, gyr = C.cp * gy - C.sp * gx;   // G in the lens frame
     const T Pd_th = P * (gxr * sthr + gyr * sthi);
     const T Pd_f = P * (gxr * J.fre + gyr * J.fim);
     const T ad = gxr * J.are + gyr * J.aim;
     const T d_xr = Pd_th * th_xr - ad * tm1R * R_xr;
     const T d_yr = Pd_th * th_yr - ad * tm1R * R_yr;
-    const T d_q = Pd_th * th_q + Pd_f * f_q + ad * (tb * b_q - tm1R * R_q - T(1) / C.opq);
-    out[0] += ad * tb * C.sq;
+    const T d_q = Pd_th * th_q + Pd_f * C.f_q + ad * (C.tb_bq - tm1R * R_q - C.iopq);
+    out[0] += ad * C.tb_sq;
     if (want_t) out[1] += P * (gxr * J.ure + gyr * J.uim) + ad * J.lbR;
     const T d_phi = d_xr * yr - d_yr * xr + (gy * J.ax - gx * J.ay);
-    const T icc2 = T(1) / (C.cc * C.cc);
-    const T q_c = T(-2) / ((T(1) + C.cc) * (T(1) + C.cc));
-    out[2] += d_q * q_c * C.e1 / C.cc - d_phi * T(0.5) * C.e2 * icc2;
-    out[3] += d_q * q_c * C.e2 / C.cc + d_phi * T(0.5) * C.e1 * icc2;
+    out[2] += d_q * C.qe1 - d_phi * C.pe2;
+    out[3] += d_q * C.qe2 + d_phi * C.pe1;
     out[4] += -C.cp * d_xr + C.sp * d_yr;
     out[5] += -C.sp * d_xr - C.cp * d_yr;
 }

@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(GP_NT) k_gp_source_static(int n, double pitch,
     const float kscale = (float)(2.0 * 3.14159265358979323846 / pitch);
     for (int i = threadIdx.x; i < n2; i += blockDim.x) {
         const int ky = i / n, kx = i - ky * n;
-        const float fx = (float)fftfreq(kx, n), fy = (float)fftfreq(ky, n);
+        const float fx = fftfreq<float>(kx, n), fy = fftfreq<float>(ky, n);
         const float k = kscale * sqrtf(fx * fx + fy * fy);
         float gdummy[3];
         const float sp = sqrtP_and_grad<float>(family, psv, k, gdummy);
