@@ -42,7 +42,7 @@ L2_BYTES = 126 * 1024 * 1024
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
 FALLBACK_HBM_GBS = 6400.0
 # algorithmic FP32 flops per supersampled ray: the EPL trace + map + interpolation of
-# one ray (about 190), its adjoint about 2.5x that ("Roofline accounting")
+# one ray (about 190), its adjoint about 2.5x that
 FLOPS_FWD_RAY = 190.0
 FLOPS_ADJ_RAY = 2.5 * FLOPS_FWD_RAY
 

@@ -33,8 +33,8 @@ Passages followed (paper sections / equations):
   * likelihood / chi^2 in the mask .......... Sec. 4
   * SVI ELBO with a Normal guide ............ Sec. 4 (location and scale)
 
-Readings where the paper is silent or ambiguous are listed in the design doc
-("Readings of the paper").  Parity unpinned (no independent pin exists):
+Where the paper is silent or ambiguous, the function that takes a reading
+says which one.  Parity unpinned (no independent pin exists):
 the linear prior T(a, lo, hi) of Table A1, whose definition lives in a cited
 paper that is not reproduced here.
 """

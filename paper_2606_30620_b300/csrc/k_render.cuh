@@ -103,11 +103,27 @@ __device__ __forceinline__ T cdf_value(const T* X, const T* U, const T* d, int K
     return h00 * U[j] + h10 * h * d[j] + h01 * U[j + 1] + h11 * h * d[j + 1];
 }
 
+// the same with the interval's 1/h from a table (no division per ray)
+template <typename T>
+__device__ __forceinline__ T cdf_value_r(const T* X, const T* U, const T* d, const T* IH, int K, int j, T z) {
+    if (j < 0) return U[0] + d[0] * (z - X[0]);
+    if (j >= K - 1) return U[K - 1] + d[K - 1] * (z - X[K - 1]);
+    T h = X[j + 1] - X[j];
+    T t = (z - X[j]) * IH[j];
+    T t2 = t * t, t3 = t2 * t;
+    T h00 = T(2) * t3 - T(3) * t2 + T(1);
+    T h10 = t3 - T(2) * t2 + t;
+    T h01 = T(-2) * t3 + T(3) * t2;
+    T h11 = t3 - t2;
+    return h00 * U[j] + h10 * h * d[j] + h01 * U[j + 1] + h11 * h * d[j + 1];
+}
+
 // value, dC/dz and the partials w.r.t. (X_j, X_{j+1}, d_j, d_{j+1}) of the
 // touched knots (for the extrapolation branches only one knot is touched: the
 // left branch reports it in slot "j+1" = knot 0, the right in slot "j" = K-1).
+// IH holds 1/(X_{j+1} - X_j) per interval.
 template <typename T>
-__device__ __forceinline__ T cdf_grad(const T* X, const T* U, const T* d, int K, int j, T z, T& dz,
+__device__ __forceinline__ T cdf_grad(const T* X, const T* U, const T* d, const T* IH, int K, int j, T z, T& dz,
                                       T& pX0, T& pX1, T& pd0, T& pd1) {
     if (j < 0) {
         dz = d[0]; pX0 = T(0); pd0 = T(0); pX1 = -d[0]; pd1 = z - X[0];
@@ -117,14 +133,14 @@ __device__ __forceinline__ T cdf_grad(const T* X, const T* U, const T* d, int K,
         dz = d[K - 1]; pX1 = T(0); pd1 = T(0); pX0 = -d[K - 1]; pd0 = z - X[K - 1];
         return U[K - 1] + d[K - 1] * (z - X[K - 1]);
     }
-    T h = X[j + 1] - X[j];
-    T t = (z - X[j]) / h;
+    T h = X[j + 1] - X[j], ih = IH[j];
+    T t = (z - X[j]) * ih;
     T t2 = t * t, t3 = t2 * t;
     T h00 = T(2) * t3 - T(3) * t2 + T(1), h10 = t3 - T(2) * t2 + t;
     T h01 = T(-2) * t3 + T(3) * t2, h11 = t3 - t2;
     T h00p = T(6) * t2 - T(6) * t, h10p = T(3) * t2 - T(4) * t + T(1);
     T h01p = T(-6) * t2 + T(6) * t, h11p = T(3) * t2 - T(2) * t;
-    T Dz = (h00p * U[j] + h01p * U[j + 1]) / h + h10p * d[j] + h11p * d[j + 1];
+    T Dz = (h00p * U[j] + h01p * U[j + 1]) * ih + h10p * d[j] + h11p * d[j + 1];
     T Hd = h10 * d[j] + h11 * d[j + 1];
     dz = Dz;
     pX0 = Dz * (t - T(1)) - Hd;
@@ -204,6 +220,7 @@ struct RenderShared {
     double trd[TR_HDR + 4 * (MAXM + 2)];
     double Ud[MAXM + 2];
     T offx[8];                 // sub-ray offsets ((a + 1/2)/s - 1/2) pix
+    T ih[2 * (MAXM + 2)];      // 1/(X_{j+1} - X_j) per knot interval, axis-major
     UDiv dv_s2, dv_n, dv_s, dv_nc;   // dividers by s^2, n_img, s, n_src - 1
 };
 
@@ -215,6 +232,18 @@ __device__ __forceinline__ void render_setup(const EvalArgs& E, RenderShared<T>&
         load_transform<double>(E, sh.trd, sh.Ud);
     }
     load_transform<T>(E, sh.trs, sh.U);
+    {
+        const int K = E.n_nodes + 2;
+        for (int i = threadIdx.x; i < 2 * K; i += blockDim.x) {
+            const int a = i / K, j = i - a * K;
+            if (j < K - 1) {
+                const int at = TR_HDR + a * K + j;
+                const T x0 = sizeof(T) == 4 ? (T)E.trf[at] : (T)E.trd[at];
+                const T x1 = sizeof(T) == 4 ? (T)E.trf[at + 1] : (T)E.trd[at + 1];
+                sh.ih[i] = T(1) / (x1 - x0);
+            }
+        }
+    }
     if (threadIdx.x < E.s) sh.offx[threadIdx.x] = (T)(((threadIdx.x + 0.5) / E.s - 0.5) * E.pix);
     if (threadIdx.x == 0) {
         sh.dv_s2 = udiv_make((uint32_t)(E.s * E.s));
@@ -226,7 +255,7 @@ __device__ __forceinline__ void render_setup(const EvalArgs& E, RenderShared<T>&
 
 // S7 + S11: one thread per image pixel, s^2 sub-rays each.
 template <typename T>
-__global__ void __launch_bounds__(CTA_R) k_render(const __grid_constant__ Batch B) {
+__global__ void __launch_bounds__(CTA_R, 6) k_render(const __grid_constant__ Batch B) {
     const int ev = find_eval(B, blockIdx.x);
     const EvalArgs& E = B.e[ev];
     const int tile = blockIdx.x - B.tile0[ev];
@@ -298,12 +327,31 @@ __global__ void __launch_bounds__(CTA_R) k_render(const __grid_constant__ Batch 
             }
         } else {
             T bx, by;
-            lens_beta(sh.K, x, y, bx, by);
+            if (sh.K.nsub == 0) {
+                // two series terms first: a ray whose partial z lies beyond the
+                // margin by more than the tail bound (and a rounding allowance)
+                // is outside the grid whatever the other terms add
+                EplPart<T> ps;
+                epl_alpha_begin(sh.K.C, x, y, 2, ps);
+                T ax, ay;
+                epl_alpha_of(sh.K.C, ps, ax, ay);
+                const T shx = sh.K.g1 * x + sh.K.g2 * y, shy = sh.K.g2 * x - sh.K.g1 * y;
+                const T px = (x - (ax + shx) - mux) * isg, py = (y - (ay + shy) - muy) * isg;
+                const T tail = (T(1.25) * epl_tail_bound(sh.K.C, ps) +
+                                T(1e-6) * (T(1) + r_abs(ax) + r_abs(ay) + r_abs(x) + r_abs(y))) * isg;
+                if (px < zlo[0] - tail || px > zhi[0] + tail || py < zlo[1] - tail || py > zhi[1] + tail)
+                    return -1;
+                epl_alpha_finish(sh.K.C, ps, ax, ay);
+                bx = x - (ax + shx);
+                by = y - (ay + shy);
+            } else {
+                lens_beta(sh.K, x, y, bx, by);
+            }
             const T zx = (bx - mux) * isg, zy = (by - muy) * isg;
             // far outside the grid (beyond the near-edge margin): no cell, zero source
             if (zx < zlo[0] || zx > zhi[0] || zy < zlo[1] || zy > zhi[1]) return -1;
-            yx = cdf_value<T>(Xx, sh.U, dx_, K, cdf_interval<T>(Xx, K, zx), zx);
-            yy = cdf_value<T>(Xy, sh.U, dy_, K, cdf_interval<T>(Xy, K, zy), zy);
+            yx = cdf_value_r<T>(Xx, sh.U, dx_, sh.ih, K, cdf_interval<T>(Xx, K, zx), zx);
+            yy = cdf_value_r<T>(Xy, sh.U, dy_, sh.ih + K, K, cdf_interval<T>(Xy, K, zy), zy);
             if (sizeof(T) == 4 && near_edge((float)(yx * T(n - 1)), (float)(yy * T(n - 1)), n)) {
                 deferred |= 1ull << q;
                 ++nin;               // may turn out outside: k_render_edge takes it back
@@ -319,19 +367,35 @@ __global__ void __launch_bounds__(CTA_R) k_render(const __grid_constant__ Batch 
         ++nin;
         return cell + 1;
     };
+    // codes of this thread's sub-rays in shared memory, then the warp's staged rays
+    // in ray order (lane-major, i.e. pixel by pixel): consecutive adjoint rays
+    // then come from the same or neighbouring pixels
+    // (layout [q][thread]: conflict-free shared-memory banks)
+    int* codes = reinterpret_cast<int*>(smem_raw + (((size_t)n * n * sizeof(T) + 127) & ~(size_t)127)) +
+                 threadIdx.x;
+    int mine = 0;
     for (int q = 0; q < s2; ++q) {
         const int code = valid ? trace(q) : -1;
-        const unsigned m = __ballot_sync(0xffffffffu, code >= 0);
-        if (code >= 0) {
-            const int pos = wpos + __popc(m & ((1u << lane) - 1u));
-            stg[pos] = (lane * s2 + q) | (code << STG_SHIFT);
-            if (code == 0) {
-                // the double pass finds the ray through its staging position
-                const int at = atomicAdd(E.ecount, 1);
-                reinterpret_cast<int*>(E.rec)[at] = (int)(ubase + pos);
-            }
+        codes[q * CTA_R] = code;
+        mine += code >= 0;
+    }
+    int excl = mine;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, excl, o);
+        if (lane >= o) excl += y;
+    }
+    wpos = __shfl_sync(0xffffffffu, excl, 31);
+    excl -= mine;
+    for (int q = 0, pos = excl; q < s2; ++q) {
+        const int code = codes[q * CTA_R];
+        if (code < 0) continue;
+        stg[pos] = (lane * s2 + q) | (code << STG_SHIFT);
+        if (code == 0) {
+            // the double pass finds the ray through its staging position
+            const int at = atomicAdd(E.ecount, 1);
+            reinterpret_cast<int*>(E.rec)[at] = (int)(ubase + pos);
         }
-        wpos += __popc(m);
+        ++pos;
     }
     if (lane == 0) E.useg[tile * (CTA_R / 32) + wid] = wpos;
     // in-grid rays of the CTA (deferred rays counted; k_render_edge takes back the
@@ -475,36 +539,36 @@ __global__ void __launch_bounds__(SCAN_NT) k_scan_cells(const __grid_constant__ 
     block_exclusive_scan(E.useg, E.n_cta_r * (CTA_R / 32), wtot);
 }
 
-// The adjoint's rays: the staged rays of all render warps, numbered in warp order
-// (k = useg[u] + position in warp u).  Finds the warp u of ray k -- advancing
-// from a previous u of a smaller k when u >= 0, else by bisection -- and decodes
-// the ray id and its cell (-1: a deferred ray that ended outside).
-__device__ __forceinline__ void staged_ray(const EvalArgs& E, int nu, int cap, int k, int& u, int& ray,
-                                           int& cell) {
-    const int* us = E.useg;
-    if (u < 0) {
-        int lo = 0, hi = nu;                 // us[lo] <= k < us[hi]
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (us[mid] <= k) lo = mid; else hi = mid;
-        }
-        u = lo;
-    } else {
-        while (us[u + 1] <= k) ++u;
+// The adjoint's rays: the staged rays of all render warps in warp order (ray k
+// of warp u at useg[u] + its position), i.e. in ray order, gathered into flat
+// arrays (ray id, or -1 for a deferred ray that ended outside; cell), one warp
+// per render warp, coalesced.
+constexpr int CMP_NT = 256;
+__global__ void __launch_bounds__(CMP_NT) k_compact(const __grid_constant__ Batch B) {
+    const int ev = find_eval(B, blockIdx.x);
+    const EvalArgs& E = B.e[ev];
+    const int tile = blockIdx.x - B.tile0[ev];
+    const int lane = threadIdx.x & 31;
+    const int nu = E.n_cta_r * (CTA_R / 32);
+    const int u = tile * (CMP_NT / 32) + (threadIdx.x >> 5);
+    if (u >= nu) return;
+    const int cap = 32 * E.s * E.s;
+    const int n_rays = E.n_img * E.n_img * E.s * E.s;
+    const int ncell = (E.n_src - 1) * (E.n_src - 1);
+    const int o = E.useg[u];
+    const int cnt = max(0, min(min(E.useg[u + 1] - o, cap), n_rays - o));
+    const int* stg = E.cell + (size_t)u * cap;
+    for (int i = lane; i < cnt; i += 32) {
+        const int e = stg[i];
+        int cell = (e >> STG_SHIFT) - 1;
+        if (cell >= ncell) cell = -1;
+        E.kray[o + i] = cell >= 0 ? u * cap + (e & ((1 << STG_SHIFT) - 1)) : -1;
+        E.kcell[o + i] = cell;
     }
-    const int pos = k - us[u];
-    if (pos < 0 || pos >= cap) {             // offsets not from a forward pass on this slot
-        ray = 0;
-        cell = -1;
-        return;
-    }
-    const int e = E.cell[(size_t)u * cap + pos];
-    ray = u * cap + min(e & ((1 << STG_SHIFT) - 1), cap - 1);
-    cell = (e >> STG_SHIFT) - 1;
 }
 
-// S9 (image -> source/transform/lens part) over the staged in-grid rays (render
-// warp order): a grid-stride loop gives every CTA a fixed set of chunks of
+// S9 (image -> source/transform/lens part) over the adjoint's rays (render-warp
+// order): a grid-stride loop gives every CTA a fixed set of chunks of
 // CTA_R x ADJ_RPT rays, thread t taking rays t, t + CTA_R, ... of a chunk.  Each ray is recomputed (value + the EPL
 // series sums) and differentiated analytically; its cell comes from the forward
 // pass.  Writes one counting-sorted record per ray and fixed-order per-CTA
@@ -539,8 +603,9 @@ __global__ void __launch_bounds__(CTA_R, 4) k_render_adj(const __grid_constant__
     }
     const int s = E.s, s2 = s * s;
     const int nsub = sh.K.nsub;
-    const int nu = E.n_cta_r * (CTA_R / 32), cap = 32 * E.s * E.s;
-    const int total = min(E.useg[nu], min(nu * cap, E.n_img * E.n_img * E.s * E.s));
+    const int nu = E.n_cta_r * (CTA_R / 32);
+    const int n_rays = E.n_img * E.n_img * E.s * E.s;
+    const int total = max(0, min(E.useg[nu], n_rays));
     const int ncell = nc * nc;
     const T mux = sh.trs[0], muy = sh.trs[1], isg = T(1) / sh.trs[2];
     const T* Xa[2] = {sh.trs + TR_HDR, sh.trs + TR_HDR + K};
@@ -591,7 +656,6 @@ __global__ void __launch_bounds__(CTA_R, 4) k_render_adj(const __grid_constant__
 
     const int chunk = CTA_R * ADJ_RPT;
     for (int base = tile * chunk; base < total; base += E.n_cta_adj * chunk) {
-        int u = -1;
         for (int r = 0; r < ADJ_RPT; ++r) {
             // coalesced: the CTA's threads take consecutive rays; a thread's rays
             // are CTA_R apart, i.e. from nearby pixels (mostly the same intervals)
@@ -599,10 +663,25 @@ __global__ void __launch_bounds__(CTA_R, 4) k_render_adj(const __grid_constant__
             int jn[2] = {cj[0], cj[1]};
             T pn[2][4];
             bool have = false;
-            int cell = -1, ray = 0;
+            int cell = -1, ray = 0, slot = -1;
             if (k < total) {
-                staged_ray(E, nu, cap, k, u, ray, cell);
-                if (cell >= ncell) cell = -1;        // only a forward pass on this slot stages rays
+                ray = E.kray[k];
+                cell = E.kcell[k];
+                if (cell >= ncell || ray < 0 || ray >= n_rays) cell = -1;
+            }
+            {
+                // the ray's record slot in the counting sort by cell: one integer
+                // atomic per group of lanes sharing the cell, ranks by lane order
+                // (used only at the record store, so its latency overlaps the ray)
+                const unsigned act = __ballot_sync(0xffffffffu, cell >= 0);
+                if (cell >= 0) {
+                    const unsigned grp = __match_any_sync(act, cell);
+                    const int leader = __ffs(grp) - 1;
+                    int b = 0;
+                    if (lane == leader) b = atomicAdd(E.cursor + cell, __popc(grp));
+                    b = __shfl_sync(grp, b, leader);
+                    slot = off[cell] + b + __popc(grp & ((1u << lane) - 1u));
+                }
             }
             T gb0 = T(0), gb1 = T(0);
             if (cell >= 0) {
@@ -630,7 +709,7 @@ __global__ void __launch_bounds__(CTA_R, 4) k_render_adj(const __grid_constant__
                 T yv[2], dz[2];
                 for (int a = 0; a < 2; ++a) {
                     jn[a] = cdf_interval<T>(Xa[a], K, z[a]);
-                    yv[a] = cdf_grad<T>(Xa[a], sh.U, Da[a], K, jn[a], z[a], dz[a], pn[a][0], pn[a][1], pn[a][2],
+                    yv[a] = cdf_grad<T>(Xa[a], sh.U, Da[a], sh.ih + a * K, K, jn[a], z[a], dz[a], pn[a][0], pn[a][1], pn[a][2],
                                         pn[a][3]);
                 }
                 const int j0 = (int)udiv((uint32_t)cell, sh.dv_nc), i0 = cell - j0 * nc;
@@ -656,9 +735,7 @@ __global__ void __launch_bounds__(CTA_R, 4) k_render_adj(const __grid_constant__
                 for (int a = 0; a < 2; ++a)
                     for (int c = 0; c < 4; ++c) pn[a][c] *= gy[a];
                 have = true;
-                // the ray's record slot in the counting sort by cell (integer cursor)
-                const int slot = off[cell] + atomicAdd(E.cursor + cell, 1);
-                if (slot < off[cell + 1]) {
+                if (slot >= off[cell] && slot < off[cell + 1]) {
                     R4 rr;
                     rr.x = fx; rr.y = fy; rr.z = gpix; rr.w = T(0);
                     rec[slot] = rr;
@@ -717,8 +794,9 @@ __global__ void __launch_bounds__(CTA_R) k_sub_adj(const __grid_constant__ Batch
     const int Kn = E.n_nodes + 2;
     const int nacc = NACC_FIX + 4 * Kn + 5 * K.nsub;
     double* out = E.apart + (size_t)tile * nacc;
-    const int nu = E.n_cta_r * (CTA_R / 32), cap = 32 * E.s * E.s;
-    const int total = min(E.useg[nu], min(nu * cap, E.n_img * E.n_img * E.s * E.s));
+    const int nu = E.n_cta_r * (CTA_R / 32);
+    const int n_rays = E.n_img * E.n_img * E.s * E.s;
+    const int total = max(0, min(E.useg[nu], n_rays));
     const int s = E.s, s2 = s * s;
     const T pixT = (T)E.pix, cT = (T)(0.5 * (E.n_img - 1) * E.pix);
     const R2* gbuf = reinterpret_cast<const R2*>(E.gbuf);
@@ -727,14 +805,13 @@ __global__ void __launch_bounds__(CTA_R) k_sub_adj(const __grid_constant__ Batch
     for (int h = 0; h < K.nsub; ++h) {
         T a5[5] = {T(0), T(0), T(0), T(0), T(0)};
         for (int base = tile * chunk; base < total; base += E.n_cta_adj * chunk) {
-            int u = -1;
             for (int r = 0; r < ADJ_RPT; ++r) {
                 const int k = base + r * CTA_R + threadIdx.x;
                 if (k >= total) continue;
                 const R2 g = gbuf[k];
                 if (g.x == T(0) && g.y == T(0)) continue;
-                int ray, cell;
-                staged_ray(E, nu, cap, k, u, ray, cell);
+                const int ray = E.kray[k];
+                if (ray < 0 || ray >= n_rays) continue;
                 const int pixel = ray / s2, q = ray - pixel * s2;
                 const int pj = pixel / E.n_img, pi = pixel - pj * E.n_img;
                 const T x = (T(pi) * pixT - cT) + offx[q % s];

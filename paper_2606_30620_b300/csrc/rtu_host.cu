@@ -136,6 +136,8 @@ size_t slot_layout(const rtu_system_desc& d, char* base, EvalArgs* e) {
     p = take((size_t)z.n_rays * 4);                   if (e) e->rval = (float*)p;
     p = take((size_t)(z.n_cta_r + 1) * 4);            if (e) e->cta_cnt = (int*)p;
     p = take((size_t)(z.n_cta_r * (CTA_R / 32) + 1) * 4); if (e) e->useg = (int*)p;
+    p = take((size_t)z.n_rays * 4);                   if (e) e->kray = (int*)p;
+    p = take((size_t)z.n_rays * 4);                   if (e) e->kcell = (int*)p;
     p = take((size_t)z.n_rays * 2 * z.tb);            if (e) e->gbuf = p;
     return o;
 }
@@ -443,6 +445,7 @@ int t_adj(const EvalArgs& e) { return e.n_cta_adj; }
 int t_psf(const EvalArgs& e) { return e.n_cta_p; }
 int t_edge(const EvalArgs&) { return EDGE_CTAS; }
 int t_fix(const EvalArgs& e) { return (e.n_img * e.n_img + 255) / 256; }
+int t_units(const EvalArgs& e) { return (e.n_cta_r * (CTA_R / 32) + CMP_NT / 32 - 1) / (CMP_NT / 32); }
 int t_cells(const EvalArgs& e) {
     const int nc = (e.n_src - 1) * (e.n_src - 1);
     return (nc + GATHER_NT / 32 - 1) / (GATHER_NT / 32);
@@ -513,7 +516,9 @@ rtu_status run_chunk(Batch& B, int phase, cudaStream_t st, const SideStream& ss)
     if (phase & PH_FORWARD) {
         if ((r = stream_after(st, ss.s, ss.join))) return r;
         if (grid_bytes > MAX_DYN) return fail(RTU_E_ARG, "source grid too large for shared memory");
-        if ((r = launch("k_render", k_render<T>, B, t_render, CTA_R, grid_bytes, st))) return r;
+        const size_t render_smem = grid_bytes + (size_t)CTA_R * max_s2 * 4;
+        if (render_smem > MAX_DYN) return fail(RTU_E_ARG, "render shared memory exceeds the limit");
+        if ((r = launch("k_render", k_render<T>, B, t_render, CTA_R, render_smem, st))) return r;
         if (sizeof(T) == 4) {
             if ((r = launch("k_render_edge", k_render_edge, B, t_edge, EDGE_NT, 0, st))) return r;
             if ((r = launch("k_render_fix", k_render_fix, B, t_fix, 256, 0, st))) return r;
@@ -532,6 +537,7 @@ rtu_status run_chunk(Batch& B, int phase, cudaStream_t st, const SideStream& ss)
         if ((r = launch("k_scan_cells", k_scan_cells, B, t_one, SCAN_NT, 0, st))) return r;
         const size_t adj = grid_bytes + (size_t)(CTA_R / 32) * 4 * maxK * 2 * sizeof(T);
         if (adj > MAX_DYN) return fail(RTU_E_ARG, "adjoint shared memory exceeds the limit");
+        if ((r = launch("k_compact", k_compact, B, t_units, CMP_NT, 0, st))) return r;
         if ((r = launch("k_render_adj", k_render_adj<T>, B, t_adj, CTA_R, adj, st))) return r;
         if (any_sub && (r = launch("k_sub_adj", k_sub_adj<T>, B, t_adj, CTA_R, 0, st))) return r;
         // transform and centre-ray adjoint (side) beside the cell gather and GP adjoint (main)

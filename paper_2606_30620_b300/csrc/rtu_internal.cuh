@@ -90,7 +90,9 @@ struct EvalArgs {
     float* rval;       // [n_rays] values of deferred rays (float mode)
     int* cta_cnt;      // [n_cta_r] in-grid rays per render CTA (the N_IN_GRID statistic)
     int* useg;         // [n_cta_r * CTA_R/32 + 1] staged rays per render warp, then exclusive offsets
-    void* gbuf;        // real2 [n_rays] d logL / d beta of each staged ray (subhalo pass)
+    int* kray;         // [n_rays] the adjoint's rays (staged rays in render-warp order): ray id, or -1
+    int* kcell;        // [n_rays] their cells
+    void* gbuf;        // real2 [n_rays] d logL / d beta of each adjoint ray (subhalo pass)
     int n_cta_adj;     // CTAs of the render adjoint (grid-stride over the compacted rays)
 };
 
@@ -257,7 +259,7 @@ struct LensK {
 };
 
 template <typename T>
-__device__ __forceinline__ T epl_tol() { return sizeof(T) == 4 ? T(1e-9) : T(1e-17); }
+__device__ __forceinline__ T epl_tol() { return sizeof(T) == 4 ? T(2e-8) : T(1e-16); }
 
 template <typename T>
 __device__ inline void lens_rest(LensK<T>& K, const double* lens, int profile, int sub_kind, int n_sub) {
@@ -274,7 +276,8 @@ __device__ inline void lens_rest(LensK<T>& K, const double* lens, int profile, i
 // Both lens blocks of an evaluation, built by one CTA: the series coefficients
 // c_n, c_n/f and the per-term t-derivative of log|c_n| in parallel (one thread
 // per term), the running products and sums, and the stopping index of each
-// precision (1e-17 for double, 1e-9 for float), by one thread.
+// precision (1e-16 for double, 2e-8 for float: a third of the type's unit
+// roundoff or less, as |c_n| <= f <= 1/4), by one thread.
 __device__ inline void lens_setup_par(LensK<double>* Kd, LensK<float>* Kf, const double* lens, int profile, int sub_kind,
                                int n_sub) {
     __shared__ double sc[EPL_MAXT], sg[EPL_MAXT], sdl[EPL_MAXT], sconst[4];
@@ -296,7 +299,7 @@ __device__ inline void lens_setup_par(LensK<double>* Kd, LensK<float>* Kf, const
     if (threadIdx.x == 0 || threadIdx.x == 32) {
         const bool dbl = threadIdx.x == 0;
         const double p[6] = {lens[0], lens[1], lens[2], lens[3], lens[4], lens[5]};
-        const double tol = dbl ? 1e-17 : 1e-9;
+        const double tol = dbl ? 1e-16 : 2e-8;
         // scalars through the shared definition, then the coefficient tables
         double a = 1.0, D = 0.0;
         int nt = EPL_MAXT;

@@ -31,6 +31,19 @@ RTU_HD float  r_atan(float x)  { return atanf(x); }
 RTU_HD double r_atan(double x) { return atan(x); }
 RTU_HD float  r_atanh(float x) { return atanhf(x); }
 RTU_HD double r_atanh(double x){ return atanh(x); }
+// R = sqrt(x) and 1/R: one reciprocal square root in float, exact ops in double
+RTU_HD void r_sqrt_inv(float x, float& R, float& iR) {
+#ifdef __CUDA_ARCH__
+    iR = rsqrtf(x);
+#else
+    iR = 1.0f / sqrtf(x);
+#endif
+    R = x * iR;
+}
+RTU_HD void r_sqrt_inv(double x, double& R, double& iR) {
+    R = sqrt(x);
+    iR = 1.0 / R;
+}
 RTU_HD float  r_abs(float x)   { return fabsf(x); }
 RTU_HD double r_abs(double x)  { return fabs(x); }
 
@@ -313,6 +326,7 @@ struct EplC {
     // lens-only factors of the vector-Jacobian product: dF/dq through f,
     // (t/b) db/dq, (t/b) db/dtheta_E, 1/(1+q), the (e1, e2) chain factors
     T f_q, tb_bq, tb_sq, iopq, qe1, qe2, pe1, pe2;
+    T ftail;          // f / (1 - f): the series tail factor, f = (1 - q)/(1 + q)
     int nterm;
     EplTerm<T> term[EPL_MAXT];
 };
@@ -340,6 +354,8 @@ RTU_HD void epl_scalars(EplC<T>& C, const double* p, bool epl) {
     C.qe2 = (T)(q_c * e2 / cc);
     C.pe1 = (T)(0.5 * e1 / (cc * cc));
     C.pe2 = (T)(0.5 * e2 / (cc * cc));
+    const double f = (1.0 - q) / (1.0 + q);
+    C.ftail = (T)(f / (1.0 - f));
 }
 
 // p = theta_E, gamma, e1, e2, x0, y0 (gamma ignored unless epl); tol = size of the
@@ -364,27 +380,72 @@ RTU_HD void epl_setup(EplC<T>& C, const double* p, bool epl, double tol) {
     C.nterm = n > EPL_MAXT ? EPL_MAXT : n;
 }
 
+// The deflection in two parts: the first terms of the series (with the
+// prefactor P), then the rest.  Between them, epl_tail_bound bounds what the
+// remaining terms can add: |c_n| < f for 0 < t < 2 and |w| = 1, so the tail is
+// at most P |Omega_m| f / (1 - f).  begin(m = 0) + finish is the plain sum, in
+// the same order, so a ray that finishes gets the same bits as epl_alpha.
 template <typename T>
-RTU_HD void epl_alpha(const EplC<T>& C, T x, T y, T& ax, T& ay) {
+struct EplPart {
+    T tre, tim, sre, sim, wre, wim, P;
+    int n;
+};
+
+template <typename T>
+RTU_HD void epl_alpha_begin(const EplC<T>& C, T x, T y, int m, EplPart<T>& s) {
     const T dx = x - C.x0, dy = y - C.y0;
     const T xr = C.cp * dx + C.sp * dy, yr = C.cp * dy - C.sp * dx;
     const T R2 = r_max(C.q * C.q * xr * xr + yr * yr, T(1e-20));
-    const T R = r_sqrt(R2), iR = T(1) / R;
+    T R, iR;
+    r_sqrt_inv(R2, R, iR);
     const T cre = C.q * xr * iR, cim = yr * iR;
-    const T wre = cre * cre - cim * cim, wim = T(2) * cre * cim;
-    T tre = cre, tim = cim, sre = cre, sim = cim;
-    for (int n = 0; n < C.nterm; ++n) {
-        const T c = C.term[n].c;
-        const T nre = tre * wre - tim * wim, nim = tre * wim + tim * wre;
-        tre = c * nre;
-        tim = c * nim;
-        sre += tre;
-        sim += tim;
+    s.wre = cre * cre - cim * cim;
+    s.wim = T(2) * cre * cim;
+    s.tre = cre; s.tim = cim; s.sre = cre; s.sim = cim;
+    s.P = C.pref0 * r_exp((C.t - T(1)) * (C.lnb - r_log(R)));
+    const int mm = m < C.nterm ? m : C.nterm;
+    for (s.n = 0; s.n < mm; ++s.n) {
+        const T c = C.term[s.n].c;
+        const T nre = s.tre * s.wre - s.tim * s.wim, nim = s.tre * s.wim + s.tim * s.wre;
+        s.tre = c * nre;
+        s.tim = c * nim;
+        s.sre += s.tre;
+        s.sim += s.tim;
     }
-    const T P = C.pref0 * r_exp((C.t - T(1)) * (C.lnb - r_log(R)));
-    const T axr = P * sre, ayr = P * sim;
+}
+
+// alpha from the terms summed so far
+template <typename T>
+RTU_HD void epl_alpha_of(const EplC<T>& C, const EplPart<T>& s, T& ax, T& ay) {
+    const T axr = s.P * s.sre, ayr = s.P * s.sim;
     ax = C.cp * axr - C.sp * ayr;
     ay = C.sp * axr + C.cp * ayr;
+}
+
+template <typename T>
+RTU_HD T epl_tail_bound(const EplC<T>& C, const EplPart<T>& s) {
+    if (s.n >= C.nterm) return T(0);
+    return s.P * r_sqrt(s.tre * s.tre + s.tim * s.tim) * C.ftail;
+}
+
+template <typename T>
+RTU_HD void epl_alpha_finish(const EplC<T>& C, EplPart<T>& s, T& ax, T& ay) {
+    for (; s.n < C.nterm; ++s.n) {
+        const T c = C.term[s.n].c;
+        const T nre = s.tre * s.wre - s.tim * s.wim, nim = s.tre * s.wim + s.tim * s.wre;
+        s.tre = c * nre;
+        s.tim = c * nim;
+        s.sre += s.tre;
+        s.sim += s.tim;
+    }
+    epl_alpha_of(C, s, ax, ay);
+}
+
+template <typename T>
+RTU_HD void epl_alpha(const EplC<T>& C, T x, T y, T& ax, T& ay) {
+    EplPart<T> s;
+    epl_alpha_begin(C, x, y, 0, s);
+    epl_alpha_finish(C, s, ax, ay);
 }
 
 // Per-ray intermediates of the EPL deflection kept for the vector-Jacobian product.
@@ -400,7 +461,8 @@ RTU_HD void epl_eval(const EplC<T>& C, bool want_t, T x, T y, EplJ<T>& J) {
     const T xr = C.cp * dx + C.sp * dy, yr = C.cp * dy - C.sp * dx;
     const T q = C.q;
     const T R2 = r_max(q * q * xr * xr + yr * yr, T(1e-20));
-    const T R = r_sqrt(R2), iR = T(1) / R;
+    T R, iR;
+    r_sqrt_inv(R2, R, iR);
     const T cre = q * xr * iR, cim = yr * iR;
     const T wre = cre * cre - cim * cim, wim = T(2) * cre * cim;
     T tre = cre, tim = cim;

@@ -61,6 +61,33 @@ int main() {
         worst_dual = fmax(worst_dual, sqrt(err / fmax(nrm, 1e-300)));
         worst_fd = fmax(worst_fd, sqrt(efd / fmax(nrm, 1e-300)));
     }
-    printf("value %.3e dual %.3e fd %.3e\n", worst_val, worst_dual, worst_fd);
+    // the series tail bound: |alpha - alpha after m terms| <= epl_tail_bound
+    double worst_tail = 0;
+    for (int trial = 0; trial < 4000; ++trial) {
+        const bool epl = trial % 3 != 0;
+        double q = 0.3 + 0.69 * urand(seed), phi = 3.14159 * urand(seed);
+        double c = (1 - q) / (1 + q);
+        double p[6] = {0.5 + urand(seed), 1.2 + 1.6 * urand(seed), c * cos(2 * phi), c * sin(2 * phi),
+                       0.2 * (urand(seed) - 0.5), 0.2 * (urand(seed) - 0.5)};
+        double x = 6 * (urand(seed) - 0.5), y = 6 * (urand(seed) - 0.5);
+        EplC<double> C;
+        epl_setup(C, p, epl, 1e-17);
+        double ax, ay;
+        epl_alpha(C, x, y, ax, ay);
+        for (int m = 0; m <= 4; ++m) {
+            EplPart<double> ps;
+            epl_alpha_begin(C, x, y, m, ps);
+            double bx, by;
+            epl_alpha_of(C, ps, bx, by);
+            const double d = sqrt((ax - bx) * (ax - bx) + (ay - by) * (ay - by));
+            const double bound = epl_tail_bound(C, ps);
+            if (bound > 0) worst_tail = fmax(worst_tail, d / bound);
+            else worst_tail = fmax(worst_tail, d > 1e-15 ? 1e9 : 0.0);
+            double fx, fy;
+            epl_alpha_finish(C, ps, fx, fy);
+            if (fx != ax || fy != ay) worst_tail = 1e9;      // split sum must equal the plain sum
+        }
+    }
+    printf("value %.3e dual %.3e fd %.3e tail %.3e\n", worst_val, worst_dual, worst_fd, worst_tail);
     return 0;
 }

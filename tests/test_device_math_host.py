@@ -19,8 +19,10 @@ def test_epl_vjp_host(tmp_path):
                     os.path.join(ROOT, "tests", "host", "epl_vjp_check.cu"), "-o", str(exe)],
                    check=True, capture_output=True)
     out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()
-    val, dual, fd = float(out[1]), float(out[3]), float(out[5])
+    val, dual, fd, tail = float(out[1]), float(out[3]), float(out[5]), float(out[7])
     assert val < 1e-13 and dual < 1e-12 and fd < 1e-7, out
+    # the early-exit bound of the forward render holds, and split sums are exact
+    assert tail <= 1.0, out
 
 
 @pytest.mark.skipif(shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"),
