@@ -18,6 +18,7 @@ build; there is no other implementation to run).
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -45,6 +46,26 @@ FALLBACK_HBM_GBS = 6400.0
 # one ray (about 190), its adjoint about 2.5x that
 FLOPS_FWD_RAY = 190.0
 FLOPS_ADJ_RAY = 2.5 * FLOPS_FWD_RAY
+# The two ray kernels and their algorithmic work: the forward render traces every
+# supersampled ray, the adjoint every ray inside the RTU grid.  DRAM read + write per
+# unit from one ncu capture (--set full, c2 shape, 8 mocks: 5,120,000 rays, 743,894 of
+# them in the grid), valid for the kernel sources with digest TRAFFIC_SRC_DIGEST.
+ROOF = {
+    "k_render": {"flops_per_unit": FLOPS_FWD_RAY, "units": "supersampled rays",
+                 "traffic_per_unit": 0.4127e6 / 5120000},
+    "k_render_adj": {"flops_per_unit": FLOPS_ADJ_RAY, "units": "in-grid rays",
+                     "traffic_per_unit": 6.872e6 / 743894},
+}
+TRAFFIC_SRC_DIGEST = ""
+KERNEL_SOURCES = ("k_render.cuh", "rtu_internal.cuh", "rtu_math.cuh")
+
+
+def kernel_digest():
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2606_30620_b300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def env_rank():
@@ -235,8 +256,6 @@ def run_ours(args):
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     torch.cuda.synchronize()
     barrier()
-    rtu.profile_report()          # clear
-    rtu.profile_enable(True)      # per-kernel CUDA events on the launching stream
     with ClockSampler(local) as clk:
         t_wall = time.perf_counter()
         for i in range(args.steps):
@@ -246,9 +265,18 @@ def run_ours(args):
             ends[i].record(stream)
         torch.cuda.synchronize()
         t_wall = time.perf_counter() - t_wall
+    barrier()
+    # ---- per-kernel times: a separate pass with CUDA events around every launch (on the
+    # stream each kernel is launched on), same workload and L2 flushes, not in `value`
+    rtu.profile_report()          # clear
+    rtu.profile_enable(True)
+    n_prof = min(args.steps, 50)
+    for i in range(n_prof):
+        flush.fill_(float(i))
+        step()
+    torch.cuda.synchronize()
     rtu.profile_enable(False)
     kern = rtu.profile_report()
-    barrier()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     ms = sum(step_ms) / len(step_ms)
     if dist:
@@ -297,10 +325,11 @@ def run_ours(args):
 
     # ---- dominant kernel: average launch duration from the events of the timed region
     top = max(kern.items(), key=lambda kv: kv[1][1])
-    ra_cnt, ra_tot = kern["k_render_adj"]
-    ra_ms = ra_tot / ra_cnt
+    dom = max(ROOF, key=lambda k: kern[k][1])
+    dom_ms = kern[dom][1] / kern[dom][0]
     kern_tot = sum(v[1] for v in kern.values())
-    launches = sum(v[0] for v in kern.values())
+    # kernels of this library per step (counted in the profiled pass) x timed steps
+    launches = sum(v[0] for v in kern.values()) // n_prof * args.steps
 
     clocks = clk.summary()
     serving = run_serving(args, dev) if args.serve_n > 0 else None
@@ -312,12 +341,11 @@ def run_ours(args):
     # the adjoint differentiates the rays inside the RTU grid (zero gradient elsewhere)
     rays_in = float(out_f64[:, rtu.STAT_N_IN_GRID].sum())
     rays = sum(m.n_rays for m in mocks)
-    achieved = FLOPS_ADJ_RAY * rays_in / (ra_ms / 1e3) / 1e12
-    traffic = None
-    tfile = os.path.join(ROOT, "profiles", "render_adj_traffic.json")
-    if os.path.exists(tfile):
-        with open(tfile) as f:
-            traffic = json.load(f).get("bytes_per_launch")
+    units = rays if dom == "k_render" else rays_in
+    achieved = ROOF[dom]["flops_per_unit"] * units / (dom_ms / 1e3) / 1e12
+    # DRAM bytes from one ncu capture, per unit, scaled to this launch; null when the
+    # kernel sources differ from the ones that were captured
+    traffic = (ROOF[dom]["traffic_per_unit"] * units) if kernel_digest() == TRAFFIC_SRC_DIGEST else None
     # cpu baseline: the oracle on the host cores, a bounded sample of the same mocks
     cpu_v, cpu_n, cpu_dt, cores = (cpu_oracle_sample(mocks, budget_s=args.cpu_budget) if not args.no_cpu
                                    else (None, 0, 0.0, 0))
@@ -334,11 +362,11 @@ def run_ours(args):
         "kernels": {k: {"launches": c, "avg_ms": t / c, "share": t / kern_tot} for k, (c, t) in kern.items()},
         "per_system_path": {"value": per_system_value, "unit": "evals/s",
                             "note": "same 32 evaluations issued as 32 single-system calls"},
-        "roofline": {"kernel": "k_render_adj<float>", "top_kernel": top[0], "bound": "alu", "achieved": achieved,
+        "roofline": {"kernel": dom + "<float>", "top_kernel": top[0], "bound": "alu", "achieved": achieved,
                      "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
-                     "traffic": traffic, "launch_ms": ra_ms, "units": "in-grid rays",
-                     "units_per_launch": rays_in, "rays_per_launch": rays,
-                     "flops_per_unit": FLOPS_ADJ_RAY,
+                     "traffic": traffic, "launch_ms": dom_ms, "units": ROOF[dom]["units"],
+                     "units_per_launch": units, "rays_per_launch": rays, "in_grid_rays_per_launch": rays_in,
+                     "flops_per_unit": ROOF[dom]["flops_per_unit"],
                      "peak_note": "FP32 FMA peak from unit counts (148 SMs x 128 lanes x 2 x 2032 MHz)",
                      "hbm_peak_gbs": peaks.get("hbm_gbs"), "hbm_peak_kind": peak_kind},
         "cpu_baseline": {"value": cpu_v, "unit": "evals/s", "cores": cores, "kind": "oracle",

@@ -222,6 +222,7 @@ struct RenderShared {
     T offx[8];                 // sub-ray offsets ((a + 1/2)/s - 1/2) pix
     T ih[2 * (MAXM + 2)];      // 1/(X_{j+1} - X_j) per knot interval, axis-major
     UDiv dv_s2, dv_n, dv_s, dv_nc;   // dividers by s^2, n_img, s, n_src - 1
+    T pixT, cT;                // pixel size and (n_img - 1)/2 pix in the kernel's type
 };
 
 template <typename T>
@@ -246,6 +247,8 @@ __device__ __forceinline__ void render_setup(const EvalArgs& E, RenderShared<T>&
     }
     if (threadIdx.x < E.s) sh.offx[threadIdx.x] = (T)(((threadIdx.x + 0.5) / E.s - 0.5) * E.pix);
     if (threadIdx.x == 0) {
+        sh.pixT = (T)E.pix;
+        sh.cT = (T)(0.5 * (E.n_img - 1) * E.pix);
         sh.dv_s2 = udiv_make((uint32_t)(E.s * E.s));
         sh.dv_n = udiv_make((uint32_t)E.n_img);
         sh.dv_s = udiv_make((uint32_t)E.s);
@@ -295,7 +298,7 @@ __global__ void __launch_bounds__(CTA_R, 6) k_render(const __grid_constant__ Bat
     }
     const int s = E.s, s2 = E.s * E.s;
     const int pj = (int)udiv((uint32_t)pixel, sh.dv_n), pi = pixel - pj * E.n_img;
-    const T pixT = (T)E.pix, cT = (T)(0.5 * (E.n_img - 1) * E.pix);
+    const T pixT = sh.pixT, cT = sh.cT;
     const T cx = T(pi) * pixT - cT, cy = T(pj) * pixT - cT;
     T acc = T(0);
     unsigned long long deferred = 0ull;      // bit q: sub-ray q went to the double pass
@@ -616,7 +619,7 @@ __global__ void __launch_bounds__(CTA_R, 4) k_render_adj(const __grid_constant__
     R2* gbuf = reinterpret_cast<R2*>(E.gbuf);
     const T* gimg = reinterpret_cast<const T*>(E.gimg);
     // pixel centre x = i pix - c, c = (n_img - 1)/2 pix, in the kernel's type
-    const T pixT = (T)E.pix, cT = (T)(0.5 * (E.n_img - 1) * E.pix);
+    const T pixT = sh.pixT, cT = sh.cT;
     const T inv_s2 = T(1) / T(s2);
 
     T acc[NACC_FIX];
