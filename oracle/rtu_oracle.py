@@ -30,6 +30,7 @@ Passages followed (paper sections / equations):
   * softplus positivity (Eq. 2-3) ........... Sec. 2.1
   * bilinear interpolation, zero outside .... Sec. 2.1
   * supersample average, PSF, Gaussian noise  Sec. 2.3, Sec. 3.1
+  * multi-Gaussian lens light ............... App. A.3
   * likelihood / chi^2 in the mask .......... Sec. 4
   * SVI ELBO with a Normal guide ............ Sec. 4 (location and scale)
 
@@ -543,22 +544,45 @@ def ray_hist(sys: System, lens, subs=None, T=None):
     return torch.bincount(cell, minlength=(n - 1) * (n - 1)).to(torch.int64)
 
 
-def forward(sys: System, lens, latents, ps, subs=None):
-    """rtu_forward: RTU grid -> GP source -> ray-traced supersampled image -> PSF -> log L."""
+def mge_light(x, y, light):
+    """Multi-Gaussian lens light (App. A.3): sum over components n of
+    A_n/(2 pi) exp(-rho_n^2 / (2 sigma_n^2)), rho_n^2 = q_n x'^2 + y'^2/q_n, where
+    (x', y') is the position relative to the component's centre (x_n, y_n) in the frame
+    rotated by its position angle phi_n (from +x, counter-clockwise; x' is the major axis
+    for q_n < 1, as for the lens profile).  light: [n, 6] rows (A, sigma, q, phi, x_n, y_n)."""
+    out = torch.zeros_like(x)
+    for n in range(light.shape[0]):
+        A, sg, q, phi, xn, yn = light[n]
+        dx, dy = x - xn, y - yn
+        c, s = torch.cos(phi), torch.sin(phi)
+        xp = c * dx + s * dy
+        yp = -s * dx + c * dy
+        rho2 = q * xp * xp + yp * yp / q
+        out = out + A / (2.0 * math.pi) * torch.exp(-0.5 * rho2 / (sg * sg))
+    return out
+
+
+def forward(sys: System, lens, latents, ps, subs=None, light=None):
+    """rtu_forward: RTU grid -> GP source -> ray-traced supersampled image (+ the MGE
+    lens light at the same sub-ray positions, when given) -> PSF -> log L."""
     T = build_grid(sys, lens, subs)
     src, f = gp_source(sys, latents, ps)
     x, y = subray_positions(sys.n_img, sys.pix, sys.s_super)
     bx, by = trace(x.reshape(-1), y.reshape(-1), lens, sys.profile, subs, sys.sub_kind)
     yx, yy = rtu_map(bx, by, T)
-    vals = bilinear(src, yx, yy).reshape(sys.n_img * sys.n_img, sys.s_super ** 2)
+    vals = bilinear(src, yx, yy)
+    if light is not None and light.shape[0] > 0:
+        vals = vals + mge_light(x.reshape(-1), y.reshape(-1), light)
+    vals = vals.reshape(sys.n_img * sys.n_img, sys.s_super ** 2)
     image = vals.mean(dim=1).reshape(sys.n_img, sys.n_img)
     model = psf_convolve(image, sys.psf)
     logL, chi2 = log_likelihood(model, sys.data, sys.sigma, sys.mask)
     return dict(logL=logL, chi2=chi2, model=model, image=image, source=src, field=f, T=T)
 
 
-def forward_adjoint(sys: System, lens, latents, ps, subs=None):
-    """rtu_adjoint reference: log L and its gradient w.r.t. lens, latents, ps (and subhaloes)."""
+def forward_adjoint(sys: System, lens, latents, ps, subs=None, light=None):
+    """rtu_adjoint reference: log L and its gradient w.r.t. lens, latents, ps (and
+    subhaloes, lens light)."""
     lens = lens.detach().clone().requires_grad_(True)
     latents = latents.detach().clone().requires_grad_(True)
     ps = ps.detach().clone().requires_grad_(True)
@@ -566,7 +590,10 @@ def forward_adjoint(sys: System, lens, latents, ps, subs=None):
     if subs is not None:
         subs = subs.detach().clone().requires_grad_(True)
         inputs.append(subs)
-    out = forward(sys, lens, latents, ps, subs)
+    if light is not None:
+        light = light.detach().clone().requires_grad_(True)
+        inputs.append(light)
+    out = forward(sys, lens, latents, ps, subs, light)
     grads = torch.autograd.grad(out["logL"], inputs, allow_unused=True)
     grads = [torch.zeros_like(v) if g is None else g for g, v in zip(grads, inputs)]
     res = dict(logL=out["logL"].detach(), chi2=out["chi2"].detach(), model=out["model"].detach(),
@@ -574,6 +601,8 @@ def forward_adjoint(sys: System, lens, latents, ps, subs=None):
                flags=out["T"].flags)
     if subs is not None:
         res["g_subs"] = grads[3]
+    if light is not None:
+        res["g_light"] = grads[-1]
     if sys.profile == PROFILE_SIE:
         res["g_lens"][1] = 0.0
     return res

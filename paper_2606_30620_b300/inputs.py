@@ -47,6 +47,7 @@ class Mock:
     latents: np.ndarray     # [n_src, n_src]
     ps: np.ndarray          # [n_family_params + 1]  (..., alpha_src)
     subs: np.ndarray | None = None   # [n_sub, 5] kappa_s, r_s, tau, x_s, y_s
+    light: np.ndarray | None = None  # [n_light, 6] MGE lens light: A, sigma, q, phi, x_n, y_n
     extra: dict = field(default_factory=dict)
 
     @property
@@ -98,6 +99,24 @@ def _finish(name, n_img, pix, s, n_src, profile, family, lens, ps, rng, *, psf_k
                 psf=gaussian_psf(psf_k, fwhm, pix), sigma=sigma, lens=np.asarray(lens, np.float64),
                 latents=latents, ps=np.asarray(ps, np.float64),
                 subs=None if subs is None else np.asarray(subs, np.float64))
+
+
+def mge_components(rng, n: int, x0: float, y0: float, amp: float = 1.0) -> np.ndarray:
+    """Lens-light parameters of n Gaussian components (App. A.3): sigma log-uniform in
+    [0.1, 1.0] arcsec and sorted, axis ratio U[0.6, 1], position angle U[0, pi), centres
+    within 0.02" of the lens centre, amplitudes U[0.5, 1.5] x amp."""
+    sig = np.sort(10 ** rng.uniform(-1.0, 0.0, size=n))
+    rows = [[amp * rng.uniform(0.5, 1.5), sig[k], rng.uniform(0.6, 1.0), rng.uniform(0.0, math.pi),
+             x0 + 0.02 * rng.standard_normal(), y0 + 0.02 * rng.standard_normal()] for k in range(n)]
+    return np.asarray(rows, np.float64).reshape(n, 6)
+
+
+def with_light(m: Mock, n: int = 5, seed: int = 0, amp: float = 0.3) -> Mock:
+    """The mock with an n-component MGE lens light (its data are unchanged: the
+    parity tests need identical inputs on both sides, not a realistic fit)."""
+    rng = np.random.default_rng(seed)
+    m.light = mge_components(rng, n, float(m.lens[4]), float(m.lens[5]), amp)
+    return m
 
 
 def _matern_like_amp(k0, pitch, rms=0.3):

@@ -14,3 +14,7 @@ def system(m):
 def params(m):
     subs = None if m.subs is None else torch.tensor(m.subs)
     return torch.tensor(m.lens), torch.tensor(m.latents), torch.tensor(m.ps), subs
+
+
+def light(m):
+    return None if m.light is None else torch.tensor(m.light)

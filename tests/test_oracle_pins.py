@@ -462,3 +462,53 @@ def test_uniform_grid_gradient_matches_central_differences():
         fd = (float(O.forward(s, *p)["logL"]) - float(O.forward(s, *q)["logL"])) / (2 * h)
         an = float((g[key] * v).sum())
         assert abs(fd - an) < 1e-5 * max(1.0, abs(an)), (key, fd, an)
+
+
+# ------------------------------------------------------- MGE lens light (App. A.3)
+def _light_grid(half=6.0, n=801):
+    x = torch.linspace(-half, half, n, dtype=torch.float64)
+    X, Y = torch.meshgrid(x, x, indexing="xy")
+    return X.reshape(-1), Y.reshape(-1), float(x[1] - x[0]) ** 2
+
+
+def test_mge_component_flux_is_amplitude_times_sigma_squared():
+    # A/(2 pi) exp(-rho^2/(2 sigma^2)) with rho^2 = q x'^2 + y'^2/q (unit Jacobian)
+    # integrates to A sigma^2 over the plane, for any axis ratio and angle
+    X, Y, dA = _light_grid()
+    for row in ([2.0, 0.4, 0.6, 0.7, 0.1, -0.2], [0.5, 0.8, 0.95, 2.9, -0.3, 0.2]):
+        L = t([row])
+        flux = float(O.mge_light(X, Y, L).sum()) * dA
+        assert abs(flux - row[0] * row[1] ** 2) < 1e-9
+
+
+def test_mge_axis_ratio_and_angle_equivalence():
+    # (q, phi) and (1/q, phi + pi/2) describe the same ellipse
+    X, Y, _ = _light_grid(3.0, 101)
+    a = O.mge_light(X, Y, t([[1.3, 0.3, 0.7, 0.4, 0.05, 0.1]]))
+    b = O.mge_light(X, Y, t([[1.3, 0.3, 1 / 0.7, 0.4 + math.pi / 2, 0.05, 0.1]]))
+    assert float((a - b).abs().max()) < 1e-14
+
+
+def test_round_mge_component_values():
+    L = t([[3.0, 0.5, 1.0, 1.1, 0.2, -0.1]])
+    x = t([0.2, 0.2 + 0.5, 0.2])
+    y = t([-0.1, -0.1, -0.1 - 1.0])
+    v = O.mge_light(x, y, L)
+    assert abs(float(v[0]) - 3.0 / (2 * math.pi)) < 1e-15
+    assert abs(float(v[1]) - 3.0 / (2 * math.pi) * math.exp(-0.5)) < 1e-15
+    assert abs(float(v[2]) - 3.0 / (2 * math.pi) * math.exp(-2.0)) < 1e-15
+
+
+def test_lens_light_gradient_matches_central_differences():
+    m = I.with_light(I.config_tiny(seed=21), n=3, seed=4, amp=0.5)
+    s = oracle_io.system(m)
+    lens, lat, ps, _ = oracle_io.params(m)
+    L = oracle_io.light(m)
+    g = O.forward_adjoint(s, lens, lat, ps, light=L)
+    rng = np.random.default_rng(5)
+    v = t(rng.standard_normal(L.shape))
+    h = 1e-6
+    fd = (float(O.forward(s, lens, lat, ps, light=L + h * v)["logL"])
+          - float(O.forward(s, lens, lat, ps, light=L - h * v)["logL"])) / (2 * h)
+    an = float((g["g_light"] * v).sum())
+    assert abs(fd - an) < 1e-6 * max(1.0, abs(an))
