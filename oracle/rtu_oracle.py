@@ -23,6 +23,7 @@ Passages followed (paper sections / equations):
     Baltz, Marshall & Oguri (2009)
   * arc-mask centre rays, standardisation ... App. C step i, Sec. 2.2 footnote
   * marginal eCDFs / quantile function ...... Sec. 2.2, App. C step ii
+  * weighted eCDFs (weighted RTU grid) ...... Sec. 5 (extension)
   * Chebyshev-node polynomial fit of the QF . App. C step iii (order 21)
   * cubic Hermite spline inverse (the CDF) .. App. C step iv
   * copula map y = g(x) (Eq. 5) ............. Sec. 2.2
@@ -257,6 +258,22 @@ def quantile_type7(sorted_vals, u):
     return sorted_vals[k] + frac * (sorted_vals[k1] - sorted_vals[k])
 
 
+def quantile_weighted(sorted_vals, sorted_w, u):
+    """Weighted empirical quantile: the type-7 quantile of the sample in which
+    value i appears w_i times (w positive integers; weighted RTU grid, Sec. 5):
+    h = u (W - 1) with W = sum w, and the expanded element of rank r is the value
+    whose cumulative weight first exceeds r."""
+    cw = torch.cumsum(sorted_w.to(torch.int64), 0)
+    W = int(cw[-1])
+    h = u * (W - 1)
+    r = torch.floor(h).long().clamp(0, W - 1)
+    r1 = (r + 1).clamp(max=W - 1)
+    k = torch.searchsorted(cw, r, right=True)
+    k1 = torch.searchsorted(cw, r1, right=True)
+    frac = h - r.to(DT)
+    return sorted_vals[k] + frac * (sorted_vals[k1] - sorted_vals[k])
+
+
 @dataclass
 class RTUTransform:
     """Per-axis smoothed CDF: mu, sigma_min and the Hermite knots (z-space)."""
@@ -281,14 +298,15 @@ def standardise(bx, by):
     return mu, sigma
 
 
-def fit_qf_polynomial(zs, u, degree):
+def fit_qf_polynomial(zs, u, degree, ws=None):
     """App. C step iii: Chebyshev coefficients c of p(u) = sum_k c_k T_k(2u-1) fitted to
     the empirical QF at the nodes u; each node weighted by the eCDF slope there
     (centred rank difference of half-width 1/(2M)).  With M = degree+1 nodes the
-    weighted fit is the interpolant and the weights drop out."""
+    weighted fit is the interpolant and the weights drop out.  ws: ray weights in
+    the order of zs (weighted RTU grid), else every ray counts once."""
     m = u.shape[0]
     V = chebyshev_T(2.0 * u - 1.0, degree)
-    Q = quantile_type7(zs, u)
+    Q = quantile_type7(zs, u) if ws is None else quantile_weighted(zs, ws, u)
     if m == degree + 1:
         return torch.linalg.solve(V, Q), Q
     d = 0.5 / m
@@ -323,17 +341,19 @@ def hermite_knots(c, u, degree, guard_eps=1e-6):
     return torch.stack(Xr), 1.0 / dp, repaired
 
 
-def fit_transform(bx, by, n_nodes=22, degree=21, guard_eps=1e-6):
+def fit_transform(bx, by, n_nodes=22, degree=21, guard_eps=1e-6, weights=None):
     """App. C steps i-iv from the traced centre rays (bx, by): standardise, sort each
-    marginal (the eCDF), fit the QF polynomial at the Chebyshev nodes, and build the
-    Hermite CDF (values u_j at knots p(u_j), slopes 1/p'(u_j), linear beyond the ends)."""
+    marginal (the eCDF, weighted by the rays' integer weights when given -- the
+    weighted RTU grid of Sec. 5), fit the QF polynomial at the Chebyshev nodes, and
+    build the Hermite CDF (values u_j at knots p(u_j), slopes 1/p'(u_j), linear beyond
+    the ends).  The standardisation (step i) is unweighted."""
     mu, sigma = standardise(bx, by)
     u = chebyshev_nodes(n_nodes)
     flags = 0
     knots, slopes, coeffs, qn = [], [], [], []
     for a, b in enumerate((bx, by)):
-        zs, _ = torch.sort((b - mu[a]) / sigma)
-        c, Q = fit_qf_polynomial(zs, u, degree)
+        zs, order = torch.sort((b - mu[a]) / sigma, stable=True)
+        c, Q = fit_qf_polynomial(zs, u, degree, None if weights is None else weights[order])
         X, d, rep = hermite_knots(c, u, degree, guard_eps)
         if rep:
             flags |= FLAG_NONMONOTONE
@@ -503,6 +523,7 @@ class System:
     n_nodes: int = 22
     degree: int = 21
     transform: int = TRANSFORM_RTU
+    weights: torch.Tensor | None = None   # [n_img, n_img] positive integer ray weights
 
     @property
     def n_img(self):
@@ -516,7 +537,8 @@ def build_grid(sys: System, lens, subs=None):
     bx, by = trace(xc[sel], yc[sel], lens, sys.profile, subs, sys.sub_kind)
     if sys.transform == TRANSFORM_UNIFORM:
         return uniform_box(bx, by)
-    return fit_transform(bx, by, sys.n_nodes, sys.degree)
+    w = None if sys.weights is None else sys.weights.reshape(-1)[sel]
+    return fit_transform(bx, by, sys.n_nodes, sys.degree, weights=w)
 
 
 def gp_source(sys: System, latents, ps):
@@ -718,8 +740,10 @@ def elbo_estimate(sys: System, state: GuideState, priors, fixed_phys, n_samples:
     ELBO = (1/S) sum_s [log L(theta_s) + sum_sites (log p + log|J|)
                         + sum_latents log N(w; 0, 1) - log q(u_s)],
     u_s = loc + softplus(rho) e_s.  `fixed_phys` is the physical vector
-    [lens (8 + 5 n_sub) | ps] that supplies the values of non-site entries
-    (gamma of an SIE, tau of each subhalo).  Returns the ELBO (with autograd graph)."""
+    [lens (8 + 5 n_sub) | ps | lens light (6 n_light, optional)] that supplies the
+    values of non-site entries (gamma of an SIE, tau of each subhalo) and the lens
+    light, which is held fixed (the paper's Table A1 gives it no prior).  Returns the
+    ELBO (with autograd graph)."""
     sub_kind, n_sub = subs_kind_n
     targets = site_targets(sys.profile, sub_kind, n_sub, sys.ps_family)
     ns = len(targets)
@@ -740,8 +764,10 @@ def elbo_estimate(sys: System, state: GuideState, priors, fixed_phys, n_samples:
         lpj = lpj + (-0.5 * w * w - 0.5 * math.log(2 * math.pi)).sum()
         lens = torch.stack(phys[:8])
         subs = torch.stack(phys[8:nl]).reshape(-1, 5) if nl > 8 else None
-        ps = torch.stack(phys[nl:])
-        logL = forward(sys, lens, w, ps, subs)["logL"]
+        nps = N_PS_PARAMS[sys.ps_family] + 1
+        ps = torch.stack(phys[nl:nl + nps])
+        light = torch.stack(phys[nl + nps:]).reshape(-1, 6) if len(phys) > nl + nps else None
+        logL = forward(sys, lens, w, ps, subs, light)["logL"]
         logq = (-0.5 * eps * eps - torch.log(scale) - 0.5 * math.log(2 * math.pi)).sum()
         total = total + logL + lpj - logq
     return total / n_samples

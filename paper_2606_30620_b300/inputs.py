@@ -48,6 +48,7 @@ class Mock:
     ps: np.ndarray          # [n_family_params + 1]  (..., alpha_src)
     subs: np.ndarray | None = None   # [n_sub, 5] kappa_s, r_s, tau, x_s, y_s
     light: np.ndarray | None = None  # [n_light, 6] MGE lens light: A, sigma, q, phi, x_n, y_n
+    weights: np.ndarray | None = None  # [n_img, n_img] uint32 ray weights (weighted RTU grid)
     extra: dict = field(default_factory=dict)
 
     @property
@@ -116,6 +117,13 @@ def with_light(m: Mock, n: int = 5, seed: int = 0, amp: float = 0.3) -> Mock:
     parity tests need identical inputs on both sides, not a realistic fit)."""
     rng = np.random.default_rng(seed)
     m.light = mge_components(rng, n, float(m.lens[4]), float(m.lens[5]), amp)
+    return m
+
+
+def with_snr_weights(m: Mock, cap: int = 100) -> Mock:
+    """Integer ray weights from the pixel SNR (data / sigma, rounded, clipped to
+    [1, cap]) -- one of the weightings Sec. 5 names for a weighted RTU grid."""
+    m.weights = np.clip(np.rint(m.data / m.sigma), 1, cap).astype(np.uint32)
     return m
 
 

@@ -8,7 +8,8 @@ def system(m):
     return O.System(data=torch.tensor(m.data), mask=torch.tensor(m.mask).bool(),
                     psf=torch.tensor(m.psf), sigma=m.sigma, pix=m.pix, s_super=m.s_super,
                     n_src=m.n_src, src_pitch=m.src_pitch, profile=m.profile,
-                    ps_family=m.ps_family, sub_kind=m.sub_kind)
+                    ps_family=m.ps_family, sub_kind=m.sub_kind,
+                    weights=None if m.weights is None else torch.tensor(m.weights.astype("int64")))
 
 
 def params(m):

@@ -512,3 +512,51 @@ def test_lens_light_gradient_matches_central_differences():
           - float(O.forward(s, lens, lat, ps, light=L - h * v)["logL"])) / (2 * h)
     an = float((g["g_light"] * v).sum())
     assert abs(fd - an) < 1e-6 * max(1.0, abs(an))
+
+
+# ------------------------------------------------------- weighted RTU grid (Sec. 5)
+def test_weighted_quantile_is_type7_of_the_expanded_sample():
+    rng = np.random.default_rng(8)
+    for n in (1, 2, 7, 40):
+        v = torch.sort(t(rng.standard_normal(n)))[0]
+        w = torch.tensor(rng.integers(1, 6, size=n), dtype=torch.int64)
+        u = t(np.concatenate([[0.0, 1.0], rng.uniform(0, 1, 30)]))
+        brute = O.quantile_type7(torch.repeat_interleave(v, w), u)
+        assert float((O.quantile_weighted(v, w, u) - brute).abs().max()) == 0.0
+
+
+def test_unit_weights_give_the_unweighted_transform():
+    m = I.config_c2(1050, n_img=48, s=2, n_src=16)
+    s = oracle_io.system(m)
+    lens, _, _, _ = oracle_io.params(m)
+    T0 = O.build_grid(s, lens)
+    s.weights = torch.ones(m.n_img, m.n_img, dtype=torch.int64)
+    T1 = O.build_grid(s, lens)
+    assert float((T0.knots - T1.knots).abs().max()) == 0.0
+    assert float((T0.slopes - T1.slopes).abs().max()) == 0.0
+
+
+def test_weights_move_the_knots_toward_heavy_rays():
+    # weighting by the pixel SNR moves the nodes' quantiles (so the knots) toward the
+    # rays of bright pixels
+    m = I.with_snr_weights(I.config_c2(1051, n_img=48, s=2, n_src=16))
+    s = oracle_io.system(m)
+    lens, _, _, _ = oracle_io.params(m)
+    Tw = O.build_grid(s, lens)
+    s.weights = None
+    Tu = O.build_grid(s, lens)
+    assert float((Tw.knots - Tu.knots).abs().max()) > 1e-3
+
+
+def test_weighted_grid_gradient_matches_central_differences():
+    m = I.with_snr_weights(I.config_tiny(seed=19), cap=7)
+    s = oracle_io.system(m)
+    lens, lat, ps, _ = oracle_io.params(m)
+    g = O.forward_adjoint(s, lens, lat, ps)
+    rng = np.random.default_rng(19)
+    v = t(rng.standard_normal(8))
+    h = 1e-7
+    fd = (float(O.forward(s, lens + h * v, lat, ps)["logL"])
+          - float(O.forward(s, lens - h * v, lat, ps)["logL"])) / (2 * h)
+    an = float((g["g_lens"] * v).sum())
+    assert abs(fd - an) < 1e-5 * max(1.0, abs(an))
