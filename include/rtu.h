@@ -86,6 +86,8 @@ enum { RTU_STAT_LOGL = 0, RTU_STAT_CHI2_MASK = 1, RTU_STAT_N_MASK = 2, RTU_STAT_
 #define RTU_N_LENS 8
 #define RTU_N_SUB_PARAMS 5
 #define RTU_MAX_SUB 16
+#define RTU_MAX_LIGHT 8     /* MGE lens-light components (App. A.3 uses 5) */
+#define RTU_N_LIGHT_PARAMS 6
 #define RTU_MAX_NODES 64
 
 /* Static description of one lens system (Sec. 3.1 observation + model choices). */
@@ -103,13 +105,18 @@ typedef struct {
     int32_t degree;      /* polynomial degree D of the quantile fit (21 in the paper) */
     int32_t n_slots;     /* concurrent evaluations of this system (e.g. ELBO samples) */
     int32_t transform;   /* RTU_TRANSFORM_RTU (Sec. 2.2) | RTU_TRANSFORM_UNIFORM (Sec. 2.1 box) */
-    int32_t reserved_;   /* 0 */
+    int32_t n_light;     /* MGE lens-light components 0..RTU_MAX_LIGHT (App. A.3); 0 = none */
     double pix;          /* arcsec per pixel */
     double src_pitch;    /* source-grid pitch entering k (arcsec) */
     double sigma;        /* Gaussian noise rms (Sec. 3.1) */
     const void* data;    /* device, real [n_img*n_img] observed image */
     const uint8_t* mask; /* device, u8 [n_img*n_img]; nonzero = in the arc mask (Sec. 2.2) */
     const void* psf;     /* device, real [psf_k*psf_k], centre at (psf_k-1)/2 */
+    const uint32_t* weights; /* device, u32 [n_img*n_img] or NULL: ray weights of the arc-mask
+                                pixels for a weighted RTU grid (Sec. 5 extension): each centre
+                                ray counts w times in the eCDFs (type-7 quantiles of the
+                                weight-expanded sample); w >= 1 on the mask, sum over the mask
+                                < 2^31.  NULL = every ray once.  Read once at create. */
 } rtu_system_desc;
 
 typedef struct rtu_system rtu_system;
@@ -134,6 +141,12 @@ typedef struct {
     void* g_latents;           /* adjoint out: real [n_src^2] */
     double* g_lens;            /* adjoint out: [8 + 5 n_sub] */
     double* g_ps;              /* adjoint out: [n_family + 1] */
+    const double* light;       /* [6 n_light] lens light (App. A.3), per component A, sigma
+                                  (arcsec), q, phi (rad, from +x counter-clockwise), x_n, y_n;
+                                  the image adds sum_n A/(2 pi) exp(-rho^2/(2 sigma^2)),
+                                  rho^2 = q x'^2 + y'^2/q about (x_n, y_n) rotated by phi, at
+                                  every sub-ray before the PSF.  Required when n_light > 0. */
+    double* g_light;           /* adjoint out: [6 n_light]; required when n_light > 0 */
 } rtu_eval;
 
 /* Bytes of device workspace one system needs (256-byte aligned base). 0 on bad desc. */
@@ -196,8 +209,9 @@ typedef struct {
 int32_t rtu_n_sites(const rtu_system_desc* desc);
 
 /* Set the guide of one system (synchronous host copies into the workspace):
- * priors[n_sites]; fixed[8 + 5 n_sub + n_ps] physical values that supply the
- * non-site entries (gamma of an SIE, tau of each subhalo); loc and rho
+ * priors[n_sites]; fixed[8 + 5 n_sub + n_ps + 6 n_light] physical values that supply
+ * the non-site entries (gamma of an SIE, tau of each subhalo) followed by the lens
+ * light, which the ELBO step holds fixed (no lens-light sites); loc and rho
  * [n_sites + n_src^2] unconstrained locations and softplus-scale parameters;
  * tag = the system's random stream.  Resets Adam's moments and the step. */
 rtu_status rtu_elbo_init(rtu_system* sys, const rtu_prior* priors, const double* fixed,

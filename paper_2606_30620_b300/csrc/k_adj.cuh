@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(CDF_NT) k_cdf_adj(const __grid_constant__ Batc
         double g = 0.0;
         for (int k = 0; k <= D; ++k) g += Ct[k * M + i] * gc[k];
         gQ[i] = g;
-        const double h = E.cheb[cheb_u(M, D) + i] * (N - 1);
+        const double h = E.cheb[cheb_u(M, D) + i] * (E.wtot - 1);
         const double frac = h - floor(h);
         E.tadj[TADJ_SEL + ax * 2 * MAXM + 2 * i] = g * (1.0 - frac) * isig;
         E.tadj[TADJ_SEL + ax * 2 * MAXM + 2 * i + 1] = g * frac * isig;
@@ -274,6 +274,12 @@ __global__ void __launch_bounds__(64) k_grad_final(const __grid_constant__ Batch
         double g = s + c;
         if (p == 1 && E.profile == 0) g = 0.0;
         E.g_lens[p] = g;
+    }
+    const int nlp = E.light ? 6 * E.n_light : 0;
+    for (int p = threadIdx.x; p < nlp; p += blockDim.x) {
+        double g = 0.0;
+        for (int t = 0; t < E.n_cta_r; ++t) g += E.lpartl[(size_t)t * nlp + p];
+        if (E.g_light) E.g_light[p] = g;
     }
 }
 

@@ -107,8 +107,9 @@ __global__ void __launch_bounds__(CTA_C) k_centre_hist(const __grid_constant__ B
     double d0 = 0.0, d1 = 0.0;
     if (k < E.n_mask) {
         double bx = E.beta[k], by = E.beta[E.n_mask + k];
-        atomicAdd(E.hist + beta_bin(bx, m[2], bin_scale(m[2], m[3])), 1);
-        atomicAdd(E.hist + HB + beta_bin(by, m[4], bin_scale(m[4], m[5])), 1);
+        const int w = E.cwt ? (int)E.cwt[k] : 1;      // weighted grid: the ray counts w times
+        atomicAdd(E.hist + beta_bin(bx, m[2], bin_scale(m[2], m[3])), w);
+        atomicAdd(E.hist + HB + beta_bin(by, m[4], bin_scale(m[4], m[5])), w);
         d0 = (bx - m[0]) * (bx - m[0]);
         d1 = (by - m[1]) * (by - m[1]);
     }
@@ -129,7 +130,9 @@ constexpr int SEL_NT = 1024;
 constexpr int SEL_ROWS = HB / 32;      // the histogram as rows of 32 bins (one per lane)
 
 // One CTA per (evaluation, axis).  Dynamic shared memory:
-//   double ck[SEL_CAP]; int ci[SEL_CAP]; unsigned bitmap[HB/32];
+//   double ck[SEL_CAP]; int ci[SEL_CAP]; unsigned bitmap[HB/32]; uint32_t cw[SEL_CAP];
+// Histogram entries are ray counts, or weight sums for a weighted grid; ranks run
+// over the weight-expanded sample (W = total weight).
 __global__ void __launch_bounds__(SEL_NT) k_select_fit(const __grid_constant__ Batch B) {
     const int ev = find_eval(B, blockIdx.x);
     const EvalArgs& E = B.e[ev];
@@ -138,12 +141,13 @@ __global__ void __launch_bounds__(SEL_NT) k_select_fit(const __grid_constant__ B
     double* ck = reinterpret_cast<double*>(smem_raw);
     int* ci = reinterpret_cast<int*>(ck + SEL_CAP);
     unsigned* bitmap = reinterpret_cast<unsigned*>(ci + SEL_CAP);
+    uint32_t* cwc = reinterpret_cast<uint32_t*>(bitmap + HB / 32);
     __shared__ double mom[6];
     __shared__ double sig[3];
     __shared__ int rowoff[SEL_ROWS + 1];
     __shared__ int wtot[SEL_NT / 32];
-    __shared__ int t_bin[2 * MAXM], t_below[2 * MAXM], t_rank[2 * MAXM], t_slot[2 * MAXM], t_cnt[2 * MAXM];
-    __shared__ int d_bin[2 * MAXM], d_off[2 * MAXM + 1], d_fill[2 * MAXM];
+    __shared__ int t_bin[2 * MAXM], t_below[2 * MAXM], t_rank[2 * MAXM], t_slot[2 * MAXM];
+    __shared__ int d_bin[2 * MAXM], d_off[2 * MAXM + 1], d_fill[2 * MAXM], d_num[2 * MAXM];
     __shared__ int n_d;
     __shared__ double Qs[MAXM];
     __shared__ double coef[MAXM];
@@ -152,6 +156,7 @@ __global__ void __launch_bounds__(SEL_NT) k_select_fit(const __grid_constant__ B
     __shared__ int flag_sh;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int N = E.n_mask, M = E.n_nodes, D = E.degree, K = M + 2;
+    const int W = E.wtot;                            // ranks of the (weight-expanded) sample
 
     if (wid == 0) {
         centre_moments(E, mom);
@@ -184,7 +189,7 @@ __global__ void __launch_bounds__(SEL_NT) k_select_fit(const __grid_constant__ B
         const int sum = __reduce_add_sync(0xffffffffu, hist[row * 32 + lane]);
         if (lane == 0) rowoff[row] = sum;
     }
-    for (int i = tid; i < 2 * MAXM; i += SEL_NT) d_fill[i] = 0;
+    for (int i = tid; i < 2 * MAXM; i += SEL_NT) { d_fill[i] = 0; d_num[i] = 0; }
     for (int i = tid; i < HB / 32; i += SEL_NT) bitmap[i] = 0u;
     __syncthreads();
     // exclusive scan of the row sums: two rows per thread, warp scans, warp totals
@@ -219,12 +224,12 @@ __global__ void __launch_bounds__(SEL_NT) k_select_fit(const __grid_constant__ B
     for (int t = tid; t < nt; t += SEL_NT) {
         int k;
         if (E.transform) {
-            k = t == 0 ? 0 : N - 1;
+            k = t == 0 ? 0 : W - 1;
         } else {
-            double h = E.cheb[cheb_u(M, D) + t / 2] * (N - 1);
+            double h = E.cheb[cheb_u(M, D) + t / 2] * (W - 1);
             k = (int)floor(h);
-            k = k < 0 ? 0 : (k > N - 1 ? N - 1 : k);
-            if (t & 1) k = k + 1 > N - 1 ? N - 1 : k + 1;
+            k = k < 0 ? 0 : (k > W - 1 ? W - 1 : k);
+            if (t & 1) k = k + 1 > W - 1 ? W - 1 : k + 1;
         }
         t_rank[t] = k;
     }
@@ -252,31 +257,42 @@ __global__ void __launch_bounds__(SEL_NT) k_select_fit(const __grid_constant__ B
         if (lane == __ffs(m3) - 1) {
             t_bin[t] = row * 32 + lane;
             t_below[t] = ex;
-            t_cnt[t] = v;
         }
     }
     __syncthreads();
     if (tid == 0) {
         // distinct target bins (ranks are non-decreasing, so are their bins)
-        int nd = 0, off = 0;
+        int nd = 0;
         for (int t = 0; t < nt; ++t) {
             if (nd == 0 || d_bin[nd - 1] != t_bin[t]) {
                 d_bin[nd] = t_bin[t];
-                d_off[nd] = off;
-                off += t_cnt[t];
                 bitmap[t_bin[t] >> 5] |= 1u << (t_bin[t] & 31);
                 ++nd;
             }
             t_slot[t] = nd - 1;
         }
-        d_off[nd] = off;
         n_d = nd;
-        if (off > SEL_CAP) flag_sh |= F_SELECT;
     }
     for (int t = tid; t < nt; t += SEL_NT) selv[t] = lo;     // overwritten by the selection
     __syncthreads();
     const int nd = n_d;
-    // gather the candidates of the target bins
+    // candidates of the target bins: count them per bin, offsets, then gather
+    for (int k = tid; k < N; k += SEL_NT) {
+        const int bn = beta_bin(beta[k], lo, scale);
+        if (bitmap[bn >> 5] & (1u << (bn & 31))) {
+            int d = 0;
+            while (d < nd - 1 && d_bin[d] != bn) ++d;
+            atomicAdd(&d_num[d], 1);
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int off = 0;
+        for (int d = 0; d < nd; ++d) { d_off[d] = off; off += d_num[d]; }
+        d_off[nd] = off;
+        if (off > SEL_CAP) flag_sh |= F_SELECT;
+    }
+    __syncthreads();
     for (int k = tid; k < N; k += SEL_NT) {
         const double b = beta[k];
         const int bn = beta_bin(b, lo, scale);
@@ -285,11 +301,16 @@ __global__ void __launch_bounds__(SEL_NT) k_select_fit(const __grid_constant__ B
             while (d < nd - 1 && d_bin[d] != bn) ++d;
             const int pos = atomicAdd(&d_fill[d], 1);
             const int at = d_off[d] + pos;
-            if (at < SEL_CAP && pos < d_off[d + 1] - d_off[d]) { ck[at] = b; ci[at] = k; }
+            if (at < SEL_CAP && pos < d_off[d + 1] - d_off[d]) {
+                ck[at] = b;
+                ci[at] = k;
+                cwc[at] = E.cwt ? E.cwt[k] : 1u;
+            }
         }
     }
     __syncthreads();
-    // the element of rank (r - below) inside its bin, ties ordered by index
+    // the element covering rank (r - below) of its bin: candidates ordered by
+    // (value, index), each covering as many ranks as its weight
     for (int t = 0; t < nt; ++t) {
         const int d = t_slot[t];
         const int o = d_off[d], cnt = min(d_off[d + 1], SEL_CAP) - o;
@@ -300,9 +321,9 @@ __global__ void __launch_bounds__(SEL_NT) k_select_fit(const __grid_constant__ B
             int rank = 0;
             for (int c2 = 0; c2 < cnt; ++c2) {
                 const double k2 = ck[o + c2];
-                rank += (k2 < kc) || (k2 == kc && ci[o + c2] < ic);
+                if ((k2 < kc) || (k2 == kc && ci[o + c2] < ic)) rank += (int)cwc[o + c2];
             }
-            if (rank == want) {
+            if (rank <= want && want < rank + (int)cwc[o + c]) {
                 E.sel_idx[a * 2 * MAXM + t] = ic;
                 selv[t] = kc;
             }
@@ -334,7 +355,7 @@ __global__ void __launch_bounds__(SEL_NT) k_select_fit(const __grid_constant__ B
     } else {
         // empirical QF at the nodes in standardized coordinates (type-7 interpolation)
         for (int j = tid; j < M; j += SEL_NT) {
-            const double h = E.cheb[cheb_u(M, D) + j] * (N - 1);
+            const double h = E.cheb[cheb_u(M, D) + j] * (W - 1);
             const double frac = h - floor(h);
             const double zl = (selv[2 * j] - mom[a]) * isig;
             const double zh = (selv[2 * j + 1] - mom[a]) * isig;

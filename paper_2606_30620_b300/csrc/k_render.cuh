@@ -223,6 +223,7 @@ struct RenderShared {
     T ih[2 * (MAXM + 2)];      // 1/(X_{j+1} - X_j) per knot interval, axis-major
     UDiv dv_s2, dv_n, dv_s, dv_nc;   // dividers by s^2, n_img, s, n_src - 1
     T pixT, cT;                // pixel size and (n_img - 1)/2 pix in the kernel's type
+    LightK<T> L;               // MGE lens light (App. A.3)
 };
 
 template <typename T>
@@ -246,6 +247,7 @@ __device__ __forceinline__ void render_setup(const EvalArgs& E, RenderShared<T>&
         }
     }
     if (threadIdx.x < E.s) sh.offx[threadIdx.x] = (T)(((threadIdx.x + 0.5) / E.s - 0.5) * E.pix);
+    light_setup<T>(sh.L, E.light, E.n_light);
     if (threadIdx.x == 0) {
         sh.pixT = (T)E.pix;
         sh.cT = (T)(0.5 * (E.n_img - 1) * E.pix);
@@ -254,6 +256,71 @@ __device__ __forceinline__ void render_setup(const EvalArgs& E, RenderShared<T>&
         sh.dv_s = udiv_make((uint32_t)E.s);
         sh.dv_nc = udiv_make((uint32_t)(E.n_src - 1));
     }
+}
+
+// True when no sub-ray of render tile `tile` can reach the RTU grid (its z range
+// plus the near-edge margin), so that every ray would take the "far outside" exit:
+// the tile's ray positions lie in a box; there the EPL deflection is at most
+// P_max (1 + f/(1 - f)) (|c_n| < f, |w| = 1) with P = pref0 (b/R)^(t-1) taken at the
+// box's smallest (t > 1) or largest (t < 1) elliptical radius R -- R >= q |theta - c|,
+// and R is convex so its maximum sits at a corner -- and the shear deflection is
+// linear (extremes at the corners).  Tiles with subhaloes are never culled.
+__device__ inline bool tile_out_of_reach(const EvalArgs& E, const LensK<double>& Kd, int tile) {
+    if (Kd.nsub > 0) return false;
+    const int n = E.n_img, tx_n = render_tiles_x(n);
+    const int ty = tile / tx_n, tx = tile - ty * tx_n;
+    const int i0 = tx * RT_X, i1 = min(i0 + RT_X - 1, n - 1);
+    const int j0 = ty * RT_Y, j1 = min(j0 + RT_Y - 1, n - 1);
+    const double c = 0.5 * (n - 1), pix = E.pix;
+    const double omin = (0.5 / E.s - 0.5) * pix, omax = ((E.s - 0.5) / E.s - 0.5) * pix;
+    const double xl = (i0 - c) * pix + omin, xh = (i1 - c) * pix + omax;
+    const double yl = (j0 - c) * pix + omin, yh = (j1 - c) * pix + omax;
+    const EplC<double>& C = Kd.C;
+    // elliptical radius bounds over the box
+    const double cx = fmin(fmax(C.x0, xl), xh), cy = fmin(fmax(C.y0, yl), yh);
+    const double dmin = sqrt((cx - C.x0) * (cx - C.x0) + (cy - C.y0) * (cy - C.y0));
+    double rmax = 0.0, shx_lo = 1e300, shx_hi = -1e300, shy_lo = 1e300, shy_hi = -1e300;
+    for (int k = 0; k < 4; ++k) {
+        const double x = (k & 1) ? xh : xl, y = (k & 2) ? yh : yl;
+        const double dx = x - C.x0, dy = y - C.y0;
+        const double xr = C.cp * dx + C.sp * dy, yr = C.cp * dy - C.sp * dx;
+        rmax = fmax(rmax, sqrt(C.q * C.q * xr * xr + yr * yr));
+        const double sx = Kd.g1 * x + Kd.g2 * y, sy = Kd.g2 * x - Kd.g1 * y;
+        shx_lo = fmin(shx_lo, sx); shx_hi = fmax(shx_hi, sx);
+        shy_lo = fmin(shy_lo, sy); shy_hi = fmax(shy_hi, sy);
+    }
+    const double rmin = C.q * dmin;
+    const double e = C.t - 1.0;
+    double pmax;
+    if (e > 1e-12) {
+        if (rmin < 1e-6) return false;
+        pmax = C.pref0 * pow(C.b / rmin, e);
+    } else if (e < -1e-12) {
+        pmax = C.pref0 * pow(C.b / fmax(rmax, 1e-10), e);
+    } else {
+        pmax = C.pref0;
+    }
+    const double amax = pmax * (1.0 + C.ftail) * (1.0 + 1e-6) + 1e-9;
+    // beta = theta - alpha_EPL - alpha_shear ranges per axis
+    const double bxl = xl - shx_hi - amax, bxh = xh - shx_lo + amax;
+    const double byl = yl - shy_hi - amax, byh = yh - shy_lo + amax;
+    // the grid's reach in beta: z in [zlo, zhi] as in the ray test, with slack
+    const int K = E.n_nodes + 2;
+    const double* tr = E.trd;
+    const double mu[2] = {tr[0], tr[1]}, sg = tr[2];
+    const double m = 4.0 * (double)EDGE_DELTA / (E.n_src - 1);
+    bool out = false;
+    for (int a = 0; a < 2; ++a) {
+        const double* X = tr + TR_HDR + a * K;
+        const double* d = tr + TR_HDR + (2 + a) * K;
+        double zlo = X[0] - m / d[0], zhi = X[K - 1] + m / d[K - 1];
+        zlo -= 1e-4 * (1.0 + fabs(zlo));
+        zhi += 1e-4 * (1.0 + fabs(zhi));
+        const double lo = mu[a] + zlo * sg, hi = mu[a] + zhi * sg;
+        const double bl = a == 0 ? bxl : byl, bh = a == 0 ? bxh : byh;
+        out |= bh < lo || bl > hi;
+    }
+    return out;
 }
 
 // S7 + S11: one thread per image pixel, s^2 sub-rays each.
@@ -268,18 +335,42 @@ __global__ void __launch_bounds__(CTA_R, 6) k_render(const __grid_constant__ Bat
     __shared__ __align__(8) uint64_t mbar;
     const int n = E.n_src, K = E.n_nodes + 2;
     render_setup<T>(E, sh);
-    __shared__ int cnt_sh;
-    if (threadIdx.x == 0) cnt_sh = 0;
+    __shared__ int cnt_sh, cull_sh;
+    bool valid;
+    const int pixel = render_pixel(E.n_img, tile, threadIdx.x, valid);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int s = E.s, s2 = E.s * E.s;
+    if (threadIdx.x == 0) {
+        cnt_sh = 0;
+        cull_sh = tile_out_of_reach(E, *reinterpret_cast<const LensK<double>*>(E.lensk), tile) ? 1 : 0;
+    }
+    __syncthreads();
+    if (cull_sh) {
+        // no ray of this tile reaches the grid: only the lens light, nothing staged
+        if (threadIdx.x < CTA_R / 32) E.useg[tile * (CTA_R / 32) + threadIdx.x] = 0;
+        if (threadIdx.x == 0) E.cta_cnt[tile] = 0;
+        if (!valid) return;
+        T acc = T(0);
+        if (sh.L.n) {
+            const int pj = (int)udiv((uint32_t)pixel, sh.dv_n), pi = pixel - pj * E.n_img;
+            const T cx = T(pi) * sh.pixT - sh.cT, cy = T(pj) * sh.pixT - sh.cT;
+            for (int q = 0; q < s2; ++q) {
+                const int qb = (int)udiv((uint32_t)q, sh.dv_s), qa = q - qb * s;
+                acc += light_at(sh.L, cx + sh.offx[qa], cy + sh.offx[qb]);
+            }
+        }
+        if (sizeof(T) == 4) E.pdef[pixel] = 0ull;
+        const T val = acc / T(s2);
+        reinterpret_cast<T*>(E.img)[pixel] = val;
+        if (E.image_out) reinterpret_cast<T*>(E.image_out)[pixel] = val;
+        return;
+    }
     if (!stage_to_smem(sgrid, E.src, (uint32_t)(n * n * sizeof(T)), &mbar, E.flags)) {
         // the copy timed out (flagged): this tile stages nothing
         if (threadIdx.x < CTA_R / 32) E.useg[tile * (CTA_R / 32) + threadIdx.x] = 0;
         if (threadIdx.x == 0) E.cta_cnt[tile] = 0;
         return;
     }
-    const int npix = E.n_img * E.n_img;
-    const int pixel = tile * CTA_R + threadIdx.x;
-    const bool valid = pixel < npix;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     int nin = 0;                 // in-grid (or deferred) sub-rays of this pixel
     const T mux = sh.trs[0], muy = sh.trs[1], isg = T(1) / sh.trs[2];
     const T* Xx = sh.trs + TR_HDR;
@@ -296,7 +387,6 @@ __global__ void __launch_bounds__(CTA_R, 6) k_render(const __grid_constant__ Bat
         zlo[a] = X[0] - m / d[0];
         zhi[a] = X[K - 1] + m / d[K - 1];
     }
-    const int s = E.s, s2 = E.s * E.s;
     const int pj = (int)udiv((uint32_t)pixel, sh.dv_n), pi = pixel - pj * E.n_img;
     const T pixT = sh.pixT, cT = sh.cT;
     const T cx = T(pi) * pixT - cT, cy = T(pj) * pixT - cT;
@@ -310,6 +400,7 @@ __global__ void __launch_bounds__(CTA_R, 6) k_render(const __grid_constant__ Bat
     auto trace = [&](int q) -> int {
         const int qb = (int)udiv((uint32_t)q, sh.dv_s), qa = q - qb * s;
         const T x = cx + sh.offx[qa], y = cy + sh.offx[qb];
+        if (sh.L.n) acc += light_at(sh.L, x, y);       // lens light at every sub-ray
         T yx, yy;
         if (sizeof(T) == 4 && lens_near_core(sh.K, x, y)) {
             double xd, yd, ydx, ydy;
@@ -434,7 +525,8 @@ __global__ void __launch_bounds__(EDGE_NT) k_render_edge(const __grid_constant__
     for (int k = tile * EDGE_NT + threadIdx.x; k < cnt; k += EDGE_CTAS * EDGE_NT) {
         const int at = reinterpret_cast<const int*>(E.rec)[k];     // staging position
         const int local = E.cell[at] & ((1 << STG_SHIFT) - 1);
-        const int ray = (at / cap) * cap + local;
+        const int u = at / cap;
+        const int ray = staged_ray_id(E.n_img, s2, u, local);
         const int pixel = ray / s2, q = ray - pixel * s2;
         double xd, yd, yx, yy;
         ray_pos(E.n_img, E.pix, E.s, pixel, q, xd, yd);
@@ -448,7 +540,7 @@ __global__ void __launch_bounds__(EDGE_NT) k_render_edge(const __grid_constant__
             atomicAdd(E.ccount + cell, 1);
             E.cell[at] = local | ((cell + 1) << STG_SHIFT);
         } else {
-            atomicSub(E.cta_cnt + pixel / CTA_R, 1);
+            atomicSub(E.cta_cnt + u / (CTA_R / 32), 1);
         }
         E.rval[ray] = v;
     }
@@ -565,7 +657,7 @@ __global__ void __launch_bounds__(CMP_NT) k_compact(const __grid_constant__ Batc
         const int e = stg[i];
         int cell = (e >> STG_SHIFT) - 1;
         if (cell >= ncell) cell = -1;
-        E.kray[o + i] = cell >= 0 ? u * cap + (e & ((1 << STG_SHIFT) - 1)) : -1;
+        E.kray[o + i] = cell >= 0 ? staged_ray_id(E.n_img, E.s * E.s, u, e & ((1 << STG_SHIFT) - 1)) : -1;
         E.kcell[o + i] = cell;
     }
 }

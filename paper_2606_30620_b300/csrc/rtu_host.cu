@@ -19,6 +19,7 @@
 #include "k_psf.cuh"
 #include "k_adj.cuh"
 #include "k_elbo.cuh"
+#include "k_light.cuh"
 
 using namespace rtu;
 
@@ -71,14 +72,14 @@ std::vector<int> digit_reversal(int n, const std::vector<int>& rad) {
 
 struct Sizes {
     int nm_max, n_cta_c_max, n_cta_r, n_cta_p, K, ncell, n_rays, nacc, nl, tb, n_cta_adj;
-    int nps, n_sites, n_state, n_phys, n_cta_upd;
+    int nps, n_sites, n_state, n_phys, n_fixed, n_cta_upd;
 };
 
 Sizes sizes_of(const rtu_system_desc& d) {
     Sizes z;
     z.nm_max = d.n_img * d.n_img;
     z.n_cta_c_max = (z.nm_max + CTA_C - 1) / CTA_C;
-    z.n_cta_r = (d.n_img * d.n_img + CTA_R - 1) / CTA_R;
+    z.n_cta_r = render_tiles(d.n_img);
     const int tiles = (d.n_img + PSF_T - 1) / PSF_T;
     z.n_cta_p = tiles * tiles;
     z.K = d.n_nodes + 2;
@@ -94,6 +95,7 @@ Sizes sizes_of(const rtu_system_desc& d) {
     z.n_sites = (d.profile == RTU_EPL ? 8 : 7) + 4 * nsub + z.nps;
     z.n_state = z.n_sites + d.n_src * d.n_src;
     z.n_phys = z.nl + z.nps;
+    z.n_fixed = z.n_phys + 6 * d.n_light;
     z.n_cta_upd = (z.n_state + ELBO_NT - 1) / ELBO_NT;
     return z;
 }
@@ -139,11 +141,12 @@ size_t slot_layout(const rtu_system_desc& d, char* base, EvalArgs* e) {
     p = take((size_t)z.n_rays * 4);                   if (e) e->kray = (int*)p;
     p = take((size_t)z.n_rays * 4);                   if (e) e->kcell = (int*)p;
     p = take((size_t)z.n_rays * 2 * z.tb);            if (e) e->gbuf = p;
+    p = take((size_t)z.n_cta_r * 6 * std::max(1, d.n_light) * 8); if (e) e->lpartl = (double*)p;
     return o;
 }
 
 // per-slot buffers of one guide sample: parameters in, statistics and gradients out
-struct SampleBufs { double *lens, *ps, *stats, *glens, *gps; void *lat, *glat; };
+struct SampleBufs { double *lens, *ps, *stats, *glens, *gps, *glight; void *lat, *glat; };
 
 size_t sample_layout(const rtu_system_desc& d, char* base, SampleBufs* b) {
     const Sizes z = sizes_of(d);
@@ -158,6 +161,7 @@ size_t sample_layout(const rtu_system_desc& d, char* base, SampleBufs* b) {
     p = take((size_t)z.nl * 8);   if (b) b->glens = (double*)p;
     p = take((size_t)z.nps * 8);  if (b) b->gps = (double*)p;
     p = take(n2 * z.tb);          if (b) b->glat = p;
+    p = take((size_t)6 * std::max(1, d.n_light) * 8); if (b) b->glight = (double*)p;
     return o;
 }
 
@@ -171,17 +175,19 @@ size_t state_layout(const rtu_system_desc& d, char* base, ElboState* st) {
     p = take((size_t)2 * z.n_state * 8);  if (st) st->m = (double*)p;
     p = take((size_t)2 * z.n_state * 8);  if (st) st->v = (double*)p;
     p = take((size_t)z.n_sites * sizeof(PriorD)); if (st) st->prior = (PriorD*)p;
-    p = take((size_t)z.n_phys * 8);       if (st) st->fixed = (double*)p;
+    p = take((size_t)z.n_fixed * 8);      if (st) st->fixed = (double*)p;
     p = take(8);                          if (st) st->t = (long long*)p;
     p = take((size_t)z.n_cta_upd * 8);    if (st) st->part = (double*)p;
     if (st) { st->n_sites = z.n_sites; st->n_state = z.n_state; st->n_phys = z.n_phys; st->tag = 0; }
     return o;
 }
 
-size_t static_layout(const rtu_system_desc& d, char* base, int** cidx, double** tw, int** rev, double** cheb) {
+size_t static_layout(const rtu_system_desc& d, char* base, int** cidx, double** tw, int** rev, double** cheb,
+                     uint32_t** cwt = nullptr) {
     size_t o = 0;
     auto take = [&](size_t bytes) { size_t at = o; o = align_up(o + bytes); return base ? base + at : nullptr; };
     char* p = take((size_t)d.n_img * d.n_img * 4); if (cidx) *cidx = (int*)p;
+    p = take((size_t)d.n_img * d.n_img * 4);       if (cwt) *cwt = (uint32_t*)p;
     p = take((size_t)2 * d.n_src * 8);             if (tw) *tw = (double*)p;
     p = take((size_t)d.n_src * 4);                 if (rev) *rev = (int*)p;
     p = take((size_t)cheb_size(d.n_nodes, d.degree) * 8); if (cheb) *cheb = (double*)p;
@@ -241,13 +247,14 @@ const char* check_desc(const rtu_system_desc* d) {
     if (d->n_nodes < 2 || d->n_nodes > MAXM) return "n_nodes must be in [2, 64]";
     if (d->n_slots < 1) return "n_slots must be >= 1";
     if (d->transform != RTU_TRANSFORM_RTU && d->transform != RTU_TRANSFORM_UNIFORM) return "bad transform";
+    if (d->n_light < 0 || d->n_light > RTU_MAX_LIGHT) return "n_light must be in [0, 8]";
     if (!(d->pix > 0) || !(d->src_pitch > 0) || !(d->sigma > 0)) return "pix, src_pitch, sigma must be > 0";
     if (!d->data || !d->mask || !d->psf) return "data, mask and psf must be device pointers";
     return nullptr;
 }
 
 std::once_flag g_attr_once;
-constexpr int SEL_SMEM = SEL_CAP * 12 + HB / 8;
+constexpr int SEL_SMEM = SEL_CAP * 16 + HB / 8;
 constexpr int MAX_DYN = 200 * 1024;
 
 void set_attributes() {
@@ -270,6 +277,8 @@ struct rtu_system {
     int n_mask, n_cta_c, nrad;
     int rad[MAX_RADIX];
     int* cidx;
+    uint32_t* cwt;                // weights of the centre rays (weighted grid), else null
+    int wtot;                     // total weight of the centre rays (n_mask when unweighted)
     double* tw;
     int* rev;
     double* cheb;
@@ -325,7 +334,8 @@ rtu_status rtu_system_create(const rtu_system_desc* d, void* ws, size_t ws_bytes
     s->nrad = (int)rad.size();
     for (int i = 0; i < MAX_RADIX; ++i) s->rad[i] = i < s->nrad ? rad[i] : 1;
     char* base = static_cast<char*>(ws);
-    const size_t st = static_layout(*d, base, &s->cidx, &s->tw, &s->rev, &s->cheb);
+    uint32_t* cwt_buf = nullptr;
+    const size_t st = static_layout(*d, base, &s->cidx, &s->tw, &s->rev, &s->cheb, &cwt_buf);
     // arc-mask pixel list (the CDF uses observed-pixel centres inside the mask)
     const size_t npx = (size_t)d->n_img * d->n_img;
     std::vector<uint8_t> mask(npx);
@@ -336,6 +346,29 @@ rtu_status rtu_system_create(const rtu_system_desc* d, void* ws, size_t ws_bytes
     if (idx.size() < 2) { delete s; return fail(RTU_E_ARG, "the arc mask must hold at least 2 pixels"); }
     s->n_mask = (int)idx.size();
     s->n_cta_c = (s->n_mask + CTA_C - 1) / CTA_C;
+    // weighted grid: the centre rays' weights, checked, in arc-mask order
+    s->cwt = nullptr;
+    s->wtot = s->n_mask;
+    if (d->weights) {
+        std::vector<uint32_t> w(npx), cw(idx.size());
+        if ((ce = cudaMemcpy(w.data(), d->weights, npx * 4, cudaMemcpyDeviceToHost)) != cudaSuccess) {
+            delete s;
+            return fail(RTU_E_CUDA, std::string("weights copy: ") + cudaGetErrorString(ce));
+        }
+        unsigned long long tot = 0;
+        for (size_t k = 0; k < idx.size(); ++k) {
+            cw[k] = w[idx[k]];
+            tot += cw[k];
+            if (cw[k] == 0) { delete s; return fail(RTU_E_ARG, "weights must be >= 1 on the arc mask"); }
+        }
+        if (tot >= (1ull << 31)) { delete s; return fail(RTU_E_ARG, "the mask's total weight must be < 2^31"); }
+        if ((ce = cudaMemcpy(cwt_buf, cw.data(), cw.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess) {
+            delete s;
+            return fail(RTU_E_CUDA, std::string("weights upload: ") + cudaGetErrorString(ce));
+        }
+        s->cwt = cwt_buf;
+        s->wtot = (int)tot;
+    }
     std::vector<double> tw(2 * d->n_src);
     for (int m = 0; m < d->n_src; ++m) {
         const double ang = -2.0 * M_PI * m / d->n_src;
@@ -395,10 +428,15 @@ rtu_status fill_args(rtu_system* s, const rtu_eval& v, EvalArgs& e) {
     e.pix = d.pix; e.pitch = d.src_pitch; e.sigma = d.sigma;
     e.data = d.data; e.mask = d.mask; e.psf = d.psf;
     e.centre_idx = s->cidx; e.tw = s->tw; e.digrev = s->rev; e.cheb = s->cheb;
+    e.cwt = s->cwt; e.wtot = s->wtot;
     e.lens = v.lens; e.latents = v.latents; e.ps = v.ps; e.dlogL = v.dlogL;
     e.stats = v.stats; e.model_out = v.model; e.image_out = v.image; e.source_out = v.source;
     e.cdf_out = v.cdf; e.hist_out = v.ray_hist;
     e.g_lat = v.g_latents; e.g_lens = v.g_lens; e.g_ps = v.g_ps;
+    e.n_light = d.n_light;
+    e.light = d.n_light > 0 ? v.light : nullptr;
+    e.g_light = d.n_light > 0 ? v.g_light : nullptr;
+    if (d.n_light > 0 && !v.light) return fail(RTU_E_ARG, "light must be set when n_light > 0");
     return RTU_OK;
 }
 
@@ -493,9 +531,10 @@ rtu_status stream_after(cudaStream_t to, cudaStream_t from, cudaEvent_t ev) {
 template <typename T>
 rtu_status run_chunk(Batch& B, int phase, cudaStream_t st, const SideStream& ss) {
     rtu_status r;
-    int max_n2 = 0, max_s2 = 0, any_sub = 0, maxK = 0, maxPsf = 0;
+    int max_n2 = 0, max_s2 = 0, any_sub = 0, maxK = 0, maxPsf = 0, any_light = 0;
     for (int i = 0; i < B.n; ++i) {
         maxPsf = std::max(maxPsf, B.e[i].psf_k);
+        any_light |= B.e[i].n_light > 0;
         max_n2 = std::max(max_n2, B.e[i].n_src * B.e[i].n_src);
         max_s2 = std::max(max_s2, B.e[i].s * B.e[i].s);
         any_sub |= (B.e[i].sub_kind && B.e[i].n_sub > 0);
@@ -534,6 +573,7 @@ rtu_status run_chunk(Batch& B, int phase, cudaStream_t st, const SideStream& ss)
         else if (sizeof(T) == 4 && maxPsf <= 21) r = launch("k_psf_adj", k_psf_adj_t<21>, B, t_psf, PSFT_NT, 0, st);
         else r = launch("k_psf_adj", k_psf_adj<T>, B, t_psf, PSF_NT, 0, st);
         if (r) return r;
+        if (any_light && (r = launch("k_light_adj", k_light_adj<T>, B, t_render, CTA_R, 0, st))) return r;
         if ((r = launch("k_scan_cells", k_scan_cells, B, t_one, SCAN_NT, 0, st))) return r;
         const size_t adj = grid_bytes + (size_t)(CTA_R / 32) * 4 * maxK * 2 * sizeof(T);
         if (adj > MAX_DYN) return fail(RTU_E_ARG, "adjoint shared memory exceeds the limit");
@@ -561,6 +601,8 @@ rtu_status run(rtu_system* const* sys, const rtu_eval* ev, int n, int phase, voi
         if (sys[i]->d.precision != prec) return fail(RTU_E_ARG, "all systems of one call must share the precision");
         if ((phase & PH_ADJOINT) && (!ev[i].g_latents || !ev[i].g_lens || !ev[i].g_ps))
             return fail(RTU_E_ARG, "adjoint outputs g_latents, g_lens, g_ps must be set");
+        if ((phase & PH_ADJOINT) && sys[i]->d.n_light > 0 && !ev[i].g_light)
+            return fail(RTU_E_ARG, "adjoint output g_light must be set when n_light > 0");
     }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     SideStream* ss = nullptr;
@@ -678,7 +720,7 @@ rtu_status rtu_elbo_init(rtu_system* s, const rtu_prior* priors, const double* f
     long long t0 = 0;
     cudaError_t ce;
     if ((ce = cudaMemcpy(s->st.prior, priors, (size_t)z.n_sites * sizeof(rtu_prior), cudaMemcpyHostToDevice)) ||
-        (ce = cudaMemcpy(s->st.fixed, fixed, (size_t)z.n_phys * 8, cudaMemcpyHostToDevice)) ||
+        (ce = cudaMemcpy(s->st.fixed, fixed, (size_t)z.n_fixed * 8, cudaMemcpyHostToDevice)) ||
         (ce = cudaMemcpy(s->st.loc, loc, (size_t)z.n_state * 8, cudaMemcpyHostToDevice)) ||
         (ce = cudaMemcpy(s->st.rho, rho, (size_t)z.n_state * 8, cudaMemcpyHostToDevice)) ||
         (ce = cudaMemcpy(s->st.m, zero.data(), zero.size() * 8, cudaMemcpyHostToDevice)) ||
@@ -733,6 +775,8 @@ rtu_status rtu_elbo_step(rtu_system* const* sys, int32_t n, int32_t n_samples, u
                 e.slot = k;
                 e.lens = b.lens; e.latents = b.lat; e.ps = b.ps; e.stats = b.stats;
                 e.g_latents = b.glat; e.g_lens = b.glens; e.g_ps = b.gps;
+                e.light = s->d.n_light > 0 ? s->st.fixed + s->z.n_phys : nullptr;   // held fixed
+                e.g_light = s->d.n_light > 0 ? b.glight : nullptr;
                 es.push_back(s);
                 ev.push_back(e);
             }

@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "rtu.h"
 #include "rtu_math.cuh"
 
 namespace rtu {
@@ -33,13 +34,15 @@ struct EvalArgs {
     int profile, sub_kind, n_sub, family;
     int n_nodes, degree, n_mask, f64;
     int nrad, n_cta_c, n_cta_r, n_cta_p;
-    int transform, pad2_;
+    int transform, n_light;
     int rad[MAX_RADIX];
     double pix, pitch, sigma, pad_;
     const void* data;
     const uint8_t* mask;
     const void* psf;
     const int* centre_idx;      // [n_mask] pixel index of each arc-mask pixel
+    const uint32_t* cwt;        // [n_mask] centre-ray weights (weighted grid) or null
+    int wtot, pad3_;            // total centre-ray weight (n_mask when unweighted)
     const double* tw;           // [2 n_src] exp(-2 pi i m / n_src)
     const int* digrev;          // [n_src] mixed-radix digit reversal
     const double* cheb;         // Chebyshev tables (layout: cheb_* helpers)
@@ -93,6 +96,9 @@ struct EvalArgs {
     int* kray;         // [n_rays] the adjoint's rays (staged rays in render-warp order): ray id, or -1
     int* kcell;        // [n_rays] their cells
     void* gbuf;        // real2 [n_rays] d logL / d beta of each adjoint ray (subhalo pass)
+    const double* light;   // [6 n_light] MGE lens light (A, sigma, q, phi, x_n, y_n)
+    double* g_light;       // [6 n_light] adjoint out
+    double* lpartl;        // [n_cta_r][6 n_light] per-CTA lens-light gradient partials
     int n_cta_adj;     // CTAs of the render adjoint (grid-stride over the compacted rays)
 };
 
@@ -411,6 +417,72 @@ __device__ __forceinline__ void load_lensk(LensK<T>& dst, const void* src) {
 template <typename T>
 __device__ __forceinline__ const void* lensk_src(const void* base) {
     return sizeof(T) == 8 ? base : static_cast<const char*>(base) + LENSK_D_BYTES;
+}
+
+// ------------------------------------------------------------ MGE lens light
+// Per component: A/(2 pi), 1/(2 sigma^2), q, 1/q, cos phi, sin phi, x_n, y_n, 1/A,
+// 1/sigma in the kernel's type (App. A.3; rho^2 = q x'^2 + y'^2/q about (x_n, y_n),
+// rotated by phi).
+constexpr int MAX_LIGHT = RTU_MAX_LIGHT;
+template <typename T>
+struct LightK {
+    T c[MAX_LIGHT][10];
+    int n;
+};
+
+template <typename T>
+__device__ __forceinline__ void light_setup(LightK<T>& L, const double* light, int n) {
+    if (threadIdx.x == 0) L.n = light ? n : 0;
+    if (light && (int)threadIdx.x < n) {
+        const double* p = light + 6 * threadIdx.x;
+        T* c = L.c[threadIdx.x];
+        c[0] = (T)(p[0] / (2.0 * 3.14159265358979323846));
+        c[1] = (T)(0.5 / (p[1] * p[1]));
+        c[2] = (T)p[2];
+        c[3] = (T)(1.0 / p[2]);
+        c[4] = (T)cos(p[3]);
+        c[5] = (T)sin(p[3]);
+        c[6] = (T)p[4];
+        c[7] = (T)p[5];
+        c[8] = (T)(1.0 / p[0]);
+        c[9] = (T)(1.0 / p[1]);
+    }
+}
+
+// the lens light at (x, y)
+template <typename T>
+__device__ __forceinline__ T light_at(const LightK<T>& L, T x, T y) {
+    T v = T(0);
+    for (int n = 0; n < L.n; ++n) {
+        const T* c = L.c[n];
+        const T dx = x - c[6], dy = y - c[7];
+        const T xp = c[4] * dx + c[5] * dy, yp = c[4] * dy - c[5] * dx;
+        v += c[0] * r_exp(-c[1] * (c[2] * xp * xp + c[3] * yp * yp));
+    }
+    return v;
+}
+
+// ------------------------------------------------------------ render tiles
+// A render CTA covers a 16 x 8 pixel tile; thread t takes pixel (t mod 16, t / 16)
+// of it, so each warp holds two 16-pixel rows.  Tiles run row-major over the image.
+constexpr int RT_X = 16, RT_Y = CTA_R / RT_X;
+__host__ __device__ inline int render_tiles_x(int n_img) { return (n_img + RT_X - 1) / RT_X; }
+__host__ __device__ inline int render_tiles(int n_img) {
+    return render_tiles_x(n_img) * ((n_img + RT_Y - 1) / RT_Y);
+}
+__device__ __forceinline__ int render_pixel(int n_img, int tile, int t, bool& valid) {
+    const int tx_n = render_tiles_x(n_img);
+    const int ty = tile / tx_n, tx = tile - ty * tx_n;
+    const int i = tx * RT_X + (t & (RT_X - 1)), j = ty * RT_Y + t / RT_X;
+    valid = i < n_img && j < n_img;
+    return valid ? j * n_img + i : 0;
+}
+// the ray id of staged entry `local` (lane s^2 + q) of render warp u
+__device__ __forceinline__ int staged_ray_id(int n_img, int s2, int u, int local) {
+    const int lane = local / s2, q = local - lane * s2;
+    bool valid;
+    const int pixel = render_pixel(n_img, u / (CTA_R / 32), (u % (CTA_R / 32)) * 32 + lane, valid);
+    return pixel * s2 + q;
 }
 
 // pixel centre and sub-ray positions (Sec. 2.3) in double

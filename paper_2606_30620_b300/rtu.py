@@ -42,15 +42,16 @@ _lib = ctypes.CDLL(LIB_PATH)
 class SystemDesc(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int32) for n in (
         "n_img", "s_super", "n_src", "psf_k", "profile", "sub_kind", "n_sub", "ps_family",
-        "precision", "n_nodes", "degree", "n_slots", "transform", "reserved_")] + [
+        "precision", "n_nodes", "degree", "n_slots", "transform", "n_light")] + [
         ("pix", ctypes.c_double), ("src_pitch", ctypes.c_double), ("sigma", ctypes.c_double),
-        ("data", ctypes.c_void_p), ("mask", ctypes.c_void_p), ("psf", ctypes.c_void_p)]
+        ("data", ctypes.c_void_p), ("mask", ctypes.c_void_p), ("psf", ctypes.c_void_p),
+        ("weights", ctypes.c_void_p)]
 
 
 class Eval(ctypes.Structure):
     _fields_ = [("slot", ctypes.c_int32), ("pad_", ctypes.c_int32)] + [(n, ctypes.c_void_p) for n in (
         "lens", "latents", "ps", "dlogL", "stats", "model", "image", "source", "cdf", "ray_hist",
-        "g_latents", "g_lens", "g_ps")]
+        "g_latents", "g_lens", "g_ps", "light", "g_light")]
 
 
 class Prior(ctypes.Structure):
@@ -133,12 +134,17 @@ class System:
 
     def __init__(self, data, mask, psf, sigma, pix, s_super, n_src, src_pitch, profile=RTU_SIE,
                  ps_family=RTU_PS_POWER_LAW, sub_kind=RTU_SUB_NONE, n_sub=0, precision=RTU_F32,
-                 n_nodes=22, degree=21, n_slots=1, device="cuda", transform=RTU_TRANSFORM_RTU):
+                 n_nodes=22, degree=21, n_slots=1, device="cuda", transform=RTU_TRANSFORM_RTU, n_light=0,
+                 weights=None):
         self.dtype = torch.float64 if precision == RTU_F64 else torch.float32
         self.device = torch.device(device)
         self.data = torch.as_tensor(data, dtype=self.dtype, device=self.device).contiguous()
         self.mask = torch.as_tensor(mask, dtype=torch.uint8, device=self.device).contiguous()
         self.psf = torch.as_tensor(psf, dtype=self.dtype, device=self.device).contiguous()
+        # weighted RTU grid: integer ray weights per pixel (read once at create)
+        self.weights = None if weights is None else torch.as_tensor(
+            weights.astype("int32") if hasattr(weights, "astype") else weights,
+            dtype=torch.int32, device=self.device).contiguous()
         self.n_img = int(self.data.shape[0])
         self.n_src = int(n_src)
         self.s_super = int(s_super)
@@ -151,9 +157,10 @@ class System:
         self.n_nodes = int(n_nodes)
         self.desc = SystemDesc(self.n_img, self.s_super, self.n_src, int(self.psf.shape[0]), self.profile,
                                self.sub_kind, self.n_sub, self.ps_family, self.precision, int(n_nodes),
-                               int(degree), self.n_slots, int(transform), 0, float(pix), float(src_pitch),
+                               int(degree), self.n_slots, int(transform), int(n_light), float(pix), float(src_pitch),
                                float(sigma),
-                               self.data.data_ptr(), self.mask.data_ptr(), self.psf.data_ptr())
+                               self.data.data_ptr(), self.mask.data_ptr(), self.psf.data_ptr(),
+                               None if self.weights is None else self.weights.data_ptr())
         nbytes = _lib.rtu_workspace_size(ctypes.byref(self.desc))
         if nbytes == 0:
             raise RTUError("invalid system description (rtu_workspace_size returned 0)")
@@ -167,12 +174,15 @@ class System:
         self.n_lens = 8 + 5 * self.n_sub
         self.n_ps = N_PS[self.ps_family] + 1
         self.n_knots = self.n_nodes + 2
+        self.n_light = int(n_light)
 
     @classmethod
     def from_mock(cls, m, precision=RTU_F32, n_slots=1, device="cuda", transform=RTU_TRANSFORM_RTU):
         return cls(m.data, m.mask, m.psf, m.sigma, m.pix, m.s_super, m.n_src, m.src_pitch, m.profile,
                    m.ps_family, m.sub_kind, 0 if m.subs is None else m.subs.shape[0], precision,
-                   n_slots=n_slots, device=device, transform=transform)
+                   n_slots=n_slots, device=device, transform=transform,
+                   n_light=0 if getattr(m, "light", None) is None else m.light.shape[0],
+                   weights=getattr(m, "weights", None))
 
     @property
     def n_sites(self) -> int:
@@ -188,7 +198,8 @@ class System:
         fixed = np.ascontiguousarray(fixed, dtype=np.float64)
         loc = np.ascontiguousarray(loc, dtype=np.float64)
         rho = np.ascontiguousarray(rho, dtype=np.float64)
-        if fixed.size != self.n_lens + self.n_ps or loc.size != ns + self.n_src ** 2 or rho.size != loc.size:
+        if fixed.size != self.n_lens + self.n_ps + 6 * self.n_light or loc.size != ns + self.n_src ** 2 \
+                or rho.size != loc.size:
             raise ValueError("fixed / loc / rho sizes do not match the system")
         dp = ctypes.POINTER(ctypes.c_double)
         _check(_lib.rtu_elbo_init(self.handle, arr, fixed.ctypes.data_as(dp), loc.ctypes.data_as(dp),
@@ -225,7 +236,8 @@ class Binding:
     """Device buffers of one evaluation (inputs, and outputs allocated on demand)."""
 
     def __init__(self, system: System, lens, latents, ps, slot=0, want_model=False, want_image=False,
-                 want_source=False, want_cdf=False, want_hist=False, grads=True, dlogL=None, out=None):
+                 want_source=False, want_cdf=False, want_hist=False, grads=True, dlogL=None, out=None,
+                 light=None):
         dev, dt = system.device, system.dtype
         self.system = system
         self.slot = slot
@@ -238,6 +250,13 @@ class Binding:
             raise ValueError("latents must hold n_src^2 values")
         if self.ps.numel() != system.n_ps:
             raise ValueError(f"ps must hold {system.n_ps} values")
+        self.light = None
+        if system.n_light > 0:
+            if light is None:
+                raise ValueError("this system has lens light: pass light [n_light, 6]")
+            self.light = torch.as_tensor(light, dtype=torch.float64, device=dev).contiguous().reshape(-1)
+            if self.light.numel() != 6 * system.n_light:
+                raise ValueError(f"light must hold {6 * system.n_light} values")
         self.dlogL = None if dlogL is None else torch.as_tensor(dlogL, dtype=torch.float64, device=dev)
         out = out or {}
         self.stats = out["stats"] if "stats" in out else torch.zeros(N_STATS, dtype=torch.float64, device=dev)
@@ -261,13 +280,15 @@ class Binding:
             for t in (self.g_latents, self.g_lens, self.g_ps):
                 if not t.is_contiguous():
                     raise ValueError("output views must be contiguous")
+            self.g_light = (torch.empty(6 * system.n_light, dtype=torch.float64, device=dev)
+                            if system.n_light > 0 else None)
         else:
-            self.g_latents = self.g_lens = self.g_ps = None
+            self.g_latents = self.g_lens = self.g_ps = self.g_light = None
 
     def as_struct(self) -> Eval:
         return Eval(self.slot, 0, *[None if t is None else t.data_ptr() for t in (
             self.lens, self.latents, self.ps, self.dlogL, self.stats, self.model, self.image, self.source,
-            self.cdf, self.ray_hist, self.g_latents, self.g_lens, self.g_ps)])
+            self.cdf, self.ray_hist, self.g_latents, self.g_lens, self.g_ps, self.light, self.g_light)])
 
 
 def _stream_ptr(stream):
@@ -337,15 +358,17 @@ def rtu_gp_source_static(n_src: int, src_pitch: float, ps_family: int, latents, 
 
 
 class RTUForward(torch.autograd.Function):
-    """log L(lens, latents, ps) of one system; backward runs rtu_adjoint, which
-    recomputes the rays instead of saving them."""
+    """log L(lens, latents, ps[, light]) of one system; backward runs rtu_adjoint,
+    which recomputes the rays instead of saving them."""
 
     @staticmethod
-    def forward(ctx, system: System, lens, latents, ps):
+    def forward(ctx, system: System, lens, latents, ps, light=None):
         b = Binding(system, lens.detach(), latents.detach(), ps.detach(), grads=True,
-                    dlogL=torch.ones(1, dtype=torch.float64, device=system.device))
+                    dlogL=torch.ones(1, dtype=torch.float64, device=system.device),
+                    light=None if light is None else light.detach())
         Batch([b]).forward()
         ctx.binding = b
+        ctx.light_shape = None if light is None else light.shape
         return b.stats[STAT_LOGL].clone()
 
     @staticmethod
@@ -353,8 +376,9 @@ class RTUForward(torch.autograd.Function):
         b = ctx.binding
         b.dlogL.copy_(g.reshape(1).to(torch.float64))
         Batch([b]).adjoint()
-        return None, b.g_lens.clone(), b.g_latents.clone(), b.g_ps.clone()
+        g_light = None if ctx.light_shape is None else b.g_light.clone().reshape(ctx.light_shape)
+        return None, b.g_lens.clone(), b.g_latents.clone(), b.g_ps.clone(), g_light
 
 
-def log_likelihood(system: System, lens, latents, ps):
-    return RTUForward.apply(system, lens, latents, ps)
+def log_likelihood(system: System, lens, latents, ps, light=None):
+    return RTUForward.apply(system, lens, latents, ps, light)

@@ -52,11 +52,12 @@ def guide_start(m: I.Mock, rho0: float = -3.0):
     priors = I.default_priors(m.profile, m.sub_kind, n_sub, m.ps_family, m.subs)
     phys = list(m.lens) + ([] if m.subs is None else list(m.subs.ravel())) + list(m.ps)
     targets = _targets(m.profile, m.sub_kind, n_sub, len(m.ps))
+    light = [] if getattr(m, "light", None) is None else list(m.light.ravel())     # held fixed
     loc = [I.unconstrain(math.log10(phys[t]) if p[1] == I.SPACE_LOG10 else phys[t], p)
            for t, p in zip(targets, priors)]
     loc = np.concatenate([np.asarray(loc, dtype=np.float64), m.latents.ravel()])
     rho = np.full(loc.size, rho0)
-    return priors, np.array(phys), loc, rho
+    return priors, np.array(phys + light), loc, rho
 
 
 def _targets(profile, sub_kind, n_sub, nps):
@@ -74,7 +75,8 @@ def workspace_bytes(m: I.Mock, precision: int, n_samples: int) -> int:
     """Device bytes a system occupies while resident (its workspace + observation)."""
     d = rtu.SystemDesc(m.n_img, m.s_super, m.n_src, m.psf.shape[0], m.profile, m.sub_kind,
                        0 if m.subs is None else m.subs.shape[0], m.ps_family, precision, 22, 21, n_samples,
-                       0, 0, m.pix, m.src_pitch, m.sigma, 1 << 20, 1 << 20, 1 << 20)
+                       0, 0 if getattr(m, "light", None) is None else m.light.shape[0],
+                       m.pix, m.src_pitch, m.sigma, 1 << 20, 1 << 20, 1 << 20, None)
     import ctypes
     ws = rtu._lib.rtu_workspace_size(ctypes.byref(d))
     tb = 8 if precision == rtu.RTU_F64 else 4

@@ -18,7 +18,7 @@ def run_gpu(m, precision, want_grads=True, n_slots=1, transform=0):
     sysm = rtu.System.from_mock(m, precision=precision, n_slots=n_slots, transform=transform)
     lens = m.lens if m.subs is None else np.concatenate([m.lens, m.subs.ravel()])
     b = rtu.Binding(sysm, lens, m.latents, m.ps, want_model=True, want_image=True, want_source=True,
-                    want_cdf=True, want_hist=True, grads=want_grads)
+                    want_cdf=True, want_hist=True, grads=want_grads, light=m.light)
     batch = rtu.Batch([b])
     batch.forward()
     if want_grads:
@@ -29,6 +29,8 @@ def run_gpu(m, precision, want_grads=True, n_slots=1, transform=0):
     if want_grads:
         out.update(g_latents=b.g_latents.cpu().numpy(), g_lens=b.g_lens.cpu().numpy(),
                    g_ps=b.g_ps.cpu().numpy())
+        if b.g_light is not None:
+            out["g_light"] = b.g_light.cpu().numpy()
     return out, sysm, b
 
 
@@ -36,10 +38,11 @@ def run_oracle(m, grads=True, transform=0):
     s = oracle_io.system(m)
     s.transform = transform
     lens, lat, ps, subs = oracle_io.params(m)
+    light = oracle_io.light(m)
     if grads:
-        r = O.forward_adjoint(s, lens, lat, ps, subs)
+        r = O.forward_adjoint(s, lens, lat, ps, subs, light)
     else:
-        f = O.forward(s, lens, lat, ps, subs)
+        f = O.forward(s, lens, lat, ps, subs, light)
         r = dict(logL=f["logL"], chi2=f["chi2"], model=f["model"], image=f["image"], flags=f["T"].flags)
     T = O.build_grid(s, lens, subs)
     src, _ = O.gp_source(s, lat, ps)
@@ -57,6 +60,8 @@ def run_oracle(m, grads=True, transform=0):
         if subs is not None:
             g_lens = np.concatenate([g_lens, r["g_subs"].numpy().ravel()])
         out.update(g_latents=r["g_latents"].numpy(), g_lens=g_lens, g_ps=r["g_ps"].numpy())
+        if light is not None:
+            out["g_light"] = r["g_light"].numpy().ravel()
     return out
 
 
@@ -74,4 +79,6 @@ def compare(g, o):
     if "g_latents" in g and "g_latents" in o:
         res.update(g_latents=rel_l2(g["g_latents"], o["g_latents"]), g_lens=rel_l2(g["g_lens"], o["g_lens"]),
                    g_ps=rel_l2(g["g_ps"], o["g_ps"]))
+    if "g_light" in g and "g_light" in o:
+        res["g_light"] = rel_l2(g["g_light"], o["g_light"])
     return res

@@ -39,26 +39,30 @@ def test_binding_structs_match_the_c_layout(tmp_path):
 #include <stddef.h>
 #include "rtu.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(rtu_system_desc), offsetof(rtu_system_desc, pix),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(rtu_system_desc), offsetof(rtu_system_desc, weights),
+         offsetof(rtu_system_desc, pix),
          offsetof(rtu_system_desc, data), sizeof(rtu_eval), offsetof(rtu_eval, lens),
-         offsetof(rtu_eval, g_ps), offsetof(rtu_eval, ray_hist));
+         offsetof(rtu_eval, g_ps), offsetof(rtu_eval, ray_hist), offsetof(rtu_eval, light),
+         offsetof(rtu_eval, g_light));
   return 0;
 }
 """)
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)], check=True)
     got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
-    want = [ctypes.sizeof(rtu.SystemDesc), rtu.SystemDesc.pix.offset, rtu.SystemDesc.data.offset,
-            ctypes.sizeof(rtu.Eval), rtu.Eval.lens.offset, rtu.Eval.g_ps.offset, rtu.Eval.ray_hist.offset]
+    want = [ctypes.sizeof(rtu.SystemDesc), rtu.SystemDesc.weights.offset, rtu.SystemDesc.pix.offset,
+            rtu.SystemDesc.data.offset,
+            ctypes.sizeof(rtu.Eval), rtu.Eval.lens.offset, rtu.Eval.g_ps.offset, rtu.Eval.ray_hist.offset,
+            rtu.Eval.light.offset, rtu.Eval.g_light.offset]
     assert got == want
 
 
 def _desc(**kw):
     from paper_2606_30620_b300 import rtu
     d = dict(n_img=64, s_super=2, n_src=32, psf_k=9, profile=0, sub_kind=0, n_sub=0, ps_family=0,
-             precision=0, n_nodes=22, degree=21, n_slots=1, transform=0, reserved_=0, pix=0.05,
+             precision=0, n_nodes=22, degree=21, n_slots=1, transform=0, n_light=0, pix=0.05,
              src_pitch=0.1, sigma=0.02,
-             data=1 << 20, mask=1 << 21, psf=1 << 22)
+             data=1 << 20, mask=1 << 21, psf=1 << 22, weights=None)
     d.update(kw)
     return rtu.SystemDesc(**d)
 
@@ -71,7 +75,8 @@ def test_workspace_size_validates_the_description():
     two = lib.rtu_workspace_size(ctypes.byref(_desc(n_slots=2)))
     assert two > ok
     for bad in (dict(n_src=50), dict(n_src=512), dict(psf_k=4), dict(n_nodes=30), dict(s_super=0),
-                dict(precision=3), dict(sigma=0.0), dict(n_sub=17), dict(data=0), dict(transform=2)):
+                dict(precision=3), dict(sigma=0.0), dict(n_sub=17), dict(data=0), dict(transform=2),
+                dict(n_light=9), dict(n_light=-1)):
         assert lib.rtu_workspace_size(ctypes.byref(_desc(**bad))) == 0, bad
 
 

@@ -33,7 +33,8 @@ def guide_start(m, rng, rho_lo=-5.0, rho_hi=-3.0):
            for t, p in zip(targets, priors)]
     loc = np.array(loc + list(m.latents.ravel()))
     rho = rng.uniform(rho_lo, rho_hi, size=loc.size)
-    return priors, np.array(phys), loc, rho
+    light = [] if m.light is None else list(m.light.ravel())       # held fixed by the ELBO step
+    return priors, np.array(phys + light), loc, rho
 
 
 def run_both(rtu, m, prec, n_samples, steps, seed=77, tag=9, lr=1e-2):
@@ -68,6 +69,14 @@ def test_elbo_steps_fp64_tiny(rtu):
 
 def test_elbo_steps_fp64_subhaloes_and_matern(rtu):
     m = I.config_tiny(seed=42, n_img=16, n_src=8, family=I.PS_MATERN, sub_kind=I.SUB_TNFW, n_sub=2)
+    res, _ = run_both(rtu, m, rtu.RTU_F64, n_samples=2, steps=2)
+    for e_g, e_o, lg, rg, lo, ro, t, to in res:
+        assert abs(e_g - e_o) < 1e-10 * abs(e_o)
+        assert G.rel_l2(lg, lo) < 1e-10 and G.rel_l2(rg, ro) < 1e-10
+
+
+def test_elbo_steps_fp64_with_fixed_lens_light(rtu):
+    m = I.with_light(I.config_tiny(seed=44, n_img=16, n_src=8), n=5, seed=6, amp=0.5)
     res, _ = run_both(rtu, m, rtu.RTU_F64, n_samples=2, steps=2)
     for e_g, e_o, lg, rg, lo, ro, t, to in res:
         assert abs(e_g - e_o) < 1e-10 * abs(e_o)

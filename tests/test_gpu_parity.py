@@ -38,6 +38,8 @@ def _check(r, prec):
         assert r["g_latents"] < tol, r
         assert r["g_ps"] < tol, r
         assert r["g_lens"] < tol, r
+    if "g_light" in r:
+        assert r["g_light"] < tol, r
     assert r["hist_diff"] == 0, r
     assert r["flags"][0] == r["flags"][1], r
 
@@ -175,3 +177,64 @@ def test_uniform_grid_c2_fp32(rtu):
     m = I.config_c2(1005)
     g, _, _ = G.run_gpu(m, rtu.RTU_F32, transform=rtu.RTU_TRANSFORM_UNIFORM)
     _check(G.compare(g, G.run_oracle(m, transform=1)), 0)
+
+
+# ------------------------------------------------------- MGE lens light (App. A.3)
+@pytest.mark.parametrize("kw,n", [(dict(seed=31), 5), (dict(seed=32, n_img=17, s=3, n_src=12, psf_k=5), 1),
+                                  (dict(seed=33, sub_kind=I.SUB_TNFW, n_sub=2), 8)])
+def test_lens_light_fp64_matches_oracle(rtu, kw, n):
+    m = I.with_light(I.config_tiny(**kw), n=n, seed=kw["seed"], amp=0.5)
+    g, _, _ = G.run_gpu(m, rtu.RTU_F64)
+    r = G.compare(g, G.run_oracle(m))
+    assert "g_light" in r
+    _check(r, 1)
+
+
+def test_lens_light_c2_fp32_matches_oracle(rtu):
+    m = I.with_light(I.config_c2(1020), n=5, seed=3, amp=0.3)
+    g, _, _ = G.run_gpu(m, rtu.RTU_F32)
+    r = G.compare(g, G.run_oracle(m))
+    assert "g_light" in r
+    _check(r, 0)
+
+
+def test_lens_light_is_required_and_autograd_carries_it(rtu):
+    m = I.with_light(I.config_tiny(seed=34), n=2, seed=2, amp=0.5)
+    s = rtu.System.from_mock(m, precision=rtu.RTU_F64)
+    with pytest.raises(ValueError, match="lens light"):
+        rtu.Binding(s, m.lens, m.latents, m.ps)
+    lens = torch.tensor(m.lens, dtype=torch.float64, device="cuda", requires_grad=True)
+    lat = torch.tensor(m.latents, dtype=torch.float64, device="cuda", requires_grad=True)
+    ps = torch.tensor(m.ps, dtype=torch.float64, device="cuda", requires_grad=True)
+    light = torch.tensor(m.light, dtype=torch.float64, device="cuda", requires_grad=True)
+    logL = rtu.log_likelihood(s, lens, lat, ps, light)
+    (2.0 * logL).backward()
+    o = G.run_oracle(m)
+    assert G.rel_l2(light.grad.cpu().numpy().ravel(), 2.0 * o["g_light"]) < F64_TOL
+    assert abs(float(logL) - o["logL"]) < F64_TOL * abs(o["logL"])
+
+
+# ------------------------------------------------------- weighted RTU grid (Sec. 5)
+@pytest.mark.parametrize("kw,cap", [(dict(seed=51), 7), (dict(seed=52, sub_kind=I.SUB_NFW, n_sub=2), 30),
+                                    (dict(seed=53, n_img=17, s=3, n_src=12, psf_k=5), 3)])
+def test_weighted_grid_fp64_matches_oracle(rtu, kw, cap):
+    m = I.with_snr_weights(I.config_tiny(**kw), cap=cap)
+    g, _, _ = G.run_gpu(m, rtu.RTU_F64)
+    _check(G.compare(g, G.run_oracle(m)), 1)
+
+
+@pytest.mark.parametrize("seed", [1060, 1061])
+def test_weighted_grid_c2_fp32_matches_oracle(rtu, seed):
+    m = I.with_snr_weights(I.config_c2(seed), cap=100)
+    g, _, _ = G.run_gpu(m, rtu.RTU_F32)
+    _check(G.compare(g, G.run_oracle(m)), 0)
+
+
+def test_weighted_grid_rejects_zero_weights_on_the_mask(rtu):
+    m = I.with_snr_weights(I.config_tiny(seed=54), cap=5)
+    rtu.System.from_mock(m, precision=rtu.RTU_F64).close()         # valid weights
+    w = m.weights.copy()
+    w[np.nonzero(m.mask)[0][0], np.nonzero(m.mask)[1][0]] = 0
+    m.weights = w
+    with pytest.raises(rtu.RTUError, match="weights must be >= 1"):
+        rtu.System.from_mock(m, precision=rtu.RTU_F64)
