@@ -285,6 +285,34 @@ def run_ours(args):
         ms = float(t)
     value = world * n / (ms / 1e3)
 
+    # ---- the same step captured once as a CUDA graph and replayed (launch overhead
+    # of the ~20 kernels and the side-stream fork/join paid once at capture)
+    graph_ms = None
+    if not args.no_graph:
+        gs = torch.cuda.Stream()
+        gs.wait_stream(stream)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(gs):
+            step_on = lambda: (batch.forward(gs), batch.adjoint(gs))
+            step_on()                         # warm on the capture stream
+            gs.synchronize()
+            with torch.cuda.graph(graph, stream=gs):
+                step_on()
+        torch.cuda.synchronize()
+        for _ in range(3):
+            graph.replay()
+        torch.cuda.synchronize()
+        g0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        g1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        cur = torch.cuda.current_stream()
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            g0[i].record(cur)
+            graph.replay()
+            g1[i].record(cur)
+        torch.cuda.synchronize()
+        graph_ms = statistics.mean(a.elapsed_time(b) for a, b in zip(g0, g1))
+
     # ---- plain per-system path (one call per mock), same work
     per_system_value = None
     if not args.no_single:
@@ -360,6 +388,9 @@ def run_ours(args):
         "e2e": {"value": e2e, "unit": "evals/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "kernels": {k: {"launches": c, "avg_ms": t / c, "share": t / kern_tot} for k, (c, t) in kern.items()},
+        "cuda_graph": None if graph_ms is None else {
+            "value": world * n / (graph_ms / 1e3), "unit": "evals/s", "ms_per_step": graph_ms,
+            "note": "the batched step captured once as a CUDA graph, replayed per step"},
         "per_system_path": {"value": per_system_value, "unit": "evals/s",
                             "note": "same 32 evaluations issued as 32 single-system calls"},
         "roofline": {"kernel": dom + "<float>", "top_kernel": top[0], "bound": "alu", "achieved": achieved,
@@ -413,6 +444,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--mocks", type=int, default=N_MOCKS, help="mocks per rank (32 is the benchmark workload)")
     ap.add_argument("--no-single", action="store_true", help="skip the per-system comparison path")
+    ap.add_argument("--no-graph", action="store_true", help="skip the CUDA-graph replay timing")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--serve-n", type=int, default=4096, help="systems in the serving stream (0 = skip)")
     args = ap.parse_args()

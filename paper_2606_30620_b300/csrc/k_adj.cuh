@@ -153,8 +153,9 @@ __global__ void __launch_bounds__(CDF_NT) k_cdf_adj(const __grid_constant__ Batc
     }
 }
 
-// centre rays: d logL / d beta_i = selected-rank terms + dmu/N
-//   + [a = argmin sigma] dsigma (beta_i,a - mu_a)/(N sigma_min); then the lens
+// centre rays: d logL / d beta_i = dmu/N + [a = argmin sigma] dsigma (beta_i,a -
+//   mu_a)/(N sigma_min) here, then the lens (the selected-rank terms, large and
+//   few, are k_sel_adj's, in double)
 template <typename T>
 __global__ void __launch_bounds__(CTA_C) k_centre_adj(const __grid_constant__ Batch B) {
     const int ev = find_eval(B, blockIdx.x);
@@ -165,36 +166,15 @@ __global__ void __launch_bounds__(CTA_C) k_centre_adj(const __grid_constant__ Ba
     const int nl = 8 + 5 * nsub;
     __shared__ LensK<T> L;
     __shared__ LensK<double> Ld;
-    __shared__ int sidx[2][2 * MAXM];
-    __shared__ double sg[2][2 * MAXM];
     __shared__ double hdr[4], mu[2];
-    __shared__ double gsel[2][CTA_C];        // selected-rank terms of this CTA's rays
     __shared__ double red[CTA_C / 32][8];
     load_lensk(L, lensk_src<T>(E.lensk));
     if (sizeof(T) == 4) load_lensk(Ld, E.lensk);
-    for (int i = threadIdx.x; i < 2 * 2 * MAXM; i += blockDim.x) {
-        const int a = i / (2 * MAXM), t = i - a * 2 * MAXM;
-        const bool on = t < 2 * M && E.sel_idx[a * 2 * MAXM + t] >= 0;
-        sidx[a][t] = on ? E.sel_idx[a * 2 * MAXM + t] : -1;
-        sg[a][t] = on ? E.tadj[TADJ_SEL + a * 2 * MAXM + t] : 0.0;
-    }
     if (threadIdx.x < 4) hdr[threadIdx.x] = E.tadj[threadIdx.x];
     if (threadIdx.x == 2) hdr[2] = (E.tadj[4] + E.tadj[5]) / (N * E.trd[2]);
     if (threadIdx.x < 2) mu[threadIdx.x] = E.trd[threadIdx.x];
-    gsel[0][threadIdx.x] = 0.0;
-    gsel[1][threadIdx.x] = 0.0;
     __syncthreads();
-    const int k0 = tile * CTA_C;
-    if (threadIdx.x < 2) {
-        // the selected rays among this CTA's: their rank terms, in target order
-        const int a = threadIdx.x;
-        for (int t = 0; t < 2 * M; ++t) {
-            const int i = sidx[a][t] - k0;
-            if (i >= 0 && i < CTA_C) gsel[a][i] += sg[a][t];
-        }
-    }
-    __syncthreads();
-    const int k = k0 + threadIdx.x;
+    const int k = tile * CTA_C + threadIdx.x;
     double gb[2] = {0.0, 0.0};
     double xd = 0.0, yd = 0.0;
     if (k < N) {
@@ -203,7 +183,7 @@ __global__ void __launch_bounds__(CTA_C) k_centre_adj(const __grid_constant__ Ba
         for (int a = 0; a < 2; ++a) {
             double g = hdr[a];
             if (a == amin) g += hdr[2] * (b[a] - mu[a]);
-            gb[a] = g + gsel[a][threadIdx.x];
+            gb[a] = g;
         }
         // the pixel centre (sub-ray offset 0 at s = 1)
         const int pix = E.centre_idx[k];
@@ -258,6 +238,66 @@ __global__ void __launch_bounds__(CTA_C) k_centre_adj(const __grid_constant__ Ba
     }
 }
 
+// The selected-rank terms: every (axis, target) whose order statistic the QF
+// interpolates passes d logL / d beta of its ray to the lens, in double (these few
+// terms are large and partly cancel the image terms).  One CTA per evaluation, one
+// thread per (axis, target); the row after the centre CTAs' rows in cadj.
+constexpr int SEL_ADJ_NT = 4 * MAXM;
+__global__ void __launch_bounds__(SEL_ADJ_NT) k_sel_adj(const __grid_constant__ Batch B) {
+    const EvalArgs& E = B.e[blockIdx.x];
+    const int M = E.n_nodes;
+    const int nsub = E.sub_kind ? E.n_sub : 0;
+    const int nl = 8 + 5 * nsub;
+    __shared__ LensK<double> Ld;
+    __shared__ double red[SEL_ADJ_NT / 32][8];
+    load_lensk(Ld, E.lensk);
+    __syncthreads();
+    const int a = threadIdx.x / (2 * MAXM), t = threadIdx.x - a * 2 * MAXM;
+    const int ray = t < 2 * M ? E.sel_idx[a * 2 * MAXM + t] : -1;
+    double o8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    double xd = 0.0, yd = 0.0, g = 0.0;
+    if (ray >= 0 && ray < E.n_mask) {
+        g = E.tadj[TADJ_SEL + a * 2 * MAXM + t];
+        const int pix = E.centre_idx[ray];
+        const int pj = pix / E.n_img, pi = pix - pj * E.n_img;
+        const double c = 0.5 * (E.n_img - 1);
+        xd = (pi - c) * E.pix;
+        yd = (pj - c) * E.pix;
+        EplJ<double> J;
+        double bx, by;
+        lens_beta_eval(Ld, xd, yd, J, bx, by);
+        lens_beta_vjp(Ld, J, xd, yd, a == 0 ? g : 0.0, a == 1 ? g : 0.0, o8);
+    }
+    double* out = E.cadj + (size_t)E.n_cta_c * nl;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int p = 0; p < 8; ++p) {
+        const double v = warp_sum(o8[p]);
+        if (lane == 0) red[wid][p] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 8) {
+        double r = 0.0;
+        for (int w = 0; w < SEL_ADJ_NT / 32; ++w) r += red[w][threadIdx.x];
+        out[threadIdx.x] = r;
+    }
+    for (int h = 0; h < nsub; ++h) {
+        __syncthreads();
+        double a5[5] = {0, 0, 0, 0, 0};
+        if (ray >= 0 && ray < E.n_mask)
+            sub_vjp<double>(Ld, h, xd, yd, a == 0 ? g : 0.0, a == 1 ? g : 0.0, a5);
+        for (int c = 0; c < 5; ++c) {
+            const double v = warp_sum(a5[c]);
+            if (lane == 0) red[wid][c] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x < 5) {
+            double r = 0.0;
+            for (int w = 0; w < SEL_ADJ_NT / 32; ++w) r += red[w][threadIdx.x];
+            out[8 + 5 * h + threadIdx.x] = r;
+        }
+    }
+}
+
 // g_lens = (render-adjoint lens sums) + (centre-adjoint lens sums), fixed order
 __global__ void __launch_bounds__(64) k_grad_final(const __grid_constant__ Batch B) {
     const EvalArgs& E = B.e[blockIdx.x];
@@ -270,7 +310,7 @@ __global__ void __launch_bounds__(64) k_grad_final(const __grid_constant__ Batch
         double s = 0.0;
         for (int t = 0; t < E.n_cta_adj; ++t) s += E.apart[(size_t)t * nacc + col];
         double c = 0.0;
-        for (int t = 0; t < E.n_cta_c; ++t) c += E.cadj[(size_t)t * nl + p];
+        for (int t = 0; t <= E.n_cta_c; ++t) c += E.cadj[(size_t)t * nl + p];   // + the selected-rank row
         double g = s + c;
         if (p == 1 && E.profile == 0) g = 0.0;
         E.g_lens[p] = g;

@@ -158,6 +158,30 @@ __device__ __forceinline__ R sqrtP_and_grad(int family, const R* ps, R k, R* g) 
 
 __device__ __forceinline__ int n_family(int family) { return family == 2 ? 3 : 2; }
 
+// sqrt(P(k)) alone (the forward filter), with the parameter-only factors hoisted:
+// c[0] = sqrt(A) (power law, Matern-like) or the log prefactor (Eq. 4)
+template <typename R>
+__device__ __forceinline__ R sqrtP_only(int family, const R* ps, const R* c, R k) {
+    if (family == 0) return k == R(0) ? R(0) : c[0] * r_exp(R(-0.5) * ps[1] * r_log(k));
+    if (family == 1) {
+        const R kk = k / ps[1];
+        return c[0] / (R(1) + kk * kk);
+    }
+    const R a = R(2) * ps[1] / (ps[2] * ps[2]);
+    return r_exp(c[0] - R(0.5) * (ps[1] + R(1)) * r_log(a + k * k));
+}
+
+template <typename R>
+__device__ __forceinline__ void sqrtP_consts(int family, const R* ps, R* c) {
+    if (family == 0 || family == 1) {
+        c[0] = r_sqrt(ps[0]);
+    } else {
+        const R sg = ps[0], nn = ps[1], ze = ps[2];
+        const R a = R(2) * nn / (ze * ze);
+        c[0] = R(0.5) * (R(2) * r_log(sg) + r_log(R(4.0 * 3.14159265358979323846) * nn) + nn * r_log(a));
+    }
+}
+
 // ln(phi_sp(x) s0) without underflow, and sigma(x)/phi_sp(x)
 template <typename T>
 __device__ __forceinline__ T log_sp_s0(T x) {
@@ -190,48 +214,90 @@ __device__ __forceinline__ void gp_setup(const EvalArgs& E, Cx<T>* tw_s, int* re
     __syncthreads();
 }
 
-// S6: f = Re F^-1(sqrt(P) F(w)) (1/N^2 on the inverse), s* = (phi_sp(f/s0) s0)^alpha
-template <typename T>
-__global__ void __launch_bounds__(GP_NT) k_gp_source(const __grid_constant__ Batch B) {
-    const EvalArgs& E = B.e[blockIdx.x];
-    const int n = E.n_src, n2 = n * n;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    Cx<T>* sm = reinterpret_cast<Cx<T>*>(smem_raw);
+// S6 spread over many CTAs: the source's 2-D FFTs as four passes of 1-D line
+// FFTs (GP_LINES lines of one evaluation per CTA), computed in double in both
+// precisions.  Near f = 0 the softplus turns an absolute error of f into a relative
+// error of s* amplified by 1/s0 = 100, and a float FFT's absolute error (~1e-7 of
+// max |f|) reaches the gradients at their 1e-5 tolerance; one CTA per evaluation
+// in double would leave the FP64 pipe of a single SM doing the whole transform.
+//   pass 0: forward FFT of the rows of w (real) -> W
+//   pass 1: forward FFT of the columns of W, times sqrt(P(k))
+//   pass 2: inverse FFT of the rows
+//   pass 3: inverse FFT of the columns; f = Re / N^2, s* = (phi_sp(f/s0) s0)^alpha
+// W (complex double, row-major) stays in the workspace between the passes (L2).
+constexpr int GP_LINES = 8;
+constexpr int GP_LINE_NT = 256;
+template <typename TS>
+__global__ void __launch_bounds__(GP_LINE_NT) k_gp_lines(const __grid_constant__ Batch B, int pass) {
+    typedef double T;
+    const int ev = find_eval(B, blockIdx.x);
+    const EvalArgs& E = B.e[ev];
+    const int tile = blockIdx.x - B.tile0[ev];
+    const int n = E.n_src;
+    __shared__ Cx<T> sm[GP_LINES * 256];
     __shared__ Cx<T> tw_s[256];
     __shared__ int rev_s[256];
     __shared__ int rad_s[MAX_RADIX];
     gp_setup<T>(E, tw_s, rev_s, rad_s);
-    const int chunk = max(1, min(n, (int)(GP_SMEM / sizeof(Cx<T>)) / n));
+    const bool cols = pass & 1, inv = pass >= 2;
+    const int l0 = tile * GP_LINES, cnt = min(GP_LINES, n - l0);
+    if (cnt <= 0) return;
     Cx<T>* W = reinterpret_cast<Cx<T>*>(E.cbufA);
-    const T* w = reinterpret_cast<const T*>(E.latents);
-    for (int i = threadIdx.x; i < n2; i += blockDim.x) W[i] = Cx<T>{w[i], T(0)};
-    __syncthreads();
-    fft2<T>(W, n, rad_s, E.nrad, tw_s, rev_s, sm, chunk, false);
-    const int nf = n_family(E.family);
-    T psv[4];
-    for (int q = 0; q < nf; ++q) psv[q] = (T)E.ps[q];
-    const T kscale = (T)(2.0 * 3.14159265358979323846 / E.pitch);
-    for (int i = threadIdx.x; i < n2; i += blockDim.x) {
-        const int ky = i / n, kx = i - ky * n;
-        const T fx = fftfreq<T>(kx, n), fy = fftfreq<T>(ky, n);
-        const T k = kscale * r_sqrt(fx * fx + fy * fy);
-        T gdummy[3];
-        const T sp = sqrtP_and_grad<T>(E.family, psv, k, gdummy);
-        W[i] = Cx<T>{W[i].x * sp, W[i].y * sp};
+    const TS* w = reinterpret_cast<const TS*>(E.latents);
+    // load with digit reversal: line q position p <- element rev[p]
+    for (int i = threadIdx.x; i < cnt * n; i += blockDim.x) {
+        if (!cols) {
+            const int q = i / n, p = i - q * n;
+            const int at = (l0 + q) * n + rev_s[p];
+            sm[q * n + p] = pass == 0 ? Cx<T>{(T)w[at], T(0)} : W[at];
+        } else {
+            const int p = i / cnt, q = i - p * cnt;
+            sm[q * n + p] = W[rev_s[p] * n + l0 + q];
+        }
     }
     __syncthreads();
-    fft2<T>(W, n, rad_s, E.nrad, tw_s, rev_s, sm, chunk, true);
-    const T alpha = (T)E.ps[nf];
-    const T inv_n2 = T(1) / T(n2);
-    T* fld = reinterpret_cast<T*>(E.fld);
-    T* src = reinterpret_cast<T*>(E.src);
-    T* so = reinterpret_cast<T*>(E.source_out);
-    for (int i = threadIdx.x; i < n2; i += blockDim.x) {
-        const T f = W[i].x * inv_n2;
-        const T s = r_exp(alpha * log_sp_s0<T>(f / T(0.01)));
-        fld[i] = f;
-        src[i] = s;
-        if (so) so[i] = s;
+    fft_seq_smem<T>(sm, cnt, n, rad_s, E.nrad, tw_s, inv);
+    if (pass == 0 || pass == 2) {
+        for (int i = threadIdx.x; i < cnt * n; i += blockDim.x) {
+            const int q = i / n, p = i - q * n;
+            W[(l0 + q) * n + p] = sm[q * n + p];
+        }
+        return;
+    }
+    if (pass == 1) {
+        // times sqrt(P(k)) (Eq. 1): column l0 + q is kx, row p is ky
+        const int nf = n_family(E.family);
+        T psv[4], pc[1];
+        for (int q = 0; q < nf; ++q) psv[q] = E.ps[q];
+        sqrtP_consts<T>(E.family, psv, pc);
+        const T kscale = 2.0 * 3.14159265358979323846 / E.pitch;
+        for (int i = threadIdx.x; i < cnt * n; i += blockDim.x) {
+            const int p = i / cnt, q = i - p * cnt;
+            const T fx = fftfreq<T>(l0 + q, n), fy = fftfreq<T>(p, n);
+            const T k = kscale * sqrt(fx * fx + fy * fy);
+            const T sp = sqrtP_only<T>(E.family, psv, pc, k);
+            const Cx<T> v = sm[q * n + p];
+            W[p * n + l0 + q] = Cx<T>{v.x * sp, v.y * sp};
+        }
+        return;
+    }
+    // pass 3: the field and the source brightness (the map in the storage type: f is
+    // already accurate, and the softplus of an accurately rounded argument is too)
+    const int nf = n_family(E.family);
+    const TS alpha = (TS)E.ps[nf];
+    const T inv_n2 = 1.0 / ((T)n * n);
+    TS* fld = reinterpret_cast<TS*>(E.fld);
+    TS* src = reinterpret_cast<TS*>(E.src);
+    TS* so = reinterpret_cast<TS*>(E.source_out);
+    for (int i = threadIdx.x; i < cnt * n; i += blockDim.x) {
+        const int p = i / cnt, q = i - p * cnt;
+        const T f = sm[q * n + p].x * inv_n2;
+        const TS fs = (TS)f;
+        const TS sv = r_exp(alpha * log_sp_s0<TS>((TS)(f / 0.01)));
+        const int at = p * n + l0 + q;
+        fld[at] = fs;
+        src[at] = sv;
+        if (so) so[at] = sv;
     }
 }
 

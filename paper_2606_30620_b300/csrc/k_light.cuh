@@ -18,10 +18,10 @@ __global__ void __launch_bounds__(CTA_R) k_light_adj(const __grid_constant__ Bat
     const EvalArgs& E = B.e[ev];
     const int tile = blockIdx.x - B.tile0[ev];
     __shared__ LightK<T> L;
-    __shared__ T offx[8];
+    __shared__ PixGeom<T> G;
     __shared__ TP wred[CTA_R / 32][6 * MAX_LIGHT];
     light_setup<T>(L, E.light, E.n_light);
-    if ((int)threadIdx.x < E.s) offx[threadIdx.x] = (T)(((threadIdx.x + 0.5) / E.s - 0.5) * E.pix);
+    pixgeom_setup<T>(G, E.pix, E.n_img, E.s);
     __syncthreads();
     const int nl = L.n;
     if (nl == 0) return;
@@ -35,10 +35,8 @@ __global__ void __launch_bounds__(CTA_R) k_light_adj(const __grid_constant__ Bat
     if (valid) {
         const T g = reinterpret_cast<const T*>(E.gimg)[pixel] / T(s2);
         const int pj = pixel / E.n_img, pi = pixel - pj * E.n_img;
-        const T cx = T(pi) * (T)E.pix - (T)(0.5 * (E.n_img - 1) * E.pix);
-        const T cy = T(pj) * (T)E.pix - (T)(0.5 * (E.n_img - 1) * E.pix);
         for (int q = 0; q < s2; ++q) {
-            const T x = cx + offx[q % s], y = cy + offx[q / s];
+            const T x = ray_coord(G, pi, q % s), y = ray_coord(G, pj, q / s);
 #pragma unroll
             for (int n = 0; n < MAX_LIGHT; ++n) {
                 if (n < nl) {

@@ -219,10 +219,9 @@ struct RenderShared {
     T U[MAXM + 2];
     double trd[TR_HDR + 4 * (MAXM + 2)];
     double Ud[MAXM + 2];
-    T offx[8];                 // sub-ray offsets ((a + 1/2)/s - 1/2) pix
+    PixGeom<T> G;              // sub-ray positions
     T ih[2 * (MAXM + 2)];      // 1/(X_{j+1} - X_j) per knot interval, axis-major
     UDiv dv_s2, dv_n, dv_s, dv_nc;   // dividers by s^2, n_img, s, n_src - 1
-    T pixT, cT;                // pixel size and (n_img - 1)/2 pix in the kernel's type
     LightK<T> L;               // MGE lens light (App. A.3)
 };
 
@@ -246,11 +245,9 @@ __device__ __forceinline__ void render_setup(const EvalArgs& E, RenderShared<T>&
             }
         }
     }
-    if (threadIdx.x < E.s) sh.offx[threadIdx.x] = (T)(((threadIdx.x + 0.5) / E.s - 0.5) * E.pix);
+    pixgeom_setup<T>(sh.G, E.pix, E.n_img, E.s);
     light_setup<T>(sh.L, E.light, E.n_light);
     if (threadIdx.x == 0) {
-        sh.pixT = (T)E.pix;
-        sh.cT = (T)(0.5 * (E.n_img - 1) * E.pix);
         sh.dv_s2 = udiv_make((uint32_t)(E.s * E.s));
         sh.dv_n = udiv_make((uint32_t)E.n_img);
         sh.dv_s = udiv_make((uint32_t)E.s);
@@ -264,61 +261,65 @@ __device__ __forceinline__ void render_setup(const EvalArgs& E, RenderShared<T>&
 // P_max (1 + f/(1 - f)) (|c_n| < f, |w| = 1) with P = pref0 (b/R)^(t-1) taken at the
 // box's smallest (t > 1) or largest (t < 1) elliptical radius R -- R >= q |theta - c|,
 // and R is convex so its maximum sits at a corner -- and the shear deflection is
-// linear (extremes at the corners).  Tiles with subhaloes are never culled.
-__device__ inline bool tile_out_of_reach(const EvalArgs& E, const LensK<double>& Kd, int tile) {
-    if (Kd.nsub > 0) return false;
+// linear (extremes at the corners).  Evaluated in float by one thread from the
+// float lens block, with slack far above float rounding.  Tiles with subhaloes are
+// never culled.
+__device__ inline bool tile_out_of_reach(const EvalArgs& E, int tile) {
+    const LensK<float>& Kf = *reinterpret_cast<const LensK<float>*>(lensk_src<float>(E.lensk));
+    if (Kf.nsub > 0) return false;
     const int n = E.n_img, tx_n = render_tiles_x(n);
     const int ty = tile / tx_n, tx = tile - ty * tx_n;
     const int i0 = tx * RT_X, i1 = min(i0 + RT_X - 1, n - 1);
     const int j0 = ty * RT_Y, j1 = min(j0 + RT_Y - 1, n - 1);
-    const double c = 0.5 * (n - 1), pix = E.pix;
-    const double omin = (0.5 / E.s - 0.5) * pix, omax = ((E.s - 0.5) / E.s - 0.5) * pix;
-    const double xl = (i0 - c) * pix + omin, xh = (i1 - c) * pix + omax;
-    const double yl = (j0 - c) * pix + omin, yh = (j1 - c) * pix + omax;
-    const EplC<double>& C = Kd.C;
+    const float c = 0.5f * (n - 1), pix = (float)E.pix;
+    const float omin = (0.5f / E.s - 0.5f) * pix, omax = ((E.s - 0.5f) / E.s - 0.5f) * pix;
+    const float xl = (i0 - c) * pix + omin, xh = (i1 - c) * pix + omax;
+    const float yl = (j0 - c) * pix + omin, yh = (j1 - c) * pix + omax;
+    const EplC<float>& C = Kf.C;
     // elliptical radius bounds over the box
-    const double cx = fmin(fmax(C.x0, xl), xh), cy = fmin(fmax(C.y0, yl), yh);
-    const double dmin = sqrt((cx - C.x0) * (cx - C.x0) + (cy - C.y0) * (cy - C.y0));
-    double rmax = 0.0, shx_lo = 1e300, shx_hi = -1e300, shy_lo = 1e300, shy_hi = -1e300;
+    const float cx = fminf(fmaxf(C.x0, xl), xh), cy = fminf(fmaxf(C.y0, yl), yh);
+    const float dmin = sqrtf((cx - C.x0) * (cx - C.x0) + (cy - C.y0) * (cy - C.y0));
+    float rmax = 0.0f, shx_lo = 1e30f, shx_hi = -1e30f, shy_lo = 1e30f, shy_hi = -1e30f;
     for (int k = 0; k < 4; ++k) {
-        const double x = (k & 1) ? xh : xl, y = (k & 2) ? yh : yl;
-        const double dx = x - C.x0, dy = y - C.y0;
-        const double xr = C.cp * dx + C.sp * dy, yr = C.cp * dy - C.sp * dx;
-        rmax = fmax(rmax, sqrt(C.q * C.q * xr * xr + yr * yr));
-        const double sx = Kd.g1 * x + Kd.g2 * y, sy = Kd.g2 * x - Kd.g1 * y;
-        shx_lo = fmin(shx_lo, sx); shx_hi = fmax(shx_hi, sx);
-        shy_lo = fmin(shy_lo, sy); shy_hi = fmax(shy_hi, sy);
+        const float x = (k & 1) ? xh : xl, y = (k & 2) ? yh : yl;
+        const float dx = x - C.x0, dy = y - C.y0;
+        const float xr = C.cp * dx + C.sp * dy, yr = C.cp * dy - C.sp * dx;
+        rmax = fmaxf(rmax, sqrtf(C.q * C.q * xr * xr + yr * yr));
+        const float sx = Kf.g1 * x + Kf.g2 * y, sy = Kf.g2 * x - Kf.g1 * y;
+        shx_lo = fminf(shx_lo, sx); shx_hi = fmaxf(shx_hi, sx);
+        shy_lo = fminf(shy_lo, sy); shy_hi = fmaxf(shy_hi, sy);
     }
-    const double rmin = C.q * dmin;
-    const double e = C.t - 1.0;
-    double pmax;
-    if (e > 1e-12) {
-        if (rmin < 1e-6) return false;
-        pmax = C.pref0 * pow(C.b / rmin, e);
-    } else if (e < -1e-12) {
-        pmax = C.pref0 * pow(C.b / fmax(rmax, 1e-10), e);
+    const float rmin = C.q * dmin * 0.999f;
+    const float e = C.t - 1.0f;
+    float pmax;
+    if (e > 1e-6f) {
+        if (rmin < 1e-4f) return false;
+        pmax = C.pref0 * powf(C.b / rmin, e);
+    } else if (e < -1e-6f) {
+        pmax = C.pref0 * powf(C.b / fmaxf(rmax * 1.001f, 1e-6f), e);
     } else {
-        pmax = C.pref0;
+        pmax = C.pref0 * powf(fmaxf(C.b / fmaxf(rmin, 1e-4f), fmaxf(rmax, 1e-4f) / C.b), fabsf(e));
     }
-    const double amax = pmax * (1.0 + C.ftail) * (1.0 + 1e-6) + 1e-9;
+    const float amax = pmax * (1.0f + C.ftail) * 1.001f + 1e-4f;
+    const float sh_slack = 1e-5f * (fabsf(xl) + fabsf(xh) + fabsf(yl) + fabsf(yh) + 1.0f);
     // beta = theta - alpha_EPL - alpha_shear ranges per axis
-    const double bxl = xl - shx_hi - amax, bxh = xh - shx_lo + amax;
-    const double byl = yl - shy_hi - amax, byh = yh - shy_lo + amax;
+    const float bxl = xl - shx_hi - amax - sh_slack, bxh = xh - shx_lo + amax + sh_slack;
+    const float byl = yl - shy_hi - amax - sh_slack, byh = yh - shy_lo + amax + sh_slack;
     // the grid's reach in beta: z in [zlo, zhi] as in the ray test, with slack
     const int K = E.n_nodes + 2;
-    const double* tr = E.trd;
-    const double mu[2] = {tr[0], tr[1]}, sg = tr[2];
-    const double m = 4.0 * (double)EDGE_DELTA / (E.n_src - 1);
+    const float* tr = E.trf;
+    const float m = 4.0f * EDGE_DELTA / (E.n_src - 1);
     bool out = false;
     for (int a = 0; a < 2; ++a) {
-        const double* X = tr + TR_HDR + a * K;
-        const double* d = tr + TR_HDR + (2 + a) * K;
-        double zlo = X[0] - m / d[0], zhi = X[K - 1] + m / d[K - 1];
-        zlo -= 1e-4 * (1.0 + fabs(zlo));
-        zhi += 1e-4 * (1.0 + fabs(zhi));
-        const double lo = mu[a] + zlo * sg, hi = mu[a] + zhi * sg;
-        const double bl = a == 0 ? bxl : byl, bh = a == 0 ? bxh : byh;
-        out |= bh < lo || bl > hi;
+        const float* X = tr + TR_HDR + a * K;
+        const float* d = tr + TR_HDR + (2 + a) * K;
+        float zlo = X[0] - m / d[0], zhi = X[K - 1] + m / d[K - 1];
+        zlo -= 1e-3f * (1.0f + fabsf(zlo));
+        zhi += 1e-3f * (1.0f + fabsf(zhi));
+        const float lo = tr[a] + zlo * tr[2], hi = tr[a] + zhi * tr[2];
+        const float lo_s = lo - 1e-5f * (1.0f + fabsf(lo)), hi_s = hi + 1e-5f * (1.0f + fabsf(hi));
+        const float bl = a == 0 ? bxl : byl, bh = a == 0 ? bxh : byh;
+        out |= bh < lo_s || bl > hi_s;
     }
     return out;
 }
@@ -334,7 +335,6 @@ __global__ void __launch_bounds__(CTA_R, 6) k_render(const __grid_constant__ Bat
     __shared__ RenderShared<T> sh;
     __shared__ __align__(8) uint64_t mbar;
     const int n = E.n_src, K = E.n_nodes + 2;
-    render_setup<T>(E, sh);
     __shared__ int cnt_sh, cull_sh;
     bool valid;
     const int pixel = render_pixel(E.n_img, tile, threadIdx.x, valid);
@@ -342,21 +342,26 @@ __global__ void __launch_bounds__(CTA_R, 6) k_render(const __grid_constant__ Bat
     const int s = E.s, s2 = E.s * E.s;
     if (threadIdx.x == 0) {
         cnt_sh = 0;
-        cull_sh = tile_out_of_reach(E, *reinterpret_cast<const LensK<double>*>(E.lensk), tile) ? 1 : 0;
+        cull_sh = tile_out_of_reach(E, tile) ? 1 : 0;
     }
     __syncthreads();
     if (cull_sh) {
         // no ray of this tile reaches the grid: only the lens light, nothing staged
         if (threadIdx.x < CTA_R / 32) E.useg[tile * (CTA_R / 32) + threadIdx.x] = 0;
         if (threadIdx.x == 0) E.cta_cnt[tile] = 0;
+        if (E.n_light > 0) {
+            pixgeom_setup<T>(sh.G, E.pix, E.n_img, E.s);
+            light_setup<T>(sh.L, E.light, E.n_light);
+            if (threadIdx.x == 0) { sh.dv_n = udiv_make((uint32_t)E.n_img); sh.dv_s = udiv_make((uint32_t)E.s); }
+            __syncthreads();
+        }
         if (!valid) return;
         T acc = T(0);
-        if (sh.L.n) {
+        if (E.n_light > 0) {
             const int pj = (int)udiv((uint32_t)pixel, sh.dv_n), pi = pixel - pj * E.n_img;
-            const T cx = T(pi) * sh.pixT - sh.cT, cy = T(pj) * sh.pixT - sh.cT;
             for (int q = 0; q < s2; ++q) {
                 const int qb = (int)udiv((uint32_t)q, sh.dv_s), qa = q - qb * s;
-                acc += light_at(sh.L, cx + sh.offx[qa], cy + sh.offx[qb]);
+                acc += light_at(sh.L, ray_coord(sh.G, pi, qa), ray_coord(sh.G, pj, qb));
             }
         }
         if (sizeof(T) == 4) E.pdef[pixel] = 0ull;
@@ -365,6 +370,7 @@ __global__ void __launch_bounds__(CTA_R, 6) k_render(const __grid_constant__ Bat
         if (E.image_out) reinterpret_cast<T*>(E.image_out)[pixel] = val;
         return;
     }
+    render_setup<T>(E, sh);
     if (!stage_to_smem(sgrid, E.src, (uint32_t)(n * n * sizeof(T)), &mbar, E.flags)) {
         // the copy timed out (flagged): this tile stages nothing
         if (threadIdx.x < CTA_R / 32) E.useg[tile * (CTA_R / 32) + threadIdx.x] = 0;
@@ -388,8 +394,7 @@ __global__ void __launch_bounds__(CTA_R, 6) k_render(const __grid_constant__ Bat
         zhi[a] = X[K - 1] + m / d[K - 1];
     }
     const int pj = (int)udiv((uint32_t)pixel, sh.dv_n), pi = pixel - pj * E.n_img;
-    const T pixT = sh.pixT, cT = sh.cT;
-    const T cx = T(pi) * pixT - cT, cy = T(pj) * pixT - cT;
+
     T acc = T(0);
     unsigned long long deferred = 0ull;      // bit q: sub-ray q went to the double pass
     // this warp's staging segment: in-grid and deferred rays appended in (q, lane) order
@@ -399,7 +404,7 @@ __global__ void __launch_bounds__(CTA_R, 6) k_render(const __grid_constant__ Bat
     // code of a sub-ray: -1 no cell, 0 deferred to the double pass, c + 1 in cell c
     auto trace = [&](int q) -> int {
         const int qb = (int)udiv((uint32_t)q, sh.dv_s), qa = q - qb * s;
-        const T x = cx + sh.offx[qa], y = cy + sh.offx[qb];
+        const T x = ray_coord(sh.G, pi, qa), y = ray_coord(sh.G, pj, qb);
         if (sh.L.n) acc += light_at(sh.L, x, y);       // lens light at every sub-ray
         T yx, yy;
         if (sizeof(T) == 4 && lens_near_core(sh.K, x, y)) {
@@ -711,7 +716,6 @@ __global__ void __launch_bounds__(CTA_R, 4) k_render_adj(const __grid_constant__
     R2* gbuf = reinterpret_cast<R2*>(E.gbuf);
     const T* gimg = reinterpret_cast<const T*>(E.gimg);
     // pixel centre x = i pix - c, c = (n_img - 1)/2 pix, in the kernel's type
-    const T pixT = sh.pixT, cT = sh.cT;
     const T inv_s2 = T(1) / T(s2);
 
     T acc[NACC_FIX];
@@ -783,8 +787,8 @@ __global__ void __launch_bounds__(CTA_R, 4) k_render_adj(const __grid_constant__
                 const int pixel = (int)udiv((uint32_t)ray, sh.dv_s2), q = ray - pixel * s2;
                 const int pj = (int)udiv((uint32_t)pixel, sh.dv_n), pi = pixel - pj * E.n_img;
                 const int qb = (int)udiv((uint32_t)q, sh.dv_s), qa = q - qb * s;
-                const T x = (T(pi) * pixT - cT) + sh.offx[qa];
-                const T y = (T(pj) * pixT - cT) + sh.offx[qb];
+                const T x = ray_coord(sh.G, pi, qa);
+                const T y = ray_coord(sh.G, pj, qb);
                 const T gpix = gimg[pixel] * inv_s2;
                 const bool near = sizeof(T) == 4 && lens_near_core(sh.K, x, y);
                 EplJ<T> J;
@@ -881,10 +885,10 @@ __global__ void __launch_bounds__(CTA_R) k_sub_adj(const __grid_constant__ Batch
     const EvalArgs& E = B.e[ev];
     const int tile = blockIdx.x - B.tile0[ev];
     __shared__ LensK<T> K;
-    __shared__ T offx[8];
+    __shared__ PixGeom<T> G;
     __shared__ double wsub[CTA_R / 32][5];
     load_lensk(K, lensk_src<T>(E.lensk));
-    if (threadIdx.x < E.s) offx[threadIdx.x] = (T)(((threadIdx.x + 0.5) / E.s - 0.5) * E.pix);
+    pixgeom_setup<T>(G, E.pix, E.n_img, E.s);
     __syncthreads();
     const int Kn = E.n_nodes + 2;
     const int nacc = NACC_FIX + 4 * Kn + 5 * K.nsub;
@@ -893,7 +897,6 @@ __global__ void __launch_bounds__(CTA_R) k_sub_adj(const __grid_constant__ Batch
     const int n_rays = E.n_img * E.n_img * E.s * E.s;
     const int total = max(0, min(E.useg[nu], n_rays));
     const int s = E.s, s2 = s * s;
-    const T pixT = (T)E.pix, cT = (T)(0.5 * (E.n_img - 1) * E.pix);
     const R2* gbuf = reinterpret_cast<const R2*>(E.gbuf);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int chunk = CTA_R * ADJ_RPT;
@@ -909,8 +912,8 @@ __global__ void __launch_bounds__(CTA_R) k_sub_adj(const __grid_constant__ Batch
                 if (ray < 0 || ray >= n_rays) continue;
                 const int pixel = ray / s2, q = ray - pixel * s2;
                 const int pj = pixel / E.n_img, pi = pixel - pj * E.n_img;
-                const T x = (T(pi) * pixT - cT) + offx[q % s];
-                const T y = (T(pj) * pixT - cT) + offx[q / s];
+                const T x = ray_coord(G, pi, q % s);
+                const T y = ray_coord(G, pj, q / s);
                 sub_vjp<T>(K, h, x, y, g.x, g.y, a5);
             }
         }

@@ -109,14 +109,14 @@ size_t slot_layout(const rtu_system_desc& d, char* base, EvalArgs* e) {
     p = take((size_t)2 * z.nm_max * 8);               if (e) e->beta = (double*)p;
     p = take((size_t)z.n_cta_c_max * 8 * 8);          if (e) e->cpart = (double*)p;
     p = take((size_t)z.n_cta_c_max * 2 * 8);          if (e) e->cpart2 = (double*)p;
-    p = take((size_t)z.n_cta_c_max * z.nl * 8);       if (e) e->cadj = (double*)p;
+    p = take((size_t)(z.n_cta_c_max + 1) * z.nl * 8); if (e) e->cadj = (double*)p;
     p = take((size_t)2 * HB * 4);                     if (e) e->hist = (int*)p;
     p = take((size_t)tr_size(z.K) * 8);               if (e) e->trd = (double*)p;
     p = take((size_t)tr_size(z.K) * 4);               if (e) e->trf = (float*)p;
     p = take((size_t)4 * MAXM * 4);                   if (e) e->sel_idx = (int*)p;
     p = take((size_t)(TADJ_SEL + 4 * MAXM) * 8);      if (e) e->tadj = (double*)p;
     const size_t n2 = (size_t)d.n_src * d.n_src;
-    p = take(n2 * 2 * z.tb);                          if (e) e->cbufA = p;
+    p = take(n2 * 2 * 8);                             if (e) e->cbufA = p;     // complex double (the GP source)
     p = take(n2 * 2 * z.tb);                          if (e) e->cbufB = p;
     p = take(n2 * z.tb);                              if (e) e->fld = p;
     p = take(n2 * z.tb);                              if (e) e->src = p;
@@ -259,8 +259,6 @@ constexpr int MAX_DYN = 200 * 1024;
 
 void set_attributes() {
     cudaFuncSetAttribute(k_select_fit, cudaFuncAttributeMaxDynamicSharedMemorySize, SEL_SMEM);
-    cudaFuncSetAttribute(k_gp_source<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, GP_SMEM);
-    cudaFuncSetAttribute(k_gp_source<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, GP_SMEM);
     cudaFuncSetAttribute(k_gp_adjoint<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, GP_SMEM);
     cudaFuncSetAttribute(k_gp_adjoint<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, GP_SMEM);
     cudaFuncSetAttribute(k_render<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN);
@@ -377,12 +375,27 @@ rtu_status rtu_system_create(const rtu_system_desc* d, void* ws, size_t ws_bytes
     }
     std::vector<int> rev = digit_reversal(d->n_src, rad);
     std::vector<double> cheb = chebyshev_tables(d->n_nodes, d->degree);
-    if ((ce = cudaMemcpy(s->cidx, idx.data(), idx.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (ce = cudaMemcpy(s->cheb, cheb.data(), cheb.size() * 8, cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (ce = cudaMemcpy(s->tw, tw.data(), tw.size() * 8, cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (ce = cudaMemcpy(s->rev, rev.data(), rev.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess) {
-        delete s;
-        return fail(RTU_E_CUDA, std::string("table upload: ") + cudaGetErrorString(ce));
+    {
+        // the static tables assembled on the host with the device layout, one copy
+        // (the centre weights, if any, were uploaded above)
+        std::vector<char> img(st, 0);
+        int* hcidx;
+        double *htw, *hcheb;
+        int* hrev;
+        uint32_t* hcwt;
+        static_layout(*d, img.data(), &hcidx, &htw, &hrev, &hcheb, &hcwt);
+        memcpy(hcidx, idx.data(), idx.size() * 4);
+        memcpy(htw, tw.data(), tw.size() * 8);
+        memcpy(hrev, rev.data(), rev.size() * 4);
+        memcpy(hcheb, cheb.data(), cheb.size() * 8);
+        const size_t cw_off = (size_t)(reinterpret_cast<char*>(hcwt) - img.data());
+        const size_t cw_end = (size_t)(reinterpret_cast<char*>(htw) - img.data());
+        // upload around the weights region so a weighted system keeps its weights
+        if ((ce = cudaMemcpy(base, img.data(), cw_off, cudaMemcpyHostToDevice)) != cudaSuccess ||
+            (ce = cudaMemcpy(base + cw_end, img.data() + cw_end, st - cw_end, cudaMemcpyHostToDevice)) != cudaSuccess) {
+            delete s;
+            return fail(RTU_E_CUDA, std::string("table upload: ") + cudaGetErrorString(ce));
+        }
     }
     const size_t per = slot_layout(*d, nullptr, nullptr);
     const size_t sper = sample_layout(*d, nullptr, nullptr);
@@ -476,6 +489,7 @@ rtu_status launch(const char* name, Kern kern, Batch& B, TileFn tiles, int threa
 
 int t_one(const EvalArgs&) { return 1; }
 int t_two(const EvalArgs&) { return 2; }
+int t_gp_lines(const EvalArgs& e) { return (e.n_src + GP_LINES - 1) / GP_LINES; }
 int t_zero(const EvalArgs&) { return ZERO_TILES; }
 int t_centre(const EvalArgs& e) { return e.n_cta_c; }
 int t_render(const EvalArgs& e) { return e.n_cta_r; }
@@ -544,7 +558,8 @@ rtu_status run_chunk(Batch& B, int phase, cudaStream_t st, const SideStream& ss)
     if (phase & PH_FORWARD) {
         // S6 only needs the latents and spectrum parameters: beside S1-S5
         if ((r = stream_after(ss.s, st, ss.fork))) return r;
-        if ((r = launch("k_gp_source", k_gp_source<T>, B, t_one, GP_NT, GP_SMEM, ss.s))) return r;
+        for (int pass = 0; pass < 4; ++pass)
+            if ((r = launch("k_gp_source", k_gp_lines<T>, B, t_gp_lines, GP_LINE_NT, 0, ss.s, pass))) return r;
     }
     if (phase & (PH_GRID | PH_FORWARD)) {
         if ((r = launch("k_zero", k_zero, B, t_zero, 256, 0, st, (phase & PH_FORWARD) ? 1 : 0))) return r;
@@ -584,6 +599,7 @@ rtu_status run_chunk(Batch& B, int phase, cudaStream_t st, const SideStream& ss)
         if ((r = stream_after(ss.s, st, ss.fork))) return r;
         if ((r = launch("k_cdf_adj", k_cdf_adj, B, t_two, CDF_NT, 0, ss.s))) return r;
         if ((r = launch("k_centre_adj", k_centre_adj<T>, B, t_centre, CTA_C, 0, ss.s))) return r;
+        if ((r = launch("k_sel_adj", k_sel_adj, B, t_one, SEL_ADJ_NT, 0, ss.s))) return r;
         if ((r = launch("k_cell_gather", k_cell_gather<T>, B, t_cells, GATHER_NT, 0, st))) return r;
         if ((r = launch("k_gp_adjoint", k_gp_adjoint<T>, B, t_one, GP_NT, GP_SMEM, st))) return r;
         if ((r = stream_after(st, ss.s, ss.join))) return r;
@@ -716,17 +732,18 @@ rtu_status rtu_elbo_init(rtu_system* s, const rtu_prior* priors, const double* f
             return fail(RTU_E_ARG, "bounded prior needs d > c");
         if (p.kind == RTU_PRIOR_LINEAR && !(p.a >= -1.0)) return fail(RTU_E_ARG, "linear prior needs a >= -1");
     }
-    std::vector<double> zero((size_t)2 * z.n_state, 0.0);
-    long long t0 = 0;
-    cudaError_t ce;
-    if ((ce = cudaMemcpy(s->st.prior, priors, (size_t)z.n_sites * sizeof(rtu_prior), cudaMemcpyHostToDevice)) ||
-        (ce = cudaMemcpy(s->st.fixed, fixed, (size_t)z.n_fixed * 8, cudaMemcpyHostToDevice)) ||
-        (ce = cudaMemcpy(s->st.loc, loc, (size_t)z.n_state * 8, cudaMemcpyHostToDevice)) ||
-        (ce = cudaMemcpy(s->st.rho, rho, (size_t)z.n_state * 8, cudaMemcpyHostToDevice)) ||
-        (ce = cudaMemcpy(s->st.m, zero.data(), zero.size() * 8, cudaMemcpyHostToDevice)) ||
-        (ce = cudaMemcpy(s->st.v, zero.data(), zero.size() * 8, cudaMemcpyHostToDevice)) ||
-        (ce = cudaMemcpy(s->st.t, &t0, 8, cudaMemcpyHostToDevice)))
-        return fail(RTU_E_CUDA, std::string("rtu_elbo_init: ") + cudaGetErrorString(ce));
+    // the state region (loc, rho, Adam m and v, priors, fixed values, step) assembled
+    // on the host with the device layout, then one copy
+    const size_t span = (size_t)(reinterpret_cast<char*>(s->st.t) + 8 - reinterpret_cast<char*>(s->st.loc));
+    std::vector<char> img(span, 0);
+    ElboState hs;
+    state_layout(s->d, img.data(), &hs);
+    memcpy(hs.loc, loc, (size_t)z.n_state * 8);
+    memcpy(hs.rho, rho, (size_t)z.n_state * 8);
+    memcpy(hs.prior, priors, (size_t)z.n_sites * sizeof(rtu_prior));
+    memcpy(hs.fixed, fixed, (size_t)z.n_fixed * 8);
+    cudaError_t ce = cudaMemcpy(s->st.loc, img.data(), span, cudaMemcpyHostToDevice);
+    if (ce != cudaSuccess) return fail(RTU_E_CUDA, std::string("rtu_elbo_init: ") + cudaGetErrorString(ce));
     s->st.tag = tag;
     s->elbo_ready = true;
     return RTU_OK;

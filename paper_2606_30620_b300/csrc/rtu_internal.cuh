@@ -485,6 +485,33 @@ __device__ __forceinline__ int staged_ray_id(int n_img, int s2, int u, int local
     return pixel * s2 + q;
 }
 
+// Sub-ray positions in the kernel's type (Sec. 2.3): the offset from the image
+// centre in pixel units, (i - (n-1)/2) + ((a + 1/2)/s - 1/2), is exact in float
+// (a multiple of 1/(2s) for s a power of two), and it is scaled by the pixel size
+// held as a (hi, lo) pair, so the position is rounded once instead of suffering a
+// rounded image-centre offset shared by every ray.
+template <typename T>
+struct PixGeom {
+    T hi, lo, ci;
+    T offp[8];
+};
+
+template <typename T>
+__device__ __forceinline__ void pixgeom_setup(PixGeom<T>& g, double pix, int n_img, int s) {
+    if (threadIdx.x == 0) {
+        g.hi = (T)pix;
+        g.lo = (T)(pix - (double)g.hi);
+        g.ci = (T)(0.5 * (n_img - 1));
+    }
+    if ((int)threadIdx.x < s) g.offp[threadIdx.x] = (T)((threadIdx.x + 0.5) / s - 0.5);
+}
+
+template <typename T>
+__device__ __forceinline__ T ray_coord(const PixGeom<T>& g, int i, int a) {
+    const T e = (T(i) - g.ci) + g.offp[a];
+    return fma(e, g.hi, e * g.lo);
+}
+
 // pixel centre and sub-ray positions (Sec. 2.3) in double
 __device__ __forceinline__ void ray_pos(int n_img, double pix, int s, int pixel, int sub,
                                         double& x, double& y) {
