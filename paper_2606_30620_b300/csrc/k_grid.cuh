@@ -25,16 +25,31 @@ __global__ void __launch_bounds__(CTA_C) k_trace_centres(const __grid_constant__
     const EvalArgs& E = B.e[ev];
     const int tile = blockIdx.x - B.tile0[ev];
     __shared__ LensK<double> L;
+    __shared__ LensK<DF> Ldf;
     __shared__ double red[6][CTA_C / 32];
     load_lensk(L, E.lensk);
     __syncthreads();
+    // the float path traces its centre rays in double-float (about 48 bits) unless
+    // subhaloes are present; the double path in double
+    const bool use_df = !E.f64 && L.nsub == 0;
+    if (use_df) {
+        lensk_to_df(L, Ldf);
+        __syncthreads();
+    }
     const int k = tile * CTA_C + threadIdx.x;
     double bx = 0.0, by = 0.0;
     double v[6];
     if (k < E.n_mask) {
         double x, y;
         ray_pos(E.n_img, E.pix, 1, E.centre_idx[k], 0, x, y);
-        lens_beta(L, x, y, bx, by);
+        if (use_df) {
+            DF bxf, byf;
+            lens_beta_smooth<DF>(Ldf, DF(x), DF(y), bxf, byf);
+            bx = bxf.to_double();
+            by = byf.to_double();
+        } else {
+            lens_beta(L, x, y, bx, by);
+        }
         E.beta[k] = bx;
         E.beta[E.n_mask + k] = by;
         v[0] = bx; v[1] = by; v[2] = bx; v[3] = bx; v[4] = by; v[5] = by;

@@ -200,6 +200,15 @@ __device__ __forceinline__ int cell_of(T yx, T yy, int n, T& fx, T& fy, int& i0,
     return j0 * (n - 1) + i0;
 }
 
+// double-precision RTU coordinates of a source-plane position
+__device__ __forceinline__ void rtu_coords_from_beta(const double* trd, const double* U, int K, double bx,
+                                                     double by, double& yx, double& yy) {
+    const double* X = trd + TR_HDR;
+    const double zx = (bx - trd[0]) / trd[2], zy = (by - trd[1]) / trd[2];
+    yx = cdf_value<double>(X, U, X + 2 * K, K, cdf_interval<double>(X, K, zx), zx);
+    yy = cdf_value<double>(X + K, U, X + 3 * K, K, cdf_interval<double>(X + K, K, zy), zy);
+}
+
 // double-precision RTU coordinates of a ray from the double lens block
 __device__ __forceinline__ void rtu_coords_d(const LensK<double>& Kd, const double* trd, const double* U, int K,
                                              double x, double y, double& yx, double& yy) {
@@ -518,11 +527,19 @@ __global__ void __launch_bounds__(EDGE_NT) k_render_edge(const __grid_constant__
     const EvalArgs& E = B.e[ev];
     const int tile = blockIdx.x - B.tile0[ev];
     __shared__ LensK<double> Kd;
+    __shared__ LensK<DF> Kdf;
     __shared__ double trd[TR_HDR + 4 * (MAXM + 2)];
     __shared__ double Ud[MAXM + 2];
     load_lensk(Kd, E.lensk);
     load_transform<double>(E, trd, Ud);
     __syncthreads();
+    // the lens in double-float (about 48 bits) unless subhaloes are present; the
+    // CDF map and the cell decision in double
+    const bool use_df = Kd.nsub == 0;
+    if (use_df) {
+        lensk_to_df(Kd, Kdf);
+        __syncthreads();
+    }
     const int n = E.n_src, K = E.n_nodes + 2, s2 = E.s * E.s;
     const int cnt = min(*E.ecount, E.n_img * E.n_img * s2);
     const float* grid = reinterpret_cast<const float*>(E.src);
@@ -535,7 +552,13 @@ __global__ void __launch_bounds__(EDGE_NT) k_render_edge(const __grid_constant__
         const int pixel = ray / s2, q = ray - pixel * s2;
         double xd, yd, yx, yy;
         ray_pos(E.n_img, E.pix, E.s, pixel, q, xd, yd);
-        rtu_coords_d(Kd, trd, Ud, K, xd, yd, yx, yy);
+        if (use_df) {
+            DF bxf, byf;
+            lens_beta_smooth<DF>(Kdf, DF(xd), DF(yd), bxf, byf);
+            rtu_coords_from_beta(trd, Ud, K, bxf.to_double(), byf.to_double(), yx, yy);
+        } else {
+            rtu_coords_d(Kd, trd, Ud, K, xd, yd, yx, yy);
+        }
         double fx, fy;
         int i0, j0;
         const int cell = cell_of<double>(yx, yy, n, fx, fy, i0, j0);

@@ -388,11 +388,11 @@ rtu_status rtu_system_create(const rtu_system_desc* d, void* ws, size_t ws_bytes
         memcpy(htw, tw.data(), tw.size() * 8);
         memcpy(hrev, rev.data(), rev.size() * 4);
         memcpy(hcheb, cheb.data(), cheb.size() * 8);
-        const size_t cw_off = (size_t)(reinterpret_cast<char*>(hcwt) - img.data());
-        const size_t cw_end = (size_t)(reinterpret_cast<char*>(htw) - img.data());
-        // upload around the weights region so a weighted system keeps its weights
-        if ((ce = cudaMemcpy(base, img.data(), cw_off, cudaMemcpyHostToDevice)) != cudaSuccess ||
-            (ce = cudaMemcpy(base + cw_end, img.data() + cw_end, st - cw_end, cudaMemcpyHostToDevice)) != cudaSuccess) {
+        const size_t tw_off = (size_t)(reinterpret_cast<char*>(htw) - img.data());
+        // the arc-mask pixel list (n_mask entries) and the FFT / Chebyshev tables; the
+        // weights region in between is written above (weighted grid) or unused
+        if ((ce = cudaMemcpy(base, img.data(), idx.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
+            (ce = cudaMemcpy(base + tw_off, img.data() + tw_off, st - tw_off, cudaMemcpyHostToDevice)) != cudaSuccess) {
             delete s;
             return fail(RTU_E_CUDA, std::string("table upload: ") + cudaGetErrorString(ce));
         }

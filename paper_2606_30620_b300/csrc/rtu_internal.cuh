@@ -10,6 +10,7 @@
 
 #include "rtu.h"
 #include "rtu_math.cuh"
+#include "rtu_df.cuh"
 
 namespace rtu {
 
@@ -363,6 +364,18 @@ __device__ __forceinline__ void lens_beta(const LensK<T>& K, T x, T y, T& bx, T&
     by = y - ay;
 }
 
+// the lens equation without subhaloes (EPL + shear), for scalar types without
+// the subhalo profiles' special functions
+template <typename T>
+__device__ __forceinline__ void lens_beta_smooth(const LensK<T>& K, T x, T y, T& bx, T& by) {
+    T ax, ay;
+    epl_alpha(K.C, x, y, ax, ay);
+    ax += K.g1 * x + K.g2 * y;
+    ay += K.g2 * x - K.g1 * y;
+    bx = x - ax;
+    by = y - ay;
+}
+
 // the same, keeping the EPL intermediates for a later vector-Jacobian product
 template <typename T>
 __device__ __forceinline__ void lens_beta_eval(const LensK<T>& K, T x, T y, EplJ<T>& J, T& bx, T& by) {
@@ -399,6 +412,30 @@ __device__ __forceinline__ void sub_vjp(const LensK<T>& K, int h, T x, T y, T gb
     nfw_deflect<D>(D(x), D(y), ks, rs, tau, xs, ys, K.kind, ax, ay);
 #pragma unroll
     for (int c = 0; c < 5; ++c) out[c] -= gbx * ax.d[c] + gby * ay.d[c];
+}
+
+// The double-float lens block of a LensK<double> (no subhaloes: the double-float
+// path serves only lenses without them), converted by the CTA's threads.
+__device__ inline void lensk_to_df(const LensK<double>& a, LensK<DF>& b) {
+    const int nt = a.C.nterm;
+    for (int i = threadIdx.x; i < nt; i += blockDim.x) {
+        b.C.term[i].c = DF(a.C.term[i].c);
+        b.C.term[i].ng = DF(a.C.term[i].ng);
+        b.C.term[i].D = DF(a.C.term[i].D);
+        b.C.term[i].pad_ = DF(0.0f);
+    }
+    if (threadIdx.x == 0) {
+        const EplC<double>& c = a.C;
+        EplC<DF>& d = b.C;
+        d.x0 = DF(c.x0); d.y0 = DF(c.y0); d.cp = DF(c.cp); d.sp = DF(c.sp); d.q = DF(c.q); d.cc = DF(c.cc);
+        d.e1 = DF(c.e1); d.e2 = DF(c.e2); d.thE = DF(c.thE); d.sq = DF(c.sq); d.b = DF(c.b); d.t = DF(c.t);
+        d.pref0 = DF(c.pref0); d.lnb = DF(c.lnb); d.opq = DF(c.opq);
+        d.f_q = DF(c.f_q); d.tb_bq = DF(c.tb_bq); d.tb_sq = DF(c.tb_sq); d.iopq = DF(c.iopq);
+        d.qe1 = DF(c.qe1); d.qe2 = DF(c.qe2); d.pe1 = DF(c.pe1); d.pe2 = DF(c.pe2); d.ftail = DF(c.ftail);
+        d.nterm = nt;
+        b.g1 = DF(a.g1); b.g2 = DF(a.g2); b.rc2 = DF(a.rc2);
+        b.nsub = 0; b.kind = a.kind; b.epl = a.epl;
+    }
 }
 
 // the evaluation's lens blocks: LensK<double> first, then LensK<float>

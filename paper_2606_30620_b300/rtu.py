@@ -138,9 +138,17 @@ class System:
                  weights=None):
         self.dtype = torch.float64 if precision == RTU_F64 else torch.float32
         self.device = torch.device(device)
-        self.data = torch.as_tensor(data, dtype=self.dtype, device=self.device).contiguous()
+        if isinstance(data, np.ndarray) and isinstance(psf, np.ndarray):
+            # host arrays: the image and the PSF travel in one copy
+            npdt = np.float64 if precision == RTU_F64 else np.float32
+            both = np.concatenate([np.asarray(data, npdt).ravel(), np.asarray(psf, npdt).ravel()])
+            dev = torch.from_numpy(both).to(self.device)
+            self.data = dev[:data.size].view(data.shape)
+            self.psf = dev[data.size:].view(psf.shape)
+        else:
+            self.data = torch.as_tensor(data, dtype=self.dtype, device=self.device).contiguous()
+            self.psf = torch.as_tensor(psf, dtype=self.dtype, device=self.device).contiguous()
         self.mask = torch.as_tensor(mask, dtype=torch.uint8, device=self.device).contiguous()
-        self.psf = torch.as_tensor(psf, dtype=self.dtype, device=self.device).contiguous()
         # weighted RTU grid: integer ray weights per pixel (read once at create)
         self.weights = None if weights is None else torch.as_tensor(
             weights.astype("int32") if hasattr(weights, "astype") else weights,
@@ -194,7 +202,10 @@ class System:
         ns = self.n_sites
         if len(priors) != ns:
             raise ValueError(f"{ns} priors expected")
-        arr = (Prior * ns)(*[Prior(int(p[0]), int(p[1]), *[float(x) for x in p[2:6]]) for p in priors])
+        arr = (Prior * ns)()
+        for i, p in enumerate(priors):
+            arr[i].kind, arr[i].space = int(p[0]), int(p[1])
+            arr[i].a, arr[i].b, arr[i].c, arr[i].d = float(p[2]), float(p[3]), float(p[4]), float(p[5])
         fixed = np.ascontiguousarray(fixed, dtype=np.float64)
         loc = np.ascontiguousarray(loc, dtype=np.float64)
         rho = np.ascontiguousarray(rho, dtype=np.float64)
