@@ -26,6 +26,7 @@ Passages followed (paper sections / equations):
   * weighted eCDFs (weighted RTU grid) ...... Sec. 5 (extension)
   * Chebyshev-node polynomial fit of the QF . App. C step iii (order 21)
   * cubic Hermite spline inverse (the CDF) .. App. C step iv
+  * unsmoothed linear-interpolated eCDF ..... App. C (first paragraph)
   * copula map y = g(x) (Eq. 5) ............. Sec. 2.2
   * GP source f = F^-1(sqrt(P) xi) (Eq. 1) .. Sec. 2.1; Matern P(k) (Eq. 4)
   * softplus positivity (Eq. 2-3) ........... Sec. 2.1
@@ -67,6 +68,7 @@ N_SUB_PARAMS = 5    # kappa_s, r_s, tau, x_s, y_s
 FLAG_NONMONOTONE = 1
 TRANSFORM_RTU = 0       # the ray-guided transformed uniform grid (Sec. 2.2)
 TRANSFORM_UNIFORM = 1   # the uniform grid over the masked rays' square box (Sec. 2.1)
+TRANSFORM_LINEAR = 2    # the unsmoothed eCDF, linearly interpolated (App. C, first paragraph)
 
 
 # ---------------------------------------------------------------------------
@@ -406,12 +408,54 @@ def uniform_box(bx, by):
     return BoxTransform(lo=centre - 0.5 * side, side=side)
 
 
+@dataclass
+class LinearTransform:
+    """The first-order transform of App. C: the marginal eCDFs of the standardised
+    centre rays, linearly interpolated between the observations."""
+    mu: torch.Tensor        # [2] standardisation (App. C step i)
+    sigma: torch.Tensor
+    knots: torch.Tensor     # [2, n] sorted standardised centre positions per axis
+    flags: int = 0
+
+
+def linear_ecdf_transform(bx, by):
+    """App. C step i (standardise) and step ii (sort each marginal: the eCDF's
+    observations).  No fit: the map interpolates the eCDF directly."""
+    mu, sigma = standardise(bx, by)
+    knots = [torch.sort((b - mu[a]) / sigma).values for a, b in enumerate((bx, by))]
+    return LinearTransform(mu=mu, sigma=sigma, knots=torch.stack(knots))
+
+
+def linear_ecdf(z, X):
+    """The eCDF of the sorted observations X (n >= 2) interpolated linearly: the
+    k-th observation (0-based) maps to k/(n-1) -- the inverse of the type-7 quantile
+    function -- and between observations the map is linear.
+
+    Readings (the paper gives the interpolation only): beyond the end observations
+    the map continues with the slope of the end segment, as the smoothed CDF
+    continues linearly beyond its end knots, so rays there leave [0, 1] and see a
+    zero source; with k the last observation <= z (clamped to [0, n-2]) a segment of
+    zero width (tied observations at an end) contributes a constant k/(n-1)."""
+    n = X.shape[0]
+    k = (torch.searchsorted(X.detach(), z.detach(), right=True) - 1).clamp(0, n - 2)
+    x0, x1 = X[k], X[k + 1]
+    h = x1 - x0
+    ok = h.detach() > 0
+    t = torch.where(ok, (z - x0) / torch.where(ok, h, torch.ones_like(h)), torch.zeros_like(z))
+    return (k.to(DT) + t) / (n - 1)
+
+
 def rtu_map(bx, by, T):
     """Source-grid coordinates of source-plane positions: for the RTU grid Eq. 5,
     y = g(x) = (C_1(z_1), C_2(z_2)) with z = (beta - mu)/sigma_min; for the uniform
-    grid the affine box map y = (beta - lo)/side."""
+    grid the affine box map y = (beta - lo)/side; for the unsmoothed transform the
+    interpolated eCDFs of z."""
     if isinstance(T, BoxTransform):
         return (bx - T.lo[0]) / T.side, (by - T.lo[1]) / T.side
+    if isinstance(T, LinearTransform):
+        zx = (bx - T.mu[0]) / T.sigma
+        zy = (by - T.mu[1]) / T.sigma
+        return linear_ecdf(zx, T.knots[0]), linear_ecdf(zy, T.knots[1])
     zx = (bx - T.mu[0]) / T.sigma
     zy = (by - T.mu[1]) / T.sigma
     return (hermite_cdf(zx, T.knots[0], T.values, T.slopes[0]),
@@ -537,6 +581,12 @@ def build_grid(sys: System, lens, subs=None):
     bx, by = trace(xc[sel], yc[sel], lens, sys.profile, subs, sys.sub_kind)
     if sys.transform == TRANSFORM_UNIFORM:
         return uniform_box(bx, by)
+    if sys.transform == TRANSFORM_LINEAR:
+        if sys.weights is not None:
+            raise ValueError("the unsmoothed eCDF transform takes unweighted rays")
+        if bx.shape[0] < 2:
+            raise ValueError("the unsmoothed eCDF transform needs at least two masked pixels")
+        return linear_ecdf_transform(bx, by)
     w = None if sys.weights is None else sys.weights.reshape(-1)[sel]
     return fit_transform(bx, by, sys.n_nodes, sys.degree, weights=w)
 

@@ -560,3 +560,101 @@ def test_weighted_grid_gradient_matches_central_differences():
           - float(O.forward(s, lens - h * v, lat, ps)["logL"])) / (2 * h)
     an = float((g["g_lens"] * v).sum())
     assert abs(fd - an) < 1e-5 * max(1.0, abs(an))
+
+
+# ------------------------------------------- unsmoothed linear eCDF (App. C, first paragraph)
+def test_linear_ecdf_is_numpy_interp_inside_and_maps_observations_to_ranks():
+    rng = np.random.default_rng(31)
+    for n in (2, 3, 17, 400):
+        X = np.sort(rng.standard_normal(n))
+        z = rng.uniform(X[0], X[-1], 200)
+        ref = np.interp(z, X, np.linspace(0.0, 1.0, n))
+        got = O.linear_ecdf(t(z), t(X)).numpy()
+        assert np.abs(got - ref).max() < 1e-14, n
+        # the k-th observation sits at the k-th rank, k/(n-1)
+        at = O.linear_ecdf(t(X), t(X)).numpy()
+        assert np.abs(at - np.arange(n) / (n - 1)).max() < 1e-15, n
+
+
+def test_linear_ecdf_inverts_the_type7_quantile_function():
+    rng = np.random.default_rng(32)
+    X = np.sort(rng.standard_normal(250))
+    u = np.concatenate([[0.0, 1.0], rng.uniform(0.0, 1.0, 300)])
+    q = np.quantile(X, u, method="linear")
+    back = O.linear_ecdf(t(q), t(X)).numpy()
+    assert np.abs(back - u).max() < 1e-12
+
+
+def test_linear_ecdf_extrapolates_with_the_end_segment_slopes():
+    X = t([-1.0, -0.5, 0.25, 2.0])
+    n = 4
+    d = t([0.3, 1.7])
+    left = O.linear_ecdf(X[0] - d, X)
+    right = O.linear_ecdf(X[-1] + d, X)
+    assert float((left - (-d / ((n - 1) * 0.5))).abs().max()) < 1e-15
+    assert float((right - (1.0 + d / ((n - 1) * 1.75))).abs().max()) < 1e-15
+    # tied end observations: a zero-width end segment gives a constant
+    Xt = t([0.0, 0.0, 1.0, 2.0])
+    v = O.linear_ecdf(t([-0.5, -3.0]), Xt)
+    assert float(v.abs().max()) == 0.0
+
+
+def _linear_mock_rays(seed):
+    m = I.config_c2(seed, n_img=48, s=2, n_src=16)
+    s = oracle_io.system(m)
+    s.transform = O.TRANSFORM_LINEAR
+    lens, _, _, _ = oracle_io.params(m)
+    xc, yc = O.pixel_centres(s.n_img, s.pix)
+    sel = s.mask.reshape(-1)
+    bx, by = O.trace(xc[sel], yc[sel], lens, s.profile)
+    return s, lens, bx, by
+
+
+def test_linear_transform_gives_exactly_uniform_marginals_of_the_centre_rays():
+    # App. C: the interpolated eCDF makes the marginals of the observations uniform
+    # by construction: the centre rays land on the ranks k/(n-1)
+    s, lens, bx, by = _linear_mock_rays(1060)
+    T = O.build_grid(s, lens)
+    yx, yy = O.rtu_map(bx, by, T)
+    n = bx.shape[0]
+    ranks = np.arange(n) / (n - 1)
+    assert np.abs(np.sort(yx.numpy()) - ranks).max() < 1e-12
+    assert np.abs(np.sort(yy.numpy()) - ranks).max() < 1e-12
+
+
+def test_linear_transform_does_not_depend_on_the_standardisation():
+    # the interpolated eCDF commutes with any increasing affine map applied to the
+    # observations and the query alike, so step i drops out: it equals numpy's
+    # interpolation of the raw source-plane positions
+    s, lens, bx, by = _linear_mock_rays(1061)
+    T = O.build_grid(s, lens)
+    x, y = O.subray_positions(s.n_img, s.pix, s.s_super)
+    rx, ry = O.trace(x.reshape(-1), y.reshape(-1), lens, s.profile)
+    yx, yy = O.rtu_map(rx, ry, T)
+    for got, b, r in ((yx, bx, rx), (yy, by, ry)):
+        X = np.sort(b.numpy())
+        inside = (r.numpy() >= X[0]) & (r.numpy() <= X[-1])
+        ref = np.interp(r.numpy()[inside], X, np.linspace(0.0, 1.0, X.size))
+        assert inside.sum() > 100
+        assert np.abs(got.numpy()[inside] - ref).max() < 1e-12
+
+
+def test_linear_grid_gradient_matches_central_differences():
+    m = I.config_tiny(seed=23)
+    s = oracle_io.system(m)
+    s.transform = O.TRANSFORM_LINEAR
+    lens, lat, ps, _ = oracle_io.params(m)
+    g = O.forward_adjoint(s, lens, lat, ps)
+    rng = np.random.default_rng(23)
+    for which, key in ((0, "g_lens"), (1, "g_latents"), (2, "g_ps")):
+        base = [lens, lat, ps]
+        v = t(rng.standard_normal(base[which].shape))
+        # the map has a kink at every observation: a small step keeps them outside +-h
+        h = 1e-8
+        p = [b.clone() for b in base]
+        q = [b.clone() for b in base]
+        p[which] = p[which] + h * v
+        q[which] = q[which] - h * v
+        fd = (float(O.forward(s, *p)["logL"]) - float(O.forward(s, *q)["logL"])) / (2 * h)
+        an = float((g[key] * v).sum())
+        assert abs(fd - an) < 1e-5 * max(1.0, abs(an)), (key, fd, an)
