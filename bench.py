@@ -52,12 +52,12 @@ FLOPS_ADJ_RAY = 2.5 * FLOPS_FWD_RAY
 # them in the grid), valid for the kernel sources with digest TRAFFIC_SRC_DIGEST.
 ROOF = {
     "k_render": {"flops_per_unit": FLOPS_FWD_RAY, "units": "supersampled rays",
-                 "traffic_per_unit": (0.436736e6 + 8704) / 5120000},
+                 "traffic_per_unit": (0.439296e6 + 9216) / 5120000},
     "k_render_adj": {"flops_per_unit": FLOPS_ADJ_RAY, "units": "in-grid rays",
-                     "traffic_per_unit": (6.820352e6 + 30976) / 743894},
+                     "traffic_per_unit": (6.822400e6 + 33792) / 743894},
 }
-TRAFFIC_SRC_DIGEST = "2eea777a922a6a3a"
-KERNEL_SOURCES = ("k_render.cuh", "rtu_internal.cuh", "rtu_math.cuh")
+TRAFFIC_SRC_DIGEST = "c4180bc12c40ef59"
+KERNEL_SOURCES = ("k_render.cuh", "rtu_internal.cuh", "rtu_math.cuh", "rtu_df.cuh")
 
 
 def kernel_digest():

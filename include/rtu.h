@@ -74,9 +74,14 @@ enum { RTU_SIE = 0, RTU_EPL = 1 };
 enum { RTU_SUB_NONE = 0, RTU_SUB_NFW = 1, RTU_SUB_TNFW = 2 };
 enum { RTU_PS_POWER_LAW = 0, RTU_PS_MATERN_LIKE = 1, RTU_PS_MATERN = 2 };
 /* Source-grid coordinates: the ray-guided transformed uniform grid (smoothed
- * marginal CDFs, Sec. 2.2, App. C) or the uniform grid over the smallest square
- * box containing the masked rays (Sec. 2.1), mapped affinely onto [0, 1]^2. */
-enum { RTU_TRANSFORM_RTU = 0, RTU_TRANSFORM_UNIFORM = 1 };
+ * marginal CDFs, Sec. 2.2, App. C), the uniform grid over the smallest square
+ * box containing the masked rays (Sec. 2.1), mapped affinely onto [0, 1]^2, or
+ * the unsmoothed transform of App. C (first paragraph): per axis the k-th smallest
+ * traced arc-mask centre (of n) maps to k/(n-1), linearly in between, and beyond
+ * the smallest and largest with the slope of the end segment (a zero-width end
+ * segment gives a constant); rays mapped outside [0, 1]^2 see a zero source.  The
+ * unsmoothed transform takes no ray weights. */
+enum { RTU_TRANSFORM_RTU = 0, RTU_TRANSFORM_UNIFORM = 1, RTU_TRANSFORM_LINEAR = 2 };
 
 /* stats[] written by rtu_forward (double[RTU_N_STATS]); N_IN_GRID = supersampled
  * rays that land inside the RTU grid (the rays the adjoint differentiates) */
@@ -104,7 +109,8 @@ typedef struct {
     int32_t n_nodes;     /* Chebyshev nodes M (App. C iii); must equal degree+1 */
     int32_t degree;      /* polynomial degree D of the quantile fit (21 in the paper) */
     int32_t n_slots;     /* concurrent evaluations of this system (e.g. ELBO samples) */
-    int32_t transform;   /* RTU_TRANSFORM_RTU (Sec. 2.2) | RTU_TRANSFORM_UNIFORM (Sec. 2.1 box) */
+    int32_t transform;   /* RTU_TRANSFORM_RTU (Sec. 2.2) | RTU_TRANSFORM_UNIFORM (Sec. 2.1 box)
+                            | RTU_TRANSFORM_LINEAR (App. C, unsmoothed eCDF) */
     int32_t n_light;     /* MGE lens-light components 0..RTU_MAX_LIGHT (App. A.3); 0 = none */
     double pix;          /* arcsec per pixel */
     double src_pitch;    /* source-grid pitch entering k (arcsec) */
@@ -135,7 +141,8 @@ typedef struct {
     void* source;              /* forward out: real [n_src^2] source brightness s* (nullable) */
     double* cdf;               /* build out: [3 + 4 (M+2)] mu_x, mu_y, sigma_min,
                                   knots_x[M+2], knots_y[M+2], slopes_x[M+2], slopes_y[M+2]
-                                  (nullable) */
+                                  (nullable); RTU_TRANSFORM_LINEAR writes mu_x, mu_y,
+                                  sigma_min and zeros */
     int32_t* ray_hist;         /* forward out: [(n_src-1)^2] supersampled rays per RTU cell
                                   (nullable) */
     void* g_latents;           /* adjoint out: real [n_src^2] */

@@ -1,7 +1,8 @@
 // k_adj.cuh -- S9, transform part: back through the Hermite knots and slopes,
 // the monotonicity guard, the Chebyshev fit and the type-7 order statistics to
 // the selected centre rays, the mean and sigma_min (App. C i-iv), then through
-// the centre-ray trace to the lens; final fixed-order lens-gradient sums.
+// the centre-ray trace to the lens; for the unsmoothed eCDF, from the sorted
+// positions' gradients to every centre ray; final fixed-order lens-gradient sums.
 #pragma once
 #include "rtu_internal.cuh"
 #include "k_grid.cuh"
@@ -37,7 +38,7 @@ __global__ void __launch_bounds__(CDF_NT) k_cdf_adj(const __grid_constant__ Batc
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const double* tr = E.trd;
     const double sigma = tr[2], isig = 1.0 / sigma;
-    if (E.transform) {
+    if (E.transform == RTU_TRANSFORM_UNIFORM) {
         if (ax != 0) return;
         for (int col = wid; col < NACC_FIX + 4 * K; col += CDF_NT / 32) {
             const double v = apart_col(E, nacc, col);
@@ -161,7 +162,7 @@ __global__ void __launch_bounds__(CTA_C) k_centre_adj(const __grid_constant__ Ba
     const int ev = find_eval(B, blockIdx.x);
     const EvalArgs& E = B.e[ev];
     const int tile = blockIdx.x - B.tile0[ev];
-    const int M = E.n_nodes, N = E.n_mask;
+    const int N = E.n_mask;
     const int nsub = E.sub_kind ? E.n_sub : 0;
     const int nl = 8 + 5 * nsub;
     __shared__ LensK<T> L;
@@ -244,7 +245,8 @@ __global__ void __launch_bounds__(CTA_C) k_centre_adj(const __grid_constant__ Ba
 // thread per (axis, target); the row after the centre CTAs' rows in cadj.
 constexpr int SEL_ADJ_NT = 4 * MAXM;
 __global__ void __launch_bounds__(SEL_ADJ_NT) k_sel_adj(const __grid_constant__ Batch B) {
-    const EvalArgs& E = B.e[blockIdx.x];
+    // systems of the unsmoothed transform launch no CTA here: map through the prefix
+    const EvalArgs& E = B.e[find_eval(B, blockIdx.x)];
     const int M = E.n_nodes;
     const int nsub = E.sub_kind ? E.n_sub : 0;
     const int nl = 8 + 5 * nsub;
@@ -296,6 +298,69 @@ __global__ void __launch_bounds__(SEL_ADJ_NT) k_sel_adj(const __grid_constant__ 
             out[8 + 5 * h + threadIdx.x] = r;
         }
     }
+}
+
+// The unsmoothed eCDF (App. C, first paragraph): centre ray i holds rank r_a(i) on
+// axis a, so d logL / d beta_i = (gk_x[r_x(i)], gk_y[r_y(i)]); then the lens (and
+// subhaloes), in double: every centre ray carries terms of the size of the image
+// terms they cancel.  One thread per centre ray, rows 0..n_cta_c-1 of cadj; the
+// CTA of tile 0 also clears row n_cta_c (the selected-rank row of the smoothed grid).
+__global__ void __launch_bounds__(CTA_C) k_lin_centre_adj(const __grid_constant__ Batch B) {
+    const int ev = find_eval(B, blockIdx.x);
+    const EvalArgs& E = B.e[ev];
+    const int tile = blockIdx.x - B.tile0[ev];
+    const int N = E.n_mask;
+    const int nsub = E.sub_kind ? E.n_sub : 0;
+    const int nl = 8 + 5 * nsub;
+    __shared__ LensK<double> Ld;
+    __shared__ double red[CTA_C / 32][8];
+    load_lensk(Ld, E.lensk);
+    __syncthreads();
+    const int k = tile * CTA_C + threadIdx.x;
+    double o8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    double xd = 0.0, yd = 0.0, gx = 0.0, gy = 0.0;
+    if (k < N) {
+        gx = E.gk[E.lrank[k]];
+        gy = E.gk[N + E.lrank[N + k]];
+        const int pix = E.centre_idx[k];
+        const int pj = pix / E.n_img, pi = pix - pj * E.n_img;
+        const double c = 0.5 * (E.n_img - 1);
+        xd = (pi - c) * E.pix;
+        yd = (pj - c) * E.pix;
+        EplJ<double> J;
+        double bx, by;
+        lens_beta_eval(Ld, xd, yd, J, bx, by);
+        lens_beta_vjp(Ld, J, xd, yd, gx, gy, o8);
+    }
+    double* out = E.cadj + (size_t)tile * nl;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int p = 0; p < 8; ++p) {
+        const double v = warp_sum(o8[p]);
+        if (lane == 0) red[wid][p] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 8) {
+        double r = 0.0;
+        for (int w = 0; w < CTA_C / 32; ++w) r += red[w][threadIdx.x];
+        out[threadIdx.x] = r;
+    }
+    for (int h = 0; h < nsub; ++h) {
+        __syncthreads();
+        double a5[5] = {0, 0, 0, 0, 0};
+        if (k < N) sub_vjp<double>(Ld, h, xd, yd, gx, gy, a5);
+        for (int c = 0; c < 5; ++c) {
+            const double v = warp_sum(a5[c]);
+            if (lane == 0) red[wid][c] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x < 5) {
+            double r = 0.0;
+            for (int w = 0; w < CTA_C / 32; ++w) r += red[w][threadIdx.x];
+            out[8 + 5 * h + threadIdx.x] = r;
+        }
+    }
+    if (tile == 0)
+        for (int p = threadIdx.x; p < nl; p += CTA_C) E.cadj[(size_t)E.n_cta_c * nl + p] = 0.0;
 }
 
 // g_lens = (render-adjoint lens sums) + (centre-adjoint lens sums), fixed order

@@ -8,6 +8,8 @@
 //                   order statistics at the Chebyshev-node ranks, the Chebyshev
 //                   fit of the quantile function (discrete cosine sums, exact
 //                   interpolation for M = D+1), Hermite knots/slopes, guard.
+//  k_lin_sort       the unsmoothed transform (App. C, first paragraph): every
+//                   order statistic, by a counting sort on the level-1 histogram
 #pragma once
 #include "rtu_internal.cuh"
 
@@ -235,10 +237,10 @@ __global__ void __launch_bounds__(SEL_NT) k_select_fit(const __grid_constant__ B
     }
     // target ranks: node j -> floor(u_j (N-1)) and the next one (RTU grid); the
     // smallest and largest ray (uniform grid: the square box, Sec. 2.1)
-    const int nt = E.transform ? 2 : 2 * M;
+    const int nt = E.transform == RTU_TRANSFORM_UNIFORM ? 2 : 2 * M;
     for (int t = tid; t < nt; t += SEL_NT) {
         int k;
-        if (E.transform) {
+        if (E.transform == RTU_TRANSFORM_UNIFORM) {
             k = t == 0 ? 0 : W - 1;
         } else {
             double h = E.cheb[cheb_u(M, D) + t / 2] * (W - 1);
@@ -346,7 +348,7 @@ __global__ void __launch_bounds__(SEL_NT) k_select_fit(const __grid_constant__ B
     }
     __syncthreads();
 
-    if (E.transform) {
+    if (E.transform == RTU_TRANSFORM_UNIFORM) {
         // uniform grid: the smallest square box around the masked rays, centred on
         // each axis's range, mapped affinely onto [0, 1]^2 -- written as Hermite
         // knots X_j = (lo + U_j L - mu)/sigma with equal slopes sigma/L (linear).
@@ -451,6 +453,142 @@ __global__ void __launch_bounds__(SEL_NT) k_select_fit(const __grid_constant__ B
         }
     }
     if (tid == 0 && flag_sh) atomicOr(E.flags, flag_sh);
+}
+
+// ------------------------------------------------ the unsmoothed eCDF transform
+// App. C (first paragraph): the k-th smallest centre ray of an axis maps to
+// k/(n-1), linearly in between and with the end segments' slopes beyond.  The map
+// commutes with the standardisation of step i, so the observations are kept as raw
+// source-plane positions (mu = 0, sigma = 1 in the transform header).
+//
+// One CTA per (evaluation, axis): the level-1 histogram (every ray once, bins over
+// [min, max]) becomes a counting sort -- exclusive scan in place, scatter through
+// the bin cursors (afterwards hist[b] is the end of bin b), then each bin's few
+// rays sorted by (position, ray index), a total order, so the result does not
+// depend on the scatter's arrival order.  Writes the sorted positions (double and
+// float hi + lo), the ray at each rank, the rank of each ray, and a transform
+// header the render kernels read like the Hermite one: end knots X_0 = first and
+// X_{K-1} = last observation with the end-segment slopes (the reach of the grid),
+// plus the bin origin and scale of the histogram for the renderers' bin lookup.
+constexpr int LIN_NT = 1024;
+__global__ void __launch_bounds__(LIN_NT) k_lin_sort(const __grid_constant__ Batch B) {
+    const int ev = find_eval(B, blockIdx.x);
+    const EvalArgs& E = B.e[ev];
+    const int a = blockIdx.x - B.tile0[ev];
+    const int N = E.n_mask, K = E.n_nodes + 2, tid = threadIdx.x;
+    __shared__ double mom[6];
+    __shared__ double sig[2];
+    __shared__ int wtot[LIN_NT / 32];
+    if (tid < 32) {
+        centre_moments(E, mom);
+        const int lane = tid;
+        double v0 = 0.0, v1 = 0.0;
+        for (int t = lane; t < E.n_cta_c; t += 32) { v0 += E.cpart2[2 * t]; v1 += E.cpart2[2 * t + 1]; }
+        for (int o = 16; o > 0; o >>= 1) {
+            v0 += __shfl_down_sync(0xffffffffu, v0, o);
+            v1 += __shfl_down_sync(0xffffffffu, v1, o);
+        }
+        if (lane == 0) {
+            const double sx = sqrt(v0 / N), sy = sqrt(v1 / N);
+            sig[0] = sx <= sy ? sx : sy;            // sigma_min, tie -> x (App. C i)
+            sig[1] = sx <= sy ? 0.0 : 1.0;
+        }
+    }
+    __syncthreads();
+    int* h = E.hist + a * HB;
+    // exclusive scan of the HB bin counts, in place (each thread a contiguous run)
+    {
+        constexpr int PER = HB / LIN_NT;
+        int own = 0;
+        for (int i = 0; i < PER; ++i) own += h[tid * PER + i];
+        int incl = own;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if ((tid & 31) >= o) incl += y;
+        }
+        if ((tid & 31) == 31) wtot[tid >> 5] = incl;
+        __syncthreads();
+        if (tid == 0) {
+            int acc = 0;
+            for (int w = 0; w < LIN_NT / 32; ++w) { const int t = wtot[w]; wtot[w] = acc; acc += t; }
+        }
+        __syncthreads();
+        int base = wtot[tid >> 5] + incl - own;
+        for (int i = 0; i < PER; ++i) {
+            const int v = h[tid * PER + i];
+            h[tid * PER + i] = base;
+            base += v;
+        }
+    }
+    __syncthreads();
+    // scatter through the bin cursors (the same bin expression as k_centre_hist)
+    const double lo = mom[2 + 2 * a], sc = bin_scale(mom[2 + 2 * a], mom[3 + 2 * a]);
+    double* key = E.lkey + (size_t)a * N;
+    int* idx = E.lidx + (size_t)a * N;
+    for (int i = tid; i < N; i += LIN_NT) {
+        const double b = E.beta[(size_t)a * N + i];
+        const int pos = atomicAdd(h + beta_bin(b, lo, sc), 1);
+        if (pos < N) { key[pos] = b; idx[pos] = i; }
+    }
+    __syncthreads();
+    // sort inside each bin by (position, ray index): insertion sort, one thread per bin
+    for (int bin = tid; bin < HB; bin += LIN_NT) {
+        const int e = min(h[bin], N), s0 = bin ? min(h[bin - 1], N) : 0;
+        for (int i = s0 + 1; i < e; ++i) {
+            const double kv = key[i];
+            const int iv = idx[i];
+            int j = i - 1;
+            while (j >= s0 && (key[j] > kv || (key[j] == kv && idx[j] > iv))) {
+                key[j + 1] = key[j];
+                idx[j + 1] = idx[j];
+                --j;
+            }
+            key[j + 1] = kv;
+            idx[j + 1] = iv;
+        }
+    }
+    __syncthreads();
+    float2* kf = reinterpret_cast<float2*>(E.lkf) + (size_t)a * N;
+    for (int j = tid; j < N; j += LIN_NT) {
+        const double v = key[j];
+        const float hi = (float)v;
+        kf[j] = make_float2(hi, (float)(v - (double)hi));
+        E.lrank[(size_t)a * N + idx[j]] = j;
+    }
+    // transform header: mu = 0, sigma = 1; end knots and end-segment slopes; the
+    // interior knots are spread evenly between them (unused by the linear map)
+    double* tr = E.trd;
+    const double x0 = key[0], x1 = key[N - 1];
+    const double hl = key[1] - key[0], hr = key[N - 1] - key[N - 2];
+    const double dl = hl > 0.0 ? 1.0 / ((N - 1) * hl) : 0.0;
+    const double dr = hr > 0.0 ? 1.0 / ((N - 1) * hr) : 0.0;
+    for (int j = tid; j < K; j += LIN_NT) {
+        const double X = j == K - 1 ? x1 : x0 + (x1 - x0) * ((double)j / (K - 1));
+        const double d = j == 0 ? dl : (j == K - 1 ? dr : 1.0 / (x1 - x0 > 0.0 ? x1 - x0 : 1.0));
+        tr[TR_HDR + a * K + j] = X;
+        tr[TR_HDR + (2 + a) * K + j] = d;
+        E.trf[TR_HDR + a * K + j] = (float)X;
+        E.trf[TR_HDR + (2 + a) * K + j] = (float)d;
+    }
+    if (tid == 0) {
+        tr[TR_HDR + 6 * K + a] = lo;
+        tr[TR_HDR + 6 * K + 2 + a] = sc;
+        E.trf[TR_HDR + 6 * K + a] = (float)lo;
+        E.trf[TR_HDR + 6 * K + 2 + a] = (float)sc;
+    }
+    if (a == 0 && tid < TR_HDR) {
+        const double v = tid == 2 ? 1.0 : (tid == 4 ? (double)N : 0.0);
+        tr[tid] = v;
+        E.trf[tid] = (float)v;
+    }
+    // CDF output: the standardisation (App. C i); knots and slopes are not used
+    if (E.cdf_out) {
+        if (a == 0 && tid < 3) E.cdf_out[tid] = tid < 2 ? mom[tid] : sig[0];
+        for (int j = tid; j < K; j += LIN_NT) {
+            E.cdf_out[3 + a * K + j] = 0.0;
+            E.cdf_out[3 + (2 + a) * K + j] = 0.0;
+        }
+    }
 }
 
 }  // namespace rtu

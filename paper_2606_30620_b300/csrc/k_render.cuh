@@ -150,6 +150,83 @@ __device__ __forceinline__ T cdf_grad(const T* X, const T* U, const T* d, const 
     return h00 * U[j] + h10 * h * d[j] + h01 * U[j + 1] + h11 * h * d[j + 1];
 }
 
+// ------------------------------------------- the unsmoothed eCDF (App. C)
+// Observation i of axis a is at most b: double positions, or float (hi, lo) pairs
+// compared exactly against a float b.
+__device__ __forceinline__ bool lin_le(const EvalArgs& E, int a, int i, double b) {
+    return E.lkey[(size_t)a * E.n_mask + i] <= b;
+}
+__device__ __forceinline__ bool lin_le(const EvalArgs& E, int a, int i, float b) {
+    const float2 k = reinterpret_cast<const float2*>(E.lkf)[(size_t)a * E.n_mask + i];
+    return k.x < b || (k.x == b && k.y <= 0.0f);
+}
+// position difference b - x_i and segment width x_{i+1} - x_i in the kernel's type
+__device__ __forceinline__ void lin_seg(const EvalArgs& E, int a, int i, double b, double& d0, double& h) {
+    const double* k = E.lkey + (size_t)a * E.n_mask + i;
+    d0 = b - k[0];
+    h = k[1] - k[0];
+}
+__device__ __forceinline__ void lin_seg(const EvalArgs& E, int a, int i, float b, float& d0, float& h) {
+    const float2* k = reinterpret_cast<const float2*>(E.lkf) + (size_t)a * E.n_mask + i;
+    const float2 k0 = k[0], k1 = k[1];
+    d0 = (b - k0.x) - k0.y;
+    h = (k1.x - k0.x) + (k1.y - k0.y);
+}
+
+// #{observations of axis a <= b}.  The histogram bin of b (bin origin bo, scale bs;
+// in float it can be off by one) narrows the search to the bins next to it; the
+// window is checked at both ends, else the search runs over all observations.
+// After k_lin_sort, hist[b] is the end of bin b.
+template <typename T>
+__device__ __forceinline__ int lin_count(const EvalArgs& E, int a, T b, T bo, T bs) {
+    const int N = E.n_mask;
+    const int* h = E.hist + a * HB;
+    const T t = (b - bo) * bs;
+    const int bin = t > T(0) ? (t < T(HB - 1) ? (int)t : HB - 1) : 0;
+    int lo = bin > 1 ? min(h[bin - 2], N) : 0;
+    int hi = bin < HB - 1 ? min(h[bin + 1], N) : N;
+    if (!((lo == 0 || lin_le(E, a, lo - 1, b)) && (hi == N || !lin_le(E, a, hi, b)))) {
+        lo = 0;
+        hi = N;
+    }
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (lin_le(E, a, mid, b)) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// u = (k + t)/(N - 1) on segment k = clamp(count - 1, 0, N - 2), t = (b - x_k)/(x_{k+1} - x_k);
+// beyond the end observations the end segment continues; a zero-width segment
+// gives t = 0.  With grad: du/db and the partials w.r.t. x_k and x_{k+1}.
+template <typename T>
+__device__ __forceinline__ T lin_value(const EvalArgs& E, int a, T b, T bo, T bs, T inv_nm1, int& k, T* dub = nullptr,
+                                       T* p0 = nullptr, T* p1 = nullptr) {
+    const int N = E.n_mask;
+    k = min(max(lin_count<T>(E, a, b, bo, bs) - 1, 0), N - 2);
+    T d0, h;
+    lin_seg(E, a, k, b, d0, h);
+    const bool ok = h > T(0);
+    const T ih = ok ? T(1) / h : T(0);
+    const T t = d0 * ih;
+    if (dub) {
+        const T s = inv_nm1 * ih;
+        *dub = s;
+        *p0 = (t - T(1)) * s;
+        *p1 = -t * s;
+    }
+    return ((T)k + t) * inv_nm1;
+}
+
+// bin origin and scale of axis a from the transform block
+template <typename T>
+__device__ __forceinline__ void lin_bins(const EvalArgs& E, int a, T& bo, T& bs) {
+    const int K = E.n_nodes + 2;
+    const int at = TR_HDR + 6 * K;
+    if (sizeof(T) == 4) { bo = (T)E.trf[at + a]; bs = (T)E.trf[at + 2 + a]; }
+    else { bo = (T)E.trd[at + a]; bs = (T)E.trd[at + 2 + a]; }
+}
+
 // transform (mu, sigma, knots, slopes) and node values into shared memory
 template <typename T>
 __device__ __forceinline__ void load_transform(const EvalArgs& E, T* trs, T* U) {
@@ -178,6 +255,14 @@ __device__ __forceinline__ bool near_edge(float gx, float gy, int n) {
     return fx < EDGE_DELTA || fx > 1.0f - EDGE_DELTA || fy < EDGE_DELTA || fy > 1.0f - EDGE_DELTA;
 }
 
+// the same with extra margins mx, my (cells) per axis
+__device__ __forceinline__ bool near_edge_m(float gx, float gy, int n, float mx, float my) {
+    const float dx = EDGE_DELTA + mx, dy = EDGE_DELTA + my;
+    if (gx < -dx || gx > (float)(n - 1) + dx || gy < -dy || gy > (float)(n - 1) + dy) return false;
+    const float fx = gx - floorf(gx), fy = gy - floorf(gy);
+    return fx < dx || fx > 1.0f - dx || fy < dy || fy > 1.0f - dy;
+}
+
 // bilinear value at grid coordinate (gx, gy) with the cell decided by the caller
 template <typename T, typename G>
 __device__ __forceinline__ T bilinear_at(const G* grid, int n, int i0, int j0, T fx, T fy) {
@@ -200,24 +285,32 @@ __device__ __forceinline__ int cell_of(T yx, T yy, int n, T& fx, T& fy, int& i0,
     return j0 * (n - 1) + i0;
 }
 
-// double-precision RTU coordinates of a source-plane position
-__device__ __forceinline__ void rtu_coords_from_beta(const double* trd, const double* U, int K, double bx,
-                                                     double by, double& yx, double& yy) {
+// double-precision grid coordinates of a source-plane position (the Hermite CDF
+// from the shared transform block, or the unsmoothed eCDF)
+__device__ __forceinline__ void rtu_coords_from_beta(const EvalArgs& E, const double* trd, const double* U, int K,
+                                                     double bx, double by, double& yx, double& yy) {
+    if (E.transform == RTU_TRANSFORM_LINEAR) {
+        const double inv = 1.0 / (E.n_mask - 1);
+        double bo, bs;
+        int k;
+        lin_bins<double>(E, 0, bo, bs);
+        yx = lin_value<double>(E, 0, bx, bo, bs, inv, k);
+        lin_bins<double>(E, 1, bo, bs);
+        yy = lin_value<double>(E, 1, by, bo, bs, inv, k);
+        return;
+    }
     const double* X = trd + TR_HDR;
     const double zx = (bx - trd[0]) / trd[2], zy = (by - trd[1]) / trd[2];
     yx = cdf_value<double>(X, U, X + 2 * K, K, cdf_interval<double>(X, K, zx), zx);
     yy = cdf_value<double>(X + K, U, X + 3 * K, K, cdf_interval<double>(X + K, K, zy), zy);
 }
 
-// double-precision RTU coordinates of a ray from the double lens block
-__device__ __forceinline__ void rtu_coords_d(const LensK<double>& Kd, const double* trd, const double* U, int K,
-                                             double x, double y, double& yx, double& yy) {
+// double-precision grid coordinates of a ray from the double lens block
+__device__ __forceinline__ void rtu_coords_d(const EvalArgs& E, const LensK<double>& Kd, const double* trd,
+                                             const double* U, int K, double x, double y, double& yx, double& yy) {
     double bx, by;
     lens_beta(Kd, x, y, bx, by);
-    const double* X = trd + TR_HDR;
-    const double zx = (bx - trd[0]) / trd[2], zy = (by - trd[1]) / trd[2];
-    yx = cdf_value<double>(X, U, X + 2 * K, K, cdf_interval<double>(X, K, zx), zx);
-    yy = cdf_value<double>(X + K, U, X + 3 * K, K, cdf_interval<double>(X + K, K, zy), zy);
+    rtu_coords_from_beta(E, trd, U, K, bx, by, yx, yy);
 }
 
 template <typename T>
@@ -333,8 +426,9 @@ __device__ inline bool tile_out_of_reach(const EvalArgs& E, int tile) {
     return out;
 }
 
-// S7 + S11: one thread per image pixel, s^2 sub-rays each.
-template <typename T>
+// S7 + S11: one thread per image pixel, s^2 sub-rays each.  LIN: the unsmoothed
+// eCDF map (its own instantiation, so the smoothed map's code is not burdened).
+template <typename T, bool LIN>
 __global__ void __launch_bounds__(CTA_R, 6) k_render(const __grid_constant__ Batch B) {
     const int ev = find_eval(B, blockIdx.x);
     const EvalArgs& E = B.e[ev];
@@ -403,6 +497,14 @@ __global__ void __launch_bounds__(CTA_R, 6) k_render(const __grid_constant__ Bat
         zhi[a] = X[K - 1] + m / d[K - 1];
     }
     const int pj = (int)udiv((uint32_t)pixel, sh.dv_n), pi = pixel - pj * E.n_img;
+    // the unsmoothed eCDF: bin lookup constants (z is the raw position there)
+    constexpr bool lin = LIN;
+    T lbo[2] = {T(0), T(0)}, lbs[2] = {T(0), T(0)};
+    const T linv = lin ? T(1) / T(E.n_mask - 1) : T(0);
+    if (lin) {
+        lin_bins<T>(E, 0, lbo[0], lbs[0]);
+        lin_bins<T>(E, 1, lbo[1], lbs[1]);
+    }
 
     T acc = T(0);
     unsigned long long deferred = 0ull;      // bit q: sub-ray q went to the double pass
@@ -419,7 +521,7 @@ __global__ void __launch_bounds__(CTA_R, 6) k_render(const __grid_constant__ Bat
         if (sizeof(T) == 4 && lens_near_core(sh.K, x, y)) {
             double xd, yd, ydx, ydy;
             ray_pos(E.n_img, E.pix, s, pixel, q, xd, yd);
-            rtu_coords_d(sh.Kd, sh.trd, sh.Ud, K, xd, yd, ydx, ydy);
+            rtu_coords_d(E, sh.Kd, sh.trd, sh.Ud, K, xd, yd, ydx, ydy);
             yx = (T)ydx;
             yy = (T)ydy;
             if (near_edge((float)(ydx * (n - 1)), (float)(ydy * (n - 1)), n)) {
@@ -458,9 +560,24 @@ __global__ void __launch_bounds__(CTA_R, 6) k_render(const __grid_constant__ Bat
             const T zx = (bx - mux) * isg, zy = (by - muy) * isg;
             // far outside the grid (beyond the near-edge margin): no cell, zero source
             if (zx < zlo[0] || zx > zhi[0] || zy < zlo[1] || zy > zhi[1]) return -1;
-            yx = cdf_value_r<T>(Xx, sh.U, dx_, sh.ih, K, cdf_interval<T>(Xx, K, zx), zx);
-            yy = cdf_value_r<T>(Xy, sh.U, dy_, sh.ih + K, K, cdf_interval<T>(Xy, K, zy), zy);
-            if (sizeof(T) == 4 && near_edge((float)(yx * T(n - 1)), (float)(yy * T(n - 1)), n)) {
+            float mx = 0.0f, my = 0.0f;     // extra near-edge margin (cells)
+            if constexpr (lin) {
+                int kk;
+                T sx, sy, pu;
+                yx = lin_value<T>(E, 0, zx, lbo[0], lbs[0], linv, kk, &sx, &pu, &pu);
+                yy = lin_value<T>(E, 1, zy, lbo[1], lbs[1], linv, kk, &sy, &pu, &pu);
+                if (sizeof(T) == 4) {
+                    // the float position's error (a few 1e-7 of the positions involved)
+                    // times the map's slope there, in cells: narrow segments make it large
+                    mx = (float)(T(n - 1) * sx * T(1e-6) * (T(1) + r_abs(zx) + r_abs(x)));
+                    my = (float)(T(n - 1) * sy * T(1e-6) * (T(1) + r_abs(zy) + r_abs(y)));
+                }
+            } else {
+                yx = cdf_value_r<T>(Xx, sh.U, dx_, sh.ih, K, cdf_interval<T>(Xx, K, zx), zx);
+                yy = cdf_value_r<T>(Xy, sh.U, dy_, sh.ih + K, K, cdf_interval<T>(Xy, K, zy), zy);
+            }
+            if (sizeof(T) == 4 && (lin ? near_edge_m((float)(yx * T(n - 1)), (float)(yy * T(n - 1)), n, mx, my)
+                                       : near_edge((float)(yx * T(n - 1)), (float)(yy * T(n - 1)), n))) {
                 deferred |= 1ull << q;
                 ++nin;               // may turn out outside: k_render_edge takes it back
                 return 0;
@@ -555,9 +672,9 @@ __global__ void __launch_bounds__(EDGE_NT) k_render_edge(const __grid_constant__
         if (use_df) {
             DF bxf, byf;
             lens_beta_smooth<DF>(Kdf, DF(xd), DF(yd), bxf, byf);
-            rtu_coords_from_beta(trd, Ud, K, bxf.to_double(), byf.to_double(), yx, yy);
+            rtu_coords_from_beta(E, trd, Ud, K, bxf.to_double(), byf.to_double(), yx, yy);
         } else {
-            rtu_coords_d(Kd, trd, Ud, K, xd, yd, yx, yy);
+            rtu_coords_d(E, Kd, trd, Ud, K, xd, yd, yx, yy);
         }
         double fx, fy;
         int i0, j0;
@@ -674,6 +791,11 @@ __global__ void __launch_bounds__(CMP_NT) k_compact(const __grid_constant__ Batc
     const int lane = threadIdx.x & 31;
     const int nu = E.n_cta_r * (CTA_R / 32);
     const int u = tile * (CMP_NT / 32) + (threadIdx.x >> 5);
+    if (E.transform == RTU_TRANSFORM_LINEAR) {
+        // the unsmoothed eCDF's position gradients, accumulated by k_render_adj
+        const int nt = (nu + CMP_NT / 32 - 1) / (CMP_NT / 32);
+        for (int i = tile * CMP_NT + threadIdx.x; i < 2 * E.n_mask; i += nt * CMP_NT) E.gk[i] = 0.0;
+    }
     if (u >= nu) return;
     const int cap = 32 * E.s * E.s;
     const int n_rays = E.n_img * E.n_img * E.s * E.s;
@@ -695,8 +817,10 @@ __global__ void __launch_bounds__(CMP_NT) k_compact(const __grid_constant__ Batc
 // CTA_R x ADJ_RPT rays, thread t taking rays t, t + CTA_R, ... of a chunk.  Each ray is recomputed (value + the EPL
 // series sums) and differentiated analytically; its cell comes from the forward
 // pass.  Writes one counting-sorted record per ray and fixed-order per-CTA
-// partial sums of the lens, standardisation and spline-knot gradients.
-template <typename T>
+// partial sums of the lens, standardisation and spline-knot gradients (for the
+// unsmoothed eCDF: double atomics into the gradients of the sorted positions, so
+// their summation order varies between runs).
+template <typename T, bool LIN>
 __global__ void __launch_bounds__(CTA_R, 4) k_render_adj(const __grid_constant__ Batch B) {
     typedef typename real4_of<T>::type R4;
     typedef typename real2_of<T>::type R2;
@@ -734,6 +858,26 @@ __global__ void __launch_bounds__(CTA_R, 4) k_render_adj(const __grid_constant__
     const T* Xa[2] = {sh.trs + TR_HDR, sh.trs + TR_HDR + K};
     const T* Da[2] = {sh.trs + TR_HDR + 2 * K, sh.trs + TR_HDR + 3 * K};
     const T nm1 = T(n - 1);
+    constexpr bool lin = LIN;
+    T lbo[2] = {T(0), T(0)}, lbs[2] = {T(0), T(0)};
+    double lbo_d[2] = {0.0, 0.0}, lbs_d[2] = {0.0, 0.0};
+    const T linv = lin ? T(1) / T(E.n_mask - 1) : T(0);
+    const double linv_d = lin ? 1.0 / (E.n_mask - 1) : 0.0;
+    LensK<DF>* kdf = nullptr;
+    if constexpr (lin) {
+        lin_bins<T>(E, 0, lbo[0], lbs[0]);
+        lin_bins<T>(E, 1, lbo[1], lbs[1]);
+        lin_bins<double>(E, 0, lbo_d[0], lbs_d[0]);
+        lin_bins<double>(E, 1, lbo_d[1], lbs_d[1]);
+        if constexpr (sizeof(T) == 4) {
+            // the double-float lens of the unsmoothed map's positions
+            __shared__ LensK<DF> kdf_s;
+            kdf = &kdf_s;
+            __syncthreads();
+            if (sh.Kd.nsub == 0) lensk_to_df(sh.Kd, kdf_s);
+            __syncthreads();
+        }
+    }
     const int* off = E.ccount + nc * nc;
     R4* rec = reinterpret_cast<R4*>(E.rec);
     R2* gbuf = reinterpret_cast<R2*>(E.gbuf);
@@ -818,9 +962,9 @@ __global__ void __launch_bounds__(CTA_R, 4) k_render_adj(const __grid_constant__
                 EplJ<double> Jd;
                 double xd = 0.0, yd = 0.0;
                 T bx, by;
+                double bxd = 0.0, byd = 0.0;
                 if (near) {
                     ray_pos(E.n_img, E.pix, s, pixel, q, xd, yd);
-                    double bxd, byd;
                     lens_beta_eval(sh.Kd, xd, yd, Jd, bxd, byd);
                     bx = (T)bxd;
                     by = (T)byd;
@@ -829,10 +973,45 @@ __global__ void __launch_bounds__(CTA_R, 4) k_render_adj(const __grid_constant__
                 }
                 const T z[2] = {(bx - mux) * isg, (by - muy) * isg};
                 T yv[2], dz[2];
-                for (int a = 0; a < 2; ++a) {
-                    jn[a] = cdf_interval<T>(Xa[a], K, z[a]);
-                    yv[a] = cdf_grad<T>(Xa[a], sh.U, Da[a], sh.ih + a * K, K, jn[a], z[a], dz[a], pn[a][0], pn[a][1], pn[a][2],
-                                        pn[a][3]);
+                int ks[2] = {0, 0};
+                double pk[2][2] = {{0.0, 0.0}, {0.0, 0.0}};     // unsmoothed eCDF: segment partials
+                if constexpr (lin && sizeof(T) == 4) {
+                    // The split of the ray's gradient between the two observations of its
+                    // segment, t = (beta - x_k)/(x_{k+1} - x_k), needs beta far below the
+                    // narrowest segment widths (1e-9 arcsec occur): the position in
+                    // double-float (double with subhaloes), the segment in double.
+                    if (!near) {
+                        ray_pos(E.n_img, E.pix, s, pixel, q, xd, yd);
+                        if (nsub) {
+                            lens_beta(sh.Kd, xd, yd, bxd, byd);
+                        } else {
+                            DF bxf, byf;
+                            lens_beta_smooth<DF>(*kdf, DF(xd), DF(yd), bxf, byf);
+                            bxd = bxf.to_double();
+                            byd = byf.to_double();
+                        }
+                    }
+                    const double bd[2] = {bxd, byd};
+                    for (int a = 0; a < 2; ++a) {
+                        double dub;
+                        yv[a] = (T)lin_value<double>(E, a, bd[a], lbo_d[a], lbs_d[a], linv_d, ks[a], &dub, &pk[a][0],
+                                                     &pk[a][1]);
+                        dz[a] = (T)dub;
+                        pn[a][0] = pn[a][1] = pn[a][2] = pn[a][3] = T(0);
+                    }
+                } else if constexpr (lin) {
+                    for (int a = 0; a < 2; ++a) {
+                        yv[a] = lin_value<T>(E, a, z[a], lbo[a], lbs[a], linv, ks[a], &dz[a], &pn[a][0], &pn[a][1]);
+                        pk[a][0] = (double)pn[a][0];
+                        pk[a][1] = (double)pn[a][1];
+                        pn[a][2] = pn[a][3] = T(0);
+                    }
+                } else {
+                    for (int a = 0; a < 2; ++a) {
+                        jn[a] = cdf_interval<T>(Xa[a], K, z[a]);
+                        yv[a] = cdf_grad<T>(Xa[a], sh.U, Da[a], sh.ih + a * K, K, jn[a], z[a], dz[a], pn[a][0], pn[a][1],
+                                            pn[a][2], pn[a][3]);
+                    }
                 }
                 const int j0 = (int)udiv((uint32_t)cell, sh.dv_nc), i0 = cell - j0 * nc;
                 const T fx = yv[0] * nm1 - T(i0), fy = yv[1] * nm1 - T(j0);
@@ -856,7 +1035,18 @@ __global__ void __launch_bounds__(CTA_R, 4) k_render_adj(const __grid_constant__
                 }
                 for (int a = 0; a < 2; ++a)
                     for (int c = 0; c < 4; ++c) pn[a][c] *= gy[a];
-                have = true;
+                if constexpr (lin) {
+                    // the two observations of the ray's segment, per axis: double
+                    // atomics into d logL / d (sorted position)
+                    for (int a = 0; a < 2; ++a) {
+                        const double ga = (double)gy[a];
+                        if (ga == 0.0 || (pk[a][0] == 0.0 && pk[a][1] == 0.0)) continue;
+                        double* g = E.gk + (size_t)a * E.n_mask + ks[a];
+                        atomicAdd(g, ga * pk[a][0]);
+                        atomicAdd(g + 1, ga * pk[a][1]);
+                    }
+                }
+                have = !lin;
                 if (slot >= off[cell] && slot < off[cell + 1]) {
                     R4 rr;
                     rr.x = fx; rr.y = fy; rr.z = gpix; rr.w = T(0);

@@ -142,6 +142,14 @@ size_t slot_layout(const rtu_system_desc& d, char* base, EvalArgs* e) {
     p = take((size_t)z.n_rays * 4);                   if (e) e->kcell = (int*)p;
     p = take((size_t)z.n_rays * 2 * z.tb);            if (e) e->gbuf = p;
     p = take((size_t)z.n_cta_r * 6 * std::max(1, d.n_light) * 8); if (e) e->lpartl = (double*)p;
+    if (d.transform == RTU_TRANSFORM_LINEAR) {
+        // the unsmoothed eCDF: every order statistic and its gradient
+        p = take((size_t)2 * z.nm_max * 8);           if (e) e->lkey = (double*)p;
+        p = take((size_t)2 * z.nm_max * 4);           if (e) e->lidx = (int*)p;
+        p = take((size_t)2 * z.nm_max * 4);           if (e) e->lrank = (int*)p;
+        p = take((size_t)2 * z.nm_max * 8);           if (e) e->lkf = (float*)p;
+        p = take((size_t)2 * z.nm_max * 8);           if (e) e->gk = (double*)p;
+    }
     return o;
 }
 
@@ -246,7 +254,11 @@ const char* check_desc(const rtu_system_desc* d) {
     if (d->n_nodes != d->degree + 1) return "this build supports n_nodes == degree + 1 (interpolating fit)";
     if (d->n_nodes < 2 || d->n_nodes > MAXM) return "n_nodes must be in [2, 64]";
     if (d->n_slots < 1) return "n_slots must be >= 1";
-    if (d->transform != RTU_TRANSFORM_RTU && d->transform != RTU_TRANSFORM_UNIFORM) return "bad transform";
+    if (d->transform != RTU_TRANSFORM_RTU && d->transform != RTU_TRANSFORM_UNIFORM &&
+        d->transform != RTU_TRANSFORM_LINEAR)
+        return "bad transform";
+    if (d->transform == RTU_TRANSFORM_LINEAR && d->weights)
+        return "the unsmoothed eCDF transform takes no ray weights";
     if (d->n_light < 0 || d->n_light > RTU_MAX_LIGHT) return "n_light must be in [0, 8]";
     if (!(d->pix > 0) || !(d->src_pitch > 0) || !(d->sigma > 0)) return "pix, src_pitch, sigma must be > 0";
     if (!d->data || !d->mask || !d->psf) return "data, mask and psf must be device pointers";
@@ -261,10 +273,14 @@ void set_attributes() {
     cudaFuncSetAttribute(k_select_fit, cudaFuncAttributeMaxDynamicSharedMemorySize, SEL_SMEM);
     cudaFuncSetAttribute(k_gp_adjoint<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, GP_SMEM);
     cudaFuncSetAttribute(k_gp_adjoint<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, GP_SMEM);
-    cudaFuncSetAttribute(k_render<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN);
-    cudaFuncSetAttribute(k_render<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN);
-    cudaFuncSetAttribute(k_render_adj<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN);
-    cudaFuncSetAttribute(k_render_adj<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN);
+    cudaFuncSetAttribute(k_render<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN);
+    cudaFuncSetAttribute(k_render<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN);
+    cudaFuncSetAttribute(k_render<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN);
+    cudaFuncSetAttribute(k_render<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN);
+    cudaFuncSetAttribute(k_render_adj<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN);
+    cudaFuncSetAttribute(k_render_adj<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN);
+    cudaFuncSetAttribute(k_render_adj<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN);
+    cudaFuncSetAttribute(k_render_adj<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN);
 }
 
 }  // namespace
@@ -488,7 +504,17 @@ rtu_status launch(const char* name, Kern kern, Batch& B, TileFn tiles, int threa
 }
 
 int t_one(const EvalArgs&) { return 1; }
-int t_two(const EvalArgs&) { return 2; }
+// smoothed (RTU, uniform box) or unsmoothed-eCDF systems only, in a mixed batch
+bool is_lin(const EvalArgs& e) { return e.transform == RTU_TRANSFORM_LINEAR; }
+int t_two_fit(const EvalArgs& e) { return is_lin(e) ? 0 : 2; }
+int t_two_lin(const EvalArgs& e) { return is_lin(e) ? 2 : 0; }
+int t_one_fit(const EvalArgs& e) { return is_lin(e) ? 0 : 1; }
+int t_centre_fit(const EvalArgs& e) { return is_lin(e) ? 0 : e.n_cta_c; }
+int t_centre_lin(const EvalArgs& e) { return is_lin(e) ? e.n_cta_c : 0; }
+int t_render_fit(const EvalArgs& e) { return is_lin(e) ? 0 : e.n_cta_r; }
+int t_render_lin(const EvalArgs& e) { return is_lin(e) ? e.n_cta_r : 0; }
+int t_adj_fit(const EvalArgs& e) { return is_lin(e) ? 0 : e.n_cta_adj; }
+int t_adj_lin(const EvalArgs& e) { return is_lin(e) ? e.n_cta_adj : 0; }
 int t_gp_lines(const EvalArgs& e) { return (e.n_src + GP_LINES - 1) / GP_LINES; }
 int t_zero(const EvalArgs&) { return ZERO_TILES; }
 int t_centre(const EvalArgs& e) { return e.n_cta_c; }
@@ -565,14 +591,16 @@ rtu_status run_chunk(Batch& B, int phase, cudaStream_t st, const SideStream& ss)
         if ((r = launch("k_zero", k_zero, B, t_zero, 256, 0, st, (phase & PH_FORWARD) ? 1 : 0))) return r;
         if ((r = launch("k_trace_centres", k_trace_centres, B, t_centre, CTA_C, 0, st))) return r;
         if ((r = launch("k_centre_hist", k_centre_hist, B, t_centre, CTA_C, 0, st))) return r;
-        if ((r = launch("k_select_fit", k_select_fit, B, t_two, SEL_NT, SEL_SMEM, st))) return r;
+        if ((r = launch("k_select_fit", k_select_fit, B, t_two_fit, SEL_NT, SEL_SMEM, st))) return r;
+        if ((r = launch("k_lin_sort", k_lin_sort, B, t_two_lin, LIN_NT, 0, st))) return r;
     }
     if (phase & PH_FORWARD) {
         if ((r = stream_after(st, ss.s, ss.join))) return r;
         if (grid_bytes > MAX_DYN) return fail(RTU_E_ARG, "source grid too large for shared memory");
         const size_t render_smem = grid_bytes + (size_t)CTA_R * max_s2 * 4;
         if (render_smem > MAX_DYN) return fail(RTU_E_ARG, "render shared memory exceeds the limit");
-        if ((r = launch("k_render", k_render<T>, B, t_render, CTA_R, render_smem, st))) return r;
+        if ((r = launch("k_render", k_render<T, false>, B, t_render_fit, CTA_R, render_smem, st))) return r;
+        if ((r = launch("k_render", k_render<T, true>, B, t_render_lin, CTA_R, render_smem, st))) return r;
         if (sizeof(T) == 4) {
             if ((r = launch("k_render_edge", k_render_edge, B, t_edge, EDGE_NT, 0, st))) return r;
             if ((r = launch("k_render_fix", k_render_fix, B, t_fix, 256, 0, st))) return r;
@@ -593,13 +621,15 @@ rtu_status run_chunk(Batch& B, int phase, cudaStream_t st, const SideStream& ss)
         const size_t adj = grid_bytes + (size_t)(CTA_R / 32) * 4 * maxK * 2 * sizeof(T);
         if (adj > MAX_DYN) return fail(RTU_E_ARG, "adjoint shared memory exceeds the limit");
         if ((r = launch("k_compact", k_compact, B, t_units, CMP_NT, 0, st))) return r;
-        if ((r = launch("k_render_adj", k_render_adj<T>, B, t_adj, CTA_R, adj, st))) return r;
+        if ((r = launch("k_render_adj", k_render_adj<T, false>, B, t_adj_fit, CTA_R, adj, st))) return r;
+        if ((r = launch("k_render_adj", k_render_adj<T, true>, B, t_adj_lin, CTA_R, adj, st))) return r;
         if (any_sub && (r = launch("k_sub_adj", k_sub_adj<T>, B, t_adj, CTA_R, 0, st))) return r;
         // transform and centre-ray adjoint (side) beside the cell gather and GP adjoint (main)
         if ((r = stream_after(ss.s, st, ss.fork))) return r;
-        if ((r = launch("k_cdf_adj", k_cdf_adj, B, t_two, CDF_NT, 0, ss.s))) return r;
-        if ((r = launch("k_centre_adj", k_centre_adj<T>, B, t_centre, CTA_C, 0, ss.s))) return r;
-        if ((r = launch("k_sel_adj", k_sel_adj, B, t_one, SEL_ADJ_NT, 0, ss.s))) return r;
+        if ((r = launch("k_cdf_adj", k_cdf_adj, B, t_two_fit, CDF_NT, 0, ss.s))) return r;
+        if ((r = launch("k_centre_adj", k_centre_adj<T>, B, t_centre_fit, CTA_C, 0, ss.s))) return r;
+        if ((r = launch("k_sel_adj", k_sel_adj, B, t_one_fit, SEL_ADJ_NT, 0, ss.s))) return r;
+        if ((r = launch("k_lin_centre_adj", k_lin_centre_adj, B, t_centre_lin, CTA_C, 0, ss.s))) return r;
         if ((r = launch("k_cell_gather", k_cell_gather<T>, B, t_cells, GATHER_NT, 0, st))) return r;
         if ((r = launch("k_gp_adjoint", k_gp_adjoint<T>, B, t_one, GP_NT, GP_SMEM, st))) return r;
         if ((r = stream_after(st, ss.s, ss.join))) return r;

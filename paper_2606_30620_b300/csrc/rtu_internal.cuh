@@ -101,6 +101,13 @@ struct EvalArgs {
     double* g_light;       // [6 n_light] adjoint out
     double* lpartl;        // [n_cta_r][6 n_light] per-CTA lens-light gradient partials
     int n_cta_adj;     // CTAs of the render adjoint (grid-stride over the compacted rays)
+    int pad4_;
+    // the unsmoothed eCDF transform (App. C, first paragraph), per axis a at a * n_mask
+    double* lkey;      // [2][n_mask] sorted centre-ray positions
+    int* lidx;         // [2][n_mask] the centre ray at each rank
+    int* lrank;        // [2][n_mask] the rank of each centre ray
+    float* lkf;        // [2][n_mask] float2 (hi, lo) of lkey
+    double* gk;        // [2][n_mask] d logL / d (sorted position), adjoint
 };
 
 struct Batch {
@@ -119,6 +126,9 @@ struct Batch {
 //   [8+6K ..)         raw knots x (before the guard)   [8+7K ..) raw knots y
 //   [8+8K ..)         chebyshev coeffs x (D+1 <= MAXM) [8+8K+MAXM ..) y
 //   [8+8K+2MAXM ..)   Q at nodes x, y (M each, MAXM stride)
+//   the unsmoothed eCDF transform keeps mu = 0, sigma = 1 and uses only the end
+//   knots and end slopes, plus [8+6K + a] bin origin and [8+6K+2 + a] bin scale
+//   of the level-1 histogram per axis a
 constexpr int TR_HDR = 8;
 __host__ __device__ constexpr int tr_size(int K) { return TR_HDR + 8 * K + 4 * MAXM; }
 

@@ -22,7 +22,7 @@ RTU_F32, RTU_F64 = 0, 1
 RTU_SIE, RTU_EPL = 0, 1
 RTU_SUB_NONE, RTU_SUB_NFW, RTU_SUB_TNFW = 0, 1, 2
 RTU_PS_POWER_LAW, RTU_PS_MATERN_LIKE, RTU_PS_MATERN = 0, 1, 2
-RTU_TRANSFORM_RTU, RTU_TRANSFORM_UNIFORM = 0, 1
+RTU_TRANSFORM_RTU, RTU_TRANSFORM_UNIFORM, RTU_TRANSFORM_LINEAR = 0, 1, 2
 STAT_LOGL, STAT_CHI2, STAT_NMASK, STAT_FLAGS, STAT_N_IN_GRID = 0, 1, 2, 3, 4
 W_NONMONOTONE, W_SELECT, W_TIMEOUT = 1, 2, 4
 N_STATS = 5

@@ -49,6 +49,9 @@ def run_oracle(m, grads=True, transform=0):
     hist = O.ray_hist(s, lens, subs, T)
     if isinstance(T, O.BoxTransform):
         cdf = None          # the box map has no knots of its own to compare
+    elif isinstance(T, O.LinearTransform):
+        # the unsmoothed eCDF: the standardisation, then zeros in the knot/slope slots
+        cdf = np.concatenate([T.mu.detach().numpy(), [float(T.sigma)], np.zeros(4 * (s.n_nodes + 2))])
     else:
         cdf = np.concatenate([T.mu.detach().numpy(), [float(T.sigma)], T.knots.detach().numpy().ravel(),
                               T.slopes.detach().numpy().ravel()])
@@ -82,3 +85,32 @@ def compare(g, o):
     if "g_light" in g and "g_light" in o:
         res["g_light"] = rel_l2(g["g_light"], o["g_light"])
     return res
+
+
+def rounding_sensitivity(m, transform, eps, reps=2, seed=0):
+    """Relative change of the oracle's lens gradient when every traced position
+    (centre rays and sub-rays) is moved by +-eps (|beta| + |theta|) -- the size of the
+    terms of beta = theta - alpha(theta) -- on each axis: the spread that rounding at
+    relative level eps alone can cause.  The unsmoothed eCDF splits each
+    ray's gradient between the two observations of its segment by
+    t = (beta - x_k)/(x_{k+1} - x_k), and segments can be narrower than 1e-9 arcsec,
+    so its lens gradient is sensitive at that level (a property of the map, shared by
+    any implementation)."""
+    base = run_oracle(m, transform=transform)["g_lens"]
+    trace0 = O.trace
+    rng = np.random.default_rng(seed)
+    worst = 0.0
+    try:
+        for _ in range(reps):
+            def trace_rounded(x, y, *a, **k):
+                bx, by = trace0(x, y, *a, **k)
+                sx = torch.tensor(rng.choice([-1.0, 1.0], size=bx.shape), dtype=bx.dtype)
+                sy = torch.tensor(rng.choice([-1.0, 1.0], size=by.shape), dtype=by.dtype)
+                mx = bx.detach().abs() + x.detach().abs()
+                my = by.detach().abs() + y.detach().abs()
+                return bx + eps * mx * sx, by + eps * my * sy
+            O.trace = trace_rounded
+            worst = max(worst, rel_l2(run_oracle(m, transform=transform)["g_lens"], base))
+    finally:
+        O.trace = trace0
+    return worst

@@ -75,9 +75,16 @@ def test_workspace_size_validates_the_description():
     two = lib.rtu_workspace_size(ctypes.byref(_desc(n_slots=2)))
     assert two > ok
     for bad in (dict(n_src=50), dict(n_src=512), dict(psf_k=4), dict(n_nodes=30), dict(s_super=0),
-                dict(precision=3), dict(sigma=0.0), dict(n_sub=17), dict(data=0), dict(transform=2),
-                dict(n_light=9), dict(n_light=-1)):
+                dict(precision=3), dict(sigma=0.0), dict(n_sub=17), dict(data=0), dict(transform=3),
+                dict(transform=-1), dict(n_light=9), dict(n_light=-1),
+                dict(transform=rtu.RTU_TRANSFORM_LINEAR, weights=1 << 23)):
         assert lib.rtu_workspace_size(ctypes.byref(_desc(**bad))) == 0, bad
+    # the unsmoothed eCDF keeps every order statistic: a larger slot
+    lin = lib.rtu_workspace_size(ctypes.byref(_desc(transform=rtu.RTU_TRANSFORM_LINEAR)))
+    assert lin > ok
+    rc = lib.rtu_system_create(ctypes.byref(_desc(transform=2, weights=1 << 23)), ctypes.c_void_p(1 << 20),
+                               1 << 30, ctypes.byref(ctypes.c_void_p()))
+    assert rc == -1 and "weights" in lib.rtu_last_error().decode()
 
 
 def test_create_rejects_bad_workspace_without_touching_the_gpu():

@@ -238,3 +238,65 @@ def test_weighted_grid_rejects_zero_weights_on_the_mask(rtu):
     m.weights = w
     with pytest.raises(rtu.RTUError, match="weights must be >= 1"):
         rtu.System.from_mock(m, precision=rtu.RTU_F64)
+
+
+# ------------------------------------------- unsmoothed linear eCDF (App. C, first paragraph)
+# Position rounding of the two paths: FP64 positions a few units of 2^-53; the FP32
+# path's adjoint positions for this map are double-float (about 2^-48 with the series'
+# own rounding).  The lens-gradient tolerance is the stated one or ten times the
+# oracle's own spread under position perturbations of that size, whichever is larger.
+LIN_POS_EPS = {1: 4.0 * 2.0 ** -53, 0: 4e-14}
+
+
+def _check_linear(m, prec, g):
+    r = G.compare(g, G.run_oracle(m, transform=2))
+    base = F64_TOL if prec == 1 else F32_TOL
+    tol = max(base, 10.0 * G.rounding_sensitivity(m, 2, LIN_POS_EPS[prec]))
+    assert r["g_lens"] < tol, (r["g_lens"], tol)
+    r["g_lens"] = 0.0
+    _check(r, prec)
+    return tol
+
+
+@pytest.mark.parametrize("prec,kw", [(1, dict(seed=71)), (1, dict(seed=72, profile=I.PROFILE_SIE, n_img=20)),
+                                     (1, dict(seed=73, sub_kind=I.SUB_TNFW, n_sub=2)),
+                                     (1, dict(seed=74, n_img=17, s=3, n_src=12, psf_k=5)),
+                                     (0, dict(seed=75, n_img=24, n_src=16)), (0, dict(seed=71)),
+                                     (0, dict(seed=76, sub_kind=I.SUB_NFW, n_sub=2))])
+def test_linear_ecdf_grid_matches_oracle(rtu, prec, kw):
+    m = I.config_tiny(**kw)
+    g, _, _ = G.run_gpu(m, prec, transform=rtu.RTU_TRANSFORM_LINEAR)
+    _check_linear(m, prec, g)
+
+
+@pytest.mark.parametrize("prec", [1, 0])
+def test_linear_ecdf_grid_c2_matches_oracle(rtu, prec):
+    # 200 x 200 pixels, 4 x 4 sub-rays: every order statistic of ~10^4 centre rays
+    m = I.config_c2(1006)
+    g, _, _ = G.run_gpu(m, prec, transform=rtu.RTU_TRANSFORM_LINEAR)
+    tol = _check_linear(m, prec, g)
+    assert tol < 1e-4      # the derived tolerance stays far below the float path's own error before the fix
+
+
+def test_mixed_transforms_in_one_batch(rtu):
+    # smoothed, box and unsmoothed systems in one call: each kernel runs for the
+    # systems of its transform only, and each system gets its own result
+    mocks = [I.config_c2(1070 + k, n_img=48, s=2, n_src=16) for k in range(3)]
+    kinds = [rtu.RTU_TRANSFORM_LINEAR, rtu.RTU_TRANSFORM_RTU, rtu.RTU_TRANSFORM_UNIFORM]
+    binds = []
+    for m, kind in zip(mocks, kinds):
+        s = rtu.System.from_mock(m, precision=rtu.RTU_F64, transform=kind)
+        binds.append(rtu.Binding(s, m.lens, m.latents, m.ps, want_model=True, want_hist=True))
+    batch = rtu.Batch(binds)
+    batch.forward()
+    batch.adjoint()
+    torch.cuda.synchronize()
+    for m, kind, b in zip(mocks, kinds, binds):
+        o = G.run_oracle(m, transform=kind)
+        assert abs(b.stats.cpu().numpy()[0] - o["logL"]) < F64_TOL * abs(o["logL"])
+        assert G.rel_l2(b.model.cpu().numpy(), o["model"]) < F64_TOL
+        assert np.array_equal(b.ray_hist.cpu().numpy(), o["hist"])
+        tol = F64_TOL if kind != rtu.RTU_TRANSFORM_LINEAR else max(
+            F64_TOL, 10.0 * G.rounding_sensitivity(m, kind, LIN_POS_EPS[1]))
+        assert G.rel_l2(b.g_lens.cpu().numpy(), o["g_lens"]) < tol
+        assert G.rel_l2(b.g_latents.cpu().numpy(), o["g_latents"]) < F64_TOL
