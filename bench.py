@@ -18,6 +18,7 @@ build; there is no other implementation to run).
 from __future__ import annotations
 
 import argparse
+import copy
 import hashlib
 import json
 import math
@@ -360,6 +361,7 @@ def run_ours(args):
     launches = sum(v[0] for v in kern.values()) // n_prof * args.steps
 
     clocks = clk.summary()
+    variants = run_variants(args, dev, mocks, flush, stream) if not args.no_variants else None
     serving = run_serving(args, dev) if args.serve_n > 0 else None
     if rank != 0:
         if dist:
@@ -403,12 +405,70 @@ def run_ours(args):
         "cpu_baseline": {"value": cpu_v, "unit": "evals/s", "cores": cores, "kind": "oracle",
                          "sample": f"{cpu_n} of the {n} mocks ({cpu_dt:.1f} s): FP64 oracle forward + autograd gradient"},
         "clocks": {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
+        "variants": variants,
         "serving": serving,
     }
     print(json.dumps(line), flush=True)
     if dist:
         tdist.destroy_process_group()
     return 0
+
+
+# the NEXT variants of the hot path on the same mocks: the kernels each one adds or
+# swaps, and its whole-step throughput
+VARIANT_KERNELS = ("k_select_fit", "k_lin_sort", "k_render", "k_render_edge", "k_render_adj", "k_cdf_adj",
+                   "k_centre_adj", "k_sel_adj", "k_lin_centre_adj", "k_light_adj")
+
+
+def run_variants(args, dev, mocks, flush, stream):
+    from paper_2606_30620_b300 import inputs as I
+    from paper_2606_30620_b300 import rtu
+    specs = [("uniform_grid", "box around the masked rays (Sec. 2.1)",
+              lambda m: m, rtu.RTU_TRANSFORM_UNIFORM),
+             ("weighted_grid", "integer SNR weights, cap 100 (Sec. 5)",
+              lambda m: I.with_snr_weights(copy.copy(m)), rtu.RTU_TRANSFORM_RTU),
+             ("lens_light", "5-component MGE lens light (App. A.3)",
+              lambda m: I.with_light(copy.copy(m), n=5, seed=3, amp=0.3), rtu.RTU_TRANSFORM_RTU),
+             ("linear_ecdf", "unsmoothed linear-interpolated eCDF (App. C)",
+              lambda m: m, rtu.RTU_TRANSFORM_LINEAR)]
+    out = {}
+    k_steps = max(1, min(args.steps, 100))
+    for name, what, make, transform in specs:
+        ms_ = [make(m) for m in mocks]
+        systems = [rtu.System.from_mock(m, precision=rtu.RTU_F32, device=dev, transform=transform) for m in ms_]
+        batch = rtu.Batch([rtu.Binding(s, m.lens, m.latents, m.ps, light=getattr(m, "light", None))
+                           for s, m in zip(systems, ms_)])
+
+        def step():
+            batch.forward(stream)
+            batch.adjoint(stream)
+
+        for _ in range(3):
+            step()
+        torch.cuda.synchronize()
+        ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(k_steps)]
+        ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(k_steps)]
+        for i in range(k_steps):
+            flush.fill_(float(i))
+            ev0[i].record(stream)
+            step()
+            ev1[i].record(stream)
+        torch.cuda.synchronize()
+        ms = statistics.mean(a.elapsed_time(b) for a, b in zip(ev0, ev1))
+        rtu.profile_report()
+        rtu.profile_enable(True)
+        n_prof = min(k_steps, 20)
+        for i in range(n_prof):
+            flush.fill_(float(i))
+            step()
+        torch.cuda.synchronize()
+        rtu.profile_enable(False)
+        kern = rtu.profile_report()
+        out[name] = {"what": what, "value": len(mocks) / (ms / 1e3), "unit": "evals/s", "ms_per_step": ms,
+                     "steps": k_steps,
+                     "kernels_ms": {k: kern[k][1] / n_prof for k in VARIANT_KERNELS if k in kern}}
+        del batch, systems
+    return out
 
 
 def run_serving(args, dev):
@@ -446,6 +506,7 @@ def main():
     ap.add_argument("--no-single", action="store_true", help="skip the per-system comparison path")
     ap.add_argument("--no-graph", action="store_true", help="skip the CUDA-graph replay timing")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-variants", action="store_true", help="skip the timing of the grid / light variants")
     ap.add_argument("--serve-n", type=int, default=4096, help="systems in the serving stream (0 = skip)")
     args = ap.parse_args()
     if args.impl == "reference":
