@@ -6,6 +6,7 @@
 #pragma once
 #include "rtu_internal.cuh"
 #include "k_grid.cuh"
+#include "k_gp.cuh"
 
 namespace rtu {
 
@@ -363,28 +364,65 @@ __global__ void __launch_bounds__(CTA_C) k_lin_centre_adj(const __grid_constant_
         for (int p = threadIdx.x; p < nl; p += CTA_C) E.cadj[(size_t)E.n_cta_c * nl + p] = 0.0;
 }
 
-// g_lens = (render-adjoint lens sums) + (centre-adjoint lens sums), fixed order
-__global__ void __launch_bounds__(64) k_grad_final(const __grid_constant__ Batch B) {
+// g_lens = (render-adjoint lens sums) + (centre-adjoint lens sums), one warp per
+// parameter (lane-strided rows, fixed shuffle tree); lens-light moments likewise
+constexpr int GRAD_NT = 256;
+__global__ void __launch_bounds__(GRAD_NT) k_grad_final(const __grid_constant__ Batch B) {
     const EvalArgs& E = B.e[blockIdx.x];
     const int K = E.n_nodes + 2;
     const int nsub = E.sub_kind ? E.n_sub : 0;
     const int nacc = NACC_FIX + 4 * K + 5 * nsub;
     const int nl = 8 + 5 * nsub;
-    for (int p = threadIdx.x; p < nl; p += blockDim.x) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    constexpr int NW = GRAD_NT / 32;
+    for (int p = wid; p < nl; p += NW) {
         const int col = p < 8 ? p : NACC_FIX + 4 * K + (p - 8);
-        double s = 0.0;
-        for (int t = 0; t < E.n_cta_adj; ++t) s += E.apart[(size_t)t * nacc + col];
-        double c = 0.0;
-        for (int t = 0; t <= E.n_cta_c; ++t) c += E.cadj[(size_t)t * nl + p];   // + the selected-rank row
+        const double s = warp_rows_sum(E.apart + col, E.n_cta_adj, nacc);
+        const double c = warp_rows_sum(E.cadj + p, E.n_cta_c + 1, nl);   // + the selected-rank row
         double g = s + c;
         if (p == 1 && E.profile == 0) g = 0.0;
-        E.g_lens[p] = g;
+        if (lane == 0) E.g_lens[p] = g;
     }
+    // spectrum parameters and alpha_src: the GP adjoint's per-CTA partials
+    {
+        const int nf = E.family == 2 ? 3 : 2;
+        const int ngl = (E.n_src + GP_LINES - 1) / GP_LINES;
+        for (int c = wid; c <= nf; c += NW) {
+            const double v = warp_rows_sum(E.gpart + (c < nf ? c : 3), ngl, 4);
+            if (lane == 0) E.g_ps[c] = v;
+        }
+    }
+    // lens light: per component the moment sums of k_light_adj, then d log L / d (A,
+    // sigma, q, phi, x_n, y_n) with L_n = A/(2 pi) exp(-E), E = (q x'^2 + y'^2/q)/(2
+    // sigma^2), x' = cos phi dx + sin phi dy, y' = cos phi dy - sin phi dx
     const int nlp = E.light ? 6 * E.n_light : 0;
-    for (int p = threadIdx.x; p < nlp; p += blockDim.x) {
-        double g = 0.0;
-        for (int t = 0; t < E.n_cta_r; ++t) g += E.lpartl[(size_t)t * nlp + p];
-        if (E.g_light) E.g_light[p] = g;
+    if (nlp == 0) return;
+    __shared__ double mom[6 * MAX_LIGHT];
+    const int nlc = light_ctas(E.n_img);
+    for (int i = wid; i < nlp; i += NW) {
+        const double v = warp_rows_sum(E.lpartl + i, nlc, nlp);
+        if (lane == 0) mom[i] = v;
+    }
+    __syncthreads();
+    for (int n = threadIdx.x; n < nlp / 6; n += GRAD_NT) {
+        const double* m = mom + 6 * n;
+        const double* p = E.light + 6 * n;
+        const double A = p[0], sg = p[1], q = p[2], cs = cos(p[3]), sn = sin(p[3]);
+        const double c1 = 0.5 / (sg * sg);
+        const double wx = cs * m[1] + sn * m[2], wy = cs * m[2] - sn * m[1];
+        const double wxx = cs * cs * m[3] + 2.0 * cs * sn * m[4] + sn * sn * m[5];
+        const double wyy = sn * sn * m[3] - 2.0 * cs * sn * m[4] + cs * cs * m[5];
+        const double wxy = -cs * sn * m[3] + (cs * cs - sn * sn) * m[4] + cs * sn * m[5];
+        const double wE = c1 * (q * wxx + wyy / q);
+        double g[6];
+        g[0] = m[0] / A;
+        g[1] = 2.0 * wE / sg;
+        g[2] = -c1 * (wxx - wyy / (q * q));
+        g[3] = -2.0 * c1 * (q - 1.0 / q) * wxy;
+        g[4] = 2.0 * c1 * (q * cs * wx - sn / q * wy);
+        g[5] = 2.0 * c1 * (q * sn * wx + cs / q * wy);
+        if (E.g_light)
+            for (int k = 0; k < 6; ++k) E.g_light[6 * n + k] = g[k];
     }
 }
 

@@ -1,7 +1,7 @@
 // k_gp.cuh -- the GP source on the uniform RTU grid (Sec. 2.1, Eq. 1-4) and
-// its adjoint.  One CTA per evaluation runs a mixed-radix (2, 3, 4)
-// decimation-in-time FFT in shared memory over chunks of rows, then chunks of
-// columns, of an n_src x n_src complex buffer that stays in L2.
+// its adjoint: mixed-radix (2, 3, 4) decimation-in-time line FFTs in shared
+// memory, a few lines of one evaluation per CTA, over an n_src x n_src complex
+// buffer that stays in L2 between the passes.
 #pragma once
 #include "rtu_internal.cuh"
 
@@ -214,19 +214,45 @@ __device__ __forceinline__ void gp_setup(const EvalArgs& E, Cx<T>* tw_s, int* re
     __syncthreads();
 }
 
-// S6 spread over many CTAs: the source's 2-D FFTs as four passes of 1-D line
-// FFTs (GP_LINES lines of one evaluation per CTA), computed in double in both
+// S6 spread over many CTAs: the source's 2-D FFTs as passes of 1-D line FFTs
+// (GP_LINES lines of one evaluation per CTA), computed in double in both
 // precisions.  Near f = 0 the softplus turns an absolute error of f into a relative
 // error of s* amplified by 1/s0 = 100, and a float FFT's absolute error (~1e-7 of
 // max |f|) reaches the gradients at their 1e-5 tolerance; one CTA per evaluation
 // in double would leave the FP64 pipe of a single SM doing the whole transform.
 //   pass 0: forward FFT of the rows of w (real) -> W
-//   pass 1: forward FFT of the columns of W, times sqrt(P(k))
-//   pass 2: inverse FFT of the rows
-//   pass 3: inverse FFT of the columns; f = Re / N^2, s* = (phi_sp(f/s0) s0)^alpha
+//   pass 1: forward FFT of the columns of W (kept, in the storage type, for the
+//           adjoint's spectrum gradient), times sqrt(P(k)), inverse FFT of the columns
+//   pass 2: inverse FFT of the rows; f = Re / N^2, s* = (phi_sp(f/s0) s0)^alpha
 // W (complex double, row-major) stays in the workspace between the passes (L2).
 constexpr int GP_LINES = 8;
 constexpr int GP_LINE_NT = 256;
+constexpr int GP_PASSES = 3;
+constexpr int GP_PER_T = GP_LINES * 256 / GP_LINE_NT;   // line elements per thread, at most
+
+// line q of the CTA's buffer from natural order into the digit-reversed order the
+// DIT butterflies take (through registers: every thread reads, then writes)
+// (called by all GP_LINE_NT threads of the CTA)
+template <typename T>
+__device__ __forceinline__ void lines_to_digit_reversed(Cx<T>* sm, int cnt, int n, const int* rev_s) {
+    Cx<T> v[GP_PER_T];
+#pragma unroll
+    for (int k = 0; k < GP_PER_T; ++k) {
+        const int i = threadIdx.x + k * GP_LINE_NT;
+        if (i < cnt * n) {
+            const int q = i / n, p = i - q * n;
+            v[k] = sm[q * n + rev_s[p]];
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < GP_PER_T; ++k) {
+        const int i = threadIdx.x + k * GP_LINE_NT;
+        if (i < cnt * n) sm[i] = v[k];
+    }
+    __syncthreads();
+}
+
 template <typename TS>
 __global__ void __launch_bounds__(GP_LINE_NT) k_gp_lines(const __grid_constant__ Batch B, int pass) {
     typedef double T;
@@ -239,7 +265,7 @@ __global__ void __launch_bounds__(GP_LINE_NT) k_gp_lines(const __grid_constant__
     __shared__ int rev_s[256];
     __shared__ int rad_s[MAX_RADIX];
     gp_setup<T>(E, tw_s, rev_s, rad_s);
-    const bool cols = pass & 1, inv = pass >= 2;
+    const bool cols = pass == 1;
     const int l0 = tile * GP_LINES, cnt = min(GP_LINES, n - l0);
     if (cnt <= 0) return;
     Cx<T>* W = reinterpret_cast<Cx<T>*>(E.cbufA);
@@ -256,8 +282,8 @@ __global__ void __launch_bounds__(GP_LINE_NT) k_gp_lines(const __grid_constant__
         }
     }
     __syncthreads();
-    fft_seq_smem<T>(sm, cnt, n, rad_s, E.nrad, tw_s, inv);
-    if (pass == 0 || pass == 2) {
+    fft_seq_smem<T>(sm, cnt, n, rad_s, E.nrad, tw_s, pass == 2);
+    if (pass == 0) {
         for (int i = threadIdx.x; i < cnt * n; i += blockDim.x) {
             const int q = i / n, p = i - q * n;
             W[(l0 + q) * n + p] = sm[q * n + p];
@@ -265,7 +291,10 @@ __global__ void __launch_bounds__(GP_LINE_NT) k_gp_lines(const __grid_constant__
         return;
     }
     if (pass == 1) {
-        // times sqrt(P(k)) (Eq. 1): column l0 + q is kx, row p is ky
+        // keep F(w) for the adjoint; times sqrt(P(k)) (Eq. 1): column l0 + q is kx,
+        // row p is ky; then the inverse FFT of the same columns
+        typedef typename real2_of<TS>::type C2;
+        C2* Wk = reinterpret_cast<C2*>(E.cbufB);
         const int nf = n_family(E.family);
         T psv[4], pc[1];
         for (int q = 0; q < nf; ++q) psv[q] = E.ps[q];
@@ -277,11 +306,22 @@ __global__ void __launch_bounds__(GP_LINE_NT) k_gp_lines(const __grid_constant__
             const T k = kscale * sqrt(fx * fx + fy * fy);
             const T sp = sqrtP_only<T>(E.family, psv, pc, k);
             const Cx<T> v = sm[q * n + p];
-            W[p * n + l0 + q] = Cx<T>{v.x * sp, v.y * sp};
+            C2 wv;
+            wv.x = (TS)v.x;
+            wv.y = (TS)v.y;
+            Wk[p * n + l0 + q] = wv;
+            sm[q * n + p] = Cx<T>{v.x * sp, v.y * sp};
+        }
+        __syncthreads();
+        lines_to_digit_reversed<T>(sm, cnt, n, rev_s);
+        fft_seq_smem<T>(sm, cnt, n, rad_s, E.nrad, tw_s, true);
+        for (int i = threadIdx.x; i < cnt * n; i += blockDim.x) {
+            const int p = i / cnt, q = i - p * cnt;
+            W[p * n + l0 + q] = sm[q * n + p];
         }
         return;
     }
-    // pass 3: the field and the source brightness (the map in the storage type: f is
+    // pass 2: the field and the source brightness (the map in the storage type: f is
     // already accurate, and the softplus of an accurately rounded argument is too)
     const int nf = n_family(E.family);
     const TS alpha = (TS)E.ps[nf];
@@ -290,88 +330,126 @@ __global__ void __launch_bounds__(GP_LINE_NT) k_gp_lines(const __grid_constant__
     TS* src = reinterpret_cast<TS*>(E.src);
     TS* so = reinterpret_cast<TS*>(E.source_out);
     for (int i = threadIdx.x; i < cnt * n; i += blockDim.x) {
-        const int p = i / cnt, q = i - p * cnt;
+        const int q = i / n, p = i - q * n;
         const T f = sm[q * n + p].x * inv_n2;
         const TS fs = (TS)f;
         const TS sv = r_exp(alpha * log_sp_s0<TS>((TS)(f / 0.01)));
-        const int at = p * n + l0 + q;
+        const int at = (l0 + q) * n + p;
         fld[at] = fs;
         src[at] = sv;
         if (so) so[at] = sv;
     }
 }
 
-// S9 (source part): node gradients from the per-cell bilinear corner sums,
-// back through the softplus/alpha map and the FFT filter (self-adjoint) to the
-// latents; d log L / d sqrt(P_k) = Re(W_k conj(G_k)) / N^2 to the spectrum
-// parameters; d s*/d alpha to alpha_src.
+// S9 (source part) as line passes over many CTAs, in the kernel's type: node
+// gradients from the per-cell bilinear corner sums, back through the softplus /
+// alpha map and the FFT filter (self-adjoint) to the latents;
+// d log L / d sqrt(P_k) = Re(F(w)_k conj(G_k)) / N^2 to the spectrum parameters with
+// F(w) kept by the forward; d s*/d alpha to alpha_src.  Per-CTA partial sums in
+// gpart[tile][0..2] (spectrum) and [3] (alpha_src), summed by k_grad_final.
+//   pass 0: G = g ds*/df row by row, forward FFT of the rows
+//   pass 1: forward FFT of the columns, the spectrum sums, times sqrt(P(k)),
+//           inverse FFT of the columns
+//   pass 2: inverse FFT of the rows; d log L / d w = Re / N^2
 template <typename T>
-__global__ void __launch_bounds__(GP_NT) k_gp_adjoint(const __grid_constant__ Batch B) {
-    const EvalArgs& E = B.e[blockIdx.x];
-    const int n = E.n_src, n2 = n * n, nc = n - 1;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    Cx<T>* sm = reinterpret_cast<Cx<T>*>(smem_raw);
+__global__ void __launch_bounds__(GP_LINE_NT) k_gp_adj_lines(const __grid_constant__ Batch B, int pass) {
+    const int ev = find_eval(B, blockIdx.x);
+    const EvalArgs& E = B.e[ev];
+    const int tile = blockIdx.x - B.tile0[ev];
+    const int n = E.n_src, nc = n - 1;
+    __shared__ Cx<T> sm[GP_LINES * 256];
     __shared__ Cx<T> tw_s[256];
     __shared__ int rev_s[256];
     __shared__ int rad_s[MAX_RADIX];
-    __shared__ double red[GP_NT / 32];
+    __shared__ double red[GP_LINE_NT / 32];
     gp_setup<T>(E, tw_s, rev_s, rad_s);
-    const int chunk = max(1, min(n, (int)(GP_SMEM / sizeof(Cx<T>)) / n));
+    const int l0 = tile * GP_LINES, cnt = min(GP_LINES, n - l0);
+    if (cnt <= 0) return;
     Cx<T>* G = reinterpret_cast<Cx<T>*>(E.cbufA);
-    Cx<T>* W = reinterpret_cast<Cx<T>*>(E.cbufB);
-    const T* w = reinterpret_cast<const T*>(E.latents);
-    const T* fld = reinterpret_cast<const T*>(E.fld);
-    const T* src = reinterpret_cast<const T*>(E.src);
     const int nf = n_family(E.family);
-    const T alpha = (T)E.ps[nf];
-    T ga_t = T(0);
-    for (int i = threadIdx.x; i < n2; i += blockDim.x) {
-        const int j = i / n, ii = i - j * n;
+    double* part = E.gpart + (size_t)tile * 4;
+    if (pass == 0) {
         typedef typename real2_of<T>::type TP;
         const TP* cor = reinterpret_cast<const TP*>(E.corner);
-        T g = T(0);
-        if (ii < nc && j < nc) { const TP c = cor[(j * nc + ii) * 4 + 0]; g += c.x + c.y; }
-        if (ii > 0 && j < nc) { const TP c = cor[(j * nc + ii - 1) * 4 + 1]; g += c.x + c.y; }
-        if (ii < nc && j > 0) { const TP c = cor[((j - 1) * nc + ii) * 4 + 2]; g += c.x + c.y; }
-        if (ii > 0 && j > 0) { const TP c = cor[((j - 1) * nc + ii - 1) * 4 + 3]; g += c.x + c.y; }
-        const T s = src[i];
-        const T x = fld[i] / T(0.01);
-        // d s / d f = alpha s (sigma(x)/phi_sp(x)) / s0
-        const T dsdf = alpha * s * sig_over_sp<T>(x) / T(0.01);
-        G[i] = Cx<T>{g * dsdf, T(0)};
-        W[i] = Cx<T>{w[i], T(0)};
-        if (s > T(0)) ga_t += g * s * log_sp_s0<T>(x);
+        const T* fld = reinterpret_cast<const T*>(E.fld);
+        const T* src = reinterpret_cast<const T*>(E.src);
+        const T alpha = (T)E.ps[nf];
+        T ga_t = T(0);
+        for (int i = threadIdx.x; i < cnt * n; i += blockDim.x) {
+            const int q = i / n, p = i - q * n;
+            const int j = l0 + q, ii = rev_s[p];       // digit-reversed load of row j
+            T g = T(0);
+            if (ii < nc && j < nc) { const TP c = cor[(j * nc + ii) * 4 + 0]; g += c.x + c.y; }
+            if (ii > 0 && j < nc) { const TP c = cor[(j * nc + ii - 1) * 4 + 1]; g += c.x + c.y; }
+            if (ii < nc && j > 0) { const TP c = cor[((j - 1) * nc + ii) * 4 + 2]; g += c.x + c.y; }
+            if (ii > 0 && j > 0) { const TP c = cor[((j - 1) * nc + ii - 1) * 4 + 3]; g += c.x + c.y; }
+            const int at = j * n + ii;
+            const T s = src[at];
+            const T x = fld[at] / T(0.01);
+            // d s / d f = alpha s (sigma(x)/phi_sp(x)) / s0
+            const T dsdf = alpha * s * sig_over_sp<T>(x) / T(0.01);
+            sm[q * n + p] = Cx<T>{g * dsdf, T(0)};
+            if (s > T(0)) ga_t += g * s * log_sp_s0<T>(x);
+        }
+        const double ga = block_sum_t<GP_LINE_NT>(ga_t, red);
+        if (threadIdx.x == 0) part[3] = ga;
+        fft_seq_smem<T>(sm, cnt, n, rad_s, E.nrad, tw_s, false);
+        for (int i = threadIdx.x; i < cnt * n; i += blockDim.x) {
+            const int q = i / n, p = i - q * n;
+            G[(l0 + q) * n + p] = sm[q * n + p];
+        }
+        return;
     }
-    const double ga = block_sum_t<GP_NT>(ga_t, red);
-    __syncthreads();
-    fft2<T>(G, n, rad_s, E.nrad, tw_s, rev_s, sm, chunk, false);
-    fft2<T>(W, n, rad_s, E.nrad, tw_s, rev_s, sm, chunk, false);
-    T psv[4];
-    for (int q = 0; q < nf; ++q) psv[q] = (T)E.ps[q];
-    const T kscale = (T)(2.0 * 3.14159265358979323846 / E.pitch);
-    const T inv_n2s = T(1) / T(n2);
-    T gp[3] = {T(0), T(0), T(0)};
-    for (int i = threadIdx.x; i < n2; i += blockDim.x) {
-        const int ky = i / n, kx = i - ky * n;
-        const T fx = fftfreq<T>(kx, n), fy = fftfreq<T>(ky, n);
-        const T k = kscale * r_sqrt(fx * fx + fy * fy);
-        T dsp[3] = {T(0), T(0), T(0)};
-        const T sp = sqrtP_and_grad<T>(E.family, psv, k, dsp);
-        const Cx<T> Gk = G[i], Wk = W[i];
-        const T d = (Wk.x * Gk.x + Wk.y * Gk.y) * inv_n2s;
-        for (int q = 0; q < nf; ++q) gp[q] += d * dsp[q];
-        G[i] = Cx<T>{Gk.x * sp, Gk.y * sp};
+    if (pass == 1) {
+        for (int i = threadIdx.x; i < cnt * n; i += blockDim.x) {
+            const int p = i / cnt, q = i - p * cnt;
+            sm[q * n + p] = G[rev_s[p] * n + l0 + q];
+        }
+        __syncthreads();
+        fft_seq_smem<T>(sm, cnt, n, rad_s, E.nrad, tw_s, false);
+        typedef typename real2_of<T>::type C2;
+        const C2* Wk = reinterpret_cast<const C2*>(E.cbufB);
+        T psv[4];
+        for (int q = 0; q < nf; ++q) psv[q] = (T)E.ps[q];
+        const T kscale = (T)(2.0 * 3.14159265358979323846 / E.pitch);
+        const T inv_n2s = T(1) / T(n * n);
+        T gp[3] = {T(0), T(0), T(0)};
+        for (int i = threadIdx.x; i < cnt * n; i += blockDim.x) {
+            const int p = i / cnt, q = i - p * cnt;
+            const T fx = fftfreq<T>(l0 + q, n), fy = fftfreq<T>(p, n);
+            const T k = kscale * r_sqrt(fx * fx + fy * fy);
+            T dsp[3] = {T(0), T(0), T(0)};
+            const T sp = sqrtP_and_grad<T>(E.family, psv, k, dsp);
+            const Cx<T> Gk = sm[q * n + p];
+            const C2 W = Wk[p * n + l0 + q];
+            const T d = (W.x * Gk.x + W.y * Gk.y) * inv_n2s;
+            for (int c = 0; c < nf; ++c) gp[c] += d * dsp[c];
+            sm[q * n + p] = Cx<T>{Gk.x * sp, Gk.y * sp};
+        }
+        for (int c = 0; c < 3; ++c) {
+            const double v = block_sum_t<GP_LINE_NT>(gp[c], red);
+            if (threadIdx.x == 0) part[c] = c < nf ? v : 0.0;
+        }
+        lines_to_digit_reversed<T>(sm, cnt, n, rev_s);
+        fft_seq_smem<T>(sm, cnt, n, rad_s, E.nrad, tw_s, true);
+        for (int i = threadIdx.x; i < cnt * n; i += blockDim.x) {
+            const int p = i / cnt, q = i - p * cnt;
+            G[p * n + l0 + q] = sm[q * n + p];
+        }
+        return;
     }
-    double gpd[3] = {0.0, 0.0, 0.0};
-    for (int q = 0; q < nf; ++q) gpd[q] = block_sum_t<GP_NT>(gp[q], red);
+    // pass 2
+    for (int i = threadIdx.x; i < cnt * n; i += blockDim.x) {
+        const int q = i / n, p = i - q * n;
+        sm[q * n + p] = G[(l0 + q) * n + rev_s[p]];
+    }
     __syncthreads();
-    fft2<T>(G, n, rad_s, E.nrad, tw_s, rev_s, sm, chunk, true);
+    fft_seq_smem<T>(sm, cnt, n, rad_s, E.nrad, tw_s, true);
     T* gl = reinterpret_cast<T*>(E.g_lat);
-    const T inv_n2 = T(1) / T(n2);
-    for (int i = threadIdx.x; i < n2; i += blockDim.x) gl[i] = G[i].x * inv_n2;
-    if (threadIdx.x == 0) {
-        for (int q = 0; q < nf; ++q) E.g_ps[q] = gpd[q];
-        E.g_ps[nf] = ga;
+    const T inv_n2 = T(1) / T(n * n);
+    for (int i = threadIdx.x; i < cnt * n; i += blockDim.x) {
+        const int q = i / n, p = i - q * n;
+        gl[(l0 + q) * n + p] = sm[q * n + p].x * inv_n2;
     }
 }
 

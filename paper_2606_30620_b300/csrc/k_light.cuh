@@ -1,16 +1,18 @@
-// k_light.cuh -- adjoint of the MGE lens light (App. A.3): d log L / d (A, sigma,
-// q, phi, x_n, y_n) of every component, one thread per image pixel over its
-// sub-rays (the forward adds the light inside the render kernel), fixed-order sums.
+// k_light.cuh -- adjoint of the MGE lens light (App. A.3).  The forward adds the
+// light inside the render kernel; here every component's six weighted moments of
+// its sub-ray offsets (dx, dy) from the centre are summed,
+//   M = sum w, (sum w dx, sum w dy), (sum w dx^2, sum w dx dy, sum w dy^2),
+//   w = (d log L / d image) / s^2 * L_n(sub-ray),
+// and k_grad_final maps them to d log L / d (A, sigma, q, phi, x_n, y_n): every
+// partial of L_n is L_n times a polynomial of degree <= 2 in (dx, dy).
 #pragma once
 #include "rtu_internal.cuh"
 
 namespace rtu {
 
-// L = A/(2 pi) exp(-E), E = (q x'^2 + y'^2/q)/(2 sigma^2):
-//   dL/dA = L/A,  dL/dsigma = 2 E L/sigma,  dL/dq = -L (x'^2 - y'^2/q^2)/(2 sigma^2),
-//   dL/dphi = -L x' y' (q - 1/q)/sigma^2,
-//   dL/dx_n = L (q x' cos phi - y' sin phi / q)/sigma^2,
-//   dL/dy_n = L (q x' sin phi + y' cos phi / q)/sigma^2
+// One thread per LIGHT_PPT pixels (CTA_R apart: coalesced), components one after
+// the other; per pixel the s^2 sub-rays are summed in T, then added to compensated
+// (hi, lo) accumulators, then fixed-order warp and CTA sums.
 template <typename T>
 __global__ void __launch_bounds__(CTA_R) k_light_adj(const __grid_constant__ Batch B) {
     typedef typename real2_of<T>::type TP;
@@ -19,56 +21,60 @@ __global__ void __launch_bounds__(CTA_R) k_light_adj(const __grid_constant__ Bat
     const int tile = blockIdx.x - B.tile0[ev];
     __shared__ LightK<T> L;
     __shared__ PixGeom<T> G;
-    __shared__ TP wred[CTA_R / 32][6 * MAX_LIGHT];
+    __shared__ TP wred[CTA_R / 32][6];
+    __shared__ UDiv dv_n;
     light_setup<T>(L, E.light, E.n_light);
     pixgeom_setup<T>(G, E.pix, E.n_img, E.s);
+    if (threadIdx.x == 0) dv_n = udiv_make((uint32_t)E.n_img);
     __syncthreads();
     const int nl = L.n;
-    if (nl == 0) return;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int s = E.s, s2 = s * s;
-    bool valid;
-    const int pixel = render_pixel(E.n_img, tile, threadIdx.x, valid);
-    T acc[6 * MAX_LIGHT];
+    const int s = E.s, s2 = s * s, npix = E.n_img * E.n_img;
+    const T inv_s2 = T(1) / T(s2);
+    const T* gimg = reinterpret_cast<const T*>(E.gimg);
+    for (int n = 0; n < nl; ++n) {
+        const T xn = L.xn[n], yn = L.yn[n], a = L.e2a[n], b = L.e2b[n], c = L.e2c[n], amp = L.amp[n];
+        TP acc[6];
 #pragma unroll
-    for (int k = 0; k < 6 * MAX_LIGHT; ++k) acc[k] = T(0);
-    if (valid) {
-        const T g = reinterpret_cast<const T*>(E.gimg)[pixel] / T(s2);
-        const int pj = pixel / E.n_img, pi = pixel - pj * E.n_img;
-        for (int q = 0; q < s2; ++q) {
-            const T x = ray_coord(G, pi, q % s), y = ray_coord(G, pj, q / s);
-#pragma unroll
-            for (int n = 0; n < MAX_LIGHT; ++n) {
-                if (n < nl) {
-                    const T* c = L.c[n];
-                    const T dx = x - c[6], dy = y - c[7];
-                    const T xp = c[4] * dx + c[5] * dy, yp = c[4] * dy - c[5] * dx;
-                    const T Ex = c[1] * (c[2] * xp * xp + c[3] * yp * yp);
-                    const T gl = g * c[0] * r_exp(-Ex);          // g L
-                    const T k2 = T(2) * c[1];                     // 1/sigma^2
-                    acc[6 * n + 0] += gl * c[8];
-                    acc[6 * n + 1] += gl * T(2) * Ex * c[9];
-                    acc[6 * n + 2] -= gl * c[1] * (xp * xp - yp * yp * c[3] * c[3]);
-                    acc[6 * n + 3] -= gl * k2 * xp * yp * (c[2] - c[3]);
-                    acc[6 * n + 4] += gl * k2 * (c[2] * xp * c[4] - yp * c[5] * c[3]);
-                    acc[6 * n + 5] += gl * k2 * (c[2] * xp * c[5] + yp * c[4] * c[3]);
+        for (int k = 0; k < 6; ++k) { acc[k].x = T(0); acc[k].y = T(0); }
+        for (int r = 0; r < LIGHT_PPT; ++r) {
+            const int pixel = (tile * LIGHT_PPT + r) * CTA_R + threadIdx.x;
+            if (pixel >= npix) break;
+            const T g = gimg[pixel] * inv_s2;
+            const int pj = (int)udiv((uint32_t)pixel, dv_n), pi = pixel - pj * E.n_img;
+            T m[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+            for (int qb = 0; qb < s; ++qb) {
+                const T dy = ray_coord(G, pj, qb) - yn;
+                for (int qa = 0; qa < s; ++qa) {
+                    const T dx = ray_coord(G, pi, qa) - xn;
+                    const T e = dx * (a * dx + b * dy) + c * dy * dy;
+                    const T w = amp * r_exp2(-e);
+                    const T wx = w * dx;
+                    m[0] += w;
+                    m[1] += wx;
+                    m[2] += w * dy;
+                    m[3] += wx * dx;
+                    m[4] += wx * dy;
+                    m[5] += w * dy * dy;
                 }
             }
-        }
-    }
 #pragma unroll
-    for (int k = 0; k < 6 * MAX_LIGHT; ++k) {
-        if (k < 6 * nl) {
-            const TP v = warp_pair_sum(acc[k]);
+            for (int k = 0; k < 6; ++k) pair_add(acc[k], g * m[k]);
+        }
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            TP v = warp_pair_sum(acc[k].x);
+            pair_add(v, warp_pair_sum(acc[k].y));
             if (lane == 0) wred[wid][k] = v;
         }
-    }
-    __syncthreads();
-    for (int k = threadIdx.x; k < 6 * nl; k += blockDim.x) {
-        TP r;
-        r.x = T(0); r.y = T(0);
-        for (int w = 0; w < CTA_R / 32; ++w) pair_add(r, wred[w][k]);
-        E.lpartl[(size_t)tile * 6 * nl + k] = (double)r.x + (double)r.y;
+        __syncthreads();
+        if (threadIdx.x < 6) {
+            TP r;
+            r.x = T(0); r.y = T(0);
+            for (int w = 0; w < CTA_R / 32; ++w) pair_add(r, wred[w][threadIdx.x]);
+            E.lpartl[(size_t)tile * 6 * nl + 6 * n + threadIdx.x] = (double)r.x + (double)r.y;
+        }
+        __syncthreads();
     }
 }
 

@@ -232,15 +232,21 @@ __global__ void __launch_bounds__(256) k_like_final(const __grid_constant__ Batc
     for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, o);
     if ((threadIdx.x & 31) == 0) red_i[threadIdx.x >> 5] = cnt;
     __syncthreads();
+    // the per-tile sums of r^2 (all pixels) and of r^2 in the mask: warps 0 and 1,
+    // lane-strided, fixed tree
+    __shared__ double sums[2];
+    if (threadIdx.x < 64) {
+        const double v = warp_rows_sum(E.lpart + (threadIdx.x >> 5), E.n_cta_p, 2);
+        if ((threadIdx.x & 31) == 0) sums[threadIdx.x >> 5] = v;
+    }
+    __syncthreads();
     if (threadIdx.x == 0 && E.stats) {
         int tot = 0;
         for (int w = 0; w < 256 / 32; ++w) tot += red_i[w];
         E.stats[4] = tot;
-        double s = 0.0, sm = 0.0;
-        for (int t = 0; t < E.n_cta_p; ++t) { s += E.lpart[2 * t]; sm += E.lpart[2 * t + 1]; }
         const double npx = (double)E.n_img * E.n_img;
-        E.stats[0] = -0.5 * s - npx * log(E.sigma * sqrt(2.0 * 3.14159265358979323846));
-        E.stats[1] = sm / (E.n_mask > 0 ? E.n_mask : 1);
+        E.stats[0] = -0.5 * sums[0] - npx * log(E.sigma * sqrt(2.0 * 3.14159265358979323846));
+        E.stats[1] = sums[1] / (E.n_mask > 0 ? E.n_mask : 1);
         E.stats[2] = E.n_mask;
         E.stats[3] = (double)(*E.flags);
     }

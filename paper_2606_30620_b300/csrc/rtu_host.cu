@@ -118,6 +118,7 @@ size_t slot_layout(const rtu_system_desc& d, char* base, EvalArgs* e) {
     const size_t n2 = (size_t)d.n_src * d.n_src;
     p = take(n2 * 2 * 8);                             if (e) e->cbufA = p;     // complex double (the GP source)
     p = take(n2 * 2 * z.tb);                          if (e) e->cbufB = p;
+    p = take((size_t)(d.n_src + GP_LINES - 1) / GP_LINES * 4 * 8); if (e) e->gpart = (double*)p;
     p = take(n2 * z.tb);                              if (e) e->fld = p;
     p = take(n2 * z.tb);                              if (e) e->src = p;
     const size_t ni = (size_t)d.n_img * d.n_img;
@@ -141,7 +142,7 @@ size_t slot_layout(const rtu_system_desc& d, char* base, EvalArgs* e) {
     p = take((size_t)z.n_rays * 4);                   if (e) e->kray = (int*)p;
     p = take((size_t)z.n_rays * 4);                   if (e) e->kcell = (int*)p;
     p = take((size_t)z.n_rays * 2 * z.tb);            if (e) e->gbuf = p;
-    p = take((size_t)z.n_cta_r * 6 * std::max(1, d.n_light) * 8); if (e) e->lpartl = (double*)p;
+    p = take((size_t)light_ctas(d.n_img) * 6 * std::max(1, d.n_light) * 8); if (e) e->lpartl = (double*)p;
     if (d.transform == RTU_TRANSFORM_LINEAR) {
         // the unsmoothed eCDF: every order statistic and its gradient
         p = take((size_t)2 * z.nm_max * 8);           if (e) e->lkey = (double*)p;
@@ -271,8 +272,6 @@ constexpr int MAX_DYN = 200 * 1024;
 
 void set_attributes() {
     cudaFuncSetAttribute(k_select_fit, cudaFuncAttributeMaxDynamicSharedMemorySize, SEL_SMEM);
-    cudaFuncSetAttribute(k_gp_adjoint<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, GP_SMEM);
-    cudaFuncSetAttribute(k_gp_adjoint<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, GP_SMEM);
     cudaFuncSetAttribute(k_render<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN);
     cudaFuncSetAttribute(k_render<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN);
     cudaFuncSetAttribute(k_render<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN);
@@ -511,6 +510,7 @@ int t_two_lin(const EvalArgs& e) { return is_lin(e) ? 2 : 0; }
 int t_one_fit(const EvalArgs& e) { return is_lin(e) ? 0 : 1; }
 int t_centre_fit(const EvalArgs& e) { return is_lin(e) ? 0 : e.n_cta_c; }
 int t_centre_lin(const EvalArgs& e) { return is_lin(e) ? e.n_cta_c : 0; }
+int t_light(const EvalArgs& e) { return e.light && e.n_light > 0 ? light_ctas(e.n_img) : 0; }
 int t_render_fit(const EvalArgs& e) { return is_lin(e) ? 0 : e.n_cta_r; }
 int t_render_lin(const EvalArgs& e) { return is_lin(e) ? e.n_cta_r : 0; }
 int t_adj_fit(const EvalArgs& e) { return is_lin(e) ? 0 : e.n_cta_adj; }
@@ -518,7 +518,6 @@ int t_adj_lin(const EvalArgs& e) { return is_lin(e) ? e.n_cta_adj : 0; }
 int t_gp_lines(const EvalArgs& e) { return (e.n_src + GP_LINES - 1) / GP_LINES; }
 int t_zero(const EvalArgs&) { return ZERO_TILES; }
 int t_centre(const EvalArgs& e) { return e.n_cta_c; }
-int t_render(const EvalArgs& e) { return e.n_cta_r; }
 int t_adj(const EvalArgs& e) { return e.n_cta_adj; }
 int t_psf(const EvalArgs& e) { return e.n_cta_p; }
 int t_edge(const EvalArgs&) { return EDGE_CTAS; }
@@ -584,7 +583,7 @@ rtu_status run_chunk(Batch& B, int phase, cudaStream_t st, const SideStream& ss)
     if (phase & PH_FORWARD) {
         // S6 only needs the latents and spectrum parameters: beside S1-S5
         if ((r = stream_after(ss.s, st, ss.fork))) return r;
-        for (int pass = 0; pass < 4; ++pass)
+        for (int pass = 0; pass < GP_PASSES; ++pass)
             if ((r = launch("k_gp_source", k_gp_lines<T>, B, t_gp_lines, GP_LINE_NT, 0, ss.s, pass))) return r;
     }
     if (phase & (PH_GRID | PH_FORWARD)) {
@@ -616,7 +615,7 @@ rtu_status run_chunk(Batch& B, int phase, cudaStream_t st, const SideStream& ss)
         else if (sizeof(T) == 4 && maxPsf <= 21) r = launch("k_psf_adj", k_psf_adj_t<21>, B, t_psf, PSFT_NT, 0, st);
         else r = launch("k_psf_adj", k_psf_adj<T>, B, t_psf, PSF_NT, 0, st);
         if (r) return r;
-        if (any_light && (r = launch("k_light_adj", k_light_adj<T>, B, t_render, CTA_R, 0, st))) return r;
+        if (any_light && (r = launch("k_light_adj", k_light_adj<T>, B, t_light, CTA_R, 0, st))) return r;
         if ((r = launch("k_scan_cells", k_scan_cells, B, t_one, SCAN_NT, 0, st))) return r;
         const size_t adj = grid_bytes + (size_t)(CTA_R / 32) * 4 * maxK * 2 * sizeof(T);
         if (adj > MAX_DYN) return fail(RTU_E_ARG, "adjoint shared memory exceeds the limit");
@@ -631,9 +630,10 @@ rtu_status run_chunk(Batch& B, int phase, cudaStream_t st, const SideStream& ss)
         if ((r = launch("k_sel_adj", k_sel_adj, B, t_one_fit, SEL_ADJ_NT, 0, ss.s))) return r;
         if ((r = launch("k_lin_centre_adj", k_lin_centre_adj, B, t_centre_lin, CTA_C, 0, ss.s))) return r;
         if ((r = launch("k_cell_gather", k_cell_gather<T>, B, t_cells, GATHER_NT, 0, st))) return r;
-        if ((r = launch("k_gp_adjoint", k_gp_adjoint<T>, B, t_one, GP_NT, GP_SMEM, st))) return r;
+        for (int pass = 0; pass < GP_PASSES; ++pass)
+            if ((r = launch("k_gp_adjoint", k_gp_adj_lines<T>, B, t_gp_lines, GP_LINE_NT, 0, st, pass))) return r;
         if ((r = stream_after(st, ss.s, ss.join))) return r;
-        if ((r = launch("k_grad_final", k_grad_final, B, t_one, 64, 0, st))) return r;
+        if ((r = launch("k_grad_final", k_grad_final, B, t_one, GRAD_NT, 0, st))) return r;
     }
     return RTU_OK;
 }

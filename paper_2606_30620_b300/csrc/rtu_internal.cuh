@@ -72,7 +72,8 @@ struct EvalArgs {
     int* sel_idx;      // [2][2 MAXM] centre-ray index at each selected rank
     double* tadj;      // transform adjoint block
     void* cbufA;       // complex real2 [n_src^2]
-    void* cbufB;       // complex real2 [n_src^2]
+    void* cbufB;       // complex real2 [n_src^2]: F(w), kept by the forward for the adjoint
+    double* gpart;     // [GP line CTAs][4] spectrum (0..2) and alpha_src (3) gradient partials
     void* fld;         // real [n_src^2] GP field f
     void* src;         // real [n_src^2] source brightness s*
     void* img;         // real [n_img^2] unconvolved image
@@ -99,7 +100,7 @@ struct EvalArgs {
     void* gbuf;        // real2 [n_rays] d logL / d beta of each adjoint ray (subhalo pass)
     const double* light;   // [6 n_light] MGE lens light (A, sigma, q, phi, x_n, y_n)
     double* g_light;       // [6 n_light] adjoint out
-    double* lpartl;        // [n_cta_r][6 n_light] per-CTA lens-light gradient partials
+    double* lpartl;        // [light CTAs][6 n_light] per-CTA lens-light moment sums
     int n_cta_adj;     // CTAs of the render adjoint (grid-stride over the compacted rays)
     int pad4_;
     // the unsmoothed eCDF transform (App. C, first paragraph), per axis a at a * n_mask
@@ -232,6 +233,16 @@ __device__ __forceinline__ double block_sum_t(T v, double* sh) {
     return r;
 }
 
+// One warp: the sum of a[t * stride] over t < rows, lanes striding over t, then a
+// fixed shuffle tree; every lane gets lane 0's result (the same bits on every call).
+__device__ __forceinline__ double warp_rows_sum(const double* a, int rows, size_t stride) {
+    const int lane = threadIdx.x & 31;
+    double s = 0.0;
+    for (int t = lane; t < rows; t += 32) s += a[(size_t)t * stride];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    return __shfl_sync(0xffffffffu, s, 0);
+}
+
 template <typename T> struct real2_of;
 template <> struct real2_of<float> { typedef float2 type; };
 template <> struct real2_of<double> { typedef double2 type; };
@@ -318,19 +329,15 @@ __device__ inline void lens_setup_par(LensK<double>* Kd, LensK<float>* Kf, const
         const double p[6] = {lens[0], lens[1], lens[2], lens[3], lens[4], lens[5]};
         const double tol = dbl ? 1e-16 : 2e-8;
         // scalars through the shared definition, then the coefficient tables
-        double a = 1.0, D = 0.0;
+        double A = 1.0, D = 0.0;
         int nt = EPL_MAXT;
+        if (dbl) epl_term0(Kd->C.term[0]); else epl_term0(Kf->C.term[0]);
         for (int n = 1; n <= EPL_MAXT; ++n) {
-            a *= sc[n - 1];
             D += sdl[n - 1];
-            if (dbl) {
-                EplTerm<double>& tm = Kd->C.term[n - 1];
-                tm.c = sc[n - 1]; tm.ng = n * sg[n - 1]; tm.D = D; tm.pad_ = 0.0;
-            } else {
-                EplTerm<float>& tm = Kf->C.term[n - 1];
-                tm.c = (float)sc[n - 1]; tm.ng = (float)(n * sg[n - 1]); tm.D = (float)D; tm.pad_ = 0.0f;
-            }
-            if (fabs(a) <= tol) { nt = n; break; }
+            if (dbl) epl_term(Kd->C.term[n], n, A, sc[n - 1], sg[n - 1], D);
+            else epl_term(Kf->C.term[n], n, A, sc[n - 1], sg[n - 1], D);
+            A *= sc[n - 1];
+            if (fabs(A) <= tol) { nt = n; break; }
         }
         if (dbl) {
             epl_scalars(Kd->C, p, profile == 1);
@@ -428,11 +435,11 @@ __device__ __forceinline__ void sub_vjp(const LensK<T>& K, int h, T x, T y, T gb
 // path serves only lenses without them), converted by the CTA's threads.
 __device__ inline void lensk_to_df(const LensK<double>& a, LensK<DF>& b) {
     const int nt = a.C.nterm;
-    for (int i = threadIdx.x; i < nt; i += blockDim.x) {
-        b.C.term[i].c = DF(a.C.term[i].c);
-        b.C.term[i].ng = DF(a.C.term[i].ng);
-        b.C.term[i].D = DF(a.C.term[i].D);
-        b.C.term[i].pad_ = DF(0.0f);
+    for (int i = threadIdx.x; i <= nt; i += blockDim.x) {
+        b.C.term[i].a = DF(a.C.term[i].a);
+        b.C.term[i].h = DF(a.C.term[i].h);
+        b.C.term[i].u = DF(a.C.term[i].u);
+        b.C.term[i].f = DF(a.C.term[i].f);
     }
     if (threadIdx.x == 0) {
         const EplC<double>& c = a.C;
@@ -473,7 +480,12 @@ __device__ __forceinline__ const void* lensk_src(const void* base) {
 constexpr int MAX_LIGHT = RTU_MAX_LIGHT;
 template <typename T>
 struct LightK {
-    T c[MAX_LIGHT][10];
+    // per component: amplitude A/(2 pi), centre, and the exponent
+    // E = (q x'^2 + y'^2/q)/(2 sigma^2) as a quadratic form a dx^2 + b dx dy + c dy^2 in
+    // the offsets (dx, dy) from the centre -- natural (e) and times log2(e) (e2)
+    T amp[MAX_LIGHT], xn[MAX_LIGHT], yn[MAX_LIGHT];
+    T ea[MAX_LIGHT], eb[MAX_LIGHT], ec[MAX_LIGHT];
+    T e2a[MAX_LIGHT], e2b[MAX_LIGHT], e2c[MAX_LIGHT];
     int n;
 };
 
@@ -481,30 +493,39 @@ template <typename T>
 __device__ __forceinline__ void light_setup(LightK<T>& L, const double* light, int n) {
     if (threadIdx.x == 0) L.n = light ? n : 0;
     if (light && (int)threadIdx.x < n) {
-        const double* p = light + 6 * threadIdx.x;
-        T* c = L.c[threadIdx.x];
-        c[0] = (T)(p[0] / (2.0 * 3.14159265358979323846));
-        c[1] = (T)(0.5 / (p[1] * p[1]));
-        c[2] = (T)p[2];
-        c[3] = (T)(1.0 / p[2]);
-        c[4] = (T)cos(p[3]);
-        c[5] = (T)sin(p[3]);
-        c[6] = (T)p[4];
-        c[7] = (T)p[5];
-        c[8] = (T)(1.0 / p[0]);
-        c[9] = (T)(1.0 / p[1]);
+        const int k = threadIdx.x;
+        const double* p = light + 6 * k;
+        const double c1 = 0.5 / (p[1] * p[1]), q = p[2], cs = cos(p[3]), sn = sin(p[3]);
+        // x' = cs dx + sn dy, y' = cs dy - sn dx
+        const double a = c1 * (q * cs * cs + sn * sn / q);
+        const double b = c1 * 2.0 * cs * sn * (q - 1.0 / q);
+        const double c = c1 * (q * sn * sn + cs * cs / q);
+        const double l2e = 1.4426950408889634;      // log2(e): exp(-E) = 2^(-E log2 e)
+        L.amp[k] = (T)(p[0] / (2.0 * 3.14159265358979323846));
+        L.xn[k] = (T)p[4];
+        L.yn[k] = (T)p[5];
+        L.ea[k] = (T)a; L.eb[k] = (T)b; L.ec[k] = (T)c;
+        L.e2a[k] = (T)(a * l2e); L.e2b[k] = (T)(b * l2e); L.e2c[k] = (T)(c * l2e);
     }
 }
+
+// the lens-light adjoint: pixels per thread and CTAs per evaluation
+constexpr int LIGHT_PPT = 8;
+__host__ __device__ inline int light_ctas(int n_img) {
+    return (n_img * n_img + CTA_R * LIGHT_PPT - 1) / (CTA_R * LIGHT_PPT);
+}
+
+__device__ __forceinline__ float r_exp2(float x) { return exp2f(x); }
+__device__ __forceinline__ double r_exp2(double x) { return exp2(x); }
 
 // the lens light at (x, y)
 template <typename T>
 __device__ __forceinline__ T light_at(const LightK<T>& L, T x, T y) {
     T v = T(0);
     for (int n = 0; n < L.n; ++n) {
-        const T* c = L.c[n];
-        const T dx = x - c[6], dy = y - c[7];
-        const T xp = c[4] * dx + c[5] * dy, yp = c[4] * dy - c[5] * dx;
-        v += c[0] * r_exp(-c[1] * (c[2] * xp * xp + c[3] * yp * yp));
+        const T dx = x - L.xn[n], dy = y - L.yn[n];
+        const T e = dx * (L.e2a[n] * dx + L.e2b[n] * dy) + L.e2c[n] * dy * dy;
+        v += L.amp[n] * r_exp2(-e);
     }
     return v;
 }

@@ -308,16 +308,23 @@ RTU_HD void nfw_deflect(const S& x, const S& y, const S& ks, const S& rs,
 // depends on the lens only (computed once per system in double) and the per-ray
 // part, plus its analytic vector-Jacobian product with respect to
 // (theta_E, gamma, e1, e2, x0, y0).
+//
+// Term n of the series is Omega_n = c_n w Omega_{n-1} with the lens-only factors
+// c_n = -f (2n - 2 + t)/(2n + 2 - t) and w = e^{2 i vphi}, so Omega_n = A_n w^n Omega_0
+// with A_n = c_1 ... c_n: every sum the deflection and its derivatives need is
+// Omega_0 times a polynomial in w with lens-only real coefficients, evaluated per ray
+// by Horner's rule (independent chains for the four sums of the adjoint).
 constexpr int EPL_MAXT = 96;
 
-// one term of the series: c_n, n g_n (g_n = c_n / f), D_n; one 16-byte (float)
-// or two 16-byte (double) shared-memory loads per term
+// the coefficients of w^n, n = 0..nterm, of the four sums
+//   S = sum Omega_n:              a_n = A_n
+//   H = sum (2n+1) Omega_n:       h_n = (2n+1) A_n
+//   U = sum D_n Omega_n:          u_n = D_n A_n, D_n = sum_{k <= n} d log|c_k| / dt
+//   F = sum n g_n Omega_{n-1} w:  f_n = n g_n A_{n-1}, g_n = c_n / f
+// one 16-byte (float) or two 16-byte (double) shared-memory loads per power
 template <typename T>
 struct __align__(16) EplTerm {
-    T c;      // c_n = -f (2n - 2 + t) / (2n + 2 - t), n = 1..nterm
-    T ng;     // n c_n / f
-    T D;      // D_n = sum_{k <= n} d log|c_k| / dt
-    T pad_;
+    T a, h, u, f;
 };
 
 template <typename T>
@@ -327,8 +334,8 @@ struct EplC {
     // (t/b) db/dq, (t/b) db/dtheta_E, 1/(1+q), the (e1, e2) chain factors
     T f_q, tb_bq, tb_sq, iopq, qe1, qe2, pe1, pe2;
     T ftail;          // f / (1 - f): the series tail factor, f = (1 - q)/(1 + q)
-    int nterm;
-    EplTerm<T> term[EPL_MAXT];
+    int nterm;        // highest power of w
+    EplTerm<T> term[EPL_MAXT + 1];
 };
 
 // the lens-only scalars of the series (everything but the term tables)
@@ -358,6 +365,20 @@ RTU_HD void epl_scalars(EplC<T>& C, const double* p, bool epl) {
     C.ftail = (T)(f / (1.0 - f));
 }
 
+// coefficient n >= 1 of the four sums from A_{n-1} (running), c_n, g_n and D_n
+template <typename T>
+RTU_HD void epl_term(EplTerm<T>& tm, int n, double A_prev, double c, double g, double D) {
+    const double A = A_prev * c;
+    tm.a = (T)A;
+    tm.h = (T)((2.0 * n + 1.0) * A);
+    tm.u = (T)(D * A);
+    tm.f = (T)(n * g * A_prev);
+}
+template <typename T>
+RTU_HD void epl_term0(EplTerm<T>& tm) {
+    tm.a = T(1); tm.h = T(1); tm.u = T(0); tm.f = T(0);
+}
+
 // p = theta_E, gamma, e1, e2, x0, y0 (gamma ignored unless epl); tol = size of the
 // last summed term relative to the leading one
 template <typename T>
@@ -367,28 +388,41 @@ RTU_HD void epl_setup(EplC<T>& C, const double* p, bool epl, double tol) {
     const double q = (1.0 - cc) / (1.0 + cc);
     const double t = (epl ? p[1] : 2.0) - 1.0;
     const double f = (1.0 - q) / (1.0 + q);
-    double a = 1.0, D = 0.0;
+    double A = 1.0, D = 0.0;
+    epl_term0(C.term[0]);
     int n = 1;
     for (; n <= EPL_MAXT; ++n) {
         const double g = -(2.0 * n - 2.0 + t) / (2.0 * n + 2.0 - t);
         const double c = f * g;
         D += 1.0 / (2.0 * n - 2.0 + t) + 1.0 / (2.0 * n + 2.0 - t);
-        a *= c;
-        C.term[n - 1].c = (T)c; C.term[n - 1].ng = (T)(n * g); C.term[n - 1].D = (T)D; C.term[n - 1].pad_ = T(0);
-        if (fabs(a) <= tol) break;
+        epl_term(C.term[n], n, A, c, g, D);
+        A *= c;
+        if (fabs(A) <= tol) break;
     }
     C.nterm = n > EPL_MAXT ? EPL_MAXT : n;
 }
 
+// sum_{n=lo..hi} k_n w^n by Horner's rule (k_n = member `K` of term n)
+#define RTU_EPL_HORNER(K, lo, hi, outr, outi)                                  \
+    {                                                                          \
+        outr = C.term[hi].K;                                                   \
+        outi = T(0);                                                           \
+        for (int n_ = (hi) - 1; n_ >= (lo); --n_) {                            \
+            const T nr_ = outr * wre - outi * wim + C.term[n_].K;              \
+            outi = outr * wim + outi * wre;                                    \
+            outr = nr_;                                                        \
+        }                                                                      \
+    }
+
 // The deflection in two parts: the first terms of the series (with the
-// prefactor P), then the rest.  Between them, epl_tail_bound bounds what the
-// remaining terms can add: |c_n| < f for 0 < t < 2 and |w| = 1, so the tail is
-// at most P |Omega_m| f / (1 - f).  begin(m = 0) + finish is the plain sum, in
-// the same order, so a ray that finishes gets the same bits as epl_alpha.
+// prefactor P), then all of it.  Between them, epl_tail_bound bounds what the
+// remaining terms can add: |c_n| < f for 0 < t < 2 and |w| = 1, so the terms beyond
+// power m add at most P |A_m| f / (1 - f).  finish evaluates the whole polynomial,
+// exactly as epl_alpha does, so a ray that finishes gets the same bits.
 template <typename T>
 struct EplPart {
-    T tre, tim, sre, sim, wre, wim, P;
-    int n;
+    T cre, cim, wre, wim, P, sre, sim;
+    int m;
 };
 
 template <typename T>
@@ -399,19 +433,14 @@ RTU_HD void epl_alpha_begin(const EplC<T>& C, T x, T y, int m, EplPart<T>& s) {
     T R, iR;
     r_sqrt_inv(R2, R, iR);
     const T cre = C.q * xr * iR, cim = yr * iR;
-    s.wre = cre * cre - cim * cim;
-    s.wim = T(2) * cre * cim;
-    s.tre = cre; s.tim = cim; s.sre = cre; s.sim = cim;
+    const T wre = cre * cre - cim * cim, wim = T(2) * cre * cim;
+    s.cre = cre; s.cim = cim; s.wre = wre; s.wim = wim;
     s.P = C.pref0 * r_exp((C.t - T(1)) * (C.lnb - r_log(R)));
-    const int mm = m < C.nterm ? m : C.nterm;
-    for (s.n = 0; s.n < mm; ++s.n) {
-        const T c = C.term[s.n].c;
-        const T nre = s.tre * s.wre - s.tim * s.wim, nim = s.tre * s.wim + s.tim * s.wre;
-        s.tre = c * nre;
-        s.tim = c * nim;
-        s.sre += s.tre;
-        s.sim += s.tim;
-    }
+    s.m = m < C.nterm ? m : C.nterm;
+    T pr, pi;
+    RTU_EPL_HORNER(a, 0, s.m, pr, pi);
+    s.sre = cre * pr - cim * pi;
+    s.sim = cre * pi + cim * pr;
 }
 
 // alpha from the terms summed so far
@@ -424,20 +453,18 @@ RTU_HD void epl_alpha_of(const EplC<T>& C, const EplPart<T>& s, T& ax, T& ay) {
 
 template <typename T>
 RTU_HD T epl_tail_bound(const EplC<T>& C, const EplPart<T>& s) {
-    if (s.n >= C.nterm) return T(0);
-    return s.P * r_sqrt(s.tre * s.tre + s.tim * s.tim) * C.ftail;
+    if (s.m >= C.nterm) return T(0);
+    return s.P * r_abs(C.term[s.m].a) * C.ftail;
 }
 
 template <typename T>
 RTU_HD void epl_alpha_finish(const EplC<T>& C, EplPart<T>& s, T& ax, T& ay) {
-    for (; s.n < C.nterm; ++s.n) {
-        const T c = C.term[s.n].c;
-        const T nre = s.tre * s.wre - s.tim * s.wim, nim = s.tre * s.wim + s.tim * s.wre;
-        s.tre = c * nre;
-        s.tim = c * nim;
-        s.sre += s.tre;
-        s.sim += s.tim;
-    }
+    const T wre = s.wre, wim = s.wim;
+    T pr, pi;
+    RTU_EPL_HORNER(a, 0, C.nterm, pr, pi);
+    s.sre = s.cre * pr - s.cim * pi;
+    s.sim = s.cre * pi + s.cim * pr;
+    s.m = C.nterm;
     epl_alpha_of(C, s, ax, ay);
 }
 
@@ -465,31 +492,38 @@ RTU_HD void epl_eval(const EplC<T>& C, bool want_t, T x, T y, EplJ<T>& J) {
     r_sqrt_inv(R2, R, iR);
     const T cre = q * xr * iR, cim = yr * iR;
     const T wre = cre * cre - cim * cim, wim = T(2) * cre * cim;
-    T tre = cre, tim = cim;
-    T sre = cre, sim = cim;            // S = sum Omega_n
-    T hre = cre, him = cim;            // sum (2n+1) Omega_n
-    T ure = T(0), uim = T(0);          // sum D_n Omega_n
-    T fre = T(0), fim = T(0);          // sum n g_n Omega_{n-1} w
-    T w2 = T(3);                       // 2n + 1 for the term n = 1, 2, ...
-    for (int n = 0; n < C.nterm; ++n) {
+    // the four polynomials by Horner's rule, in one loop (independent chains)
+    const int N = C.nterm;
+    T ar = C.term[N].a, ai = T(0), hr = C.term[N].h, hi = T(0);
+    T ur = C.term[N].u, ui = T(0), fr = C.term[N].f, fi = T(0);
+    for (int n = N - 1; n >= 0; --n) {
         const EplTerm<T> tm = C.term[n];
-        const T nre = tre * wre - tim * wim, nim = tre * wim + tim * wre;
-        fre += tm.ng * nre;
-        fim += tm.ng * nim;
-        tre = tm.c * nre;
-        tim = tm.c * nim;
-        sre += tre; sim += tim;
-        hre += w2 * tre; him += w2 * tim;
-        w2 += T(2);
-        if (want_t) { ure += tm.D * tre; uim += tm.D * tim; }
+        const T ar2 = ar * wre - ai * wim + tm.a;
+        ai = ar * wim + ai * wre;
+        ar = ar2;
+        const T hr2 = hr * wre - hi * wim + tm.h;
+        hi = hr * wim + hi * wre;
+        hr = hr2;
+        if (want_t) {
+            const T ur2 = ur * wre - ui * wim + tm.u;
+            ui = ur * wim + ui * wre;
+            ur = ur2;
+        }
+        const T fr2 = fr * wre - fi * wim + tm.f;
+        fi = fr * wim + fi * wre;
+        fr = fr2;
     }
+    const T sre = cre * ar - cim * ai, sim = cre * ai + cim * ar;
     const T lbR = C.lnb - r_log(R);
     const T P = C.pref0 * r_exp((C.t - T(1)) * lbR);
     J.xr = xr; J.yr = yr; J.iR = iR; J.P = P; J.lbR = lbR;
     J.are = P * sre; J.aim = P * sim;
     J.ax = C.cp * J.are - C.sp * J.aim;
     J.ay = C.sp * J.are + C.cp * J.aim;
-    J.hre = hre; J.him = him; J.ure = ure; J.uim = uim; J.fre = fre; J.fim = fim;
+    J.hre = cre * hr - cim * hi; J.him = cre * hi + cim * hr;
+    if (want_t) { J.ure = cre * ur - cim * ui; J.uim = cre * ui + cim * ur; }
+    else { J.ure = T(0); J.uim = T(0); }
+    J.fre = cre * fr - cim * fi; J.fim = cre * fi + cim * fr;
 }
 
 // out[k] += Re(conj(G) d alpha / d p_k), G = (gx, gy) = dL/d alpha,
