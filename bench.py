@@ -417,7 +417,7 @@ def run_ours(args):
 # the NEXT variants of the hot path on the same mocks: the kernels each one adds or
 # swaps, and its whole-step throughput
 VARIANT_KERNELS = ("k_select_fit", "k_lin_sort", "k_render", "k_render_edge", "k_render_adj", "k_cdf_adj",
-                   "k_centre_adj", "k_sel_adj", "k_lin_centre_adj", "k_light_adj")
+                   "k_centre_adj", "k_sel_adj", "k_lin_centre_adj", "k_light_fwd", "k_light_adj")
 
 
 def run_variants(args, dev, mocks, flush, stream):

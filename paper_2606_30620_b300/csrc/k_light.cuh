@@ -1,5 +1,5 @@
-// k_light.cuh -- adjoint of the MGE lens light (App. A.3).  The forward adds the
-// light inside the render kernel; here every component's six weighted moments of
+// k_light.cuh -- the MGE lens light (App. A.3): the forward adds the supersample mean
+// of the light to the unconvolved image; in the adjoint every component's six weighted moments of
 // its sub-ray offsets (dx, dy) from the centre are summed,
 //   M = sum w, (sum w dx, sum w dy), (sum w dx^2, sum w dx dy, sum w dy^2),
 //   w = (d log L / d image) / s^2 * L_n(sub-ray),
@@ -9,6 +9,34 @@
 #include "rtu_internal.cuh"
 
 namespace rtu {
+
+// The forward: one thread per pixel adds the supersample mean of the light to the
+// unconvolved image the render kernel wrote (after the near-edge pass), before the PSF.
+constexpr int LIGHT_FWD_NT = 256;
+template <typename T>
+__global__ void __launch_bounds__(LIGHT_FWD_NT) k_light_fwd(const __grid_constant__ Batch B) {
+    const int ev = find_eval(B, blockIdx.x);
+    const EvalArgs& E = B.e[ev];
+    const int tile = blockIdx.x - B.tile0[ev];
+    __shared__ LightK<T> L;
+    __shared__ PixGeom<T> G;
+    light_setup<T>(L, E.light, E.n_light);
+    pixgeom_setup<T>(G, E.pix, E.n_img, E.s);
+    __syncthreads();
+    const int npix = E.n_img * E.n_img, s = E.s;
+    const int pixel = tile * LIGHT_FWD_NT + threadIdx.x;
+    if (L.n == 0 || pixel >= npix) return;
+    const int pj = pixel / E.n_img, pi = pixel - pj * E.n_img;
+    T v = T(0);
+    for (int qb = 0; qb < s; ++qb) {
+        const T y = ray_coord(G, pj, qb);
+        for (int qa = 0; qa < s; ++qa) v += light_at(L, ray_coord(G, pi, qa), y);
+    }
+    T* img = reinterpret_cast<T*>(E.img);
+    const T val = img[pixel] + v / T(s * s);
+    img[pixel] = val;
+    if (E.image_out) reinterpret_cast<T*>(E.image_out)[pixel] = val;
+}
 
 // One thread per LIGHT_PPT pixels (CTA_R apart: coalesced), components one after
 // the other; per pixel the s^2 sub-rays are summed in T, then added to compensated

@@ -324,7 +324,6 @@ struct RenderShared {
     PixGeom<T> G;              // sub-ray positions
     T ih[2 * (MAXM + 2)];      // 1/(X_{j+1} - X_j) per knot interval, axis-major
     UDiv dv_s2, dv_n, dv_s, dv_nc;   // dividers by s^2, n_img, s, n_src - 1
-    LightK<T> L;               // MGE lens light (App. A.3)
 };
 
 template <typename T>
@@ -348,7 +347,6 @@ __device__ __forceinline__ void render_setup(const EvalArgs& E, RenderShared<T>&
         }
     }
     pixgeom_setup<T>(sh.G, E.pix, E.n_img, E.s);
-    light_setup<T>(sh.L, E.light, E.n_light);
     if (threadIdx.x == 0) {
         sh.dv_s2 = udiv_make((uint32_t)(E.s * E.s));
         sh.dv_n = udiv_make((uint32_t)E.n_img);
@@ -449,28 +447,13 @@ __global__ void __launch_bounds__(CTA_R, 6) k_render(const __grid_constant__ Bat
     }
     __syncthreads();
     if (cull_sh) {
-        // no ray of this tile reaches the grid: only the lens light, nothing staged
+        // no ray of this tile reaches the grid: a zero source image, nothing staged
         if (threadIdx.x < CTA_R / 32) E.useg[tile * (CTA_R / 32) + threadIdx.x] = 0;
         if (threadIdx.x == 0) E.cta_cnt[tile] = 0;
-        if (E.n_light > 0) {
-            pixgeom_setup<T>(sh.G, E.pix, E.n_img, E.s);
-            light_setup<T>(sh.L, E.light, E.n_light);
-            if (threadIdx.x == 0) { sh.dv_n = udiv_make((uint32_t)E.n_img); sh.dv_s = udiv_make((uint32_t)E.s); }
-            __syncthreads();
-        }
         if (!valid) return;
-        T acc = T(0);
-        if (E.n_light > 0) {
-            const int pj = (int)udiv((uint32_t)pixel, sh.dv_n), pi = pixel - pj * E.n_img;
-            for (int q = 0; q < s2; ++q) {
-                const int qb = (int)udiv((uint32_t)q, sh.dv_s), qa = q - qb * s;
-                acc += light_at(sh.L, ray_coord(sh.G, pi, qa), ray_coord(sh.G, pj, qb));
-            }
-        }
         if (sizeof(T) == 4) E.pdef[pixel] = 0ull;
-        const T val = acc / T(s2);
-        reinterpret_cast<T*>(E.img)[pixel] = val;
-        if (E.image_out) reinterpret_cast<T*>(E.image_out)[pixel] = val;
+        reinterpret_cast<T*>(E.img)[pixel] = T(0);
+        if (E.image_out) reinterpret_cast<T*>(E.image_out)[pixel] = T(0);
         return;
     }
     render_setup<T>(E, sh);
@@ -516,7 +499,6 @@ __global__ void __launch_bounds__(CTA_R, 6) k_render(const __grid_constant__ Bat
     auto trace = [&](int q) -> int {
         const int qb = (int)udiv((uint32_t)q, sh.dv_s), qa = q - qb * s;
         const T x = ray_coord(sh.G, pi, qa), y = ray_coord(sh.G, pj, qb);
-        if (sh.L.n) acc += light_at(sh.L, x, y);       // lens light at every sub-ray
         T yx, yy;
         if (sizeof(T) == 4 && lens_near_core(sh.K, x, y)) {
             double xd, yd, ydx, ydy;

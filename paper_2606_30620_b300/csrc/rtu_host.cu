@@ -511,6 +511,9 @@ int t_one_fit(const EvalArgs& e) { return is_lin(e) ? 0 : 1; }
 int t_centre_fit(const EvalArgs& e) { return is_lin(e) ? 0 : e.n_cta_c; }
 int t_centre_lin(const EvalArgs& e) { return is_lin(e) ? e.n_cta_c : 0; }
 int t_light(const EvalArgs& e) { return e.light && e.n_light > 0 ? light_ctas(e.n_img) : 0; }
+int t_light_fwd(const EvalArgs& e) {
+    return e.light && e.n_light > 0 ? (e.n_img * e.n_img + LIGHT_FWD_NT - 1) / LIGHT_FWD_NT : 0;
+}
 int t_render_fit(const EvalArgs& e) { return is_lin(e) ? 0 : e.n_cta_r; }
 int t_render_lin(const EvalArgs& e) { return is_lin(e) ? e.n_cta_r : 0; }
 int t_adj_fit(const EvalArgs& e) { return is_lin(e) ? 0 : e.n_cta_adj; }
@@ -604,6 +607,7 @@ rtu_status run_chunk(Batch& B, int phase, cudaStream_t st, const SideStream& ss)
             if ((r = launch("k_render_edge", k_render_edge, B, t_edge, EDGE_NT, 0, st))) return r;
             if ((r = launch("k_render_fix", k_render_fix, B, t_fix, 256, 0, st))) return r;
         }
+        if (any_light && (r = launch("k_light_fwd", k_light_fwd<T>, B, t_light_fwd, LIGHT_FWD_NT, 0, st))) return r;
         if (sizeof(T) == 4 && maxPsf <= 9) r = launch("k_psf_like", k_psf_like_t<9>, B, t_psf, PSFT_NT, 0, st);
         else if (sizeof(T) == 4 && maxPsf <= 21) r = launch("k_psf_like", k_psf_like_t<21>, B, t_psf, PSFT_NT, 0, st);
         else r = launch("k_psf_like", k_psf_like<T>, B, t_psf, PSF_NT, 0, st);
