@@ -223,6 +223,148 @@ __global__ void __launch_bounds__(PSFT_NT) k_psf_adj_t(const __grid_constant__ B
     }
 }
 
+// ---- rank-1 PSF, psf[b][a] = u[b] v[a]: two one-dimensional passes over a 32 x 32
+// output tile staged with its halo -- the taps v along x into a shared row buffer,
+// then the taps u along y -- K + K multiply-adds per output instead of K^2.  Each
+// thread computes 4 adjacent outputs of a pass from a sliding register window.
+// CONV: convolution (the forward model); else correlation (its adjoint).
+constexpr int PSFS_NT = 256;
+constexpr int PSFS_W = PSF_T + PSF_MAXK - 1;
+
+template <typename T, bool CONV>
+__device__ __forceinline__ void psf_sep_passes(const EvalArgs& E, const T* src, int i0, int j0,
+                                               T (*in)[PSFS_W + 1], T (*h)[PSF_T + 1], T* u, T* v, T* out4,
+                                               int& ox, int& oy0) {
+    const int K = E.psf_k, c = (K - 1) / 2, n = E.n_img, W = PSF_T + 2 * c;
+    for (int i = threadIdx.x; i < 2 * K; i += PSFS_NT) {
+        const T x = (T)E.psf_uv[i];
+        if (i < K) u[i] = x; else v[i - K] = x;
+    }
+    for (int w = threadIdx.x; w < W * W; w += PSFS_NT) {
+        const int r = w / W, q = w - r * W;
+        const int gj = j0 - c + r, gi = i0 - c + q;
+        in[r][q] = (gj >= 0 && gj < n && gi >= 0 && gi < n) ? src[gj * n + gi] : T(0);
+    }
+    __syncthreads();
+    // along x: h[r][x] = sum_a v[a] in[r][x + 2c - a] (convolution) or in[r][x + a]
+    for (int t = threadIdx.x; t < W * (PSF_T / 4); t += PSFS_NT) {
+        const int r = t / (PSF_T / 4), x0 = 4 * (t - r * (PSF_T / 4));
+        T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+        if (CONV) {
+            const T* row = in[r] + x0 + 2 * c;          // row[u - a] for output x0 + u
+            T w0 = row[0], w1 = row[1], w2 = row[2], w3 = row[3];
+            for (int a = 0; a < K; ++a) {
+                const T f = v[a];
+                a0 += f * w0; a1 += f * w1; a2 += f * w2; a3 += f * w3;
+                w3 = w2; w2 = w1; w1 = w0;
+                w0 = a + 1 < K ? row[-(a + 1)] : T(0);
+            }
+        } else {
+            const T* row = in[r] + x0;                  // row[u + a]
+            T w0 = row[0], w1 = row[1], w2 = row[2], w3 = row[3];
+            for (int a = 0; a < K; ++a) {
+                const T f = v[a];
+                a0 += f * w0; a1 += f * w1; a2 += f * w2; a3 += f * w3;
+                w0 = w1; w1 = w2; w2 = w3;
+                w3 = a + 1 < K ? row[a + 4] : T(0);
+            }
+        }
+        h[r][x0] = a0; h[r][x0 + 1] = a1; h[r][x0 + 2] = a2; h[r][x0 + 3] = a3;
+    }
+    __syncthreads();
+    // along y: 4 adjacent rows of one column per thread (256 threads = 8 x 32)
+    const int x = threadIdx.x & (PSF_T - 1), y0 = 4 * (threadIdx.x >> 5);
+    T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+    if (CONV) {
+        const int base = y0 + 2 * c;                    // h[y - b + 2c]
+        T w0 = h[base][x], w1 = h[base + 1][x], w2 = h[base + 2][x], w3 = h[base + 3][x];
+        for (int b = 0; b < K; ++b) {
+            const T f = u[b];
+            a0 += f * w0; a1 += f * w1; a2 += f * w2; a3 += f * w3;
+            w3 = w2; w2 = w1; w1 = w0;
+            w0 = b + 1 < K ? h[base - (b + 1)][x] : T(0);
+        }
+    } else {
+        T w0 = h[y0][x], w1 = h[y0 + 1][x], w2 = h[y0 + 2][x], w3 = h[y0 + 3][x];
+        for (int b = 0; b < K; ++b) {
+            const T f = u[b];
+            a0 += f * w0; a1 += f * w1; a2 += f * w2; a3 += f * w3;
+            w0 = w1; w1 = w2; w2 = w3;
+            w3 = b + 1 < K ? h[y0 + b + 4][x] : T(0);
+        }
+    }
+    out4[0] = a0; out4[1] = a1; out4[2] = a2; out4[3] = a3;
+    ox = x;
+    oy0 = y0;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(PSFS_NT) k_psf_like_sep(const __grid_constant__ Batch B) {
+    const int ev = find_eval(B, blockIdx.x);
+    const EvalArgs& E = B.e[ev];
+    const int tile = blockIdx.x - B.tile0[ev];
+    __shared__ T in[PSFS_W][PSFS_W + 1];
+    __shared__ T h[PSFS_W][PSF_T + 1];
+    __shared__ T u[PSF_MAXK], v[PSF_MAXK];
+    __shared__ double red[2][PSFS_NT / 32];
+    const int n = E.n_img;
+    int ti, tj;
+    psf_tile_of(E, tile, ti, tj);
+    const int i0 = ti * PSF_T, j0 = tj * PSF_T;
+    T m4[4];
+    int x, y0;
+    psf_sep_passes<T, true>(E, reinterpret_cast<const T*>(E.img), i0, j0, in, h, u, v, m4, x, y0);
+    const T isg = T(1) / T(E.sigma);
+    T r2t = T(0), r2mt = T(0);
+    const int i = i0 + x;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int j = j0 + y0 + k;
+        if (i < n && j < n) {
+            const T m = m4[k];
+            const T d = reinterpret_cast<const T*>(E.data)[j * n + i];
+            const T r = (d - m) * isg;
+            reinterpret_cast<T*>(E.resid)[j * n + i] = r * isg;
+            if (E.model_out) reinterpret_cast<T*>(E.model_out)[j * n + i] = m;
+            r2t += r * r;
+            if (E.mask[j * n + i]) r2mt += r * r;
+        }
+    }
+    // per-thread partials of 4 pixels, then double across threads, fixed order
+    const double r2 = warp_sum((double)r2t), r2m = warp_sum((double)r2mt);
+    if ((threadIdx.x & 31) == 0) { red[0][threadIdx.x >> 5] = r2; red[1][threadIdx.x >> 5] = r2m; }
+    __syncthreads();
+    if (threadIdx.x < 2) {
+        double sacc = 0.0;
+        for (int w = 0; w < PSFS_NT / 32; ++w) sacc += red[threadIdx.x][w];
+        E.lpart[tile * 2 + threadIdx.x] = sacc;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(PSFS_NT) k_psf_adj_sep(const __grid_constant__ Batch B) {
+    const int ev = find_eval(B, blockIdx.x);
+    const EvalArgs& E = B.e[ev];
+    const int tile = blockIdx.x - B.tile0[ev];
+    __shared__ T in[PSFS_W][PSFS_W + 1];
+    __shared__ T h[PSFS_W][PSF_T + 1];
+    __shared__ T u[PSF_MAXK], v[PSF_MAXK];
+    const int n = E.n_img;
+    int ti, tj;
+    psf_tile_of(E, tile, ti, tj);
+    const int i0 = ti * PSF_T, j0 = tj * PSF_T;
+    T g4[4];
+    int x, y0;
+    psf_sep_passes<T, false>(E, reinterpret_cast<const T*>(E.resid), i0, j0, in, h, u, v, g4, x, y0);
+    const T sc = E.dlogL ? (T)(*E.dlogL) : T(1);
+    const int i = i0 + x;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int j = j0 + y0 + k;
+        if (i < n && j < n) reinterpret_cast<T*>(E.gimg)[j * n + i] = g4[k] * sc;
+    }
+}
+
 // log L = -1/2 sum r^2 - N log(sigma sqrt(2 pi)); chi^2_img = sum_mask r^2 / N_mask
 __global__ void __launch_bounds__(256) k_like_final(const __grid_constant__ Batch B) {
     const EvalArgs& E = B.e[blockIdx.x];

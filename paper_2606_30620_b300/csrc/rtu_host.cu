@@ -194,7 +194,7 @@ size_t state_layout(const rtu_system_desc& d, char* base, ElboState* st) {
 }
 
 size_t static_layout(const rtu_system_desc& d, char* base, int** cidx, double** tw, int** rev, double** cheb,
-                     uint32_t** cwt = nullptr) {
+                     uint32_t** cwt = nullptr, double** psf_uv = nullptr) {
     size_t o = 0;
     auto take = [&](size_t bytes) { size_t at = o; o = align_up(o + bytes); return base ? base + at : nullptr; };
     char* p = take((size_t)d.n_img * d.n_img * 4); if (cidx) *cidx = (int*)p;
@@ -202,7 +202,27 @@ size_t static_layout(const rtu_system_desc& d, char* base, int** cidx, double** 
     p = take((size_t)2 * d.n_src * 8);             if (tw) *tw = (double*)p;
     p = take((size_t)d.n_src * 4);                 if (rev) *rev = (int*)p;
     p = take((size_t)cheb_size(d.n_nodes, d.degree) * 8); if (cheb) *cheb = (double*)p;
+    p = take((size_t)2 * d.psf_k * 8);             if (psf_uv) *psf_uv = (double*)p;
     return o;
+}
+
+// A rank-1 PSF psf[b][a] = u[b] v[a] (a sampled circular or axis-aligned Gaussian, for
+// one) is convolved in two one-dimensional passes.  The factors are a column and a row
+// through the largest tap; the PSF counts as rank 1 when no tap differs from u[b] v[a]
+// by more than 8 rounding units of its precision times the largest tap.
+bool psf_rank1(const std::vector<double>& P, int K, bool f64, double* uv) {
+    int b0 = 0, a0 = 0;
+    for (int i = 0; i < K * K; ++i)
+        if (std::fabs(P[i]) > std::fabs(P[b0 * K + a0])) { b0 = i / K; a0 = i % K; }
+    const double p0 = P[b0 * K + a0];
+    if (!(std::fabs(p0) > 0.0)) return false;
+    for (int b = 0; b < K; ++b) uv[b] = P[b * K + a0];
+    for (int a = 0; a < K; ++a) uv[K + a] = P[b0 * K + a] / p0;
+    const double tol = 8.0 * (f64 ? std::ldexp(1.0, -53) : std::ldexp(1.0, -24)) * std::fabs(p0);
+    for (int b = 0; b < K; ++b)
+        for (int a = 0; a < K; ++a)
+            if (!(std::fabs(P[b * K + a] - uv[b] * uv[K + a]) <= tol)) return false;
+    return true;
 }
 
 // Chebyshev nodes and the matrices of the interpolating fit (App. C iii-iv), by
@@ -297,6 +317,7 @@ struct rtu_system {
     double* tw;
     int* rev;
     double* cheb;
+    double* psf_uv;               // factors of a rank-1 PSF, or null
     std::vector<EvalArgs> slot;   // workspace pointers of each slot
     std::vector<SampleBufs> sbuf; // guide-sample buffers of each slot
     ElboState st;
@@ -350,7 +371,8 @@ rtu_status rtu_system_create(const rtu_system_desc* d, void* ws, size_t ws_bytes
     for (int i = 0; i < MAX_RADIX; ++i) s->rad[i] = i < s->nrad ? rad[i] : 1;
     char* base = static_cast<char*>(ws);
     uint32_t* cwt_buf = nullptr;
-    const size_t st = static_layout(*d, base, &s->cidx, &s->tw, &s->rev, &s->cheb, &cwt_buf);
+    double* uv_buf = nullptr;
+    const size_t st = static_layout(*d, base, &s->cidx, &s->tw, &s->rev, &s->cheb, &cwt_buf, &uv_buf);
     // arc-mask pixel list (the CDF uses observed-pixel centres inside the mask)
     const size_t npx = (size_t)d->n_img * d->n_img;
     std::vector<uint8_t> mask(npx);
@@ -392,6 +414,19 @@ rtu_status rtu_system_create(const rtu_system_desc* d, void* ws, size_t ws_bytes
     }
     std::vector<int> rev = digit_reversal(d->n_src, rad);
     std::vector<double> cheb = chebyshev_tables(d->n_nodes, d->degree);
+    // the PSF: rank 1 or not
+    const int K = d->psf_k;
+    const bool f64 = d->precision == RTU_F64;
+    std::vector<double> P(K * K), uv(2 * K);
+    {
+        std::vector<float> pf(f64 ? 0 : K * K);
+        ce = f64 ? cudaMemcpy(P.data(), d->psf, K * K * 8, cudaMemcpyDeviceToHost)
+                 : cudaMemcpy(pf.data(), d->psf, K * K * 4, cudaMemcpyDeviceToHost);
+        if (ce != cudaSuccess) { delete s; return fail(RTU_E_CUDA, std::string("psf copy: ") + cudaGetErrorString(ce)); }
+        if (!f64) for (int i = 0; i < K * K; ++i) P[i] = pf[i];
+    }
+    const bool sep = psf_rank1(P, K, f64, uv.data());
+    s->psf_uv = sep ? uv_buf : nullptr;
     {
         // the static tables assembled on the host with the device layout, one copy
         // (the centre weights, if any, were uploaded above)
@@ -400,13 +435,15 @@ rtu_status rtu_system_create(const rtu_system_desc* d, void* ws, size_t ws_bytes
         double *htw, *hcheb;
         int* hrev;
         uint32_t* hcwt;
-        static_layout(*d, img.data(), &hcidx, &htw, &hrev, &hcheb, &hcwt);
+        double* huv;
+        static_layout(*d, img.data(), &hcidx, &htw, &hrev, &hcheb, &hcwt, &huv);
         memcpy(hcidx, idx.data(), idx.size() * 4);
         memcpy(htw, tw.data(), tw.size() * 8);
         memcpy(hrev, rev.data(), rev.size() * 4);
         memcpy(hcheb, cheb.data(), cheb.size() * 8);
+        memcpy(huv, uv.data(), uv.size() * 8);
         const size_t tw_off = (size_t)(reinterpret_cast<char*>(htw) - img.data());
-        // the arc-mask pixel list (n_mask entries) and the FFT / Chebyshev tables; the
+        // the arc-mask pixel list (n_mask entries) and the FFT / Chebyshev / PSF tables; the
         // weights region in between is written above (weighted grid) or unused
         if ((ce = cudaMemcpy(base, img.data(), idx.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
             (ce = cudaMemcpy(base + tw_off, img.data() + tw_off, st - tw_off, cudaMemcpyHostToDevice)) != cudaSuccess) {
@@ -459,6 +496,7 @@ rtu_status fill_args(rtu_system* s, const rtu_eval& v, EvalArgs& e) {
     e.data = d.data; e.mask = d.mask; e.psf = d.psf;
     e.centre_idx = s->cidx; e.tw = s->tw; e.digrev = s->rev; e.cheb = s->cheb;
     e.cwt = s->cwt; e.wtot = s->wtot;
+    e.psf_uv = s->psf_uv;
     e.lens = v.lens; e.latents = v.latents; e.ps = v.ps; e.dlogL = v.dlogL;
     e.stats = v.stats; e.model_out = v.model; e.image_out = v.image; e.source_out = v.source;
     e.cdf_out = v.cdf; e.hist_out = v.ray_hist;
@@ -524,7 +562,8 @@ int t_gp_lines(const EvalArgs& e) { return (e.n_src + GP_LINES - 1) / GP_LINES; 
 int t_zero(const EvalArgs&) { return ZERO_TILES; }
 int t_centre(const EvalArgs& e) { return e.n_cta_c; }
 int t_adj(const EvalArgs& e) { return e.n_cta_adj; }
-int t_psf(const EvalArgs& e) { return e.n_cta_p; }
+int t_psf_gen(const EvalArgs& e) { return e.psf_uv ? 0 : e.n_cta_p; }
+int t_psf_sep(const EvalArgs& e) { return e.psf_uv ? e.n_cta_p : 0; }
 int t_edge(const EvalArgs&) { return EDGE_CTAS; }
 int t_fix(const EvalArgs& e) { return (e.n_img * e.n_img + 255) / 256; }
 int t_units(const EvalArgs& e) { return (e.n_cta_r * (CTA_R / 32) + CMP_NT / 32 - 1) / (CMP_NT / 32); }
@@ -610,16 +649,18 @@ rtu_status run_chunk(Batch& B, int phase, cudaStream_t st, const SideStream& ss)
             if ((r = launch("k_render_fix", k_render_fix, B, t_fix, 256, 0, st))) return r;
         }
         if (any_light && (r = launch("k_light_fwd", k_light_fwd<T>, B, t_light_fwd, LIGHT_FWD_NT, 0, st))) return r;
-        if (sizeof(T) == 4 && maxPsf <= 9) r = launch("k_psf_like", k_psf_like_t<9>, B, t_psf, PSFT_NT, 0, st);
-        else if (sizeof(T) == 4 && maxPsf <= 21) r = launch("k_psf_like", k_psf_like_t<21>, B, t_psf, PSFT_NT, 0, st);
-        else r = launch("k_psf_like", k_psf_like<T>, B, t_psf, PSF_NT, 0, st);
+        if ((r = launch("k_psf_like", k_psf_like_sep<T>, B, t_psf_sep, PSFS_NT, 0, st))) return r;
+        if (sizeof(T) == 4 && maxPsf <= 9) r = launch("k_psf_like", k_psf_like_t<9>, B, t_psf_gen, PSFT_NT, 0, st);
+        else if (sizeof(T) == 4 && maxPsf <= 21) r = launch("k_psf_like", k_psf_like_t<21>, B, t_psf_gen, PSFT_NT, 0, st);
+        else r = launch("k_psf_like", k_psf_like<T>, B, t_psf_gen, PSF_NT, 0, st);
         if (r) return r;
         if ((r = launch("k_like_final", k_like_final, B, t_one, 256, 0, st))) return r;
     }
     if (phase & PH_ADJOINT) {
-        if (sizeof(T) == 4 && maxPsf <= 9) r = launch("k_psf_adj", k_psf_adj_t<9>, B, t_psf, PSFT_NT, 0, st);
-        else if (sizeof(T) == 4 && maxPsf <= 21) r = launch("k_psf_adj", k_psf_adj_t<21>, B, t_psf, PSFT_NT, 0, st);
-        else r = launch("k_psf_adj", k_psf_adj<T>, B, t_psf, PSF_NT, 0, st);
+        if ((r = launch("k_psf_adj", k_psf_adj_sep<T>, B, t_psf_sep, PSFS_NT, 0, st))) return r;
+        if (sizeof(T) == 4 && maxPsf <= 9) r = launch("k_psf_adj", k_psf_adj_t<9>, B, t_psf_gen, PSFT_NT, 0, st);
+        else if (sizeof(T) == 4 && maxPsf <= 21) r = launch("k_psf_adj", k_psf_adj_t<21>, B, t_psf_gen, PSFT_NT, 0, st);
+        else r = launch("k_psf_adj", k_psf_adj<T>, B, t_psf_gen, PSF_NT, 0, st);
         if (r) return r;
         if (any_light && (r = launch("k_light_adj", k_light_adj<T>, B, t_light, CTA_R, 0, st))) return r;
         if ((r = launch("k_scan_cells", k_scan_cells, B, t_one, SCAN_NT, 0, st))) return r;

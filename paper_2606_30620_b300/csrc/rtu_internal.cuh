@@ -42,6 +42,7 @@ struct EvalArgs {
     const uint8_t* mask;
     const void* psf;
     const int* centre_idx;      // [n_mask] pixel index of each arc-mask pixel
+    const double* psf_uv;       // [2 psf_k] psf[b][a] = u[b] v[a] (u then v) of a rank-1 PSF, or null
     const uint32_t* cwt;        // [n_mask] centre-ray weights (weighted grid) or null
     int wtot, pad3_;            // total centre-ray weight (n_mask when unweighted)
     const double* tw;           // [2 n_src] exp(-2 pi i m / n_src)
