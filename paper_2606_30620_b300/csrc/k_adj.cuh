@@ -15,14 +15,10 @@ namespace rtu {
 //              [8 + a*2MAXM + t]  d logL / d beta of the ray selected at (axis a, target t)
 constexpr int TADJ_SEL = 8;
 
-// one warp: column sums over the render-adjoint CTAs, fixed lane stride and a
-// fixed shuffle tree (lane 0 returns the sum)
-__device__ __forceinline__ double apart_col(const EvalArgs& E, int nacc, int col) {
-    const int lane = threadIdx.x & 31;
-    double s = 0.0;
-    for (int t = lane; t < E.n_cta_adj; t += 32) s += E.apart[(size_t)t * nacc + col];
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    return s;
+// one warp: column sums over the render-adjoint CTAs (the partials are column-major,
+// so the lanes read consecutive CTAs), fixed lane stride and a fixed shuffle tree
+__device__ __forceinline__ double apart_col(const EvalArgs& E, int col) {
+    return warp_rows_sum(E.apart + (size_t)col * E.n_cta_adj, E.n_cta_adj, 1);
 }
 
 // One CTA per (evaluation, axis); the uniform-grid transform couples the axes
@@ -33,7 +29,6 @@ __global__ void __launch_bounds__(CDF_NT) k_cdf_adj(const __grid_constant__ Batc
     const EvalArgs& E = B.e[ev];
     const int ax = blockIdx.x - B.tile0[ev];
     const int M = E.n_nodes, D = E.degree, K = M + 2, N = E.n_mask;
-    const int nacc = NACC_FIX + 4 * K + 5 * (E.sub_kind ? E.n_sub : 0);
     __shared__ double tot[NACC_FIX + 4 * (MAXM + 2)];
     __shared__ double gXr[MAXM + 2], gpr[MAXM + 2], gc[MAXM], gQ[MAXM];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -42,7 +37,7 @@ __global__ void __launch_bounds__(CDF_NT) k_cdf_adj(const __grid_constant__ Batc
     if (E.transform == RTU_TRANSFORM_UNIFORM) {
         if (ax != 0) return;
         for (int col = wid; col < NACC_FIX + 4 * K; col += CDF_NT / 32) {
-            const double v = apart_col(E, nacc, col);
+            const double v = apart_col(E, col);
             if (lane == 0) tot[col] = v;
         }
         __syncthreads();
@@ -83,7 +78,7 @@ __global__ void __launch_bounds__(CDF_NT) k_cdf_adj(const __grid_constant__ Batc
     for (int w = wid; w < ncol; w += CDF_NT / 32) {
         const int col = w == 0 ? 8 + ax : (w == 1 ? 10 : (w < 2 + K ? NACC_FIX + ax * K + (w - 2)
                                                                    : NACC_FIX + 2 * K + ax * K + (w - 2 - K)));
-        const double v = apart_col(E, nacc, col);
+        const double v = apart_col(E, col);
         if (lane == 0) tot[col] = v;
     }
     __syncthreads();
@@ -371,13 +366,12 @@ __global__ void __launch_bounds__(GRAD_NT) k_grad_final(const __grid_constant__ 
     const EvalArgs& E = B.e[blockIdx.x];
     const int K = E.n_nodes + 2;
     const int nsub = E.sub_kind ? E.n_sub : 0;
-    const int nacc = NACC_FIX + 4 * K + 5 * nsub;
     const int nl = 8 + 5 * nsub;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     constexpr int NW = GRAD_NT / 32;
     for (int p = wid; p < nl; p += NW) {
         const int col = p < 8 ? p : NACC_FIX + 4 * K + (p - 8);
-        const double s = warp_rows_sum(E.apart + col, E.n_cta_adj, nacc);
+        const double s = apart_col(E, col);
         const double c = warp_rows_sum(E.cadj + p, E.n_cta_c + 1, nl);   // + the selected-rank row
         double g = s + c;
         if (p == 1 && E.profile == 0) g = 0.0;

@@ -13,6 +13,19 @@ namespace rtu {
 // The forward: one thread per pixel adds the supersample mean of the light to the
 // unconvolved image the render kernel wrote (after the near-edge pass), before the PSF.
 constexpr int LIGHT_FWD_NT = 256;
+constexpr int LIGHT_MAXS = 8;          // the largest supersampling factor s
+
+// the s sub-ray coordinates of pixel index i along one axis (registers; s <= 8)
+template <typename T>
+__device__ __forceinline__ void subray_coords(const PixGeom<T>& G, int i, int s, T* c) {
+    const T hi = G.hi, lo = G.lo, e0 = T(i) - G.ci;
+#pragma unroll
+    for (int q = 0; q < LIGHT_MAXS; ++q) {
+        const T e = e0 + G.offp[q < s ? q : 0];
+        c[q] = fma(e, hi, e * lo);
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(LIGHT_FWD_NT) k_light_fwd(const __grid_constant__ Batch B) {
     const int ev = find_eval(B, blockIdx.x);
@@ -27,10 +40,26 @@ __global__ void __launch_bounds__(LIGHT_FWD_NT) k_light_fwd(const __grid_constan
     const int pixel = tile * LIGHT_FWD_NT + threadIdx.x;
     if (L.n == 0 || pixel >= npix) return;
     const int pj = pixel / E.n_img, pi = pixel - pj * E.n_img;
+    T xs[LIGHT_MAXS], ys[LIGHT_MAXS];
+    subray_coords(G, pi, s, xs);
+    subray_coords(G, pj, s, ys);
     T v = T(0);
-    for (int qb = 0; qb < s; ++qb) {
-        const T y = ray_coord(G, pj, qb);
-        for (int qa = 0; qa < s; ++qa) v += light_at(L, ray_coord(G, pi, qa), y);
+    for (int n = 0; n < L.n; ++n) {
+        const T xn = L.xn[n], yn = L.yn[n], a = L.e2a[n], b = L.e2b[n], c = L.e2c[n];
+        T vn = T(0);
+#pragma unroll
+        for (int qb = 0; qb < LIGHT_MAXS; ++qb) {
+            if (qb >= s) break;
+            const T dy = ys[qb] - yn;
+            const T cy = c * dy * dy, by = b * dy;
+#pragma unroll
+            for (int qa = 0; qa < LIGHT_MAXS; ++qa) {
+                if (qa >= s) break;
+                const T dx = xs[qa] - xn;
+                vn += r_exp2(-(dx * (a * dx + by) + cy));
+            }
+        }
+        v += L.amp[n] * vn;
     }
     T* img = reinterpret_cast<T*>(E.img);
     const T val = img[pixel] + v / T(s * s);
@@ -70,20 +99,27 @@ __global__ void __launch_bounds__(CTA_R) k_light_adj(const __grid_constant__ Bat
             if (pixel >= npix) break;
             const T g = gimg[pixel] * inv_s2;
             const int pj = (int)udiv((uint32_t)pixel, dv_n), pi = pixel - pj * E.n_img;
+            T xs[LIGHT_MAXS], ys[LIGHT_MAXS];
+            subray_coords(G, pi, s, xs);
+            subray_coords(G, pj, s, ys);
             T m[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
-            for (int qb = 0; qb < s; ++qb) {
-                const T dy = ray_coord(G, pj, qb) - yn;
-                for (int qa = 0; qa < s; ++qa) {
-                    const T dx = ray_coord(G, pi, qa) - xn;
-                    const T e = dx * (a * dx + b * dy) + c * dy * dy;
-                    const T w = amp * r_exp2(-e);
-                    const T wx = w * dx;
+#pragma unroll
+            for (int qb = 0; qb < LIGHT_MAXS; ++qb) {
+                if (qb >= s) break;
+                const T dy = ys[qb] - yn;
+                const T cy = c * dy * dy, by = b * dy;
+#pragma unroll
+                for (int qa = 0; qa < LIGHT_MAXS; ++qa) {
+                    if (qa >= s) break;
+                    const T dx = xs[qa] - xn;
+                    const T w = amp * r_exp2(-(dx * (a * dx + by) + cy));
+                    const T wx = w * dx, wy = w * dy;
                     m[0] += w;
                     m[1] += wx;
-                    m[2] += w * dy;
+                    m[2] += wy;
                     m[3] += wx * dx;
                     m[4] += wx * dy;
-                    m[5] += w * dy * dy;
+                    m[5] += wy * dy;
                 }
             }
 #pragma unroll

@@ -824,10 +824,11 @@ __global__ void __launch_bounds__(CTA_R, 4) k_render_adj(const __grid_constant__
     render_setup<T>(E, sh);
     for (int i = threadIdx.x; i < NW * 4 * K; i += blockDim.x) { tab[i].x = T(0); tab[i].y = T(0); }
     const bool staged = stage_to_smem(sgrid, E.src, (uint32_t)(n * n * sizeof(T)), &mbar, E.flags);
-    const int nacc = NACC_FIX + 4 * K + 5 * (E.sub_kind ? E.n_sub : 0);
-    double* out = E.apart + (size_t)tile * nacc;
+    // column-major partials: column i of this CTA at apart[i * n_cta_adj + tile]
+    double* out = E.apart + tile;
+    const size_t ostr = (size_t)E.n_cta_adj;
     if (!staged) {
-        for (int i = threadIdx.x; i < NACC_FIX + 4 * K; i += blockDim.x) out[i] = 0.0;
+        for (int i = threadIdx.x; i < NACC_FIX + 4 * K; i += blockDim.x) out[i * ostr] = 0.0;
         return;
     }
     const int s = E.s, s2 = s * s;
@@ -1067,7 +1068,7 @@ __global__ void __launch_bounds__(CTA_R, 4) k_render_adj(const __grid_constant__
             const int kk = i - NACC_FIX;    // [0, 2K) knots X (axis-major), [2K, 4K) slopes d
             for (int w = 0; w < NW; ++w) pair_add(r, tab[w * 4 * K + kk]);
         }
-        out[i] = (double)r.x + (double)r.y;
+        out[i * ostr] = (double)r.x + (double)r.y;
     }
 }
 
@@ -1086,8 +1087,8 @@ __global__ void __launch_bounds__(CTA_R) k_sub_adj(const __grid_constant__ Batch
     pixgeom_setup<T>(G, E.pix, E.n_img, E.s);
     __syncthreads();
     const int Kn = E.n_nodes + 2;
-    const int nacc = NACC_FIX + 4 * Kn + 5 * K.nsub;
-    double* out = E.apart + (size_t)tile * nacc;
+    double* out = E.apart + tile;           // column-major, as k_render_adj
+    const size_t ostr = (size_t)E.n_cta_adj;
     const int nu = E.n_cta_r * (CTA_R / 32);
     const int n_rays = E.n_img * E.n_img * E.s * E.s;
     const int total = max(0, min(E.useg[nu], n_rays));
@@ -1121,7 +1122,7 @@ __global__ void __launch_bounds__(CTA_R) k_sub_adj(const __grid_constant__ Batch
         if (threadIdx.x < 5) {
             double r = 0.0;
             for (int w = 0; w < CTA_R / 32; ++w) r += wsub[w][threadIdx.x];
-            out[NACC_FIX + 4 * Kn + 5 * h + threadIdx.x] = r;
+            out[(NACC_FIX + 4 * Kn + 5 * h + threadIdx.x) * ostr] = r;
         }
         __syncthreads();
     }

@@ -88,7 +88,7 @@ struct EvalArgs {
     int* cursor;       // [n_cells]
     void* rec;         // real4 [n_rays] counting-sorted (fx, fy, g, -) records
     void* corner;      // real2 [n_cells][4] per-cell bilinear corner sums (float: hi + lo pairs)
-    double* apart;     // [n_cta_r][nacc] render-adjoint partials
+    double* apart;     // [nacc][n_cta_adj] render-adjoint partials (column-major)
     int* flags;        // device flag word
     void* lensk;       // LensK<T> then LensK<double> of the evaluation
     int* ecount;       // number of deferred near-edge rays (float mode)
