@@ -496,28 +496,33 @@ __global__ void __launch_bounds__(LIN_NT) k_lin_sort(const __grid_constant__ Bat
     }
     __syncthreads();
     int* h = E.hist + a * HB;
-    // exclusive scan of the HB bin counts, in place (each thread a contiguous run)
+    // exclusive scan of the HB bin counts, in place: warp w owns the contiguous segment
+    // [w SEG, (w+1) SEG) and walks it in 32-bin chunks (coalesced); segment totals,
+    // then their exclusive scan, then each warp rescans its segment with its offset
     {
-        constexpr int PER = HB / LIN_NT;
-        int own = 0;
-        for (int i = 0; i < PER; ++i) own += h[tid * PER + i];
-        int incl = own;
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, incl, o);
-            if ((tid & 31) >= o) incl += y;
-        }
-        if ((tid & 31) == 31) wtot[tid >> 5] = incl;
+        constexpr int SEG = HB / (LIN_NT / 32);
+        const int lane = tid & 31, w = tid >> 5;
+        int* hs = h + w * SEG;
+        int tot = 0;
+        for (int c = 0; c < SEG; c += 32) tot += hs[c + lane];
+        for (int o = 16; o > 0; o >>= 1) tot += __shfl_down_sync(0xffffffffu, tot, o);
+        if (lane == 0) wtot[w] = tot;
         __syncthreads();
         if (tid == 0) {
             int acc = 0;
-            for (int w = 0; w < LIN_NT / 32; ++w) { const int t = wtot[w]; wtot[w] = acc; acc += t; }
+            for (int i = 0; i < LIN_NT / 32; ++i) { const int t = wtot[i]; wtot[i] = acc; acc += t; }
         }
         __syncthreads();
-        int base = wtot[tid >> 5] + incl - own;
-        for (int i = 0; i < PER; ++i) {
-            const int v = h[tid * PER + i];
-            h[tid * PER + i] = base;
-            base += v;
+        int carry = wtot[w];
+        for (int c = 0; c < SEG; c += 32) {
+            const int v = hs[c + lane];
+            int incl = v;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            hs[c + lane] = carry + incl - v;
+            carry += __shfl_sync(0xffffffffu, incl, 31);
         }
     }
     __syncthreads();

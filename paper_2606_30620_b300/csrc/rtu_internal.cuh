@@ -516,20 +516,15 @@ __host__ __device__ inline int light_ctas(int n_img) {
     return (n_img * n_img + CTA_R * LIGHT_PPT - 1) / (CTA_R * LIGHT_PPT);
 }
 
-__device__ __forceinline__ float r_exp2(float x) { return exp2f(x); }
+// 2^x: the float path takes the hardware approximation (PTX ex2.approx, relative error
+// about 2^-22; subnormal results flushed to zero), the double path exp2
+__device__ __forceinline__ float r_exp2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 __device__ __forceinline__ double r_exp2(double x) { return exp2(x); }
 
-// the lens light at (x, y)
-template <typename T>
-__device__ __forceinline__ T light_at(const LightK<T>& L, T x, T y) {
-    T v = T(0);
-    for (int n = 0; n < L.n; ++n) {
-        const T dx = x - L.xn[n], dy = y - L.yn[n];
-        const T e = dx * (L.e2a[n] * dx + L.e2b[n] * dy) + L.e2c[n] * dy * dy;
-        v += L.amp[n] * r_exp2(-e);
-    }
-    return v;
-}
 
 // ------------------------------------------------------------ render tiles
 // A render CTA covers a 16 x 8 pixel tile; thread t takes pixel (t mod 16, t / 16)
