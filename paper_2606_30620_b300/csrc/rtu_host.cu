@@ -511,7 +511,8 @@ rtu_status fill_args(rtu_system* s, const rtu_eval& v, EvalArgs& e) {
 typedef int (*TileFn)(const EvalArgs&);
 
 // ---- optional per-kernel event timing
-struct ProfRec { const char* name; cudaEvent_t a, b; };
+struct ProfRec { const char* name; cudaEvent_t a, b; int side; };
+cudaStream_t g_side_hint[2] = {nullptr, nullptr};   // the side streams of the launching thread (timeline)
 std::mutex g_prof_mu;
 bool g_prof_on = false;
 std::vector<ProfRec> g_prof_pending;
@@ -524,7 +525,7 @@ rtu_status launch(const char* name, Kern kern, Batch& B, TileFn tiles, int threa
     for (int i = 0; i < B.n; ++i) { B.tile0[i] = tot; tot += tiles(B.e[i]); }
     B.tile0[B.n] = tot;
     if (tot == 0) return RTU_OK;
-    ProfRec pr{name, nullptr, nullptr};
+    ProfRec pr{name, nullptr, nullptr, st == nullptr ? 0 : (st == g_side_hint[0] ? 1 : (st == g_side_hint[1] ? 2 : 0))};
     const bool prof = g_prof_on;
     if (prof) {
         cudaEventCreate(&pr.a);
@@ -574,16 +575,17 @@ int t_cells(const EvalArgs& e) {
 
 enum Phase { PH_GRID = 1, PH_FORWARD = 2, PH_ADJOINT = 4 };
 
-// A second stream per (host thread, device) for the steps that do not depend on
-// the main chain: the GP source beside the grid build, the transform/centre-ray
-// adjoint beside the cell gather and GP adjoint.  Fork and join are event waits,
-// so a call still orders everything after the work already on the caller's
-// stream and leaves nothing pending on the side stream when it returns (and the
-// pattern is legal inside CUDA graph capture).  Created at the first call on a
-// device and kept for the life of the thread.
+// Two side streams per (host thread, device), created at the highest stream priority,
+// carry the step's critical branch where the step forks: the grid build (S1-S5) beside
+// the GP source of the forward, and the transform / centre-ray adjoint beside the cell
+// gather and GP adjoint of the adjoint (its selected-rank and centre-ray kernels on one
+// side stream each).  Fork and join are event waits, so a call still orders everything
+// after the work already on the caller's stream and leaves nothing pending on the side
+// streams when it returns (and the pattern is legal inside CUDA graph capture).
+// Created at the first call on a device and kept for the life of the thread.
 struct SideStream {
-    cudaStream_t s = nullptr;
-    cudaEvent_t fork = nullptr, join = nullptr;
+    cudaStream_t s = nullptr, s2 = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr, fork2 = nullptr, join2 = nullptr;
 };
 constexpr int MAX_DEV = 64;
 
@@ -595,9 +597,14 @@ rtu_status side_stream(SideStream*& out) {
     if (dev < 0 || dev >= MAX_DEV) return fail(RTU_E_ARG, "device index too large");
     SideStream& ss = tab[dev];
     if (!ss.s) {
-        if ((ce = cudaStreamCreateWithFlags(&ss.s, cudaStreamNonBlocking)) != cudaSuccess ||
+        int least = 0, greatest = 0;
+        if ((ce = cudaDeviceGetStreamPriorityRange(&least, &greatest)) != cudaSuccess ||
+            (ce = cudaStreamCreateWithPriority(&ss.s, cudaStreamNonBlocking, greatest)) != cudaSuccess ||
+            (ce = cudaStreamCreateWithPriority(&ss.s2, cudaStreamNonBlocking, greatest)) != cudaSuccess ||
             (ce = cudaEventCreateWithFlags(&ss.fork, cudaEventDisableTiming)) != cudaSuccess ||
-            (ce = cudaEventCreateWithFlags(&ss.join, cudaEventDisableTiming)) != cudaSuccess)
+            (ce = cudaEventCreateWithFlags(&ss.join, cudaEventDisableTiming)) != cudaSuccess ||
+            (ce = cudaEventCreateWithFlags(&ss.fork2, cudaEventDisableTiming)) != cudaSuccess ||
+            (ce = cudaEventCreateWithFlags(&ss.join2, cudaEventDisableTiming)) != cudaSuccess)
             return fail(RTU_E_CUDA, std::string("side stream: ") + cudaGetErrorString(ce));
     }
     out = &ss;
@@ -624,18 +631,21 @@ rtu_status run_chunk(Batch& B, int phase, cudaStream_t st, const SideStream& ss)
         maxK = std::max(maxK, B.e[i].n_nodes + 2);
     }
     const size_t grid_bytes = align_up((size_t)max_n2 * sizeof(T), 128);
-    if (phase & PH_FORWARD) {
-        // S6 only needs the latents and spectrum parameters: beside S1-S5
-        if ((r = stream_after(ss.s, st, ss.fork))) return r;
-        for (int pass = 0; pass < GP_PASSES; ++pass)
-            if ((r = launch("k_gp_source", k_gp_lines<T>, B, t_gp_lines, GP_LINE_NT, 0, ss.s, pass))) return r;
-    }
     if (phase & (PH_GRID | PH_FORWARD)) {
-        if ((r = launch("k_zero", k_zero, B, t_zero, 256, 0, st, (phase & PH_FORWARD) ? 1 : 0))) return r;
-        if ((r = launch("k_trace_centres", k_trace_centres, B, t_centre, CTA_C, 0, st))) return r;
-        if ((r = launch("k_centre_hist", k_centre_hist, B, t_centre, CTA_C, 0, st))) return r;
-        if ((r = launch("k_select_fit", k_select_fit, B, t_two_fit, SEL_NT, SEL_SMEM, st))) return r;
-        if ((r = launch("k_lin_sort", k_lin_sort, B, t_two_lin, LIN_NT, 0, st))) return r;
+        // S1-S5 (the forward's critical branch: on the high-priority side stream when the
+        // GP source, which only needs the latents and spectrum parameters, runs beside it
+        // on the caller's stream -- issued first, so that it starts at once)
+        const bool fork = (phase & PH_FORWARD) != 0;
+        const cudaStream_t sg = fork ? ss.s : st;
+        if (fork && (r = stream_after(ss.s, st, ss.fork))) return r;
+        if (fork)
+            for (int pass = 0; pass < GP_PASSES; ++pass)
+                if ((r = launch("k_gp_source", k_gp_lines<T>, B, t_gp_lines, GP_LINE_NT, 0, st, pass))) return r;
+        if ((r = launch("k_zero", k_zero, B, t_zero, 256, 0, sg, fork ? 1 : 0))) return r;
+        if ((r = launch("k_trace_centres", k_trace_centres, B, t_centre, CTA_C, 0, sg))) return r;
+        if ((r = launch("k_centre_hist", k_centre_hist, B, t_centre, CTA_C, 0, sg))) return r;
+        if ((r = launch("k_select_fit", k_select_fit, B, t_two_fit, SEL_NT, SEL_SMEM, sg))) return r;
+        if ((r = launch("k_lin_sort", k_lin_sort, B, t_two_lin, LIN_NT, 0, sg))) return r;
     }
     if (phase & PH_FORWARD) {
         if ((r = stream_after(st, ss.s, ss.join))) return r;
@@ -670,16 +680,20 @@ rtu_status run_chunk(Batch& B, int phase, cudaStream_t st, const SideStream& ss)
         if ((r = launch("k_render_adj", k_render_adj<T, false>, B, t_adj_fit, CTA_R, adj, st))) return r;
         if ((r = launch("k_render_adj", k_render_adj<T, true>, B, t_adj_lin, CTA_R, adj, st))) return r;
         if (any_sub && (r = launch("k_sub_adj", k_sub_adj<T>, B, t_adj, CTA_R, 0, st))) return r;
-        // transform and centre-ray adjoint (side) beside the cell gather and GP adjoint (main)
+        // transform and centre-ray adjoint (the critical branch, side streams: the
+        // selected-rank terms beside the centre rays) beside the cell gather and GP
+        // adjoint (main)
         if ((r = stream_after(ss.s, st, ss.fork))) return r;
         if ((r = launch("k_cdf_adj", k_cdf_adj, B, t_two_fit, CDF_NT, 0, ss.s))) return r;
+        if ((r = stream_after(ss.s2, ss.s, ss.fork2))) return r;
+        if ((r = launch("k_sel_adj", k_sel_adj, B, t_one_fit, SEL_ADJ_NT, 0, ss.s2))) return r;
         if ((r = launch("k_centre_adj", k_centre_adj<T>, B, t_centre_fit, CTA_C, 0, ss.s))) return r;
-        if ((r = launch("k_sel_adj", k_sel_adj, B, t_one_fit, SEL_ADJ_NT, 0, ss.s))) return r;
         if ((r = launch("k_lin_centre_adj", k_lin_centre_adj, B, t_centre_lin, CTA_C, 0, ss.s))) return r;
         if ((r = launch("k_cell_gather", k_cell_gather<T>, B, t_cells, GATHER_NT, 0, st))) return r;
         for (int pass = 0; pass < GP_PASSES; ++pass)
             if ((r = launch("k_gp_adjoint", k_gp_adj_lines<T>, B, t_gp_lines, GP_LINE_NT, 0, st, pass))) return r;
         if ((r = stream_after(st, ss.s, ss.join))) return r;
+        if ((r = stream_after(st, ss.s2, ss.join2))) return r;
         if ((r = launch("k_grad_final", k_grad_final, B, t_one, GRAD_NT, 0, st))) return r;
     }
     return RTU_OK;
@@ -700,6 +714,7 @@ rtu_status run(rtu_system* const* sys, const rtu_eval* ev, int n, int phase, voi
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     SideStream* ss = nullptr;
     if (rtu_status r = side_stream(ss)) return r;
+    if (g_prof_on) { g_side_hint[0] = ss->s; g_side_hint[1] = ss->s2; }
     static thread_local Batch B;
     for (int c0 = 0; c0 < n; c0 += MAXB) {
         B.n = std::min(MAXB, n - c0);
@@ -733,6 +748,34 @@ rtu_status rtu_profile_enable(int32_t on) {
     std::lock_guard<std::mutex> g(g_prof_mu);
     g_prof_on = on != 0;
     return RTU_OK;
+}
+
+rtu_status rtu_profile_timeline(char* buf, size_t bytes) {
+    std::lock_guard<std::mutex> g(g_prof_mu);
+    rtu_status rc = RTU_OK;
+    std::string out;
+    cudaEvent_t t0 = g_prof_pending.empty() ? nullptr : g_prof_pending.front().a;
+    for (ProfRec& p : g_prof_pending) {
+        float a = 0.f, b = 0.f;
+        if (cudaEventSynchronize(p.b) != cudaSuccess || cudaEventElapsedTime(&a, t0, p.a) != cudaSuccess ||
+            cudaEventElapsedTime(&b, t0, p.b) != cudaSuccess)
+            rc = fail(RTU_E_CUDA, "profile event failed");
+        char line[160];
+        snprintf(line, sizeof(line), "%s %d %.6f %.6f\n", p.name, p.side, a, b);
+        out += line;
+    }
+    for (ProfRec& p : g_prof_pending) {
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
+    }
+    g_prof_pending.clear();
+    g_prof_acc.clear();
+    if (buf && bytes) {
+        size_t n = std::min(bytes - 1, out.size());
+        memcpy(buf, out.data(), n);
+        buf[n] = 0;
+    }
+    return rc;
 }
 
 rtu_status rtu_profile_report(char* buf, size_t bytes) {

@@ -91,6 +91,8 @@ _lib.rtu_profile_enable.argtypes = [ctypes.c_int32]
 _lib.rtu_profile_enable.restype = ctypes.c_int32
 _lib.rtu_profile_report.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
 _lib.rtu_profile_report.restype = ctypes.c_int32
+_lib.rtu_profile_timeline.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
+_lib.rtu_profile_timeline.restype = ctypes.c_int32
 _lib.rtu_last_error.restype = ctypes.c_char_p
 _lib.rtu_version.restype = ctypes.c_char_p
 
@@ -98,7 +100,7 @@ EXPORTED = ("rtu_workspace_size", "rtu_system_create", "rtu_system_destroy", "rt
             "rtu_forward", "rtu_adjoint", "rtu_n_sites", "rtu_elbo_init", "rtu_elbo_step",
             "rtu_elbo_state_bytes", "rtu_elbo_export", "rtu_elbo_import", "rtu_gp_source_static",
             "rtu_profile_enable",
-            "rtu_profile_report", "rtu_last_error", "rtu_version")
+            "rtu_profile_report", "rtu_profile_timeline", "rtu_last_error", "rtu_version")
 
 
 def _check(rc: int, what: str):
@@ -122,6 +124,18 @@ def profile_report() -> dict:
     for line in buf.value.decode().splitlines():
         name, cnt, ms = line.split()
         out[name] = (int(cnt), float(ms))
+    return out
+
+
+def profile_timeline() -> list:
+    """[(kernel, stream, start_ms, end_ms)] of the recorded launches in launch order,
+    relative to the first one's start; stream 0 = the call's, 1 and 2 = the side streams."""
+    buf = ctypes.create_string_buffer(1 << 20)
+    _check(_lib.rtu_profile_timeline(buf, len(buf)), "rtu_profile_timeline")
+    out = []
+    for line in buf.value.decode().splitlines():
+        name, side, a, b = line.split()
+        out.append((name, int(side), float(a), float(b)))
     return out
 
 

@@ -300,3 +300,31 @@ def test_mixed_transforms_in_one_batch(rtu):
             F64_TOL, 10.0 * G.rounding_sensitivity(m, kind, LIN_POS_EPS[1]))
         assert G.rel_l2(b.g_lens.cpu().numpy(), o["g_lens"]) < tol
         assert G.rel_l2(b.g_latents.cpu().numpy(), o["g_latents"]) < F64_TOL
+
+
+def test_profile_timeline_covers_every_launch(rtu):
+    # tracing: each launch of a call appears once, on the call's stream or the side
+    # stream, with its end after its start; the per-kernel report counts the same
+    m = I.config_tiny(seed=81)
+    s = rtu.System.from_mock(m, precision=rtu.RTU_F32)
+    b = rtu.Binding(s, m.lens, m.latents, m.ps)
+    batch = rtu.Batch([b])
+    batch.forward()
+    batch.adjoint()
+    torch.cuda.synchronize()
+    rtu.profile_report()
+    rtu.profile_enable(True)
+    batch.forward()
+    batch.adjoint()
+    rtu.profile_enable(False)
+    tl = rtu.profile_timeline()
+    names = [t[0] for t in tl]
+    assert "k_render" in names and "k_render_adj" in names and "k_grad_final" in names
+    assert all(t[1] in (0, 1, 2) for t in tl) and any(t[1] == 1 for t in tl)
+    assert all(t[3] >= t[2] for t in tl) and tl[0][2] == 0.0
+    rtu.profile_enable(True)
+    batch.forward()
+    batch.adjoint()
+    rtu.profile_enable(False)
+    rep = rtu.profile_report()
+    assert sum(c for c, _ in rep.values()) == len(tl)
