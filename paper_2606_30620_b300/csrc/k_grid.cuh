@@ -22,6 +22,32 @@ __device__ __forceinline__ int beta_bin(double b, double lo, double scale) {
     return k < 0 ? 0 : (k >= HB ? HB - 1 : k);
 }
 
+// reduce the per-CTA centre sums: mean and range per axis.  Called by one whole
+// warp; lane l takes the CTAs t = l mod 32 in order, then a fixed shuffle tree, so
+// every call gets the same bits.  Lane 0 writes out6.
+__device__ __forceinline__ void centre_moments(const EvalArgs& E, double* out6) {
+    const int lane = threadIdx.x & 31;
+    double s0 = 0.0, s1 = 0.0, lo0 = 1e300, hi0 = -1e300, lo1 = 1e300, hi1 = -1e300;
+    for (int t = lane; t < E.n_cta_c; t += 32) {
+        const double* c = E.cpart + t * 8;          // written by other CTAs: read through L2
+        s0 += __ldcg(c); s1 += __ldcg(c + 1);
+        lo0 = fmin(lo0, __ldcg(c + 2)); hi0 = fmax(hi0, __ldcg(c + 3));
+        lo1 = fmin(lo1, __ldcg(c + 4)); hi1 = fmax(hi1, __ldcg(c + 5));
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        s0 += __shfl_down_sync(0xffffffffu, s0, o);
+        s1 += __shfl_down_sync(0xffffffffu, s1, o);
+        lo0 = fmin(lo0, __shfl_down_sync(0xffffffffu, lo0, o));
+        hi0 = fmax(hi0, __shfl_down_sync(0xffffffffu, hi0, o));
+        lo1 = fmin(lo1, __shfl_down_sync(0xffffffffu, lo1, o));
+        hi1 = fmax(hi1, __shfl_down_sync(0xffffffffu, hi1, o));
+    }
+    if (lane == 0) {
+        out6[0] = s0 / E.n_mask; out6[1] = s1 / E.n_mask;
+        out6[2] = lo0; out6[3] = hi0; out6[4] = lo1; out6[5] = hi1;
+    }
+}
+
 __global__ void __launch_bounds__(CTA_C) k_trace_centres(const __grid_constant__ Batch B) {
     const int ev = find_eval(B, blockIdx.x);
     const EvalArgs& E = B.e[ev];
@@ -79,32 +105,20 @@ __global__ void __launch_bounds__(CTA_C) k_trace_centres(const __grid_constant__
             r = q < 2 ? r + o : ((q & 1) == 0 ? fmin(r, o) : fmax(r, o));
         }
         E.cpart[tile * 8 + q] = r;
+        __threadfence();
     }
-}
-
-// reduce the per-CTA centre sums: mean and range per axis.  Called by one whole
-// warp; lane l takes the CTAs t = l mod 32 in order, then a fixed shuffle tree, so
-// every kernel that calls it gets the same bits.  Lane 0 writes out6.
-__device__ __forceinline__ void centre_moments(const EvalArgs& E, double* out6) {
-    const int lane = threadIdx.x & 31;
-    double s0 = 0.0, s1 = 0.0, lo0 = 1e300, hi0 = -1e300, lo1 = 1e300, hi1 = -1e300;
-    for (int t = lane; t < E.n_cta_c; t += 32) {
-        const double* c = E.cpart + t * 8;
-        s0 += c[0]; s1 += c[1];
-        lo0 = fmin(lo0, c[2]); hi0 = fmax(hi0, c[3]);
-        lo1 = fmin(lo1, c[4]); hi1 = fmax(hi1, c[5]);
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        s0 += __shfl_down_sync(0xffffffffu, s0, o);
-        s1 += __shfl_down_sync(0xffffffffu, s1, o);
-        lo0 = fmin(lo0, __shfl_down_sync(0xffffffffu, lo0, o));
-        hi0 = fmax(hi0, __shfl_down_sync(0xffffffffu, hi0, o));
-        lo1 = fmin(lo1, __shfl_down_sync(0xffffffffu, lo1, o));
-        hi1 = fmax(hi1, __shfl_down_sync(0xffffffffu, hi1, o));
-    }
-    if (lane == 0) {
-        out6[0] = s0 / E.n_mask; out6[1] = s1 / E.n_mask;
-        out6[2] = lo0; out6[3] = hi0; out6[4] = lo1; out6[5] = hi1;
+    // the last CTA of the evaluation to finish reduces the partials once (fixed order)
+    __shared__ int last;
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(E.ccnt, 1) == E.n_cta_c - 1;
+    __syncthreads();
+    if (last && threadIdx.x < 32) {
+        double m6[6];
+        centre_moments(E, m6);
+        if (threadIdx.x == 0) {
+            for (int q = 0; q < 6; ++q) E.mom[q] = m6[q];
+            E.ccnt[0] = 0;
+        }
     }
 }
 
@@ -118,15 +132,19 @@ __global__ void __launch_bounds__(CTA_C) k_centre_hist(const __grid_constant__ B
     const int tile = blockIdx.x - B.tile0[ev];
     __shared__ double m[6];
     __shared__ double red[2][CTA_C / 32];
-    if (threadIdx.x < 32) centre_moments(E, m);
+    if (threadIdx.x < 6) m[threadIdx.x] = __ldcg(E.mom + threadIdx.x);
     __syncthreads();
     const int k = tile * CTA_C + threadIdx.x;
     double d0 = 0.0, d1 = 0.0;
     if (k < E.n_mask) {
         double bx = E.beta[k], by = E.beta[E.n_mask + k];
         const int w = E.cwt ? (int)E.cwt[k] : 1;      // weighted grid: the ray counts w times
-        atomicAdd(E.hist + beta_bin(bx, m[2], bin_scale(m[2], m[3])), w);
-        atomicAdd(E.hist + HB + beta_bin(by, m[4], bin_scale(m[4], m[5])), w);
+        const int b0 = beta_bin(bx, m[2], bin_scale(m[2], m[3]));
+        const int b1 = beta_bin(by, m[4], bin_scale(m[4], m[5]));
+        atomicAdd(E.hist + b0, w);
+        atomicAdd(E.hist + HB + b1, w);
+        E.cbin[k] = b0;
+        E.cbin[E.n_mask + k] = b1;
         d0 = (bx - m[0]) * (bx - m[0]);
         d1 = (by - m[1]) * (by - m[1]);
     }
@@ -140,6 +158,27 @@ __global__ void __launch_bounds__(CTA_C) k_centre_hist(const __grid_constant__ B
         double r = 0.0;
         for (int i = 0; i < CTA_C / 32; ++i) r += red[threadIdx.x][i];
         E.cpart2[tile * 2 + threadIdx.x] = r;
+        __threadfence();
+    }
+    // the last CTA to finish: sums of squared deviations over the CTAs (lanes over
+    // CTAs, fixed tree), once per evaluation
+    __shared__ int last;
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(E.ccnt + 1, 1) == E.n_cta_c - 1;
+    __syncthreads();
+    if (last && threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        double v0 = 0.0, v1 = 0.0;
+        for (int t = lane; t < E.n_cta_c; t += 32) { v0 += __ldcg(E.cpart2 + 2 * t); v1 += __ldcg(E.cpart2 + 2 * t + 1); }
+        for (int o = 16; o > 0; o >>= 1) {
+            v0 += __shfl_down_sync(0xffffffffu, v0, o);
+            v1 += __shfl_down_sync(0xffffffffu, v1, o);
+        }
+        if (lane == 0) {
+            E.mom[6] = v0;
+            E.mom[7] = v1;
+            E.ccnt[1] = 0;
+        }
     }
 }
 
@@ -175,36 +214,31 @@ __global__ void __launch_bounds__(SEL_NT) k_select_fit(const __grid_constant__ B
     const int N = E.n_mask, M = E.n_nodes, D = E.degree, K = M + 2;
     const int W = E.wtot;                            // ranks of the (weight-expanded) sample
 
-    if (wid == 0) {
-        centre_moments(E, mom);
-        // sums of squared deviations: lanes over CTAs, fixed tree
-        double v0 = 0.0, v1 = 0.0;
-        for (int t = lane; t < E.n_cta_c; t += 32) { v0 += E.cpart2[2 * t]; v1 += E.cpart2[2 * t + 1]; }
-        for (int o = 16; o > 0; o >>= 1) {
-            v0 += __shfl_down_sync(0xffffffffu, v0, o);
-            v1 += __shfl_down_sync(0xffffffffu, v1, o);
-        }
-        if (lane == 0) {
-            double sx = sqrt(v0 / N), sy = sqrt(v1 / N);
-            sig[0] = sx <= sy ? sx : sy;            // sigma_min, tie -> x (App. C i)
-            sig[1] = sx <= sy ? 0.0 : 1.0;
-            sig[2] = 1.0 / sig[0];
-            flag_sh = 0;
-        }
+    if (tid < 6) mom[tid] = __ldcg(E.mom + tid);
+    if (tid == 0) {
+        const double sx = sqrt(__ldcg(E.mom + 6) / N), sy = sqrt(__ldcg(E.mom + 7) / N);
+        sig[0] = sx <= sy ? sx : sy;            // sigma_min, tie -> x (App. C i)
+        sig[1] = sx <= sy ? 0.0 : 1.0;
+        sig[2] = 1.0 / sig[0];
+        flag_sh = 0;
     }
     __syncthreads();
     const double sigma = sig[0], isig = sig[2];
     double* tr = E.trd;
     const int* hist = E.hist + a * HB;
     const double* beta = E.beta + a * N;
-    const double lo = mom[2 + 2 * a], hi = mom[3 + 2 * a];
-    const double scale = bin_scale(lo, hi);
-    // row sums: warp w reads its 64 rows of 32 bins coalesced
+    const double lo = mom[2 + 2 * a];
+    // row sums: warp w reads its 64 rows of 32 bins coalesced, 8 loads in flight
     constexpr int RPW = SEL_ROWS / (SEL_NT / 32);
-    for (int i = 0; i < RPW; ++i) {
-        const int row = wid * RPW + i;
-        const int sum = __reduce_add_sync(0xffffffffu, hist[row * 32 + lane]);
-        if (lane == 0) rowoff[row] = sum;
+    for (int i = 0; i < RPW; i += 8) {
+        int v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = hist[(wid * RPW + i + u) * 32 + lane];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int sum = __reduce_add_sync(0xffffffffu, v[u]);
+            if (lane == 0) rowoff[wid * RPW + i + u] = sum;
+        }
     }
     for (int i = tid; i < 2 * MAXM; i += SEL_NT) { d_fill[i] = 0; d_num[i] = 0; }
     for (int i = tid; i < HB / 32; i += SEL_NT) bitmap[i] = 0u;
@@ -277,25 +311,33 @@ __global__ void __launch_bounds__(SEL_NT) k_select_fit(const __grid_constant__ B
         }
     }
     __syncthreads();
-    if (tid == 0) {
-        // distinct target bins (ranks are non-decreasing, so are their bins)
-        int nd = 0;
-        for (int t = 0; t < nt; ++t) {
-            if (nd == 0 || d_bin[nd - 1] != t_bin[t]) {
-                d_bin[nd] = t_bin[t];
-                bitmap[t_bin[t] >> 5] |= 1u << (t_bin[t] & 31);
-                ++nd;
+    if (wid == 0) {
+        // distinct target bins (ranks are non-decreasing, so are their bins): a new bin
+        // where it differs from the previous target's; slots by a running ballot count
+        int base = 0;
+        for (int t0 = 0; t0 < nt; t0 += 32) {
+            const int t = t0 + lane;
+            const bool isnew = t < nt && (t == 0 || t_bin[t] != t_bin[t - 1]);
+            const unsigned nb = __ballot_sync(0xffffffffu, isnew);
+            const int slot = base + __popc(nb & ((2u << lane) - 1u)) - 1;
+            if (t < nt) {
+                t_slot[t] = slot;
+                if (isnew) {
+                    d_bin[slot] = t_bin[t];
+                    atomicOr(&bitmap[t_bin[t] >> 5], 1u << (t_bin[t] & 31));
+                }
             }
-            t_slot[t] = nd - 1;
+            base += __popc(nb);
         }
-        n_d = nd;
+        if (lane == 0) n_d = base;
     }
     for (int t = tid; t < nt; t += SEL_NT) selv[t] = lo;     // overwritten by the selection
     __syncthreads();
     const int nd = n_d;
     // candidates of the target bins: count them per bin, offsets, then gather
+    const int* cbin = E.cbin + (size_t)a * N;    // the bins k_centre_hist used
     for (int k = tid; k < N; k += SEL_NT) {
-        const int bn = beta_bin(beta[k], lo, scale);
+        const int bn = cbin[k];
         if (bitmap[bn >> 5] & (1u << (bn & 31))) {
             int d = 0;
             while (d < nd - 1 && d_bin[d] != bn) ++d;
@@ -311,9 +353,9 @@ __global__ void __launch_bounds__(SEL_NT) k_select_fit(const __grid_constant__ B
     }
     __syncthreads();
     for (int k = tid; k < N; k += SEL_NT) {
-        const double b = beta[k];
-        const int bn = beta_bin(b, lo, scale);
+        const int bn = cbin[k];
         if (bitmap[bn >> 5] & (1u << (bn & 31))) {
+            const double b = beta[k];
             int d = 0;
             while (d < nd - 1 && d_bin[d] != bn) ++d;
             const int pos = atomicAdd(&d_fill[d], 1);
@@ -328,11 +370,11 @@ __global__ void __launch_bounds__(SEL_NT) k_select_fit(const __grid_constant__ B
     __syncthreads();
     // the element covering rank (r - below) of its bin: candidates ordered by
     // (value, index), each covering as many ranks as its weight
-    for (int t = 0; t < nt; ++t) {
+    for (int t = wid; t < nt; t += SEL_NT / 32) {
         const int d = t_slot[t];
         const int o = d_off[d], cnt = min(d_off[d + 1], SEL_CAP) - o;
         const int want = t_rank[t] - t_below[t];
-        for (int c = tid; c < cnt; c += SEL_NT) {
+        for (int c = lane; c < cnt; c += 32) {
             const double kc = ck[o + c];
             const int ic = ci[o + c];
             int rank = 0;
@@ -348,6 +390,13 @@ __global__ void __launch_bounds__(SEL_NT) k_select_fit(const __grid_constant__ B
     }
     __syncthreads();
 
+    // the Chebyshev tables of the fit in shared memory (the candidates are done with)
+    const double* cb = E.cheb;
+    if (cheb_size(M, D) <= SEL_CAP) {
+        for (int i = tid; i < cheb_size(M, D); i += SEL_NT) ck[i] = E.cheb[i];
+        __syncthreads();
+        cb = ck;
+    }
     if (E.transform == RTU_TRANSFORM_UNIFORM) {
         // uniform grid: the smallest square box around the masked rays, centred on
         // each axis's range, mapped affinely onto [0, 1]^2 -- written as Hermite
@@ -358,7 +407,7 @@ __global__ void __launch_bounds__(SEL_NT) k_select_fit(const __grid_constant__ B
         const double mn = mom[2 + 2 * a], mx = mom[3 + 2 * a];
         const double lo_a = 0.5 * (mn + mx) - 0.5 * L;
         for (int j = tid; j < K; j += SEL_NT) {
-            const double U = j == 0 ? 0.0 : (j == K - 1 ? 1.0 : E.cheb[cheb_u(M, D) + j - 1]);
+            const double U = j == 0 ? 0.0 : (j == K - 1 ? 1.0 : cb[cheb_u(M, D) + j - 1]);
             const double X = (lo_a + U * L - mom[a]) * isig;
             tr[TR_HDR + a * K + j] = X;
             tr[TR_HDR + (6 + a) * K + j] = X;
@@ -372,7 +421,7 @@ __global__ void __launch_bounds__(SEL_NT) k_select_fit(const __grid_constant__ B
     } else {
         // empirical QF at the nodes in standardized coordinates (type-7 interpolation)
         for (int j = tid; j < M; j += SEL_NT) {
-            const double h = E.cheb[cheb_u(M, D) + j] * (W - 1);
+            const double h = cb[cheb_u(M, D) + j] * (W - 1);
             const double frac = h - floor(h);
             const double zl = (selv[2 * j] - mom[a]) * isig;
             const double zh = (selv[2 * j + 1] - mom[a]) * isig;
@@ -381,7 +430,7 @@ __global__ void __launch_bounds__(SEL_NT) k_select_fit(const __grid_constant__ B
         __syncthreads();
         // App. C iii: Chebyshev coefficients of the QF from M = D+1 nodes by the
         // discrete orthogonality of T_k on the nodes: c = C Q (one thread per coefficient)
-        const double* Ct = E.cheb + cheb_C(M, D);
+        const double* Ct = cb + cheb_C(M, D);
         for (int k = tid; k <= D; k += SEL_NT) {
             double sacc = 0.0;
             for (int j = 0; j < M; ++j) sacc += Ct[k * M + j] * Qs[j];
@@ -390,8 +439,8 @@ __global__ void __launch_bounds__(SEL_NT) k_select_fit(const __grid_constant__ B
         __syncthreads();
         // App. C iv: knots p(0), p(u_j), p(1) and p'(u) there (one thread per point),
         // the slope floor of the guard and the slopes 1/p' (per point)
-        const double* Vt = E.cheb + cheb_V(M, D);
-        const double* dVt = E.cheb + cheb_dV(M, D);
+        const double* Vt = cb + cheb_V(M, D);
+        const double* dVt = cb + cheb_dV(M, D);
         for (int j = tid; j < K; j += SEL_NT) {
             double p = 0.0, d = 0.0;
             for (int k = 0; k <= D; ++k) {
@@ -479,20 +528,11 @@ __global__ void __launch_bounds__(LIN_NT) k_lin_sort(const __grid_constant__ Bat
     __shared__ double mom[6];
     __shared__ double sig[2];
     __shared__ int wtot[LIN_NT / 32];
-    if (tid < 32) {
-        centre_moments(E, mom);
-        const int lane = tid;
-        double v0 = 0.0, v1 = 0.0;
-        for (int t = lane; t < E.n_cta_c; t += 32) { v0 += E.cpart2[2 * t]; v1 += E.cpart2[2 * t + 1]; }
-        for (int o = 16; o > 0; o >>= 1) {
-            v0 += __shfl_down_sync(0xffffffffu, v0, o);
-            v1 += __shfl_down_sync(0xffffffffu, v1, o);
-        }
-        if (lane == 0) {
-            const double sx = sqrt(v0 / N), sy = sqrt(v1 / N);
-            sig[0] = sx <= sy ? sx : sy;            // sigma_min, tie -> x (App. C i)
-            sig[1] = sx <= sy ? 0.0 : 1.0;
-        }
+    if (tid < 6) mom[tid] = __ldcg(E.mom + tid);
+    if (tid == 0) {
+        const double sx = sqrt(__ldcg(E.mom + 6) / N), sy = sqrt(__ldcg(E.mom + 7) / N);
+        sig[0] = sx <= sy ? sx : sy;            // sigma_min, tie -> x (App. C i)
+        sig[1] = sx <= sy ? 0.0 : 1.0;
     }
     __syncthreads();
     int* h = E.hist + a * HB;
@@ -526,13 +566,13 @@ __global__ void __launch_bounds__(LIN_NT) k_lin_sort(const __grid_constant__ Bat
         }
     }
     __syncthreads();
-    // scatter through the bin cursors (the same bin expression as k_centre_hist)
+    // scatter through the bin cursors (the bins k_centre_hist used)
     const double lo = mom[2 + 2 * a], sc = bin_scale(mom[2 + 2 * a], mom[3 + 2 * a]);
     double* key = E.lkey + (size_t)a * N;
     int* idx = E.lidx + (size_t)a * N;
     for (int i = tid; i < N; i += LIN_NT) {
         const double b = E.beta[(size_t)a * N + i];
-        const int pos = atomicAdd(h + beta_bin(b, lo, sc), 1);
+        const int pos = atomicAdd(h + E.cbin[(size_t)a * N + i], 1);
         if (pos < N) { key[pos] = b; idx[pos] = i; }
     }
     __syncthreads();

@@ -111,6 +111,9 @@ size_t slot_layout(const rtu_system_desc& d, char* base, EvalArgs* e) {
     p = take((size_t)2 * z.nm_max * 8);               if (e) e->beta = (double*)p;
     p = take((size_t)z.n_cta_c_max * 8 * 8);          if (e) e->cpart = (double*)p;
     p = take((size_t)z.n_cta_c_max * 2 * 8);          if (e) e->cpart2 = (double*)p;
+    p = take(8 * 8);                                  if (e) e->mom = (double*)p;
+    p = take(16);                                     if (e) e->ccnt = (int*)p;
+    p = take((size_t)2 * z.nm_max * 4);               if (e) e->cbin = (int*)p;
     p = take((size_t)(z.n_cta_c_max + 1) * z.nl * 8); if (e) e->cadj = (double*)p;
     p = take((size_t)2 * HB * 4);                     if (e) e->hist = (int*)p;
     p = take((size_t)tr_size(z.K) * 8);               if (e) e->trd = (double*)p;
@@ -337,7 +340,7 @@ __global__ void __launch_bounds__(256) k_zero(const __grid_constant__ Batch B, i
         if (i < nh) E.hist[i] = 0; else E.ccount[i - nh] = 0;
     }
     if (tile == 0) {
-        if (threadIdx.x == 0) { *E.flags = 0; *E.ecount = 0; }
+        if (threadIdx.x == 0) { *E.flags = 0; *E.ecount = 0; E.ccnt[0] = 0; E.ccnt[1] = 0; }
         const int nsub = E.sub_kind ? E.n_sub : 0;
         lens_setup_par(reinterpret_cast<LensK<double>*>(E.lensk),
                        reinterpret_cast<LensK<float>*>(static_cast<char*>(E.lensk) + LENSK_D_BYTES), E.lens,

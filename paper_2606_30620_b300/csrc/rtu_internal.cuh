@@ -66,6 +66,11 @@ struct EvalArgs {
     double* beta;      // [2][n_mask] traced centre rays (double)
     double* cpart;     // [n_cta_c][8] centre partial sums and ranges of beta
     double* cpart2;    // [n_cta_c][2] sum of squared deviations
+    double* mom;       // [8] of the centre rays: mean x, y; min x, max x; min y, max y;
+                       // sum of squared deviations x, y (each written once per call by the
+                       // last CTA of k_trace_centres / k_centre_hist to finish)
+    int* ccnt;         // [2] CTA-completion counters of those two kernels
+    int* cbin;         // [2][n_mask] level-1 histogram bin of each centre ray
     double* cadj;      // [n_cta_c][8 + 5 n_sub] centre-ray adjoint lens partials
     int* hist;         // [2][HB] level-1 histograms
     double* trd;       // transform, double (layout in tr_* helpers)
