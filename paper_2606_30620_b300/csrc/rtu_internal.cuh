@@ -314,45 +314,57 @@ __device__ inline void lens_rest(LensK<T>& K, const double* lens, int profile, i
 // roundoff or less, as |c_n| <= f <= 1/4), by one thread.
 __device__ inline void lens_setup_par(LensK<double>* Kd, LensK<float>* Kf, const double* lens, int profile, int sub_kind,
                                int n_sub) {
-    __shared__ double sc[EPL_MAXT], sg[EPL_MAXT], sdl[EPL_MAXT], sconst[4];
-    if (threadIdx.x == 0) {
+    // Called by all threads of a CTA of at least 160.  Warps 0-2 build the series
+    // coefficients (term n by thread n - 1: the products A_n = c_1 ... c_n and the sums
+    // D_n by warp scans, synchronised among themselves by a named barrier); meanwhile
+    // one thread of warp 3 computes the double lens scalars and one of warp 4 the float
+    // ones, so the serial FP64 chains of the two run side by side.
+    __shared__ double sconst[2], wA[3], wD[3];
+    __shared__ int nt_sh[2];
+    const int tid = threadIdx.x;
+    if (tid == 0) {
         const double cc = sqrt(fmax(lens[2] * lens[2] + lens[3] * lens[3], 1e-30));
         const double q = (1.0 - cc) / (1.0 + cc);
         sconst[0] = (1.0 - q) / (1.0 + q);
         sconst[1] = (profile == 1 ? lens[1] : 2.0) - 1.0;
+        nt_sh[0] = EPL_MAXT;
+        nt_sh[1] = EPL_MAXT;
     }
     __syncthreads();
-    const double f = sconst[0], t = sconst[1];
-    for (int n = threadIdx.x + 1; n <= EPL_MAXT; n += blockDim.x) {
+    const double p[6] = {lens[0], lens[1], lens[2], lens[3], lens[4], lens[5]};
+    if (tid == 96) {
+        epl_scalars(Kd->C, p, profile == 1);
+        lens_rest(*Kd, lens, profile, sub_kind, n_sub);
+    } else if (tid == 128) {
+        epl_scalars(Kf->C, p, profile == 1);
+        lens_rest(*Kf, lens, profile, sub_kind, n_sub);
+    } else if (tid < 96) {
+        const int lane = tid & 31, w = tid >> 5, n = tid + 1;
+        const double f = sconst[0], t = sconst[1];
         const double g = -(2.0 * n - 2.0 + t) / (2.0 * n + 2.0 - t);
-        sg[n - 1] = g;
-        sc[n - 1] = f * g;
-        sdl[n - 1] = 1.0 / (2.0 * n - 2.0 + t) + 1.0 / (2.0 * n + 2.0 - t);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0 || threadIdx.x == 32) {
-        const bool dbl = threadIdx.x == 0;
-        const double p[6] = {lens[0], lens[1], lens[2], lens[3], lens[4], lens[5]};
-        const double tol = dbl ? 1e-16 : 2e-8;
-        // scalars through the shared definition, then the coefficient tables
-        double A = 1.0, D = 0.0;
-        int nt = EPL_MAXT;
-        if (dbl) epl_term0(Kd->C.term[0]); else epl_term0(Kf->C.term[0]);
-        for (int n = 1; n <= EPL_MAXT; ++n) {
-            D += sdl[n - 1];
-            if (dbl) epl_term(Kd->C.term[n], n, A, sc[n - 1], sg[n - 1], D);
-            else epl_term(Kf->C.term[n], n, A, sc[n - 1], sg[n - 1], D);
-            A *= sc[n - 1];
-            if (fabs(A) <= tol) { nt = n; break; }
+        const double c = f * g;
+        const double dl = 1.0 / (2.0 * n - 2.0 + t) + 1.0 / (2.0 * n + 2.0 - t);
+        // inclusive warp scans: A = product of c, D = sum of dl
+        double A = c, D = dl;
+        for (int o = 1; o < 32; o <<= 1) {
+            const double a2 = __shfl_up_sync(0xffffffffu, A, o), d2 = __shfl_up_sync(0xffffffffu, D, o);
+            if (lane >= o) { A *= a2; D += d2; }
         }
-        if (dbl) {
-            epl_scalars(Kd->C, p, profile == 1);
-            Kd->C.nterm = nt;
-            lens_rest(*Kd, lens, profile, sub_kind, n_sub);
-        } else {
-            epl_scalars(Kf->C, p, profile == 1);
-            Kf->C.nterm = nt;
-            lens_rest(*Kf, lens, profile, sub_kind, n_sub);
+        if (lane == 31) { wA[w] = A; wD[w] = D; }
+        asm volatile("bar.sync 1, 96;" ::: "memory");
+        for (int v = 0; v < w; ++v) { A *= wA[v]; D += wD[v]; }
+        double Ap = __shfl_up_sync(0xffffffffu, A, 1);          // A_{n-1}
+        if (lane == 0) Ap = w == 0 ? 1.0 : wA[0] * (w == 2 ? wA[1] : 1.0);
+        epl_term(Kd->C.term[n], n, Ap, c, g, D);
+        epl_term(Kf->C.term[n], n, Ap, c, g, D);
+        if (tid == 0) { epl_term0(Kd->C.term[0]); epl_term0(Kf->C.term[0]); }
+        const double An = fabs(Ap * c);
+        if (An <= 1e-16) atomicMin(&nt_sh[0], n);
+        if (An <= 2e-8) atomicMin(&nt_sh[1], n);
+        asm volatile("bar.sync 1, 96;" ::: "memory");
+        if (tid == 0) {
+            Kd->C.nterm = nt_sh[0];
+            Kf->C.nterm = nt_sh[1];
         }
     }
 }
