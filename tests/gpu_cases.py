@@ -95,13 +95,19 @@ def rounding_sensitivity(m, transform, eps, reps=2, seed=0):
     ray's gradient between the two observations of its segment by
     t = (beta - x_k)/(x_{k+1} - x_k), and segments can be narrower than 1e-9 arcsec,
     so its lens gradient is sensitive at that level (a property of the map, shared by
-    any implementation)."""
+    any implementation).  Each trial also moves every lens parameter by +-eps of its
+    size: two implementations round the lens constants (axis ratio, position angle,
+    ...) differently, and that error is the same for every ray, which independent
+    position errors do not cover."""
+    import copy
     base = run_oracle(m, transform=transform)["g_lens"]
     trace0 = O.trace
     rng = np.random.default_rng(seed)
     worst = 0.0
     try:
         for _ in range(reps):
+            mp = copy.copy(m)
+            mp.lens = m.lens * (1.0 + eps * rng.choice([-1.0, 1.0], size=m.lens.shape))
             def trace_rounded(x, y, *a, **k):
                 bx, by = trace0(x, y, *a, **k)
                 sx = torch.tensor(rng.choice([-1.0, 1.0], size=bx.shape), dtype=bx.dtype)
@@ -110,7 +116,7 @@ def rounding_sensitivity(m, transform, eps, reps=2, seed=0):
                 my = by.detach().abs() + y.detach().abs()
                 return bx + eps * mx * sx, by + eps * my * sy
             O.trace = trace_rounded
-            worst = max(worst, rel_l2(run_oracle(m, transform=transform)["g_lens"], base))
+            worst = max(worst, rel_l2(run_oracle(mp, transform=transform)["g_lens"], base))
     finally:
         O.trace = trace0
     return worst
