@@ -323,9 +323,8 @@ __device__ inline void lens_setup_par(LensK<double>* Kd, LensK<float>* Kf, const
     __shared__ int nt_sh[2];
     const int tid = threadIdx.x;
     if (tid == 0) {
-        const double cc = sqrt(fmax(lens[2] * lens[2] + lens[3] * lens[3], 1e-30));
-        const double q = (1.0 - cc) / (1.0 + cc);
-        sconst[0] = (1.0 - q) / (1.0 + q);
+        // f = (1 - q)/(1 + q) with q = (1 - c)/(1 + c) is c itself
+        sconst[0] = sqrt(fmax(lens[2] * lens[2] + lens[3] * lens[3], 1e-30));
         sconst[1] = (profile == 1 ? lens[1] : 2.0) - 1.0;
         nt_sh[0] = EPL_MAXT;
         nt_sh[1] = EPL_MAXT;
@@ -341,9 +340,10 @@ __device__ inline void lens_setup_par(LensK<double>* Kd, LensK<float>* Kf, const
     } else if (tid < 96) {
         const int lane = tid & 31, w = tid >> 5, n = tid + 1;
         const double f = sconst[0], t = sconst[1];
-        const double g = -(2.0 * n - 2.0 + t) / (2.0 * n + 2.0 - t);
+        const double r1 = 1.0 / (2.0 * n - 2.0 + t), r2 = 1.0 / (2.0 * n + 2.0 - t);
+        const double g = -(2.0 * n - 2.0 + t) * r2;
         const double c = f * g;
-        const double dl = 1.0 / (2.0 * n - 2.0 + t) + 1.0 / (2.0 * n + 2.0 - t);
+        const double dl = r1 + r2;
         // inclusive warp scans: A = product of c, D = sum of dl
         double A = c, D = dl;
         for (int o = 1; o < 32; o <<= 1) {
