@@ -215,8 +215,8 @@ __device__ __forceinline__ void gp_setup(const EvalArgs& E, Cx<T>* tw_s, int* re
 }
 
 // S6 spread over many CTAs: the source's 2-D FFTs as passes of 1-D line FFTs
-// (GP_LINES lines of one evaluation per CTA), computed in double in both
-// precisions.  Near f = 0 the softplus turns an absolute error of f into a relative
+// (GP_LINES lines of one evaluation per CTA), computed in FP64-class arithmetic in
+// both precisions (double-float for a float source).  Near f = 0 the softplus turns an absolute error of f into a relative
 // error of s* amplified by 1/s0 = 100, and a float FFT's absolute error (~1e-7 of
 // max |f|) reaches the gradients at their 1e-5 tolerance; one CTA per evaluation
 // in double would leave the FP64 pipe of a single SM doing the whole transform.
@@ -253,9 +253,19 @@ __device__ __forceinline__ void lines_to_digit_reversed(Cx<T>* sm, int cnt, int 
     __syncthreads();
 }
 
+// the arithmetic type of the source's transforms: double-float on the FP32 pipes for
+// a float source (about 48 bits; the FP64 pipe is shared with the grid build's FP64
+// set-up running beside it), double for a double source
+template <typename TS> struct gp_src_type { typedef DF type; };
+template <> struct gp_src_type<double> { typedef double type; };
+__device__ __forceinline__ float gp_store(const DF& v, float) { return v.hi; }   // hi is the rounded value
+__device__ __forceinline__ double gp_store(double v, double) { return v; }
+__device__ __forceinline__ DF gp_sqrt(const DF& v) { return r_sqrt(v); }
+__device__ __forceinline__ double gp_sqrt(double v) { return sqrt(v); }
+
 template <typename TS>
 __global__ void __launch_bounds__(GP_LINE_NT) k_gp_lines(const __grid_constant__ Batch B, int pass) {
-    typedef double T;
+    typedef typename gp_src_type<TS>::type T;
     const int ev = find_eval(B, blockIdx.x);
     const EvalArgs& E = B.e[ev];
     const int tile = blockIdx.x - B.tile0[ev];
@@ -297,18 +307,18 @@ __global__ void __launch_bounds__(GP_LINE_NT) k_gp_lines(const __grid_constant__
         C2* Wk = reinterpret_cast<C2*>(E.cbufB);
         const int nf = n_family(E.family);
         T psv[4], pc[1];
-        for (int q = 0; q < nf; ++q) psv[q] = E.ps[q];
+        for (int q = 0; q < nf; ++q) psv[q] = T(E.ps[q]);
         sqrtP_consts<T>(E.family, psv, pc);
-        const T kscale = 2.0 * 3.14159265358979323846 / E.pitch;
+        const T kscale = T(2.0 * 3.14159265358979323846 / E.pitch);
         for (int i = threadIdx.x; i < cnt * n; i += blockDim.x) {
             const int p = i / cnt, q = i - p * cnt;
             const T fx = fftfreq<T>(l0 + q, n), fy = fftfreq<T>(p, n);
-            const T k = kscale * sqrt(fx * fx + fy * fy);
+            const T k = kscale * gp_sqrt(fx * fx + fy * fy);
             const T sp = sqrtP_only<T>(E.family, psv, pc, k);
             const Cx<T> v = sm[q * n + p];
             C2 wv;
-            wv.x = (TS)v.x;
-            wv.y = (TS)v.y;
+            wv.x = gp_store(v.x, TS(0));
+            wv.y = gp_store(v.y, TS(0));
             Wk[p * n + l0 + q] = wv;
             sm[q * n + p] = Cx<T>{v.x * sp, v.y * sp};
         }
@@ -325,15 +335,15 @@ __global__ void __launch_bounds__(GP_LINE_NT) k_gp_lines(const __grid_constant__
     // already accurate, and the softplus of an accurately rounded argument is too)
     const int nf = n_family(E.family);
     const TS alpha = (TS)E.ps[nf];
-    const T inv_n2 = 1.0 / ((T)n * n);
+    const T inv_n2 = T(1.0 / ((double)n * n));
     TS* fld = reinterpret_cast<TS*>(E.fld);
     TS* src = reinterpret_cast<TS*>(E.src);
     TS* so = reinterpret_cast<TS*>(E.source_out);
     for (int i = threadIdx.x; i < cnt * n; i += blockDim.x) {
         const int q = i / n, p = i - q * n;
         const T f = sm[q * n + p].x * inv_n2;
-        const TS fs = (TS)f;
-        const TS sv = r_exp(alpha * log_sp_s0<TS>((TS)(f / 0.01)));
+        const TS fs = gp_store(f, TS(0));
+        const TS sv = r_exp(alpha * log_sp_s0<TS>(gp_store(f * T(100.0), TS(0))));
         const int at = (l0 + q) * n + p;
         fld[at] = fs;
         src[at] = sv;
