@@ -635,20 +635,20 @@ rtu_status run_chunk(Batch& B, int phase, cudaStream_t st, const SideStream& ss)
     }
     const size_t grid_bytes = align_up((size_t)max_n2 * sizeof(T), 128);
     if (phase & (PH_GRID | PH_FORWARD)) {
-        // S1-S5 (the forward's critical branch: on the high-priority side stream when the
-        // GP source, which only needs the latents and spectrum parameters, runs beside it
-        // on the caller's stream -- issued first, so that it starts at once)
+        // S1-S5 (the forward's critical branch: on the high-priority side stream, issued
+        // first, when the GP source, which only needs the latents and spectrum
+        // parameters, runs beside it on the caller's stream)
         const bool fork = (phase & PH_FORWARD) != 0;
         const cudaStream_t sg = fork ? ss.s : st;
         if (fork && (r = stream_after(ss.s, st, ss.fork))) return r;
-        if (fork)
-            for (int pass = 0; pass < GP_PASSES; ++pass)
-                if ((r = launch("k_gp_source", k_gp_lines<T>, B, t_gp_lines, GP_LINE_NT, 0, st, pass))) return r;
         if ((r = launch("k_zero", k_zero, B, t_zero, 256, 0, sg, fork ? 1 : 0))) return r;
         if ((r = launch("k_trace_centres", k_trace_centres, B, t_centre, CTA_C, 0, sg))) return r;
         if ((r = launch("k_centre_hist", k_centre_hist, B, t_centre, CTA_C, 0, sg))) return r;
         if ((r = launch("k_select_fit", k_select_fit, B, t_two_fit, SEL_NT, SEL_SMEM, sg))) return r;
         if ((r = launch("k_lin_sort", k_lin_sort, B, t_two_lin, LIN_NT, 0, sg))) return r;
+        if (fork)
+            for (int pass = 0; pass < GP_PASSES; ++pass)
+                if ((r = launch("k_gp_source", k_gp_lines<T>, B, t_gp_lines, GP_LINE_NT, 0, st, pass))) return r;
     }
     if (phase & PH_FORWARD) {
         if ((r = stream_after(st, ss.s, ss.join))) return r;
