@@ -53,11 +53,11 @@ FLOPS_ADJ_RAY = 2.5 * FLOPS_FWD_RAY
 # them in the grid), valid for the kernel sources with digest TRAFFIC_SRC_DIGEST.
 ROOF = {
     "k_render": {"flops_per_unit": FLOPS_FWD_RAY, "units": "supersampled rays",
-                 "traffic_per_unit": (0.413952e6 + 6400) / 5120000},
+                 "traffic_per_unit": (0.413184e6 + 2304) / 5120000},
     "k_render_adj": {"flops_per_unit": FLOPS_ADJ_RAY, "units": "in-grid rays",
-                     "traffic_per_unit": (6.836992e6 + 51456) / 743894},
+                     "traffic_per_unit": (6.835968e6 + 49408) / 743894},
 }
-TRAFFIC_SRC_DIGEST = "be08905950fc790e"
+TRAFFIC_SRC_DIGEST = "bf73078ba7a128cf"
 KERNEL_SOURCES = ("k_render.cuh", "rtu_internal.cuh", "rtu_math.cuh", "rtu_df.cuh")
 
 
