@@ -1156,12 +1156,31 @@ __global__ void __launch_bounds__(GATHER_NT) k_cell_gather(const __grid_constant
         l2 += (T(1) - fx) * gy1;
         l3 += fx * gy1;
     }
+    // The four warp sums by a transposing butterfly (compensated pairs in the float
+    // path): at xor 16 the lower half keeps corners 0, 1 and the upper half 2, 3, at
+    // xor 8 each quarter keeps one corner, then three levels on that one pair -- 12
+    // shuffles of pairs instead of 40.  Lanes 0, 8, 16, 24 store corners 0..3; the
+    // order of operations is fixed, so the sums are the same from run to run.
     typedef typename real2_of<T>::type TP;
-    const TP c0 = warp_pair_sum(l0), c1 = warp_pair_sum(l1), c2 = warp_pair_sum(l2), c3 = warp_pair_sum(l3);
-    if (lane == 0) {
-        TP* c = reinterpret_cast<TP*>(E.corner) + (size_t)cell * 4;
-        c[0] = c0; c[1] = c1; c[2] = c2; c[3] = c3;
+    auto pr = [](T v) { TP p; p.x = v; p.y = T(0); return p; };
+    auto xs = [](TP p, int o) {
+        TP q;
+        q.x = __shfl_xor_sync(0xffffffffu, p.x, o);
+        q.y = __shfl_xor_sync(0xffffffffu, p.y, o);
+        return q;
+    };
+    const bool up = lane & 16;
+    TP k0 = pr(up ? l2 : l0), k1 = pr(up ? l3 : l1);
+    {
+        const TP s0 = xs(pr(up ? l0 : l2), 16), s1 = xs(pr(up ? l1 : l3), 16);
+        pair_add(k0, s0);
+        pair_add(k1, s1);
     }
+    const bool hi8 = lane & 8;
+    TP k = hi8 ? k1 : k0;
+    pair_add(k, xs(hi8 ? k0 : k1, 8));
+    for (int o = 4; o > 0; o >>= 1) pair_add(k, xs(k, o));
+    if ((lane & 7) == 0) reinterpret_cast<TP*>(E.corner)[(size_t)cell * 4 + (lane >> 3)] = k;
 }
 
 }  // namespace rtu
