@@ -1,6 +1,7 @@
 // k_psf.cuh -- S8: PSF convolution ('same', zero padding) fused with the
 // Gaussian residual and the likelihood partial sums (Sec. 3.1, Sec. 4); its
-// adjoint (correlation with the PSF); the per-evaluation final reductions.
+// adjoint (correlation with the PSF); the per-evaluation final reductions (by the
+// likelihood kernel's last CTA).
 #pragma once
 #include "rtu_internal.cuh"
 
@@ -9,6 +10,58 @@ namespace rtu {
 constexpr int PSF_NT = PSF_T * PSF_T / 4;   // each thread: 4 horizontally adjacent outputs
 constexpr int PSF_MAXK = 31;
 constexpr int PSF_IN = PSF_T + PSF_MAXK - 1;
+
+__device__ __forceinline__ double warp_rows_sum_cg(const double* a, int rows, size_t stride) {
+    const int lane = threadIdx.x & 31;
+    double s = 0.0;
+    for (int t = lane; t < rows; t += 32) s += __ldcg(a + (size_t)t * stride);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    return __shfl_sync(0xffffffffu, s, 0);
+}
+
+// The end of the forward, run by the last CTA of the likelihood kernel to finish
+// (any block of at least 64 threads): log L = -1/2 sum r^2 - N log(sigma sqrt(2 pi)),
+// chi^2_img = sum_mask r^2 / N_mask, N_in_grid, flags, the ray histogram.  The per-tile
+// partials were written by the other CTAs: read through L2.
+__device__ void like_final_cta(const EvalArgs& E) {
+    __shared__ int red_i[32];
+    __shared__ double sums[2];
+    int cnt = 0;
+    for (int t = threadIdx.x; t < E.n_cta_r; t += blockDim.x) cnt += __ldcg(E.cta_cnt + t);
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, o);
+    if ((threadIdx.x & 31) == 0) red_i[threadIdx.x >> 5] = cnt;
+    // the per-tile sums of r^2 (all pixels) and of r^2 in the mask: warps 0 and 1,
+    // lane-strided, fixed tree
+    if (threadIdx.x < 64) {
+        const double v = warp_rows_sum_cg(E.lpart + (threadIdx.x >> 5), E.n_cta_p, 2);
+        if ((threadIdx.x & 31) == 0) sums[threadIdx.x >> 5] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && E.stats) {
+        int tot = 0;
+        for (int w = 0; w < (int)(blockDim.x / 32); ++w) tot += red_i[w];
+        E.stats[4] = tot;
+        const double npx = (double)E.n_img * E.n_img;
+        E.stats[0] = -0.5 * sums[0] - npx * log(E.sigma * sqrt(2.0 * 3.14159265358979323846));
+        E.stats[1] = sums[1] / (E.n_mask > 0 ? E.n_mask : 1);
+        E.stats[2] = E.n_mask;
+        E.stats[3] = (double)(*E.flags);
+    }
+    if (E.hist_out) {
+        const int nc = (E.n_src - 1) * (E.n_src - 1);
+        for (int i = threadIdx.x; i < nc; i += blockDim.x) E.hist_out[i] = __ldcg(E.ccount + i);
+    }
+    if (threadIdx.x == 0) E.ccnt[2] = 0;
+}
+
+// after a CTA's likelihood partials: the last CTA of the evaluation finishes the forward
+__device__ __forceinline__ void like_last_cta(const EvalArgs& E) {
+    __shared__ int last;
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(E.ccnt + 2, 1) == E.n_cta_p - 1;
+    __syncthreads();
+    if (last) like_final_cta(E);
+}
 
 __device__ __forceinline__ void psf_tile_of(const EvalArgs& E, int tile, int& ti, int& tj) {
     const int nt = (E.n_img + PSF_T - 1) / PSF_T;
@@ -82,7 +135,9 @@ __global__ void __launch_bounds__(PSF_NT) k_psf_like(const __grid_constant__ Bat
         double sacc = 0.0;
         for (int w = 0; w < PSF_NT / 32; ++w) sacc += red[threadIdx.x][w];
         E.lpart[tile * 2 + threadIdx.x] = sacc;
+        __threadfence();
     }
+    like_last_cta(E);
 }
 
 // ---- float path with a compile-time tap count KT (9 or 21): a PSF of K <= KT
@@ -192,7 +247,9 @@ __global__ void __launch_bounds__(PSFT_NT) k_psf_like_t(const __grid_constant__ 
         double sacc = 0.0;
         for (int w = 0; w < PSFT_NT / 32; ++w) sacc += red[threadIdx.x][w];
         E.lpart[tile * 2 + threadIdx.x] = sacc;
+        __threadfence();
     }
+    like_last_cta(E);
 }
 
 // d L / d img[p, q] = dlogL sum_{b,a} psf[b][a] resid[p + b - C, q + a - C]
@@ -338,7 +395,9 @@ __global__ void __launch_bounds__(PSFS_NT) k_psf_like_sep(const __grid_constant_
         double sacc = 0.0;
         for (int w = 0; w < PSFS_NT / 32; ++w) sacc += red[threadIdx.x][w];
         E.lpart[tile * 2 + threadIdx.x] = sacc;
+        __threadfence();
     }
+    like_last_cta(E);
 }
 
 template <typename T>
@@ -366,37 +425,6 @@ __global__ void __launch_bounds__(PSFS_NT) k_psf_adj_sep(const __grid_constant__
 }
 
 // log L = -1/2 sum r^2 - N log(sigma sqrt(2 pi)); chi^2_img = sum_mask r^2 / N_mask
-__global__ void __launch_bounds__(256) k_like_final(const __grid_constant__ Batch B) {
-    const EvalArgs& E = B.e[blockIdx.x];
-    __shared__ int red_i[256 / 32];
-    int cnt = 0;
-    for (int t = threadIdx.x; t < E.n_cta_r; t += blockDim.x) cnt += E.cta_cnt[t];
-    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, o);
-    if ((threadIdx.x & 31) == 0) red_i[threadIdx.x >> 5] = cnt;
-    __syncthreads();
-    // the per-tile sums of r^2 (all pixels) and of r^2 in the mask: warps 0 and 1,
-    // lane-strided, fixed tree
-    __shared__ double sums[2];
-    if (threadIdx.x < 64) {
-        const double v = warp_rows_sum(E.lpart + (threadIdx.x >> 5), E.n_cta_p, 2);
-        if ((threadIdx.x & 31) == 0) sums[threadIdx.x >> 5] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0 && E.stats) {
-        int tot = 0;
-        for (int w = 0; w < 256 / 32; ++w) tot += red_i[w];
-        E.stats[4] = tot;
-        const double npx = (double)E.n_img * E.n_img;
-        E.stats[0] = -0.5 * sums[0] - npx * log(E.sigma * sqrt(2.0 * 3.14159265358979323846));
-        E.stats[1] = sums[1] / (E.n_mask > 0 ? E.n_mask : 1);
-        E.stats[2] = E.n_mask;
-        E.stats[3] = (double)(*E.flags);
-    }
-    if (E.hist_out) {
-        const int nc = (E.n_src - 1) * (E.n_src - 1);
-        for (int i = threadIdx.x; i < nc; i += blockDim.x) E.hist_out[i] = E.ccount[i];
-    }
-}
 
 // d L / d img[p,q] = dlogL * sum_{b,a} psf[b,a] resid[p+b-c, q+a-c]
 template <typename T>

@@ -340,7 +340,7 @@ __global__ void __launch_bounds__(256) k_zero(const __grid_constant__ Batch B, i
         if (i < nh) E.hist[i] = 0; else E.ccount[i - nh] = 0;
     }
     if (tile == 0) {
-        if (threadIdx.x == 0) { *E.flags = 0; *E.ecount = 0; E.ccnt[0] = 0; E.ccnt[1] = 0; }
+        if (threadIdx.x == 0) { *E.flags = 0; *E.ecount = 0; E.ccnt[0] = 0; E.ccnt[1] = 0; E.ccnt[2] = 0; }
         const int nsub = E.sub_kind ? E.n_sub : 0;
         lens_setup_par(reinterpret_cast<LensK<double>*>(E.lensk),
                        reinterpret_cast<LensK<float>*>(static_cast<char*>(E.lensk) + LENSK_D_BYTES), E.lens,
@@ -667,7 +667,6 @@ rtu_status run_chunk(Batch& B, int phase, cudaStream_t st, const SideStream& ss)
         else if (sizeof(T) == 4 && maxPsf <= 21) r = launch("k_psf_like", k_psf_like_t<21>, B, t_psf_gen, PSFT_NT, 0, st);
         else r = launch("k_psf_like", k_psf_like<T>, B, t_psf_gen, PSF_NT, 0, st);
         if (r) return r;
-        if ((r = launch("k_like_final", k_like_final, B, t_one, 256, 0, st))) return r;
     }
     if (phase & PH_ADJOINT) {
         if ((r = launch("k_psf_adj", k_psf_adj_sep<T>, B, t_psf_sep, PSFS_NT, 0, st))) return r;

@@ -69,7 +69,8 @@ struct EvalArgs {
     double* mom;       // [8] of the centre rays: mean x, y; min x, max x; min y, max y;
                        // sum of squared deviations x, y (each written once per call by the
                        // last CTA of k_trace_centres / k_centre_hist to finish)
-    int* ccnt;         // [2] CTA-completion counters of those two kernels
+    int* ccnt;         // [3] CTA-completion counters of those two kernels and of the
+                       // likelihood kernel (whose last CTA finishes the forward)
     int* cbin;         // [2][n_mask] level-1 histogram bin of each centre ray
     double* cadj;      // [n_cta_c][8 + 5 n_sub] centre-ray adjoint lens partials
     int* hist;         // [2][HB] level-1 histograms
