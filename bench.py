@@ -55,9 +55,9 @@ ROOF = {
     "k_render": {"flops_per_unit": FLOPS_FWD_RAY, "units": "supersampled rays",
                  "traffic_per_unit": (0.413184e6 + 2304) / 5120000},
     "k_render_adj": {"flops_per_unit": FLOPS_ADJ_RAY, "units": "in-grid rays",
-                     "traffic_per_unit": (6.835968e6 + 49408) / 743894},
+                     "traffic_per_unit": (6.841088e6 + 46592) / 743894},
 }
-TRAFFIC_SRC_DIGEST = "bf73078ba7a128cf"
+TRAFFIC_SRC_DIGEST = "1acfb68016bc378f"
 KERNEL_SOURCES = ("k_render.cuh", "rtu_internal.cuh", "rtu_math.cuh", "rtu_df.cuh")
 
 
