@@ -18,7 +18,7 @@ constexpr int TADJ_SEL = 8;
 // one warp: column sums over the render-adjoint CTAs (the partials are column-major,
 // so the lanes read consecutive CTAs), fixed lane stride and a fixed shuffle tree
 __device__ __forceinline__ double apart_col(const EvalArgs& E, int col) {
-    return warp_rows_sum(E.apart + (size_t)col * E.n_cta_adj, E.n_cta_adj, 1);
+    return warp_rows_sum(E.apart + (size_t)col * E.n_row_adj, E.n_row_adj, 1);
 }
 
 // One CTA per (evaluation, axis); the uniform-grid transform couples the axes

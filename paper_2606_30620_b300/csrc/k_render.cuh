@@ -449,6 +449,7 @@ __global__ void __launch_bounds__(CTA_R, 6) k_render(const __grid_constant__ Bat
     if (cull_sh) {
         // no ray of this tile reaches the grid: a zero source image, nothing staged
         if (threadIdx.x < CTA_R / 32) E.useg[tile * (CTA_R / 32) + threadIdx.x] = 0;
+        if (threadIdx.x < CTA_R / 32) E.nseg[tile * (CTA_R / 32) + threadIdx.x] = 0;
         if (threadIdx.x == 0) E.cta_cnt[tile] = 0;
         if (!valid) return;
         if (sizeof(T) == 4) E.pdef[pixel] = 0ull;
@@ -460,6 +461,7 @@ __global__ void __launch_bounds__(CTA_R, 6) k_render(const __grid_constant__ Bat
     if (!stage_to_smem(sgrid, E.src, (uint32_t)(n * n * sizeof(T)), &mbar, E.flags)) {
         // the copy timed out (flagged): this tile stages nothing
         if (threadIdx.x < CTA_R / 32) E.useg[tile * (CTA_R / 32) + threadIdx.x] = 0;
+        if (threadIdx.x < CTA_R / 32) E.nseg[tile * (CTA_R / 32) + threadIdx.x] = 0;
         if (threadIdx.x == 0) E.cta_cnt[tile] = 0;
         return;
     }
@@ -496,11 +498,15 @@ __global__ void __launch_bounds__(CTA_R, 6) k_render(const __grid_constant__ Bat
     int* stg = E.cell + ubase;
     int wpos = 0;
     // code of a sub-ray: -1 no cell, 0 deferred to the double pass, c + 1 in cell c
+    // (with NEAR_CODE set when the float path traced it in double near a lens core)
+    constexpr int NEAR_CODE = STG_NEAR >> STG_SHIFT;
     auto trace = [&](int q) -> int {
         const int qb = (int)udiv((uint32_t)q, sh.dv_s), qa = q - qb * s;
         const T x = ray_coord(sh.G, pi, qa), y = ray_coord(sh.G, pj, qb);
         T yx, yy;
+        int nflag = 0;
         if (sizeof(T) == 4 && lens_near_core(sh.K, x, y)) {
+            nflag = NEAR_CODE;
             double xd, yd, ydx, ydy;
             ray_pos(E.n_img, E.pix, s, pixel, q, xd, yd);
             rtu_coords_d(E, sh.Kd, sh.trd, sh.Ud, K, xd, yd, ydx, ydy);
@@ -515,7 +521,7 @@ __global__ void __launch_bounds__(CTA_R, 6) k_render(const __grid_constant__ Bat
                 acc += bilinear_at<T, T>(sgrid, n, i0, j0, (T)fxd, (T)fyd);
                 atomicAdd(E.ccount + cell, 1);
                 ++nin;
-                return cell + 1;
+                return (cell + 1) | nflag;
             }
         } else {
             T bx, by;
@@ -572,7 +578,7 @@ __global__ void __launch_bounds__(CTA_R, 6) k_render(const __grid_constant__ Bat
         acc += bilinear_at<T, T>(sgrid, n, i0, j0, fx, fy);
         atomicAdd(E.ccount + cell, 1);
         ++nin;
-        return cell + 1;
+        return (cell + 1) | nflag;
     };
     // codes of this thread's sub-rays in shared memory, then the warp's staged rays
     // in ray order (lane-major, i.e. pixel by pixel): consecutive adjoint rays
@@ -593,9 +599,11 @@ __global__ void __launch_bounds__(CTA_R, 6) k_render(const __grid_constant__ Bat
     }
     wpos = __shfl_sync(0xffffffffu, excl, 31);
     excl -= mine;
+    int mnear = 0;               // staged near-core rays of this thread
     for (int q = 0, pos = excl; q < s2; ++q) {
         const int code = codes[q * CTA_R];
         if (code < 0) continue;
+        mnear += (code & NEAR_CODE) != 0;
         stg[pos] = (lane * s2 + q) | (code << STG_SHIFT);
         if (code == 0) {
             // the double pass finds the ray through its staging position
@@ -604,7 +612,11 @@ __global__ void __launch_bounds__(CTA_R, 6) k_render(const __grid_constant__ Bat
         }
         ++pos;
     }
-    if (lane == 0) E.useg[tile * (CTA_R / 32) + wid] = wpos;
+    mnear = __reduce_add_sync(0xffffffffu, mnear);
+    if (lane == 0) {
+        E.useg[tile * (CTA_R / 32) + wid] = wpos;
+        E.nseg[tile * (CTA_R / 32) + wid] = mnear;
+    }
     // in-grid rays of the CTA (deferred rays counted; k_render_edge takes back the
     // ones that end outside): the N_IN_GRID statistic
     atomicAdd(&cnt_sh, nin);
@@ -756,15 +768,18 @@ __global__ void __launch_bounds__(SCAN_NT) k_scan_cells(const __grid_constant__ 
         if (c < nc) { off[c] = base; base += E.ccount[c]; E.cursor[c] = 0; }
     }
     if (tid == SCAN_NT - 1) off[nc] = base;
-    // exclusive scan of the per-render-warp staged counts
+    // exclusive scans of the per-render-warp staged and near-core counts
     __syncthreads();
     block_exclusive_scan(E.useg, E.n_cta_r * (CTA_R / 32), wtot);
+    block_exclusive_scan(E.nseg, E.n_cta_r * (CTA_R / 32), wtot);
 }
 
 // The adjoint's rays: the staged rays of all render warps in warp order (ray k
 // of warp u at useg[u] + its position), i.e. in ray order, gathered into flat
-// arrays (ray id, or -1 for a deferred ray that ended outside; cell), one warp
-// per render warp, coalesced.
+// arrays (ray id, or -1 for a deferred ray that ended outside; cell, or -2 - cell
+// for a near-core ray of the float path), one warp per render warp, coalesced.
+// The near-core rays' adjoint positions go to nlist in the same order (warp u's
+// at nseg[u] on), for the adjoint's separate double-precision pass.
 constexpr int CMP_NT = 256;
 __global__ void __launch_bounds__(CMP_NT) k_compact(const __grid_constant__ Batch B) {
     const int ev = find_eval(B, blockIdx.x);
@@ -785,12 +800,22 @@ __global__ void __launch_bounds__(CMP_NT) k_compact(const __grid_constant__ Batc
     const int o = E.useg[u];
     const int cnt = max(0, min(min(E.useg[u + 1] - o, cap), n_rays - o));
     const int* stg = E.cell + (size_t)u * cap;
-    for (int i = lane; i < cnt; i += 32) {
-        const int e = stg[i];
-        int cell = (e >> STG_SHIFT) - 1;
-        if (cell >= ncell) cell = -1;
-        E.kray[o + i] = cell >= 0 ? staged_ray_id(E.n_img, E.s * E.s, u, e & ((1 << STG_SHIFT) - 1)) : -1;
-        E.kcell[o + i] = cell;
+    int nat = E.nseg[u];
+    for (int i0 = 0; i0 < cnt; i0 += 32) {
+        const int i = i0 + lane;
+        bool nr = false;
+        if (i < cnt) {
+            const int e = stg[i];
+            int cell = ((e & (STG_NEAR - 1)) >> STG_SHIFT) - 1;
+            if (cell >= ncell) cell = -1;
+            nr = cell >= 0 && (e & STG_NEAR) != 0;
+            E.kray[o + i] = cell >= 0 ? staged_ray_id(E.n_img, E.s * E.s, u, e & ((1 << STG_SHIFT) - 1)) : -1;
+            E.kcell[o + i] = nr ? -2 - cell : cell;
+        }
+        const unsigned bn = __ballot_sync(0xffffffffu, nr);
+        const int at = nat + __popc(bn & ((1u << lane) - 1u));
+        if (nr && at >= 0 && at < n_rays) E.nlist[at] = o + i;
+        nat += __popc(bn);
     }
 }
 
@@ -802,8 +827,13 @@ __global__ void __launch_bounds__(CMP_NT) k_compact(const __grid_constant__ Batc
 // partial sums of the lens, standardisation and spline-knot gradients (for the
 // unsmoothed eCDF: double atomics into the gradients of the sorted positions, so
 // their summation order varies between runs).
-template <typename T, bool LIN>
-__global__ void __launch_bounds__(CTA_R, 4) k_render_adj(const __grid_constant__ Batch B) {
+// The float path splits the rays in two launches that may run concurrently: the
+// main one (NEAR false) in float, leaving out the near-core rays the forward traced
+// in double, and a small one (NEAR true, NEAR_CTAS CTAs per evaluation) over those
+// rays' list, lens and lens adjoint in double, writing partial rows of its own
+// after the main pass's (the double code kept out of the main pass's registers).
+template <typename T, bool LIN, bool NEAR>
+__global__ void __launch_bounds__(CTA_R, NEAR ? 1 : (sizeof(T) == 4 && !LIN ? 6 : 4)) k_render_adj(const __grid_constant__ Batch B) {
     typedef typename real4_of<T>::type R4;
     typedef typename real2_of<T>::type R2;
     const int ev = find_eval(B, blockIdx.x);
@@ -824,11 +854,14 @@ __global__ void __launch_bounds__(CTA_R, 4) k_render_adj(const __grid_constant__
     render_setup<T>(E, sh);
     for (int i = threadIdx.x; i < NW * 4 * K; i += blockDim.x) { tab[i].x = T(0); tab[i].y = T(0); }
     const bool staged = stage_to_smem(sgrid, E.src, (uint32_t)(n * n * sizeof(T)), &mbar, E.flags);
-    // column-major partials: column i of this CTA at apart[i * n_cta_adj + tile]
-    double* out = E.apart + tile;
-    const size_t ostr = (size_t)E.n_cta_adj;
+    // column-major partials: column i of this CTA's row at apart[i * n_row_adj + row];
+    // the near-core pass also owns the subhalo columns of its rows (zero: k_sub_adj
+    // takes every ray in its own rows)
+    double* out = E.apart + (NEAR ? E.n_cta_adj + tile : tile);
+    const size_t ostr = (size_t)E.n_row_adj;
+    const int ncol = NACC_FIX + 4 * K + (NEAR ? 5 * (E.sub_kind ? E.n_sub : 0) : 0);
     if (!staged) {
-        for (int i = threadIdx.x; i < NACC_FIX + 4 * K; i += blockDim.x) out[i * ostr] = 0.0;
+        for (int i = threadIdx.x; i < ncol; i += blockDim.x) out[i * ostr] = 0.0;
         return;
     }
     const int s = E.s, s2 = s * s;
@@ -836,6 +869,9 @@ __global__ void __launch_bounds__(CTA_R, 4) k_render_adj(const __grid_constant__
     const int nu = E.n_cta_r * (CTA_R / 32);
     const int n_rays = E.n_img * E.n_img * E.s * E.s;
     const int total = max(0, min(E.useg[nu], n_rays));
+    // rays of this pass: all adjoint positions, or the near-core list
+    const int count = NEAR ? max(0, min(E.nseg[nu], total)) : total;
+    const int nstride = NEAR ? NEAR_CTAS : E.n_cta_adj;
     const int ncell = nc * nc;
     const T mux = sh.trs[0], muy = sh.trs[1], isg = T(1) / sh.trs[2];
     const T* Xa[2] = {sh.trs + TR_HDR, sh.trs + TR_HDR + K};
@@ -904,18 +940,27 @@ __global__ void __launch_bounds__(CTA_R, 4) k_render_adj(const __grid_constant__
     };
 
     const int chunk = CTA_R * ADJ_RPT;
-    for (int base = tile * chunk; base < total; base += E.n_cta_adj * chunk) {
+    for (int base = tile * chunk; base < count; base += nstride * chunk) {
         for (int r = 0; r < ADJ_RPT; ++r) {
             // coalesced: the CTA's threads take consecutive rays; a thread's rays
             // are CTA_R apart, i.e. from nearby pixels (mostly the same intervals)
-            const int k = base + r * CTA_R + threadIdx.x;
+            const int idx = base + r * CTA_R + threadIdx.x;
+            int k = idx;
+            if constexpr (NEAR) k = idx < count ? E.nlist[idx] : total;
             int jn[2] = {cj[0], cj[1]};
             T pn[2][4];
             bool have = false;
             int cell = -1, ray = 0, slot = -1;
-            if (k < total) {
+            bool other = false;      // a near-core ray in the main pass: the near pass takes it
+            if (k >= 0 && k < total) {
                 ray = E.kray[k];
-                cell = E.kcell[k];
+                const int kc = E.kcell[k];
+                if constexpr (NEAR) {
+                    cell = kc <= -2 ? -2 - kc : -1;
+                } else {
+                    cell = kc;
+                    other = kc <= -2;
+                }
                 if (cell >= ncell || ray < 0 || ray >= n_rays) cell = -1;
             }
             {
@@ -940,7 +985,7 @@ __global__ void __launch_bounds__(CTA_R, 4) k_render_adj(const __grid_constant__
                 const T x = ray_coord(sh.G, pi, qa);
                 const T y = ray_coord(sh.G, pj, qb);
                 const T gpix = gimg[pixel] * inv_s2;
-                const bool near = sizeof(T) == 4 && lens_near_core(sh.K, x, y);
+                constexpr bool near = NEAR;
                 EplJ<T> J;
                 EplJ<double> Jd;
                 double xd = 0.0, yd = 0.0;
@@ -1036,7 +1081,7 @@ __global__ void __launch_bounds__(CTA_R, 4) k_render_adj(const __grid_constant__
                     rec[slot] = rr;
                 }
             }
-            if (nsub && k < total) {
+            if (nsub && k >= 0 && k < total && !other) {
                 R2 g;
                 g.x = gb0; g.y = gb1;
                 gbuf[k] = g;
@@ -1059,12 +1104,12 @@ __global__ void __launch_bounds__(CTA_R, 4) k_render_adj(const __grid_constant__
         if (lane == 0) wacc[wid][i] = v;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < NACC_FIX + 4 * K; i += blockDim.x) {
+    for (int i = threadIdx.x; i < ncol; i += blockDim.x) {
         TP r;
         r.x = T(0); r.y = T(0);
         if (i < NACC_FIX) {
             for (int w = 0; w < NW; ++w) pair_add(r, wacc[w][i]);
-        } else {
+        } else if (i < NACC_FIX + 4 * K) {
             const int kk = i - NACC_FIX;    // [0, 2K) knots X (axis-major), [2K, 4K) slopes d
             for (int w = 0; w < NW; ++w) pair_add(r, tab[w * 4 * K + kk]);
         }
@@ -1088,7 +1133,7 @@ __global__ void __launch_bounds__(CTA_R) k_sub_adj(const __grid_constant__ Batch
     __syncthreads();
     const int Kn = E.n_nodes + 2;
     double* out = E.apart + tile;           // column-major, as k_render_adj
-    const size_t ostr = (size_t)E.n_cta_adj;
+    const size_t ostr = (size_t)E.n_row_adj;
     const int nu = E.n_cta_r * (CTA_R / 32);
     const int n_rays = E.n_img * E.n_img * E.s * E.s;
     const int total = max(0, min(E.useg[nu], n_rays));

@@ -136,7 +136,7 @@ size_t slot_layout(const rtu_system_desc& d, char* base, EvalArgs* e) {
     p = take((size_t)z.ncell * 4);                    if (e) e->cursor = (int*)p;
     p = take((size_t)z.n_rays * 4 * z.tb);            if (e) e->rec = p;
     p = take((size_t)z.ncell * 4 * 2 * z.tb);         if (e) e->corner = p;
-    p = take((size_t)std::max(z.n_cta_r, z.n_cta_adj) * z.nacc * 8); if (e) e->apart = (double*)p;
+    p = take((size_t)std::max(z.n_cta_r, z.n_cta_adj + NEAR_CTAS) * z.nacc * 8); if (e) e->apart = (double*)p;
     p = take(16);                                     if (e) e->flags = (int*)p;
     p = take(LENSK_BYTES);                            if (e) e->lensk = p;
     p = take(16);                                     if (e) e->ecount = (int*)p;
@@ -144,6 +144,8 @@ size_t slot_layout(const rtu_system_desc& d, char* base, EvalArgs* e) {
     p = take((size_t)z.n_rays * 4);                   if (e) e->rval = (float*)p;
     p = take((size_t)(z.n_cta_r + 1) * 4);            if (e) e->cta_cnt = (int*)p;
     p = take((size_t)(z.n_cta_r * (CTA_R / 32) + 1) * 4); if (e) e->useg = (int*)p;
+    p = take((size_t)(z.n_cta_r * (CTA_R / 32) + 1) * 4); if (e) e->nseg = (int*)p;
+    p = take((size_t)z.n_rays * 4);                   if (e) e->nlist = (int*)p;
     p = take((size_t)z.n_rays * 4);                   if (e) e->kray = (int*)p;
     p = take((size_t)z.n_rays * 4);                   if (e) e->kcell = (int*)p;
     p = take((size_t)z.n_rays * 2 * z.tb);            if (e) e->gbuf = p;
@@ -301,10 +303,12 @@ void set_attributes() {
     cudaFuncSetAttribute(k_render<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN);
     cudaFuncSetAttribute(k_render<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN);
     cudaFuncSetAttribute(k_render<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN);
-    cudaFuncSetAttribute(k_render_adj<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN);
-    cudaFuncSetAttribute(k_render_adj<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN);
-    cudaFuncSetAttribute(k_render_adj<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN);
-    cudaFuncSetAttribute(k_render_adj<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN);
+    cudaFuncSetAttribute(k_render_adj<float, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN);
+    cudaFuncSetAttribute(k_render_adj<double, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN);
+    cudaFuncSetAttribute(k_render_adj<float, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN);
+    cudaFuncSetAttribute(k_render_adj<double, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN);
+    cudaFuncSetAttribute(k_render_adj<float, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN);
+    cudaFuncSetAttribute(k_render_adj<float, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN);
 }
 
 }  // namespace
@@ -494,6 +498,7 @@ rtu_status fill_args(rtu_system* s, const rtu_eval& v, EvalArgs& e) {
     e.transform = d.transform;
     e.nrad = s->nrad; e.n_cta_c = s->n_cta_c; e.n_cta_r = s->z.n_cta_r; e.n_cta_p = s->z.n_cta_p;
     e.n_cta_adj = s->z.n_cta_adj;
+    e.n_row_adj = s->z.n_cta_adj + (d.precision == RTU_F64 ? 0 : NEAR_CTAS);
     for (int i = 0; i < MAX_RADIX; ++i) e.rad[i] = s->rad[i];
     e.pix = d.pix; e.pitch = d.src_pitch; e.sigma = d.sigma;
     e.data = d.data; e.mask = d.mask; e.psf = d.psf;
@@ -562,6 +567,8 @@ int t_render_fit(const EvalArgs& e) { return is_lin(e) ? 0 : e.n_cta_r; }
 int t_render_lin(const EvalArgs& e) { return is_lin(e) ? e.n_cta_r : 0; }
 int t_adj_fit(const EvalArgs& e) { return is_lin(e) ? 0 : e.n_cta_adj; }
 int t_adj_lin(const EvalArgs& e) { return is_lin(e) ? e.n_cta_adj : 0; }
+int t_near_fit(const EvalArgs& e) { return is_lin(e) ? 0 : NEAR_CTAS; }
+int t_near_lin(const EvalArgs& e) { return is_lin(e) ? NEAR_CTAS : 0; }
 int t_gp_lines(const EvalArgs& e) { return (e.n_src + GP_LINES - 1) / GP_LINES; }
 int t_zero(const EvalArgs&) { return ZERO_TILES; }
 int t_centre(const EvalArgs& e) { return e.n_cta_c; }
@@ -679,8 +686,18 @@ rtu_status run_chunk(Batch& B, int phase, cudaStream_t st, const SideStream& ss)
         const size_t adj = grid_bytes + (size_t)(CTA_R / 32) * 4 * maxK * 2 * sizeof(T);
         if (adj > MAX_DYN) return fail(RTU_E_ARG, "adjoint shared memory exceeds the limit");
         if ((r = launch("k_compact", k_compact, B, t_units, CMP_NT, 0, st))) return r;
-        if ((r = launch("k_render_adj", k_render_adj<T, false>, B, t_adj_fit, CTA_R, adj, st))) return r;
-        if ((r = launch("k_render_adj", k_render_adj<T, true>, B, t_adj_lin, CTA_R, adj, st))) return r;
+        if (sizeof(T) == 4) {
+            // the near-core rays' double-precision pass on the side stream, beside the
+            // float pass (disjoint partial rows, records and subhalo entries)
+            if ((r = stream_after(ss.s, st, ss.fork))) return r;
+            if ((r = launch("k_render_adj_near", k_render_adj<float, false, true>, B, t_near_fit, CTA_R, adj, ss.s)))
+                return r;
+            if ((r = launch("k_render_adj_near", k_render_adj<float, true, true>, B, t_near_lin, CTA_R, adj, ss.s)))
+                return r;
+        }
+        if ((r = launch("k_render_adj", k_render_adj<T, false, false>, B, t_adj_fit, CTA_R, adj, st))) return r;
+        if ((r = launch("k_render_adj", k_render_adj<T, true, false>, B, t_adj_lin, CTA_R, adj, st))) return r;
+        if (sizeof(T) == 4 && (r = stream_after(st, ss.s, ss.join))) return r;
         if (any_sub && (r = launch("k_sub_adj", k_sub_adj<T>, B, t_adj, CTA_R, 0, st))) return r;
         // transform and centre-ray adjoint (the critical branch, side streams: the
         // selected-rank terms beside the centre rays) beside the cell gather and GP

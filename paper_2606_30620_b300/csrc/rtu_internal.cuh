@@ -22,6 +22,8 @@ constexpr int MAX_RADIX = 12;     // max FFT stages
 constexpr int CTA_C = 256;        // centre-ray kernels: rays per CTA
 constexpr int CTA_R = 128;        // render kernels: pixels per CTA (one thread each)
 constexpr int STG_SHIFT = 11;      // staged entry: low bits the ray within its render warp (< 32 * 64)
+constexpr int STG_NEAR = 1 << 28;  // staged entry: a near-core ray (traced in FP64 by the float path)
+constexpr int NEAR_CTAS = 4;       // float render adjoint: CTAs per evaluation for the near-core rays
 constexpr int ADJ_RPT = 16;        // render adjoint: compacted rays per thread per chunk
 constexpr int PSF_T = 32;         // PSF kernels: 32 x 32 output tile per CTA (4 outputs per thread)
 constexpr int NACC_FIX = 11;      // render-adjoint partials: 8 lens + mu_x, mu_y, sigma
@@ -89,12 +91,13 @@ struct EvalArgs {
     double* lpart;     // [n_cta_p][2]
     int* cell;         // staged in-grid rays: render warp u owns [u*32*s^2, (u+1)*32*s^2), entries
                        // (lane*s^2 + q) | (cell + 1) << STG_SHIFT in append order; cell + 1 = 0
-                       // while a deferred ray is undecided, and after it ended outside
+                       // while a deferred ray is undecided, and after it ended outside;
+                       // STG_NEAR set on the near-core rays of the float path
     int* ccount;       // [n_cells] ray counts, then [n_cells + 1] exclusive offsets
     int* cursor;       // [n_cells]
     void* rec;         // real4 [n_rays] counting-sorted (fx, fy, g, -) records
     void* corner;      // real2 [n_cells][4] per-cell bilinear corner sums (float: hi + lo pairs)
-    double* apart;     // [nacc][n_cta_adj] render-adjoint partials (column-major)
+    double* apart;     // [nacc][n_row_adj] render-adjoint partials (column-major)
     int* flags;        // device flag word
     void* lensk;       // LensK<T> then LensK<double> of the evaluation
     int* ecount;       // number of deferred near-edge rays (float mode)
@@ -103,13 +106,15 @@ struct EvalArgs {
     int* cta_cnt;      // [n_cta_r] in-grid rays per render CTA (the N_IN_GRID statistic)
     int* useg;         // [n_cta_r * CTA_R/32 + 1] staged rays per render warp, then exclusive offsets
     int* kray;         // [n_rays] the adjoint's rays (staged rays in render-warp order): ray id, or -1
-    int* kcell;        // [n_rays] their cells
+    int* kcell;        // [n_rays] their cells; -2 - cell for a near-core ray of the float path
+    int* nseg;         // [n_cta_r * CTA_R/32 + 1] near-core staged rays per render warp, then offsets
+    int* nlist;        // [n_rays] adjoint positions of the near-core rays, in adjoint order
     void* gbuf;        // real2 [n_rays] d logL / d beta of each adjoint ray (subhalo pass)
     const double* light;   // [6 n_light] MGE lens light (A, sigma, q, phi, x_n, y_n)
     double* g_light;       // [6 n_light] adjoint out
     double* lpartl;        // [light CTAs][6 n_light] per-CTA lens-light moment sums
     int n_cta_adj;     // CTAs of the render adjoint (grid-stride over the compacted rays)
-    int pad4_;
+    int n_row_adj;     // rows of apart: n_cta_adj, plus NEAR_CTAS for the float path's near-core pass
     // the unsmoothed eCDF transform (App. C, first paragraph), per axis a at a * n_mask
     double* lkey;      // [2][n_mask] sorted centre-ray positions
     int* lidx;         // [2][n_mask] the centre ray at each rank

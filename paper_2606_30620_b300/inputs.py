@@ -184,6 +184,30 @@ def tnfw_from_mass(m_sun: float, tau: float = 10.0):
     return 10 ** 0.3 * f, 10 ** -1.42 * f, tau
 
 
+def config_core(seed: int = 4000, n_img: int = 40, s: int = 2, n_src: int = 24) -> Mock:
+    """The field of view on the lens core: n_img^2 pixels spanning 2.4 x 0.01 theta_E
+    around the lens centre, so that about half of the rays lie within 0.01 theta_E of it
+    (where the FP32 path traces rays in FP64); EPL + shear, Matern-like spectrum, a smooth
+    blob as data and the whole field masked (a ring mask would hold no pixel here)."""
+    rng = np.random.default_rng(seed)
+    lens = _epl_lens(rng)
+    lens[4] = lens[5] = 0.0
+    pix = 2.4 * 0.01 * lens[0] / n_img
+    pitch = 3.0 * lens[0] / n_src
+    k0 = rng.uniform(0.5, 4.0)
+    ps = [_matern_like_amp(k0, pitch), k0, rng.uniform(1.0, 2.0)]
+    c = (np.arange(n_img) - (n_img - 1) / 2.0) / n_img
+    yy, xx = np.meshgrid(c, c, indexing="ij")
+    clean = np.exp(-0.5 * ((xx - 0.1) ** 2 + (yy + 0.05) ** 2) / 0.3 ** 2)
+    sigma = 1.0 / 30.0
+    data = clean + sigma * rng.standard_normal(clean.shape)
+    latents = rng.standard_normal((n_src, n_src))
+    return Mock(name=f"core-{seed}", n_img=n_img, pix=pix, s_super=s, n_src=n_src, src_pitch=pitch,
+                profile=PROFILE_EPL, ps_family=PS_MATERN_LIKE, sub_kind=SUB_NONE, data=data,
+                mask=np.ones((n_img, n_img), np.uint8), psf=gaussian_psf(5, 2.0 * pix, pix), sigma=sigma,
+                lens=np.asarray(lens, np.float64), latents=latents, ps=np.asarray(ps, np.float64))
+
+
 def config_c4(seed: int = 3000, with_subs: bool = True, n_img: int = 400, s: int = 3,
               n_src: int = 128) -> Mock:
     """400^2 at 0.03"/pix, 3x3 rays, EPL + shear + 1-10 truncated NFW subhaloes

@@ -100,6 +100,36 @@ def test_c4_shape_with_subhaloes_fp64(rtu):
     _check(G.compare(g, G.run_oracle(m)), 1)
 
 
+@pytest.mark.parametrize("kw", [dict(seed=4000), dict(seed=4001, n_img=24, s=3, n_src=16)])
+def test_core_field_fp32_matches_oracle(rtu, kw):
+    # about half of the rays lie within 0.01 theta_E of the lens centre: the FP32 path
+    # traces those in FP64 and differentiates them in its separate near-core pass
+    m = I.config_core(**kw)
+    g, _, _ = G.run_gpu(m, rtu.RTU_F32)
+    _check(G.compare(g, G.run_oracle(m)), 0)
+
+
+def test_core_field_in_a_batch_equals_alone(rtu):
+    # the near-core pass of each system writes its own partial rows: a batch mixing
+    # core fields and an ordinary field gives every system its result alone
+    mocks = [I.config_core(4002), I.config_c2(1031, n_img=64, s=2, n_src=32), I.config_core(4003, n_img=24, s=3)]
+    alone = [G.run_gpu(m, rtu.RTU_F32)[0] for m in mocks]
+    binds = []
+    for m in mocks:
+        s = rtu.System.from_mock(m, precision=rtu.RTU_F32)
+        binds.append(rtu.Binding(s, m.lens, m.latents, m.ps, want_model=True))
+    batch = rtu.Batch(binds)
+    batch.forward()
+    batch.adjoint()
+    torch.cuda.synchronize()
+    for a, b in zip(alone, binds):
+        assert np.array_equal(a["model"], b.model.cpu().numpy())
+        assert np.array_equal(a["stats"], b.stats.cpu().numpy())
+        assert G.rel_l2(b.g_latents.cpu().numpy(), a["g_latents"]) < 1e-6
+        assert G.rel_l2(b.g_lens.cpu().numpy(), a["g_lens"]) < 1e-12
+        assert G.rel_l2(b.g_ps.cpu().numpy(), a["g_ps"]) < 1e-6
+
+
 def test_batch_equals_alone(rtu):
     # every step is per evaluation, so a batch gives each system its own result;
     # the per-cell source-gradient sums run over counting-sorted records whose
