@@ -243,7 +243,8 @@ __device__ __forceinline__ void load_transform(const EvalArgs& E, T* trs, T* U) 
 // EDGE_DELTA cells of a cell edge or of the grid boundary is not decided in
 // float.  The render kernel appends it to a per-evaluation list; k_render_edge
 // traces the listed rays in double (no warp divergence in the float kernel), and
-// k_render_fix completes the affected pixels in a fixed order.  So the integer
+// the thread finishing a pixel's last deferred ray completes the pixel in a fixed
+// order.  So the integer
 // cell of every ray -- the rays-per-cell histogram and the kink of the bilinear
 // slope the adjoint differentiates -- is the double-precision decision.
 constexpr float EDGE_DELTA = 2e-3f;
@@ -623,8 +624,11 @@ __global__ void __launch_bounds__(CTA_R, 6) k_render(const __grid_constant__ Bat
     __syncthreads();
     if (threadIdx.x == 0) E.cta_cnt[tile] = cnt_sh;
     if (!valid) return;
-    if (sizeof(T) == 4) E.pdef[pixel] = deferred;
-    // pixels with deferred rays keep the partial sum; k_render_fix completes them
+    if (sizeof(T) == 4) {
+        E.pdef[pixel] = deferred;
+        if (deferred) E.pcnt[pixel] = __popcll(deferred);
+    }
+    // pixels with deferred rays keep the partial sum; k_render_edge completes them
     const T val = deferred ? acc : acc / T(s2);
     reinterpret_cast<T*>(E.img)[pixel] = val;
     if (E.image_out && !deferred) reinterpret_cast<T*>(E.image_out)[pixel] = val;
@@ -654,6 +658,7 @@ __global__ void __launch_bounds__(EDGE_NT) k_render_edge(const __grid_constant__
     const int n = E.n_src, K = E.n_nodes + 2, s2 = E.s * E.s;
     const int cnt = min(*E.ecount, E.n_img * E.n_img * s2);
     const float* grid = reinterpret_cast<const float*>(E.src);
+    float* img = reinterpret_cast<float*>(E.img);
     const int cap = 32 * s2;                 // staged entries per render warp
     for (int k = tile * EDGE_NT + threadIdx.x; k < cnt; k += EDGE_CTAS * EDGE_NT) {
         const int at = reinterpret_cast<const int*>(E.rec)[k];     // staging position
@@ -682,27 +687,19 @@ __global__ void __launch_bounds__(EDGE_NT) k_render_edge(const __grid_constant__
             atomicSub(E.cta_cnt + u / (CTA_R / 32), 1);
         }
         E.rval[ray] = v;
+        // the thread that finishes a pixel's last deferred ray completes the pixel:
+        // the render's partial sum plus the deferred values in sub-ray order, / s^2
+        __threadfence();
+        if (atomicSub(E.pcnt + pixel, 1) == 1) {
+            const unsigned long long mask = E.pdef[pixel];
+            float val = img[pixel];
+            for (int qq = 0; qq < s2; ++qq)
+                if (mask >> qq & 1ull) val += __ldcg(E.rval + (size_t)pixel * s2 + qq);
+            val = val / (float)s2;
+            img[pixel] = val;
+            if (E.image_out) reinterpret_cast<float*>(E.image_out)[pixel] = val;
+        }
     }
-}
-
-// pixels with deferred rays: partial + deferred values in sub-ray order, / s^2
-__global__ void __launch_bounds__(256) k_render_fix(const __grid_constant__ Batch B) {
-    const int ev = find_eval(B, blockIdx.x);
-    const EvalArgs& E = B.e[ev];
-    const int tile = blockIdx.x - B.tile0[ev];
-    const int pixel = tile * 256 + threadIdx.x;
-    const int npix = E.n_img * E.n_img, s2 = E.s * E.s;
-    if (pixel >= npix) return;
-    float* img = reinterpret_cast<float*>(E.img);
-    float val = img[pixel];
-    const unsigned long long mask = E.pdef[pixel];
-    if (mask) {
-        for (int q = 0; q < s2; ++q)
-            if (mask >> q & 1ull) val += E.rval[(size_t)pixel * s2 + q];
-        val = val / (float)s2;
-        img[pixel] = val;
-    }
-    if (E.image_out) reinterpret_cast<float*>(E.image_out)[pixel] = val;
 }
 
 // exclusive scan of the per-cell ray counts into offsets; cursors zeroed
@@ -820,8 +817,8 @@ __global__ void __launch_bounds__(CMP_NT) k_compact(const __grid_constant__ Batc
 }
 
 // S9 (image -> source/transform/lens part) over the adjoint's rays (render-warp
-// order): a grid-stride loop gives every CTA a fixed set of chunks of
-// CTA_R x ADJ_RPT rays, thread t taking rays t, t + CTA_R, ... of a chunk.  Each ray is recomputed (value + the EPL
+// order): every CTA takes one equal chunk of CTA_R x per consecutive rays (per set
+// from the device-side ray count), thread t taking rays t, t + CTA_R, ... of it.  Each ray is recomputed (value + the EPL
 // series sums) and differentiated analytically; its cell comes from the forward
 // pass.  Writes one counting-sorted record per ray and fixed-order per-CTA
 // partial sums of the lens, standardisation and spline-knot gradients (for the
@@ -939,9 +936,11 @@ __global__ void __launch_bounds__(CTA_R, NEAR ? 1 : (sizeof(T) == 4 && !LIN ? 6 
         if (need) { ca[a][0] = ca[a][1] = ca[a][2] = ca[a][3] = T(0); }
     };
 
-    const int chunk = CTA_R * ADJ_RPT;
+    // an equal share of the pass's rays per CTA: per rays per thread, CTA_R apart
+    const int per = max(1, (count + nstride * CTA_R - 1) / (nstride * CTA_R));
+    const int chunk = CTA_R * per;
     for (int base = tile * chunk; base < count; base += nstride * chunk) {
-        for (int r = 0; r < ADJ_RPT; ++r) {
+        for (int r = 0; r < per; ++r) {
             // coalesced: the CTA's threads take consecutive rays; a thread's rays
             // are CTA_R apart, i.e. from nearby pixels (mostly the same intervals)
             const int idx = base + r * CTA_R + threadIdx.x;

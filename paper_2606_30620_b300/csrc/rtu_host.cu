@@ -141,6 +141,7 @@ size_t slot_layout(const rtu_system_desc& d, char* base, EvalArgs* e) {
     p = take(LENSK_BYTES);                            if (e) e->lensk = p;
     p = take(16);                                     if (e) e->ecount = (int*)p;
     p = take(ni * 8);                                 if (e) e->pdef = (unsigned long long*)p;
+    p = take(ni * 4);                                 if (e) e->pcnt = (int*)p;
     p = take((size_t)z.n_rays * 4);                   if (e) e->rval = (float*)p;
     p = take((size_t)(z.n_cta_r + 1) * 4);            if (e) e->cta_cnt = (int*)p;
     p = take((size_t)(z.n_cta_r * (CTA_R / 32) + 1) * 4); if (e) e->useg = (int*)p;
@@ -576,7 +577,6 @@ int t_adj(const EvalArgs& e) { return e.n_cta_adj; }
 int t_psf_gen(const EvalArgs& e) { return e.psf_uv ? 0 : e.n_cta_p; }
 int t_psf_sep(const EvalArgs& e) { return e.psf_uv ? e.n_cta_p : 0; }
 int t_edge(const EvalArgs&) { return EDGE_CTAS; }
-int t_fix(const EvalArgs& e) { return (e.n_img * e.n_img + 255) / 256; }
 int t_units(const EvalArgs& e) { return (e.n_cta_r * (CTA_R / 32) + CMP_NT / 32 - 1) / (CMP_NT / 32); }
 int t_cells(const EvalArgs& e) {
     const int nc = (e.n_src - 1) * (e.n_src - 1);
@@ -664,10 +664,7 @@ rtu_status run_chunk(Batch& B, int phase, cudaStream_t st, const SideStream& ss)
         if (render_smem > MAX_DYN) return fail(RTU_E_ARG, "render shared memory exceeds the limit");
         if ((r = launch("k_render", k_render<T, false>, B, t_render_fit, CTA_R, render_smem, st))) return r;
         if ((r = launch("k_render", k_render<T, true>, B, t_render_lin, CTA_R, render_smem, st))) return r;
-        if (sizeof(T) == 4) {
-            if ((r = launch("k_render_edge", k_render_edge, B, t_edge, EDGE_NT, 0, st))) return r;
-            if ((r = launch("k_render_fix", k_render_fix, B, t_fix, 256, 0, st))) return r;
-        }
+        if (sizeof(T) == 4 && (r = launch("k_render_edge", k_render_edge, B, t_edge, EDGE_NT, 0, st))) return r;
         if (any_light && (r = launch("k_light_fwd", k_light_fwd<T>, B, t_light_fwd, LIGHT_FWD_NT, 0, st))) return r;
         if ((r = launch("k_psf_like", k_psf_like_sep<T>, B, t_psf_sep, PSFS_NT, 0, st))) return r;
         if (sizeof(T) == 4 && maxPsf <= 9) r = launch("k_psf_like", k_psf_like_t<9>, B, t_psf_gen, PSFT_NT, 0, st);

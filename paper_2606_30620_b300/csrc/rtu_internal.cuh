@@ -102,6 +102,7 @@ struct EvalArgs {
     void* lensk;       // LensK<T> then LensK<double> of the evaluation
     int* ecount;       // number of deferred near-edge rays (float mode)
     unsigned long long* pdef;  // [n_img^2] bit q: sub-ray q deferred to the double pass (float mode)
+    int* pcnt;         // [n_img^2] deferred sub-rays of the pixel still to finish (float mode)
     float* rval;       // [n_rays] values of deferred rays (float mode)
     int* cta_cnt;      // [n_cta_r] in-grid rays per render CTA (the N_IN_GRID statistic)
     int* useg;         // [n_cta_r * CTA_R/32 + 1] staged rays per render warp, then exclusive offsets
