@@ -48,7 +48,8 @@ __device__ __forceinline__ void centre_moments(const EvalArgs& E, double* out6) 
     }
 }
 
-__global__ void __launch_bounds__(CTA_C) k_trace_centres(const __grid_constant__ Batch B) {
+// 5 CTAs per SM (48 registers): the c2 batch's 678 CTAs then run in one wave
+__global__ void __launch_bounds__(CTA_C, 5) k_trace_centres(const __grid_constant__ Batch B) {
     const int ev = find_eval(B, blockIdx.x);
     const EvalArgs& E = B.e[ev];
     const int tile = blockIdx.x - B.tile0[ev];

@@ -428,7 +428,7 @@ __device__ inline bool tile_out_of_reach(const EvalArgs& E, int tile) {
 // S7 + S11: one thread per image pixel, s^2 sub-rays each.  LIN: the unsmoothed
 // eCDF map (its own instantiation, so the smoothed map's code is not burdened).
 template <typename T, bool LIN>
-__global__ void __launch_bounds__(CTA_R, 6) k_render(const __grid_constant__ Batch B) {
+__global__ void __launch_bounds__(CTA_R, sizeof(T) == 4 && !LIN ? 7 : 6) k_render(const __grid_constant__ Batch B) {
     const int ev = find_eval(B, blockIdx.x);
     const EvalArgs& E = B.e[ev];
     const int tile = blockIdx.x - B.tile0[ev];
@@ -499,31 +499,18 @@ __global__ void __launch_bounds__(CTA_R, 6) k_render(const __grid_constant__ Bat
     int* stg = E.cell + ubase;
     int wpos = 0;
     // code of a sub-ray: -1 no cell, 0 deferred to the double pass, c + 1 in cell c
-    // (with NEAR_CODE set when the float path traced it in double near a lens core)
-    constexpr int NEAR_CODE = STG_NEAR >> STG_SHIFT;
+    unsigned long long nearm = 0ull;         // bit q: sub-ray q is near a lens core
     auto trace = [&](int q) -> int {
         const int qb = (int)udiv((uint32_t)q, sh.dv_s), qa = q - qb * s;
         const T x = ray_coord(sh.G, pi, qa), y = ray_coord(sh.G, pj, qb);
         T yx, yy;
-        int nflag = 0;
         if (sizeof(T) == 4 && lens_near_core(sh.K, x, y)) {
-            nflag = NEAR_CODE;
-            double xd, yd, ydx, ydy;
-            ray_pos(E.n_img, E.pix, s, pixel, q, xd, yd);
-            rtu_coords_d(E, sh.Kd, sh.trd, sh.Ud, K, xd, yd, ydx, ydy);
-            yx = (T)ydx;
-            yy = (T)ydy;
-            if (near_edge((float)(ydx * (n - 1)), (float)(ydy * (n - 1)), n)) {
-                // decide in double right here (rare: near-core and near-edge)
-                double fxd, fyd;
-                int i0, j0;
-                const int cell = cell_of<double>(ydx, ydy, n, fxd, fyd, i0, j0);
-                if (cell < 0) return -1;
-                acc += bilinear_at<T, T>(sgrid, n, i0, j0, (T)fxd, (T)fyd);
-                atomicAdd(E.ccount + cell, 1);
-                ++nin;
-                return (cell + 1) | nflag;
-            }
+            // near a lens core: traced and decided by the double pass, and
+            // differentiated by the adjoint's near-core pass
+            nearm |= 1ull << q;
+            deferred |= 1ull << q;
+            ++nin;
+            return 0;
         } else {
             T bx, by;
             if (sh.K.nsub == 0) {
@@ -579,18 +566,19 @@ __global__ void __launch_bounds__(CTA_R, 6) k_render(const __grid_constant__ Bat
         acc += bilinear_at<T, T>(sgrid, n, i0, j0, fx, fy);
         atomicAdd(E.ccount + cell, 1);
         ++nin;
-        return (cell + 1) | nflag;
+        return cell + 1;
     };
-    // codes of this thread's sub-rays in shared memory, then the warp's staged rays
-    // in ray order (lane-major, i.e. pixel by pixel): consecutive adjoint rays
-    // then come from the same or neighbouring pixels
-    // (layout [q][thread]: conflict-free shared-memory banks)
-    int* codes = reinterpret_cast<int*>(smem_raw + (((size_t)n * n * sizeof(T) + 127) & ~(size_t)127)) +
-                 threadIdx.x;
+    // codes of this thread's sub-rays in shared memory (16 bits: cell + 1 < 2^16 - 1
+    // for n_src <= 256, 0xffff for no cell), then the warp's staged rays in ray
+    // order (lane-major, i.e. pixel by pixel): consecutive adjoint rays then come
+    // from the same or neighbouring pixels (layout [q][thread]: conflict-free banks)
+    unsigned short* codes =
+        reinterpret_cast<unsigned short*>(smem_raw + (((size_t)n * n * sizeof(T) + 127) & ~(size_t)127)) +
+        threadIdx.x;
     int mine = 0;
     for (int q = 0; q < s2; ++q) {
         const int code = valid ? trace(q) : -1;
-        codes[q * CTA_R] = code;
+        codes[q * CTA_R] = (unsigned short)(code < 0 ? 0xffff : code);
         mine += code >= 0;
     }
     int excl = mine;
@@ -600,12 +588,12 @@ __global__ void __launch_bounds__(CTA_R, 6) k_render(const __grid_constant__ Bat
     }
     wpos = __shfl_sync(0xffffffffu, excl, 31);
     excl -= mine;
-    int mnear = 0;               // staged near-core rays of this thread
+    const int mnear = __popcll(nearm);      // near-core rays of this thread (all staged)
     for (int q = 0, pos = excl; q < s2; ++q) {
-        const int code = codes[q * CTA_R];
-        if (code < 0) continue;
-        mnear += (code & NEAR_CODE) != 0;
-        stg[pos] = (lane * s2 + q) | (code << STG_SHIFT);
+        const int c16 = codes[q * CTA_R];
+        if (c16 == 0xffff) continue;
+        const int code = c16;
+        stg[pos] = (lane * s2 + q) | (code << STG_SHIFT) | ((nearm >> q & 1ull) ? STG_NEAR : 0);
         if (code == 0) {
             // the double pass finds the ray through its staging position
             const int at = atomicAdd(E.ecount, 1);
@@ -613,10 +601,10 @@ __global__ void __launch_bounds__(CTA_R, 6) k_render(const __grid_constant__ Bat
         }
         ++pos;
     }
-    mnear = __reduce_add_sync(0xffffffffu, mnear);
+    const int wnear = __reduce_add_sync(0xffffffffu, mnear);
     if (lane == 0) {
         E.useg[tile * (CTA_R / 32) + wid] = wpos;
-        E.nseg[tile * (CTA_R / 32) + wid] = mnear;
+        E.nseg[tile * (CTA_R / 32) + wid] = wnear;
     }
     // in-grid rays of the CTA (deferred rays counted; k_render_edge takes back the
     // ones that end outside): the N_IN_GRID statistic
@@ -662,7 +650,8 @@ __global__ void __launch_bounds__(EDGE_NT) k_render_edge(const __grid_constant__
     const int cap = 32 * s2;                 // staged entries per render warp
     for (int k = tile * EDGE_NT + threadIdx.x; k < cnt; k += EDGE_CTAS * EDGE_NT) {
         const int at = reinterpret_cast<const int*>(E.rec)[k];     // staging position
-        const int local = E.cell[at] & ((1 << STG_SHIFT) - 1);
+        const int e0 = E.cell[at];
+        const int local = e0 & ((1 << STG_SHIFT) - 1);
         const int u = at / cap;
         const int ray = staged_ray_id(E.n_img, s2, u, local);
         const int pixel = ray / s2, q = ray - pixel * s2;
@@ -682,7 +671,7 @@ __global__ void __launch_bounds__(EDGE_NT) k_render_edge(const __grid_constant__
         if (cell >= 0) {
             v = bilinear_at<float, float>(grid, n, i0, j0, (float)fx, (float)fy);
             atomicAdd(E.ccount + cell, 1);
-            E.cell[at] = local | ((cell + 1) << STG_SHIFT);
+            E.cell[at] = (e0 & STG_NEAR) | local | ((cell + 1) << STG_SHIFT);
         } else {
             atomicSub(E.cta_cnt + u / (CTA_R / 32), 1);
         }
@@ -801,17 +790,20 @@ __global__ void __launch_bounds__(CMP_NT) k_compact(const __grid_constant__ Batc
     for (int i0 = 0; i0 < cnt; i0 += 32) {
         const int i = i0 + lane;
         bool nr = false;
+        int cell = -1;
         if (i < cnt) {
             const int e = stg[i];
-            int cell = ((e & (STG_NEAR - 1)) >> STG_SHIFT) - 1;
+            cell = ((e & (STG_NEAR - 1)) >> STG_SHIFT) - 1;
             if (cell >= ncell) cell = -1;
-            nr = cell >= 0 && (e & STG_NEAR) != 0;
+            nr = (e & STG_NEAR) != 0;
             E.kray[o + i] = cell >= 0 ? staged_ray_id(E.n_img, E.s * E.s, u, e & ((1 << STG_SHIFT) - 1)) : -1;
-            E.kcell[o + i] = nr ? -2 - cell : cell;
+            E.kcell[o + i] = nr && cell >= 0 ? -2 - cell : cell;
         }
+        // every flagged entry keeps its list slot (counted by the render); one that
+        // the double pass found outside the grid lists -1
         const unsigned bn = __ballot_sync(0xffffffffu, nr);
         const int at = nat + __popc(bn & ((1u << lane) - 1u));
-        if (nr && at >= 0 && at < n_rays) E.nlist[at] = o + i;
+        if (nr && at >= 0 && at < n_rays) E.nlist[at] = cell >= 0 ? o + i : -1;
         nat += __popc(bn);
     }
 }

@@ -301,6 +301,9 @@ constexpr int MAX_DYN = 200 * 1024;
 void set_attributes() {
     cudaFuncSetAttribute(k_select_fit, cudaFuncAttributeMaxDynamicSharedMemorySize, SEL_SMEM);
     cudaFuncSetAttribute(k_render<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN);
+    // 7 CTAs per SM at the c2 shape (31 KB each): the largest shared-memory carveout
+    cudaFuncSetAttribute(k_render<float, false>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         cudaSharedmemCarveoutMaxShared);
     cudaFuncSetAttribute(k_render<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN);
     cudaFuncSetAttribute(k_render<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN);
     cudaFuncSetAttribute(k_render<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN);
@@ -660,7 +663,7 @@ rtu_status run_chunk(Batch& B, int phase, cudaStream_t st, const SideStream& ss)
     if (phase & PH_FORWARD) {
         if ((r = stream_after(st, ss.s, ss.join))) return r;
         if (grid_bytes > MAX_DYN) return fail(RTU_E_ARG, "source grid too large for shared memory");
-        const size_t render_smem = grid_bytes + (size_t)CTA_R * max_s2 * 4;
+        const size_t render_smem = grid_bytes + (size_t)CTA_R * max_s2 * 2;
         if (render_smem > MAX_DYN) return fail(RTU_E_ARG, "render shared memory exceeds the limit");
         if ((r = launch("k_render", k_render<T, false>, B, t_render_fit, CTA_R, render_smem, st))) return r;
         if ((r = launch("k_render", k_render<T, true>, B, t_render_lin, CTA_R, render_smem, st))) return r;
