@@ -317,11 +317,8 @@ __device__ __forceinline__ void rtu_coords_d(const EvalArgs& E, const LensK<doub
 template <typename T>
 struct RenderShared {
     LensK<T> K;
-    LensK<double> Kd;          // the FP64 islands of the float path
     T trs[TR_HDR + 4 * (MAXM + 2)];
     T U[MAXM + 2];
-    double trd[TR_HDR + 4 * (MAXM + 2)];
-    double Ud[MAXM + 2];
     PixGeom<T> G;              // sub-ray positions
     T ih[2 * (MAXM + 2)];      // 1/(X_{j+1} - X_j) per knot interval, axis-major
     UDiv dv_s2, dv_n, dv_s, dv_nc;   // dividers by s^2, n_img, s, n_src - 1
@@ -330,10 +327,6 @@ struct RenderShared {
 template <typename T>
 __device__ __forceinline__ void render_setup(const EvalArgs& E, RenderShared<T>& sh) {
     load_lensk(sh.K, lensk_src<T>(E.lensk));
-    if (sizeof(T) == 4) {
-        load_lensk(sh.Kd, E.lensk);
-        load_transform<double>(E, sh.trd, sh.Ud);
-    }
     load_transform<T>(E, sh.trs, sh.U);
     {
         const int K = E.n_nodes + 2;
@@ -428,7 +421,7 @@ __device__ inline bool tile_out_of_reach(const EvalArgs& E, int tile) {
 // S7 + S11: one thread per image pixel, s^2 sub-rays each.  LIN: the unsmoothed
 // eCDF map (its own instantiation, so the smoothed map's code is not burdened).
 template <typename T, bool LIN>
-__global__ void __launch_bounds__(CTA_R, sizeof(T) == 4 && !LIN ? 7 : 6) k_render(const __grid_constant__ Batch B) {
+__global__ void __launch_bounds__(CTA_R, sizeof(T) == 4 && !LIN ? 8 : 6) k_render(const __grid_constant__ Batch B) {
     const int ev = find_eval(B, blockIdx.x);
     const EvalArgs& E = B.e[ev];
     const int tile = blockIdx.x - B.tile0[ev];
@@ -841,6 +834,14 @@ __global__ void __launch_bounds__(CTA_R, NEAR ? 1 : (sizeof(T) == 4 && !LIN ? 6 
     __shared__ __align__(8) uint64_t mbar;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     render_setup<T>(E, sh);
+    // the lens in double for the float path's FP64 islands (the near-core pass; the
+    // unsmoothed map's positions), loaded by the instantiations that use it
+    const LensK<double>* Kdp = nullptr;
+    if constexpr (sizeof(T) == 4 && (LIN || NEAR)) {
+        __shared__ LensK<double> kd_s;
+        load_lensk(kd_s, E.lensk);
+        Kdp = &kd_s;
+    }
     for (int i = threadIdx.x; i < NW * 4 * K; i += blockDim.x) { tab[i].x = T(0); tab[i].y = T(0); }
     const bool staged = stage_to_smem(sgrid, E.src, (uint32_t)(n * n * sizeof(T)), &mbar, E.flags);
     // column-major partials: column i of this CTA's row at apart[i * n_row_adj + row];
@@ -882,7 +883,7 @@ __global__ void __launch_bounds__(CTA_R, NEAR ? 1 : (sizeof(T) == 4 && !LIN ? 6 
             __shared__ LensK<DF> kdf_s;
             kdf = &kdf_s;
             __syncthreads();
-            if (sh.Kd.nsub == 0) lensk_to_df(sh.Kd, kdf_s);
+            if (Kdp->nsub == 0) lensk_to_df(*Kdp, kdf_s);
             __syncthreads();
         }
     }
@@ -984,7 +985,7 @@ __global__ void __launch_bounds__(CTA_R, NEAR ? 1 : (sizeof(T) == 4 && !LIN ? 6 
                 double bxd = 0.0, byd = 0.0;
                 if (near) {
                     ray_pos(E.n_img, E.pix, s, pixel, q, xd, yd);
-                    lens_beta_eval(sh.Kd, xd, yd, Jd, bxd, byd);
+                    lens_beta_eval(*Kdp, xd, yd, Jd, bxd, byd);
                     bx = (T)bxd;
                     by = (T)byd;
                 } else {
@@ -1002,7 +1003,7 @@ __global__ void __launch_bounds__(CTA_R, NEAR ? 1 : (sizeof(T) == 4 && !LIN ? 6 
                     if (!near) {
                         ray_pos(E.n_img, E.pix, s, pixel, q, xd, yd);
                         if (nsub) {
-                            lens_beta(sh.Kd, xd, yd, bxd, byd);
+                            lens_beta(*Kdp, xd, yd, bxd, byd);
                         } else {
                             DF bxf, byf;
                             lens_beta_smooth<DF>(*kdf, DF(xd), DF(yd), bxf, byf);
@@ -1046,7 +1047,7 @@ __global__ void __launch_bounds__(CTA_R, NEAR ? 1 : (sizeof(T) == 4 && !LIN ? 6 
                 acc[10] -= (gz0 * z[0] + gz1 * z[1]) * isg;
                 if (near) {
                     double o8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-                    lens_beta_vjp(sh.Kd, Jd, xd, yd, (double)gb0, (double)gb1, o8);
+                    lens_beta_vjp(*Kdp, Jd, xd, yd, (double)gb0, (double)gb1, o8);
 #pragma unroll
                     for (int p = 0; p < 8; ++p) acc[p] += (T)o8[p];
                 } else {

@@ -301,7 +301,7 @@ constexpr int MAX_DYN = 200 * 1024;
 void set_attributes() {
     cudaFuncSetAttribute(k_select_fit, cudaFuncAttributeMaxDynamicSharedMemorySize, SEL_SMEM);
     cudaFuncSetAttribute(k_render<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN);
-    // 7 CTAs per SM at the c2 shape (31 KB each): the largest shared-memory carveout
+    // 8 CTAs per SM at the c2 shape (24 KB each): the largest shared-memory carveout
     cudaFuncSetAttribute(k_render<float, false>, cudaFuncAttributePreferredSharedMemoryCarveout,
                          cudaSharedmemCarveoutMaxShared);
     cudaFuncSetAttribute(k_render<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN);
