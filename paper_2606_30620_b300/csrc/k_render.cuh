@@ -687,35 +687,44 @@ __global__ void __launch_bounds__(EDGE_NT) k_render_edge(const __grid_constant__
 // exclusive scan of the per-cell ray counts into offsets; cursors zeroed
 constexpr int SCAN_NT = 1024;
 
-// in-place exclusive scan of a[0..n) by one CTA of SCAN_NT threads, total in a[n]
-__device__ __forceinline__ void block_exclusive_scan(int* a, int n, int* wtot) {
+// in-place exclusive scans of a[0..n) and b[0..n) by one CTA of SCAN_NT threads
+// (both in one pass), totals in a[n] and b[n]; wtot holds 2 x SCAN_NT/32 ints
+__device__ __forceinline__ void block_exclusive_scan2(int* a, int* b, int n, int* wtot) {
     const int tid = threadIdx.x;
     const int per = (n + SCAN_NT - 1) / SCAN_NT;
-    int own = 0;
+    int own_a = 0, own_b = 0;
     for (int i = 0; i < per; ++i) {
         const int c = tid * per + i;
-        if (c < n) own += a[c];
+        if (c < n) { own_a += a[c]; own_b += b[c]; }
     }
-    int incl = own;
+    int inc_a = own_a, inc_b = own_b;
     for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, incl, o);
-        if ((tid & 31) >= o) incl += y;
+        const int ya = __shfl_up_sync(0xffffffffu, inc_a, o);
+        const int yb = __shfl_up_sync(0xffffffffu, inc_b, o);
+        if ((tid & 31) >= o) { inc_a += ya; inc_b += yb; }
     }
     __syncthreads();
-    if ((tid & 31) == 31) wtot[tid >> 5] = incl;
+    if ((tid & 31) == 31) { wtot[tid >> 5] = inc_a; wtot[SCAN_NT / 32 + (tid >> 5)] = inc_b; }
     __syncthreads();
-    if (tid == 0) {
+    if (tid < 2) {
         int acc = 0;
-        for (int w = 0; w < SCAN_NT / 32; ++w) { const int t = wtot[w]; wtot[w] = acc; acc += t; }
+        for (int w = 0; w < SCAN_NT / 32; ++w) {
+            const int t = wtot[tid * (SCAN_NT / 32) + w];
+            wtot[tid * (SCAN_NT / 32) + w] = acc;
+            acc += t;
+        }
     }
     __syncthreads();
-    int base = wtot[tid >> 5] + incl - own;
+    int base_a = wtot[tid >> 5] + inc_a - own_a, base_b = wtot[SCAN_NT / 32 + (tid >> 5)] + inc_b - own_b;
     for (int i = 0; i < per; ++i) {
         const int c = tid * per + i;
-        if (c < n) { const int v = a[c]; a[c] = base; base += v; }
+        if (c < n) {
+            const int va = a[c], vb = b[c];
+            a[c] = base_a; b[c] = base_b;
+            base_a += va; base_b += vb;
+        }
     }
-    if (tid == SCAN_NT - 1) a[n] = base;
-    __syncthreads();
+    if (tid == SCAN_NT - 1) { a[n] = base_a; b[n] = base_b; }
 }
 __global__ void __launch_bounds__(SCAN_NT) k_scan_cells(const __grid_constant__ Batch B) {
     const EvalArgs& E = B.e[blockIdx.x];
@@ -732,7 +741,7 @@ __global__ void __launch_bounds__(SCAN_NT) k_scan_cells(const __grid_constant__ 
         int y = __shfl_up_sync(0xffffffffu, incl, o);
         if ((tid & 31) >= o) incl += y;
     }
-    __shared__ int wtot[SCAN_NT / 32];
+    __shared__ int wtot[2 * (SCAN_NT / 32)];
     if ((tid & 31) == 31) wtot[tid >> 5] = incl;
     __syncthreads();
     if (tid == 0) {
@@ -749,8 +758,7 @@ __global__ void __launch_bounds__(SCAN_NT) k_scan_cells(const __grid_constant__ 
     if (tid == SCAN_NT - 1) off[nc] = base;
     // exclusive scans of the per-render-warp staged and near-core counts
     __syncthreads();
-    block_exclusive_scan(E.useg, E.n_cta_r * (CTA_R / 32), wtot);
-    block_exclusive_scan(E.nseg, E.n_cta_r * (CTA_R / 32), wtot);
+    block_exclusive_scan2(E.useg, E.nseg, E.n_cta_r * (CTA_R / 32), wtot);
 }
 
 // The adjoint's rays: the staged rays of all render warps in warp order (ray k
@@ -758,7 +766,9 @@ __global__ void __launch_bounds__(SCAN_NT) k_scan_cells(const __grid_constant__ 
 // arrays (ray id, or -1 for a deferred ray that ended outside; cell, or -2 - cell
 // for a near-core ray of the float path), one warp per render warp, coalesced.
 // The near-core rays' adjoint positions go to nlist in the same order (warp u's
-// at nseg[u] on), for the adjoint's separate double-precision pass.
+// at nseg[u] on), for the adjoint's separate double-precision pass.  The warp
+// loads up to four groups of 32 entries before it stores any (the loads would
+// otherwise wait for the previous group's stores).
 constexpr int CMP_NT = 256;
 __global__ void __launch_bounds__(CMP_NT) k_compact(const __grid_constant__ Batch B) {
     const int ev = find_eval(B, blockIdx.x);
@@ -780,24 +790,34 @@ __global__ void __launch_bounds__(CMP_NT) k_compact(const __grid_constant__ Batc
     const int cnt = max(0, min(min(E.useg[u + 1] - o, cap), n_rays - o));
     const int* stg = E.cell + (size_t)u * cap;
     int nat = E.nseg[u];
-    for (int i0 = 0; i0 < cnt; i0 += 32) {
-        const int i = i0 + lane;
-        bool nr = false;
-        int cell = -1;
-        if (i < cnt) {
-            const int e = stg[i];
-            cell = ((e & (STG_NEAR - 1)) >> STG_SHIFT) - 1;
-            if (cell >= ncell) cell = -1;
-            nr = (e & STG_NEAR) != 0;
-            E.kray[o + i] = cell >= 0 ? staged_ray_id(E.n_img, E.s * E.s, u, e & ((1 << STG_SHIFT) - 1)) : -1;
-            E.kcell[o + i] = nr && cell >= 0 ? -2 - cell : cell;
+    for (int g0 = 0; g0 < cnt; g0 += 128) {
+        int ent[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int i = g0 + 32 * j + lane;
+            ent[j] = i < cnt ? stg[i] : 0;
         }
-        // every flagged entry keeps its list slot (counted by the render); one that
-        // the double pass found outside the grid lists -1
-        const unsigned bn = __ballot_sync(0xffffffffu, nr);
-        const int at = nat + __popc(bn & ((1u << lane) - 1u));
-        if (nr && at >= 0 && at < n_rays) E.nlist[at] = cell >= 0 ? o + i : -1;
-        nat += __popc(bn);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int i = g0 + 32 * j + lane;
+            if (g0 + 32 * j >= cnt) break;
+            bool nr = false;
+            int cell = -1;
+            if (i < cnt) {
+                const int e = ent[j];
+                cell = ((e & (STG_NEAR - 1)) >> STG_SHIFT) - 1;
+                if (cell >= ncell) cell = -1;
+                nr = (e & STG_NEAR) != 0;
+                E.kray[o + i] = cell >= 0 ? staged_ray_id(E.n_img, E.s * E.s, u, e & ((1 << STG_SHIFT) - 1)) : -1;
+                E.kcell[o + i] = nr && cell >= 0 ? -2 - cell : cell;
+            }
+            // every flagged entry keeps its list slot (counted by the render); one
+            // that the double pass found outside the grid lists -1
+            const unsigned bn = __ballot_sync(0xffffffffu, nr);
+            const int at = nat + __popc(bn & ((1u << lane) - 1u));
+            if (nr && at >= 0 && at < n_rays) E.nlist[at] = cell >= 0 ? o + i : -1;
+            nat += __popc(bn);
+        }
     }
 }
 
