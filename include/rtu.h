@@ -241,6 +241,18 @@ size_t rtu_elbo_state_bytes(const rtu_system* sys);
 rtu_status rtu_elbo_export(const rtu_system* sys, void* host, size_t bytes);
 rtu_status rtu_elbo_import(rtu_system* sys, const void* host, size_t bytes);
 
+/* Replay of recorded launch sequences (on by default).  rtu_build_grid,
+ * rtu_forward and rtu_adjoint record the kernel launches of a call into a CUDA
+ * graph the second time they see its systems and evaluation arguments (every
+ * pointer and size of the batch, the step, the precision) and replay that graph
+ * on the caller's stream whenever a later call repeats them; the data behind the
+ * pointers is read when the graph runs.  Calls made while per-kernel timing is
+ * on, or on a stream the caller is capturing, launch plainly.  Per host thread
+ * and device the 8 most recently used graphs are kept.  on = 0 switches replay
+ * off and frees the calling thread's graphs on the current device.  Process-wide
+ * switch; always returns RTU_OK. */
+rtu_status rtu_graph_replay(int32_t on);
+
 /* Per-kernel timing (tracing aid, off by default).  While enabled, every kernel
  * launch of every call is bracketed by two CUDA events recorded on the call's
  * stream.  rtu_profile_report waits for those events, then writes one line

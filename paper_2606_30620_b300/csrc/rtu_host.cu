@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -722,6 +723,141 @@ rtu_status run_chunk(Batch& B, int phase, cudaStream_t st, const SideStream& ss)
     return RTU_OK;
 }
 
+// ---- replay of recorded launch sequences
+// Every kernel of a chunk takes the Batch by value (plus a pass index) and its grid
+// and shared-memory sizes follow from the Batch, so a chunk's launches are a pure
+// function of (phase, precision, the Batch's systems).  The second time a call
+// repeats those bytes, its launches are recorded into a CUDA graph (captured on a
+// stream of the library's) and replayed on the caller's stream from then on while
+// the bytes repeat; a batch seen once (serving's changing batches) launches plainly.
+// Device data is read when the graph runs: new contents behind the same pointers
+// are seen.  Per host thread and device, the GRAPH_CACHE most recently used graphs
+// and the GRAPH_SEEN most recent batches' hashes are kept.
+std::atomic<bool> g_graphs_on{true};
+constexpr int GRAPH_CACHE = 8;
+constexpr int GRAPH_SEEN = 32;
+struct GraphEntry {
+    int phase = 0, prec = 0;
+    std::vector<unsigned char> key;
+    cudaGraphExec_t exec = nullptr;
+    unsigned long long used = 0;
+};
+struct GraphCache {
+    cudaStream_t cs = nullptr;
+    std::vector<GraphEntry> ent;
+    unsigned long long tick = 0;
+    unsigned long long seen[GRAPH_SEEN] = {};
+    int seen_at = 0;
+};
+// 64-bit multiplicative hash of the key bytes (it only decides when to record; a
+// replay needs the bytes equal)
+unsigned long long key_hash(int phase, int prec, const void* p, size_t bytes) {
+    unsigned long long h = 0x9e3779b97f4a7c15ull ^ (unsigned long long)(phase * 31 + prec);
+    const unsigned char* c = static_cast<const unsigned char*>(p);
+    size_t i = 0;
+    for (; i + 8 <= bytes; i += 8) {
+        unsigned long long w;
+        std::memcpy(&w, c + i, 8);
+        h = (h ^ w) * 0x100000001b3ull;
+        h ^= h >> 29;
+    }
+    for (; i < bytes; ++i) h = (h ^ c[i]) * 0x100000001b3ull;
+    return h ? h : 1ull;
+}
+GraphCache* graph_cache() {
+    static thread_local GraphCache tab[MAX_DEV];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEV) return nullptr;
+    GraphCache& gc = tab[dev];
+    if (!gc.cs && cudaStreamCreateWithFlags(&gc.cs, cudaStreamNonBlocking) != cudaSuccess) {
+        gc.cs = nullptr;
+        return nullptr;
+    }
+    return &gc;
+}
+void graph_cache_clear() {
+    GraphCache* gc = graph_cache();
+    if (!gc) return;
+    for (GraphEntry& e : gc->ent) cudaGraphExecDestroy(e.exec);
+    gc->ent.clear();
+}
+
+// the caller's stream is being captured (by the caller): launch plainly into it
+bool stream_capturing(cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        return true;
+    }
+    return cs != cudaStreamCaptureStatusNone;
+}
+
+rtu_status run_chunk_any(Batch& B, int phase, int prec, cudaStream_t st, const SideStream& ss) {
+    return prec == RTU_F64 ? run_chunk<double>(B, phase, st, ss) : run_chunk<float>(B, phase, st, ss);
+}
+
+rtu_status run_chunk_graph(Batch& B, int phase, int prec, cudaStream_t st, const SideStream& ss) {
+    GraphCache* gc = graph_cache();
+    if (!gc) return run_chunk_any(B, phase, prec, st, ss);
+    const size_t kb = sizeof(int) + (size_t)B.n * sizeof(EvalArgs);
+    const unsigned char* kp = reinterpret_cast<const unsigned char*>(B.e);
+    GraphEntry* hit = nullptr;
+    for (GraphEntry& e : gc->ent)
+        if (e.phase == phase && e.prec == prec && e.key.size() == kb &&
+            std::memcmp(e.key.data(), &B.n, sizeof(int)) == 0 &&
+            std::memcmp(e.key.data() + sizeof(int), kp, kb - sizeof(int)) == 0) {
+            hit = &e;
+            break;
+        }
+    if (!hit) {
+        // record only a batch seen before
+        const unsigned long long h = key_hash(phase, prec, kp, kb - sizeof(int)) ^ (unsigned long long)B.n;
+        bool seen = false;
+        for (int i = 0; i < GRAPH_SEEN; ++i) seen |= gc->seen[i] == h;
+        if (!seen) {
+            gc->seen[gc->seen_at] = h;
+            gc->seen_at = (gc->seen_at + 1) % GRAPH_SEEN;
+            return run_chunk_any(B, phase, prec, st, ss);
+        }
+        cudaGraph_t g = nullptr;
+        cudaError_t ce = cudaStreamBeginCapture(gc->cs, cudaStreamCaptureModeThreadLocal);
+        if (ce != cudaSuccess) {
+            cudaGetLastError();
+            return run_chunk_any(B, phase, prec, st, ss);
+        }
+        const rtu_status r = run_chunk_any(B, phase, prec, gc->cs, ss);
+        ce = cudaStreamEndCapture(gc->cs, &g);
+        cudaGraphExec_t exec = nullptr;
+        if (r == RTU_OK && ce == cudaSuccess && g) ce = cudaGraphInstantiate(&exec, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (r != RTU_OK) return r;
+        if (ce != cudaSuccess || !exec) {
+            // not recordable here: run the chunk plainly
+            cudaGetLastError();
+            return run_chunk_any(B, phase, prec, st, ss);
+        }
+        if ((int)gc->ent.size() >= GRAPH_CACHE) {
+            auto lru = std::min_element(gc->ent.begin(), gc->ent.end(),
+                                        [](const GraphEntry& x, const GraphEntry& y) { return x.used < y.used; });
+            cudaGraphExecDestroy(lru->exec);
+            gc->ent.erase(lru);
+        }
+        GraphEntry e;
+        e.phase = phase;
+        e.prec = prec;
+        e.key.resize(kb);
+        std::memcpy(e.key.data(), &B.n, sizeof(int));
+        std::memcpy(e.key.data() + sizeof(int), kp, kb - sizeof(int));
+        e.exec = exec;
+        gc->ent.push_back(std::move(e));
+        hit = &gc->ent.back();
+    }
+    hit->used = ++gc->tick;
+    const cudaError_t ce = cudaGraphLaunch(hit->exec, st);
+    if (ce != cudaSuccess) return fail(RTU_E_CUDA, std::string("graph launch: ") + cudaGetErrorString(ce));
+    return RTU_OK;
+}
+
 rtu_status run(rtu_system* const* sys, const rtu_eval* ev, int n, int phase, void* stream) {
     if (n < 0 || (n > 0 && (!sys || !ev))) return fail(RTU_E_ARG, "bad system/eval arrays");
     if (n == 0) return RTU_OK;
@@ -739,13 +875,14 @@ rtu_status run(rtu_system* const* sys, const rtu_eval* ev, int n, int phase, voi
     if (rtu_status r = side_stream(ss)) return r;
     if (g_prof_on) { g_side_hint[0] = ss->s; g_side_hint[1] = ss->s2; }
     static thread_local Batch B;
+    const bool replay = g_graphs_on.load(std::memory_order_relaxed) && !g_prof_on && !stream_capturing(st);
     for (int c0 = 0; c0 < n; c0 += MAXB) {
         B.n = std::min(MAXB, n - c0);
         for (int i = 0; i < B.n; ++i) {
             rtu_status r = fill_args(sys[c0 + i], ev[c0 + i], B.e[i]);
             if (r) return r;
         }
-        rtu_status r = prec == RTU_F64 ? run_chunk<double>(B, phase, st, *ss) : run_chunk<float>(B, phase, st, *ss);
+        rtu_status r = replay ? run_chunk_graph(B, phase, prec, st, *ss) : run_chunk_any(B, phase, prec, st, *ss);
         if (r) return r;
     }
     return RTU_OK;
@@ -765,6 +902,12 @@ rtu_status rtu_forward(rtu_system* const* sys, const rtu_eval* ev, int32_t n, vo
 
 rtu_status rtu_adjoint(rtu_system* const* sys, const rtu_eval* ev, int32_t n, void* stream) {
     return run(sys, ev, n, PH_ADJOINT, stream);
+}
+
+rtu_status rtu_graph_replay(int32_t on) {
+    g_graphs_on.store(on != 0, std::memory_order_relaxed);
+    if (!on) graph_cache_clear();
+    return RTU_OK;
 }
 
 rtu_status rtu_profile_enable(int32_t on) {

@@ -87,6 +87,8 @@ _lib.rtu_elbo_import.restype = ctypes.c_int32
 _lib.rtu_gp_source_static.argtypes = [ctypes.c_int32, ctypes.c_double, ctypes.c_int32, ctypes.c_void_p,
                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
 _lib.rtu_gp_source_static.restype = ctypes.c_int32
+_lib.rtu_graph_replay.argtypes = [ctypes.c_int32]
+_lib.rtu_graph_replay.restype = ctypes.c_int32
 _lib.rtu_profile_enable.argtypes = [ctypes.c_int32]
 _lib.rtu_profile_enable.restype = ctypes.c_int32
 _lib.rtu_profile_report.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
@@ -99,7 +101,7 @@ _lib.rtu_version.restype = ctypes.c_char_p
 EXPORTED = ("rtu_workspace_size", "rtu_system_create", "rtu_system_destroy", "rtu_build_grid",
             "rtu_forward", "rtu_adjoint", "rtu_n_sites", "rtu_elbo_init", "rtu_elbo_step",
             "rtu_elbo_state_bytes", "rtu_elbo_export", "rtu_elbo_import", "rtu_gp_source_static",
-            "rtu_profile_enable",
+            "rtu_graph_replay", "rtu_profile_enable",
             "rtu_profile_report", "rtu_profile_timeline", "rtu_last_error", "rtu_version")
 
 
@@ -110,6 +112,11 @@ def _check(rc: int, what: str):
 
 def version() -> str:
     return _lib.rtu_version().decode()
+
+
+def graph_replay(on: bool = True):
+    """Replay of recorded launch sequences for repeated calls (on by default)."""
+    _check(_lib.rtu_graph_replay(1 if on else 0), "rtu_graph_replay")
 
 
 def profile_enable(on: bool = True):

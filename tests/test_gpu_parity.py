@@ -130,6 +130,51 @@ def test_core_field_in_a_batch_equals_alone(rtu):
         assert G.rel_l2(b.g_ps.cpu().numpy(), a["g_ps"]) < 1e-6
 
 
+def test_graph_replay_matches_plain_launches(rtu):
+    # a repeated call replays its recorded launches: the plain launches' bits for the
+    # image and statistics, and new inputs behind the same pointers are read when
+    # the graph runs
+    mocks = [I.config_c2(1041, n_img=64, s=2, n_src=32), I.config_core(4004)]
+
+    def make():
+        binds = [rtu.Binding(rtu.System.from_mock(m, precision=rtu.RTU_F32), m.lens, m.latents, m.ps,
+                             want_model=True) for m in mocks]
+        return binds, rtu.Batch(binds)
+
+    def step(batch, binds):
+        batch.forward()
+        batch.adjoint()
+        torch.cuda.synchronize()
+        return [(b.model.cpu().numpy(), b.stats.cpu().numpy(), b.g_latents.cpu().numpy(),
+                 b.g_lens.cpu().numpy(), b.g_ps.cpu().numpy()) for b in binds]
+
+    def perturb(binds):
+        for b in binds:
+            b.latents.mul_(0.5)
+            b.lens[0] *= 1.01
+
+    def same(x, y):
+        for a, b in zip(x, y):
+            assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+            assert G.rel_l2(b[2], a[2]) < 1e-6 and G.rel_l2(b[3], a[3]) < 1e-12 and G.rel_l2(b[4], a[4]) < 1e-6
+
+    rtu.graph_replay(False)
+    try:
+        pb, pbatch = make()
+        plain = step(pbatch, pb)
+        perturb(pb)
+        plain2 = step(pbatch, pb)
+    finally:
+        rtu.graph_replay(True)
+    gb, gbatch = make()
+    for _ in range(4):          # plain, recorded, then replayed
+        same(plain, step(gbatch, gb))
+    perturb(gb)
+    got2 = step(gbatch, gb)
+    same(plain2, got2)
+    assert not np.array_equal(plain2[0][0], plain[0][0])
+
+
 def test_batch_equals_alone(rtu):
     # every step is per evaluation, so a batch gives each system its own result;
     # the per-cell source-gradient sums run over counting-sorted records whose
