@@ -53,11 +53,11 @@ FLOPS_ADJ_RAY = 2.5 * FLOPS_FWD_RAY
 # them in the grid), valid for the kernel sources with digest TRAFFIC_SRC_DIGEST.
 ROOF = {
     "k_render": {"flops_per_unit": FLOPS_FWD_RAY, "units": "supersampled rays",
-                 "traffic_per_unit": (0.413184e6 + 2304) / 5120000},
+                 "traffic_per_unit": (0.342528e6 + 0) / 5120000},
     "k_render_adj": {"flops_per_unit": FLOPS_ADJ_RAY, "units": "in-grid rays",
-                     "traffic_per_unit": (6.841088e6 + 46592) / 743894},
+                     "traffic_per_unit": (6.770944e6 + 52736) / 743894},
 }
-TRAFFIC_SRC_DIGEST = "1acfb68016bc378f"
+TRAFFIC_SRC_DIGEST = "7e2064b484b8afb5"
 KERNEL_SOURCES = ("k_render.cuh", "rtu_internal.cuh", "rtu_math.cuh", "rtu_df.cuh")
 
 
@@ -495,6 +495,43 @@ def run_serving(args, dev):
             "plain_per_system": {k: plain[k] for k in ("systems", "wall_s", "systems_per_s")}}
 
 
+def run_timeline(args):
+    """Per-launch timeline of one batched step (forward + adjoint) with every launch
+    bracketed by events (the library's tracing aid, which launches plainly and adds a
+    little time per launch): the median over 5 steps after warm-up and an L2 flush,
+    one line per launch "<kernel> <stream> <start_us> <end_us> <us>", stream 0 the
+    call's, 1 and 2 the library's side streams.  A diagnostic, not a bench line."""
+    from paper_2606_30620_b300 import rtu
+    mocks = make_mocks(0, args.mocks)
+    binds = [rtu.Binding(rtu.System.from_mock(m, precision=rtu.RTU_F32), m.lens, m.latents, m.ps) for m in mocks]
+    batch = rtu.Batch(binds)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    for _ in range(max(3, args.warmup)):
+        batch.forward()
+        batch.adjoint()
+    torch.cuda.synchronize()
+    rtu.profile_report()
+    runs = []
+    for _ in range(5):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        rtu.profile_enable(True)
+        batch.forward()
+        batch.adjoint()
+        rtu.profile_enable(False)
+        torch.cuda.synchronize()
+        runs.append(rtu.profile_timeline())
+    rows = []
+    for i in range(len(runs[0])):
+        a = float(np.median([r[i][2] for r in runs]))
+        b = float(np.median([r[i][3] for r in runs]))
+        rows.append((runs[0][i][0], runs[0][i][1], a, b))
+    for name, side, a, b in sorted(rows, key=lambda r: r[2]):
+        print(f"{name} {side} {a * 1e3:.1f} {b * 1e3:.1f} {(b - a) * 1e3:.1f}")
+    print(f"end {max(r[3] for r in rows) * 1e3:.1f}")
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -508,9 +545,13 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-variants", action="store_true", help="skip the timing of the grid / light variants")
     ap.add_argument("--serve-n", type=int, default=4096, help="systems in the serving stream (0 = skip)")
+    ap.add_argument("--timeline", action="store_true",
+                    help="print the per-launch timeline of one traced step instead of the bench line")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.timeline:
+        return run_timeline(args)
     return run_ours(args)
 
 
