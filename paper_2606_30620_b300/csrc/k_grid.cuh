@@ -61,38 +61,62 @@ __global__ void __launch_bounds__(CTA_C, 5) k_trace_centres(const __grid_constan
     // the float path traces its centre rays in double-float (about 48 bits) unless
     // subhaloes are present; the double path in double
     const bool use_df = !E.f64 && L.nsub == 0;
+    __shared__ DF pix_df;
     if (use_df) {
         lensk_to_df(L, Ldf);
+        if (threadIdx.x == 0) pix_df = DF(E.pix);
         __syncthreads();
     }
     const int k = tile * CTA_C + threadIdx.x;
-    double bx = 0.0, by = 0.0;
-    double v[6];
-    if (k < E.n_mask) {
-        double x, y;
-        ray_pos(E.n_img, E.pix, 1, E.centre_idx[k], 0, x, y);
-        if (use_df) {
-            DF bxf, byf;
-            lens_beta_smooth<DF>(Ldf, DF(x), DF(y), bxf, byf);
-            bx = bxf.to_double();
-            by = byf.to_double();
-        } else {
-            lens_beta(L, x, y, bx, by);
+    const bool ok = k < E.n_mask;
+    double v[6];       // sum x, sum y, min x, max x, min y, max y of the warp (lane 0)
+    if (use_df) {
+        // positions and the warp reductions in double-float as well: on this part an
+        // FP64 instruction holds the FP64 pipe for many cycles, and a warp tree of six
+        // doubles per ray cost more than the lens itself
+        DF bxf(0.0f, 0.0f), byf(0.0f, 0.0f);
+        if (ok) {
+            const int pix = E.centre_idx[k];
+            const int pj = pix / E.n_img, pi = pix - pj * E.n_img;
+            const float c = 0.5f * (float)(E.n_img - 1);      // pixel offsets are exact in float
+            lens_beta_smooth<DF>(Ldf, DF((float)pi - c) * pix_df, DF((float)pj - c) * pix_df, bxf, byf);
+            E.beta[k] = bxf.to_double();
+            E.beta[E.n_mask + k] = byf.to_double();
         }
-        E.beta[k] = bx;
-        E.beta[E.n_mask + k] = by;
-        v[0] = bx; v[1] = by; v[2] = bx; v[3] = bx; v[4] = by; v[5] = by;
+        const DF inf(INFINITY, 0.0f), ninf(-INFINITY, 0.0f), zero(0.0f, 0.0f);
+        DF a[6] = {ok ? bxf : zero, ok ? byf : zero, ok ? bxf : inf, ok ? bxf : ninf, ok ? byf : inf, ok ? byf : ninf};
+        for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+            for (int q = 0; q < 6; ++q) {
+                const DF t(__shfl_down_sync(0xffffffffu, a[q].hi, o), __shfl_down_sync(0xffffffffu, a[q].lo, o));
+                if (q < 2) a[q] = a[q] + t;
+                else if ((q & 1) == 0) a[q] = t < a[q] ? t : a[q];
+                else a[q] = a[q] < t ? t : a[q];
+            }
+        }
+        if ((threadIdx.x & 31) == 0)
+            for (int q = 0; q < 6; ++q) v[q] = a[q].to_double();
     } else {
-        v[0] = 0.0; v[1] = 0.0; v[2] = 1e300; v[3] = -1e300; v[4] = 1e300; v[5] = -1e300;
-    }
-    // fixed-order reduction: warp tree, then warps in order
-    for (int o = 16; o > 0; o >>= 1) {
-        v[0] += __shfl_down_sync(0xffffffffu, v[0], o);
-        v[1] += __shfl_down_sync(0xffffffffu, v[1], o);
-        v[2] = fmin(v[2], __shfl_down_sync(0xffffffffu, v[2], o));
-        v[3] = fmax(v[3], __shfl_down_sync(0xffffffffu, v[3], o));
-        v[4] = fmin(v[4], __shfl_down_sync(0xffffffffu, v[4], o));
-        v[5] = fmax(v[5], __shfl_down_sync(0xffffffffu, v[5], o));
+        double bx = 0.0, by = 0.0;
+        if (ok) {
+            double x, y;
+            ray_pos(E.n_img, E.pix, 1, E.centre_idx[k], 0, x, y);
+            lens_beta(L, x, y, bx, by);
+            E.beta[k] = bx;
+            E.beta[E.n_mask + k] = by;
+            v[0] = bx; v[1] = by; v[2] = bx; v[3] = bx; v[4] = by; v[5] = by;
+        } else {
+            v[0] = 0.0; v[1] = 0.0; v[2] = 1e300; v[3] = -1e300; v[4] = 1e300; v[5] = -1e300;
+        }
+        // fixed-order reduction: warp tree, then warps in order
+        for (int o = 16; o > 0; o >>= 1) {
+            v[0] += __shfl_down_sync(0xffffffffu, v[0], o);
+            v[1] += __shfl_down_sync(0xffffffffu, v[1], o);
+            v[2] = fmin(v[2], __shfl_down_sync(0xffffffffu, v[2], o));
+            v[3] = fmax(v[3], __shfl_down_sync(0xffffffffu, v[3], o));
+            v[4] = fmin(v[4], __shfl_down_sync(0xffffffffu, v[4], o));
+            v[5] = fmax(v[5], __shfl_down_sync(0xffffffffu, v[5], o));
+        }
     }
     const int w = threadIdx.x >> 5;
     if ((threadIdx.x & 31) == 0)
@@ -131,17 +155,20 @@ __global__ void __launch_bounds__(CTA_C) k_centre_hist(const __grid_constant__ B
     const int ev = find_eval(B, blockIdx.x);
     const EvalArgs& E = B.e[ev];
     const int tile = blockIdx.x - B.tile0[ev];
-    __shared__ double m[6];
+    __shared__ double m[6], sc[2];
     __shared__ double red[2][CTA_C / 32];
     if (threadIdx.x < 6) m[threadIdx.x] = __ldcg(E.mom + threadIdx.x);
+    __syncthreads();
+    // the bin scales once per CTA (an FP64 divide each)
+    if (threadIdx.x < 2) sc[threadIdx.x] = bin_scale(m[2 + 2 * threadIdx.x], m[3 + 2 * threadIdx.x]);
     __syncthreads();
     const int k = tile * CTA_C + threadIdx.x;
     double d0 = 0.0, d1 = 0.0;
     if (k < E.n_mask) {
         double bx = E.beta[k], by = E.beta[E.n_mask + k];
         const int w = E.cwt ? (int)E.cwt[k] : 1;      // weighted grid: the ray counts w times
-        const int b0 = beta_bin(bx, m[2], bin_scale(m[2], m[3]));
-        const int b1 = beta_bin(by, m[4], bin_scale(m[4], m[5]));
+        const int b0 = beta_bin(bx, m[2], sc[0]);
+        const int b1 = beta_bin(by, m[4], sc[1]);
         atomicAdd(E.hist + b0, w);
         atomicAdd(E.hist + HB + b1, w);
         E.cbin[k] = b0;

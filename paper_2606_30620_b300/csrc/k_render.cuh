@@ -741,7 +741,7 @@ __global__ void __launch_bounds__(SCAN_NT) k_scan_cells(const __grid_constant__ 
         int y = __shfl_up_sync(0xffffffffu, incl, o);
         if ((tid & 31) >= o) incl += y;
     }
-    __shared__ int wtot[2 * (SCAN_NT / 32)];
+    __shared__ int wtot[SCAN_NT / 32];
     if ((tid & 31) == 31) wtot[tid >> 5] = incl;
     __syncthreads();
     if (tid == 0) {
@@ -756,8 +756,13 @@ __global__ void __launch_bounds__(SCAN_NT) k_scan_cells(const __grid_constant__ 
         if (c < nc) { off[c] = base; base += E.ccount[c]; E.cursor[c] = 0; }
     }
     if (tid == SCAN_NT - 1) off[nc] = base;
-    // exclusive scans of the per-render-warp staged and near-core counts
-    __syncthreads();
+}
+
+// exclusive scans of the per-render-warp staged and near-core counts (what the
+// compaction needs; the cell offsets are the render adjoint's)
+__global__ void __launch_bounds__(SCAN_NT) k_scan_warps(const __grid_constant__ Batch B) {
+    const EvalArgs& E = B.e[blockIdx.x];
+    __shared__ int wtot[2 * (SCAN_NT / 32)];
     block_exclusive_scan2(E.useg, E.nseg, E.n_cta_r * (CTA_R / 32), wtot);
 }
 

@@ -679,10 +679,10 @@ rtu_status run_chunk(Batch& B, int phase, cudaStream_t st, const SideStream& ss)
     if (phase & PH_ADJOINT) {
         const size_t adj = grid_bytes + (size_t)(CTA_R / 32) * 4 * maxK * 2 * sizeof(T);
         if (adj > MAX_DYN) return fail(RTU_E_ARG, "adjoint shared memory exceeds the limit");
-        // the cell offsets and the adjoint's ray list (side stream, from the forward's
-        // counts and staging) beside the PSF and lens-light adjoints (main)
+        // the adjoint's ray list (side stream, from the forward's counts and staging)
+        // beside the PSF and lens-light adjoints and the cell offsets (main)
         if ((r = stream_after(ss.s, st, ss.fork))) return r;
-        if ((r = launch("k_scan_cells", k_scan_cells, B, t_one, SCAN_NT, 0, ss.s))) return r;
+        if ((r = launch("k_scan_warps", k_scan_warps, B, t_one, SCAN_NT, 0, ss.s))) return r;
         if ((r = launch("k_compact", k_compact, B, t_units, CMP_NT, 0, ss.s))) return r;
         if ((r = launch("k_psf_adj", k_psf_adj_sep<T>, B, t_psf_sep, PSFS_NT, 0, st))) return r;
         if (sizeof(T) == 4 && maxPsf <= 9) r = launch("k_psf_adj", k_psf_adj_t<9>, B, t_psf_gen, PSFT_NT, 0, st);
@@ -690,6 +690,7 @@ rtu_status run_chunk(Batch& B, int phase, cudaStream_t st, const SideStream& ss)
         else r = launch("k_psf_adj", k_psf_adj<T>, B, t_psf_gen, PSF_NT, 0, st);
         if (r) return r;
         if (any_light && (r = launch("k_light_adj", k_light_adj<T>, B, t_light, CTA_R, 0, st))) return r;
+        if ((r = launch("k_scan_cells", k_scan_cells, B, t_one, SCAN_NT, 0, st))) return r;
         if ((r = stream_after(st, ss.s, ss.join))) return r;
         if (sizeof(T) == 4) {
             // the near-core rays' double-precision pass on the side stream, beside the
