@@ -1190,8 +1190,9 @@ __global__ void __launch_bounds__(CTA_R) k_sub_adj(const __grid_constant__ Batch
     }
 }
 
-// per-cell bilinear corner sums over the counting-sorted records: one warp per
-// cell, fixed lane-stride order and a fixed warp tree, in double
+// per-cell bilinear corner sums over the counting-sorted records: one half-warp
+// per cell (two cells' loads in flight per warp), fixed lane-stride order and a
+// fixed tree, in compensated pairs (float) or double
 constexpr int GATHER_NT = 256;
 template <typename T>
 __global__ void __launch_bounds__(GATHER_NT) k_cell_gather(const __grid_constant__ Batch B) {
@@ -1200,16 +1201,16 @@ __global__ void __launch_bounds__(GATHER_NT) k_cell_gather(const __grid_constant
     const EvalArgs& E = B.e[ev];
     const int tile = blockIdx.x - B.tile0[ev];
     const int nc = E.n_src - 1, ncell = nc * nc;
-    const int cell = tile * (GATHER_NT / 32) + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    if (cell >= ncell) return;
+    const int cell = tile * (GATHER_NT / 16) + (threadIdx.x >> 4);
+    const int hl = threadIdx.x & 15;
+    const bool valid = cell < ncell;
     const int* off = E.ccount + ncell;
     const R4* rec = reinterpret_cast<const R4*>(E.rec);
-    // lane sums in the record type (a few records each), the warp tree in double
+    // lane sums in the record type (a few records each), the tree in pairs
     T l0 = T(0), l1 = T(0), l2 = T(0), l3 = T(0);
     const int n_rays = E.n_img * E.n_img * E.s * E.s;
-    const int lo = max(0, off[cell]), hi = min(off[cell + 1], n_rays);
-    for (int i = lo + lane; i < hi; i += 32) {
+    const int lo = valid ? max(0, off[cell]) : 0, hi = valid ? min(off[cell + 1], n_rays) : 0;
+    for (int i = lo + hl; i < hi; i += 16) {
         const R4 r = rec[i];
         const T fx = r.x, fy = r.y, g = r.z;
         const T gy0 = (T(1) - fy) * g, gy1 = fy * g;
@@ -1218,11 +1219,11 @@ __global__ void __launch_bounds__(GATHER_NT) k_cell_gather(const __grid_constant
         l2 += (T(1) - fx) * gy1;
         l3 += fx * gy1;
     }
-    // The four warp sums by a transposing butterfly (compensated pairs in the float
-    // path): at xor 16 the lower half keeps corners 0, 1 and the upper half 2, 3, at
-    // xor 8 each quarter keeps one corner, then three levels on that one pair -- 12
-    // shuffles of pairs instead of 40.  Lanes 0, 8, 16, 24 store corners 0..3; the
-    // order of operations is fixed, so the sums are the same from run to run.
+    // The four sums of the half-warp by a transposing butterfly: at xor 8 the lower
+    // eight lanes keep corners 0, 1 and the upper eight 2, 3, at xor 4 each quarter
+    // keeps one corner, then two levels on that one pair -- 8 shuffles of pairs.
+    // Lanes 0, 4, 8, 12 of the half store corners 0..3; the order of operations is
+    // fixed, so the sums are the same from run to run.
     typedef typename real2_of<T>::type TP;
     auto pr = [](T v) { TP p; p.x = v; p.y = T(0); return p; };
     auto xs = [](TP p, int o) {
@@ -1231,18 +1232,18 @@ __global__ void __launch_bounds__(GATHER_NT) k_cell_gather(const __grid_constant
         q.y = __shfl_xor_sync(0xffffffffu, p.y, o);
         return q;
     };
-    const bool up = lane & 16;
+    const bool up = hl & 8;
     TP k0 = pr(up ? l2 : l0), k1 = pr(up ? l3 : l1);
     {
-        const TP s0 = xs(pr(up ? l0 : l2), 16), s1 = xs(pr(up ? l1 : l3), 16);
+        const TP s0 = xs(pr(up ? l0 : l2), 8), s1 = xs(pr(up ? l1 : l3), 8);
         pair_add(k0, s0);
         pair_add(k1, s1);
     }
-    const bool hi8 = lane & 8;
-    TP k = hi8 ? k1 : k0;
-    pair_add(k, xs(hi8 ? k0 : k1, 8));
-    for (int o = 4; o > 0; o >>= 1) pair_add(k, xs(k, o));
-    if ((lane & 7) == 0) reinterpret_cast<TP*>(E.corner)[(size_t)cell * 4 + (lane >> 3)] = k;
+    const bool hi4 = hl & 4;
+    TP k = hi4 ? k1 : k0;
+    pair_add(k, xs(hi4 ? k0 : k1, 4));
+    for (int o = 2; o > 0; o >>= 1) pair_add(k, xs(k, o));
+    if (valid && (hl & 3) == 0) reinterpret_cast<TP*>(E.corner)[(size_t)cell * 4 + (hl >> 2)] = k;
 }
 
 }  // namespace rtu

@@ -584,7 +584,7 @@ int t_edge(const EvalArgs&) { return EDGE_CTAS; }
 int t_units(const EvalArgs& e) { return (e.n_cta_r * (CTA_R / 32) + CMP_NT / 32 - 1) / (CMP_NT / 32); }
 int t_cells(const EvalArgs& e) {
     const int nc = (e.n_src - 1) * (e.n_src - 1);
-    return (nc + GATHER_NT / 32 - 1) / (GATHER_NT / 32);
+    return (nc + GATHER_NT / 16 - 1) / (GATHER_NT / 16);
 }
 
 enum Phase { PH_GRID = 1, PH_FORWARD = 2, PH_ADJOINT = 4 };
