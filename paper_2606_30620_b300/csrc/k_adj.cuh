@@ -73,6 +73,15 @@ __global__ void __launch_bounds__(CDF_NT) k_cdf_adj(const __grid_constant__ Batc
         }
         return;
     }
+    // this axis's guarded knots, raw knots, raw p' and slopes, staged (the serial
+    // parts below walk them)
+    __shared__ double sXf[MAXM + 2], sXr[MAXM + 2], spr[MAXM + 2], ssl[MAXM + 2];
+    for (int j = threadIdx.x; j < K; j += CDF_NT) {
+        sXf[j] = tr[TR_HDR + ax * K + j];
+        sXr[j] = tr[TR_HDR + (6 + ax) * K + j];
+        spr[j] = tr[TR_HDR + (4 + ax) * K + j];
+        ssl[j] = tr[TR_HDR + (2 + ax) * K + j];
+    }
     // this axis's columns: dmu_a, dsigma (axis 0), knots X and slopes d
     const int ncol = 2 + 2 * K;
     for (int w = wid; w < ncol; w += CDF_NT / 32) {
@@ -84,10 +93,10 @@ __global__ void __launch_bounds__(CDF_NT) k_cdf_adj(const __grid_constant__ Batc
     __syncthreads();
     const double* gX = tot + NACC_FIX + ax * K;
     const double* gd = tot + NACC_FIX + 2 * K + ax * K;
-    const double* Xf = tr + TR_HDR + ax * K;          // guarded knots
-    const double* Xr = tr + TR_HDR + (6 + ax) * K;    // raw knots
-    const double* pr = tr + TR_HDR + (4 + ax) * K;    // raw p'
-    const double* sl = tr + TR_HDR + (2 + ax) * K;    // slopes 1/p'
+    const double* Xf = sXf;      // guarded knots
+    const double* Xr = sXr;      // raw knots
+    const double* pr = spr;      // raw p'
+    const double* sl = ssl;      // slopes 1/p'
     double span = Xr[K - 1] - Xr[0];
     const bool span_ok = span > 0.0;
     if (!span_ok) span = fabs(span) + 1e-300;
@@ -99,11 +108,16 @@ __global__ void __launch_bounds__(CDF_NT) k_cdf_adj(const __grid_constant__ Batc
         gXr[j] = gX[j];
     }
     __syncthreads();
-    // ... and the knot floor (sequential in the knots; the floor's span terms)
-    if (threadIdx.x == 0) {
-        double gfl = 0.0;
-        for (int j = 0; j < K; ++j)
+    // ... and the knot floor (sequential in the knots; the floor's span terms): the
+    // floored slopes' terms summed by warp 0 (lane stride, fixed tree), the carry down
+    // the floored knots by its lane 0
+    double gfl = 0.0;
+    if (wid == 0) {
+        for (int j = lane; j < K; j += 32)
             if (pr[j] < floor_d) gfl += -gd[j] * sl[j] * sl[j];
+        for (int o = 16; o > 0; o >>= 1) gfl += __shfl_down_sync(0xffffffffu, gfl, o);
+    }
+    if (threadIdx.x == 0) {
         for (int j = K - 1; j >= 1; --j)
             if (Xf[j] != Xr[j]) { gXr[j - 1] += gXr[j]; gfl += gXr[j]; gXr[j] = 0.0; }
         if (span_ok) { gXr[K - 1] += 1e-6 * gfl; gXr[0] -= 1e-6 * gfl; }
@@ -114,6 +128,7 @@ __global__ void __launch_bounds__(CDF_NT) k_cdf_adj(const __grid_constant__ Batc
     const double* dVt = E.cheb + cheb_dV(M, D);
     for (int k = threadIdx.x; k <= D; k += CDF_NT) {
         double g = 0.0;
+#pragma unroll 8
         for (int j = 0; j < K; ++j) g += Vt[j * (D + 1) + k] * gXr[j] + dVt[j * (D + 1) + k] * gpr[j];
         gc[k] = g;
     }
@@ -122,6 +137,7 @@ __global__ void __launch_bounds__(CDF_NT) k_cdf_adj(const __grid_constant__ Batc
     const double* Ct = E.cheb + cheb_C(M, D);
     for (int i = threadIdx.x; i < M; i += CDF_NT) {
         double g = 0.0;
+#pragma unroll 8
         for (int k = 0; k <= D; ++k) g += Ct[k * M + i] * gc[k];
         gQ[i] = g;
         const double h = E.cheb[cheb_u(M, D) + i] * (E.wtot - 1);
@@ -247,9 +263,17 @@ __global__ void __launch_bounds__(SEL_ADJ_NT) k_sel_adj(const __grid_constant__ 
     const int nsub = E.sub_kind ? E.n_sub : 0;
     const int nl = 8 + 5 * nsub;
     __shared__ LensK<double> Ld;
+    __shared__ LensK<DF> Ldf;
     __shared__ double red[SEL_ADJ_NT / 32][8];
     load_lensk(Ld, E.lensk);
     __syncthreads();
+    // the float path without subhaloes evaluates these terms in double-float (about
+    // 48 bits) on the FP32 pipes: FP64 instructions are scarce on this part
+    const bool use_df = !E.f64 && Ld.nsub == 0;
+    if (use_df) {
+        lensk_to_df(Ld, Ldf);
+        __syncthreads();
+    }
     const int a = threadIdx.x / (2 * MAXM), t = threadIdx.x - a * 2 * MAXM;
     const int ray = t < 2 * M ? E.sel_idx[a * 2 * MAXM + t] : -1;
     double o8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -261,10 +285,20 @@ __global__ void __launch_bounds__(SEL_ADJ_NT) k_sel_adj(const __grid_constant__ 
         const double c = 0.5 * (E.n_img - 1);
         xd = (pi - c) * E.pix;
         yd = (pj - c) * E.pix;
-        EplJ<double> J;
-        double bx, by;
-        lens_beta_eval(Ld, xd, yd, J, bx, by);
-        lens_beta_vjp(Ld, J, xd, yd, a == 0 ? g : 0.0, a == 1 ? g : 0.0, o8);
+        if (use_df) {
+            EplJ<DF> J;
+            DF bx, by;
+            const DF xf(xd), yf(yd), gf(g), zero(0.0f, 0.0f);
+            lens_beta_eval_smooth(Ldf, xf, yf, J, bx, by);
+            DF o8f[8] = {zero, zero, zero, zero, zero, zero, zero, zero};
+            lens_beta_vjp(Ldf, J, xf, yf, a == 0 ? gf : zero, a == 1 ? gf : zero, o8f);
+            for (int p = 0; p < 8; ++p) o8[p] = o8f[p].to_double();
+        } else {
+            EplJ<double> J;
+            double bx, by;
+            lens_beta_eval(Ld, xd, yd, J, bx, by);
+            lens_beta_vjp(Ld, J, xd, yd, a == 0 ? g : 0.0, a == 1 ? g : 0.0, o8);
+        }
     }
     double* out = E.cadj + (size_t)E.n_cta_c * nl;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;

@@ -434,6 +434,15 @@ __device__ __forceinline__ void lens_beta_eval(const LensK<T>& K, T x, T y, EplJ
     by = y - ay;
 }
 
+// the same without subhaloes (EPL + shear), for scalar types without the subhalo
+// profiles' special functions
+template <typename T>
+__device__ __forceinline__ void lens_beta_eval_smooth(const LensK<T>& K, T x, T y, EplJ<T>& J, T& bx, T& by) {
+    epl_eval(K.C, K.epl != 0, x, y, J);
+    bx = x - (J.ax + K.g1 * x + K.g2 * y);
+    by = y - (J.ay + K.g2 * x - K.g1 * y);
+}
+
 // out[0..7] += dL/d(theta_E, gamma, e1, e2, x0, y0, Gamma1, Gamma2) given dL/dbeta = (gbx, gby)
 template <typename T>
 __device__ __forceinline__ void lens_beta_vjp(const LensK<T>& K, const EplJ<T>& J, T x, T y, T gbx, T gby,
