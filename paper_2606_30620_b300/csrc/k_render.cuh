@@ -858,6 +858,20 @@ __global__ void __launch_bounds__(CTA_R, NEAR ? 1 : (sizeof(T) == 4 && !LIN ? 6 
     __shared__ TP wacc[NW][NACC_FIX];
     __shared__ __align__(8) uint64_t mbar;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if constexpr (NEAR) {
+        // a CTA of the near-core pass with no share of the list (the list is short)
+        // writes its zero row and leaves before any set-up
+        const int nu_ = E.n_cta_r * (CTA_R / 32);
+        const int tot_ = max(0, min(E.useg[nu_], E.n_img * E.n_img * E.s * E.s));
+        const int cnt_ = max(0, min(E.nseg[nu_], tot_));
+        const int per_ = max(1, (cnt_ + NEAR_CTAS * CTA_R - 1) / (NEAR_CTAS * CTA_R));
+        if (tile * CTA_R * per_ >= cnt_) {
+            double* o0 = E.apart + E.n_cta_adj + tile;
+            const int nc0 = NACC_FIX + 4 * K + 5 * (E.sub_kind ? E.n_sub : 0);
+            for (int i = threadIdx.x; i < nc0; i += blockDim.x) o0[(size_t)i * E.n_row_adj] = 0.0;
+            return;
+        }
+    }
     render_setup<T>(E, sh);
     // the lens in double for the float path's FP64 islands (the near-core pass; the
     // unsmoothed map's positions), loaded by the instantiations that use it
@@ -903,15 +917,18 @@ __global__ void __launch_bounds__(CTA_R, NEAR ? 1 : (sizeof(T) == 4 && !LIN ? 6 
         lin_bins<T>(E, 1, lbo[1], lbs[1]);
         lin_bins<double>(E, 0, lbo_d[0], lbs_d[0]);
         lin_bins<double>(E, 1, lbo_d[1], lbs_d[1]);
-        if constexpr (sizeof(T) == 4) {
-            // the double-float lens of the unsmoothed map's positions
-            __shared__ LensK<DF> kdf_s;
-            kdf = &kdf_s;
-            __syncthreads();
-            if (Kdp->nsub == 0) lensk_to_df(*Kdp, kdf_s);
-            __syncthreads();
-        }
     }
+    if constexpr (sizeof(T) == 4 && (LIN || NEAR)) {
+        // the double-float lens (no subhaloes): the unsmoothed map's positions, and
+        // the near-core pass's lens and lens adjoint (about 48 bits on the FP32 pipes)
+        __shared__ LensK<DF> kdf_s;
+        kdf = &kdf_s;
+        __syncthreads();
+        if (Kdp->nsub == 0) lensk_to_df(*Kdp, kdf_s);
+        __syncthreads();
+    }
+    // the near-core pass in double-float when there are no subhaloes
+    const bool near_df = NEAR && kdf != nullptr && Kdp->nsub == 0;
     const int* off = E.ccount + nc * nc;
     R4* rec = reinterpret_cast<R4*>(E.rec);
     R2* gbuf = reinterpret_cast<R2*>(E.gbuf);
@@ -1005,12 +1022,20 @@ __global__ void __launch_bounds__(CTA_R, NEAR ? 1 : (sizeof(T) == 4 && !LIN ? 6 
                 constexpr bool near = NEAR;
                 EplJ<T> J;
                 EplJ<double> Jd;
+                EplJ<DF> Jf;
                 double xd = 0.0, yd = 0.0;
                 T bx, by;
                 double bxd = 0.0, byd = 0.0;
                 if (near) {
                     ray_pos(E.n_img, E.pix, s, pixel, q, xd, yd);
-                    lens_beta_eval(*Kdp, xd, yd, Jd, bxd, byd);
+                    if (near_df) {
+                        DF bxf, byf;
+                        lens_beta_eval_smooth(*kdf, DF(xd), DF(yd), Jf, bxf, byf);
+                        bxd = bxf.to_double();
+                        byd = byf.to_double();
+                    } else {
+                        lens_beta_eval(*Kdp, xd, yd, Jd, bxd, byd);
+                    }
                     bx = (T)bxd;
                     by = (T)byd;
                 } else {
@@ -1072,7 +1097,15 @@ __global__ void __launch_bounds__(CTA_R, NEAR ? 1 : (sizeof(T) == 4 && !LIN ? 6 
                 acc[10] -= (gz0 * z[0] + gz1 * z[1]) * isg;
                 if (near) {
                     double o8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-                    lens_beta_vjp(*Kdp, Jd, xd, yd, (double)gb0, (double)gb1, o8);
+                    if (near_df) {
+                        const DF zero(0.0f, 0.0f);
+                        DF o8f[8] = {zero, zero, zero, zero, zero, zero, zero, zero};
+                        lens_beta_vjp(*kdf, Jf, DF(xd), DF(yd), DF((double)gb0), DF((double)gb1), o8f);
+#pragma unroll
+                        for (int p = 0; p < 8; ++p) o8[p] = o8f[p].to_double();
+                    } else {
+                        lens_beta_vjp(*Kdp, Jd, xd, yd, (double)gb0, (double)gb1, o8);
+                    }
 #pragma unroll
                     for (int p = 0; p < 8; ++p) acc[p] += (T)o8[p];
                 } else {
