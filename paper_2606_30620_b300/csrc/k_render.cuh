@@ -951,20 +951,24 @@ __global__ void __launch_bounds__(CTA_R, NEAR ? 1 : (sizeof(T) == 4 && !LIN ? 6 
             const int key = __shfl_sync(0xffffffffu, cj[a], __ffs(m) - 1);
             const bool in = need && cj[a] == key;
             m &= ~__ballot_sync(0xffffffffu, in);
-            T v0 = in ? ca[a][0] : T(0), v1 = in ? ca[a][1] : T(0);
-            T v2 = in ? ca[a][2] : T(0), v3 = in ? ca[a][3] : T(0);
+            const T v0 = in ? ca[a][0] : T(0), v1 = in ? ca[a][1] : T(0);
+            const T v2 = in ? ca[a][2] : T(0), v3 = in ? ca[a][3] : T(0);
+            // the four warp sums by a transposing butterfly: at xor 16 the lower half
+            // keeps (v0, v1) and the upper (v2, v3), at xor 8 each quarter keeps one,
+            // then three levels on it -- 6 shuffles instead of 20; lanes 0, 8, 16, 24
+            // end with the sums of v0 (X, key), v1 (X, key+1), v2 (d, key), v3 (d, key+1)
+            const bool up = lane & 16, h8 = lane & 8;
+            T k0 = up ? v2 : v0, k1 = up ? v3 : v1;
+            k0 += __shfl_xor_sync(0xffffffffu, up ? v0 : v2, 16);
+            k1 += __shfl_xor_sync(0xffffffffu, up ? v1 : v3, 16);
+            T kk = h8 ? k1 : k0;
+            kk += __shfl_xor_sync(0xffffffffu, h8 ? k0 : k1, 8);
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                v0 += __shfl_down_sync(0xffffffffu, v0, o);
-                v1 += __shfl_down_sync(0xffffffffu, v1, o);
-                v2 += __shfl_down_sync(0xffffffffu, v2, o);
-                v3 += __shfl_down_sync(0xffffffffu, v3, o);
-            }
-            if (lane == 0) {
-                TP* tX = mytab + a * K;
-                TP* tD = mytab + 2 * K + a * K;
-                if (key >= 0) { pair_add(tX[key], v0); pair_add(tD[key], v2); }
-                if (key + 1 <= K - 1) { pair_add(tX[key + 1], v1); pair_add(tD[key + 1], v3); }
+            for (int o = 4; o > 0; o >>= 1) kk += __shfl_xor_sync(0xffffffffu, kk, o);
+            if ((lane & 7) == 0) {
+                const int c = lane >> 3;
+                const int at = key + (c & 1);
+                if (at >= 0 && at <= K - 1) pair_add(mytab[(c >= 2 ? 2 * K : 0) + a * K + at], kk);
             }
         }
         __syncwarp();
