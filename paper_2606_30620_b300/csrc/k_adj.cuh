@@ -225,7 +225,7 @@ __global__ void __launch_bounds__(CTA_C) k_centre_adj(const __grid_constant__ Ba
     double* out = E.cadj + (size_t)tile * nl;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int p = 0; p < 8; ++p) {
-        const double v = warp_sum(acc[p]);
+        const double v = warp_sum_lane0(acc[p]);
         if (lane == 0) red[wid][p] = v;
     }
     __syncthreads();
@@ -239,7 +239,7 @@ __global__ void __launch_bounds__(CTA_C) k_centre_adj(const __grid_constant__ Ba
         T a5[5] = {T(0), T(0), T(0), T(0), T(0)};
         if (k < N) sub_vjp<T>(L, h, (T)xd, (T)yd, (T)gb[0], (T)gb[1], a5);
         for (int c = 0; c < 5; ++c) {
-            const double v = warp_sum(a5[c]);
+            const double v = warp_sum_lane0(a5[c]);
             if (lane == 0) red[wid][c] = v;
         }
         __syncthreads();

@@ -239,8 +239,9 @@ __global__ void __launch_bounds__(PSFT_NT) k_psf_like_t(const __grid_constant__ 
             if (E.mask[j * n + i]) r2mf += r * r;
         }
     }
-    // per-thread float partials of 8 pixels, then double across threads
-    double r2 = warp_sum((double)r2f), r2m = warp_sum((double)r2mf);
+    // per-thread float partials of 8 pixels, a compensated warp tree, then double
+    // across warps
+    const double r2 = warp_sum_lane0(r2f), r2m = warp_sum_lane0(r2mf);
     if ((threadIdx.x & 31) == 0) { red[0][threadIdx.x >> 5] = r2; red[1][threadIdx.x >> 5] = r2m; }
     __syncthreads();
     if (threadIdx.x < 2) {
@@ -387,8 +388,9 @@ __global__ void __launch_bounds__(PSFS_NT) k_psf_like_sep(const __grid_constant_
             if (E.mask[j * n + i]) r2mt += r * r;
         }
     }
-    // per-thread partials of 4 pixels, then double across threads, fixed order
-    const double r2 = warp_sum((double)r2t), r2m = warp_sum((double)r2mt);
+    // per-thread partials of 4 pixels, a (compensated, for float) warp tree, then
+    // double across warps, fixed order
+    const double r2 = warp_sum_lane0(r2t), r2m = warp_sum_lane0(r2mt);
     if ((threadIdx.x & 31) == 0) { red[0][threadIdx.x >> 5] = r2; red[1][threadIdx.x >> 5] = r2m; }
     __syncthreads();
     if (threadIdx.x < 2) {

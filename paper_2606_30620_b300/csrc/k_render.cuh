@@ -1214,7 +1214,7 @@ __global__ void __launch_bounds__(CTA_R) k_sub_adj(const __grid_constant__ Batch
         }
 #pragma unroll
         for (int c = 0; c < 5; ++c) {
-            const double v = warp_sum(a5[c]);
+            const double v = warp_sum_lane0(a5[c]);
             if (lane == 0) wsub[wid][c] = v;
         }
         __syncthreads();

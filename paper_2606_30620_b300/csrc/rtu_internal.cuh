@@ -74,7 +74,8 @@ struct EvalArgs {
     int* ccnt;         // [3] CTA-completion counters of those two kernels and of the
                        // likelihood kernel (whose last CTA finishes the forward)
     int* cbin;         // [2][n_mask] level-1 histogram bin of each centre ray
-    double* cadj;      // [n_cta_c][8 + 5 n_sub] centre-ray adjoint lens partials
+    double* cadj;      // [n_cta_c + 1][8 + 5 n_sub] centre-ray adjoint lens partials; the last
+                       // row the selected-rank terms
     int* hist;         // [2][HB] level-1 histograms
     double* trd;       // transform, double (layout in tr_* helpers)
     float* trf;        // transform, float copy
@@ -281,6 +282,13 @@ __device__ __forceinline__ float2 warp_pair_sum(float v) {
     return make_float2(a.hi, a.lo);
 }
 __device__ __forceinline__ double2 warp_pair_sum(double v) { return make_double2(warp_sum(v), 0.0); }
+// the warp sum (compensated pair for float) as a double, formed in lane 0 only (the
+// other lanes get 0): the FP64 conversion is not repeated on every lane
+template <typename T>
+__device__ __forceinline__ double warp_sum_lane0(T v) {
+    const auto p = warp_pair_sum(v);
+    return (threadIdx.x & 31) == 0 ? (double)p.x + (double)p.y : 0.0;
+}
 template <typename T> struct real4_of;
 template <> struct real4_of<float> { typedef float4 type; };
 template <> struct real4_of<double> { typedef double4_32a type; };
