@@ -175,6 +175,35 @@ def test_graph_replay_matches_plain_launches(rtu):
     assert not np.array_equal(plain2[0][0], plain[0][0])
 
 
+def test_graph_replay_cache_eviction(rtu):
+    # more recorded calls than the per-thread cache keeps (10 systems x forward and
+    # adjoint > 8 graphs): an evicted call is recorded again when it repeats, and every
+    # call gives the plain launches' image and statistics
+    mocks = [I.config_tiny(seed=90 + k) for k in range(10)]
+    runs = []
+    for m in mocks:
+        b = rtu.Binding(rtu.System.from_mock(m, precision=rtu.RTU_F32), m.lens, m.latents, m.ps, want_model=True)
+        runs.append((b, rtu.Batch([b])))
+
+    def step(run):
+        b, batch = run
+        batch.forward()
+        batch.adjoint()
+        torch.cuda.synchronize()
+        return b.model.cpu().numpy().copy(), b.stats.cpu().numpy().copy(), b.g_lens.cpu().numpy().copy()
+
+    rtu.graph_replay(False)
+    try:
+        plain = [step(r) for r in runs]
+    finally:
+        rtu.graph_replay(True)
+    for _ in range(3):          # plain, recorded, then recorded again after eviction
+        for r, p in zip(runs, plain):
+            got = step(r)
+            assert np.array_equal(got[0], p[0]) and np.array_equal(got[1], p[1])
+            assert G.rel_l2(got[2], p[2]) < 1e-12
+
+
 def test_batch_equals_alone(rtu):
     # every step is per evaluation, so a batch gives each system its own result;
     # the per-cell source-gradient sums run over counting-sorted records whose
