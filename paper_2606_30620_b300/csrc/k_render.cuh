@@ -418,6 +418,16 @@ __device__ inline bool tile_out_of_reach(const EvalArgs& E, int tile) {
     return out;
 }
 
+// the tile test for every render tile of an evaluation, one thread per tile, after
+// the transform is built (k_render reads the byte instead of testing in one thread)
+constexpr int CULL_NT = 256;
+__global__ void __launch_bounds__(CULL_NT) k_cull_tiles(const __grid_constant__ Batch B) {
+    const int ev = find_eval(B, blockIdx.x);
+    const EvalArgs& E = B.e[ev];
+    const int tile = (blockIdx.x - B.tile0[ev]) * CULL_NT + threadIdx.x;
+    if (tile < E.n_cta_r) E.tcull[tile] = tile_out_of_reach(E, tile) ? 1 : 0;
+}
+
 // S7 + S11: one thread per image pixel, s^2 sub-rays each.  LIN: the unsmoothed
 // eCDF map (its own instantiation, so the smoothed map's code is not burdened).
 template <typename T, bool LIN>
@@ -437,7 +447,7 @@ __global__ void __launch_bounds__(CTA_R, sizeof(T) == 4 && !LIN ? 8 : 6) k_rende
     const int s = E.s, s2 = E.s * E.s;
     if (threadIdx.x == 0) {
         cnt_sh = 0;
-        cull_sh = tile_out_of_reach(E, tile) ? 1 : 0;
+        cull_sh = E.tcull[tile];
     }
     __syncthreads();
     if (cull_sh) {

@@ -145,6 +145,7 @@ size_t slot_layout(const rtu_system_desc& d, char* base, EvalArgs* e) {
     p = take(ni * 4);                                 if (e) e->pcnt = (int*)p;
     p = take((size_t)z.n_rays * 4);                   if (e) e->rval = (float*)p;
     p = take((size_t)(z.n_cta_r + 1) * 4);            if (e) e->cta_cnt = (int*)p;
+    p = take((size_t)z.n_cta_r);                      if (e) e->tcull = (unsigned char*)p;
     p = take((size_t)(z.n_cta_r * (CTA_R / 32) + 1) * 4); if (e) e->useg = (int*)p;
     p = take((size_t)(z.n_cta_r * (CTA_R / 32) + 1) * 4); if (e) e->nseg = (int*)p;
     p = take((size_t)z.n_rays * 4);                   if (e) e->nlist = (int*)p;
@@ -581,6 +582,7 @@ int t_adj(const EvalArgs& e) { return e.n_cta_adj; }
 int t_psf_gen(const EvalArgs& e) { return e.psf_uv ? 0 : e.n_cta_p; }
 int t_psf_sep(const EvalArgs& e) { return e.psf_uv ? e.n_cta_p : 0; }
 int t_edge(const EvalArgs&) { return EDGE_CTAS; }
+int t_cull(const EvalArgs& e) { return (e.n_cta_r + CULL_NT - 1) / CULL_NT; }
 int t_units(const EvalArgs& e) { return (e.n_cta_r * (CTA_R / 32) + CMP_NT / 32 - 1) / (CMP_NT / 32); }
 int t_cells(const EvalArgs& e) {
     const int nc = (e.n_src - 1) * (e.n_src - 1);
@@ -657,6 +659,7 @@ rtu_status run_chunk(Batch& B, int phase, cudaStream_t st, const SideStream& ss)
         if ((r = launch("k_centre_hist", k_centre_hist, B, t_centre, CTA_C, 0, sg))) return r;
         if ((r = launch("k_select_fit", k_select_fit, B, t_two_fit, SEL_NT, SEL_SMEM, sg))) return r;
         if ((r = launch("k_lin_sort", k_lin_sort, B, t_two_lin, LIN_NT, 0, sg))) return r;
+        if ((phase & PH_FORWARD) && (r = launch("k_cull_tiles", k_cull_tiles, B, t_cull, CULL_NT, 0, sg))) return r;
         if (fork)
             for (int pass = 0; pass < GP_PASSES; ++pass)
                 if ((r = launch("k_gp_source", k_gp_lines<T>, B, t_gp_lines, GP_LINE_NT, 0, st, pass))) return r;

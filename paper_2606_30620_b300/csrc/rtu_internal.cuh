@@ -106,6 +106,7 @@ struct EvalArgs {
     int* pcnt;         // [n_img^2] deferred sub-rays of the pixel still to finish (float mode)
     float* rval;       // [n_rays] values of deferred rays (float mode)
     int* cta_cnt;      // [n_cta_r] in-grid rays per render CTA (the N_IN_GRID statistic)
+    unsigned char* tcull;  // [n_cta_r] 1: no ray of the render tile can reach the grid
     int* useg;         // [n_cta_r * CTA_R/32 + 1] staged rays per render warp, then exclusive offsets
     int* kray;         // [n_rays] the adjoint's rays (staged rays in render-warp order): ray id, or -1
     int* kcell;        // [n_rays] their cells; -2 - cell for a near-core ray of the float path
