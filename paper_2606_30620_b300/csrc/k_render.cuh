@@ -15,15 +15,31 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-// Stage `bytes` from global to shared.  Bulk path: bytes % 16 == 0 and both
-// addresses 16-byte aligned; otherwise plain loads.  The wait is bounded: on
-// give-up the flag word gets F_TIMEOUT and the caller skips its work.
-// Returns false on timeout.  Must be called by all threads of the CTA.
-__device__ __forceinline__ bool stage_to_smem(void* dst, const void* src, uint32_t bytes, uint64_t* mbar,
-                                              int* flags) {
-    const bool bulk = (bytes % 16u == 0u) && ((reinterpret_cast<uintptr_t>(src) & 15u) == 0u) &&
-                      ((smem_u32(dst) & 15u) == 0u) && bytes > 0u;
-    if (!bulk) {
+// Stage `bytes` from global to shared in two parts, so that the copy runs while the
+// CTA does other set-up: stage_begin (thread 0 initialises the barrier and issues the
+// bulk copy; no CTA barrier) and stage_end (every thread; the wait).  Bulk path:
+// bytes % 16 == 0 and both addresses 16-byte aligned; otherwise stage_end copies with
+// plain loads.  No thread may leave between the two parts (a copy would be in flight).
+// The wait is bounded: on give-up the flag word gets F_TIMEOUT and stage_end returns
+// false after a second bounded wait for the copy; the caller then skips its work.
+__device__ __forceinline__ bool stage_is_bulk(const void* dst, const void* src, uint32_t bytes) {
+    return (bytes % 16u == 0u) && ((reinterpret_cast<uintptr_t>(src) & 15u) == 0u) &&
+           ((smem_u32(dst) & 15u) == 0u) && bytes > 0u;
+}
+__device__ __forceinline__ void stage_begin(void* dst, const void* src, uint32_t bytes, uint64_t* mbar) {
+    if (!stage_is_bulk(dst, src, bytes) || threadIdx.x != 0) return;
+    const uint32_t mb = smem_u32(mbar);
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(bytes) : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(mb)
+        : "memory");
+}
+__device__ __forceinline__ bool stage_end(void* dst, const void* src, uint32_t bytes, uint64_t* mbar, int* flags) {
+    if (!stage_is_bulk(dst, src, bytes)) {
         const unsigned char* s = static_cast<const unsigned char*>(src);
         unsigned char* d = static_cast<unsigned char*>(dst);
         for (uint32_t i = threadIdx.x; i < bytes; i += blockDim.x) d[i] = s[i];
@@ -31,19 +47,7 @@ __device__ __forceinline__ bool stage_to_smem(void* dst, const void* src, uint32
         return true;
     }
     const uint32_t mb = smem_u32(mbar);
-    if (threadIdx.x == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb));
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(bytes) : "memory");
-        asm volatile(
-            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                smem_u32(dst)),
-            "l"(src), "r"(bytes), "r"(mb)
-            : "memory");
-    }
+    __syncthreads();         // the barrier's initialisation is visible to every thread
     // bounded wait on phase 0
     uint32_t done = 0;
     for (int it = 0; it < (1 << 22) && !done; ++it) {
@@ -461,8 +465,10 @@ __global__ void __launch_bounds__(CTA_R, sizeof(T) == 4 && !LIN ? 8 : 6) k_rende
         if (E.image_out) reinterpret_cast<T*>(E.image_out)[pixel] = T(0);
         return;
     }
+    // the source grid's copy runs beside the set-up
+    stage_begin(sgrid, E.src, (uint32_t)(n * n * sizeof(T)), &mbar);
     render_setup<T>(E, sh);
-    if (!stage_to_smem(sgrid, E.src, (uint32_t)(n * n * sizeof(T)), &mbar, E.flags)) {
+    if (!stage_end(sgrid, E.src, (uint32_t)(n * n * sizeof(T)), &mbar, E.flags)) {
         // the copy timed out (flagged): this tile stages nothing
         if (threadIdx.x < CTA_R / 32) E.useg[tile * (CTA_R / 32) + threadIdx.x] = 0;
         if (threadIdx.x < CTA_R / 32) E.nseg[tile * (CTA_R / 32) + threadIdx.x] = 0;
@@ -882,6 +888,8 @@ __global__ void __launch_bounds__(CTA_R, NEAR ? 1 : (sizeof(T) == 4 && !LIN ? 6 
             return;
         }
     }
+    // the source grid's copy runs beside the set-up
+    stage_begin(sgrid, E.src, (uint32_t)(n * n * sizeof(T)), &mbar);
     render_setup<T>(E, sh);
     // the lens in double for the float path's FP64 islands (the near-core pass; the
     // unsmoothed map's positions), loaded by the instantiations that use it
@@ -892,7 +900,7 @@ __global__ void __launch_bounds__(CTA_R, NEAR ? 1 : (sizeof(T) == 4 && !LIN ? 6 
         Kdp = &kd_s;
     }
     for (int i = threadIdx.x; i < NW * 4 * K; i += blockDim.x) { tab[i].x = T(0); tab[i].y = T(0); }
-    const bool staged = stage_to_smem(sgrid, E.src, (uint32_t)(n * n * sizeof(T)), &mbar, E.flags);
+    const bool staged = stage_end(sgrid, E.src, (uint32_t)(n * n * sizeof(T)), &mbar, E.flags);
     // column-major partials: column i of this CTA's row at apart[i * n_row_adj + row];
     // the near-core pass also owns the subhalo columns of its rows (zero: k_sub_adj
     // takes every ray in its own rows)
