@@ -530,6 +530,22 @@ __global__ void __launch_bounds__(SEL_NT) k_select_fit(const __grid_constant__ B
         }
     }
     if (tid == 0 && flag_sh) atomicOr(E.flags, flag_sh);
+    // the last of the evaluation's two CTAs to finish (an atomic counter after a fence)
+    // tests every render tile against the grid's reach, reading the other axis's float
+    // transform through L2: k_render reads one byte per tile
+    __shared__ int last_sf;
+    __shared__ float reach[4];
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) last_sf = atomicAdd(E.ccnt + 3, 1) == 1;
+    __syncthreads();
+    if (!last_sf) return;
+    if (tid == 0) {
+        grid_reach(E, true, reach);
+        E.ccnt[3] = 0;
+    }
+    __syncthreads();
+    for (int t = tid; t < E.n_cta_r; t += SEL_NT) E.tcull[t] = tile_out_of_reach(E, t, reach) ? 1 : 0;
 }
 
 // ------------------------------------------------ the unsmoothed eCDF transform

@@ -251,7 +251,6 @@ __device__ __forceinline__ void load_transform(const EvalArgs& E, T* trs, T* U) 
 // order.  So the integer
 // cell of every ray -- the rays-per-cell histogram and the kink of the bilinear
 // slope the adjoint differentiates -- is the double-precision decision.
-constexpr float EDGE_DELTA = 2e-3f;
 
 __device__ __forceinline__ bool near_edge(float gx, float gy, int n) {
     const float lo = -EDGE_DELTA, hi = (float)(n - 1) + EDGE_DELTA;
@@ -353,83 +352,18 @@ __device__ __forceinline__ void render_setup(const EvalArgs& E, RenderShared<T>&
     }
 }
 
-// True when no sub-ray of render tile `tile` can reach the RTU grid (its z range
-// plus the near-edge margin), so that every ray would take the "far outside" exit:
-// the tile's ray positions lie in a box; there the EPL deflection is at most
-// P_max (1 + f/(1 - f)) (|c_n| < f, |w| = 1) with P = pref0 (b/R)^(t-1) taken at the
-// box's smallest (t > 1) or largest (t < 1) elliptical radius R -- R >= q |theta - c|,
-// and R is convex so its maximum sits at a corner -- and the shear deflection is
-// linear (extremes at the corners).  Evaluated in float by one thread from the
-// float lens block, with slack far above float rounding.  Tiles with subhaloes are
-// never culled.
-__device__ inline bool tile_out_of_reach(const EvalArgs& E, int tile) {
-    const LensK<float>& Kf = *reinterpret_cast<const LensK<float>*>(lensk_src<float>(E.lensk));
-    if (Kf.nsub > 0) return false;
-    const int n = E.n_img, tx_n = render_tiles_x(n);
-    const int ty = tile / tx_n, tx = tile - ty * tx_n;
-    const int i0 = tx * RT_X, i1 = min(i0 + RT_X - 1, n - 1);
-    const int j0 = ty * RT_Y, j1 = min(j0 + RT_Y - 1, n - 1);
-    const float c = 0.5f * (n - 1), pix = (float)E.pix;
-    const float omin = (0.5f / E.s - 0.5f) * pix, omax = ((E.s - 0.5f) / E.s - 0.5f) * pix;
-    const float xl = (i0 - c) * pix + omin, xh = (i1 - c) * pix + omax;
-    const float yl = (j0 - c) * pix + omin, yh = (j1 - c) * pix + omax;
-    const EplC<float>& C = Kf.C;
-    // elliptical radius bounds over the box
-    const float cx = fminf(fmaxf(C.x0, xl), xh), cy = fminf(fmaxf(C.y0, yl), yh);
-    const float dmin = sqrtf((cx - C.x0) * (cx - C.x0) + (cy - C.y0) * (cy - C.y0));
-    float rmax = 0.0f, shx_lo = 1e30f, shx_hi = -1e30f, shy_lo = 1e30f, shy_hi = -1e30f;
-    for (int k = 0; k < 4; ++k) {
-        const float x = (k & 1) ? xh : xl, y = (k & 2) ? yh : yl;
-        const float dx = x - C.x0, dy = y - C.y0;
-        const float xr = C.cp * dx + C.sp * dy, yr = C.cp * dy - C.sp * dx;
-        rmax = fmaxf(rmax, sqrtf(C.q * C.q * xr * xr + yr * yr));
-        const float sx = Kf.g1 * x + Kf.g2 * y, sy = Kf.g2 * x - Kf.g1 * y;
-        shx_lo = fminf(shx_lo, sx); shx_hi = fmaxf(shx_hi, sx);
-        shy_lo = fminf(shy_lo, sy); shy_hi = fmaxf(shy_hi, sy);
-    }
-    const float rmin = C.q * dmin * 0.999f;
-    const float e = C.t - 1.0f;
-    float pmax;
-    if (e > 1e-6f) {
-        if (rmin < 1e-4f) return false;
-        pmax = C.pref0 * powf(C.b / rmin, e);
-    } else if (e < -1e-6f) {
-        pmax = C.pref0 * powf(C.b / fmaxf(rmax * 1.001f, 1e-6f), e);
-    } else {
-        pmax = C.pref0 * powf(fmaxf(C.b / fmaxf(rmin, 1e-4f), fmaxf(rmax, 1e-4f) / C.b), fabsf(e));
-    }
-    const float amax = pmax * (1.0f + C.ftail) * 1.001f + 1e-4f;
-    const float sh_slack = 1e-5f * (fabsf(xl) + fabsf(xh) + fabsf(yl) + fabsf(yh) + 1.0f);
-    // beta = theta - alpha_EPL - alpha_shear ranges per axis
-    const float bxl = xl - shx_hi - amax - sh_slack, bxh = xh - shx_lo + amax + sh_slack;
-    const float byl = yl - shy_hi - amax - sh_slack, byh = yh - shy_lo + amax + sh_slack;
-    // the grid's reach in beta: z in [zlo, zhi] as in the ray test, with slack
-    const int K = E.n_nodes + 2;
-    const float* tr = E.trf;
-    const float m = 4.0f * EDGE_DELTA / (E.n_src - 1);
-    bool out = false;
-    for (int a = 0; a < 2; ++a) {
-        const float* X = tr + TR_HDR + a * K;
-        const float* d = tr + TR_HDR + (2 + a) * K;
-        float zlo = X[0] - m / d[0], zhi = X[K - 1] + m / d[K - 1];
-        zlo -= 1e-3f * (1.0f + fabsf(zlo));
-        zhi += 1e-3f * (1.0f + fabsf(zhi));
-        const float lo = tr[a] + zlo * tr[2], hi = tr[a] + zhi * tr[2];
-        const float lo_s = lo - 1e-5f * (1.0f + fabsf(lo)), hi_s = hi + 1e-5f * (1.0f + fabsf(hi));
-        const float bl = a == 0 ? bxl : byl, bh = a == 0 ? bxh : byh;
-        out |= bh < lo_s || bl > hi_s;
-    }
-    return out;
-}
-
-// the tile test for every render tile of an evaluation, one thread per tile, after
-// the transform is built (k_render reads the byte instead of testing in one thread)
+// the tile test for every render tile of an evaluation, one thread per tile (the
+// unsmoothed map's systems; the smoothed grid's last k_select_fit CTA does it for its
+// own), after the transform is built: k_render reads the byte
 constexpr int CULL_NT = 256;
 __global__ void __launch_bounds__(CULL_NT) k_cull_tiles(const __grid_constant__ Batch B) {
     const int ev = find_eval(B, blockIdx.x);
     const EvalArgs& E = B.e[ev];
+    __shared__ float reach[4];
+    if (threadIdx.x == 0) grid_reach(E, false, reach);
+    __syncthreads();
     const int tile = (blockIdx.x - B.tile0[ev]) * CULL_NT + threadIdx.x;
-    if (tile < E.n_cta_r) E.tcull[tile] = tile_out_of_reach(E, tile) ? 1 : 0;
+    if (tile < E.n_cta_r) E.tcull[tile] = tile_out_of_reach(E, tile, reach) ? 1 : 0;
 }
 
 // S7 + S11: one thread per image pixel, s^2 sub-rays each.  LIN: the unsmoothed

@@ -350,7 +350,7 @@ __global__ void __launch_bounds__(256) k_zero(const __grid_constant__ Batch B, i
         if (i < nh) E.hist[i] = 0; else E.ccount[i - nh] = 0;
     }
     if (tile == 0) {
-        if (threadIdx.x == 0) { *E.flags = 0; *E.ecount = 0; E.ccnt[0] = 0; E.ccnt[1] = 0; E.ccnt[2] = 0; }
+        if (threadIdx.x == 0) { *E.flags = 0; *E.ecount = 0; E.ccnt[0] = 0; E.ccnt[1] = 0; E.ccnt[2] = 0; E.ccnt[3] = 0; }
         const int nsub = E.sub_kind ? E.n_sub : 0;
         lens_setup_par(reinterpret_cast<LensK<double>*>(E.lensk),
                        reinterpret_cast<LensK<float>*>(static_cast<char*>(E.lensk) + LENSK_D_BYTES), E.lens,
@@ -582,7 +582,7 @@ int t_adj(const EvalArgs& e) { return e.n_cta_adj; }
 int t_psf_gen(const EvalArgs& e) { return e.psf_uv ? 0 : e.n_cta_p; }
 int t_psf_sep(const EvalArgs& e) { return e.psf_uv ? e.n_cta_p : 0; }
 int t_edge(const EvalArgs&) { return EDGE_CTAS; }
-int t_cull(const EvalArgs& e) { return (e.n_cta_r + CULL_NT - 1) / CULL_NT; }
+int t_cull_lin(const EvalArgs& e) { return is_lin(e) ? (e.n_cta_r + CULL_NT - 1) / CULL_NT : 0; }
 int t_units(const EvalArgs& e) { return (e.n_cta_r * (CTA_R / 32) + CMP_NT / 32 - 1) / (CMP_NT / 32); }
 int t_cells(const EvalArgs& e) {
     const int nc = (e.n_src - 1) * (e.n_src - 1);
@@ -659,7 +659,8 @@ rtu_status run_chunk(Batch& B, int phase, cudaStream_t st, const SideStream& ss)
         if ((r = launch("k_centre_hist", k_centre_hist, B, t_centre, CTA_C, 0, sg))) return r;
         if ((r = launch("k_select_fit", k_select_fit, B, t_two_fit, SEL_NT, SEL_SMEM, sg))) return r;
         if ((r = launch("k_lin_sort", k_lin_sort, B, t_two_lin, LIN_NT, 0, sg))) return r;
-        if ((phase & PH_FORWARD) && (r = launch("k_cull_tiles", k_cull_tiles, B, t_cull, CULL_NT, 0, sg))) return r;
+        if ((phase & PH_FORWARD) && (r = launch("k_cull_tiles", k_cull_tiles, B, t_cull_lin, CULL_NT, 0, sg)))
+            return r;
         if (fork)
             for (int pass = 0; pass < GP_PASSES; ++pass)
                 if ((r = launch("k_gp_source", k_gp_lines<T>, B, t_gp_lines, GP_LINE_NT, 0, st, pass))) return r;

@@ -71,8 +71,9 @@ struct EvalArgs {
     double* mom;       // [8] of the centre rays: mean x, y; min x, max x; min y, max y;
                        // sum of squared deviations x, y (each written once per call by the
                        // last CTA of k_trace_centres / k_centre_hist to finish)
-    int* ccnt;         // [3] CTA-completion counters of those two kernels and of the
-                       // likelihood kernel (whose last CTA finishes the forward)
+    int* ccnt;         // [4] CTA-completion counters of those two kernels, of the
+                       // likelihood kernel (whose last CTA finishes the forward) and of
+                       // k_select_fit (whose last CTA tests the render tiles)
     int* cbin;         // [2][n_mask] level-1 histogram bin of each centre ray
     double* cadj;      // [n_cta_c + 1][8 + 5 n_sub] centre-ray adjoint lens partials; the last
                        // row the selected-rank terms
@@ -583,6 +584,82 @@ __device__ __forceinline__ int render_pixel(int n_img, int tile, int t, bool& va
     valid = i < n_img && j < n_img;
     return valid ? j * n_img + i : 0;
 }
+// Near-edge margin of the FP32 render: a ray whose grid coordinate lies within this
+// many cells of a cell edge or of the grid boundary is decided in double.
+constexpr float EDGE_DELTA = 2e-3f;
+
+// The RTU grid's reach in beta per axis, [reach[2a], reach[2a+1]]: the z range whose
+// image under the CDF comes within the near-edge margin of [0, 1] (the CDF is linear
+// beyond its end knots), with slack, mapped back through the standardisation.  From the
+// float transform; cg: read it through L2 (written by another CTA of the same kernel).
+__device__ inline void grid_reach(const EvalArgs& E, bool cg, float* reach) {
+    const int K = E.n_nodes + 2;
+    const float* tr = E.trf;
+    auto ld = [&](int i) { return cg ? __ldcg(tr + i) : tr[i]; };
+    const float m = 4.0f * EDGE_DELTA / (E.n_src - 1);
+    for (int a = 0; a < 2; ++a) {
+        const int X = TR_HDR + a * K, d = TR_HDR + (2 + a) * K;
+        float zlo = ld(X) - m / ld(d), zhi = ld(X + K - 1) + m / ld(d + K - 1);
+        zlo -= 1e-3f * (1.0f + fabsf(zlo));
+        zhi += 1e-3f * (1.0f + fabsf(zhi));
+        const float lo = ld(a) + zlo * ld(2), hi = ld(a) + zhi * ld(2);
+        reach[2 * a] = lo - 1e-5f * (1.0f + fabsf(lo));
+        reach[2 * a + 1] = hi + 1e-5f * (1.0f + fabsf(hi));
+    }
+}
+
+// True when no sub-ray of render tile `tile` can reach the RTU grid (beta beyond the
+// reach on an axis), so that every ray would take the "far outside" exit: the tile's
+// ray positions lie in a box; there the EPL deflection is at most
+// P_max (1 + f/(1 - f)) (|c_n| < f, |w| = 1) with P = pref0 (b/R)^(t-1) taken at the
+// box's smallest (t > 1) or largest (t < 1) elliptical radius R -- R >= q |theta - c|,
+// and R is convex so its maximum sits at a corner -- and the shear deflection is
+// linear (extremes at the corners).  Evaluated in float from the float lens block, with
+// slack far above float rounding.  Tiles with subhaloes are never culled.
+__device__ inline bool tile_out_of_reach(const EvalArgs& E, int tile, const float* reach) {
+    const LensK<float>& Kf = *reinterpret_cast<const LensK<float>*>(lensk_src<float>(E.lensk));
+    if (Kf.nsub > 0) return false;
+    const int n = E.n_img, tx_n = render_tiles_x(n);
+    const int ty = tile / tx_n, tx = tile - ty * tx_n;
+    const int i0 = tx * RT_X, i1 = min(i0 + RT_X - 1, n - 1);
+    const int j0 = ty * RT_Y, j1 = min(j0 + RT_Y - 1, n - 1);
+    const float c = 0.5f * (n - 1), pix = (float)E.pix;
+    const float omin = (0.5f / E.s - 0.5f) * pix, omax = ((E.s - 0.5f) / E.s - 0.5f) * pix;
+    const float xl = (i0 - c) * pix + omin, xh = (i1 - c) * pix + omax;
+    const float yl = (j0 - c) * pix + omin, yh = (j1 - c) * pix + omax;
+    const EplC<float>& C = Kf.C;
+    // elliptical radius bounds over the box
+    const float cx = fminf(fmaxf(C.x0, xl), xh), cy = fminf(fmaxf(C.y0, yl), yh);
+    const float dmin = sqrtf((cx - C.x0) * (cx - C.x0) + (cy - C.y0) * (cy - C.y0));
+    float rmax = 0.0f, shx_lo = 1e30f, shx_hi = -1e30f, shy_lo = 1e30f, shy_hi = -1e30f;
+    for (int k = 0; k < 4; ++k) {
+        const float x = (k & 1) ? xh : xl, y = (k & 2) ? yh : yl;
+        const float dx = x - C.x0, dy = y - C.y0;
+        const float xr = C.cp * dx + C.sp * dy, yr = C.cp * dy - C.sp * dx;
+        rmax = fmaxf(rmax, sqrtf(C.q * C.q * xr * xr + yr * yr));
+        const float sx = Kf.g1 * x + Kf.g2 * y, sy = Kf.g2 * x - Kf.g1 * y;
+        shx_lo = fminf(shx_lo, sx); shx_hi = fmaxf(shx_hi, sx);
+        shy_lo = fminf(shy_lo, sy); shy_hi = fmaxf(shy_hi, sy);
+    }
+    const float rmin = C.q * dmin * 0.999f;
+    const float e = C.t - 1.0f;
+    float pmax;
+    if (e > 1e-6f) {
+        if (rmin < 1e-4f) return false;
+        pmax = C.pref0 * powf(C.b / rmin, e);
+    } else if (e < -1e-6f) {
+        pmax = C.pref0 * powf(C.b / fmaxf(rmax * 1.001f, 1e-6f), e);
+    } else {
+        pmax = C.pref0 * powf(fmaxf(C.b / fmaxf(rmin, 1e-4f), fmaxf(rmax, 1e-4f) / C.b), fabsf(e));
+    }
+    const float amax = pmax * (1.0f + C.ftail) * 1.001f + 1e-4f;
+    const float sh_slack = 1e-5f * (fabsf(xl) + fabsf(xh) + fabsf(yl) + fabsf(yh) + 1.0f);
+    // beta = theta - alpha_EPL - alpha_shear ranges per axis
+    const float bxl = xl - shx_hi - amax - sh_slack, bxh = xh - shx_lo + amax + sh_slack;
+    const float byl = yl - shy_hi - amax - sh_slack, byh = yh - shy_lo + amax + sh_slack;
+    return bxh < reach[0] || bxl > reach[1] || byh < reach[2] || byl > reach[3];
+}
+
 // the ray id of staged entry `local` (lane s^2 + q) of render warp u
 __device__ __forceinline__ int staged_ray_id(int n_img, int s2, int u, int local) {
     const int lane = local / s2, q = local - lane * s2;
