@@ -212,18 +212,25 @@ def run_ours(args):
     n = len(mocks)
     n2 = mocks[0].n_src ** 2
     nps = mocks[0].ps.size
-    # packed inputs [lens(8) | ps(3)] as float64 and latents as float32; packed outputs
-    in_f64 = torch.empty(n, 8 + nps, dtype=torch.float64, device=dev)
-    in_lat = torch.empty(n, n2, dtype=torch.float32, device=dev)
+    # inputs [lens(8) | ps(3)] as float64 and latents as float32, outputs [stats | g_lens |
+    # g_ps] as float64 and g_latents as float32, each direction packed in one byte buffer
+    # (one copy each way per step) with typed views for the bindings
     NS = rtu.N_STATS
-    out_f64 = torch.empty(n, NS + 8 + nps, dtype=torch.float64, device=dev)
-    out_lat = torch.empty(n, n2, dtype=torch.float32, device=dev)
-    h_in_f64 = torch.tensor(np.stack([np.concatenate([m.lens, m.ps]) for m in mocks]), dtype=torch.float64).pin_memory()
-    h_in_lat = torch.tensor(np.stack([m.latents.ravel() for m in mocks]), dtype=torch.float32).pin_memory()
-    h_out_f64 = torch.empty_like(out_f64, device="cpu").pin_memory()
-    h_out_lat = torch.empty_like(out_lat, device="cpu").pin_memory()
-    in_f64.copy_(h_in_f64)
-    in_lat.copy_(h_in_lat)
+    a_in, a_out = n * (8 + nps) * 8, n * (NS + 8 + nps) * 8
+
+    def packed(a_bytes, device, pin=False):
+        buf = torch.empty(a_bytes + n * n2 * 4, dtype=torch.uint8, device=device)
+        if pin:
+            buf = buf.pin_memory()
+        return buf, buf[:a_bytes].view(torch.float64).view(n, -1), buf[a_bytes:].view(torch.float32).view(n, n2)
+
+    in_buf, in_f64, in_lat = packed(a_in, dev)
+    out_buf, out_f64, out_lat = packed(a_out, dev)
+    h_in_buf, h_in_f64, h_in_lat = packed(a_in, "cpu", pin=True)
+    h_out_buf, h_out_f64, h_out_lat = packed(a_out, "cpu", pin=True)
+    h_in_f64.copy_(torch.tensor(np.stack([np.concatenate([m.lens, m.ps]) for m in mocks]), dtype=torch.float64))
+    h_in_lat.copy_(torch.tensor(np.stack([m.latents.ravel() for m in mocks]), dtype=torch.float32))
+    in_buf.copy_(h_in_buf)
     binds = []
     for k, s in enumerate(systems):
         binds.append(rtu.Binding(s, in_f64[k, :8], in_lat[k].view(mocks[k].n_src, mocks[k].n_src),
@@ -340,11 +347,9 @@ def run_ours(args):
     for i in range(args.steps):
         flush.fill_(float(i))
         e0.record(stream)
-        in_f64.copy_(h_in_f64, non_blocking=True)
-        in_lat.copy_(h_in_lat, non_blocking=True)
+        in_buf.copy_(h_in_buf, non_blocking=True)
         step()
-        h_out_f64.copy_(out_f64, non_blocking=True)
-        h_out_lat.copy_(out_lat, non_blocking=True)
+        h_out_buf.copy_(out_buf, non_blocking=True)
         e1.record(stream)
         torch.cuda.synchronize()
         e_ms.append(e0.elapsed_time(e1))
