@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(SEL_ADJ_NT) k_sel_adj(const __grid_constant__ 
     // 48 bits) on the FP32 pipes: FP64 instructions are scarce on this part
     const bool use_df = !E.f64 && Ld.nsub == 0;
     if (use_df) {
-        lensk_to_df(Ld, Ldf);
+        load_lensk(Ldf, lensk_df_src(E.lensk));
         __syncthreads();
     }
     const int a = threadIdx.x / (2 * MAXM), t = threadIdx.x - a * 2 * MAXM;

@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(CTA_C, 5) k_trace_centres(const __grid_constan
     const bool use_df = !E.f64 && L.nsub == 0;
     __shared__ DF pix_df;
     if (use_df) {
-        lensk_to_df(L, Ldf);
+        load_lensk(Ldf, lensk_df_src(E.lensk));
         if (threadIdx.x == 0) pix_df = DF(E.pix);
         __syncthreads();
     }

@@ -583,7 +583,7 @@ __global__ void __launch_bounds__(EDGE_NT) k_render_edge(const __grid_constant__
     // CDF map and the cell decision in double
     const bool use_df = Kd.nsub == 0;
     if (use_df) {
-        lensk_to_df(Kd, Kdf);
+        load_lensk(Kdf, lensk_df_src(E.lensk));
         __syncthreads();
     }
     const int n = E.n_src, K = E.n_nodes + 2, s2 = E.s * E.s;
@@ -876,7 +876,7 @@ __global__ void __launch_bounds__(CTA_R, NEAR ? 1 : (sizeof(T) == 4 && !LIN ? 6 
         __shared__ LensK<DF> kdf_s;
         kdf = &kdf_s;
         __syncthreads();
-        if (Kdp->nsub == 0) lensk_to_df(*Kdp, kdf_s);
+        if (Kdp->nsub == 0) load_lensk(kdf_s, lensk_df_src(E.lensk));
         __syncthreads();
     }
     // the near-core pass in double-float when there are no subhaloes

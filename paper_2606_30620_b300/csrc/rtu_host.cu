@@ -355,6 +355,11 @@ __global__ void __launch_bounds__(256) k_zero(const __grid_constant__ Batch B, i
         lens_setup_par(reinterpret_cast<LensK<double>*>(E.lensk),
                        reinterpret_cast<LensK<float>*>(static_cast<char*>(E.lensk) + LENSK_D_BYTES), E.lens,
                        E.profile, E.sub_kind, nsub);
+        // the double-float copy, once per call (the kernels of the FP32 path's islands
+        // load it instead of converting per CTA)
+        __syncthreads();
+        lensk_to_df(*reinterpret_cast<const LensK<double>*>(E.lensk),
+                    *reinterpret_cast<LensK<DF>*>(static_cast<char*>(E.lensk) + LENSK_DF_AT));
     }
 }
 

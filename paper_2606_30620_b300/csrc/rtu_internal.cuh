@@ -499,9 +499,14 @@ __device__ inline void lensk_to_df(const LensK<double>& a, LensK<DF>& b) {
     }
 }
 
-// the evaluation's lens blocks: LensK<double> first, then LensK<float>
+// the evaluation's lens blocks: LensK<double> first, then LensK<float>, then the
+// double-float copy of the double block (written once per call by the lens set-up)
 constexpr size_t LENSK_D_BYTES = (sizeof(LensK<double>) + 255) / 256 * 256;
-constexpr size_t LENSK_BYTES = LENSK_D_BYTES + (sizeof(LensK<float>) + 255) / 256 * 256;
+constexpr size_t LENSK_DF_AT = LENSK_D_BYTES + (sizeof(LensK<float>) + 255) / 256 * 256;
+constexpr size_t LENSK_BYTES = LENSK_DF_AT + (sizeof(LensK<DF>) + 255) / 256 * 256;
+__host__ __device__ inline const void* lensk_df_src(const void* base) {
+    return static_cast<const char*>(base) + LENSK_DF_AT;
+}
 
 // copy a lens block from global memory into shared memory (all threads)
 template <typename T>
