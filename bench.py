@@ -53,11 +53,11 @@ FLOPS_ADJ_RAY = 2.5 * FLOPS_FWD_RAY
 # them in the grid), valid for the kernel sources with digest TRAFFIC_SRC_DIGEST.
 ROOF = {
     "k_render": {"flops_per_unit": FLOPS_FWD_RAY, "units": "supersampled rays",
-                 "traffic_per_unit": (0.333568e6 + 512) / 5120000},
+                 "traffic_per_unit": (0.335360e6 + 2560) / 5120000},
     "k_render_adj": {"flops_per_unit": FLOPS_ADJ_RAY, "units": "in-grid rays",
-                     "traffic_per_unit": (6.769664e6 + 52480) / 743894},
+                     "traffic_per_unit": (6.771456e6 + 50688) / 743894},
 }
-TRAFFIC_SRC_DIGEST = "828b90f43d45a70a"
+TRAFFIC_SRC_DIGEST = "8dd0852d3bf71804"
 KERNEL_SOURCES = ("k_render.cuh", "rtu_internal.cuh", "rtu_math.cuh", "rtu_df.cuh")
 
 
