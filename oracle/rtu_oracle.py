@@ -23,7 +23,7 @@ Passages followed (paper sections / equations):
     Baltz, Marshall & Oguri (2009)
   * arc-mask centre rays, standardisation ... App. C step i, Sec. 2.2 footnote
   * marginal eCDFs / quantile function ...... Sec. 2.2, App. C step ii
-  * weighted eCDFs (weighted RTU grid) ...... Sec. 5 (extension)
+  * weighted eCDFs (weighted RTU grid) ...... Sec. 6.3 (extension)
   * Chebyshev-node polynomial fit of the QF . App. C step iii (order 21)
   * cubic Hermite spline inverse (the CDF) .. App. C step iv
   * unsmoothed linear-interpolated eCDF ..... App. C (first paragraph)
@@ -262,7 +262,7 @@ def quantile_type7(sorted_vals, u):
 
 def quantile_weighted(sorted_vals, sorted_w, u):
     """Weighted empirical quantile: the type-7 quantile of the sample in which
-    value i appears w_i times (w positive integers; weighted RTU grid, Sec. 5):
+    value i appears w_i times (w positive integers; weighted RTU grid, Sec. 6.3):
     h = u (W - 1) with W = sum w, and the expanded element of rank r is the value
     whose cumulative weight first exceeds r."""
     cw = torch.cumsum(sorted_w.to(torch.int64), 0)
@@ -300,21 +300,38 @@ def standardise(bx, by):
     return mu, sigma
 
 
+SEL_BINS = 65536
+
+
+def selection_histogram(values, weights=None, nbins=SEL_BINS):
+    """The integer histogram behind the exact order statistics of one axis (App. C
+    step ii: the eCDF's counts): nbins equal bins over [min, max] of the traced centre
+    positions, value v in bin floor((v - min) * (nbins / (max - min))) clamped to
+    [0, nbins - 1] (every value in bin 0 when max = min); each ray adds its integer
+    weight (1 when unweighted).  Bit-exact for identical positions: one subtraction,
+    one division and one product, each correctly rounded in float64."""
+    v = values.detach().to(DT)
+    lo, hi = float(v.min()), float(v.max())
+    scale = nbins / (hi - lo) if hi > lo else 0.0
+    b = torch.floor((v - lo) * scale).clamp(0, nbins - 1).long()
+    w = torch.ones_like(b) if weights is None else weights.to(torch.int64)
+    h = torch.zeros(nbins, dtype=torch.int64)
+    return h.index_add_(0, b, w)
+
+
 def fit_qf_polynomial(zs, u, degree, ws=None):
     """App. C step iii: Chebyshev coefficients c of p(u) = sum_k c_k T_k(2u-1) fitted to
-    the empirical QF at the nodes u; each node weighted by the eCDF slope there
-    (centred rank difference of half-width 1/(2M)).  With M = degree+1 nodes the
-    weighted fit is the interpolant and the weights drop out.  ws: ray weights in
-    the order of zs (weighted RTU grid), else every ray counts once."""
+    the empirical QF at the nodes u.  The paper takes as many Chebyshev nodes as the
+    order of the fit; with M = degree+1 nodes the fit is the interpolant (the node
+    weights -- the eCDF slopes -- drop out of a square solve), which is the reading
+    taken here; other node counts are rejected.  ws: ray weights in the order of zs
+    (weighted RTU grid), else every ray counts once."""
     m = u.shape[0]
+    if m != degree + 1:
+        raise ValueError("the quantile fit takes M = degree + 1 Chebyshev nodes")
     V = chebyshev_T(2.0 * u - 1.0, degree)
     Q = quantile_type7(zs, u) if ws is None else quantile_weighted(zs, ws, u)
-    if m == degree + 1:
-        return torch.linalg.solve(V, Q), Q
-    d = 0.5 / m
-    lo, hi = (u - d).clamp(0.0, 1.0), (u + d).clamp(0.0, 1.0)
-    wgt = (hi - lo) / (quantile_type7(zs, hi) - quantile_type7(zs, lo)).clamp_min(1e-300)
-    return torch.linalg.lstsq(wgt[:, None] * V, wgt * Q).solution, Q
+    return torch.linalg.solve(V, Q), Q
 
 
 def hermite_knots(c, u, degree, guard_eps=1e-6):
@@ -346,7 +363,7 @@ def hermite_knots(c, u, degree, guard_eps=1e-6):
 def fit_transform(bx, by, n_nodes=22, degree=21, guard_eps=1e-6, weights=None):
     """App. C steps i-iv from the traced centre rays (bx, by): standardise, sort each
     marginal (the eCDF, weighted by the rays' integer weights when given -- the
-    weighted RTU grid of Sec. 5), fit the QF polynomial at the Chebyshev nodes, and
+    weighted RTU grid of Sec. 6.3), fit the QF polynomial at the Chebyshev nodes, and
     build the Hermite CDF (values u_j at knots p(u_j), slopes 1/p'(u_j), linear beyond
     the ends).  The standardisation (step i) is unweighted."""
     mu, sigma = standardise(bx, by)

@@ -514,7 +514,7 @@ def test_lens_light_gradient_matches_central_differences():
     assert abs(fd - an) < 1e-6 * max(1.0, abs(an))
 
 
-# ------------------------------------------------------- weighted RTU grid (Sec. 5)
+# ------------------------------------------------------- weighted RTU grid (Sec. 6.3)
 def test_weighted_quantile_is_type7_of_the_expanded_sample():
     rng = np.random.default_rng(8)
     for n in (1, 2, 7, 40):
@@ -658,3 +658,126 @@ def test_linear_grid_gradient_matches_central_differences():
         fd = (float(O.forward(s, *p)["logL"]) - float(O.forward(s, *q)["logL"])) / (2 * h)
         an = float((g[key] * v).sum())
         assert abs(fd - an) < 1e-5 * max(1.0, abs(an)), (key, fd, an)
+
+
+# ------------------------------------------------- monotonicity guard (App. C iv)
+def test_hermite_guard_repairs_a_non_monotone_fit():
+    # p(t) = T_3(t) = 4 t^3 - 3 t (t = 2u - 1) falls for |t| < 1/2.  With M = 4 nodes the
+    # knot points are t = -1, -cos((2j-1) pi/8) (j = 1..4), +1 and p there is
+    # -1, -cos(3 pi/8), -cos(9 pi/8), -cos(15 pi/8), -cos(21 pi/8), 1 (T_3(-cos a) =
+    # -cos 3a); dp/du = 2 (12 t^2 - 3).  span = p(1) - p(0) = 2, floor = 1e-6 span.
+    # Written out by hand: the two interior points with dp/du = 2 (12 t^2 - 3) < 0 get
+    # the floor slope, and the knots after the fall are lifted to prev + floor.
+    D = 3
+    u = O.chebyshev_nodes(4)
+    c = t([0.0, 0.0, 0.0, 1.0])
+    X, d, rep = O.hermite_knots(c, u, D)
+    c1, c3 = math.cos(math.pi / 8), math.cos(3 * math.pi / 8)   # cos(pi/8), cos(3pi/8)
+    fl = 2e-6
+    raw = [-1.0, -c3, c1, -c1, c3, 1.0]                          # -cos(9pi/8) = c1, ...
+    want = [raw[0], raw[1], raw[2], raw[2] + fl, raw[2] + 2 * fl, 1.0]
+    tk = [-1.0, -c1, -c3, c3, c1, 1.0]
+    dp = [2 * (12 * v * v - 3) for v in tk]
+    want_d = [1.0 / max(v, fl) for v in dp]
+    assert rep
+    assert np.allclose(X.numpy(), want, rtol=0, atol=1e-13)
+    assert np.allclose(d.numpy(), want_d, rtol=1e-12)
+    assert want_d[2] == want_d[3] == 1.0 / fl
+
+
+def test_hermite_guard_repairs_a_falling_fit():
+    # p(t) = -t: the span p(1) - p(0) = -2 is not positive -> repaired with |span|;
+    # every slope gets the floor 2e-6 and every knot after the first is lifted.
+    u = O.chebyshev_nodes(4)
+    X, d, rep = O.hermite_knots(t([0.0, -1.0, 0.0, 0.0]), u, 3)
+    assert rep
+    fl = 1e-6 * 2.0
+    assert np.allclose(X.numpy(), [1.0 + k * fl for k in range(6)], rtol=0, atol=1e-14)
+    assert np.allclose(d.numpy(), np.full(6, 1.0 / fl), rtol=1e-12)
+
+
+def test_quantile_fit_takes_degree_plus_one_nodes():
+    zs = torch.sort(t(np.random.default_rng(1).standard_normal(100)))[0]
+    with pytest.raises(ValueError):
+        O.fit_qf_polynomial(zs, O.chebyshev_nodes(30), 21)
+
+
+# ------------------------------------------- rays-per-cell histogram (Fig. 1, S11)
+def test_ray_hist_of_a_closed_form_box_grid():
+    # A lens of negligible deflection (theta_E = 1e-300) and the uniform box grid:
+    # 4 x 4 pixels of 1", 2 x 2 sub-rays at +-0.25" -> sub-ray coordinates
+    # -1.75 ... 1.75 in steps of 0.5 on each axis.  Mask rows j = 2, 3: the masked
+    # centres span x in [-1.5, 1.5], y in [0.5, 1.5]; box side 3, lower corner
+    # (-1.5, -0.5).  So y_x = (x + 1.5)/3 puts 2 sub-ray columns in each of the 3 cells
+    # per axis (6 inside), and y_y = (y + 0.5)/3 puts 2, 2, 1 sub-ray rows in cells
+    # 0, 1, 2 (5 inside).  Counts are x_count[i] y_count[j], row-major [j][i].
+    n = 4
+    mask = torch.zeros(n, n, dtype=torch.bool)
+    mask[2:, :] = True
+    s = O.System(data=torch.zeros(n, n, dtype=DT), mask=mask, psf=torch.ones(1, 1, dtype=DT), sigma=1.0,
+                 pix=1.0, s_super=2, n_src=4, src_pitch=1.0, transform=O.TRANSFORM_UNIFORM)
+    lens = t([1e-300, 2.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0])
+    h = O.ray_hist(s, lens)
+    assert h.tolist() == [4, 4, 4, 4, 4, 4, 2, 2, 2]
+
+
+def test_ray_hist_equals_a_per_ray_count():
+    # each supersampled ray counted by hand: its RTU position, then the cell (i, j)
+    # with i <= y_x (n-1) < i + 1 (the last cell closed at y = 1), rays outside the
+    # unit square skipped, cell index j (n-1) + i
+    m = I.config_tiny(seed=5, n_img=12, s=2, n_src=7)
+    s = oracle_io.system(m)
+    lens, _, _, _ = oracle_io.params(m)
+    T = O.build_grid(s, lens)
+    x, y = O.subray_positions(s.n_img, s.pix, s.s_super)
+    bx, by = O.trace(x.reshape(-1), y.reshape(-1), lens, s.profile)
+    yx, yy = O.rtu_map(bx, by, T)
+    n = s.n_src
+    counts = [0] * ((n - 1) * (n - 1))
+    inside = 0
+    for px, py in zip(yx.tolist(), yy.tolist()):
+        if not (0.0 <= px <= 1.0 and 0.0 <= py <= 1.0):
+            continue
+        inside += 1
+        gx, gy = px * (n - 1), py * (n - 1)
+        ci = next(i for i in range(n - 1) if i <= gx < i + 1 or (i == n - 2 and gx >= n - 2))
+        cj = next(j for j in range(n - 1) if j <= gy < j + 1 or (j == n - 2 and gy >= n - 2))
+        counts[cj * (n - 1) + ci] += 1
+    h = O.ray_hist(s, lens, T=T)
+    assert 0 < inside < len(yx)
+    assert h.tolist() == counts
+
+
+# ------------------------------- the order statistics' integer histograms (App. C ii)
+def test_selection_histogram_counts_by_explicit_bin_edges():
+    # 8 bins over [min, max]: each value counted in the bin whose edges
+    # min + b (max - min)/8 <= v < min + (b + 1)(max - min)/8 contain it (the maximum in
+    # the last bin); random values stay far from the edges at this size
+    rng = np.random.default_rng(11)
+    v = rng.uniform(-3.0, 5.0, 500)
+    lo, hi = v.min(), v.max()
+    want = [0] * 8
+    for x in v:
+        b = next((k for k in range(8) if lo + k * (hi - lo) / 8 <= x < lo + (k + 1) * (hi - lo) / 8), 7)
+        want[b] += 1
+    assert O.selection_histogram(t(v), nbins=8).tolist() == want
+
+
+def test_selection_histogram_is_a_counting_sort_of_the_sorted_values():
+    # the k-th smallest value lies in the bin whose cumulative count first exceeds k;
+    # weights count as repeated values; min in bin 0, max in the last bin
+    rng = np.random.default_rng(12)
+    v = np.concatenate([rng.normal(0.0, 1.0, 3000), [40.0, -25.0]])     # with far outliers
+    w = rng.integers(1, 5, v.size)
+    h = O.selection_histogram(t(v), torch.tensor(w)).numpy()
+    assert h.sum() == w.sum() and h[0] >= 1 and h[-1] >= 1
+    order = np.argsort(v, kind="stable")
+    cum = np.cumsum(h)
+    lo, hi = v.min(), v.max()
+    r = 0
+    for i in order:
+        b = int(np.floor((v[i] - lo) * (65536 / (hi - lo))))
+        b = min(max(b, 0), 65535)
+        assert (cum[b - 1] if b else 0) <= r < cum[b]
+        r += w[i]
+    assert O.selection_histogram(t(np.full(5, 2.5))).tolist()[0] == 5
