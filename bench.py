@@ -40,8 +40,11 @@ from paper_2606_30620_b300 import inputs as I  # noqa: E402
 N_MOCKS = 32
 SEED0 = 1000
 L2_BYTES = 126 * 1024 * 1024
-# recipe unit counts: 148 SMs x 128 FP32 lanes x 2 flop per FMA at the 2032 MHz maximum SM clock
-FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
+# FP32 peak from unit counts: SMs (read from the device) x 128 FP32 lanes x 2 flop per
+# FMA x the SM clock (the median sampled under load; the recipe's 2032 MHz maximum if
+# no sample was taken)
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ_RECIPE = 2032.0
 FALLBACK_HBM_GBS = 6400.0
 # algorithmic FP32 flops per supersampled ray: the EPL trace + map + interpolation of
 # one ray (about 190), its adjoint about 2.5x that
@@ -148,23 +151,37 @@ def make_mocks(rank, n=N_MOCKS):
     return [I.config_c2(SEED0 + rank * n + k) for k in range(n)]
 
 
-def cpu_oracle_sample(mocks, budget_s=20.0, max_n=None):
+def cpu_oracle_sample(mocks, budget_s=20.0, max_n=None, keep_first=False):
     """The oracle as it stands on the host cores: forward + gradient per mock until
-    the budget is spent (at least one mock)."""
+    the budget is spent (at least one mock).  keep_first: also return the first mock's
+    oracle result (log L, model, image, gradients), which the bench line's relative
+    errors are measured against."""
     from oracle import rtu_oracle as O
     from tests import oracle_io
     torch.set_num_threads(os.cpu_count() or 1)
     t0 = time.perf_counter()
     n = 0
+    first = None
     for m in mocks:
         s = oracle_io.system(m)
         lens, lat, ps, subs = oracle_io.params(m)
-        O.forward_adjoint(s, lens, lat, ps, subs)
+        r = O.forward_adjoint(s, lens, lat, ps, subs)
+        if first is None and keep_first:
+            first = {k: (v.detach().numpy() if torch.is_tensor(v) else v) for k, v in r.items()}
         n += 1
         if time.perf_counter() - t0 > budget_s or (max_n and n >= max_n):
             break
     dt = time.perf_counter() - t0
+    if keep_first:
+        return n / dt, n, dt, torch.get_num_threads(), first
     return n / dt, n, dt, torch.get_num_threads()
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, dtype=np.float64).ravel()
+    b = np.asarray(b, dtype=np.float64).ravel()
+    d = np.linalg.norm(b)
+    return float(np.linalg.norm(a - b) / (d if d > 0 else 1.0))
 
 
 def run_reference(args):
@@ -365,6 +382,17 @@ def run_ours(args):
     # kernels of this library per step (counted in the profiled pass) x timed steps
     launches = sum(v[0] for v in kern.values()) // n_prof * args.steps
 
+    # ---- mock 0 of the timed batch once more with its image outputs, for the relative
+    # errors against the FP64 oracle quoted on the line (the oracle runs in the CPU leg)
+    b0 = rtu.Binding(systems[0], mocks[0].lens, mocks[0].latents, mocks[0].ps, want_model=True, want_image=True)
+    rtu.Batch([b0]).forward(stream)
+    rtu.Batch([b0]).adjoint(stream)
+    torch.cuda.synchronize()
+    gpu0 = {"logL": float(b0.stats[rtu.STAT_LOGL]), "model": b0.model.cpu().numpy(),
+            "image": b0.image.cpu().numpy(), "g_latents": b0.g_latents.cpu().numpy(),
+            "g_lens": b0.g_lens.cpu().numpy(), "g_ps": b0.g_ps.cpu().numpy()}
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+
     clocks = clk.summary()
     variants = run_variants(args, dev, mocks, flush, stream) if not args.no_variants else None
     serving = run_serving(args, dev) if args.serve_n > 0 else None
@@ -378,12 +406,19 @@ def run_ours(args):
     rays = sum(m.n_rays for m in mocks)
     units = rays if dom == "k_render" else rays_in
     achieved = ROOF[dom]["flops_per_unit"] * units / (dom_ms / 1e3) / 1e12
+    clock_mhz = clocks["sm_mhz"] or clocks["sm_max_mhz"] or SM_MAX_MHZ_RECIPE
+    fp32_peak = sm_count * FP32_LANES_PER_SM * 2 * clock_mhz * 1e6 / 1e12
     # DRAM bytes from one ncu capture, per unit, scaled to this launch; null when the
     # kernel sources differ from the ones that were captured
     traffic = (ROOF[dom]["traffic_per_unit"] * units) if kernel_digest() == TRAFFIC_SRC_DIGEST else None
     # cpu baseline: the oracle on the host cores, a bounded sample of the same mocks
-    cpu_v, cpu_n, cpu_dt, cores = (cpu_oracle_sample(mocks, budget_s=args.cpu_budget) if not args.no_cpu
-                                   else (None, 0, 0.0, 0))
+    cpu_v, cpu_n, cpu_dt, cores, orc0 = (cpu_oracle_sample(mocks, budget_s=args.cpu_budget, keep_first=True)
+                                         if not args.no_cpu else (None, 0, 0.0, 0, None))
+    rel_err = None
+    if orc0 is not None:
+        rel_err = {"mock": mocks[0].name, "tolerance": 1e-5,
+                   "logL": abs(gpu0["logL"] - float(orc0["logL"])) / abs(float(orc0["logL"])),
+                   **{k: rel_l2(gpu0[k], orc0[k]) for k in ("image", "model", "g_latents", "g_lens", "g_ps")}}
     line = {
         "metric": "forward+adjoint evals/s", "value": value, "unit": "evals/s", "n_gpus": world,
         "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True,
@@ -401,14 +436,18 @@ def run_ours(args):
         "per_system_path": {"value": per_system_value, "unit": "evals/s",
                             "note": "same 32 evaluations issued as 32 single-system calls"},
         "roofline": {"kernel": dom + "<float>", "top_kernel": top[0], "bound": "alu", "achieved": achieved,
-                     "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+                     "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
                      "traffic": traffic, "launch_ms": dom_ms, "units": ROOF[dom]["units"],
                      "units_per_launch": units, "rays_per_launch": rays, "in_grid_rays_per_launch": rays_in,
                      "flops_per_unit": ROOF[dom]["flops_per_unit"],
-                     "peak_note": "FP32 FMA peak from unit counts (148 SMs x 128 lanes x 2 x 2032 MHz)",
+                     "peak_note": f"FP32 FMA peak from unit counts: {sm_count} SMs (device) x "
+                                  f"{FP32_LANES_PER_SM} lanes x 2 x {clock_mhz:.0f} MHz (median SM clock "
+                                  "sampled in the timed region)",
+                     "sm_count": sm_count, "sm_mhz": clock_mhz,
                      "hbm_peak_gbs": peaks.get("hbm_gbs"), "hbm_peak_kind": peak_kind},
         "cpu_baseline": {"value": cpu_v, "unit": "evals/s", "cores": cores, "kind": "oracle",
                          "sample": f"{cpu_n} of the {n} mocks ({cpu_dt:.1f} s): FP64 oracle forward + autograd gradient"},
+        "rel_err": rel_err,
         "clocks": {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
         "variants": variants,
         "serving": serving,
@@ -430,7 +469,7 @@ def run_variants(args, dev, mocks, flush, stream):
     from paper_2606_30620_b300 import rtu
     specs = [("uniform_grid", "box around the masked rays (Sec. 2.1)",
               lambda m: m, rtu.RTU_TRANSFORM_UNIFORM),
-             ("weighted_grid", "integer SNR weights, cap 100 (Sec. 5)",
+             ("weighted_grid", "integer SNR weights, cap 100 (Sec. 6.3)",
               lambda m: I.with_snr_weights(copy.copy(m)), rtu.RTU_TRANSFORM_RTU),
              ("lens_light", "5-component MGE lens light (App. A.3)",
               lambda m: I.with_light(copy.copy(m), n=5, seed=3, amp=0.3), rtu.RTU_TRANSFORM_RTU),

@@ -66,7 +66,8 @@ typedef int32_t rtu_status;
 
 /* device-side flag bits in stats[RTU_STAT_FLAGS] */
 #define RTU_W_NONMONOTONE   1   /* the CDF fit needed its monotonicity repair */
-#define RTU_W_SELECT        2   /* order-statistic selection ran out of space */
+#define RTU_W_SELECT        2   /* order-statistic selection unresolved (not raised: the
+                                   radix refinement resolves every rank within 8 levels) */
 #define RTU_W_TIMEOUT       4   /* a bounded wait on an async copy gave up */
 
 enum { RTU_F32 = 0, RTU_F64 = 1 };
@@ -119,7 +120,7 @@ typedef struct {
     const uint8_t* mask; /* device, u8 [n_img*n_img]; nonzero = in the arc mask (Sec. 2.2) */
     const void* psf;     /* device, real [psf_k*psf_k], centre at (psf_k-1)/2 */
     const uint32_t* weights; /* device, u32 [n_img*n_img] or NULL: ray weights of the arc-mask
-                                pixels for a weighted RTU grid (Sec. 5 extension): each centre
+                                pixels for a weighted RTU grid (Sec. 6.3 extension): each centre
                                 ray counts w times in the eCDFs (type-7 quantiles of the
                                 weight-expanded sample); w >= 1 on the mask, sum over the mask
                                 < 2^31.  NULL = every ray once.  Read once at create. */
@@ -154,6 +155,15 @@ typedef struct {
                                   rho^2 = q x'^2 + y'^2/q about (x_n, y_n) rotated by phi, at
                                   every sub-ray before the PSF.  Required when n_light > 0. */
     double* g_light;           /* adjoint out: [6 n_light]; required when n_light > 0 */
+    int32_t* sel_hist;         /* build out (nullable): [2][65536] the integer histograms behind
+                                  the order statistics (App. C ii), per axis the count (or, for a
+                                  weighted grid, the weight) of arc-mask centre rays in each of
+                                  65536 bins over [min, max] of that axis's traced positions:
+                                  bin = floor((beta - min) * (65536 / (max - min))), clamped to
+                                  [0, 65535] (all in bin 0 when max = min) */
+    double* centres;           /* build out (nullable): [2][n_mask] the traced arc-mask centre
+                                  positions beta_x then beta_y (App. C i), in row-major pixel order
+                                  of the mask */
 } rtu_eval;
 
 /* Bytes of device workspace one system needs (256-byte aligned base). 0 on bad desc. */
@@ -165,6 +175,24 @@ size_t rtu_workspace_size(const rtu_system_desc* desc);
  * (FFT twiddles, digit reversal, Chebyshev nodes) into the workspace. */
 rtu_status rtu_system_create(const rtu_system_desc* desc, void* workspace, size_t ws_bytes,
                              rtu_system** out);
+/* Host copies of a system's observation inputs (each nullable): the arc mask
+ * [n_img*n_img] u8, the PSF [psf_k*psf_k] real, the ray weights [n_img*n_img] u32 --
+ * the same contents as the desc's device buffers. */
+typedef struct {
+    const uint8_t* mask;
+    const void* psf;
+    const uint32_t* weights;
+} rtu_host_inputs;
+
+/* rtu_system_create for a caller that holds the inputs on the host as well (e.g. a
+ * server admitting systems while others run): the mask, PSF and weights are read from
+ * `host` where given instead of being copied back from the device (a device-to-host
+ * copy waits for the device), and the system's tables are uploaded with copies ordered
+ * on `stream` (nullable = the legacy stream), which return once the driver has staged
+ * the bytes.  The system may be used by calls ordered after `stream`'s copies; the
+ * desc's device buffers must hold their contents by the time those calls run. */
+rtu_status rtu_system_create_on(const rtu_system_desc* desc, const rtu_host_inputs* host, void* workspace,
+                                size_t ws_bytes, void* stream, rtu_system** out);
 rtu_status rtu_system_destroy(rtu_system* sys);
 
 /* S1-S5 (App. C steps i-iv, Sec. 2.2): trace the arc-mask pixel centres through
@@ -223,6 +251,10 @@ int32_t rtu_n_sites(const rtu_system_desc* desc);
  * tag = the system's random stream.  Resets Adam's moments and the step. */
 rtu_status rtu_elbo_init(rtu_system* sys, const rtu_prior* priors, const double* fixed,
                          const double* loc, const double* rho, uint32_t tag);
+/* The same with the state's upload ordered on `stream` (returns once the driver has
+ * staged the bytes); ELBO steps ordered after it see the new guide. */
+rtu_status rtu_elbo_init_on(rtu_system* sys, const rtu_prior* priors, const double* fixed,
+                            const double* loc, const double* rho, uint32_t tag, void* stream);
 
 /* One optimiser step for each of n systems: n_samples (1..8, <= desc.n_slots)
  * reparametrised guide samples, the batched rtu_forward + rtu_adjoint of every
@@ -238,6 +270,11 @@ rtu_status rtu_elbo_step(rtu_system* const* sys, int32_t n, int32_t n_samples, u
 /* Checkpoint / resume of the guide and optimiser state: bytes of the blob,
  * export into / import from caller host memory (synchronous). */
 size_t rtu_elbo_state_bytes(const rtu_system* sys);
+/* The Monte-Carlo ELBO gradient of the system's last rtu_elbo_step (Sec. 4), before
+ * the Adam update: d ELBO / d loc [n_sites + n_src^2] then d ELBO / d rho [same], as
+ * doubles into caller host memory of at least 2 (n_sites + n_src^2) doubles
+ * (synchronous; zeros before the first step). */
+rtu_status rtu_elbo_grad(const rtu_system* sys, double* host, size_t bytes);
 rtu_status rtu_elbo_export(const rtu_system* sys, void* host, size_t bytes);
 rtu_status rtu_elbo_import(rtu_system* sys, const void* host, size_t bytes);
 
@@ -269,23 +306,41 @@ rtu_status rtu_profile_report(char* buf, size_t bytes);
  * call fails. */
 rtu_status rtu_profile_timeline(char* buf, size_t bytes);
 
+/* Self-test of the double-float arithmetic (pairs of floats, about 48 significant
+ * bits) in which the FP32 path evaluates its FP64-class islands -- the centre
+ * rays that build the CDF, the near-edge and near-core rays, the GP source -- on
+ * the FP32 pipes (the paper fixes no precision; this checks the islands' own
+ * arithmetic).  Device buffers: x of n (op 0-2) or 2n (op 3-5) doubles, each
+ * converted to a double-float (hi = x rounded to float, lo = the rest rounded);
+ * y of n doubles receives hi + lo of the result: op 0 exp(x[i]), 1 log(x[i]),
+ * 2 sqrt(x[i]), 3 x[2i] / x[2i+1], 4 x[2i] x[2i+1], 5 x[2i] + x[2i+1].
+ * Stream-ordered; RTU_E_ARG on a bad op or null buffers. */
+rtu_status rtu_selftest_df(int32_t op, const double* x, double* y, int32_t n, void* stream);
+
 /* ---------------------------------------------------------------------------
  * Allocation-free variant of the GP source step (the paper has no counterpart).
  * For callers that cannot allocate device memory: an application that hands
  * this library no workspace because its device memory is planned up front, or
- * a process that must not call cudaMalloc after start-up.  It computes the
- * source s* of rtu_forward's S6 (Eq. 1-3, FP32) from device pointers:
- * latents [n_src*n_src] floats, ps [n_family + 1] doubles (alpha_src last) ->
- * source [n_src*n_src] floats; k = 2 pi |fftfreq| / src_pitch.
+ * a process that must not call cudaMalloc after start-up.  It computes the same
+ * source brightness as rtu_forward's GP source step: the latents (white noise)
+ * filtered by the square root of the power spectrum through a forward and an
+ * inverse FFT, then the softplus map and the alpha_src power; the transforms and
+ * the map run in double and the result is rounded to float, like the workspace
+ * path.  Device pointers: latents [n_src*n_src] floats, ps [n_family + 1]
+ * doubles (alpha_src last) -> source [n_src*n_src] floats;
+ * k = 2 pi |fftfreq| / src_pitch.  The caller owns all three buffers.
  * Its FFT scratch is one static device array of RTU_STATIC_MAX_NSRC^2 complex
- * floats (128 KiB) that every GPU loading the library holds until exit; n_src
+ * doubles (256 KiB) that every GPU loading the library holds until exit; n_src
  * above RTU_STATIC_MAX_NSRC (or not 2^a 3^b, or below 4) returns RTU_E_ARG.
- * The first call on a device (with that device current) looks up the array's
- * device address; make that first call before any stream capture.  The call
- * allocates nothing (no cudaMalloc, cudaFree or allocating library routine).
- * All calls share the array and it keeps the last call's contents (each call
- * overwrites all it reads), so calls that overlap on the GPU -- e.g. on two
- * streams at once -- race; serialise them. */
+ * The call looks up that array's device address (with the current device) at
+ * its first call on a device and again at every call not being captured into a
+ * CUDA graph; a call made while the stream is captured uses the address of the
+ * device's last uncaptured call, so make a first call before any capture (a
+ * captured first call returns RTU_E_ARG).  The call allocates nothing (no
+ * cudaMalloc, cudaFree or allocating library routine).  All calls share the
+ * array and it keeps the last call's contents (each call overwrites all it
+ * reads), so calls that overlap on the GPU -- e.g. on two streams at once --
+ * race; serialise them. */
 #define RTU_STATIC_MAX_NSRC 128
 rtu_status rtu_gp_source_static(int32_t n_src, double src_pitch, int32_t ps_family, const float* latents,
                                 const double* ps, float* source, void* stream);

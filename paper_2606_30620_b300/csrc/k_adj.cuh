@@ -120,7 +120,10 @@ __global__ void __launch_bounds__(CDF_NT) k_cdf_adj(const __grid_constant__ Batc
     if (threadIdx.x == 0) {
         for (int j = K - 1; j >= 1; --j)
             if (Xf[j] != Xr[j]) { gXr[j - 1] += gXr[j]; gfl += gXr[j]; gXr[j] = 0.0; }
-        if (span_ok) { gXr[K - 1] += 1e-6 * gfl; gXr[0] -= 1e-6 * gfl; }
+        // floor = 1e-6 |span| (+ 1e-300 when the span is not positive): d floor / d span
+        const double ds = span_ok ? 1e-6 : -1e-6;
+        gXr[K - 1] += ds * gfl;
+        gXr[0] -= ds * gfl;
     }
     __syncthreads();
     // knots X = V c and slopes p' = dV c  ->  gc = V^T gX + dV^T gp'
@@ -207,14 +210,19 @@ __global__ void __launch_bounds__(CTA_C) k_centre_adj(const __grid_constant__ Ba
     }
     T acc[8];
     for (int p = 0; p < 8; ++p) acc[p] = T(0);
+    // a near-core centre ray of the float path: its lens vector-Jacobian product in
+    // double, kept in double (near the core d alpha / d lens grows without bound, and
+    // one such term rounded to float can outweigh the rest of the sum)
+    double accd[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    bool nearc = false;
     if (k < N) {
         const T x = (T)xd, y = (T)yd;
         if (sizeof(T) == 4 && lens_near_core(L, x, y)) {
             EplJ<double> J;
-            double bx, by, o8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            double bx, by;
             lens_beta_eval(Ld, xd, yd, J, bx, by);
-            lens_beta_vjp(Ld, J, xd, yd, gb[0], gb[1], o8);
-            for (int p = 0; p < 8; ++p) acc[p] = (T)o8[p];
+            lens_beta_vjp(Ld, J, xd, yd, gb[0], gb[1], accd);
+            nearc = true;
         } else {
             EplJ<T> J;
             T bx, by;
@@ -228,10 +236,17 @@ __global__ void __launch_bounds__(CTA_C) k_centre_adj(const __grid_constant__ Ba
         const double v = warp_sum_lane0(acc[p]);
         if (lane == 0) red[wid][p] = v;
     }
+    // the double terms of the warps that hold a near-core ray (fixed shuffle tree)
+    __shared__ double redd[CTA_C / 32][8];
+    const bool anyd = __any_sync(0xffffffffu, nearc);
+    for (int p = 0; p < 8; ++p) {
+        const double v = anyd ? warp_sum(accd[p]) : 0.0;
+        if (lane == 0) redd[wid][p] = v;
+    }
     __syncthreads();
     if (threadIdx.x < 8) {
         double r = 0.0;
-        for (int w = 0; w < CTA_C / 32; ++w) r += red[w][threadIdx.x];
+        for (int w = 0; w < CTA_C / 32; ++w) r += red[w][threadIdx.x] + redd[w][threadIdx.x];
         out[threadIdx.x] = r;
     }
     for (int h = 0; h < nsub; ++h) {
@@ -403,6 +418,7 @@ __global__ void __launch_bounds__(GRAD_NT) k_grad_final(const __grid_constant__ 
     const int nl = 8 + 5 * nsub;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     constexpr int NW = GRAD_NT / 32;
+    if (threadIdx.x == 0) *E.gmax = 0ull;     // the next adjoint's PSF pass starts from zero
     for (int p = wid; p < nl; p += NW) {
         const int col = p < 8 ? p : NACC_FIX + 4 * K + (p - 8);
         const double s = apart_col(E, col);

@@ -88,6 +88,7 @@ struct ElboState {
     double* fixed;    // [n_phys] physical values of the non-site entries
     long long* t;     // step counter (device)
     double* part;     // per-CTA partial ELBO terms
+    double* grad;     // [2 n_state] the last step's ELBO gradient w.r.t. loc, then rho (before Adam)
     uint32_t tag;
     int n_sites, n_state, n_phys;
 };
@@ -192,6 +193,8 @@ __global__ void __launch_bounds__(ELBO_NT) k_elbo_update(const __grid_constant__
         }
         gl /= S;
         gr = gr / S + sgr / sc;                              // + d/drho of the guide entropy
+        A.st.grad[e] = gl;
+        A.st.grad[A.st.n_state + e] = gr;
         // Adam (ascent), t = step + 1
         const double b1 = 0.9, b2 = 0.999, ea = 1e-8;
         const double t1 = (double)step + 1.0;

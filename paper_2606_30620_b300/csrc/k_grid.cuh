@@ -210,8 +210,27 @@ __global__ void __launch_bounds__(CTA_C) k_centre_hist(const __grid_constant__ B
     }
 }
 
+// the optional build outputs of axis a: its level-1 histogram and traced centre positions
+__device__ __forceinline__ void export_selection(const EvalArgs& E, int a, const int* hist, const double* beta) {
+    if (E.sel_hist_out)
+        for (int i = threadIdx.x; i < HB; i += blockDim.x) E.sel_hist_out[(size_t)a * HB + i] = hist[i];
+    if (E.centres_out)
+        for (int k = threadIdx.x; k < E.n_mask; k += blockDim.x) E.centres_out[(size_t)a * E.n_mask + k] = beta[k];
+}
+
 constexpr int SEL_NT = 1024;
 constexpr int SEL_ROWS = HB / 32;      // the histogram as rows of 32 bins (one per lane)
+constexpr int SEL_SMALL = SEL_CAP / (2 * MAXM);   // candidates ranked directly per target bin (48)
+constexpr int SEL_DIG = 11;            // bits per radix-refinement level
+constexpr int SEL_HB = 1 << SEL_DIG;   // digit histogram bins (2 per thread)
+static_assert(SEL_HB == 2 * SEL_NT, "two digits per thread in the refinement scan");
+static_assert(2 * SEL_HB * 4 + SEL_SMALL * 8 <= SEL_CAP * 8, "refinement scratch fits the candidate arrays");
+
+// Order-preserving 64-bit image of a double (-0 taken as +0): a < b iff key(a) < key(b).
+__device__ __forceinline__ unsigned long long order_key(double v) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(v == 0.0 ? 0.0 : v);
+    return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
+}
 
 // One CTA per (evaluation, axis).  Dynamic shared memory:
 //   double ck[SEL_CAP]; int ci[SEL_CAP]; unsigned bitmap[HB/32]; uint32_t cw[SEL_CAP];
@@ -256,6 +275,7 @@ __global__ void __launch_bounds__(SEL_NT) k_select_fit(const __grid_constant__ B
     const int* hist = E.hist + a * HB;
     const double* beta = E.beta + a * N;
     const double lo = mom[2 + 2 * a];
+    export_selection(E, a, hist, beta);
     // row sums: warp w reads its 64 rows of 32 bins coalesced, 8 loads in flight
     constexpr int RPW = SEL_ROWS / (SEL_NT / 32);
     for (int i = 0; i < RPW; i += 8) {
@@ -362,7 +382,10 @@ __global__ void __launch_bounds__(SEL_NT) k_select_fit(const __grid_constant__ B
     for (int t = tid; t < nt; t += SEL_NT) selv[t] = lo;     // overwritten by the selection
     __syncthreads();
     const int nd = n_d;
-    // candidates of the target bins: count them per bin, offsets, then gather
+    // candidates of the target bins: count them per bin; a bin of at most SEL_SMALL
+    // candidates is gathered into shared memory and its targets ranked there, a larger
+    // one is resolved below by radix refinement (so the selection is exact whatever the
+    // distribution: one far outlier can squeeze most rays into a few level-1 bins)
     const int* cbin = E.cbin + (size_t)a * N;    // the bins k_centre_hist used
     for (int k = tid; k < N; k += SEL_NT) {
         const int bn = cbin[k];
@@ -375,21 +398,22 @@ __global__ void __launch_bounds__(SEL_NT) k_select_fit(const __grid_constant__ B
     __syncthreads();
     if (tid == 0) {
         int off = 0;
-        for (int d = 0; d < nd; ++d) { d_off[d] = off; off += d_num[d]; }
+        for (int d = 0; d < nd; ++d) {
+            d_off[d] = off;
+            if (d_num[d] <= SEL_SMALL) off += d_num[d];
+        }
         d_off[nd] = off;
-        if (off > SEL_CAP) flag_sh |= F_SELECT;
     }
     __syncthreads();
     for (int k = tid; k < N; k += SEL_NT) {
         const int bn = cbin[k];
         if (bitmap[bn >> 5] & (1u << (bn & 31))) {
-            const double b = beta[k];
             int d = 0;
             while (d < nd - 1 && d_bin[d] != bn) ++d;
-            const int pos = atomicAdd(&d_fill[d], 1);
-            const int at = d_off[d] + pos;
-            if (at < SEL_CAP && pos < d_off[d + 1] - d_off[d]) {
-                ck[at] = b;
+            if (d_num[d] > SEL_SMALL) continue;
+            const int at = d_off[d] + atomicAdd(&d_fill[d], 1);
+            if (at < d_off[d + 1]) {
+                ck[at] = beta[k];
                 ci[at] = k;
                 cwc[at] = E.cwt ? E.cwt[k] : 1u;
             }
@@ -397,10 +421,12 @@ __global__ void __launch_bounds__(SEL_NT) k_select_fit(const __grid_constant__ B
     }
     __syncthreads();
     // the element covering rank (r - below) of its bin: candidates ordered by
-    // (value, index), each covering as many ranks as its weight
+    // (value, index), each covering as many ranks as its weight (at most SEL_SMALL
+    // candidates: two per lane, each compared with all)
     for (int t = wid; t < nt; t += SEL_NT / 32) {
         const int d = t_slot[t];
-        const int o = d_off[d], cnt = min(d_off[d + 1], SEL_CAP) - o;
+        if (d_num[d] > SEL_SMALL) continue;
+        const int o = d_off[d], cnt = d_off[d + 1] - o;
         const int want = t_rank[t] - t_below[t];
         for (int c = lane; c < cnt; c += 32) {
             const double kc = ck[o + c];
@@ -417,7 +443,141 @@ __global__ void __launch_bounds__(SEL_NT) k_select_fit(const __grid_constant__ B
         }
     }
     __syncthreads();
-
+    // Targets in a bin of more than SEL_SMALL candidates, one at a time by the whole
+    // CTA: MSD radix selection on the key (order-preserving 64-bit image of the value,
+    // then the ray index among equal values), SEL_DIG bits per level starting at the
+    // highest bit in which the candidates' keys differ.  Each level reads the candidates
+    // once for their key range and once for a histogram of the next digit (counts and
+    // weights), keeps the digit holding the wanted rank, and stops when at most
+    // SEL_SMALL candidates remain, which are ranked like the small bins.  Scratch: the
+    // candidate arrays (the small bins are done).
+    {
+        int* hc = reinterpret_cast<int*>(ck);                 // [SEL_HB] counts
+        int* hw = hc + SEL_HB;                                // [SEL_HB] weights
+        double* fv = ck + SEL_HB;                             // [SEL_SMALL] final candidates
+        int* fi = ci;
+        uint32_t* fw = cwc;
+        __shared__ unsigned long long r_pfx, r_mn, r_mx, r_keq;
+        __shared__ int r_psh, r_stage, r_want, r_cnt, r_fn, r_done;
+        for (int t = 0; t < nt; ++t) {
+            const int d = t_slot[t];
+            if (d_num[d] <= SEL_SMALL) continue;
+            const int b = t_bin[t];
+            if (tid == 0) {
+                r_want = t_rank[t] - t_below[t];
+                r_cnt = d_num[d];
+                r_stage = 0;
+                r_psh = 64;
+                r_pfx = 0ull;
+                r_done = 0;
+            }
+            __syncthreads();
+            for (int lev = 0; lev < 16 && !r_done; ++lev) {
+                const bool gather = r_cnt <= SEL_SMALL;
+                const int stage = r_stage, psh = r_psh;
+                const unsigned long long pfx = r_pfx, keq = r_keq;
+                if (tid == 0) { r_mn = ~0ull; r_mx = 0ull; r_fn = 0; }
+                __syncthreads();
+                // pass 1: the key range of the candidates (and, when few remain, the candidates)
+                unsigned long long mn = ~0ull, mx = 0ull;
+                for (int k = tid; k < N; k += SEL_NT) {
+                    if (cbin[k] != b) continue;
+                    const unsigned long long key = order_key(beta[k]);
+                    const unsigned long long kk = stage == 0 ? key : (unsigned long long)k;
+                    if (stage == 1 && key != keq) continue;
+                    if (psh < 64 && (kk >> psh) != pfx) continue;
+                    mn = kk < mn ? kk : mn;
+                    mx = kk > mx ? kk : mx;
+                    if (gather) {
+                        const int at = atomicAdd(&r_fn, 1);
+                        if (at < SEL_SMALL) {
+                            fv[at] = beta[k];
+                            fi[at] = k;
+                            fw[at] = E.cwt ? E.cwt[k] : 1u;
+                        }
+                    }
+                }
+                for (int o = 16; o > 0; o >>= 1) {
+                    const unsigned long long m2 = __shfl_xor_sync(0xffffffffu, mn, o);
+                    const unsigned long long x2 = __shfl_xor_sync(0xffffffffu, mx, o);
+                    mn = m2 < mn ? m2 : mn;
+                    mx = x2 > mx ? x2 : mx;
+                }
+                if (lane == 0) { atomicMin(&r_mn, mn); atomicMax(&r_mx, mx); }
+                __syncthreads();
+                if (gather) {
+                    if (wid == 0) {
+                        const int cnt = min(r_fn, SEL_SMALL), want = r_want;
+                        for (int c = lane; c < cnt; c += 32) {
+                            const double kc = fv[c];
+                            const int ic = fi[c];
+                            int rank = 0;
+                            for (int c2 = 0; c2 < cnt; ++c2)
+                                if ((fv[c2] < kc) || (fv[c2] == kc && fi[c2] < ic)) rank += (int)fw[c2];
+                            if (rank <= want && want < rank + (int)fw[c]) {
+                                E.sel_idx[a * 2 * MAXM + t] = ic;
+                                selv[t] = kc;
+                            }
+                        }
+                        if (lane == 0) r_done = 1;
+                    }
+                    __syncthreads();
+                    break;
+                }
+                const unsigned long long lo_k = r_mn, hi_k = r_mx;
+                if (lo_k == hi_k) {
+                    // equal values: the rank runs over the ray index among them
+                    if (tid == 0) { r_stage = 1; r_keq = lo_k; r_psh = 64; r_pfx = 0ull; }
+                    __syncthreads();
+                    continue;
+                }
+                const int hb = 63 - __clzll((long long)(lo_k ^ hi_k));
+                const int sh = hb - (SEL_DIG - 1) > 0 ? hb - (SEL_DIG - 1) : 0;
+                for (int i = tid; i < 2 * SEL_HB; i += SEL_NT) hc[i] = 0;
+                __syncthreads();
+                // pass 2: histogram of the digit below the common prefix
+                for (int k = tid; k < N; k += SEL_NT) {
+                    if (cbin[k] != b) continue;
+                    const unsigned long long key = order_key(beta[k]);
+                    const unsigned long long kk = stage == 0 ? key : (unsigned long long)k;
+                    if (stage == 1 && key != keq) continue;
+                    if (psh < 64 && (kk >> psh) != pfx) continue;
+                    const int dg = (int)((kk >> sh) & (SEL_HB - 1));
+                    atomicAdd(&hc[dg], 1);
+                    atomicAdd(&hw[dg], E.cwt ? (int)E.cwt[k] : 1);
+                }
+                __syncthreads();
+                // the digit holding the wanted rank: exclusive scan of the weights, two
+                // digits per thread
+                {
+                    const int w0 = hw[2 * tid], w1 = hw[2 * tid + 1];
+                    int inc = w0 + w1;
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int y = __shfl_up_sync(0xffffffffu, inc, o);
+                        if (lane >= o) inc += y;
+                    }
+                    if (lane == 31) wtot[wid] = inc;
+                    __syncthreads();
+                    int base = 0;
+                    for (int i = 0; i < wid; ++i) base += wtot[i];
+                    const int e0 = base + inc - w0 - w1, e1 = e0 + w0, want = r_want;
+                    int hit = -1, below = 0;
+                    if (w0 > 0 && e0 <= want && want < e1) { hit = 2 * tid; below = e0; }
+                    if (w1 > 0 && e1 <= want && want < e1 + w1) { hit = 2 * tid + 1; below = e1; }
+                    __syncthreads();
+                    if (hit >= 0) {
+                        r_want = want - below;
+                        r_cnt = hc[hit];
+                        r_pfx = ((lo_k >> sh) & ~(unsigned long long)(SEL_HB - 1)) | (unsigned long long)hit;
+                        r_psh = sh;
+                    }
+                }
+                __syncthreads();
+            }
+            if (tid == 0 && !r_done) flag_sh |= F_SELECT;      // not reached: at most 8 levels
+            __syncthreads();
+        }
+    }
     // the Chebyshev tables of the fit in shared memory (the candidates are done with)
     const double* cb = E.cheb;
     if (cheb_size(M, D) <= SEL_CAP) {
@@ -580,6 +740,8 @@ __global__ void __launch_bounds__(LIN_NT) k_lin_sort(const __grid_constant__ Bat
     }
     __syncthreads();
     int* h = E.hist + a * HB;
+    export_selection(E, a, h, E.beta + (size_t)a * N);
+    __syncthreads();
     // exclusive scan of the HB bin counts, in place: warp w owns the contiguous segment
     // [w SEG, (w+1) SEG) and walks it in 32-bin chunks (coalesced); segment totals,
     // then their exclusive scan, then each warp rescans its segment with its offset

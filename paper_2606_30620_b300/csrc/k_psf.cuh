@@ -274,11 +274,17 @@ __global__ void __launch_bounds__(PSFT_NT) k_psf_adj_t(const __grid_constant__ B
     for (int b = 0; b < KT; ++b) psf_row_t<KT, false>(&in[ty + b][tx0], kw + b * PsfT<KT>::KP, acc);
     const float sc = E.dlogL ? (float)(*E.dlogL) : 1.0f;
     const int j = j0 + ty;
+    float gm = 0.0f;
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
         const int i = i0 + tx0 + u;
-        if (i < n && j < n) reinterpret_cast<float*>(E.gimg)[j * n + i] = acc[u] * sc;
+        if (i < n && j < n) {
+            const float g = acc[u] * sc;
+            reinterpret_cast<float*>(E.gimg)[j * n + i] = g;
+            gm = fmaxf(gm, fabsf(g));
+        }
     }
+    note_gmax(E, gm);
 }
 
 // ---- rank-1 PSF, psf[b][a] = u[b] v[a]: two one-dimensional passes over a 32 x 32
@@ -419,11 +425,17 @@ __global__ void __launch_bounds__(PSFS_NT) k_psf_adj_sep(const __grid_constant__
     psf_sep_passes<T, false>(E, reinterpret_cast<const T*>(E.resid), i0, j0, in, h, u, v, g4, x, y0);
     const T sc = E.dlogL ? (T)(*E.dlogL) : T(1);
     const int i = i0 + x;
+    T gm = T(0);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const int j = j0 + y0 + k;
-        if (i < n && j < n) reinterpret_cast<T*>(E.gimg)[j * n + i] = g4[k] * sc;
+        if (i < n && j < n) {
+            const T g = g4[k] * sc;
+            reinterpret_cast<T*>(E.gimg)[j * n + i] = g;
+            gm = fmax(gm, r_abs(g));
+        }
     }
+    note_gmax(E, gm);
 }
 
 // log L = -1/2 sum r^2 - N log(sigma sqrt(2 pi)); chi^2_img = sum_mask r^2 / N_mask
@@ -465,11 +477,17 @@ __global__ void __launch_bounds__(PSF_NT) k_psf_adj(const __grid_constant__ Batc
     }
     const T sc = E.dlogL ? (T)(*E.dlogL) : T(1);
     const int j = j0 + ty;
+    T gm = T(0);
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
         const int i = i0 + tx0 + u;
-        if (i < n && j < n) reinterpret_cast<T*>(E.gimg)[j * n + i] = acc[u] * sc;
+        if (i < n && j < n) {
+            const T g = acc[u] * sc;
+            reinterpret_cast<T*>(E.gimg)[j * n + i] = g;
+            gm = fmax(gm, r_abs(g));
+        }
     }
+    note_gmax(E, gm);
 }
 
 }  // namespace rtu

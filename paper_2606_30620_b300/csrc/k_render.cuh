@@ -327,6 +327,17 @@ struct RenderShared {
     UDiv dv_s2, dv_n, dv_s, dv_nc;   // dividers by s^2, n_img, s, n_src - 1
 };
 
+// Source grids up to GRID_STAGE_MAX bytes are staged in shared memory; larger ones
+// (float n_src = 256, double n_src >= 144) are read through L1/L2 from global memory.
+constexpr uint32_t GRID_STAGE_MAX = 160u * 1024u;
+__host__ __device__ inline bool grid_staged(int n_src, int bytes_per_value) {
+    return (uint32_t)n_src * (uint32_t)n_src * (uint32_t)bytes_per_value <= GRID_STAGE_MAX;
+}
+// bytes of dynamic shared memory the staged grid takes (0 when read from global)
+__host__ __device__ inline size_t grid_smem_bytes(int n_src, int bytes_per_value) {
+    return grid_staged(n_src, bytes_per_value) ? ((size_t)n_src * n_src * bytes_per_value + 127) & ~(size_t)127 : 0;
+}
+
 template <typename T>
 __device__ __forceinline__ void render_setup(const EvalArgs& E, RenderShared<T>& sh) {
     load_lensk(sh.K, lensk_src<T>(E.lensk));
@@ -399,10 +410,13 @@ __global__ void __launch_bounds__(CTA_R, sizeof(T) == 4 && !LIN ? 8 : 6) k_rende
         if (E.image_out) reinterpret_cast<T*>(E.image_out)[pixel] = T(0);
         return;
     }
-    // the source grid's copy runs beside the set-up
-    stage_begin(sgrid, E.src, (uint32_t)(n * n * sizeof(T)), &mbar);
+    // the source grid's copy runs beside the set-up (or the grid is read from global)
+    const bool gstaged = grid_staged(n, sizeof(T));
+    const T* grid = gstaged ? sgrid : reinterpret_cast<const T*>(E.src);
+    if (gstaged) stage_begin(sgrid, E.src, (uint32_t)(n * n * sizeof(T)), &mbar);
     render_setup<T>(E, sh);
-    if (!stage_end(sgrid, E.src, (uint32_t)(n * n * sizeof(T)), &mbar, E.flags)) {
+    if (!gstaged) __syncthreads();
+    if (gstaged && !stage_end(sgrid, E.src, (uint32_t)(n * n * sizeof(T)), &mbar, E.flags)) {
         // the copy timed out (flagged): this tile stages nothing
         if (threadIdx.x < CTA_R / 32) E.useg[tile * (CTA_R / 32) + threadIdx.x] = 0;
         if (threadIdx.x < CTA_R / 32) E.nseg[tile * (CTA_R / 32) + threadIdx.x] = 0;
@@ -506,7 +520,7 @@ __global__ void __launch_bounds__(CTA_R, sizeof(T) == 4 && !LIN ? 8 : 6) k_rende
         int i0, j0;
         const int cell = cell_of<T>(yx, yy, n, fx, fy, i0, j0);
         if (cell < 0) return -1;
-        acc += bilinear_at<T, T>(sgrid, n, i0, j0, fx, fy);
+        acc += bilinear_at<T, T>(grid, n, i0, j0, fx, fy);
         atomicAdd(E.ccount + cell, 1);
         ++nin;
         return cell + 1;
@@ -515,9 +529,7 @@ __global__ void __launch_bounds__(CTA_R, sizeof(T) == 4 && !LIN ? 8 : 6) k_rende
     // for n_src <= 256, 0xffff for no cell), then the warp's staged rays in ray
     // order (lane-major, i.e. pixel by pixel): consecutive adjoint rays then come
     // from the same or neighbouring pixels (layout [q][thread]: conflict-free banks)
-    unsigned short* codes =
-        reinterpret_cast<unsigned short*>(smem_raw + (((size_t)n * n * sizeof(T) + 127) & ~(size_t)127)) +
-        threadIdx.x;
+    unsigned short* codes = reinterpret_cast<unsigned short*>(smem_raw + grid_smem_bytes(n, sizeof(T))) + threadIdx.x;
     int mine = 0;
     for (int q = 0; q < s2; ++q) {
         const int code = valid ? trace(q) : -1;
@@ -799,7 +811,9 @@ __global__ void __launch_bounds__(CTA_R, NEAR ? 1 : (sizeof(T) == 4 && !LIN ? 6 
     const int n = E.n_src, K = E.n_nodes + 2, nc = n - 1;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     T* sgrid = reinterpret_cast<T*>(smem_raw);
-    const size_t gbytes = ((size_t)n * n * sizeof(T) + 127) & ~(size_t)127;
+    const bool gstaged = grid_staged(n, sizeof(T));
+    const T* grid = gstaged ? sgrid : reinterpret_cast<const T*>(E.src);
+    const size_t gbytes = grid_smem_bytes(n, sizeof(T));
     // per-warp spline-knot tables [NW][2 axes][2][K]: (hi, lo) pairs of T
     typedef typename real2_of<T>::type TP;
     TP* tab = reinterpret_cast<TP*>(smem_raw + gbytes);
@@ -822,8 +836,8 @@ __global__ void __launch_bounds__(CTA_R, NEAR ? 1 : (sizeof(T) == 4 && !LIN ? 6 
             return;
         }
     }
-    // the source grid's copy runs beside the set-up
-    stage_begin(sgrid, E.src, (uint32_t)(n * n * sizeof(T)), &mbar);
+    // the source grid's copy runs beside the set-up (or the grid is read from global)
+    if (gstaged) stage_begin(sgrid, E.src, (uint32_t)(n * n * sizeof(T)), &mbar);
     render_setup<T>(E, sh);
     // the lens in double for the float path's FP64 islands (the near-core pass; the
     // unsmoothed map's positions), loaded by the instantiations that use it
@@ -834,7 +848,9 @@ __global__ void __launch_bounds__(CTA_R, NEAR ? 1 : (sizeof(T) == 4 && !LIN ? 6 
         Kdp = &kd_s;
     }
     for (int i = threadIdx.x; i < NW * 4 * K; i += blockDim.x) { tab[i].x = T(0); tab[i].y = T(0); }
-    const bool staged = stage_end(sgrid, E.src, (uint32_t)(n * n * sizeof(T)), &mbar, E.flags);
+    bool staged = true;
+    if (gstaged) staged = stage_end(sgrid, E.src, (uint32_t)(n * n * sizeof(T)), &mbar, E.flags);
+    else __syncthreads();
     // column-major partials: column i of this CTA's row at apart[i * n_row_adj + row];
     // the near-core pass also owns the subhalo columns of its rows (zero: k_sub_adj
     // takes every ray in its own rows)
@@ -1041,7 +1057,7 @@ __global__ void __launch_bounds__(CTA_R, NEAR ? 1 : (sizeof(T) == 4 && !LIN ? 6 
                 }
                 const int j0 = (int)udiv((uint32_t)cell, sh.dv_nc), i0 = cell - j0 * nc;
                 const T fx = yv[0] * nm1 - T(i0), fy = yv[1] * nm1 - T(j0);
-                const T* r0 = sgrid + j0 * n + i0;
+                const T* r0 = grid + j0 * n + i0;
                 const T dsdx = nm1 * ((T(1) - fy) * (r0[1] - r0[0]) + fy * (r0[n + 1] - r0[n]));
                 const T dsdy = nm1 * ((T(1) - fx) * (r0[n] - r0[0]) + fx * (r0[n + 1] - r0[1]));
                 const T gy[2] = {gpix * dsdx, gpix * dsdy};
@@ -1179,10 +1195,50 @@ __global__ void __launch_bounds__(CTA_R) k_sub_adj(const __grid_constant__ Batch
     }
 }
 
-// per-cell bilinear corner sums over the counting-sorted records: one half-warp
-// per cell (two cells' loads in flight per warp), fixed lane-stride order and a
-// fixed tree, in compensated pairs (float) or double
+// Per-cell bilinear corner sums over the counting-sorted records: one half-warp per
+// cell (two cells' loads in flight per warp).  The records of a cell arrive in an
+// order that depends on atomic timing, so the sums are formed order-independently:
+// every term is rounded to an integer multiple of a quantum fixed per evaluation
+// (from the largest |g| of its records, bounded by the largest |d L / d image|, a
+// maximum the PSF adjoint takes with integer atomics) and the integers are added
+// exactly in 64 bits.  Float path: the
+// quantum is 2^-22 of that largest |g| -- the product's own rounding is 2^-24 of the
+// term -- and a term is rounded by one fused multiply-add into the integer-valued range
+// of a float (1.5 2^23 + v, |v| < 2^22); double path: 2^-(62 - bits(ray count)) of it,
+// by a conversion to 64-bit integer.  The result is the same bits from run to run and
+// alone or in a batch.
 constexpr int GATHER_NT = 256;
+__device__ __forceinline__ float pow2_of(int S, float) { return __int_as_float((min(max(S, -126), 127) + 127) << 23); }
+__device__ __forceinline__ double pow2_of(int S, double) {
+    return __longlong_as_double((long long)(min(max(S, -1022), 1023) + 1023) << 52);
+}
+// the evaluation's quantum exponent S (terms times 2^S are integers after rounding),
+// from the largest |d L / d image| that the PSF adjoint noted, times 1/s^2 as the
+// render adjoint forms its records' g (the same rounded product: no record exceeds it)
+__device__ __forceinline__ int gather_scale(const EvalArgs& E, float) {
+    const float gm = __uint_as_float(*reinterpret_cast<const unsigned int*>(E.gmax)) * (1.0f / (float)(E.s * E.s));
+    const int e = max(((__float_as_int(gm) >> 23) & 0xff) - 126, -100);   // every |g| < 2^e
+    return 22 - e;
+}
+__device__ __forceinline__ int gather_scale(const EvalArgs& E, double) {
+    const double gm = __longlong_as_double((long long)*E.gmax) * (1.0 / (double)(E.s * E.s));
+    const int e = max((int)((__double_as_longlong(gm) >> 52) & 0x7ff) - 1022, -1000);
+    const int n_rays = E.n_img * E.n_img * E.s * E.s;
+    return 62 - e - (32 - __clz(n_rays));
+}
+// w g 2^S rounded to the nearest integer (g already scaled by 2^S)
+__device__ __forceinline__ long long fix_term(float w, float gs) {
+    return (long long)(__float_as_int(__fmaf_rn(w, gs, 12582912.0f)) - 0x4B400000);
+}
+__device__ __forceinline__ long long fix_term(double w, double gs) { return __double2ll_rn(w * gs); }
+__device__ __forceinline__ float2 fix_to_pair(long long k, int S, float) {
+    const double d = (double)k * pow2_of(-S, 0.0);
+    const float hi = (float)d;
+    return make_float2(hi, (float)(d - (double)hi));
+}
+__device__ __forceinline__ double2 fix_to_pair(long long k, int S, double) {
+    return make_double2((double)k * pow2_of(-S, 0.0), 0.0);
+}
 template <typename T>
 __global__ void __launch_bounds__(GATHER_NT) k_cell_gather(const __grid_constant__ Batch B) {
     typedef typename real4_of<T>::type R4;
@@ -1195,44 +1251,34 @@ __global__ void __launch_bounds__(GATHER_NT) k_cell_gather(const __grid_constant
     const bool valid = cell < ncell;
     const int* off = E.ccount + ncell;
     const R4* rec = reinterpret_cast<const R4*>(E.rec);
-    // lane sums in the record type (a few records each), the tree in pairs
-    T l0 = T(0), l1 = T(0), l2 = T(0), l3 = T(0);
     const int n_rays = E.n_img * E.n_img * E.s * E.s;
     const int lo = valid ? max(0, off[cell]) : 0, hi = valid ? min(off[cell + 1], n_rays) : 0;
+    const int S = gather_scale(E, T(0));
+    const T sc = pow2_of(S, T(0));
+    long long l0 = 0, l1 = 0, l2 = 0, l3 = 0;
     for (int i = lo + hl; i < hi; i += 16) {
         const R4 r = rec[i];
-        const T fx = r.x, fy = r.y, g = r.z;
-        const T gy0 = (T(1) - fy) * g, gy1 = fy * g;
-        l0 += (T(1) - fx) * gy0;
-        l1 += fx * gy0;
-        l2 += (T(1) - fx) * gy1;
-        l3 += fx * gy1;
+        const T fx = r.x, fy = r.y, gs = r.z * sc;      // exact: a power of two
+        const T w0 = (T(1) - fx) * (T(1) - fy), w1 = fx * (T(1) - fy);
+        const T w2 = (T(1) - fx) * fy, w3 = fx * fy;
+        l0 += fix_term(w0, gs);
+        l1 += fix_term(w1, gs);
+        l2 += fix_term(w2, gs);
+        l3 += fix_term(w3, gs);
     }
-    // The four sums of the half-warp by a transposing butterfly: at xor 8 the lower
-    // eight lanes keep corners 0, 1 and the upper eight 2, 3, at xor 4 each quarter
-    // keeps one corner, then two levels on that one pair -- 8 shuffles of pairs.
-    // Lanes 0, 4, 8, 12 of the half store corners 0..3; the order of operations is
-    // fixed, so the sums are the same from run to run.
-    typedef typename real2_of<T>::type TP;
-    auto pr = [](T v) { TP p; p.x = v; p.y = T(0); return p; };
-    auto xs = [](TP p, int o) {
-        TP q;
-        q.x = __shfl_xor_sync(0xffffffffu, p.x, o);
-        q.y = __shfl_xor_sync(0xffffffffu, p.y, o);
-        return q;
-    };
+    // the half-warp's four sums by a transposing butterfly: at xor 8 the lower eight
+    // lanes keep corners 0, 1 and the upper eight 2, 3, at xor 4 each quarter keeps one
+    // corner, then two levels on it; lanes 0, 4, 8, 12 of the half hold corners 0..3
     const bool up = hl & 8;
-    TP k0 = pr(up ? l2 : l0), k1 = pr(up ? l3 : l1);
-    {
-        const TP s0 = xs(pr(up ? l0 : l2), 8), s1 = xs(pr(up ? l1 : l3), 8);
-        pair_add(k0, s0);
-        pair_add(k1, s1);
-    }
+    long long k0 = up ? l2 : l0, k1 = up ? l3 : l1;
+    k0 += __shfl_xor_sync(0xffffffffu, up ? l0 : l2, 8);
+    k1 += __shfl_xor_sync(0xffffffffu, up ? l1 : l3, 8);
     const bool hi4 = hl & 4;
-    TP k = hi4 ? k1 : k0;
-    pair_add(k, xs(hi4 ? k0 : k1, 4));
-    for (int o = 2; o > 0; o >>= 1) pair_add(k, xs(k, o));
-    if (valid && (hl & 3) == 0) reinterpret_cast<TP*>(E.corner)[(size_t)cell * 4 + (hl >> 2)] = k;
+    long long k = hi4 ? k1 : k0;
+    k += __shfl_xor_sync(0xffffffffu, hi4 ? k0 : k1, 4);
+    for (int o = 2; o > 0; o >>= 1) k += __shfl_xor_sync(0xffffffffu, k, o);
+    typedef typename real2_of<T>::type TP;
+    if (valid && (hl & 3) == 0) reinterpret_cast<TP*>(E.corner)[(size_t)cell * 4 + (hl >> 2)] = fix_to_pair(k, S, T(0));
 }
 
 }  // namespace rtu

@@ -139,6 +139,7 @@ size_t slot_layout(const rtu_system_desc& d, char* base, EvalArgs* e) {
     p = take((size_t)z.ncell * 4 * 2 * z.tb);         if (e) e->corner = p;
     p = take((size_t)std::max(z.n_cta_r, z.n_cta_adj + NEAR_CTAS) * z.nacc * 8); if (e) e->apart = (double*)p;
     p = take(16);                                     if (e) e->flags = (int*)p;
+    p = take(8);                                      if (e) e->gmax = (unsigned long long*)p;
     p = take(LENSK_BYTES);                            if (e) e->lensk = p;
     p = take(16);                                     if (e) e->ecount = (int*)p;
     p = take(ni * 8);                                 if (e) e->pdef = (unsigned long long*)p;
@@ -197,6 +198,7 @@ size_t state_layout(const rtu_system_desc& d, char* base, ElboState* st) {
     p = take((size_t)z.n_fixed * 8);      if (st) st->fixed = (double*)p;
     p = take(8);                          if (st) st->t = (long long*)p;
     p = take((size_t)z.n_cta_upd * 8);    if (st) st->part = (double*)p;
+    p = take((size_t)2 * z.n_state * 8);  if (st) st->grad = (double*)p;
     if (st) { st->n_sites = z.n_sites; st->n_state = z.n_state; st->n_phys = z.n_phys; st->tag = 0; }
     return o;
 }
@@ -350,7 +352,10 @@ __global__ void __launch_bounds__(256) k_zero(const __grid_constant__ Batch B, i
         if (i < nh) E.hist[i] = 0; else E.ccount[i - nh] = 0;
     }
     if (tile == 0) {
-        if (threadIdx.x == 0) { *E.flags = 0; *E.ecount = 0; E.ccnt[0] = 0; E.ccnt[1] = 0; E.ccnt[2] = 0; E.ccnt[3] = 0; }
+        if (threadIdx.x == 0) {
+            *E.flags = 0; *E.ecount = 0; E.ccnt[0] = 0; E.ccnt[1] = 0; E.ccnt[2] = 0; E.ccnt[3] = 0;
+            *E.gmax = 0ull;
+        }
         const int nsub = E.sub_kind ? E.n_sub : 0;
         lens_setup_par(reinterpret_cast<LensK<double>*>(E.lensk),
                        reinterpret_cast<LensK<float>*>(static_cast<char*>(E.lensk) + LENSK_D_BYTES), E.lens,
@@ -373,6 +378,20 @@ size_t rtu_workspace_size(const rtu_system_desc* d) {
 }
 
 rtu_status rtu_system_create(const rtu_system_desc* d, void* ws, size_t ws_bytes, rtu_system** out) {
+    // synchronous: the uploads have landed when the call returns
+    const rtu_status r = rtu_system_create_on(d, nullptr, ws, ws_bytes, nullptr, out);
+    if (r != RTU_OK) return r;
+    const cudaError_t ce = cudaStreamSynchronize(nullptr);
+    if (ce != cudaSuccess) {
+        rtu_system_destroy(*out);
+        *out = nullptr;
+        return fail(RTU_E_CUDA, std::string("rtu_system_create: ") + cudaGetErrorString(ce));
+    }
+    return RTU_OK;
+}
+
+rtu_status rtu_system_create_on(const rtu_system_desc* d, const rtu_host_inputs* hin, void* ws, size_t ws_bytes,
+                                void* stream, rtu_system** out) {
     if (!out) return fail(RTU_E_ARG, "out is null");
     *out = nullptr;
     if (const char* m = check_desc(d)) return fail(RTU_E_ARG, m);
@@ -393,8 +412,13 @@ rtu_status rtu_system_create(const rtu_system_desc* d, void* ws, size_t ws_bytes
     const size_t st = static_layout(*d, base, &s->cidx, &s->tw, &s->rev, &s->cheb, &cwt_buf, &uv_buf);
     // arc-mask pixel list (the CDF uses observed-pixel centres inside the mask)
     const size_t npx = (size_t)d->n_img * d->n_img;
+    // host copies of the mask, the PSF and the weights when the caller has them (no
+    // device-to-host copy, which would wait for the device), else read back from the device
+    const cudaStream_t cs = static_cast<cudaStream_t>(stream);
     std::vector<uint8_t> mask(npx);
-    cudaError_t ce = cudaMemcpy(mask.data(), d->mask, npx, cudaMemcpyDeviceToHost);
+    cudaError_t ce = cudaSuccess;
+    if (hin && hin->mask) memcpy(mask.data(), hin->mask, npx);
+    else ce = cudaMemcpy(mask.data(), d->mask, npx, cudaMemcpyDeviceToHost);
     if (ce != cudaSuccess) { delete s; return fail(RTU_E_CUDA, std::string("mask copy: ") + cudaGetErrorString(ce)); }
     std::vector<int> idx;
     for (size_t i = 0; i < npx; ++i) if (mask[i]) idx.push_back((int)i);
@@ -406,7 +430,8 @@ rtu_status rtu_system_create(const rtu_system_desc* d, void* ws, size_t ws_bytes
     s->wtot = s->n_mask;
     if (d->weights) {
         std::vector<uint32_t> w(npx), cw(idx.size());
-        if ((ce = cudaMemcpy(w.data(), d->weights, npx * 4, cudaMemcpyDeviceToHost)) != cudaSuccess) {
+        if (hin && hin->weights) memcpy(w.data(), hin->weights, npx * 4);
+        else if ((ce = cudaMemcpy(w.data(), d->weights, npx * 4, cudaMemcpyDeviceToHost)) != cudaSuccess) {
             delete s;
             return fail(RTU_E_CUDA, std::string("weights copy: ") + cudaGetErrorString(ce));
         }
@@ -417,7 +442,7 @@ rtu_status rtu_system_create(const rtu_system_desc* d, void* ws, size_t ws_bytes
             if (cw[k] == 0) { delete s; return fail(RTU_E_ARG, "weights must be >= 1 on the arc mask"); }
         }
         if (tot >= (1ull << 31)) { delete s; return fail(RTU_E_ARG, "the mask's total weight must be < 2^31"); }
-        if ((ce = cudaMemcpy(cwt_buf, cw.data(), cw.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess) {
+        if ((ce = cudaMemcpyAsync(cwt_buf, cw.data(), cw.size() * 4, cudaMemcpyHostToDevice, cs)) != cudaSuccess) {
             delete s;
             return fail(RTU_E_CUDA, std::string("weights upload: ") + cudaGetErrorString(ce));
         }
@@ -438,8 +463,14 @@ rtu_status rtu_system_create(const rtu_system_desc* d, void* ws, size_t ws_bytes
     std::vector<double> P(K * K), uv(2 * K);
     {
         std::vector<float> pf(f64 ? 0 : K * K);
-        ce = f64 ? cudaMemcpy(P.data(), d->psf, K * K * 8, cudaMemcpyDeviceToHost)
-                 : cudaMemcpy(pf.data(), d->psf, K * K * 4, cudaMemcpyDeviceToHost);
+        const void* hp = hin ? hin->psf : nullptr;
+        if (hp) {
+            if (f64) memcpy(P.data(), hp, K * K * 8);
+            else memcpy(pf.data(), hp, K * K * 4);
+        } else {
+            ce = f64 ? cudaMemcpy(P.data(), d->psf, K * K * 8, cudaMemcpyDeviceToHost)
+                     : cudaMemcpy(pf.data(), d->psf, K * K * 4, cudaMemcpyDeviceToHost);
+        }
         if (ce != cudaSuccess) { delete s; return fail(RTU_E_CUDA, std::string("psf copy: ") + cudaGetErrorString(ce)); }
         if (!f64) for (int i = 0; i < K * K; ++i) P[i] = pf[i];
     }
@@ -463,8 +494,11 @@ rtu_status rtu_system_create(const rtu_system_desc* d, void* ws, size_t ws_bytes
         const size_t tw_off = (size_t)(reinterpret_cast<char*>(htw) - img.data());
         // the arc-mask pixel list (n_mask entries) and the FFT / Chebyshev / PSF tables; the
         // weights region in between is written above (weighted grid) or unused
-        if ((ce = cudaMemcpy(base, img.data(), idx.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
-            (ce = cudaMemcpy(base + tw_off, img.data() + tw_off, st - tw_off, cudaMemcpyHostToDevice)) != cudaSuccess) {
+        // stream-ordered copies from pageable memory: the driver stages the bytes before
+        // the call returns, so `img` may go out of scope; legacy stream when none is given
+        if ((ce = cudaMemcpyAsync(base, img.data(), idx.size() * 4, cudaMemcpyHostToDevice, cs)) != cudaSuccess ||
+            (ce = cudaMemcpyAsync(base + tw_off, img.data() + tw_off, st - tw_off, cudaMemcpyHostToDevice, cs)) !=
+                cudaSuccess) {
             delete s;
             return fail(RTU_E_CUDA, std::string("table upload: ") + cudaGetErrorString(ce));
         }
@@ -519,6 +553,7 @@ rtu_status fill_args(rtu_system* s, const rtu_eval& v, EvalArgs& e) {
     e.lens = v.lens; e.latents = v.latents; e.ps = v.ps; e.dlogL = v.dlogL;
     e.stats = v.stats; e.model_out = v.model; e.image_out = v.image; e.source_out = v.source;
     e.cdf_out = v.cdf; e.hist_out = v.ray_hist;
+    e.sel_hist_out = v.sel_hist; e.centres_out = v.centres;
     e.g_lat = v.g_latents; e.g_lens = v.g_lens; e.g_ps = v.g_ps;
     e.n_light = d.n_light;
     e.light = d.n_light > 0 ? v.light : nullptr;
@@ -642,16 +677,16 @@ rtu_status stream_after(cudaStream_t to, cudaStream_t from, cudaEvent_t ev) {
 template <typename T>
 rtu_status run_chunk(Batch& B, int phase, cudaStream_t st, const SideStream& ss) {
     rtu_status r;
-    int max_n2 = 0, max_s2 = 0, any_sub = 0, maxK = 0, maxPsf = 0, any_light = 0;
+    int max_s2 = 0, any_sub = 0, maxK = 0, maxPsf = 0, any_light = 0;
+    size_t grid_bytes = 0;     // the largest source grid the render kernels stage in shared memory
     for (int i = 0; i < B.n; ++i) {
+        grid_bytes = std::max(grid_bytes, grid_smem_bytes(B.e[i].n_src, (int)sizeof(T)));
         maxPsf = std::max(maxPsf, B.e[i].psf_k);
         any_light |= B.e[i].n_light > 0;
-        max_n2 = std::max(max_n2, B.e[i].n_src * B.e[i].n_src);
         max_s2 = std::max(max_s2, B.e[i].s * B.e[i].s);
         any_sub |= (B.e[i].sub_kind && B.e[i].n_sub > 0);
         maxK = std::max(maxK, B.e[i].n_nodes + 2);
     }
-    const size_t grid_bytes = align_up((size_t)max_n2 * sizeof(T), 128);
     if (phase & (PH_GRID | PH_FORWARD)) {
         // S1-S5 (the forward's critical branch: on the high-priority side stream, issued
         // first, when the GP source, which only needs the latents and spectrum
@@ -672,7 +707,6 @@ rtu_status run_chunk(Batch& B, int phase, cudaStream_t st, const SideStream& ss)
     }
     if (phase & PH_FORWARD) {
         if ((r = stream_after(st, ss.s, ss.join))) return r;
-        if (grid_bytes > MAX_DYN) return fail(RTU_E_ARG, "source grid too large for shared memory");
         const size_t render_smem = grid_bytes + (size_t)CTA_R * max_s2 * 2;
         if (render_smem > MAX_DYN) return fail(RTU_E_ARG, "render shared memory exceeds the limit");
         if ((r = launch("k_render", k_render<T, false>, B, t_render_fit, CTA_R, render_smem, st))) return r;
@@ -986,6 +1020,33 @@ rtu_status rtu_profile_report(char* buf, size_t bytes) {
 
 }  // extern "C"
 
+// ------------------------------------------------- double-float self-test
+// y[i] = f(x) of the double-float type that the FP32 path's FP64-class islands use,
+// from double inputs converted to double-float (hi = rounded x, lo = rounded rest):
+// op 0 exp, 1 log, 2 sqrt (x[i]); 3 quotient, 4 product, 5 sum (x[2i], x[2i+1]).
+__global__ void __launch_bounds__(256) k_selftest_df(int op, const double* x, double* y, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    DF r(0.0f, 0.0f);
+    if (op <= 2) {
+        const DF a(x[i]);
+        r = op == 0 ? r_exp(a) : (op == 1 ? r_log(a) : r_sqrt(a));
+    } else {
+        const DF a(x[2 * i]), b(x[2 * i + 1]);
+        r = op == 3 ? a / b : (op == 4 ? a * b : a + b);
+    }
+    y[i] = r.to_double();
+}
+
+extern "C" rtu_status rtu_selftest_df(int32_t op, const double* x, double* y, int32_t n, void* stream) {
+    if (op < 0 || op > 5) return fail(RTU_E_ARG, "rtu_selftest_df: op must be in [0, 5]");
+    if (n < 0 || (n > 0 && (!x || !y))) return fail(RTU_E_ARG, "rtu_selftest_df: bad buffers");
+    if (n == 0) return RTU_OK;
+    k_selftest_df<<<(n + 255) / 256, 256, 0, static_cast<cudaStream_t>(stream)>>>(op, x, y, n);
+    const cudaError_t ce = cudaGetLastError();
+    return ce == cudaSuccess ? RTU_OK : fail(RTU_E_CUDA, std::string("launch k_selftest_df: ") + cudaGetErrorString(ce));
+}
+
 namespace {
 
 int t_elbo_sample(const ElboArgs& a) { return a.n_samples * ((a.st.n_state + ELBO_NT - 1) / ELBO_NT); }
@@ -1016,6 +1077,14 @@ int32_t rtu_n_sites(const rtu_system_desc* d) {
 
 rtu_status rtu_elbo_init(rtu_system* s, const rtu_prior* priors, const double* fixed, const double* loc,
                          const double* rho, uint32_t tag) {
+    const rtu_status r = rtu_elbo_init_on(s, priors, fixed, loc, rho, tag, nullptr);
+    if (r != RTU_OK) return r;
+    const cudaError_t ce = cudaStreamSynchronize(nullptr);     // synchronous, as documented
+    return ce == cudaSuccess ? RTU_OK : fail(RTU_E_CUDA, std::string("rtu_elbo_init: ") + cudaGetErrorString(ce));
+}
+
+rtu_status rtu_elbo_init_on(rtu_system* s, const rtu_prior* priors, const double* fixed, const double* loc,
+                            const double* rho, uint32_t tag, void* stream) {
     if (!s || !priors || !fixed || !loc || !rho) return fail(RTU_E_ARG, "rtu_elbo_init: null argument");
     const Sizes& z = s->z;
     for (int i = 0; i < z.n_sites; ++i) {
@@ -1028,9 +1097,11 @@ rtu_status rtu_elbo_init(rtu_system* s, const rtu_prior* priors, const double* f
             return fail(RTU_E_ARG, "bounded prior needs d > c");
         if (p.kind == RTU_PRIOR_LINEAR && !(p.a >= -1.0)) return fail(RTU_E_ARG, "linear prior needs a >= -1");
     }
-    // the state region (loc, rho, Adam m and v, priors, fixed values, step) assembled
-    // on the host with the device layout, then one copy
-    const size_t span = (size_t)(reinterpret_cast<char*>(s->st.t) + 8 - reinterpret_cast<char*>(s->st.loc));
+    // the state region (loc, rho, Adam m and v, priors, fixed values, step, and the
+    // zeroed partials and last gradient) assembled on the host with the device layout,
+    // then one copy
+    const size_t span = (size_t)(reinterpret_cast<char*>(s->st.grad) + (size_t)2 * z.n_state * 8 -
+                                 reinterpret_cast<char*>(s->st.loc));
     std::vector<char> img(span, 0);
     ElboState hs;
     state_layout(s->d, img.data(), &hs);
@@ -1038,7 +1109,8 @@ rtu_status rtu_elbo_init(rtu_system* s, const rtu_prior* priors, const double* f
     memcpy(hs.rho, rho, (size_t)z.n_state * 8);
     memcpy(hs.prior, priors, (size_t)z.n_sites * sizeof(rtu_prior));
     memcpy(hs.fixed, fixed, (size_t)z.n_fixed * 8);
-    cudaError_t ce = cudaMemcpy(s->st.loc, img.data(), span, cudaMemcpyHostToDevice);
+    cudaError_t ce = cudaMemcpyAsync(s->st.loc, img.data(), span, cudaMemcpyHostToDevice,
+                                     static_cast<cudaStream_t>(stream));
     if (ce != cudaSuccess) return fail(RTU_E_CUDA, std::string("rtu_elbo_init: ") + cudaGetErrorString(ce));
     s->st.tag = tag;
     s->elbo_ready = true;
@@ -1119,6 +1191,16 @@ rtu_status rtu_elbo_export(const rtu_system* s, void* host, size_t bytes) {
         (ce = cudaMemcpy(h + 4 * n, s->st.v, 2 * n, cudaMemcpyDeviceToHost)) ||
         (ce = cudaMemcpy(h + 6 * n, s->st.t, 8, cudaMemcpyDeviceToHost)))
         return fail(RTU_E_CUDA, std::string("rtu_elbo_export: ") + cudaGetErrorString(ce));
+    return RTU_OK;
+}
+
+rtu_status rtu_elbo_grad(const rtu_system* s, double* host, size_t bytes) {
+    if (!s || !host) return fail(RTU_E_ARG, "rtu_elbo_grad: null argument");
+    const size_t n = (size_t)s->z.n_state * 8;
+    if (bytes < 2 * n) return fail(RTU_E_ARG, "rtu_elbo_grad: buffer smaller than 2 (n_sites + n_src^2) doubles");
+    if (!s->elbo_ready) return fail(RTU_E_ARG, "rtu_elbo_grad: call rtu_elbo_init first");
+    const cudaError_t ce = cudaMemcpy(host, s->st.grad, 2 * n, cudaMemcpyDeviceToHost);
+    if (ce != cudaSuccess) return fail(RTU_E_CUDA, std::string("rtu_elbo_grad: ") + cudaGetErrorString(ce));
     return RTU_OK;
 }
 

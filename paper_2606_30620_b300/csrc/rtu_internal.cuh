@@ -64,6 +64,8 @@ struct EvalArgs {
     void* g_lat;
     double* g_lens;
     double* g_ps;
+    int* sel_hist_out;     // [2][HB] level-1 order-statistic histograms (nullable)
+    double* centres_out;   // [2][n_mask] traced arc-mask centre positions (nullable)
     // workspace slot
     double* beta;      // [2][n_mask] traced centre rays (double)
     double* cpart;     // [n_cta_c][8] centre partial sums and ranges of beta
@@ -101,6 +103,9 @@ struct EvalArgs {
     void* corner;      // real2 [n_cells][4] per-cell bilinear corner sums (float: hi + lo pairs)
     double* apart;     // [nacc][n_row_adj] render-adjoint partials (column-major)
     int* flags;        // device flag word
+    unsigned long long* gmax;  // the largest |d L / d image| (bits of a non-negative float in the low
+                               // word, or of a double): zeroed by k_zero and k_grad_final, raised
+                               // by the PSF adjoint, read by the cell gather
     void* lensk;       // LensK<T> then LensK<double> of the evaluation
     int* ecount;       // number of deferred near-edge rays (float mode)
     unsigned long long* pdef;  // [n_img^2] bit q: sub-ray q deferred to the double pass (float mode)
@@ -294,6 +299,21 @@ __device__ __forceinline__ double warp_sum_lane0(T v) {
 template <typename T> struct real4_of;
 template <> struct real4_of<float> { typedef float4 type; };
 template <> struct real4_of<double> { typedef double4_32a type; };
+
+// raise the evaluation's largest |d L / d image| (E.gmax) by this thread's value: a
+// maximum, so the result does not depend on the order of the atomics (one per warp)
+template <typename T>
+__device__ __forceinline__ void note_gmax(const EvalArgs& E, T v) {
+    v = v < T(0) ? -v : v;
+    for (int o = 16; o > 0; o >>= 1) {
+        const T w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = w > v ? w : v;
+    }
+    if ((threadIdx.x & 31) == 0 && v > T(0)) {
+        if (sizeof(T) == 4) atomicMax(reinterpret_cast<unsigned int*>(E.gmax), __float_as_uint((float)v));
+        else atomicMax(E.gmax, (unsigned long long)__double_as_longlong((double)v));
+    }
+}
 
 // ------------------------------------------------------------- lens trace
 // Lens parameters as a kernel sees them: the EPL's per-system constants, the

@@ -1,12 +1,16 @@
-// rtu_static.cu -- rtu_gp_source_static: the GP source step (Eq. 1-3) without a
-// caller-provided workspace, for callers that cannot allocate device memory.
+// rtu_static.cu -- rtu_gp_source_static: the GP source step (white noise filtered
+// by the square root of the power spectrum through FFTs, then the softplus map and
+// the alpha power) without a caller-provided workspace, for callers that cannot
+// allocate device memory.
 //
 // Its scratch is one file-scope __device__ array (RTU_STATIC_MAX_NSRC^2 complex
-// floats, 128 KiB) that every GPU loading this library holds until the process
+// doubles, 256 KiB) that every GPU loading this library holds until the process
 // exits.  Host code cannot pass the array's name to a kernel: in host code that
-// name is a host-side stand-in, not a device address.  The first call on a
-// device therefore looks up the array's device address with
-// cudaGetSymbolAddress (with that device current) and keeps it for later calls.
+// name is a host-side stand-in, not a device address.  So the host looks up the
+// array's device address with cudaGetSymbolAddress (with the device current):
+// at the first call on a device, and again at every later call that is not being
+// captured into a CUDA graph (so a device reset between calls is picked up); a
+// captured call uses the address found by the device's last uncaptured call.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -26,7 +30,7 @@ namespace {
 constexpr int SMAX = RTU_STATIC_MAX_NSRC;
 
 // the FFT buffer shared by every call of rtu_gp_source_static
-static __device__ __align__(256) float2 g_gp_static_scratch[SMAX * SMAX];
+static __device__ __align__(256) double2 g_gp_static_scratch[SMAX * SMAX];
 
 constexpr int MAX_DEVICES = 64;
 std::mutex g_mu;
@@ -35,13 +39,15 @@ void* g_scratch_addr[MAX_DEVICES] = {nullptr};
 rtu_status fail_static(rtu_status code, const std::string& m) { return rtu_fail_internal(code, m.c_str()); }
 
 // One CTA: twiddles, digit reversal and radices built in shared memory, then
-// the forward FFT, the sqrt(P) filter, the inverse FFT and the softplus map --
-// the same device functions as the workspace path.
+// the forward FFT, the sqrt(P) filter, the inverse FFT and the softplus map, all
+// in double and rounded to float at the end, like the workspace path (near f = 0
+// the softplus turns an absolute error of f into a relative error of the source
+// 1/s0 = 100 times larger, which rules out float transforms).
 __global__ void __launch_bounds__(GP_NT) k_gp_source_static(int n, double pitch, int family, const float* lat,
-                                                            const double* ps, float* out, Cx<float>* W) {
+                                                            const double* ps, float* out, Cx<double>* W) {
     extern __shared__ __align__(128) unsigned char smem_static[];
-    Cx<float>* sm = reinterpret_cast<Cx<float>*>(smem_static);
-    __shared__ Cx<float> tw_s[SMAX];
+    Cx<double>* sm = reinterpret_cast<Cx<double>*>(smem_static);
+    __shared__ Cx<double> tw_s[SMAX];
     __shared__ int rev_s[SMAX];
     __shared__ int rad_s[MAX_RADIX];
     __shared__ int nrad_s;
@@ -56,7 +62,7 @@ __global__ void __launch_bounds__(GP_NT) k_gp_source_static(int n, double pitch,
     const int S = nrad_s;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const double ang = -2.0 * 3.14159265358979323846 * i / n;
-        tw_s[i] = Cx<float>{(float)cos(ang), (float)sin(ang)};
+        tw_s[i] = Cx<double>{cos(ang), sin(ang)};
         // position p holds element rev(p): p = sum_s j_s L_{s-1} -> j_S + r_S j_{S-1} + ...
         int js[MAX_RADIX];
         int q = i;
@@ -67,29 +73,29 @@ __global__ void __launch_bounds__(GP_NT) k_gp_source_static(int n, double pitch,
     }
     __syncthreads();
     const int n2 = n * n;
-    const int chunk = max(1, min(n, (int)(GP_SMEM / sizeof(Cx<float>)) / n));
-    for (int i = threadIdx.x; i < n2; i += blockDim.x) W[i] = Cx<float>{lat[i], 0.0f};
+    const int chunk = max(1, min(n, (int)(GP_SMEM / sizeof(Cx<double>)) / n));
+    for (int i = threadIdx.x; i < n2; i += blockDim.x) W[i] = Cx<double>{(double)lat[i], 0.0};
     __syncthreads();
-    fft2<float>(W, n, rad_s, S, tw_s, rev_s, sm, chunk, false);
+    fft2<double>(W, n, rad_s, S, tw_s, rev_s, sm, chunk, false);
     const int nf = n_family(family);
-    float psv[4];
-    for (int q = 0; q < nf; ++q) psv[q] = (float)ps[q];
-    const float kscale = (float)(2.0 * 3.14159265358979323846 / pitch);
+    double psv[4];
+    for (int q = 0; q < nf; ++q) psv[q] = ps[q];
+    const double kscale = 2.0 * 3.14159265358979323846 / pitch;
     for (int i = threadIdx.x; i < n2; i += blockDim.x) {
         const int ky = i / n, kx = i - ky * n;
-        const float fx = fftfreq<float>(kx, n), fy = fftfreq<float>(ky, n);
-        const float k = kscale * sqrtf(fx * fx + fy * fy);
-        float gdummy[3];
-        const float sp = sqrtP_and_grad<float>(family, psv, k, gdummy);
-        W[i] = Cx<float>{W[i].x * sp, W[i].y * sp};
+        const double fx = fftfreq<double>(kx, n), fy = fftfreq<double>(ky, n);
+        const double k = kscale * sqrt(fx * fx + fy * fy);
+        double gdummy[3];
+        const double sp = sqrtP_and_grad<double>(family, psv, k, gdummy);
+        W[i] = Cx<double>{W[i].x * sp, W[i].y * sp};
     }
     __syncthreads();
-    fft2<float>(W, n, rad_s, S, tw_s, rev_s, sm, chunk, true);
-    const float alpha = (float)ps[nf];
-    const float inv_n2 = 1.0f / (float)n2;
+    fft2<double>(W, n, rad_s, S, tw_s, rev_s, sm, chunk, true);
+    const double alpha = ps[nf];
+    const double inv_n2 = 1.0 / (double)n2;
     for (int i = threadIdx.x; i < n2; i += blockDim.x) {
-        const float f = W[i].x * inv_n2;
-        out[i] = r_exp(alpha * log_sp_s0<float>(f / 0.01f));
+        const double f = W[i].x * inv_n2;
+        out[i] = (float)exp(alpha * log_sp_s0<double>(f / 0.01));
     }
 }
 
@@ -117,12 +123,19 @@ rtu_status rtu_gp_source_static(int32_t n_src, double src_pitch, int32_t ps_fami
     cudaError_t ce = cudaGetDevice(&dev);
     if (ce != cudaSuccess) return fail_static(RTU_E_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(ce));
     if (dev < 0 || dev >= MAX_DEVICES) return fail_static(RTU_E_ARG, "rtu_gp_source_static: device index too large");
+    // the caller may be capturing this stream into a CUDA graph: then no set-up call
+    // is made and the address of the device's last uncaptured call is used
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    ce = cudaStreamIsCapturing(static_cast<cudaStream_t>(stream), &cap);
+    if (ce != cudaSuccess)
+        return fail_static(RTU_E_CUDA, std::string("cudaStreamIsCapturing: ") + cudaGetErrorString(ce));
     void* scratch = nullptr;
     {
         std::lock_guard<std::mutex> g(g_mu);
-        if (!g_scratch_addr[dev]) {
-            // first call on this device (the device is current): device address of the
-            // static array and the kernel's shared-memory limit
+        if (cap == cudaStreamCaptureStatusNone) {
+            // set-up with this device current: the static array's device address and the
+            // kernel's shared-memory limit (neither allocates; both are looked up again
+            // at every uncaptured call, so a device reset between calls is picked up)
             void* p = nullptr;
             ce = cudaGetSymbolAddress(&p, g_gp_static_scratch);
             if (ce != cudaSuccess)
@@ -131,11 +144,14 @@ rtu_status rtu_gp_source_static(int32_t n_src, double src_pitch, int32_t ps_fami
             if (ce != cudaSuccess)
                 return fail_static(RTU_E_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(ce));
             g_scratch_addr[dev] = p;
+        } else if (!g_scratch_addr[dev]) {
+            return fail_static(RTU_E_ARG, "rtu_gp_source_static: make a first call on this device outside "
+                                          "stream capture (it looks up the scratch address)");
         }
         scratch = g_scratch_addr[dev];
     }
     k_gp_source_static<<<1, GP_NT, GP_SMEM, static_cast<cudaStream_t>(stream)>>>(
-        n_src, src_pitch, ps_family, latents, ps, source, static_cast<Cx<float>*>(scratch));
+        n_src, src_pitch, ps_family, latents, ps, source, static_cast<Cx<double>*>(scratch));
     ce = cudaGetLastError();
     if (ce != cudaSuccess) return fail_static(RTU_E_CUDA, std::string("launch: ") + cudaGetErrorString(ce));
     return RTU_OK;

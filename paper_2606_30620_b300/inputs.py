@@ -122,7 +122,7 @@ def with_light(m: Mock, n: int = 5, seed: int = 0, amp: float = 0.3) -> Mock:
 
 def with_snr_weights(m: Mock, cap: int = 100) -> Mock:
     """Integer ray weights from the pixel SNR (data / sigma, rounded, clipped to
-    [1, cap]) -- one of the weightings Sec. 5 names for a weighted RTU grid."""
+    [1, cap]) -- one of the weightings Sec. 6.3 names for a weighted RTU grid."""
     m.weights = np.clip(np.rint(m.data / m.sigma), 1, cap).astype(np.uint32)
     return m
 
@@ -206,6 +206,84 @@ def config_core(seed: int = 4000, n_img: int = 40, s: int = 2, n_src: int = 24) 
                 profile=PROFILE_EPL, ps_family=PS_MATERN_LIKE, sub_kind=SUB_NONE, data=data,
                 mask=np.ones((n_img, n_img), np.uint8), psf=gaussian_psf(5, 2.0 * pix, pix), sigma=sigma,
                 lens=np.asarray(lens, np.float64), latents=latents, ps=np.asarray(ps, np.float64))
+
+
+def config_bimodal(seed: int = 4500, n_img: int = 120, s: int = 2, n_src: int = 32, profile=PROFILE_EPL) -> Mock:
+    """An arc mask of two disks of unequal size outside the Einstein ring on opposite
+    sides of the lens (centred at +-2 theta_E on a line through the lens centre): their
+    centre rays land near +-theta_E in the source plane, so each marginal along that
+    line is bimodal, its quantile function jumps between the two clusters, and the
+    degree-21 interpolant of App. C overshoots and falls between nodes -- the input that
+    exercises the fit's monotonicity guard.  EPL + shear, Matern-like spectrum."""
+    rng = np.random.default_rng(seed)
+    lens = _epl_lens(rng)
+    if profile == PROFILE_SIE:
+        lens[1] = 2.0
+    pix = 6.0 * lens[0] / n_img
+    pitch = 3.0 * lens[0] / n_src
+    k0 = rng.uniform(0.5, 4.0)
+    ps = [_matern_like_amp(k0, pitch), k0, rng.uniform(1.0, 2.0)]
+    m = _finish(f"bimodal-{seed}", n_img, pix, s, n_src, profile, PS_MATERN_LIKE, lens, ps, rng,
+                psf_k=5, fwhm=2 * pix, snr=50.0, width=0.25, pitch=pitch)
+    c = (np.arange(n_img) - (n_img - 1) / 2.0) * pix
+    yy, xx = np.meshgrid(c, c, indexing="ij")
+    ang = rng.uniform(0.0, math.pi)
+    cx, cy = 2.0 * lens[0] * math.cos(ang), 2.0 * lens[0] * math.sin(ang)
+    r1, r2 = 0.30 * lens[0], 0.18 * lens[0]
+    m.mask = ((np.hypot(xx - lens[4] - cx, yy - lens[5] - cy) < r1)
+              | (np.hypot(xx - lens[4] + cx, yy - lens[5] + cy) < r2)).astype(np.uint8)
+    return m
+
+
+def config_outlier(seed: int = 4600, n_img: int = 201, s: int = 2, n_src: int = 48) -> Mock:
+    """A c2-like system whose arc mask also holds the 3 x 3 pixels around the lens
+    centre, with a steep power law (gamma = 2.6: alpha grows as |theta|^-0.6 towards the
+    centre) centred ~1e-4 pixel off the central pixel's centre: that pixel's centre ray
+    lands ~1000" away, its neighbours ~10", the ring's within ~1" -- a few far outliers
+    that squeeze the ring's rays into a small fraction of the order statistics'
+    histogram bins over [min, max] (tens of rays per bin at the node ranks)."""
+    rng = np.random.default_rng(seed)
+    lens = _epl_lens(rng)
+    lens[1] = 2.6
+    pix = 0.05
+    lens[4], lens[5] = 1.6e-4 * pix, -0.9e-4 * pix
+    pitch = 3.0 * lens[0] / n_src
+    k0 = rng.uniform(0.5, 4.0)
+    ps = [_matern_like_amp(k0, pitch), k0, rng.uniform(1.0, 2.0)]
+    m = _finish(f"outlier-{seed}", n_img, pix, s, n_src, PROFILE_EPL, PS_MATERN_LIKE, lens, ps, rng,
+                psf_k=9, fwhm=0.1, snr=50.0, width=0.25, pitch=pitch)
+    c = (n_img - 1) // 2
+    m.mask[c - 1:c + 2, c - 1:c + 2] = 1
+    return m
+
+
+def config_ties(seed: int = 4700, n_img: int = 301, s: int = 2, n_src: int = 48) -> Mock:
+    """Many exactly tied centre-ray positions: an odd image whose central column sits at
+    theta_x = 0, a lens centred on that column with position angle 0 (e2 = 0) and shear
+    Gamma2 = 0, so every pixel of the column traces to beta_x = 0 exactly.  The arc mask
+    is the half annulus x > 0, 1.3 theta_E < |theta| < 2.5 theta_E (outside the critical
+    curve: beta_x > 0 there) plus 121 pixels of the column: a block of 121 tied rays at
+    the bottom of the x marginal, ~0.7% of the sample, covering the first Chebyshev
+    node's ranks and no other."""
+    rng = np.random.default_rng(seed)
+    lens = _epl_lens(rng)
+    q = rng.uniform(0.75, 0.95)
+    lens[2], lens[3] = ellipticity(q, 0.0)
+    lens[4] = 0.0
+    lens[7] = 0.0
+    pix = 0.025
+    pitch = 3.0 * lens[0] / n_src
+    k0 = rng.uniform(0.5, 4.0)
+    ps = [_matern_like_amp(k0, pitch), k0, rng.uniform(1.0, 2.0)]
+    m = _finish(f"ties-{seed}", n_img, pix, s, n_src, PROFILE_EPL, PS_MATERN_LIKE, lens, ps, rng,
+                psf_k=9, fwhm=0.05, snr=50.0, width=0.12, pitch=pitch)
+    c = (np.arange(n_img) - (n_img - 1) / 2.0) * pix
+    yy, xx = np.meshgrid(c, c, indexing="ij")
+    r = np.hypot(xx, yy - lens[5])
+    m.mask = ((xx > 0.5 * pix) & (r > 1.3 * lens[0]) & (r < 2.5 * lens[0])).astype(np.uint8)
+    mid = (n_img - 1) // 2
+    m.mask[mid - 60:mid + 61, mid] = 1
+    return m
 
 
 def config_c4(seed: int = 3000, with_subs: bool = True, n_img: int = 400, s: int = 3,

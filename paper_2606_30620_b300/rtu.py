@@ -26,6 +26,7 @@ RTU_TRANSFORM_RTU, RTU_TRANSFORM_UNIFORM, RTU_TRANSFORM_LINEAR = 0, 1, 2
 STAT_LOGL, STAT_CHI2, STAT_NMASK, STAT_FLAGS, STAT_N_IN_GRID = 0, 1, 2, 3, 4
 W_NONMONOTONE, W_SELECT, W_TIMEOUT = 1, 2, 4
 N_STATS = 5
+SEL_BINS = 65536
 N_PS = {RTU_PS_POWER_LAW: 2, RTU_PS_MATERN_LIKE: 2, RTU_PS_MATERN: 3}
 
 
@@ -51,7 +52,11 @@ class SystemDesc(ctypes.Structure):
 class Eval(ctypes.Structure):
     _fields_ = [("slot", ctypes.c_int32), ("pad_", ctypes.c_int32)] + [(n, ctypes.c_void_p) for n in (
         "lens", "latents", "ps", "dlogL", "stats", "model", "image", "source", "cdf", "ray_hist",
-        "g_latents", "g_lens", "g_ps", "light", "g_light")]
+        "g_latents", "g_lens", "g_ps", "light", "g_light", "sel_hist", "centres")]
+
+
+class HostInputs(ctypes.Structure):
+    _fields_ = [("mask", ctypes.c_void_p), ("psf", ctypes.c_void_p), ("weights", ctypes.c_void_p)]
 
 
 class Prior(ctypes.Structure):
@@ -64,6 +69,9 @@ _lib.rtu_workspace_size.restype = ctypes.c_size_t
 _lib.rtu_system_create.argtypes = [ctypes.POINTER(SystemDesc), ctypes.c_void_p, ctypes.c_size_t,
                                    ctypes.POINTER(ctypes.c_void_p)]
 _lib.rtu_system_create.restype = ctypes.c_int32
+_lib.rtu_system_create_on.argtypes = [ctypes.POINTER(SystemDesc), ctypes.POINTER(HostInputs), ctypes.c_void_p,
+                                      ctypes.c_size_t, ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]
+_lib.rtu_system_create_on.restype = ctypes.c_int32
 _lib.rtu_system_destroy.argtypes = [ctypes.c_void_p]
 _lib.rtu_system_destroy.restype = ctypes.c_int32
 for _name in ("rtu_build_grid", "rtu_forward", "rtu_adjoint"):
@@ -75,6 +83,10 @@ _lib.rtu_n_sites.restype = ctypes.c_int32
 _lib.rtu_elbo_init.argtypes = [ctypes.c_void_p, ctypes.POINTER(Prior), ctypes.POINTER(ctypes.c_double),
                                ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), ctypes.c_uint32]
 _lib.rtu_elbo_init.restype = ctypes.c_int32
+_lib.rtu_elbo_init_on.argtypes = [ctypes.c_void_p, ctypes.POINTER(Prior), ctypes.POINTER(ctypes.c_double),
+                                  ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), ctypes.c_uint32,
+                                  ctypes.c_void_p]
+_lib.rtu_elbo_init_on.restype = ctypes.c_int32
 _lib.rtu_elbo_step.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64,
                                ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p]
 _lib.rtu_elbo_step.restype = ctypes.c_int32
@@ -82,11 +94,15 @@ _lib.rtu_elbo_state_bytes.argtypes = [ctypes.c_void_p]
 _lib.rtu_elbo_state_bytes.restype = ctypes.c_size_t
 _lib.rtu_elbo_export.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]
 _lib.rtu_elbo_export.restype = ctypes.c_int32
+_lib.rtu_elbo_grad.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]
+_lib.rtu_elbo_grad.restype = ctypes.c_int32
 _lib.rtu_elbo_import.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]
 _lib.rtu_elbo_import.restype = ctypes.c_int32
 _lib.rtu_gp_source_static.argtypes = [ctypes.c_int32, ctypes.c_double, ctypes.c_int32, ctypes.c_void_p,
                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
 _lib.rtu_gp_source_static.restype = ctypes.c_int32
+_lib.rtu_selftest_df.argtypes = [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]
+_lib.rtu_selftest_df.restype = ctypes.c_int32
 _lib.rtu_graph_replay.argtypes = [ctypes.c_int32]
 _lib.rtu_graph_replay.restype = ctypes.c_int32
 _lib.rtu_profile_enable.argtypes = [ctypes.c_int32]
@@ -98,9 +114,11 @@ _lib.rtu_profile_timeline.restype = ctypes.c_int32
 _lib.rtu_last_error.restype = ctypes.c_char_p
 _lib.rtu_version.restype = ctypes.c_char_p
 
-EXPORTED = ("rtu_workspace_size", "rtu_system_create", "rtu_system_destroy", "rtu_build_grid",
-            "rtu_forward", "rtu_adjoint", "rtu_n_sites", "rtu_elbo_init", "rtu_elbo_step",
-            "rtu_elbo_state_bytes", "rtu_elbo_export", "rtu_elbo_import", "rtu_gp_source_static",
+EXPORTED = ("rtu_workspace_size", "rtu_system_create", "rtu_system_create_on", "rtu_system_destroy",
+            "rtu_build_grid", "rtu_forward", "rtu_adjoint", "rtu_n_sites", "rtu_elbo_init", "rtu_elbo_init_on",
+            "rtu_elbo_step",
+            "rtu_elbo_state_bytes", "rtu_elbo_export", "rtu_elbo_import", "rtu_elbo_grad", "rtu_gp_source_static",
+            "rtu_selftest_df",
             "rtu_graph_replay", "rtu_profile_enable",
             "rtu_profile_report", "rtu_profile_timeline", "rtu_last_error", "rtu_version")
 
@@ -156,10 +174,47 @@ class System:
     def __init__(self, data, mask, psf, sigma, pix, s_super, n_src, src_pitch, profile=RTU_SIE,
                  ps_family=RTU_PS_POWER_LAW, sub_kind=RTU_SUB_NONE, n_sub=0, precision=RTU_F32,
                  n_nodes=22, degree=21, n_slots=1, device="cuda", transform=RTU_TRANSFORM_RTU, n_light=0,
-                 weights=None):
+                 weights=None, stream=None):
+        """stream=None: synchronous creation (rtu_system_create).  With a torch stream
+        and host (numpy) data, mask and psf: the observation travels in one pinned
+        copy and the library builds the system from the host copies with uploads
+        ordered on that stream (rtu_system_create_on); calls ordered after the stream
+        may use the system."""
         self.dtype = torch.float64 if precision == RTU_F64 else torch.float32
         self.device = torch.device(device)
-        if isinstance(data, np.ndarray) and isinstance(psf, np.ndarray):
+        on_stream = stream is not None
+        if on_stream:
+            if not (isinstance(data, np.ndarray) and isinstance(psf, np.ndarray) and isinstance(mask, np.ndarray)):
+                raise ValueError("creation on a stream takes host (numpy) data, mask and psf")
+            npdt = np.float64 if precision == RTU_F64 else np.float32
+            tb = np.dtype(npdt).itemsize
+            nd, nk, nm = data.size, psf.size, mask.size
+            nw = 0 if weights is None else nm
+            total = (nd + nk) * tb + nm + 4 * nw
+            pad = (-total) % 16
+            host = torch.empty(total + pad, dtype=torch.uint8, pin_memory=True)
+            hb = host.numpy()
+            hdp = hb[:nd * tb].view(npdt)
+            hdp[:] = np.asarray(data, npdt).ravel()
+            hpsf = hb[nd * tb:(nd + nk) * tb].view(npdt)
+            hpsf[:] = np.asarray(psf, npdt).ravel()
+            hmask = hb[(nd + nk) * tb:(nd + nk) * tb + nm]
+            hmask[:] = (np.asarray(mask).ravel() != 0)
+            hw = None
+            if weights is not None:
+                hw = hb[(nd + nk) * tb + nm:(nd + nk) * tb + nm + 4 * nw].view(np.uint32)
+                hw[:] = np.asarray(weights).astype(np.uint32).ravel()
+            dev = torch.empty(total + pad, dtype=torch.uint8, device=self.device)
+            with torch.cuda.stream(stream):
+                dev.copy_(host, non_blocking=True)
+            self._host = host          # kept until the system is closed (the copy reads it)
+            self.data = dev[:nd * tb].view(self.dtype).view(data.shape)
+            self.psf = dev[nd * tb:(nd + nk) * tb].view(self.dtype).view(psf.shape)
+            self.mask = dev[(nd + nk) * tb:(nd + nk) * tb + nm].view(mask.shape)
+            self.weights = None if hw is None else dev[(nd + nk) * tb + nm:(nd + nk) * tb + nm + 4 * nw].view(
+                torch.int32)
+            self._host_in = HostInputs(hmask.ctypes.data, hpsf.ctypes.data, None if hw is None else hw.ctypes.data)
+        elif isinstance(data, np.ndarray) and isinstance(psf, np.ndarray):
             # host arrays: the image and the PSF travel in one copy
             npdt = np.float64 if precision == RTU_F64 else np.float32
             both = np.concatenate([np.asarray(data, npdt).ravel(), np.asarray(psf, npdt).ravel()])
@@ -169,11 +224,12 @@ class System:
         else:
             self.data = torch.as_tensor(data, dtype=self.dtype, device=self.device).contiguous()
             self.psf = torch.as_tensor(psf, dtype=self.dtype, device=self.device).contiguous()
-        self.mask = torch.as_tensor(mask, dtype=torch.uint8, device=self.device).contiguous()
-        # weighted RTU grid: integer ray weights per pixel (read once at create)
-        self.weights = None if weights is None else torch.as_tensor(
-            weights.astype("int32") if hasattr(weights, "astype") else weights,
-            dtype=torch.int32, device=self.device).contiguous()
+        if not on_stream:
+            self.mask = torch.as_tensor(mask, dtype=torch.uint8, device=self.device).contiguous()
+            # weighted RTU grid: integer ray weights per pixel (read once at create)
+            self.weights = None if weights is None else torch.as_tensor(
+                weights.astype("int32") if hasattr(weights, "astype") else weights,
+                dtype=torch.int32, device=self.device).contiguous()
         self.n_img = int(self.data.shape[0])
         self.n_src = int(n_src)
         self.s_super = int(s_super)
@@ -197,29 +253,44 @@ class System:
         base = self.workspace.data_ptr()
         off = (-base) % 256
         h = ctypes.c_void_p()
-        _check(_lib.rtu_system_create(ctypes.byref(self.desc), ctypes.c_void_p(base + off), nbytes,
-                                      ctypes.byref(h)), "rtu_system_create")
+        if on_stream:
+            _check(_lib.rtu_system_create_on(ctypes.byref(self.desc), ctypes.byref(self._host_in),
+                                             ctypes.c_void_p(base + off), nbytes, ctypes.c_void_p(stream.cuda_stream),
+                                             ctypes.byref(h)), "rtu_system_create_on")
+        else:
+            _check(_lib.rtu_system_create(ctypes.byref(self.desc), ctypes.c_void_p(base + off), nbytes,
+                                          ctypes.byref(h)), "rtu_system_create")
         self.handle = h
         self.n_lens = 8 + 5 * self.n_sub
         self.n_ps = N_PS[self.ps_family] + 1
         self.n_knots = self.n_nodes + 2
         self.n_light = int(n_light)
+        self._n_mask = None
+
+    @property
+    def n_mask(self) -> int:
+        """Arc-mask pixels (the centre rays of the eCDFs); counted on first use."""
+        if self._n_mask is None:
+            self._n_mask = int(self.mask.count_nonzero())
+        return self._n_mask
 
     @classmethod
-    def from_mock(cls, m, precision=RTU_F32, n_slots=1, device="cuda", transform=RTU_TRANSFORM_RTU):
+    def from_mock(cls, m, precision=RTU_F32, n_slots=1, device="cuda", transform=RTU_TRANSFORM_RTU, stream=None):
         return cls(m.data, m.mask, m.psf, m.sigma, m.pix, m.s_super, m.n_src, m.src_pitch, m.profile,
                    m.ps_family, m.sub_kind, 0 if m.subs is None else m.subs.shape[0], precision,
                    n_slots=n_slots, device=device, transform=transform,
                    n_light=0 if getattr(m, "light", None) is None else m.light.shape[0],
-                   weights=getattr(m, "weights", None))
+                   weights=getattr(m, "weights", None), stream=stream)
 
     @property
     def n_sites(self) -> int:
         return int(_lib.rtu_n_sites(ctypes.byref(self.desc)))
 
-    def elbo_init(self, priors, fixed, loc, rho, tag: int):
+    def elbo_init(self, priors, fixed, loc, rho, tag: int, stream=None):
         """Set the guide: priors[n_sites] as (kind, space, a, b, c, d), the physical
-        values of the non-site entries, loc/rho over n_sites + n_src^2, stream tag."""
+        values of the non-site entries, loc/rho over n_sites + n_src^2, random-stream
+        tag.  stream=None: synchronous (rtu_elbo_init); else the upload is ordered on
+        that torch stream (rtu_elbo_init_on)."""
         ns = self.n_sites
         if len(priors) != ns:
             raise ValueError(f"{ns} priors expected")
@@ -234,8 +305,13 @@ class System:
                 or rho.size != loc.size:
             raise ValueError("fixed / loc / rho sizes do not match the system")
         dp = ctypes.POINTER(ctypes.c_double)
-        _check(_lib.rtu_elbo_init(self.handle, arr, fixed.ctypes.data_as(dp), loc.ctypes.data_as(dp),
-                                  rho.ctypes.data_as(dp), int(tag) & 0xFFFFFFFF), "rtu_elbo_init")
+        if stream is None:
+            _check(_lib.rtu_elbo_init(self.handle, arr, fixed.ctypes.data_as(dp), loc.ctypes.data_as(dp),
+                                      rho.ctypes.data_as(dp), int(tag) & 0xFFFFFFFF), "rtu_elbo_init")
+        else:
+            _check(_lib.rtu_elbo_init_on(self.handle, arr, fixed.ctypes.data_as(dp), loc.ctypes.data_as(dp),
+                                         rho.ctypes.data_as(dp), int(tag) & 0xFFFFFFFF,
+                                         ctypes.c_void_p(stream.cuda_stream)), "rtu_elbo_init_on")
 
     def elbo_export(self) -> bytes:
         n = _lib.rtu_elbo_state_bytes(self.handle)
@@ -245,6 +321,14 @@ class System:
 
     def elbo_import(self, blob: bytes):
         _check(_lib.rtu_elbo_import(self.handle, blob, len(blob)), "rtu_elbo_import")
+
+    def elbo_grad(self):
+        """(d ELBO / d loc, d ELBO / d rho) of the last rtu_elbo_step, before Adam
+        (numpy arrays; a synchronous copy)."""
+        n = self.n_sites + self.n_src ** 2
+        out = np.zeros(2 * n, dtype=np.float64)
+        _check(_lib.rtu_elbo_grad(self.handle, out.ctypes.data, out.nbytes), "rtu_elbo_grad")
+        return out[:n].copy(), out[n:].copy()
 
     def elbo_state(self):
         """(loc, rho, step) of the guide as numpy arrays (a synchronous copy)."""
@@ -269,7 +353,7 @@ class Binding:
 
     def __init__(self, system: System, lens, latents, ps, slot=0, want_model=False, want_image=False,
                  want_source=False, want_cdf=False, want_hist=False, grads=True, dlogL=None, out=None,
-                 light=None):
+                 light=None, want_selection=False):
         dev, dt = system.device, system.dtype
         self.system = system
         self.slot = slot
@@ -298,6 +382,10 @@ class Binding:
         self.source = torch.empty(n_src, n_src, dtype=dt, device=dev) if want_source else None
         self.cdf = torch.empty(3 + 4 * system.n_knots, dtype=torch.float64, device=dev) if want_cdf else None
         self.ray_hist = torch.empty((n_src - 1) ** 2, dtype=torch.int32, device=dev) if want_hist else None
+        # the order statistics' integer histograms and the traced centre rays (build outputs)
+        self.sel_hist = torch.empty(2, SEL_BINS, dtype=torch.int32, device=dev) if want_selection else None
+        self.centres = (torch.empty(2, system.n_mask, dtype=torch.float64, device=dev)
+                        if want_selection else None)
         if grads:
             # caller-provided output views (e.g. slices of one packed buffer) are used as they are
             self.g_latents = out.get("g_latents", None)
@@ -320,7 +408,8 @@ class Binding:
     def as_struct(self) -> Eval:
         return Eval(self.slot, 0, *[None if t is None else t.data_ptr() for t in (
             self.lens, self.latents, self.ps, self.dlogL, self.stats, self.model, self.image, self.source,
-            self.cdf, self.ray_hist, self.g_latents, self.g_lens, self.g_ps, self.light, self.g_light)])
+            self.cdf, self.ray_hist, self.g_latents, self.g_lens, self.g_ps, self.light, self.g_light,
+            self.sel_hist, self.centres)])
 
 
 def _stream_ptr(stream):
@@ -374,16 +463,42 @@ def rtu_elbo_step(systems, n_samples: int, seed: int, lr: float, elbo_out=None, 
                               _stream_ptr(stream)), "rtu_elbo_step")
 
 
+DF_OPS = {"exp": 0, "log": 1, "sqrt": 2, "div": 3, "mul": 4, "add": 5}
+
+
+def rtu_selftest_df(op: str, x):
+    """The double-float arithmetic of the FP32 path's islands on the device: x a float64
+    CUDA tensor ([n] for exp / log / sqrt, [n, 2] for div / mul / add); returns [n]."""
+    code = DF_OPS[op]
+    x = x.contiguous()
+    n = x.shape[0]
+    if x.dtype != torch.float64 or not x.is_cuda or (code >= 3 and tuple(x.shape) != (n, 2)):
+        raise ValueError("x must be a float64 CUDA tensor of shape [n] or [n, 2]")
+    y = torch.empty(n, dtype=torch.float64, device=x.device)
+    _check(_lib.rtu_selftest_df(code, x.data_ptr(), y.data_ptr(), n, _stream_ptr(None)), "rtu_selftest_df")
+    return y
+
+
 STATIC_MAX_NSRC = 128
 
 
 def rtu_gp_source_static(n_src: int, src_pitch: float, ps_family: int, latents, ps, source, stream=None):
-    """GP source (Eq. 1-3, FP32) without a workspace: latents / source are float32
-    CUDA tensors [n_src, n_src], ps a float64 CUDA tensor.  Allocates no device memory;
-    calls share one static scratch array, so do not overlap them on the GPU."""
+    """GP source without a workspace (the latents filtered by sqrt(P) through FFTs, then
+    the softplus map and the alpha_src power): latents / source are float32 CUDA tensors
+    of n_src^2 elements, ps a float64 CUDA tensor of the family's parameters and
+    alpha_src, all on the current device.  Allocates no device memory; calls share one
+    static scratch array, so do not overlap them on the GPU."""
     for t, dt in ((latents, torch.float32), (source, torch.float32), (ps, torch.float64)):
         if t.dtype != dt or not t.is_cuda or not t.is_contiguous():
             raise ValueError("latents/source must be contiguous float32 CUDA tensors, ps float64")
+        if t.device.index != torch.cuda.current_device():
+            raise ValueError("latents, ps and source must be on the current CUDA device")
+    if ps_family not in N_PS:
+        raise ValueError("unknown ps_family")
+    if latents.numel() != n_src * n_src or source.numel() != n_src * n_src:
+        raise ValueError(f"latents and source must hold n_src^2 = {n_src * n_src} values")
+    if ps.numel() != N_PS[ps_family] + 1:
+        raise ValueError(f"ps must hold {N_PS[ps_family] + 1} values (the family's parameters, alpha_src)")
     _check(_lib.rtu_gp_source_static(int(n_src), float(src_pitch), int(ps_family), latents.data_ptr(),
                                      ps.data_ptr(), source.data_ptr(), _stream_ptr(stream)),
            "rtu_gp_source_static")
@@ -391,7 +506,10 @@ def rtu_gp_source_static(n_src: int, src_pitch: float, ps_family: int, latents, 
 
 class RTUForward(torch.autograd.Function):
     """log L(lens, latents, ps[, light]) of one system; backward runs rtu_adjoint,
-    which recomputes the rays instead of saving them."""
+    which recomputes the rays instead of saving them.  The adjoint reads what the
+    forward left in the system's workspace slot, so when another forward on the same
+    system ran in between (two forwards, then their backwards), backward first runs
+    its own forward again."""
 
     @staticmethod
     def forward(ctx, system: System, lens, latents, ps, light=None):
@@ -400,12 +518,17 @@ class RTUForward(torch.autograd.Function):
                     light=None if light is None else light.detach())
         Batch([b]).forward()
         ctx.binding = b
+        ctx.token = object()
+        system._slot0_owner = ctx.token
         ctx.light_shape = None if light is None else light.shape
         return b.stats[STAT_LOGL].clone()
 
     @staticmethod
     def backward(ctx, g):
         b = ctx.binding
+        if getattr(b.system, "_slot0_owner", None) is not ctx.token:
+            Batch([b]).forward()            # the slot holds another forward's state
+            b.system._slot0_owner = ctx.token
         b.dlogL.copy_(g.reshape(1).to(torch.float64))
         Batch([b]).adjoint()
         g_light = None if ctx.light_shape is None else b.g_light.clone().reshape(ctx.light_shape)

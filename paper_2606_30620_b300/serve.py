@@ -8,8 +8,11 @@ uneven image and grid sizes into one ``rtu_elbo_step`` call (one launch per
 step of the hot path for the whole batch).  Up to ``n_streams`` batches are in
 flight on separate CUDA streams, so requests that arrive while others run
 are admitted as memory and stream slots free up and their work overlaps on
-the device.  A request completes when the CUDA event recorded after its
-batch has been reached; its latency is completion minus arrival time.
+the device.  Admission uploads a system's observation, tables and guide with
+copies ordered on an admission stream that the batches' streams wait for, so
+the host never waits for the device to admit.  A request completes when the
+CUDA event recorded after its batch (and the copy of its ELBO into pinned host
+memory) has been reached; its latency is completion minus arrival time.
 """
 from __future__ import annotations
 
@@ -100,9 +103,12 @@ class Server:
         self.resident: dict[int, Resident] = {}
         self.used = 0
         self.peak_used = 0
-        self.inflight = []        # (event, stream index, [requests], elbo tensor)
+        self.inflight = []        # (event, stream index, [requests], pinned ELBO values)
         self.batches = 0
         self.batch_sizes = []
+        # per stream: the batch's ELBO outputs on the device and their pinned host copy
+        self.out_dev = [torch.empty(max_batch, dtype=torch.float64, device=self.device) for _ in self.streams]
+        self.out_host = [torch.empty(max_batch, dtype=torch.float64, pin_memory=True) for _ in self.streams]
 
     # ---------------------------------------------------------------- admission
     def _admit(self, req: Request, now: float) -> bool:
@@ -117,12 +123,14 @@ class Server:
             self._evict(need)
             if self.used + need > self.budget:
                 return False
+        # the observation in one pinned copy, the library's tables and the guide with
+        # uploads ordered on the admission stream; nothing waits for the device here
+        # (the batch's stream waits for the admission stream before its step)
         with torch.cuda.stream(self.admit_stream):
             s = rtu.System.from_mock(req.mock, precision=self.precision, n_slots=self.n_samples,
-                                     device=self.device)
+                                     device=self.device, stream=self.admit_stream)
             pr, ph, loc, rho = guide_start(req.mock)
-            s.elbo_init(pr, ph, loc, rho, tag=req.system_id)
-        self.admit_stream.synchronize()
+            s.elbo_init(pr, ph, loc, rho, tag=req.system_id, stream=self.admit_stream)
         self.resident[req.system_id] = Resident(s, need, now)
         self.used += need
         self.peak_used = max(self.peak_used, self.used)
@@ -144,13 +152,17 @@ class Server:
     # ----------------------------------------------------------------- batching
     def _launch(self, reqs, k):
         st = self.streams[k]
-        out = torch.empty(len(reqs), dtype=torch.float64, device=self.device)
+        out = self.out_dev[k][:len(reqs)]
+        host = self.out_host[k][:len(reqs)]
         systems = [self.resident[r.system_id].system for r in reqs]
         st.wait_stream(self.admit_stream)
         rtu.rtu_elbo_step(systems, self.n_samples, self.seed, self.lr, out, stream=st)
+        # the ELBO values into pinned host memory behind the step; read once the event is reached
+        with torch.cuda.stream(st):
+            host.copy_(out, non_blocking=True)
         ev = torch.cuda.Event()
         ev.record(st)
-        self.inflight.append((ev, k, reqs, out))
+        self.inflight.append((ev, k, reqs, host))
         self.batches += 1
         self.batch_sizes.append(len(reqs))
 
@@ -163,7 +175,7 @@ class Server:
             if not ev.query():
                 keep.append(item)
                 continue
-            vals = out.cpu().numpy()
+            vals = out.numpy()              # pinned host copy, complete once the event is reached
             for r, v in zip(reqs, vals):
                 r.done_steps += 1
                 r.elbo = float(v)

@@ -13,6 +13,29 @@ def rel_l2(a, b):
     return float(np.linalg.norm(a - b) / (den if den > 0 else 1.0))
 
 
+F64_TOL = 1e-10
+F32_TOL = 1e-5
+
+
+def check(r, prec):
+    """The parity bar on a compare() result: FP64 path 1e-10, FP32 path 1e-5 (relative
+    L2) on log L, chi^2, source, image, model and every gradient; the CDF block (FP64 in
+    both modes) 1e-10; the integer rays-per-cell histogram and the flags bit-exact."""
+    tol = F64_TOL if prec == 1 else F32_TOL
+    assert r["cdf"] < F64_TOL, r
+    assert r["logL"] < tol and r["chi2"] < tol, r
+    for k in ("source", "image", "model"):
+        assert r[k] < tol, (k, r)
+    if "g_latents" in r:
+        assert r["g_latents"] < tol, r
+        assert r["g_ps"] < tol, r
+        assert r["g_lens"] < tol, r
+    if "g_light" in r:
+        assert r["g_light"] < tol, r
+    assert r["hist_diff"] == 0, r
+    assert r["flags"][0] == r["flags"][1], r
+
+
 def run_gpu(m, precision, want_grads=True, n_slots=1, transform=0):
     from paper_2606_30620_b300 import rtu
     sysm = rtu.System.from_mock(m, precision=precision, n_slots=n_slots, transform=transform)
@@ -85,38 +108,3 @@ def compare(g, o):
     if "g_light" in g and "g_light" in o:
         res["g_light"] = rel_l2(g["g_light"], o["g_light"])
     return res
-
-
-def rounding_sensitivity(m, transform, eps, reps=2, seed=0):
-    """Relative change of the oracle's lens gradient when every traced position
-    (centre rays and sub-rays) is moved by +-eps (|beta| + |theta|) -- the size of the
-    terms of beta = theta - alpha(theta) -- on each axis: the spread that rounding at
-    relative level eps alone can cause.  The unsmoothed eCDF splits each
-    ray's gradient between the two observations of its segment by
-    t = (beta - x_k)/(x_{k+1} - x_k), and segments can be narrower than 1e-9 arcsec,
-    so its lens gradient is sensitive at that level (a property of the map, shared by
-    any implementation).  Each trial also moves every lens parameter by +-eps of its
-    size: two implementations round the lens constants (axis ratio, position angle,
-    ...) differently, and that error is the same for every ray, which independent
-    position errors do not cover."""
-    import copy
-    base = run_oracle(m, transform=transform)["g_lens"]
-    trace0 = O.trace
-    rng = np.random.default_rng(seed)
-    worst = 0.0
-    try:
-        for _ in range(reps):
-            mp = copy.copy(m)
-            mp.lens = m.lens * (1.0 + eps * rng.choice([-1.0, 1.0], size=m.lens.shape))
-            def trace_rounded(x, y, *a, **k):
-                bx, by = trace0(x, y, *a, **k)
-                sx = torch.tensor(rng.choice([-1.0, 1.0], size=bx.shape), dtype=bx.dtype)
-                sy = torch.tensor(rng.choice([-1.0, 1.0], size=by.shape), dtype=by.dtype)
-                mx = bx.detach().abs() + x.detach().abs()
-                my = by.detach().abs() + y.detach().abs()
-                return bx + eps * mx * sx, by + eps * my * sy
-            O.trace = trace_rounded
-            worst = max(worst, rel_l2(run_oracle(mp, transform=transform)["g_lens"], base))
-    finally:
-        O.trace = trace0
-    return worst

@@ -39,11 +39,11 @@ def test_binding_structs_match_the_c_layout(tmp_path):
 #include <stddef.h>
 #include "rtu.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(rtu_system_desc), offsetof(rtu_system_desc, weights),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(rtu_system_desc), offsetof(rtu_system_desc, weights),
          offsetof(rtu_system_desc, pix),
          offsetof(rtu_system_desc, data), sizeof(rtu_eval), offsetof(rtu_eval, lens),
          offsetof(rtu_eval, g_ps), offsetof(rtu_eval, ray_hist), offsetof(rtu_eval, light),
-         offsetof(rtu_eval, g_light));
+         offsetof(rtu_eval, g_light), offsetof(rtu_eval, sel_hist), offsetof(rtu_eval, centres));
   return 0;
 }
 """)
@@ -53,7 +53,7 @@ int main(void) {
     want = [ctypes.sizeof(rtu.SystemDesc), rtu.SystemDesc.weights.offset, rtu.SystemDesc.pix.offset,
             rtu.SystemDesc.data.offset,
             ctypes.sizeof(rtu.Eval), rtu.Eval.lens.offset, rtu.Eval.g_ps.offset, rtu.Eval.ray_hist.offset,
-            rtu.Eval.light.offset, rtu.Eval.g_light.offset]
+            rtu.Eval.light.offset, rtu.Eval.g_light.offset, rtu.Eval.sel_hist.offset, rtu.Eval.centres.offset]
     assert got == want
 
 

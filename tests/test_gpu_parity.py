@@ -16,8 +16,8 @@ from tests import gpu_cases as G
 
 pytestmark = pytest.mark.gpu
 
-F64_TOL = 1e-10
-F32_TOL = 1e-5
+F64_TOL = G.F64_TOL
+F32_TOL = G.F32_TOL
 
 
 @pytest.fixture(scope="module")
@@ -28,20 +28,7 @@ def rtu():
     return mod
 
 
-def _check(r, prec):
-    tol = F64_TOL if prec == 1 else F32_TOL
-    assert r["cdf"] < F64_TOL, r
-    assert r["logL"] < tol and r["chi2"] < tol, r
-    for k in ("source", "image", "model"):
-        assert r[k] < tol, (k, r)
-    if "g_latents" in r:
-        assert r["g_latents"] < tol, r
-        assert r["g_ps"] < tol, r
-        assert r["g_lens"] < tol, r
-    if "g_light" in r:
-        assert r["g_light"] < tol, r
-    assert r["hist_diff"] == 0, r
-    assert r["flags"][0] == r["flags"][1], r
+_check = G.check
 
 
 def test_c1_fp64_matches_oracle(rtu):
@@ -125,9 +112,9 @@ def test_core_field_in_a_batch_equals_alone(rtu):
     for a, b in zip(alone, binds):
         assert np.array_equal(a["model"], b.model.cpu().numpy())
         assert np.array_equal(a["stats"], b.stats.cpu().numpy())
-        assert G.rel_l2(b.g_latents.cpu().numpy(), a["g_latents"]) < 1e-6
-        assert G.rel_l2(b.g_lens.cpu().numpy(), a["g_lens"]) < 1e-12
-        assert G.rel_l2(b.g_ps.cpu().numpy(), a["g_ps"]) < 1e-6
+        assert np.array_equal(b.g_latents.cpu().numpy(), a["g_latents"])
+        assert np.array_equal(b.g_lens.cpu().numpy(), a["g_lens"])
+        assert np.array_equal(b.g_ps.cpu().numpy(), a["g_ps"])
 
 
 def test_graph_replay_matches_plain_launches(rtu):
@@ -155,8 +142,8 @@ def test_graph_replay_matches_plain_launches(rtu):
 
     def same(x, y):
         for a, b in zip(x, y):
-            assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
-            assert G.rel_l2(b[2], a[2]) < 1e-6 and G.rel_l2(b[3], a[3]) < 1e-12 and G.rel_l2(b[4], a[4]) < 1e-6
+            for u, v in zip(a, b):
+                assert np.array_equal(u, v)
 
     rtu.graph_replay(False)
     try:
@@ -201,14 +188,13 @@ def test_graph_replay_cache_eviction(rtu):
         for r, p in zip(runs, plain):
             got = step(r)
             assert np.array_equal(got[0], p[0]) and np.array_equal(got[1], p[1])
-            assert G.rel_l2(got[2], p[2]) < 1e-12
+            assert np.array_equal(got[2], p[2])
 
 
 def test_batch_equals_alone(rtu):
-    # every step is per evaluation, so a batch gives each system its own result;
-    # the per-cell source-gradient sums run over counting-sorted records whose
-    # order inside a cell follows integer-atomic timing, so the latent gradient is
-    # reproducible to rounding of those sums (FP32 lane sums: ~1e-7)
+    # every step is per evaluation and every sum has a fixed order (the per-cell
+    # source-gradient sums are exact integer sums), so a batch gives each system its
+    # own result bit for bit, call after call
     mocks = [I.config_c2(1020 + k, n_img=64 + 16 * k, s=2 + (k % 3), n_src=(32, 48, 64)[k % 3]) for k in range(5)]
     alone = []
     for m in mocks:
@@ -227,9 +213,9 @@ def test_batch_equals_alone(rtu):
         for a, b in zip(alone, binds):
             assert np.array_equal(a["model"], b.model.cpu().numpy())
             assert np.array_equal(a["stats"], b.stats.cpu().numpy())
-            assert G.rel_l2(b.g_latents.cpu().numpy(), a["g_latents"]) < 1e-6
-            assert G.rel_l2(b.g_lens.cpu().numpy(), a["g_lens"]) < 1e-12
-            assert G.rel_l2(b.g_ps.cpu().numpy(), a["g_ps"]) < 1e-6
+            assert np.array_equal(b.g_latents.cpu().numpy(), a["g_latents"])
+            assert np.array_equal(b.g_lens.cpu().numpy(), a["g_lens"])
+            assert np.array_equal(b.g_ps.cpu().numpy(), a["g_ps"])
 
 
 def test_upstream_scale_and_autograd_function(rtu):
@@ -318,7 +304,7 @@ def test_lens_light_is_required_and_autograd_carries_it(rtu):
     assert abs(float(logL) - o["logL"]) < F64_TOL * abs(o["logL"])
 
 
-# ------------------------------------------------------- weighted RTU grid (Sec. 5)
+# ------------------------------------------------------- weighted RTU grid (Sec. 6.3)
 @pytest.mark.parametrize("kw,cap", [(dict(seed=51), 7), (dict(seed=52, sub_kind=I.SUB_NFW, n_sub=2), 30),
                                     (dict(seed=53, n_img=17, s=3, n_src=12, psf_k=5), 3)])
 def test_weighted_grid_fp64_matches_oracle(rtu, kw, cap):
@@ -345,17 +331,20 @@ def test_weighted_grid_rejects_zero_weights_on_the_mask(rtu):
 
 
 # ------------------------------------------- unsmoothed linear eCDF (App. C, first paragraph)
-# Position rounding of the two paths: FP64 positions a few units of 2^-53; the FP32
-# path's adjoint positions for this map are double-float (about 2^-48 with the series'
-# own rounding).  The lens-gradient tolerance is the stated one or ten times the
-# oracle's own spread under position perturbations of that size, whichever is larger.
-LIN_POS_EPS = {1: 4.0 * 2.0 ** -53, 0: 4e-14}
+# The lens gradient of the unsmoothed map splits each ray's gradient between the two
+# observations of its segment by t = (beta - x_k)/(x_{k+1} - x_k); a rounding error
+# delta of the positions moves t by delta / h for a segment of width h, and segments
+# as narrow as 1.2e-9 arcsec occur on these mocks (median 1.7e-4).  With the FP64
+# positions' delta ~ 4 x 2^-53 x |beta| (|beta| ~ 1 arcsec) the worst ray's share
+# moves by ~4e-7 relative, diluted over the other rays: a fixed FP64 tolerance of 1e-7
+# for this one output.  The FP32 path computes these positions in double-float
+# (delta ~ 2^-46), ~3e-6 for the worst ray: its stated tolerance 1e-5 holds as it is.
+LIN_F64_LENS_TOL = 1e-7
 
 
 def _check_linear(m, prec, g):
     r = G.compare(g, G.run_oracle(m, transform=2))
-    base = F64_TOL if prec == 1 else F32_TOL
-    tol = max(base, 10.0 * G.rounding_sensitivity(m, 2, LIN_POS_EPS[prec]))
+    tol = LIN_F64_LENS_TOL if prec == 1 else F32_TOL
     assert r["g_lens"] < tol, (r["g_lens"], tol)
     r["g_lens"] = 0.0
     _check(r, prec)
@@ -378,8 +367,7 @@ def test_linear_ecdf_grid_c2_matches_oracle(rtu, prec):
     # 200 x 200 pixels, 4 x 4 sub-rays: every order statistic of ~10^4 centre rays
     m = I.config_c2(1006)
     g, _, _ = G.run_gpu(m, prec, transform=rtu.RTU_TRANSFORM_LINEAR)
-    tol = _check_linear(m, prec, g)
-    assert tol < 1e-4      # the derived tolerance stays far below the float path's own error before the fix
+    _check_linear(m, prec, g)
 
 
 def test_mixed_transforms_in_one_batch(rtu):
@@ -400,8 +388,7 @@ def test_mixed_transforms_in_one_batch(rtu):
         assert abs(b.stats.cpu().numpy()[0] - o["logL"]) < F64_TOL * abs(o["logL"])
         assert G.rel_l2(b.model.cpu().numpy(), o["model"]) < F64_TOL
         assert np.array_equal(b.ray_hist.cpu().numpy(), o["hist"])
-        tol = F64_TOL if kind != rtu.RTU_TRANSFORM_LINEAR else max(
-            F64_TOL, 10.0 * G.rounding_sensitivity(m, kind, LIN_POS_EPS[1]))
+        tol = F64_TOL if kind != rtu.RTU_TRANSFORM_LINEAR else LIN_F64_LENS_TOL
         assert G.rel_l2(b.g_lens.cpu().numpy(), o["g_lens"]) < tol
         assert G.rel_l2(b.g_latents.cpu().numpy(), o["g_latents"]) < F64_TOL
 
@@ -432,3 +419,55 @@ def test_profile_timeline_covers_every_launch(rtu):
     rtu.profile_enable(False)
     rep = rtu.profile_report()
     assert sum(c for c, _ in rep.values()) == len(tl)
+
+
+# ------------------------------------------- the fit's monotonicity guard (App. C iv)
+@pytest.mark.parametrize("prec,kw", [(1, dict(seed=4500)), (1, dict(seed=4502, profile=I.PROFILE_SIE)),
+                                     (0, dict(seed=4501)), (0, dict(seed=4503, n_img=200, s=4, n_src=64))])
+def test_nonmonotone_fit_repair_matches_oracle(rtu, prec, kw):
+    # two disjoint arc-mask disks: a bimodal marginal whose degree-21 interpolant falls
+    # between nodes, so both sides take the repair branch (flags non-zero on both).
+    # The repaired slopes (1e6 / span where p' was floored) make the map there a million
+    # times steeper than elsewhere, which float ray positions cannot follow: the FP32
+    # path is held to the knots, slopes and flags (computed in FP64 in both modes), the
+    # FP64 path to everything.
+    m = I.config_bimodal(**kw)
+    g, _, _ = G.run_gpu(m, prec)
+    r = G.compare(g, G.run_oracle(m))
+    assert r["flags"][1] & rtu.W_NONMONOTONE, r
+    if prec == 1:
+        _check(r, prec)
+    else:
+        assert r["cdf"] < F64_TOL and r["flags"][0] == r["flags"][1], r
+
+
+# ------------------------------------------- the largest source grid (256^2)
+@pytest.mark.parametrize("prec", [1, 0])
+def test_n_src_256_matches_oracle(rtu, prec):
+    # 256^2 grid: read by the render kernels from global memory (it exceeds the
+    # shared-memory staging limit in both precisions)
+    m = I.config_c2(1090, n_img=128, s=2, n_src=256)
+    g, _, _ = G.run_gpu(m, prec)
+    _check(G.compare(g, G.run_oracle(m)), prec)
+
+
+def test_autograd_two_forwards_then_two_backwards(rtu):
+    # both forwards use slot 0 of one system; each backward still gets its own
+    # forward's gradient
+    m = I.config_tiny(seed=23, n_img=20, n_src=12)
+    s = rtu.System.from_mock(m, precision=rtu.RTU_F64)
+    lens = torch.tensor(m.lens, device="cuda", requires_grad=True)
+    lat1 = torch.tensor(m.latents, device="cuda", requires_grad=True)
+    lat2 = torch.tensor(0.5 * m.latents, device="cuda", requires_grad=True)
+    ps = torch.tensor(m.ps, device="cuda")
+    L1 = rtu.log_likelihood(s, lens, lat1, ps)
+    L2 = rtu.log_likelihood(s, lens, lat2, ps)
+    L1.backward()
+    g1 = lat1.grad.cpu().numpy().copy()
+    L2.backward()
+    o1 = G.run_oracle(m)
+    m2 = I.config_tiny(seed=23, n_img=20, n_src=12)
+    m2.latents = 0.5 * m.latents
+    o2 = G.run_oracle(m2)
+    assert G.rel_l2(g1, o1["g_latents"]) < F64_TOL
+    assert G.rel_l2(lat2.grad.cpu().numpy(), o2["g_latents"]) < F64_TOL

@@ -1,6 +1,7 @@
 """Continuous-batching server: every request completes, each system's result is
-the same alone and in the mix (within the FP32 tolerance), admission respects
-the HBM budget, and multi-step requests keep their state on the device."""
+the same alone and in the mix (bit for bit: every sum of a step is per system and
+in a fixed order), admission respects the HBM budget, and multi-step requests keep
+their state on the device."""
 import numpy as np
 import pytest
 import torch
@@ -39,7 +40,7 @@ def test_results_alone_equal_results_in_the_mix(serve):
     alone = small_stream(serve, 24)
     serve.serve_plain(alone, n_samples=1, lr=1e-3)
     for a, b in zip(reqs, alone):
-        assert abs(a.elbo - b.elbo) <= 1e-5 * abs(b.elbo), (a.rid, a.elbo, b.elbo)
+        assert a.elbo == b.elbo, (a.rid, a.elbo, b.elbo)
     assert out["mean_batch"] >= 1.0
 
 
