@@ -393,6 +393,10 @@ def run_ours(args):
             "g_lens": b0.g_lens.cpu().numpy(), "g_ps": b0.g_ps.cpu().numpy()}
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
 
+    # ---- the autotuner: the benchmark bucket timed live with the default launch shapes
+    # and with the cached tuned ones; the serving buckets' speed-ups as cached
+    tune_info = run_autotune_report(systems, step, flush, stream) if not args.no_autotune else None
+
     clocks = clk.summary()
     variants = run_variants(args, dev, mocks, flush, stream) if not args.no_variants else None
     serving = run_serving(args, dev) if args.serve_n > 0 else None
@@ -448,6 +452,7 @@ def run_ours(args):
         "cpu_baseline": {"value": cpu_v, "unit": "evals/s", "cores": cores, "kind": "oracle",
                          "sample": f"{cpu_n} of the {n} mocks ({cpu_dt:.1f} s): FP64 oracle forward + autograd gradient"},
         "rel_err": rel_err,
+        "autotune": tune_info,
         "clocks": {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
         "variants": variants,
         "serving": serving,
@@ -513,6 +518,30 @@ def run_variants(args, dev, mocks, flush, stream):
                      "kernels_ms": {k: kern[k][1] / n_prof for k in VARIANT_KERNELS if k in kern}}
         del batch, systems
     return out
+
+
+def run_autotune_report(systems, step, flush, stream, steps=50):
+    from paper_2606_30620_b300 import autotune
+    cached = autotune.lookup(systems[0].n_img, systems[0].n_src, systems[0].s_super, systems[0].precision)
+
+    def timed(tuning):
+        for s in systems:
+            s.tune(tuning)
+        return autotune._time(step, flush, steps)
+
+    ms_default = timed(autotune.DEFAULT)
+    ms_tuned = timed(cached) if cached is not None else ms_default
+    for s in systems:                       # leave the systems as the timed region ran them
+        s.tune(cached if cached is not None else autotune.DEFAULT)
+    entries = autotune.load().get(autotune.gpu_name(), {})
+    sp = [v["ms_default"] / v["ms_tuned"] for k, v in entries.items() if v.get("step", "").startswith("ELBO")]
+    return {"cache": "paper_2606_30620_b300/tuning.json", "gpu": autotune.gpu_name(), "buckets": len(entries),
+            "bench_bucket": {"tuning": cached, "ms_default": ms_default, "ms_tuned": ms_tuned,
+                             "note": "batched forward + adjoint of the 32 mocks, live (median of 50 steps)"},
+            "serving_buckets": None if not sp else {
+                "n": len(sp), "speedup_median": float(np.median(sp)), "speedup_min": float(min(sp)),
+                "speedup_max": float(max(sp)),
+                "note": "one batched ELBO step of 16 systems per bucket, default / tuned, as measured by the tuner"}}
 
 
 def run_serving(args, dev):
@@ -589,6 +618,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-variants", action="store_true", help="skip the timing of the grid / light variants")
     ap.add_argument("--serve-n", type=int, default=4096, help="systems in the serving stream (0 = skip)")
+    ap.add_argument("--no-autotune", action="store_true", help="skip the tuned / default launch-shape timing")
     ap.add_argument("--timeline", action="store_true",
                     help="print the per-launch timeline of one traced step instead of the bench line")
     args = ap.parse_args()

@@ -69,6 +69,8 @@ typedef int32_t rtu_status;
 #define RTU_W_SELECT        2   /* order-statistic selection unresolved (not raised: the
                                    radix refinement resolves every rank within 8 levels) */
 #define RTU_W_TIMEOUT       4   /* a bounded wait on an async copy gave up */
+#define RTU_W_RANGE         8   /* the unsmoothed transform's exact position-gradient sums met a
+                                   term of magnitude >= 2^40 (left out; the gradient is wrong) */
 
 enum { RTU_F32 = 0, RTU_F64 = 1 };
 enum { RTU_SIE = 0, RTU_EPL = 1 };
@@ -193,6 +195,21 @@ typedef struct {
  * desc's device buffers must hold their contents by the time those calls run. */
 rtu_status rtu_system_create_on(const rtu_system_desc* desc, const rtu_host_inputs* host, void* workspace,
                                 size_t ws_bytes, void* stream, rtu_system** out);
+/* Launch shapes of a system's kernels that may be tuned per problem size (they
+ * change the work split only: results agree to the rounding of the partial sums, and
+ * a given tuning gives the same bits from run to run):
+ *   adj_div    render adjoint CTAs per evaluation = ceil(rays / (adj_div x 2048))
+ *              (default 4: one chunk per CTA when a quarter of the rays are in the grid)
+ *   near_ctas  CTAs per evaluation of the FP32 path's near-core adjoint pass (default 4)
+ *   edge_ctas  CTAs per evaluation of the FP32 path's near-edge double pass (default 16)
+ * rtu_system_tune sets them for later calls (ranges [1, 64], [1, 16], [1, 256];
+ * RTU_E_ARG otherwise); the workspace holds any value in range. */
+typedef struct {
+    int32_t adj_div;
+    int32_t near_ctas;
+    int32_t edge_ctas;
+} rtu_tuning;
+rtu_status rtu_system_tune(rtu_system* sys, const rtu_tuning* tuning);
 rtu_status rtu_system_destroy(rtu_system* sys);
 
 /* S1-S5 (App. C steps i-iv, Sec. 2.2): trace the arc-mask pixel centres through

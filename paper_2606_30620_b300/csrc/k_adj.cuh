@@ -365,8 +365,8 @@ __global__ void __launch_bounds__(CTA_C) k_lin_centre_adj(const __grid_constant_
     double o8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     double xd = 0.0, yd = 0.0, gx = 0.0, gy = 0.0;
     if (k < N) {
-        gx = E.gk[E.lrank[k]];
-        gy = E.gk[N + E.lrank[N + k]];
+        gx = fix128_value(E.gk + 2 * (size_t)E.lrank[k]);
+        gy = fix128_value(E.gk + 2 * ((size_t)N + E.lrank[N + k]));
         const int pix = E.centre_idx[k];
         const int pj = pix / E.n_img, pi = pix - pj * E.n_img;
         const double c = 0.5 * (E.n_img - 1);

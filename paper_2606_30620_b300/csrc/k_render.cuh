@@ -93,6 +93,23 @@ __device__ __forceinline__ int cdf_interval(const T* X, int K, T z) {
     return lo;
 }
 
+// the same from a table of the interval at IV_BINS equal bins over [X_0, X_{K-1}]
+// (iv[b] = the interval holding the bin's left edge, origin o, scale sc = IV_BINS /
+// (X_{K-1} - X_0)): the table's guess is moved up or down to the interval holding z,
+// so the result is the binary search's; the knots inside one bin bound the steps
+constexpr int IV_BINS = 64;
+template <typename T>
+__device__ __forceinline__ int cdf_interval_lut(const T* X, int K, T z, const unsigned char* iv, T o, T sc) {
+    if (z < X[0]) return -1;
+    if (z >= X[K - 1]) return K - 1;
+    int b = (int)((z - o) * sc);
+    b = b < 0 ? 0 : (b > IV_BINS - 1 ? IV_BINS - 1 : b);
+    int j = iv[b];
+    while (j < K - 2 && X[j + 1] <= z) ++j;
+    while (j > 0 && X[j] > z) --j;
+    return j;
+}
+
 template <typename T>
 __device__ __forceinline__ T cdf_value(const T* X, const T* U, const T* d, int K, int j, T z) {
     if (j < 0) return U[0] + d[0] * (z - X[0]);
@@ -325,6 +342,8 @@ struct RenderShared {
     PixGeom<T> G;              // sub-ray positions
     T ih[2 * (MAXM + 2)];      // 1/(X_{j+1} - X_j) per knot interval, axis-major
     UDiv dv_s2, dv_n, dv_s, dv_nc;   // dividers by s^2, n_img, s, n_src - 1
+    unsigned char iv[2][IV_BINS];    // per axis: the knot interval at each table bin's left edge
+    T ivo[2], ivs[2];                // per axis: the table's origin X_0 and scale IV_BINS/(X_{K-1} - X_0)
 };
 
 // Source grids up to GRID_STAGE_MAX bytes are staged in shared memory; larger ones
@@ -352,6 +371,23 @@ __device__ __forceinline__ void render_setup(const EvalArgs& E, RenderShared<T>&
                 const T x1 = sizeof(T) == 4 ? (T)E.trf[at + 1] : (T)E.trd[at + 1];
                 sh.ih[i] = T(1) / (x1 - x0);
             }
+        }
+    }
+    // the interval table: one thread per (axis, bin), a scan of the axis's knots
+    {
+        const int K = E.n_nodes + 2;
+        for (int i = threadIdx.x; i < 2 * IV_BINS; i += blockDim.x) {
+            const int a = i / IV_BINS, b = i - a * IV_BINS;
+            auto X = [&](int j) {
+                const int at = TR_HDR + a * K + j;
+                return sizeof(T) == 4 ? (T)E.trf[at] : (T)E.trd[at];
+            };
+            const T o = X(0), sc = T(IV_BINS) / (X(K - 1) - o);
+            const T edge = o + T(b) / sc;
+            int j = 0;
+            while (j < K - 2 && X(j + 1) <= edge) ++j;
+            sh.iv[a][b] = (unsigned char)j;
+            if (b == 0) { sh.ivo[a] = o; sh.ivs[a] = sc; }
         }
     }
     pixgeom_setup<T>(sh.G, E.pix, E.n_img, E.s);
@@ -506,8 +542,10 @@ __global__ void __launch_bounds__(CTA_R, sizeof(T) == 4 && !LIN ? 8 : 6) k_rende
                     my = (float)(T(n - 1) * sy * T(1e-6) * (T(1) + r_abs(zy) + r_abs(y)));
                 }
             } else {
-                yx = cdf_value_r<T>(Xx, sh.U, dx_, sh.ih, K, cdf_interval<T>(Xx, K, zx), zx);
-                yy = cdf_value_r<T>(Xy, sh.U, dy_, sh.ih + K, K, cdf_interval<T>(Xy, K, zy), zy);
+                const int jx = cdf_interval_lut<T>(Xx, K, zx, sh.iv[0], sh.ivo[0], sh.ivs[0]);
+                const int jy = cdf_interval_lut<T>(Xy, K, zy, sh.iv[1], sh.ivo[1], sh.ivs[1]);
+                yx = cdf_value_r<T>(Xx, sh.U, dx_, sh.ih, K, jx, zx);
+                yy = cdf_value_r<T>(Xy, sh.U, dy_, sh.ih + K, K, jy, zy);
             }
             if (sizeof(T) == 4 && (lin ? near_edge_m((float)(yx * T(n - 1)), (float)(yy * T(n - 1)), n, mx, my)
                                        : near_edge((float)(yx * T(n - 1)), (float)(yy * T(n - 1)), n))) {
@@ -579,7 +617,7 @@ __global__ void __launch_bounds__(CTA_R, sizeof(T) == 4 && !LIN ? 8 : 6) k_rende
 
 // the deferred near-edge rays of the float path, traced and decided in double
 constexpr int EDGE_NT = 128;
-constexpr int EDGE_CTAS = 16;
+constexpr int EDGE_CTAS = 16;      // CTAs per evaluation (default; E.n_edge when tuned)
 __global__ void __launch_bounds__(EDGE_NT) k_render_edge(const __grid_constant__ Batch B) {
     const int ev = find_eval(B, blockIdx.x);
     const EvalArgs& E = B.e[ev];
@@ -603,7 +641,7 @@ __global__ void __launch_bounds__(EDGE_NT) k_render_edge(const __grid_constant__
     const float* grid = reinterpret_cast<const float*>(E.src);
     float* img = reinterpret_cast<float*>(E.img);
     const int cap = 32 * s2;                 // staged entries per render warp
-    for (int k = tile * EDGE_NT + threadIdx.x; k < cnt; k += EDGE_CTAS * EDGE_NT) {
+    for (int k = tile * EDGE_NT + threadIdx.x; k < cnt; k += E.n_edge * EDGE_NT) {
         const int at = reinterpret_cast<const int*>(E.rec)[k];     // staging position
         const int e0 = E.cell[at];
         const int local = e0 & ((1 << STG_SHIFT) - 1);
@@ -646,7 +684,7 @@ __global__ void __launch_bounds__(EDGE_NT) k_render_edge(const __grid_constant__
     }
 }
 
-// exclusive scan of the per-cell ray counts into offsets; cursors zeroed
+// exclusive scan of the per-cell ray counts into offsets
 constexpr int SCAN_NT = 1024;
 
 // in-place exclusive scans of a[0..n) and b[0..n) by one CTA of SCAN_NT threads
@@ -715,7 +753,7 @@ __global__ void __launch_bounds__(SCAN_NT) k_scan_cells(const __grid_constant__ 
     int* off = E.ccount + nc;              // counts [0, ncell), offsets [ncell, 2 ncell + 1)
     for (int i = 0; i < per; ++i) {
         int c = tid * per + i;
-        if (c < nc) { off[c] = base; base += E.ccount[c]; E.cursor[c] = 0; }
+        if (c < nc) { off[c] = base; base += E.ccount[c]; }
     }
     if (tid == SCAN_NT - 1) off[nc] = base;
 }
@@ -725,6 +763,9 @@ __global__ void __launch_bounds__(SCAN_NT) k_scan_cells(const __grid_constant__ 
 __global__ void __launch_bounds__(SCAN_NT) k_scan_warps(const __grid_constant__ Batch B) {
     const EvalArgs& E = B.e[blockIdx.x];
     __shared__ int wtot[2 * (SCAN_NT / 32)];
+    // the cell cursors the compaction ranks the rays with (before it, on its stream)
+    const int nc = (E.n_src - 1) * (E.n_src - 1);
+    for (int c = threadIdx.x; c < nc; c += SCAN_NT) E.cursor[c] = 0;
     block_exclusive_scan2(E.useg, E.nseg, E.n_cta_r * (CTA_R / 32), wtot);
 }
 
@@ -747,7 +788,7 @@ __global__ void __launch_bounds__(CMP_NT) k_compact(const __grid_constant__ Batc
     if (E.transform == RTU_TRANSFORM_LINEAR) {
         // the unsmoothed eCDF's position gradients, accumulated by k_render_adj
         const int nt = (nu + CMP_NT / 32 - 1) / (CMP_NT / 32);
-        for (int i = tile * CMP_NT + threadIdx.x; i < 2 * E.n_mask; i += nt * CMP_NT) E.gk[i] = 0.0;
+        for (int i = tile * CMP_NT + threadIdx.x; i < 4 * E.n_mask; i += nt * CMP_NT) E.gk[i] = 0ull;
     }
     if (u >= nu) return;
     const int cap = 32 * E.s * E.s;
@@ -778,6 +819,20 @@ __global__ void __launch_bounds__(CMP_NT) k_compact(const __grid_constant__ Batc
                 E.kray[o + i] = cell >= 0 ? staged_ray_id(E.n_img, E.s * E.s, u, e & ((1 << STG_SHIFT) - 1)) : -1;
                 E.kcell[o + i] = nr && cell >= 0 ? -2 - cell : cell;
             }
+            {
+                // the ray's rank inside its cell (the counting sort's slot, any order: the
+                // cell sums are exact integer sums): one integer atomic per group of
+                // lanes sharing the cell, ranks by lane order
+                const unsigned act = __ballot_sync(0xffffffffu, cell >= 0);
+                if (cell >= 0) {
+                    const unsigned grp = __match_any_sync(act, cell);
+                    const int leader = __ffs(grp) - 1;
+                    int b = 0;
+                    if (lane == leader) b = atomicAdd(E.cursor + cell, __popc(grp));
+                    b = __shfl_sync(grp, b, leader);
+                    E.krank[o + i] = b + __popc(grp & ((1u << lane) - 1u));
+                }
+            }
             // every flagged entry keeps its list slot (counted by the render); one
             // that the double pass found outside the grid lists -1
             const unsigned bn = __ballot_sync(0xffffffffu, nr);
@@ -794,8 +849,8 @@ __global__ void __launch_bounds__(CMP_NT) k_compact(const __grid_constant__ Batc
 // series sums) and differentiated analytically; its cell comes from the forward
 // pass.  Writes one counting-sorted record per ray and fixed-order per-CTA
 // partial sums of the lens, standardisation and spline-knot gradients (for the
-// unsmoothed eCDF: double atomics into the gradients of the sorted positions, so
-// their summation order varies between runs).
+// unsmoothed eCDF: exact 128-bit fixed-point sums into the gradients of the sorted
+// positions).
 // The float path splits the rays in two launches that may run concurrently: the
 // main one (NEAR false) in float, leaving out the near-core rays the forward traced
 // in double, and a small one (NEAR true, NEAR_CTAS CTAs per evaluation) over those
@@ -828,7 +883,7 @@ __global__ void __launch_bounds__(CTA_R, NEAR ? 1 : (sizeof(T) == 4 && !LIN ? 6 
         const int nu_ = E.n_cta_r * (CTA_R / 32);
         const int tot_ = max(0, min(E.useg[nu_], E.n_img * E.n_img * E.s * E.s));
         const int cnt_ = max(0, min(E.nseg[nu_], tot_));
-        const int per_ = max(1, (cnt_ + NEAR_CTAS * CTA_R - 1) / (NEAR_CTAS * CTA_R));
+        const int per_ = max(1, (cnt_ + E.n_near * CTA_R - 1) / (E.n_near * CTA_R));
         if (tile * CTA_R * per_ >= cnt_) {
             double* o0 = E.apart + E.n_cta_adj + tile;
             const int nc0 = NACC_FIX + 4 * K + 5 * (E.sub_kind ? E.n_sub : 0);
@@ -868,7 +923,7 @@ __global__ void __launch_bounds__(CTA_R, NEAR ? 1 : (sizeof(T) == 4 && !LIN ? 6 
     const int total = max(0, min(E.useg[nu], n_rays));
     // rays of this pass: all adjoint positions, or the near-core list
     const int count = NEAR ? max(0, min(E.nseg[nu], total)) : total;
-    const int nstride = NEAR ? NEAR_CTAS : E.n_cta_adj;
+    const int nstride = NEAR ? E.n_near : E.n_cta_adj;
     const int ncell = nc * nc;
     const T mux = sh.trs[0], muy = sh.trs[1], isg = T(1) / sh.trs[2];
     const T* Xa[2] = {sh.trs + TR_HDR, sh.trs + TR_HDR + K};
@@ -969,20 +1024,8 @@ __global__ void __launch_bounds__(CTA_R, NEAR ? 1 : (sizeof(T) == 4 && !LIN ? 6 
                 }
                 if (cell >= ncell || ray < 0 || ray >= n_rays) cell = -1;
             }
-            {
-                // the ray's record slot in the counting sort by cell: one integer
-                // atomic per group of lanes sharing the cell, ranks by lane order
-                // (used only at the record store, so its latency overlaps the ray)
-                const unsigned act = __ballot_sync(0xffffffffu, cell >= 0);
-                if (cell >= 0) {
-                    const unsigned grp = __match_any_sync(act, cell);
-                    const int leader = __ffs(grp) - 1;
-                    int b = 0;
-                    if (lane == leader) b = atomicAdd(E.cursor + cell, __popc(grp));
-                    b = __shfl_sync(grp, b, leader);
-                    slot = off[cell] + b + __popc(grp & ((1u << lane) - 1u));
-                }
-            }
+            // the ray's record slot in the counting sort by cell (rank from the compaction)
+            if (cell >= 0) slot = off[cell] + E.krank[k];
             T gb0 = T(0), gb1 = T(0);
             if (cell >= 0) {
                 const int pixel = (int)udiv((uint32_t)ray, sh.dv_s2), q = ray - pixel * s2;
@@ -1050,7 +1093,7 @@ __global__ void __launch_bounds__(CTA_R, NEAR ? 1 : (sizeof(T) == 4 && !LIN ? 6 
                     }
                 } else {
                     for (int a = 0; a < 2; ++a) {
-                        jn[a] = cdf_interval<T>(Xa[a], K, z[a]);
+                        jn[a] = cdf_interval_lut<T>(Xa[a], K, z[a], sh.iv[a], sh.ivo[a], sh.ivs[a]);
                         yv[a] = cdf_grad<T>(Xa[a], sh.U, Da[a], sh.ih + a * K, K, jn[a], z[a], dz[a], pn[a][0], pn[a][1],
                                             pn[a][2], pn[a][3]);
                     }
@@ -1086,14 +1129,15 @@ __global__ void __launch_bounds__(CTA_R, NEAR ? 1 : (sizeof(T) == 4 && !LIN ? 6 
                 for (int a = 0; a < 2; ++a)
                     for (int c = 0; c < 4; ++c) pn[a][c] *= gy[a];
                 if constexpr (lin) {
-                    // the two observations of the ray's segment, per axis: double
-                    // atomics into d logL / d (sorted position)
+                    // the two observations of the ray's segment, per axis: exact
+                    // fixed-point sums into d logL / d (sorted position), the same bits
+                    // whatever the order of the rays
                     for (int a = 0; a < 2; ++a) {
                         const double ga = (double)gy[a];
                         if (ga == 0.0 || (pk[a][0] == 0.0 && pk[a][1] == 0.0)) continue;
-                        double* g = E.gk + (size_t)a * E.n_mask + ks[a];
-                        atomicAdd(g, ga * pk[a][0]);
-                        atomicAdd(g + 1, ga * pk[a][1]);
+                        unsigned long long* g = E.gk + 2 * ((size_t)a * E.n_mask + ks[a]);
+                        fix128_add(g, ga * pk[a][0], E.flags);
+                        fix128_add(g + 2, ga * pk[a][1], E.flags);
                     }
                 }
                 have = !lin;

@@ -89,7 +89,7 @@ Sizes sizes_of(const rtu_system_desc& d) {
     // the adjoint's grid-stride CTAs: one chunk each when a quarter of the rays is in the
     // grid (c2: 79 CTAs per system; measured against an eighth, 0.289 vs 0.300 ms, and a
     // sixteenth or a half, both slower)
-    z.n_cta_adj = std::max(1, (z.n_rays + 4 * CTA_R * ADJ_RPT - 1) / (4 * CTA_R * ADJ_RPT));
+    z.n_cta_adj = std::max(1, (z.n_rays + ADJ_DIV * CTA_R * ADJ_RPT - 1) / (ADJ_DIV * CTA_R * ADJ_RPT));
     const int nsub = d.sub_kind ? d.n_sub : 0;
     z.nacc = NACC_FIX + 4 * z.K + 5 * nsub;
     z.nl = 8 + 5 * nsub;
@@ -137,7 +137,10 @@ size_t slot_layout(const rtu_system_desc& d, char* base, EvalArgs* e) {
     p = take((size_t)z.ncell * 4);                    if (e) e->cursor = (int*)p;
     p = take((size_t)z.n_rays * 4 * z.tb);            if (e) e->rec = p;
     p = take((size_t)z.ncell * 4 * 2 * z.tb);         if (e) e->corner = p;
-    p = take((size_t)std::max(z.n_cta_r, z.n_cta_adj + NEAR_CTAS) * z.nacc * 8); if (e) e->apart = (double*)p;
+    // partial rows for the largest tunable adjoint split (one CTA per CTA_R ADJ_RPT rays)
+    // and near-core pass
+    const int adj_max = std::max(1, (z.n_rays + CTA_R * ADJ_RPT - 1) / (CTA_R * ADJ_RPT));
+    p = take((size_t)std::max(z.n_cta_r, adj_max + NEAR_CTAS_MAX) * z.nacc * 8); if (e) e->apart = (double*)p;
     p = take(16);                                     if (e) e->flags = (int*)p;
     p = take(8);                                      if (e) e->gmax = (unsigned long long*)p;
     p = take(LENSK_BYTES);                            if (e) e->lensk = p;
@@ -152,6 +155,7 @@ size_t slot_layout(const rtu_system_desc& d, char* base, EvalArgs* e) {
     p = take((size_t)z.n_rays * 4);                   if (e) e->nlist = (int*)p;
     p = take((size_t)z.n_rays * 4);                   if (e) e->kray = (int*)p;
     p = take((size_t)z.n_rays * 4);                   if (e) e->kcell = (int*)p;
+    p = take((size_t)z.n_rays * 4);                   if (e) e->krank = (int*)p;
     p = take((size_t)z.n_rays * 2 * z.tb);            if (e) e->gbuf = p;
     p = take((size_t)light_ctas(d.n_img) * 6 * std::max(1, d.n_light) * 8); if (e) e->lpartl = (double*)p;
     if (d.transform == RTU_TRANSFORM_LINEAR) {
@@ -160,7 +164,7 @@ size_t slot_layout(const rtu_system_desc& d, char* base, EvalArgs* e) {
         p = take((size_t)2 * z.nm_max * 4);           if (e) e->lidx = (int*)p;
         p = take((size_t)2 * z.nm_max * 4);           if (e) e->lrank = (int*)p;
         p = take((size_t)2 * z.nm_max * 8);           if (e) e->lkf = (float*)p;
-        p = take((size_t)2 * z.nm_max * 8);           if (e) e->gk = (double*)p;
+        p = take((size_t)2 * z.nm_max * 16);          if (e) e->gk = (unsigned long long*)p;
     }
     return o;
 }
@@ -334,6 +338,9 @@ struct rtu_system {
     double* cheb;
     double* psf_uv;               // factors of a rank-1 PSF, or null
     std::vector<EvalArgs> slot;   // workspace pointers of each slot
+    int adj_div = ADJ_DIV;        // launch shapes (rtu_system_tune)
+    int n_near = NEAR_CTAS;
+    int n_edge = EDGE_CTAS;
     std::vector<SampleBufs> sbuf; // guide-sample buffers of each slot
     ElboState st;
     bool elbo_ready = false;
@@ -520,6 +527,18 @@ rtu_status rtu_system_create_on(const rtu_system_desc* d, const rtu_host_inputs*
     return RTU_OK;
 }
 
+rtu_status rtu_system_tune(rtu_system* s, const rtu_tuning* t) {
+    if (!s || !t) return fail(RTU_E_ARG, "rtu_system_tune: null argument");
+    if (t->adj_div < 1 || t->adj_div > 64) return fail(RTU_E_ARG, "rtu_system_tune: adj_div must be in [1, 64]");
+    if (t->near_ctas < 1 || t->near_ctas > NEAR_CTAS_MAX)
+        return fail(RTU_E_ARG, "rtu_system_tune: near_ctas must be in [1, 16]");
+    if (t->edge_ctas < 1 || t->edge_ctas > 256) return fail(RTU_E_ARG, "rtu_system_tune: edge_ctas must be in [1, 256]");
+    s->adj_div = t->adj_div;
+    s->n_near = t->near_ctas;
+    s->n_edge = t->edge_ctas;
+    return RTU_OK;
+}
+
 rtu_status rtu_system_destroy(rtu_system* s) {
     delete s;
     return RTU_OK;
@@ -542,8 +561,10 @@ rtu_status fill_args(rtu_system* s, const rtu_eval& v, EvalArgs& e) {
     e.n_nodes = d.n_nodes; e.degree = d.degree; e.n_mask = s->n_mask; e.f64 = d.precision == RTU_F64;
     e.transform = d.transform;
     e.nrad = s->nrad; e.n_cta_c = s->n_cta_c; e.n_cta_r = s->z.n_cta_r; e.n_cta_p = s->z.n_cta_p;
-    e.n_cta_adj = s->z.n_cta_adj;
-    e.n_row_adj = s->z.n_cta_adj + (d.precision == RTU_F64 ? 0 : NEAR_CTAS);
+    e.n_cta_adj = std::max(1, (s->z.n_rays + s->adj_div * CTA_R * ADJ_RPT - 1) / (s->adj_div * CTA_R * ADJ_RPT));
+    e.n_near = s->n_near;
+    e.n_edge = s->n_edge;
+    e.n_row_adj = e.n_cta_adj + (d.precision == RTU_F64 ? 0 : s->n_near);
     for (int i = 0; i < MAX_RADIX; ++i) e.rad[i] = s->rad[i];
     e.pix = d.pix; e.pitch = d.src_pitch; e.sigma = d.sigma;
     e.data = d.data; e.mask = d.mask; e.psf = d.psf;
@@ -613,15 +634,15 @@ int t_render_fit(const EvalArgs& e) { return is_lin(e) ? 0 : e.n_cta_r; }
 int t_render_lin(const EvalArgs& e) { return is_lin(e) ? e.n_cta_r : 0; }
 int t_adj_fit(const EvalArgs& e) { return is_lin(e) ? 0 : e.n_cta_adj; }
 int t_adj_lin(const EvalArgs& e) { return is_lin(e) ? e.n_cta_adj : 0; }
-int t_near_fit(const EvalArgs& e) { return is_lin(e) ? 0 : NEAR_CTAS; }
-int t_near_lin(const EvalArgs& e) { return is_lin(e) ? NEAR_CTAS : 0; }
+int t_near_fit(const EvalArgs& e) { return is_lin(e) ? 0 : e.n_near; }
+int t_near_lin(const EvalArgs& e) { return is_lin(e) ? e.n_near : 0; }
 int t_gp_lines(const EvalArgs& e) { return (e.n_src + GP_LINES - 1) / GP_LINES; }
 int t_zero(const EvalArgs&) { return ZERO_TILES; }
 int t_centre(const EvalArgs& e) { return e.n_cta_c; }
 int t_adj(const EvalArgs& e) { return e.n_cta_adj; }
 int t_psf_gen(const EvalArgs& e) { return e.psf_uv ? 0 : e.n_cta_p; }
 int t_psf_sep(const EvalArgs& e) { return e.psf_uv ? e.n_cta_p : 0; }
-int t_edge(const EvalArgs&) { return EDGE_CTAS; }
+int t_edge(const EvalArgs& e) { return e.n_edge; }
 int t_cull_lin(const EvalArgs& e) { return is_lin(e) ? (e.n_cta_r + CULL_NT - 1) / CULL_NT : 0; }
 int t_units(const EvalArgs& e) { return (e.n_cta_r * (CTA_R / 32) + CMP_NT / 32 - 1) / (CMP_NT / 32); }
 int t_cells(const EvalArgs& e) {

@@ -23,13 +23,39 @@ constexpr int CTA_C = 256;        // centre-ray kernels: rays per CTA
 constexpr int CTA_R = 128;        // render kernels: pixels per CTA (one thread each)
 constexpr int STG_SHIFT = 11;      // staged entry: low bits the ray within its render warp (< 32 * 64)
 constexpr int STG_NEAR = 1 << 28;  // staged entry: a near-core ray (traced in FP64 by the float path)
-constexpr int NEAR_CTAS = 4;       // float render adjoint: CTAs per evaluation for the near-core rays
+constexpr int NEAR_CTAS = 4;       // float render adjoint: CTAs per evaluation for the near-core rays (default)
+constexpr int NEAR_CTAS_MAX = 16;  // the largest tuned value (the workspace holds its partial rows)
+constexpr int ADJ_DIV = 4;         // render adjoint: CTAs per evaluation = rays / (ADJ_DIV CTA_R ADJ_RPT) (default)
 constexpr int ADJ_RPT = 16;        // render adjoint: compacted rays per thread per chunk
 constexpr int PSF_T = 32;         // PSF kernels: 32 x 32 output tile per CTA (4 outputs per thread)
 constexpr int NACC_FIX = 11;      // render-adjoint partials: 8 lens + mu_x, mu_y, sigma
 
 // flag bits (mirror rtu.h)
-constexpr int F_NONMONO = 1, F_SELECT = 2, F_TIMEOUT = 4;
+constexpr int F_NONMONO = 1, F_SELECT = 2, F_TIMEOUT = 4, F_RANGE = 8;
+
+// Exact, order-independent accumulation of doubles as 128-bit fixed point: value
+// v is v 2^80 rounded to an integer (a quantum of 2^-80), held as a low word (unsigned)
+// and a high word (two's complement) at acc[0], acc[1].  Integer atomic additions are
+// associative, so the sum has the same bits whatever the order of the additions; the
+// low word's carry is detected from the value it returns.  |sum| must stay below 2^46:
+// a term of |v| >= 2^40 raises F_RANGE instead of being added.
+__device__ __forceinline__ void fix128_add(unsigned long long* acc, double v, int* flags) {
+    if (v == 0.0) return;
+    if (!(fabs(v) < 1099511627776.0)) {          // 2^40
+        atomicOr(flags, F_RANGE);
+        return;
+    }
+    const double s = v * 65536.0;                  // v 2^16: the high word's units
+    const double h = floor(s);
+    const long long hi = (long long)h;
+    const unsigned long long lo = __double2ull_rn((s - h) * 18446744073709551616.0);   // (s - h) 2^64
+    const unsigned long long old = atomicAdd(acc, lo);
+    const unsigned long long carry = old + lo < old ? 1ull : 0ull;
+    atomicAdd(acc + 1, (unsigned long long)hi + carry);
+}
+__device__ __forceinline__ double fix128_value(const unsigned long long* acc) {
+    return (double)(long long)acc[1] * (1.0 / 65536.0) + (double)acc[0] * 0x1p-80;
+}
 
 struct EvalArgs {
     // static, from the system
@@ -116,6 +142,7 @@ struct EvalArgs {
     int* useg;         // [n_cta_r * CTA_R/32 + 1] staged rays per render warp, then exclusive offsets
     int* kray;         // [n_rays] the adjoint's rays (staged rays in render-warp order): ray id, or -1
     int* kcell;        // [n_rays] their cells; -2 - cell for a near-core ray of the float path
+    int* krank;        // [n_rays] their ranks inside their cells (the counting sort's slot = offset + rank)
     int* nseg;         // [n_cta_r * CTA_R/32 + 1] near-core staged rays per render warp, then offsets
     int* nlist;        // [n_rays] adjoint positions of the near-core rays, in adjoint order
     void* gbuf;        // real2 [n_rays] d logL / d beta of each adjoint ray (subhalo pass)
@@ -123,13 +150,16 @@ struct EvalArgs {
     double* g_light;       // [6 n_light] adjoint out
     double* lpartl;        // [light CTAs][6 n_light] per-CTA lens-light moment sums
     int n_cta_adj;     // CTAs of the render adjoint (grid-stride over the compacted rays)
-    int n_row_adj;     // rows of apart: n_cta_adj, plus NEAR_CTAS for the float path's near-core pass
+    int n_row_adj;     // rows of apart: n_cta_adj, plus n_near for the float path's near-core pass
+    int n_near;        // CTAs per evaluation of the float path's near-core adjoint pass (tunable)
+    int n_edge;        // CTAs per evaluation of the near-edge double pass (tunable)
     // the unsmoothed eCDF transform (App. C, first paragraph), per axis a at a * n_mask
     double* lkey;      // [2][n_mask] sorted centre-ray positions
     int* lidx;         // [2][n_mask] the centre ray at each rank
     int* lrank;        // [2][n_mask] the rank of each centre ray
     float* lkf;        // [2][n_mask] float2 (hi, lo) of lkey
-    double* gk;        // [2][n_mask] d logL / d (sorted position), adjoint
+    unsigned long long* gk;  // [2][n_mask] d logL / d (sorted position), adjoint: (low, high) words of
+                             // a 128-bit fixed-point sum (fix128_add)
 };
 
 struct Batch {

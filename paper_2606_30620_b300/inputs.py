@@ -351,13 +351,17 @@ SERVE_SRC = (32, 48, 64, 96, 128)
 SERVE_S = (2, 3, 4)
 
 
-def config_serving_system(seed: int) -> Mock:
+def config_serving_system(seed: int, n_img: int | None = None, n_src: int | None = None,
+                          s: int | None = None) -> Mock:
     """One request of the serving stream: image size U{64..256}, grid U{32..128},
-    supersampling U{2,3,4}, SIE or EPL + shear with equal odds."""
+    supersampling U{2,3,4}, SIE or EPL + shear with equal odds (a size given fixes it)."""
     rng = np.random.default_rng(seed)
-    n_img = int(rng.choice(SERVE_IMG))
-    n_src = int(rng.choice(SERVE_SRC))
-    s = int(rng.choice(SERVE_S))
+    n_img_d = int(rng.choice(SERVE_IMG))
+    n_src_d = int(rng.choice(SERVE_SRC))
+    s_d = int(rng.choice(SERVE_S))
+    n_img = n_img_d if n_img is None else int(n_img)
+    n_src = n_src_d if n_src is None else int(n_src)
+    s = s_d if s is None else int(s)
     profile = PROFILE_SIE if rng.uniform() < 0.5 else PROFILE_EPL
     lens = _epl_lens(rng, 0.8, 1.3)
     if profile == PROFILE_SIE:

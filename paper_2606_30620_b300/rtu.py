@@ -24,7 +24,7 @@ RTU_SUB_NONE, RTU_SUB_NFW, RTU_SUB_TNFW = 0, 1, 2
 RTU_PS_POWER_LAW, RTU_PS_MATERN_LIKE, RTU_PS_MATERN = 0, 1, 2
 RTU_TRANSFORM_RTU, RTU_TRANSFORM_UNIFORM, RTU_TRANSFORM_LINEAR = 0, 1, 2
 STAT_LOGL, STAT_CHI2, STAT_NMASK, STAT_FLAGS, STAT_N_IN_GRID = 0, 1, 2, 3, 4
-W_NONMONOTONE, W_SELECT, W_TIMEOUT = 1, 2, 4
+W_NONMONOTONE, W_SELECT, W_TIMEOUT, W_RANGE = 1, 2, 4, 8
 N_STATS = 5
 SEL_BINS = 65536
 N_PS = {RTU_PS_POWER_LAW: 2, RTU_PS_MATERN_LIKE: 2, RTU_PS_MATERN: 3}
@@ -59,6 +59,10 @@ class HostInputs(ctypes.Structure):
     _fields_ = [("mask", ctypes.c_void_p), ("psf", ctypes.c_void_p), ("weights", ctypes.c_void_p)]
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("adj_div", ctypes.c_int32), ("near_ctas", ctypes.c_int32), ("edge_ctas", ctypes.c_int32)]
+
+
 class Prior(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("space", ctypes.c_int32), ("a", ctypes.c_double),
                 ("b", ctypes.c_double), ("c", ctypes.c_double), ("d", ctypes.c_double)]
@@ -72,6 +76,8 @@ _lib.rtu_system_create.restype = ctypes.c_int32
 _lib.rtu_system_create_on.argtypes = [ctypes.POINTER(SystemDesc), ctypes.POINTER(HostInputs), ctypes.c_void_p,
                                       ctypes.c_size_t, ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]
 _lib.rtu_system_create_on.restype = ctypes.c_int32
+_lib.rtu_system_tune.argtypes = [ctypes.c_void_p, ctypes.POINTER(Tuning)]
+_lib.rtu_system_tune.restype = ctypes.c_int32
 _lib.rtu_system_destroy.argtypes = [ctypes.c_void_p]
 _lib.rtu_system_destroy.restype = ctypes.c_int32
 for _name in ("rtu_build_grid", "rtu_forward", "rtu_adjoint"):
@@ -114,7 +120,8 @@ _lib.rtu_profile_timeline.restype = ctypes.c_int32
 _lib.rtu_last_error.restype = ctypes.c_char_p
 _lib.rtu_version.restype = ctypes.c_char_p
 
-EXPORTED = ("rtu_workspace_size", "rtu_system_create", "rtu_system_create_on", "rtu_system_destroy",
+EXPORTED = ("rtu_workspace_size", "rtu_system_create", "rtu_system_create_on", "rtu_system_tune",
+            "rtu_system_destroy",
             "rtu_build_grid", "rtu_forward", "rtu_adjoint", "rtu_n_sites", "rtu_elbo_init", "rtu_elbo_init_on",
             "rtu_elbo_step",
             "rtu_elbo_state_bytes", "rtu_elbo_export", "rtu_elbo_import", "rtu_elbo_grad", "rtu_gp_source_static",
@@ -174,12 +181,15 @@ class System:
     def __init__(self, data, mask, psf, sigma, pix, s_super, n_src, src_pitch, profile=RTU_SIE,
                  ps_family=RTU_PS_POWER_LAW, sub_kind=RTU_SUB_NONE, n_sub=0, precision=RTU_F32,
                  n_nodes=22, degree=21, n_slots=1, device="cuda", transform=RTU_TRANSFORM_RTU, n_light=0,
-                 weights=None, stream=None):
+                 weights=None, stream=None, host_staging=None, tune=True):
         """stream=None: synchronous creation (rtu_system_create).  With a torch stream
         and host (numpy) data, mask and psf: the observation travels in one pinned
         copy and the library builds the system from the host copies with uploads
         ordered on that stream (rtu_system_create_on); calls ordered after the stream
-        may use the system."""
+        may use the system.  host_staging: a pinned uint8 tensor of at least
+        staging_bytes(...) to stage that copy in (the caller keeps it untouched until
+        the stream has passed the copy), else one is allocated.  tune: apply the
+        autotuner's cached launch shape for this GPU and problem bucket, if any."""
         self.dtype = torch.float64 if precision == RTU_F64 else torch.float32
         self.device = torch.device(device)
         on_stream = stream is not None
@@ -190,9 +200,10 @@ class System:
             tb = np.dtype(npdt).itemsize
             nd, nk, nm = data.size, psf.size, mask.size
             nw = 0 if weights is None else nm
-            total = (nd + nk) * tb + nm + 4 * nw
-            pad = (-total) % 16
-            host = torch.empty(total + pad, dtype=torch.uint8, pin_memory=True)
+            total = System.staging_bytes(data.size, psf.size, precision, weights is not None)
+            pad = 0
+            host = (host_staging[:total] if host_staging is not None
+                    else torch.empty(total, dtype=torch.uint8, pin_memory=True))
             hb = host.numpy()
             hdp = hb[:nd * tb].view(npdt)
             hdp[:] = np.asarray(data, npdt).ravel()
@@ -204,7 +215,7 @@ class System:
             if weights is not None:
                 hw = hb[(nd + nk) * tb + nm:(nd + nk) * tb + nm + 4 * nw].view(np.uint32)
                 hw[:] = np.asarray(weights).astype(np.uint32).ravel()
-            dev = torch.empty(total + pad, dtype=torch.uint8, device=self.device)
+            dev = torch.empty(total, dtype=torch.uint8, device=self.device)
             with torch.cuda.stream(stream):
                 dev.copy_(host, non_blocking=True)
             self._host = host          # kept until the system is closed (the copy reads it)
@@ -266,6 +277,27 @@ class System:
         self.n_knots = self.n_nodes + 2
         self.n_light = int(n_light)
         self._n_mask = None
+        self.tuning = None
+        if tune:
+            from . import autotune
+            t = autotune.lookup(self.n_img, self.n_src, self.s_super, self.precision)
+            if t is not None:
+                self.tune(t)
+
+    def tune(self, tuning: dict):
+        """Launch shapes for later calls (rtu_system_tune): adj_div, near_ctas, edge_ctas."""
+        t = Tuning(int(tuning["adj_div"]), int(tuning["near_ctas"]), int(tuning["edge_ctas"]))
+        _check(_lib.rtu_system_tune(self.handle, ctypes.byref(t)), "rtu_system_tune")
+        self.tuning = dict(tuning)
+
+    @staticmethod
+    def staging_bytes(n_pixels: int, n_psf: int, precision: int, weighted: bool) -> int:
+        """Bytes of the pinned staging copy of an observation created on a stream: the
+        image and PSF in the precision's type, the mask bytes and the weights, rounded up
+        to 16."""
+        tb = 8 if precision == RTU_F64 else 4
+        total = (n_pixels + n_psf) * tb + n_pixels + (4 * n_pixels if weighted else 0)
+        return total + (-total) % 16
 
     @property
     def n_mask(self) -> int:
@@ -275,12 +307,13 @@ class System:
         return self._n_mask
 
     @classmethod
-    def from_mock(cls, m, precision=RTU_F32, n_slots=1, device="cuda", transform=RTU_TRANSFORM_RTU, stream=None):
+    def from_mock(cls, m, precision=RTU_F32, n_slots=1, device="cuda", transform=RTU_TRANSFORM_RTU, stream=None,
+                  host_staging=None, tune=True):
         return cls(m.data, m.mask, m.psf, m.sigma, m.pix, m.s_super, m.n_src, m.src_pitch, m.profile,
                    m.ps_family, m.sub_kind, 0 if m.subs is None else m.subs.shape[0], precision,
                    n_slots=n_slots, device=device, transform=transform,
                    n_light=0 if getattr(m, "light", None) is None else m.light.shape[0],
-                   weights=getattr(m, "weights", None), stream=stream)
+                   weights=getattr(m, "weights", None), stream=stream, host_staging=host_staging, tune=tune)
 
     @property
     def n_sites(self) -> int:

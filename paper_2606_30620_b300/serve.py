@@ -86,10 +86,45 @@ def workspace_bytes(m: I.Mock, precision: int, n_samples: int) -> int:
     return int(ws) + m.n_img * m.n_img * (tb + 1) + m.psf.size * tb + 4096
 
 
+class PinnedRing:
+    """Pinned host memory for the admission copies, handed out in FIFO order: a slice
+    is reused once the event recorded after its copy has been reached (no pinned
+    allocation per admitted system)."""
+
+    def __init__(self, nbytes: int):
+        self.buf = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+        self.n = nbytes
+        self.head = 0                     # next free byte (wraps)
+        self.live = deque()               # (start, end, event) of slices still being copied
+
+    def _retire(self, block: bool):
+        while self.live and (block or self.live[0][2].query()):
+            self.live[0][2].synchronize()
+            self.live.popleft()
+            block = False
+
+    def take(self, nbytes: int):
+        if nbytes > self.n:
+            return torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+        self._retire(False)
+        while True:
+            start = self.head if self.head + nbytes <= self.n else 0
+            end = start + nbytes
+            busy = any(a < end and start < b for a, b, _ in self.live)
+            if not busy:
+                self.head = end
+                return self.buf[start:end], (start, end)
+            self._retire(True)
+
+    def commit(self, span, event):
+        if span is not None:
+            self.live.append((span[0], span[1], event))
+
+
 class Server:
     def __init__(self, budget_bytes: int, max_batch: int = 32, n_samples: int = 1, lr: float = 1e-3,
                  seed: int = 0, precision: int = rtu.RTU_F32, n_streams: int = 2, device: str = "cuda",
-                 keep_resident: bool = False):
+                 keep_resident: bool = False, staging_bytes: int = 64 << 20):
         self.budget = int(budget_bytes)
         self.max_batch = max_batch
         self.n_samples = n_samples
@@ -109,6 +144,7 @@ class Server:
         # per stream: the batch's ELBO outputs on the device and their pinned host copy
         self.out_dev = [torch.empty(max_batch, dtype=torch.float64, device=self.device) for _ in self.streams]
         self.out_host = [torch.empty(max_batch, dtype=torch.float64, pin_memory=True) for _ in self.streams]
+        self.staging = PinnedRing(staging_bytes)
 
     # ---------------------------------------------------------------- admission
     def _admit(self, req: Request, now: float) -> bool:
@@ -126,11 +162,18 @@ class Server:
         # the observation in one pinned copy, the library's tables and the guide with
         # uploads ordered on the admission stream; nothing waits for the device here
         # (the batch's stream waits for the admission stream before its step)
+        m = req.mock
+        got = self.staging.take(rtu.System.staging_bytes(m.data.size, m.psf.size, self.precision,
+                                                          getattr(m, "weights", None) is not None))
+        buf, span = got if isinstance(got, tuple) else (got, None)
         with torch.cuda.stream(self.admit_stream):
-            s = rtu.System.from_mock(req.mock, precision=self.precision, n_slots=self.n_samples,
-                                     device=self.device, stream=self.admit_stream)
-            pr, ph, loc, rho = guide_start(req.mock)
+            s = rtu.System.from_mock(m, precision=self.precision, n_slots=self.n_samples, device=self.device,
+                                     stream=self.admit_stream, host_staging=buf)
+            pr, ph, loc, rho = guide_start(m)
             s.elbo_init(pr, ph, loc, rho, tag=req.system_id, stream=self.admit_stream)
+        ev = torch.cuda.Event()
+        ev.record(self.admit_stream)
+        self.staging.commit(span, ev)
         self.resident[req.system_id] = Resident(s, need, now)
         self.used += need
         self.peak_used = max(self.peak_used, self.used)

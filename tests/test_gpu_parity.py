@@ -471,3 +471,31 @@ def test_autograd_two_forwards_then_two_backwards(rtu):
     o2 = G.run_oracle(m2)
     assert G.rel_l2(g1, o1["g_latents"]) < F64_TOL
     assert G.rel_l2(lat2.grad.cpu().numpy(), o2["g_latents"]) < F64_TOL
+
+
+def test_linear_ecdf_gradient_is_reproducible_bit_for_bit(rtu):
+    # the unsmoothed map's position gradients are exact fixed-point sums: repeated calls
+    # and a batch with other systems give the same bits (FP64 and FP32)
+    for prec in (1, 0):
+        m = I.config_c2(1008, n_img=96, s=3, n_src=48)
+        other = I.config_c2(1009, n_img=64, s=2, n_src=32)
+        s = rtu.System.from_mock(m, precision=prec, transform=rtu.RTU_TRANSFORM_LINEAR)
+        b = rtu.Binding(s, m.lens, m.latents, m.ps)
+        runs = []
+        for _ in range(2):
+            rtu.Batch([b]).forward()
+            rtu.Batch([b]).adjoint()
+            torch.cuda.synchronize()
+            runs.append((b.g_lens.cpu().numpy().copy(), b.g_latents.cpu().numpy().copy(),
+                         int(b.stats.cpu().numpy()[rtu.STAT_FLAGS])))
+        s2 = rtu.System.from_mock(m, precision=prec, transform=rtu.RTU_TRANSFORM_LINEAR)
+        so = rtu.System.from_mock(other, precision=prec, transform=rtu.RTU_TRANSFORM_LINEAR)
+        b2 = rtu.Binding(s2, m.lens, m.latents, m.ps)
+        bo = rtu.Binding(so, other.lens, other.latents, other.ps)
+        batch = rtu.Batch([bo, b2])
+        batch.forward()
+        batch.adjoint()
+        torch.cuda.synchronize()
+        for r in runs[1:] + [(b2.g_lens.cpu().numpy(), b2.g_latents.cpu().numpy(), runs[0][2])]:
+            assert np.array_equal(r[0], runs[0][0]) and np.array_equal(r[1], runs[0][1])
+        assert runs[0][2] == 0
