@@ -799,45 +799,51 @@ __global__ void __launch_bounds__(CMP_NT) k_compact(const __grid_constant__ Batc
     const int* stg = E.cell + (size_t)u * cap;
     int nat = E.nseg[u];
     for (int g0 = 0; g0 < cnt; g0 += 128) {
-        int ent[4];
+        int ent[4], cell[4], rank[4];
+        bool nr[4];
+        unsigned grp[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int i = g0 + 32 * j + lane;
             ent[j] = i < cnt ? stg[i] : 0;
         }
+        // decode the four groups, then their rank atomics (the ray's rank inside its
+        // cell, the counting sort's slot in any order: the cell sums are exact integer
+        // sums; one atomic per group of lanes sharing the cell, ranks by lane order),
+        // all four in flight before any result is used
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int i = g0 + 32 * j + lane;
+            cell[j] = -1;
+            nr[j] = false;
+            if (i < cnt) {
+                const int e = ent[j];
+                int c = ((e & (STG_NEAR - 1)) >> STG_SHIFT) - 1;
+                cell[j] = c >= ncell ? -1 : c;
+                nr[j] = (e & STG_NEAR) != 0;
+            }
+            const unsigned act = __ballot_sync(0xffffffffu, cell[j] >= 0);
+            grp[j] = cell[j] >= 0 ? __match_any_sync(act, cell[j]) : 0u;
+            rank[j] = 0;
+            if (cell[j] >= 0 && lane == __ffs(grp[j]) - 1) rank[j] = atomicAdd(E.cursor + cell[j], __popc(grp[j]));
+        }
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int i = g0 + 32 * j + lane;
             if (g0 + 32 * j >= cnt) break;
-            bool nr = false;
-            int cell = -1;
+            const int leader = cell[j] >= 0 ? __ffs(grp[j]) - 1 : lane;
+            const int b = __shfl_sync(0xffffffffu, rank[j], leader);
             if (i < cnt) {
                 const int e = ent[j];
-                cell = ((e & (STG_NEAR - 1)) >> STG_SHIFT) - 1;
-                if (cell >= ncell) cell = -1;
-                nr = (e & STG_NEAR) != 0;
-                E.kray[o + i] = cell >= 0 ? staged_ray_id(E.n_img, E.s * E.s, u, e & ((1 << STG_SHIFT) - 1)) : -1;
-                E.kcell[o + i] = nr && cell >= 0 ? -2 - cell : cell;
-            }
-            {
-                // the ray's rank inside its cell (the counting sort's slot, any order: the
-                // cell sums are exact integer sums): one integer atomic per group of
-                // lanes sharing the cell, ranks by lane order
-                const unsigned act = __ballot_sync(0xffffffffu, cell >= 0);
-                if (cell >= 0) {
-                    const unsigned grp = __match_any_sync(act, cell);
-                    const int leader = __ffs(grp) - 1;
-                    int b = 0;
-                    if (lane == leader) b = atomicAdd(E.cursor + cell, __popc(grp));
-                    b = __shfl_sync(grp, b, leader);
-                    E.krank[o + i] = b + __popc(grp & ((1u << lane) - 1u));
-                }
+                E.kray[o + i] = cell[j] >= 0 ? staged_ray_id(E.n_img, E.s * E.s, u, e & ((1 << STG_SHIFT) - 1)) : -1;
+                E.kcell[o + i] = nr[j] && cell[j] >= 0 ? -2 - cell[j] : cell[j];
+                if (cell[j] >= 0) E.krank[o + i] = b + __popc(grp[j] & ((1u << lane) - 1u));
             }
             // every flagged entry keeps its list slot (counted by the render); one
             // that the double pass found outside the grid lists -1
-            const unsigned bn = __ballot_sync(0xffffffffu, nr);
+            const unsigned bn = __ballot_sync(0xffffffffu, nr[j]);
             const int at = nat + __popc(bn & ((1u << lane) - 1u));
-            if (nr && at >= 0 && at < n_rays) E.nlist[at] = cell >= 0 ? o + i : -1;
+            if (nr[j] && at >= 0 && at < n_rays) E.nlist[at] = cell[j] >= 0 ? o + i : -1;
             nat += __popc(bn);
         }
     }
@@ -1274,6 +1280,7 @@ __device__ __forceinline__ int gather_scale(const EvalArgs& E, double) {
 __device__ __forceinline__ long long fix_term(float w, float gs) {
     return (long long)(__float_as_int(__fmaf_rn(w, gs, 12582912.0f)) - 0x4B400000);
 }
+// (the 32-bit accumulation below casts this back to int: exact, |value| < 2^22)
 __device__ __forceinline__ long long fix_term(double w, double gs) { return __double2ll_rn(w * gs); }
 __device__ __forceinline__ float2 fix_to_pair(long long k, int S, float) {
     const double d = (double)k * pow2_of(-S, 0.0);
@@ -1300,15 +1307,30 @@ __global__ void __launch_bounds__(GATHER_NT) k_cell_gather(const __grid_constant
     const int S = gather_scale(E, T(0));
     const T sc = pow2_of(S, T(0));
     long long l0 = 0, l1 = 0, l2 = 0, l3 = 0;
-    for (int i = lo + hl; i < hi; i += 16) {
-        const R4 r = rec[i];
+    auto terms = [&](const R4& r, long long& t0, long long& t1, long long& t2, long long& t3) {
         const T fx = r.x, fy = r.y, gs = r.z * sc;      // exact: a power of two
         const T w0 = (T(1) - fx) * (T(1) - fy), w1 = fx * (T(1) - fy);
         const T w2 = (T(1) - fx) * fy, w3 = fx * fy;
-        l0 += fix_term(w0, gs);
-        l1 += fix_term(w1, gs);
-        l2 += fix_term(w2, gs);
-        l3 += fix_term(w3, gs);
+        t0 = fix_term(w0, gs);
+        t1 = fix_term(w1, gs);
+        t2 = fix_term(w2, gs);
+        t3 = fix_term(w3, gs);
+    };
+    if (sizeof(T) == 4 && hi - lo <= 16 * 511) {
+        // float terms are below 2^22: a lane's at most 511 of them sum exactly in 32 bits
+        int a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+        for (int i = lo + hl; i < hi; i += 16) {
+            long long t0, t1, t2, t3;
+            terms(rec[i], t0, t1, t2, t3);
+            a0 += (int)t0; a1 += (int)t1; a2 += (int)t2; a3 += (int)t3;
+        }
+        l0 = a0; l1 = a1; l2 = a2; l3 = a3;
+    } else {
+        for (int i = lo + hl; i < hi; i += 16) {
+            long long t0, t1, t2, t3;
+            terms(rec[i], t0, t1, t2, t3);
+            l0 += t0; l1 += t1; l2 += t2; l3 += t3;
+        }
     }
     // the half-warp's four sums by a transposing butterfly: at xor 8 the lower eight
     // lanes keep corners 0, 1 and the upper eight 2, 3, at xor 4 each quarter keeps one
