@@ -466,7 +466,7 @@ def run_ours(args):
 # the NEXT variants of the hot path on the same mocks: the kernels each one adds or
 # swaps, and its whole-step throughput
 VARIANT_KERNELS = ("k_select_fit", "k_lin_sort", "k_render", "k_render_edge", "k_render_adj", "k_cdf_adj",
-                   "k_centre_adj", "k_sel_adj", "k_lin_centre_adj", "k_light_fwd", "k_light_adj")
+                   "k_centre_adj", "k_sel_jac", "k_lin_centre_adj", "k_light_fwd", "k_light_adj")
 
 
 def run_variants(args, dev, mocks, flush, stream):
@@ -573,7 +573,7 @@ def run_timeline(args):
     bracketed by events (the library's tracing aid, which launches plainly and adds a
     little time per launch): the median over 5 steps after warm-up and an L2 flush,
     one line per launch "<kernel> <stream> <start_us> <end_us> <us>", stream 0 the
-    call's, 1 and 2 the library's side streams.  A diagnostic, not a bench line."""
+    call's, 1 the library's side stream.  A diagnostic, not a bench line."""
     from paper_2606_30620_b300 import rtu
     mocks = make_mocks(0, args.mocks)
     binds = [rtu.Binding(rtu.System.from_mock(m, precision=rtu.RTU_F32), m.lens, m.latents, m.ps) for m in mocks]

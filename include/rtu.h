@@ -318,7 +318,7 @@ rtu_status rtu_profile_report(char* buf, size_t bytes);
 /* The same records as a timeline: waits for the events, then writes one line
  * "<kernel> <stream> <start_ms> <end_ms>" per launch, in launch order, with times
  * relative to the start of the first recorded launch and <stream> 0 for the
- * call's stream, 1 or 2 for the library's side streams; clears the record like
+ * call's stream, 1 for the library's side stream; clears the record like
  * rtu_profile_report (so call one or the other).  Returns RTU_E_CUDA if an event
  * call fails. */
 rtu_status rtu_profile_timeline(char* buf, size_t bytes);

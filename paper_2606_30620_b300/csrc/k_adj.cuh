@@ -21,9 +21,26 @@ __device__ __forceinline__ double apart_col(const EvalArgs& E, int col) {
     return warp_rows_sum(E.apart + (size_t)col * E.n_row_adj, E.n_row_adj, 1);
 }
 
+// the selected-rank lens terms of axis a: sum over targets t of tadj[sel a t] jsel[a
+// t], into row n_cta_c + a of cadj; one warp per lens parameter, lanes over the targets
+// (fixed lane stride and shuffle tree)
+__device__ __forceinline__ void sel_terms(const EvalArgs& E, int a) {
+    const int T2 = min(2 * E.n_nodes, 2 * MAXM);
+    const int nl = 8 + 5 * (E.sub_kind ? E.n_sub : 0);
+    const int lane = threadIdx.x & 31;
+    for (int p = threadIdx.x >> 5; p < nl; p += blockDim.x >> 5) {
+        double s = 0.0;
+        for (int t = lane; t < T2; t += 32)
+            s += E.tadj[TADJ_SEL + a * 2 * MAXM + t] * E.jsel[(size_t)(a * 2 * MAXM + t) * nl + p];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) E.cadj[(size_t)(E.n_cta_c + a) * nl + p] = s;
+    }
+}
+
 // One CTA per (evaluation, axis); the uniform-grid transform couples the axes
 // (one box side) and is done by the axis-0 CTA alone.
 constexpr int CDF_NT = 256;
+constexpr int CDF_CHEB_STAGE = 2048;      // doubles of the fit's matrices staged in shared memory
 __global__ void __launch_bounds__(CDF_NT) k_cdf_adj(const __grid_constant__ Batch B) {
     const int ev = find_eval(B, blockIdx.x);
     const EvalArgs& E = B.e[ev];
@@ -71,24 +88,55 @@ __global__ void __launch_bounds__(CDF_NT) k_cdf_adj(const __grid_constant__ Batc
             E.tadj[4] = dsig;
             E.tadj[5] = 0.0;
         }
+        __syncthreads();
+        sel_terms(E, 0);
+        sel_terms(E, 1);
         return;
     }
     // this axis's guarded knots, raw knots, raw p' and slopes, staged (the serial
-    // parts below walk them)
+    // parts below walk them), and the fit's matrices when they fit the staging buffer
     __shared__ double sXf[MAXM + 2], sXr[MAXM + 2], spr[MAXM + 2], ssl[MAXM + 2];
+    __shared__ double scheb[CDF_CHEB_STAGE];
     for (int j = threadIdx.x; j < K; j += CDF_NT) {
         sXf[j] = tr[TR_HDR + ax * K + j];
         sXr[j] = tr[TR_HDR + (6 + ax) * K + j];
         spr[j] = tr[TR_HDR + (4 + ax) * K + j];
         ssl[j] = tr[TR_HDR + (2 + ax) * K + j];
     }
-    // this axis's columns: dmu_a, dsigma (axis 0), knots X and slopes d
+    const int ncheb = cheb_C(M, D) + (D + 1) * M;
+    const bool cstaged = ncheb <= CDF_CHEB_STAGE;
+    if (cstaged)
+        for (int i = threadIdx.x; i < ncheb; i += CDF_NT) scheb[i] = E.cheb[i];
+    const double* cheb = cstaged ? scheb : E.cheb;
+    // this axis's columns: dmu_a, dsigma (axis 0), knots X and slopes d; a warp's
+    // columns' rows loaded before any of its shuffle trees (fixed lane stride and tree)
     const int ncol = 2 + 2 * K;
-    for (int w = wid; w < ncol; w += CDF_NT / 32) {
-        const int col = w == 0 ? 8 + ax : (w == 1 ? 10 : (w < 2 + K ? NACC_FIX + ax * K + (w - 2)
-                                                                   : NACC_FIX + 2 * K + ax * K + (w - 2 - K)));
-        const double v = apart_col(E, col);
-        if (lane == 0) tot[col] = v;
+    constexpr int NWD = CDF_NT / 32, CPW = (2 + 2 * (MAXM + 2) + NWD - 1) / NWD;
+    {
+        const int rows = E.n_row_adj;
+        double v[CPW];
+#pragma unroll
+        for (int j = 0; j < CPW; ++j) {
+            const int w = wid + j * NWD;
+            v[j] = 0.0;
+            if (w < ncol) {
+                const int col = w == 0 ? 8 + ax : (w == 1 ? 10 : (w < 2 + K ? NACC_FIX + ax * K + (w - 2)
+                                                                           : NACC_FIX + 2 * K + ax * K + (w - 2 - K)));
+                const double* a = E.apart + (size_t)col * rows;
+#pragma unroll 4
+                for (int t = lane; t < rows; t += 32) v[j] += a[t];
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < CPW; ++j) {
+            const int w = wid + j * NWD;
+            if (w >= ncol) break;            // warp-uniform
+            double x = v[j];
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+            const int col = w == 0 ? 8 + ax : (w == 1 ? 10 : (w < 2 + K ? NACC_FIX + ax * K + (w - 2)
+                                                                       : NACC_FIX + 2 * K + ax * K + (w - 2 - K)));
+            if (lane == 0) tot[col] = x;
+        }
     }
     __syncthreads();
     const double* gX = tot + NACC_FIX + ax * K;
@@ -127,8 +175,8 @@ __global__ void __launch_bounds__(CDF_NT) k_cdf_adj(const __grid_constant__ Batc
     }
     __syncthreads();
     // knots X = V c and slopes p' = dV c  ->  gc = V^T gX + dV^T gp'
-    const double* Vt = E.cheb + cheb_V(M, D);
-    const double* dVt = E.cheb + cheb_dV(M, D);
+    const double* Vt = cheb + cheb_V(M, D);
+    const double* dVt = cheb + cheb_dV(M, D);
     for (int k = threadIdx.x; k <= D; k += CDF_NT) {
         double g = 0.0;
 #pragma unroll 8
@@ -137,13 +185,13 @@ __global__ void __launch_bounds__(CDF_NT) k_cdf_adj(const __grid_constant__ Batc
     }
     __syncthreads();
     // c = C Q  ->  gQ = C^T gc; Q = z_lo + frac (z_hi - z_lo), z = (beta - mu)/sigma
-    const double* Ct = E.cheb + cheb_C(M, D);
+    const double* Ct = cheb + cheb_C(M, D);
     for (int i = threadIdx.x; i < M; i += CDF_NT) {
         double g = 0.0;
 #pragma unroll 8
         for (int k = 0; k <= D; ++k) g += Ct[k * M + i] * gc[k];
         gQ[i] = g;
-        const double h = E.cheb[cheb_u(M, D) + i] * (E.wtot - 1);
+        const double h = cheb[cheb_u(M, D) + i] * (E.wtot - 1);
         const double frac = h - floor(h);
         E.tadj[TADJ_SEL + ax * 2 * MAXM + 2 * i] = g * (1.0 - frac) * isig;
         E.tadj[TADJ_SEL + ax * 2 * MAXM + 2 * i + 1] = g * frac * isig;
@@ -167,11 +215,12 @@ __global__ void __launch_bounds__(CDF_NT) k_cdf_adj(const __grid_constant__ Batc
             if (ax == 0) E.tadj[3] = tr[3];
         }
     }
+    sel_terms(E, ax);      // the selected-rank tadj entries were written before the barrier
 }
 
 // centre rays: d logL / d beta_i = dmu/N + [a = argmin sigma] dsigma (beta_i,a -
 //   mu_a)/(N sigma_min) here, then the lens (the selected-rank terms, large and
-//   few, are k_sel_adj's, in double)
+//   few, come from k_sel_jac's rows, in double)
 template <typename T>
 __global__ void __launch_bounds__(CTA_C) k_centre_adj(const __grid_constant__ Batch B) {
     const int ev = find_eval(B, blockIdx.x);
@@ -266,12 +315,15 @@ __global__ void __launch_bounds__(CTA_C) k_centre_adj(const __grid_constant__ Ba
     }
 }
 
-// The selected-rank terms: every (axis, target) whose order statistic the QF
-// interpolates passes d logL / d beta of its ray to the lens, in double (these few
-// terms are large and partly cancel the image terms).  One CTA per evaluation, one
-// thread per (axis, target); the row after the centre CTAs' rows in cadj.
+// The selected-rank lens Jacobians: every (axis a, target t) whose order statistic
+// the QF interpolates contributes (d logL / d beta_a of its ray) times the row
+// d beta_a / d lens of that ray, in double (these few terms are large and partly
+// cancel the image terms).  The rows depend on the lens and the selection only, so the
+// forward computes them (beside the render, after the selection) and the transform
+// adjoint takes the weighted sum once the cotangents are known.  One CTA per
+// evaluation, one thread per (axis, target): jsel[(a 2 MAXM + t) nl + p].
 constexpr int SEL_ADJ_NT = 4 * MAXM;
-__global__ void __launch_bounds__(SEL_ADJ_NT) k_sel_adj(const __grid_constant__ Batch B) {
+__global__ void __launch_bounds__(SEL_ADJ_NT) k_sel_jac(const __grid_constant__ Batch B) {
     // systems of the unsmoothed transform launch no CTA here: map through the prefix
     const EvalArgs& E = B.e[find_eval(B, blockIdx.x)];
     const int M = E.n_nodes;
@@ -279,10 +331,9 @@ __global__ void __launch_bounds__(SEL_ADJ_NT) k_sel_adj(const __grid_constant__ 
     const int nl = 8 + 5 * nsub;
     __shared__ LensK<double> Ld;
     __shared__ LensK<DF> Ldf;
-    __shared__ double red[SEL_ADJ_NT / 32][8];
     load_lensk(Ld, E.lensk);
     __syncthreads();
-    // the float path without subhaloes evaluates these terms in double-float (about
+    // the float path without subhaloes evaluates these rows in double-float (about
     // 48 bits) on the FP32 pipes: FP64 instructions are scarce on this part
     const bool use_df = !E.f64 && Ld.nsub == 0;
     if (use_df) {
@@ -292,9 +343,9 @@ __global__ void __launch_bounds__(SEL_ADJ_NT) k_sel_adj(const __grid_constant__ 
     const int a = threadIdx.x / (2 * MAXM), t = threadIdx.x - a * 2 * MAXM;
     const int ray = t < 2 * M ? E.sel_idx[a * 2 * MAXM + t] : -1;
     double o8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    double xd = 0.0, yd = 0.0, g = 0.0;
-    if (ray >= 0 && ray < E.n_mask) {
-        g = E.tadj[TADJ_SEL + a * 2 * MAXM + t];
+    double xd = 0.0, yd = 0.0;
+    const bool ok = ray >= 0 && ray < E.n_mask;
+    if (ok) {
         const int pix = E.centre_idx[ray];
         const int pj = pix / E.n_img, pi = pix - pj * E.n_img;
         const double c = 0.5 * (E.n_img - 1);
@@ -303,45 +354,24 @@ __global__ void __launch_bounds__(SEL_ADJ_NT) k_sel_adj(const __grid_constant__ 
         if (use_df) {
             EplJ<DF> J;
             DF bx, by;
-            const DF xf(xd), yf(yd), gf(g), zero(0.0f, 0.0f);
+            const DF xf(xd), yf(yd), one(1.0f), zero(0.0f, 0.0f);
             lens_beta_eval_smooth(Ldf, xf, yf, J, bx, by);
             DF o8f[8] = {zero, zero, zero, zero, zero, zero, zero, zero};
-            lens_beta_vjp(Ldf, J, xf, yf, a == 0 ? gf : zero, a == 1 ? gf : zero, o8f);
+            lens_beta_vjp(Ldf, J, xf, yf, a == 0 ? one : zero, a == 1 ? one : zero, o8f);
             for (int p = 0; p < 8; ++p) o8[p] = o8f[p].to_double();
         } else {
             EplJ<double> J;
             double bx, by;
             lens_beta_eval(Ld, xd, yd, J, bx, by);
-            lens_beta_vjp(Ld, J, xd, yd, a == 0 ? g : 0.0, a == 1 ? g : 0.0, o8);
+            lens_beta_vjp(Ld, J, xd, yd, a == 0 ? 1.0 : 0.0, a == 1 ? 1.0 : 0.0, o8);
         }
     }
-    double* out = E.cadj + (size_t)E.n_cta_c * nl;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int p = 0; p < 8; ++p) {
-        const double v = warp_sum(o8[p]);
-        if (lane == 0) red[wid][p] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x < 8) {
-        double r = 0.0;
-        for (int w = 0; w < SEL_ADJ_NT / 32; ++w) r += red[w][threadIdx.x];
-        out[threadIdx.x] = r;
-    }
+    double* row = E.jsel + (size_t)threadIdx.x * nl;
+    for (int p = 0; p < 8; ++p) row[p] = o8[p];
     for (int h = 0; h < nsub; ++h) {
-        __syncthreads();
         double a5[5] = {0, 0, 0, 0, 0};
-        if (ray >= 0 && ray < E.n_mask)
-            sub_vjp<double>(Ld, h, xd, yd, a == 0 ? g : 0.0, a == 1 ? g : 0.0, a5);
-        for (int c = 0; c < 5; ++c) {
-            const double v = warp_sum(a5[c]);
-            if (lane == 0) red[wid][c] = v;
-        }
-        __syncthreads();
-        if (threadIdx.x < 5) {
-            double r = 0.0;
-            for (int w = 0; w < SEL_ADJ_NT / 32; ++w) r += red[w][threadIdx.x];
-            out[8 + 5 * h + threadIdx.x] = r;
-        }
+        if (ok) sub_vjp<double>(Ld, h, xd, yd, a == 0 ? 1.0 : 0.0, a == 1 ? 1.0 : 0.0, a5);
+        for (int c = 0; c < 5; ++c) row[8 + 5 * h + c] = a5[c];
     }
 }
 
@@ -349,7 +379,8 @@ __global__ void __launch_bounds__(SEL_ADJ_NT) k_sel_adj(const __grid_constant__ 
 // axis a, so d logL / d beta_i = (gk_x[r_x(i)], gk_y[r_y(i)]); then the lens (and
 // subhaloes), in double: every centre ray carries terms of the size of the image
 // terms they cancel.  One thread per centre ray, rows 0..n_cta_c-1 of cadj; the
-// CTA of tile 0 also clears row n_cta_c (the selected-rank row of the smoothed grid).
+// CTA of tile 0 also clears rows n_cta_c and n_cta_c + 1 (the selected-rank rows of
+// the smoothed grid).
 __global__ void __launch_bounds__(CTA_C) k_lin_centre_adj(const __grid_constant__ Batch B) {
     const int ev = find_eval(B, blockIdx.x);
     const EvalArgs& E = B.e[ev];
@@ -405,7 +436,7 @@ __global__ void __launch_bounds__(CTA_C) k_lin_centre_adj(const __grid_constant_
         }
     }
     if (tile == 0)
-        for (int p = threadIdx.x; p < nl; p += CTA_C) E.cadj[(size_t)E.n_cta_c * nl + p] = 0.0;
+        for (int p = threadIdx.x; p < 2 * nl; p += CTA_C) E.cadj[(size_t)E.n_cta_c * nl + p] = 0.0;
 }
 
 // g_lens = (render-adjoint lens sums) + (centre-adjoint lens sums), one warp per
@@ -422,7 +453,7 @@ __global__ void __launch_bounds__(GRAD_NT) k_grad_final(const __grid_constant__ 
     for (int p = wid; p < nl; p += NW) {
         const int col = p < 8 ? p : NACC_FIX + 4 * K + (p - 8);
         const double s = apart_col(E, col);
-        const double c = warp_rows_sum(E.cadj + p, E.n_cta_c + 1, nl);   // + the selected-rank row
+        const double c = warp_rows_sum(E.cadj + p, E.n_cta_c + 2, nl);   // + the selected-rank rows
         double g = s + c;
         if (p == 1 && E.profile == 0) g = 0.0;
         if (lane == 0) E.g_lens[p] = g;
@@ -430,7 +461,7 @@ __global__ void __launch_bounds__(GRAD_NT) k_grad_final(const __grid_constant__ 
     // spectrum parameters and alpha_src: the GP adjoint's per-CTA partials
     {
         const int nf = E.family == 2 ? 3 : 2;
-        const int ngl = (E.n_src + GP_LINES - 1) / GP_LINES;
+        const int ngl = gp_part_rows(E.n_src);
         for (int c = wid; c <= nf; c += NW) {
             const double v = warp_rows_sum(E.gpart + (c < nf ? c : 3), ngl, 4);
             if (lane == 0) E.g_ps[c] = v;

@@ -3,6 +3,7 @@
 // memory, a few lines of one evaluation per CTA, over an n_src x n_src complex
 // buffer that stays in L2 between the passes.
 #pragma once
+#include <cooperative_groups.h>
 #include "rtu_internal.cuh"
 
 namespace rtu {
@@ -228,6 +229,10 @@ __device__ __forceinline__ void gp_setup(const EvalArgs& E, Cx<T>* tw_s, int* re
 constexpr int GP_LINES = 8;
 constexpr int GP_LINE_NT = 256;
 constexpr int GP_PASSES = 3;
+constexpr int GP_CL = 8;              // CTAs of the GP adjoint's cluster kernel
+// rows of per-CTA GP adjoint partials: one per line CTA, at least one per cluster CTA
+// (rows a kernel does not write are zeroed by its first CTA)
+__host__ __device__ inline int gp_part_rows(int n) { return max((n + GP_LINES - 1) / GP_LINES, GP_CL); }
 constexpr int GP_PER_T = GP_LINES * 256 / GP_LINE_NT;   // line elements per thread, at most
 
 // line q of the CTA's buffer from natural order into the digit-reversed order the
@@ -378,6 +383,10 @@ __global__ void __launch_bounds__(GP_LINE_NT) k_gp_adj_lines(const __grid_consta
     Cx<T>* G = reinterpret_cast<Cx<T>*>(E.cbufA);
     const int nf = n_family(E.family);
     double* part = E.gpart + (size_t)tile * 4;
+    if (pass == 0 && tile == 0) {
+        const int ngl = (n + GP_LINES - 1) / GP_LINES;
+        for (int i = ngl * 4 + threadIdx.x; i < gp_part_rows(n) * 4; i += blockDim.x) E.gpart[i] = 0.0;
+    }
     if (pass == 0) {
         typedef typename real2_of<T>::type TP;
         const TP* cor = reinterpret_cast<const TP*>(E.corner);
@@ -460,6 +469,137 @@ __global__ void __launch_bounds__(GP_LINE_NT) k_gp_adj_lines(const __grid_consta
     for (int i = threadIdx.x; i < cnt * n; i += blockDim.x) {
         const int q = i / n, p = i - q * n;
         gl[(l0 + q) * n + p] = sm[q * n + p].x * inv_n2;
+    }
+}
+
+// S9 (source part) as one kernel per evaluation on a thread-block cluster of GP_CL
+// CTAs: CTA r holds lines [r L, r L + L), L = n / GP_CL, and the transposes between
+// the row and column passes read the other CTAs' shared memory (distributed shared
+// memory) instead of a global buffer, with cluster barriers where the three line
+// passes of k_gp_adj_lines had kernel boundaries.  The same arithmetic per line:
+//   rows:    G = g ds*/df (node gradients from the corner sums), forward row FFTs  -> A
+//   columns: forward column FFTs of A (remote), spectrum sums, times sqrt(P(k)),
+//            digit-reversed into C, inverse column FFTs                            -> C
+//   rows:    inverse row FFTs of C (remote); d log L / d w = Re / N^2
+// Needs n % GP_CL == 0 and 3 L n complex values of shared memory (gp_cluster_ok).
+constexpr int GP_CL_NT = 256;
+constexpr size_t GP_CL_SMEM_MAX = 192 * 1024;
+__host__ __device__ inline size_t gp_cluster_bytes(int n, int tb) { return (size_t)3 * (n / GP_CL) * n * 2 * tb; }
+__host__ __device__ inline bool gp_cluster_ok(int n, int tb) {
+    return n % GP_CL == 0 && n <= 256 && gp_cluster_bytes(n, tb) <= GP_CL_SMEM_MAX;
+}
+template <typename T>
+__global__ void __cluster_dims__(GP_CL, 1, 1) __launch_bounds__(GP_CL_NT) k_gp_adj_cluster(const __grid_constant__ Batch B) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    const int ev = find_eval(B, blockIdx.x);
+    const EvalArgs& E = B.e[ev];
+    const int rank = (int)cl.block_rank();
+    const int n = E.n_src, nc = n - 1, L = n / GP_CL, l0 = rank * L;
+    extern __shared__ __align__(16) unsigned char gp_smem[];
+    Cx<T>* A = reinterpret_cast<Cx<T>*>(gp_smem);
+    Cx<T>* Bf = A + (size_t)L * n;
+    Cx<T>* C = Bf + (size_t)L * n;
+    __shared__ Cx<T> tw_s[256];
+    __shared__ int rev_s[256], inv_s[256];
+    __shared__ int rad_s[MAX_RADIX];
+    __shared__ double red[4][GP_CL_NT / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    gp_setup<T>(E, tw_s, rev_s, rad_s);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) inv_s[rev_s[i]] = i;
+    const int nf = n_family(E.family);
+    double* part = E.gpart + (size_t)rank * 4;
+    if (rank == 0)
+        for (int i = GP_CL * 4 + threadIdx.x; i < gp_part_rows(n) * 4; i += blockDim.x) E.gpart[i] = 0.0;
+    // rows: node gradients (digit-reversed load of each row), then forward FFTs
+    {
+        typedef typename real2_of<T>::type TP;
+        const TP* cor = reinterpret_cast<const TP*>(E.corner);
+        const T* fld = reinterpret_cast<const T*>(E.fld);
+        const T* src = reinterpret_cast<const T*>(E.src);
+        const T alpha = (T)E.ps[nf];
+        T ga_t = T(0);
+        for (int i = threadIdx.x; i < L * n; i += blockDim.x) {
+            const int q = i / n, p = i - q * n;
+            const int j = l0 + q, ii = rev_s[p];
+            T g = T(0);
+            if (ii < nc && j < nc) { const TP c = cor[(j * nc + ii) * 4 + 0]; g += c.x + c.y; }
+            if (ii > 0 && j < nc) { const TP c = cor[(j * nc + ii - 1) * 4 + 1]; g += c.x + c.y; }
+            if (ii < nc && j > 0) { const TP c = cor[((j - 1) * nc + ii) * 4 + 2]; g += c.x + c.y; }
+            if (ii > 0 && j > 0) { const TP c = cor[((j - 1) * nc + ii - 1) * 4 + 3]; g += c.x + c.y; }
+            const int at = j * n + ii;
+            const T sv = src[at];
+            const T x = fld[at] / T(0.01);
+            // d s / d f = alpha s (sigma(x)/phi_sp(x)) / s0
+            const T dsdf = alpha * sv * sig_over_sp<T>(x) / T(0.01);
+            A[q * n + p] = Cx<T>{g * dsdf, T(0)};
+            if (sv > T(0)) ga_t += g * sv * log_sp_s0<T>(x);
+        }
+        // the alpha_src partial: warp sums now, the CTA's sum with the spectrum's below
+        const double w = warp_sum(ga_t);
+        if (lane == 0) red[3][wid] = w;
+        __syncthreads();                 // the rows are written before the butterflies read them
+        fft_seq_smem<T>(A, L, n, rad_s, E.nrad, tw_s, false);
+    }
+    cl.sync();
+    // columns: element (row r, column l0 + q) from the CTA holding row r
+    for (int i = threadIdx.x; i < L * n; i += blockDim.x) {
+        const int p = i / L, q = i - p * L;
+        const int r = rev_s[p], owner = r / L;
+        const Cx<T>* rA = cl.map_shared_rank(A, owner);
+        Bf[q * n + p] = rA[(r - owner * L) * n + l0 + q];
+    }
+    __syncthreads();
+    fft_seq_smem<T>(Bf, L, n, rad_s, E.nrad, tw_s, false);
+    {
+        typedef typename real2_of<T>::type C2;
+        const C2* Wk = reinterpret_cast<const C2*>(E.cbufB);
+        T psv[4];
+        for (int q = 0; q < nf; ++q) psv[q] = (T)E.ps[q];
+        const T kscale = (T)(2.0 * 3.14159265358979323846 / E.pitch);
+        const T inv_n2s = T(1) / T(n * n);
+        T gp[3] = {T(0), T(0), T(0)};
+        for (int i = threadIdx.x; i < L * n; i += blockDim.x) {
+            const int p = i / L, q = i - p * L;
+            const T fx = fftfreq<T>(l0 + q, n), fy = fftfreq<T>(p, n);
+            const T k = kscale * r_sqrt(fx * fx + fy * fy);
+            T dsp[3] = {T(0), T(0), T(0)};
+            const T sp = sqrtP_and_grad<T>(E.family, psv, k, dsp);
+            const Cx<T> Gk = Bf[q * n + p];
+            const C2 W = Wk[p * n + l0 + q];
+            const T d = (W.x * Gk.x + W.y * Gk.y) * inv_n2s;
+            for (int c = 0; c < nf; ++c) gp[c] += d * dsp[c];
+            C[q * n + inv_s[p]] = Cx<T>{Gk.x * sp, Gk.y * sp};    // digit-reversed for the inverse
+        }
+        for (int c = 0; c < 3; ++c) {
+            const double w = warp_sum(gp[c]);
+            if (lane == 0) red[c][wid] = w;
+        }
+    }
+    __syncthreads();
+    // the CTA's four partials: warps in order, one thread each
+    if (threadIdx.x < 4) {
+        double v = 0.0;
+        for (int w = 0; w < GP_CL_NT / 32; ++w) v += red[threadIdx.x][w];
+        part[threadIdx.x] = threadIdx.x < 3 && threadIdx.x >= nf ? 0.0 : v;
+    }
+    fft_seq_smem<T>(C, L, n, rad_s, E.nrad, tw_s, true);
+    cl.sync();
+    // rows again: element (row l0 + q, column c) from the CTA holding column c
+    for (int i = threadIdx.x; i < L * n; i += blockDim.x) {
+        const int q = i / n, p = i - q * n;
+        const int c = rev_s[p], owner = c / L;
+        const Cx<T>* rC = cl.map_shared_rank(C, owner);
+        A[q * n + p] = rC[(c - owner * L) * n + l0 + q];
+    }
+    // every CTA's remote reads are done before any CTA leaves or moves on
+    cl.sync();
+    fft_seq_smem<T>(A, L, n, rad_s, E.nrad, tw_s, true);
+    T* gl = reinterpret_cast<T*>(E.g_lat);
+    const T inv_n2 = T(1) / T(n * n);
+    for (int i = threadIdx.x; i < L * n; i += blockDim.x) {
+        const int q = i / n, p = i - q * n;
+        gl[(l0 + q) * n + p] = A[q * n + p].x * inv_n2;
     }
 }
 

@@ -586,11 +586,12 @@ __global__ void __launch_bounds__(CTA_R, sizeof(T) == 4 && !LIN ? 8 : 6) k_rende
         const int c16 = codes[q * CTA_R];
         if (c16 == 0xffff) continue;
         const int code = c16;
-        stg[pos] = (lane * s2 + q) | (code << STG_SHIFT) | ((nearm >> q & 1ull) ? STG_NEAR : 0);
+        stg[pos] = (lane * s2 + q) | (code << STG_SHIFT) | ((nearm >> q & 1ull) ? STG_NEAR : 0) |
+                   (code == 0 ? STG_DEFER : 0);
         if (code == 0) {
             // the double pass finds the ray through its staging position
             const int at = atomicAdd(E.ecount, 1);
-            reinterpret_cast<int*>(E.rec)[at] = (int)(ubase + pos);
+            E.elist[at] = (int)(ubase + pos);
         }
         ++pos;
     }
@@ -642,7 +643,7 @@ __global__ void __launch_bounds__(EDGE_NT) k_render_edge(const __grid_constant__
     float* img = reinterpret_cast<float*>(E.img);
     const int cap = 32 * s2;                 // staged entries per render warp
     for (int k = tile * EDGE_NT + threadIdx.x; k < cnt; k += E.n_edge * EDGE_NT) {
-        const int at = reinterpret_cast<const int*>(E.rec)[k];     // staging position
+        const int at = E.elist[k];     // staging position
         const int e0 = E.cell[at];
         const int local = e0 & ((1 << STG_SHIFT) - 1);
         const int u = at / cap;
@@ -664,7 +665,7 @@ __global__ void __launch_bounds__(EDGE_NT) k_render_edge(const __grid_constant__
         if (cell >= 0) {
             v = bilinear_at<float, float>(grid, n, i0, j0, (float)fx, (float)fy);
             atomicAdd(E.ccount + cell, 1);
-            E.cell[at] = (e0 & STG_NEAR) | local | ((cell + 1) << STG_SHIFT);
+            E.cell[at] = (e0 & (STG_NEAR | STG_DEFER)) | local | ((cell + 1) << STG_SHIFT);
         } else {
             atomicSub(E.cta_cnt + u / (CTA_R / 32), 1);
         }
@@ -684,11 +685,9 @@ __global__ void __launch_bounds__(EDGE_NT) k_render_edge(const __grid_constant__
     }
 }
 
-// exclusive scan of the per-cell ray counts into offsets
-constexpr int SCAN_NT = 1024;
-
 // in-place exclusive scans of a[0..n) and b[0..n) by one CTA of SCAN_NT threads
 // (both in one pass), totals in a[n] and b[n]; wtot holds 2 x SCAN_NT/32 ints
+constexpr int SCAN_NT = 256;
 __device__ __forceinline__ void block_exclusive_scan2(int* a, int* b, int n, int* wtot) {
     const int tid = threadIdx.x;
     const int per = (n + SCAN_NT - 1) / SCAN_NT;
@@ -703,16 +702,19 @@ __device__ __forceinline__ void block_exclusive_scan2(int* a, int* b, int n, int
         const int yb = __shfl_up_sync(0xffffffffu, inc_b, o);
         if ((tid & 31) >= o) { inc_a += ya; inc_b += yb; }
     }
-    __syncthreads();
     if ((tid & 31) == 31) { wtot[tid >> 5] = inc_a; wtot[SCAN_NT / 32 + (tid >> 5)] = inc_b; }
     __syncthreads();
-    if (tid < 2) {
-        int acc = 0;
-        for (int w = 0; w < SCAN_NT / 32; ++w) {
-            const int t = wtot[tid * (SCAN_NT / 32) + w];
-            wtot[tid * (SCAN_NT / 32) + w] = acc;
-            acc += t;
+    if (tid < 64) {
+        // exclusive scans of the warp totals: warp 0 for a, warp 1 for b
+        int* w = wtot + (tid >> 5) * (SCAN_NT / 32);
+        const int l = tid & 31;
+        const int t = l < SCAN_NT / 32 ? w[l] : 0;
+        int x = t;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (l >= o) x += y;
         }
+        if (l < SCAN_NT / 32) w[l] = x - t;
     }
     __syncthreads();
     int base_a = wtot[tid >> 5] + inc_a - own_a, base_b = wtot[SCAN_NT / 32 + (tid >> 5)] + inc_b - own_b;
@@ -726,8 +728,21 @@ __device__ __forceinline__ void block_exclusive_scan2(int* a, int* b, int n, int
     }
     if (tid == SCAN_NT - 1) { a[n] = base_a; b[n] = base_b; }
 }
-__global__ void __launch_bounds__(SCAN_NT) k_scan_cells(const __grid_constant__ Batch B) {
+
+// The render warps' list offsets, one small CTA per evaluation right after the
+// render (it fits beside the near-edge pass): the per-render-warp staged and
+// near-core counts scanned in place into offsets, totals at the end (the near-edge
+// pass changes neither count)
+__global__ void __launch_bounds__(SCAN_NT) k_scan_warps(const __grid_constant__ Batch B) {
     const EvalArgs& E = B.e[blockIdx.x];
+    __shared__ int wtot[2 * (SCAN_NT / 32)];
+    block_exclusive_scan2(E.useg, E.nseg, E.n_cta_r * (CTA_R / 32), wtot);
+}
+
+// S11's cell offsets: the exclusive scan of the per-cell ray counts by one CTA of
+// SCAN_NT threads, after the near-edge pass (the last counts)
+__device__ __forceinline__ void cell_offsets(const EvalArgs& E) {
+    __shared__ int wtot[SCAN_NT / 32];
     const int nc = (E.n_src - 1) * (E.n_src - 1);
     const int per = (nc + SCAN_NT - 1) / SCAN_NT;
     const int tid = threadIdx.x;
@@ -741,12 +756,16 @@ __global__ void __launch_bounds__(SCAN_NT) k_scan_cells(const __grid_constant__ 
         int y = __shfl_up_sync(0xffffffffu, incl, o);
         if ((tid & 31) >= o) incl += y;
     }
-    __shared__ int wtot[SCAN_NT / 32];
     if ((tid & 31) == 31) wtot[tid >> 5] = incl;
     __syncthreads();
-    if (tid == 0) {
-        int acc = 0;
-        for (int w = 0; w < SCAN_NT / 32; ++w) { int t = wtot[w]; wtot[w] = acc; acc += t; }
+    if (tid < 32) {
+        const int t = tid < SCAN_NT / 32 ? wtot[tid] : 0;
+        int x = t;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (tid >= o) x += y;
+        }
+        if (tid < SCAN_NT / 32) wtot[tid] = x - t;
     }
     __syncthreads();
     int base = wtot[tid >> 5] + incl - own;
@@ -758,94 +777,190 @@ __global__ void __launch_bounds__(SCAN_NT) k_scan_cells(const __grid_constant__ 
     if (tid == SCAN_NT - 1) off[nc] = base;
 }
 
-// exclusive scans of the per-render-warp staged and near-core counts (what the
-// compaction needs; the cell offsets are the render adjoint's)
-__global__ void __launch_bounds__(SCAN_NT) k_scan_warps(const __grid_constant__ Batch B) {
-    const EvalArgs& E = B.e[blockIdx.x];
-    __shared__ int wtot[2 * (SCAN_NT / 32)];
-    // the cell cursors the compaction ranks the rays with (before it, on its stream)
-    const int nc = (E.n_src - 1) * (E.n_src - 1);
-    for (int c = threadIdx.x; c < nc; c += SCAN_NT) E.cursor[c] = 0;
-    block_exclusive_scan2(E.useg, E.nseg, E.n_cta_r * (CTA_R / 32), wtot);
-}
-
 // The adjoint's rays: the staged rays of all render warps in warp order (ray k
 // of warp u at useg[u] + its position), i.e. in ray order, gathered into flat
-// arrays (ray id, or -1 for a deferred ray that ended outside; cell, or -2 - cell
-// for a near-core ray of the float path), one warp per render warp, coalesced.
-// The near-core rays' adjoint positions go to nlist in the same order (warp u's
-// at nseg[u] on), for the adjoint's separate double-precision pass.  The warp
-// loads up to four groups of 32 entries before it stores any (the loads would
-// otherwise wait for the previous group's stores).
+// arrays (ray id; cell, or -2 - cell for a near-core ray of the float path; the ray's
+// rank inside its cell, from an atomic on the cell's cursor, zeroed with the counts:
+// the counting sort's slot is the cell's offset plus the rank), coalesced.  It runs
+// right after the render, beside the near-edge pass: the rays that pass defers
+// (STG_DEFER: their cells are decided there) are left to k_compact_deferred.  The
+// near-core rays' adjoint positions go to nlist in the same order (warp u's at
+// nseg[u] on), for the adjoint's separate double-precision pass; near-core rays are
+// always deferred, so their cells come from k_compact_deferred too.
+// CMP_CTAS CTAs per evaluation (one wave); each warp takes an equal share of
+// consecutive list positions (the rays cluster in the few render tiles the grid's
+// reach leaves unculled, so shares by render warp would be uneven) and walks the
+// render warps it overlaps: it finds the first with a 32-wide probe of the offsets,
+// and the near-core entries before its share in that warp with one strided count.
+// It loads up to four groups of 32 entries before it stores any and keeps their slot
+// atomics in flight together.
 constexpr int CMP_NT = 256;
+constexpr int CMP_CTAS = 20;
+// the largest u in [from, nu) with useg[u] <= pos (useg non-decreasing, useg[from] <= pos),
+// by a 32-ary search: the warp's lanes probe 32 evenly spaced offsets of the range
+// and keep the segment below the first one past pos (about log_32(nu) rounds)
+__device__ __forceinline__ int cmp_find_warp(const int* useg, int nu, int from, int pos) {
+    const int lane = threadIdx.x & 31;
+    int lo = from, n = nu - from;            // answer in [lo, lo + n)
+    while (n > 1) {
+        const int step = (n + 31) / 32;
+        const int v = lo + lane * step;
+        const bool past = lane > 0 && (v >= lo + n || useg[v] > pos);
+        const unsigned pm = __ballot_sync(0xffffffffu, past);
+        const int k = pm ? __ffs(pm) - 1 : 32;  // probes 0..k-1 are not past pos
+        lo += (k - 1) * step;
+        n = min(step, n - (k - 1) * step);
+    }
+    return lo;
+}
 __global__ void __launch_bounds__(CMP_NT) k_compact(const __grid_constant__ Batch B) {
     const int ev = find_eval(B, blockIdx.x);
     const EvalArgs& E = B.e[ev];
     const int tile = blockIdx.x - B.tile0[ev];
     const int lane = threadIdx.x & 31;
+    constexpr int NWC = CMP_NT / 32;
     const int nu = E.n_cta_r * (CTA_R / 32);
-    const int u = tile * (CMP_NT / 32) + (threadIdx.x >> 5);
     if (E.transform == RTU_TRANSFORM_LINEAR) {
         // the unsmoothed eCDF's position gradients, accumulated by k_render_adj
-        const int nt = (nu + CMP_NT / 32 - 1) / (CMP_NT / 32);
-        for (int i = tile * CMP_NT + threadIdx.x; i < 4 * E.n_mask; i += nt * CMP_NT) E.gk[i] = 0ull;
+        for (int i = tile * CMP_NT + threadIdx.x; i < 4 * E.n_mask; i += CMP_CTAS * CMP_NT) E.gk[i] = 0ull;
     }
-    if (u >= nu) return;
     const int cap = 32 * E.s * E.s;
     const int n_rays = E.n_img * E.n_img * E.s * E.s;
     const int ncell = (E.n_src - 1) * (E.n_src - 1);
-    const int o = E.useg[u];
-    const int cnt = max(0, min(min(E.useg[u + 1] - o, cap), n_rays - o));
-    const int* stg = E.cell + (size_t)u * cap;
-    int nat = E.nseg[u];
-    for (int g0 = 0; g0 < cnt; g0 += 128) {
-        int ent[4], cell[4], rank[4];
-        bool nr[4];
-        unsigned grp[4];
+    const int s2 = E.s * E.s;
+    const float inv_s2 = 1.0f / (float)s2;
+    const int total = max(0, min(E.useg[nu], n_rays));
+    const int nw = CMP_CTAS * NWC, w = tile * NWC + (threadIdx.x >> 5);
+    const int share = (total + nw - 1) / nw;
+    const int lo = min(total, w * share), hi = min(total, lo + share);
+    if (lo >= hi) return;
+    int u = cmp_find_warp(E.useg, nu, 0, lo);
+    // near-core entries of warp u before position lo (lanes count strided entries)
+    int nat;
+    {
+        const int* stg = E.cell + (size_t)u * cap;
+        const int i0 = min(lo - E.useg[u], cap);
+        int c = 0;
+        for (int i0k = 0; i0k < i0; i0k += 32 * 8) {
+            int e8[8];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int i = g0 + 32 * j + lane;
-            ent[j] = i < cnt ? stg[i] : 0;
-        }
-        // decode the four groups, then their rank atomics (the ray's rank inside its
-        // cell, the counting sort's slot in any order: the cell sums are exact integer
-        // sums; one atomic per group of lanes sharing the cell, ranks by lane order),
-        // all four in flight before any result is used
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int i = g0 + 32 * j + lane;
-            cell[j] = -1;
-            nr[j] = false;
-            if (i < cnt) {
-                const int e = ent[j];
-                int c = ((e & (STG_NEAR - 1)) >> STG_SHIFT) - 1;
-                cell[j] = c >= ncell ? -1 : c;
-                nr[j] = (e & STG_NEAR) != 0;
+            for (int k = 0; k < 8; ++k) {
+                const int i = i0k + 32 * k + lane;
+                e8[k] = i < i0 ? stg[i] : 0;
             }
-            const unsigned act = __ballot_sync(0xffffffffu, cell[j] >= 0);
-            grp[j] = cell[j] >= 0 ? __match_any_sync(act, cell[j]) : 0u;
-            rank[j] = 0;
-            if (cell[j] >= 0 && lane == __ffs(grp[j]) - 1) rank[j] = atomicAdd(E.cursor + cell[j], __popc(grp[j]));
-        }
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int i = g0 + 32 * j + lane;
-            if (g0 + 32 * j >= cnt) break;
-            const int leader = cell[j] >= 0 ? __ffs(grp[j]) - 1 : lane;
-            const int b = __shfl_sync(0xffffffffu, rank[j], leader);
-            if (i < cnt) {
-                const int e = ent[j];
-                E.kray[o + i] = cell[j] >= 0 ? staged_ray_id(E.n_img, E.s * E.s, u, e & ((1 << STG_SHIFT) - 1)) : -1;
-                E.kcell[o + i] = nr[j] && cell[j] >= 0 ? -2 - cell[j] : cell[j];
-                if (cell[j] >= 0) E.krank[o + i] = b + __popc(grp[j] & ((1u << lane) - 1u));
-            }
-            // every flagged entry keeps its list slot (counted by the render); one
-            // that the double pass found outside the grid lists -1
-            const unsigned bn = __ballot_sync(0xffffffffu, nr[j]);
-            const int at = nat + __popc(bn & ((1u << lane) - 1u));
-            if (nr[j] && at >= 0 && at < n_rays) E.nlist[at] = cell[j] >= 0 ? o + i : -1;
-            nat += __popc(bn);
+            for (int k = 0; k < 8; ++k) c += (e8[k] & STG_NEAR) ? 1 : 0;
         }
+        nat = E.nseg[u] + (int)__reduce_add_sync(0xffffffffu, (unsigned)c);
+    }
+    // the pixel of each lane of render warp u: a staged entry's ray is the pixel of its
+    // lane (one shuffle) times s^2 plus its sub-ray
+    auto lane_pixel = [&](int uu) {
+        bool valid;
+        return render_pixel(E.n_img, uu / (CTA_R / 32), (uu % (CTA_R / 32)) * 32 + lane, valid);
+    };
+    int pix = lane_pixel(u);
+    int pos = lo;
+    while (pos < hi) {
+        if (u + 1 < nu && E.useg[u + 1] <= pos) {
+            u = cmp_find_warp(E.useg, nu, u + 1, pos);
+            nat = E.nseg[u];
+            pix = lane_pixel(u);
+        }
+        const int o = E.useg[u];
+        const int end = min(hi, min(u + 1 < nu ? E.useg[u + 1] : total, o + cap));
+        if (end <= pos) break;          // inconsistent offsets: leave the rest unwritten
+        const int* stg = E.cell + (size_t)u * cap;
+        for (int g0 = pos - o; g0 < end - o; g0 += 128) {
+            const int gend = end - o;
+            int ent[4], cell[4], slot[4];
+            bool nr[4];
+            unsigned grp[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int i = g0 + 32 * j + lane;
+                ent[j] = i < gend ? stg[i] : 0;
+            }
+            // decode the four groups, then their slot atomics (one per group of lanes
+            // sharing the cell, slots by lane order inside the group; the order of the
+            // records inside a cell is free: the cell sums are exact integer sums), all
+            // four in flight before any result is used
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int i = g0 + 32 * j + lane;
+                cell[j] = -1;
+                nr[j] = false;
+                if (i < gend) {
+                    const int e = ent[j];
+                    int c = ((e & (STG_NEAR - 1)) >> STG_SHIFT) - 1;
+                    cell[j] = c >= ncell || (e & STG_DEFER) ? -1 : c;
+                    nr[j] = (e & STG_NEAR) != 0;
+                }
+                const unsigned act = __ballot_sync(0xffffffffu, cell[j] >= 0);
+                grp[j] = cell[j] >= 0 ? __match_any_sync(act, cell[j]) : 0u;
+                slot[j] = 0;
+                if (cell[j] >= 0 && lane == __ffs(grp[j]) - 1) slot[j] = atomicAdd(E.cursor + cell[j], __popc(grp[j]));
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int i = g0 + 32 * j + lane;
+                if (g0 + 32 * j >= gend) break;
+                const int leader = cell[j] >= 0 ? __ffs(grp[j]) - 1 : lane;
+                const int b = __shfl_sync(0xffffffffu, slot[j], leader);
+                // the entry's render lane (local / s^2, exact in float: local < 32 s^2)
+                const int local = ent[j] & ((1 << STG_SHIFT) - 1);
+                const int le = min(31, (int)(((float)local + 0.5f) * inv_s2));
+                const int ppix = __shfl_sync(0xffffffffu, pix, le);
+                if (i < gend && !(ent[j] & STG_DEFER)) {
+                    const int c = cell[j];
+                    E.kray[o + i] = c >= 0 ? ppix * s2 + (local - le * s2) : -1;
+                    E.kcell[o + i] = c;
+                    if (c >= 0) E.krank[o + i] = b + __popc(grp[j] & ((1u << lane) - 1u));
+                }
+                // every flagged entry keeps its list slot (counted by the render); one
+                // that the double pass found outside the grid lists -1
+                const unsigned bn = __ballot_sync(0xffffffffu, nr[j]);
+                const int at = nat + __popc(bn & ((1u << lane) - 1u));
+                if (nr[j] && at >= 0 && at < n_rays) E.nlist[at] = o + i;
+                nat += __popc(bn);
+            }
+        }
+        pos = end;
+    }
+}
+
+// The rays the near-edge pass decided (STG_DEFER), after it: their flat-array
+// entries at list position useg[u] + i of staging position u cap + i, from the decided
+// entry (ray id, or -1 for a ray that ended outside the grid; cell, or -2 - cell for a
+// near-core ray; the rank from the cell's cursor), one thread per deferred ray over
+// n_edge CTAs per evaluation; one more CTA computes S11's cell offsets meanwhile.
+constexpr int CMPD_NT = SCAN_NT;
+__global__ void __launch_bounds__(CMPD_NT) k_compact_deferred(const __grid_constant__ Batch B) {
+    const int ev = find_eval(B, blockIdx.x);
+    const EvalArgs& E = B.e[ev];
+    const int tile = blockIdx.x - B.tile0[ev];
+    if (tile == E.n_edge) {
+        cell_offsets(E);
+        return;
+    }
+    const int s2 = E.s * E.s, cap = 32 * s2;
+    const int n_rays = E.n_img * E.n_img * s2;
+    const int ncell = (E.n_src - 1) * (E.n_src - 1);
+    const int nu = E.n_cta_r * (CTA_R / 32);
+    const int cnt = min(*E.ecount, n_rays);
+    for (int j = tile * CMPD_NT + threadIdx.x; j < cnt; j += E.n_edge * CMPD_NT) {
+        const int at = E.elist[j];
+        const int u = at / cap, i = at - u * cap;
+        if (u < 0 || u >= nu) continue;
+        const int e = E.cell[at];
+        const int k = E.useg[u] + i;
+        if (k < 0 || k >= n_rays) continue;
+        int c = ((e & (STG_NEAR - 1)) >> STG_SHIFT) - 1;
+        if (c >= ncell) c = -1;
+        const bool nr = (e & STG_NEAR) != 0;
+        E.kray[k] = c >= 0 ? staged_ray_id(E.n_img, s2, u, e & ((1 << STG_SHIFT) - 1)) : -1;
+        E.kcell[k] = nr && c >= 0 ? -2 - c : c;
+        if (c >= 0) E.krank[k] = atomicAdd(E.cursor + c, 1);
     }
 }
 

@@ -115,7 +115,9 @@ size_t slot_layout(const rtu_system_desc& d, char* base, EvalArgs* e) {
     p = take(8 * 8);                                  if (e) e->mom = (double*)p;
     p = take(16);                                     if (e) e->ccnt = (int*)p;
     p = take((size_t)2 * z.nm_max * 4);               if (e) e->cbin = (int*)p;
-    p = take((size_t)(z.n_cta_c_max + 1) * z.nl * 8); if (e) e->cadj = (double*)p;
+    p = take((size_t)(z.n_cta_c_max + 2) * z.nl * 8); if (e) e->cadj = (double*)p;
+    p = take((size_t)4 * MAXM * z.nl * 8);           if (e) e->jsel = (double*)p;
+
     p = take((size_t)2 * HB * 4);                     if (e) e->hist = (int*)p;
     p = take((size_t)tr_size(z.K) * 8);               if (e) e->trd = (double*)p;
     p = take((size_t)tr_size(z.K) * 4);               if (e) e->trf = (float*)p;
@@ -124,7 +126,7 @@ size_t slot_layout(const rtu_system_desc& d, char* base, EvalArgs* e) {
     const size_t n2 = (size_t)d.n_src * d.n_src;
     p = take(n2 * 2 * 8);                             if (e) e->cbufA = p;     // complex double (the GP source)
     p = take(n2 * 2 * z.tb);                          if (e) e->cbufB = p;
-    p = take((size_t)(d.n_src + GP_LINES - 1) / GP_LINES * 4 * 8); if (e) e->gpart = (double*)p;
+    p = take((size_t)gp_part_rows(d.n_src) * 4 * 8); if (e) e->gpart = (double*)p;
     p = take(n2 * z.tb);                              if (e) e->fld = p;
     p = take(n2 * z.tb);                              if (e) e->src = p;
     const size_t ni = (size_t)d.n_img * d.n_img;
@@ -135,6 +137,7 @@ size_t slot_layout(const rtu_system_desc& d, char* base, EvalArgs* e) {
     p = take((size_t)z.n_cta_r * CTA_R * d.s_super * d.s_super * 4); if (e) e->cell = (int*)p;
     p = take((size_t)(2 * z.ncell + 1) * 4);          if (e) e->ccount = (int*)p;
     p = take((size_t)z.ncell * 4);                    if (e) e->cursor = (int*)p;
+    p = take((size_t)z.n_rays * 4);                   if (e) e->elist = (int*)p;
     p = take((size_t)z.n_rays * 4 * z.tb);            if (e) e->rec = p;
     p = take((size_t)z.ncell * 4 * 2 * z.tb);         if (e) e->corner = p;
     // partial rows for the largest tunable adjoint split (one CTA per CTA_R ADJ_RPT rays)
@@ -309,6 +312,8 @@ constexpr int MAX_DYN = 200 * 1024;
 void set_attributes() {
     cudaFuncSetAttribute(k_select_fit, cudaFuncAttributeMaxDynamicSharedMemorySize, SEL_SMEM);
     cudaFuncSetAttribute(k_render<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN);
+    cudaFuncSetAttribute(k_gp_adj_cluster<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GP_CL_SMEM_MAX);
+    cudaFuncSetAttribute(k_gp_adj_cluster<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GP_CL_SMEM_MAX);
     // 8 CTAs per SM at the c2 shape (24 KB each): the largest shared-memory carveout
     cudaFuncSetAttribute(k_render<float, false>, cudaFuncAttributePreferredSharedMemoryCarveout,
                          cudaSharedmemCarveoutMaxShared);
@@ -354,9 +359,11 @@ __global__ void __launch_bounds__(256) k_zero(const __grid_constant__ Batch B, i
     const int tile = blockIdx.x - B.tile0[ev];
     const int nh = 2 * HB;
     const int ncell = (E.n_src - 1) * (E.n_src - 1);
-    const int tot = nh + (with_cells ? ncell : 0);
+    const int tot = nh + (with_cells ? 2 * ncell : 0);
     for (int i = tile * 256 + threadIdx.x; i < tot; i += ZERO_TILES * 256) {
-        if (i < nh) E.hist[i] = 0; else E.ccount[i - nh] = 0;
+        if (i < nh) E.hist[i] = 0;
+        else if (i < nh + ncell) E.ccount[i - nh] = 0;
+        else E.cursor[i - nh - ncell] = 0;          // the compaction's rank cursors
     }
     if (tile == 0) {
         if (threadIdx.x == 0) {
@@ -587,7 +594,7 @@ typedef int (*TileFn)(const EvalArgs&);
 
 // ---- optional per-kernel event timing
 struct ProfRec { const char* name; cudaEvent_t a, b; int side; };
-cudaStream_t g_side_hint[2] = {nullptr, nullptr};   // the side streams of the launching thread (timeline)
+cudaStream_t g_side_hint = nullptr;   // the side stream of the launching thread (timeline)
 std::mutex g_prof_mu;
 bool g_prof_on = false;
 std::vector<ProfRec> g_prof_pending;
@@ -600,7 +607,7 @@ rtu_status launch(const char* name, Kern kern, Batch& B, TileFn tiles, int threa
     for (int i = 0; i < B.n; ++i) { B.tile0[i] = tot; tot += tiles(B.e[i]); }
     B.tile0[B.n] = tot;
     if (tot == 0) return RTU_OK;
-    ProfRec pr{name, nullptr, nullptr, st == nullptr ? 0 : (st == g_side_hint[0] ? 1 : (st == g_side_hint[1] ? 2 : 0))};
+    ProfRec pr{name, nullptr, nullptr, st == nullptr ? 0 : (st == g_side_hint ? 1 : 0)};
     const bool prof = g_prof_on;
     if (prof) {
         cudaEventCreate(&pr.a);
@@ -637,6 +644,11 @@ int t_adj_lin(const EvalArgs& e) { return is_lin(e) ? e.n_cta_adj : 0; }
 int t_near_fit(const EvalArgs& e) { return is_lin(e) ? 0 : e.n_near; }
 int t_near_lin(const EvalArgs& e) { return is_lin(e) ? e.n_near : 0; }
 int t_gp_lines(const EvalArgs& e) { return (e.n_src + GP_LINES - 1) / GP_LINES; }
+// the GP adjoint's cluster kernel where it fits (per storage type), else the line passes
+int t_gp_cl_f(const EvalArgs& e) { return gp_cluster_ok(e.n_src, 4) ? GP_CL : 0; }
+int t_gp_cl_d(const EvalArgs& e) { return gp_cluster_ok(e.n_src, 8) ? GP_CL : 0; }
+int t_gp_lines_f(const EvalArgs& e) { return gp_cluster_ok(e.n_src, 4) ? 0 : t_gp_lines(e); }
+int t_gp_lines_d(const EvalArgs& e) { return gp_cluster_ok(e.n_src, 8) ? 0 : t_gp_lines(e); }
 int t_zero(const EvalArgs&) { return ZERO_TILES; }
 int t_centre(const EvalArgs& e) { return e.n_cta_c; }
 int t_adj(const EvalArgs& e) { return e.n_cta_adj; }
@@ -644,7 +656,8 @@ int t_psf_gen(const EvalArgs& e) { return e.psf_uv ? 0 : e.n_cta_p; }
 int t_psf_sep(const EvalArgs& e) { return e.psf_uv ? e.n_cta_p : 0; }
 int t_edge(const EvalArgs& e) { return e.n_edge; }
 int t_cull_lin(const EvalArgs& e) { return is_lin(e) ? (e.n_cta_r + CULL_NT - 1) / CULL_NT : 0; }
-int t_units(const EvalArgs& e) { return (e.n_cta_r * (CTA_R / 32) + CMP_NT / 32 - 1) / (CMP_NT / 32); }
+int t_units(const EvalArgs&) { return CMP_CTAS; }
+int t_defer(const EvalArgs& e) { return e.n_edge + 1; }
 int t_cells(const EvalArgs& e) {
     const int nc = (e.n_src - 1) * (e.n_src - 1);
     return (nc + GATHER_NT / 16 - 1) / (GATHER_NT / 16);
@@ -652,17 +665,17 @@ int t_cells(const EvalArgs& e) {
 
 enum Phase { PH_GRID = 1, PH_FORWARD = 2, PH_ADJOINT = 4 };
 
-// Two side streams per (host thread, device), created at the highest stream priority,
-// carry the step's critical branch where the step forks: the grid build (S1-S5) beside
-// the GP source of the forward, and the transform / centre-ray adjoint beside the cell
-// gather and GP adjoint of the adjoint (its selected-rank and centre-ray kernels on one
-// side stream each).  Fork and join are event waits, so a call still orders everything
+// A side stream per (host thread, device), created at the highest stream priority,
+// carries the step's critical branch where the step forks: the grid build (S1-S5)
+// beside the GP source of the forward (then the selected-rank lens Jacobians beside
+// the render), the adjoint's ray list beside the forward's PSF and likelihood, and the
+// transform / centre-ray adjoint beside the cell gather and GP adjoint of the adjoint.  Fork and join are event waits, so a call still orders everything
 // after the work already on the caller's stream and leaves nothing pending on the side
 // streams when it returns (and the pattern is legal inside CUDA graph capture).
 // Created at the first call on a device and kept for the life of the thread.
 struct SideStream {
-    cudaStream_t s = nullptr, s2 = nullptr;
-    cudaEvent_t fork = nullptr, join = nullptr, fork2 = nullptr, join2 = nullptr;
+    cudaStream_t s = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
 };
 constexpr int MAX_DEV = 64;
 
@@ -677,11 +690,8 @@ rtu_status side_stream(SideStream*& out) {
         int least = 0, greatest = 0;
         if ((ce = cudaDeviceGetStreamPriorityRange(&least, &greatest)) != cudaSuccess ||
             (ce = cudaStreamCreateWithPriority(&ss.s, cudaStreamNonBlocking, greatest)) != cudaSuccess ||
-            (ce = cudaStreamCreateWithPriority(&ss.s2, cudaStreamNonBlocking, greatest)) != cudaSuccess ||
             (ce = cudaEventCreateWithFlags(&ss.fork, cudaEventDisableTiming)) != cudaSuccess ||
-            (ce = cudaEventCreateWithFlags(&ss.join, cudaEventDisableTiming)) != cudaSuccess ||
-            (ce = cudaEventCreateWithFlags(&ss.fork2, cudaEventDisableTiming)) != cudaSuccess ||
-            (ce = cudaEventCreateWithFlags(&ss.join2, cudaEventDisableTiming)) != cudaSuccess)
+            (ce = cudaEventCreateWithFlags(&ss.join, cudaEventDisableTiming)) != cudaSuccess)
             return fail(RTU_E_CUDA, std::string("side stream: ") + cudaGetErrorString(ce));
     }
     out = &ss;
@@ -728,34 +738,40 @@ rtu_status run_chunk(Batch& B, int phase, cudaStream_t st, const SideStream& ss)
     }
     if (phase & PH_FORWARD) {
         if ((r = stream_after(st, ss.s, ss.join))) return r;
+        // the selected-rank lens Jacobians (for the adjoint) beside the render
+        if ((r = launch("k_sel_jac", k_sel_jac, B, t_one_fit, SEL_ADJ_NT, 0, ss.s))) return r;
+
         const size_t render_smem = grid_bytes + (size_t)CTA_R * max_s2 * 2;
         if (render_smem > MAX_DYN) return fail(RTU_E_ARG, "render shared memory exceeds the limit");
         if ((r = launch("k_render", k_render<T, false>, B, t_render_fit, CTA_R, render_smem, st))) return r;
         if ((r = launch("k_render", k_render<T, true>, B, t_render_lin, CTA_R, render_smem, st))) return r;
+        // the adjoint's ray list (the adjoint follows the forward on the same slots) on
+        // the side stream: the render warps' offsets and the compaction of the rays the
+        // render decided beside the near-edge pass, then the rays that pass decides and
+        // S11's cell offsets beside the lens light, the PSF and the likelihood
+        if ((r = stream_after(ss.s, st, ss.fork))) return r;
+        if ((r = launch("k_scan_warps", k_scan_warps, B, t_one, SCAN_NT, 0, ss.s))) return r;
+        if ((r = launch("k_compact", k_compact, B, t_units, CMP_NT, 0, ss.s))) return r;
         if (sizeof(T) == 4 && (r = launch("k_render_edge", k_render_edge, B, t_edge, EDGE_NT, 0, st))) return r;
+        if ((r = stream_after(ss.s, st, ss.fork))) return r;
+        if ((r = launch("k_compact_deferred", k_compact_deferred, B, t_defer, CMPD_NT, 0, ss.s))) return r;
         if (any_light && (r = launch("k_light_fwd", k_light_fwd<T>, B, t_light_fwd, LIGHT_FWD_NT, 0, st))) return r;
         if ((r = launch("k_psf_like", k_psf_like_sep<T>, B, t_psf_sep, PSFS_NT, 0, st))) return r;
         if (sizeof(T) == 4 && maxPsf <= 9) r = launch("k_psf_like", k_psf_like_t<9>, B, t_psf_gen, PSFT_NT, 0, st);
         else if (sizeof(T) == 4 && maxPsf <= 21) r = launch("k_psf_like", k_psf_like_t<21>, B, t_psf_gen, PSFT_NT, 0, st);
         else r = launch("k_psf_like", k_psf_like<T>, B, t_psf_gen, PSF_NT, 0, st);
         if (r) return r;
+        if ((r = stream_after(st, ss.s, ss.join))) return r;
     }
     if (phase & PH_ADJOINT) {
         const size_t adj = grid_bytes + (size_t)(CTA_R / 32) * 4 * maxK * 2 * sizeof(T);
         if (adj > MAX_DYN) return fail(RTU_E_ARG, "adjoint shared memory exceeds the limit");
-        // the adjoint's ray list (side stream, from the forward's counts and staging)
-        // beside the PSF and lens-light adjoints and the cell offsets (main)
-        if ((r = stream_after(ss.s, st, ss.fork))) return r;
-        if ((r = launch("k_scan_warps", k_scan_warps, B, t_one, SCAN_NT, 0, ss.s))) return r;
-        if ((r = launch("k_compact", k_compact, B, t_units, CMP_NT, 0, ss.s))) return r;
         if ((r = launch("k_psf_adj", k_psf_adj_sep<T>, B, t_psf_sep, PSFS_NT, 0, st))) return r;
         if (sizeof(T) == 4 && maxPsf <= 9) r = launch("k_psf_adj", k_psf_adj_t<9>, B, t_psf_gen, PSFT_NT, 0, st);
         else if (sizeof(T) == 4 && maxPsf <= 21) r = launch("k_psf_adj", k_psf_adj_t<21>, B, t_psf_gen, PSFT_NT, 0, st);
         else r = launch("k_psf_adj", k_psf_adj<T>, B, t_psf_gen, PSF_NT, 0, st);
         if (r) return r;
         if (any_light && (r = launch("k_light_adj", k_light_adj<T>, B, t_light, CTA_R, 0, st))) return r;
-        if ((r = launch("k_scan_cells", k_scan_cells, B, t_one, SCAN_NT, 0, st))) return r;
-        if ((r = stream_after(st, ss.s, ss.join))) return r;
         if (sizeof(T) == 4) {
             // the near-core rays' double-precision pass on the side stream, beside the
             // float pass (disjoint partial rows, records and subhalo entries)
@@ -769,20 +785,24 @@ rtu_status run_chunk(Batch& B, int phase, cudaStream_t st, const SideStream& ss)
         if ((r = launch("k_render_adj", k_render_adj<T, true, false>, B, t_adj_lin, CTA_R, adj, st))) return r;
         if (sizeof(T) == 4 && (r = stream_after(st, ss.s, ss.join))) return r;
         if (any_sub && (r = launch("k_sub_adj", k_sub_adj<T>, B, t_adj, CTA_R, 0, st))) return r;
-        // transform and centre-ray adjoint (the critical branch, side streams: the
-        // selected-rank terms beside the centre rays) beside the cell gather and GP
-        // adjoint (main)
+        // transform and centre-ray adjoint (the critical branch, side stream) beside
+        // the cell gather and GP adjoint (main)
         if ((r = stream_after(ss.s, st, ss.fork))) return r;
         if ((r = launch("k_cdf_adj", k_cdf_adj, B, t_two_fit, CDF_NT, 0, ss.s))) return r;
-        if ((r = stream_after(ss.s2, ss.s, ss.fork2))) return r;
-        if ((r = launch("k_sel_adj", k_sel_adj, B, t_one_fit, SEL_ADJ_NT, 0, ss.s2))) return r;
         if ((r = launch("k_centre_adj", k_centre_adj<T>, B, t_centre_fit, CTA_C, 0, ss.s))) return r;
         if ((r = launch("k_lin_centre_adj", k_lin_centre_adj, B, t_centre_lin, CTA_C, 0, ss.s))) return r;
         if ((r = launch("k_cell_gather", k_cell_gather<T>, B, t_cells, GATHER_NT, 0, st))) return r;
+        // the GP adjoint: one cluster per evaluation where its lines fit, else line passes
+        size_t gp_cl = 0;
+        for (int i = 0; i < B.n; ++i)
+            if (gp_cluster_ok(B.e[i].n_src, (int)sizeof(T))) gp_cl = std::max(gp_cl, gp_cluster_bytes(B.e[i].n_src, (int)sizeof(T)));
+        if ((r = launch("k_gp_adjoint", k_gp_adj_cluster<T>, B, sizeof(T) == 4 ? t_gp_cl_f : t_gp_cl_d, GP_CL_NT, gp_cl, st)))
+            return r;
         for (int pass = 0; pass < GP_PASSES; ++pass)
-            if ((r = launch("k_gp_adjoint", k_gp_adj_lines<T>, B, t_gp_lines, GP_LINE_NT, 0, st, pass))) return r;
+            if ((r = launch("k_gp_adjoint", k_gp_adj_lines<T>, B, sizeof(T) == 4 ? t_gp_lines_f : t_gp_lines_d, GP_LINE_NT,
+                            0, st, pass)))
+                return r;
         if ((r = stream_after(st, ss.s, ss.join))) return r;
-        if ((r = stream_after(st, ss.s2, ss.join2))) return r;
         if ((r = launch("k_grad_final", k_grad_final, B, t_one, GRAD_NT, 0, st))) return r;
     }
     return RTU_OK;
@@ -938,7 +958,7 @@ rtu_status run(rtu_system* const* sys, const rtu_eval* ev, int n, int phase, voi
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     SideStream* ss = nullptr;
     if (rtu_status r = side_stream(ss)) return r;
-    if (g_prof_on) { g_side_hint[0] = ss->s; g_side_hint[1] = ss->s2; }
+    if (g_prof_on) g_side_hint = ss->s;
     static thread_local Batch B;
     const bool replay = g_graphs_on.load(std::memory_order_relaxed) && !g_prof_on && !stream_capturing(st);
     for (int c0 = 0; c0 < n; c0 += MAXB) {

@@ -23,6 +23,7 @@ constexpr int CTA_C = 256;        // centre-ray kernels: rays per CTA
 constexpr int CTA_R = 128;        // render kernels: pixels per CTA (one thread each)
 constexpr int STG_SHIFT = 11;      // staged entry: low bits the ray within its render warp (< 32 * 64)
 constexpr int STG_NEAR = 1 << 28;  // staged entry: a near-core ray (traced in FP64 by the float path)
+constexpr int STG_DEFER = 1 << 29; // staged entry: a ray the near-edge pass decides (float path)
 constexpr int NEAR_CTAS = 4;       // float render adjoint: CTAs per evaluation for the near-core rays (default)
 constexpr int NEAR_CTAS_MAX = 16;  // the largest tuned value (the workspace holds its partial rows)
 constexpr int ADJ_DIV = 4;         // render adjoint: CTAs per evaluation = rays / (ADJ_DIV CTA_R ADJ_RPT) (default)
@@ -103,8 +104,9 @@ struct EvalArgs {
                        // likelihood kernel (whose last CTA finishes the forward) and of
                        // k_select_fit (whose last CTA tests the render tiles)
     int* cbin;         // [2][n_mask] level-1 histogram bin of each centre ray
-    double* cadj;      // [n_cta_c + 1][8 + 5 n_sub] centre-ray adjoint lens partials; the last
-                       // row the selected-rank terms
+    double* cadj;      // [n_cta_c + 2][8 + 5 n_sub] centre-ray adjoint lens partials; the last
+                       // two rows the selected-rank terms of each axis
+    double* jsel;      // [2][2 MAXM][8 + 5 n_sub] d beta_a / d lens of each selected-rank ray
     int* hist;         // [2][HB] level-1 histograms
     double* trd;       // transform, double (layout in tr_* helpers)
     float* trf;        // transform, float copy
@@ -124,7 +126,8 @@ struct EvalArgs {
                        // while a deferred ray is undecided, and after it ended outside;
                        // STG_NEAR set on the near-core rays of the float path
     int* ccount;       // [n_cells] ray counts, then [n_cells + 1] exclusive offsets
-    int* cursor;       // [n_cells]
+    int* cursor;       // [n_cells] the compaction's rank cursors (zeroed with the counts)
+    int* elist;        // [n_rays] staging positions of the deferred rays (float mode)
     void* rec;         // real4 [n_rays] counting-sorted (fx, fy, g, -) records
     void* corner;      // real2 [n_cells][4] per-cell bilinear corner sums (float: hi + lo pairs)
     double* apart;     // [nacc][n_row_adj] render-adjoint partials (column-major)
@@ -139,11 +142,11 @@ struct EvalArgs {
     float* rval;       // [n_rays] values of deferred rays (float mode)
     int* cta_cnt;      // [n_cta_r] in-grid rays per render CTA (the N_IN_GRID statistic)
     unsigned char* tcull;  // [n_cta_r] 1: no ray of the render tile can reach the grid
-    int* useg;         // [n_cta_r * CTA_R/32 + 1] staged rays per render warp, then exclusive offsets
+    int* useg;         // [n_cta_r * CTA_R/32 + 1] staged rays per render warp; the total at the end
     int* kray;         // [n_rays] the adjoint's rays (staged rays in render-warp order): ray id, or -1
     int* kcell;        // [n_rays] their cells; -2 - cell for a near-core ray of the float path
     int* krank;        // [n_rays] their ranks inside their cells (the counting sort's slot = offset + rank)
-    int* nseg;         // [n_cta_r * CTA_R/32 + 1] near-core staged rays per render warp, then offsets
+    int* nseg;         // [n_cta_r * CTA_R/32 + 1] near-core staged rays per render warp; the total at the end
     int* nlist;        // [n_rays] adjoint positions of the near-core rays, in adjoint order
     void* gbuf;        // real2 [n_rays] d logL / d beta of each adjoint ray (subhalo pass)
     const double* light;   // [6 n_light] MGE lens light (A, sigma, q, phi, x_n, y_n)
@@ -422,8 +425,8 @@ __device__ inline void lens_setup_par(LensK<double>* Kd, LensK<float>* Kf, const
         for (int v = 0; v < w; ++v) { A *= wA[v]; D += wD[v]; }
         double Ap = __shfl_up_sync(0xffffffffu, A, 1);          // A_{n-1}
         if (lane == 0) Ap = w == 0 ? 1.0 : wA[0] * (w == 2 ? wA[1] : 1.0);
-        epl_term(Kd->C.term[n], n, Ap, c, g, D);
-        epl_term(Kf->C.term[n], n, Ap, c, g, D);
+        epl_term(Kd->C.term[n], Ap, c, D);
+        epl_term(Kf->C.term[n], Ap, c, D);
         if (tid == 0) { epl_term0(Kd->C.term[0]); epl_term0(Kf->C.term[0]); }
         const double An = fabs(Ap * c);
         if (An <= 1e-16) atomicMin(&nt_sh[0], n);
@@ -531,9 +534,7 @@ __device__ inline void lensk_to_df(const LensK<double>& a, LensK<DF>& b) {
     const int nt = a.C.nterm;
     for (int i = threadIdx.x; i <= nt; i += blockDim.x) {
         b.C.term[i].a = DF(a.C.term[i].a);
-        b.C.term[i].h = DF(a.C.term[i].h);
         b.C.term[i].u = DF(a.C.term[i].u);
-        b.C.term[i].f = DF(a.C.term[i].f);
     }
     if (threadIdx.x == 0) {
         const EplC<double>& c = a.C;
@@ -543,6 +544,7 @@ __device__ inline void lensk_to_df(const LensK<double>& a, LensK<DF>& b) {
         d.pref0 = DF(c.pref0); d.lnb = DF(c.lnb); d.opq = DF(c.opq);
         d.f_q = DF(c.f_q); d.tb_bq = DF(c.tb_bq); d.tb_sq = DF(c.tb_sq); d.iopq = DF(c.iopq);
         d.qe1 = DF(c.qe1); d.qe2 = DF(c.qe2); d.pe1 = DF(c.pe1); d.pe2 = DF(c.pe2); d.ftail = DF(c.ftail);
+        d.ic = DF(c.ic);
         d.nterm = nt;
         b.g1 = DF(a.g1); b.g2 = DF(a.g2); b.rc2 = DF(a.rc2);
         b.nsub = 0; b.kind = a.kind; b.epl = a.epl;

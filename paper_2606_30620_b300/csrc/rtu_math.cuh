@@ -316,15 +316,16 @@ RTU_HD void nfw_deflect(const S& x, const S& y, const S& ks, const S& rs,
 // by Horner's rule (independent chains for the four sums of the adjoint).
 constexpr int EPL_MAXT = 96;
 
-// the coefficients of w^n, n = 0..nterm, of the four sums
+// the coefficients of w^n, n = 0..nterm, of the series sums
 //   S = sum Omega_n:              a_n = A_n
-//   H = sum (2n+1) Omega_n:       h_n = (2n+1) A_n
 //   U = sum D_n Omega_n:          u_n = D_n A_n, D_n = sum_{k <= n} d log|c_k| / dt
-//   F = sum n g_n Omega_{n-1} w:  f_n = n g_n A_{n-1}, g_n = c_n / f
-// one 16-byte (float) or two 16-byte (double) shared-memory loads per power
+// The two other sums of the derivatives follow from S and S' = dS/dw, since
+// A_n = f g_n A_{n-1} (g_n = c_n / f):
+//   H = sum (2n+1) Omega_n = S + 2 w S',   F = sum n g_n A_{n-1} w^n = w S' / f.
+// one 8-byte (float) or 16-byte (double) shared-memory load per power
 template <typename T>
-struct __align__(16) EplTerm {
-    T a, h, u, f;
+struct __align__(2 * sizeof(T) >= 16 ? 16 : 2 * sizeof(T)) EplTerm {
+    T a, u;
 };
 
 template <typename T>
@@ -334,6 +335,7 @@ struct EplC {
     // (t/b) db/dq, (t/b) db/dtheta_E, 1/(1+q), the (e1, e2) chain factors
     T f_q, tb_bq, tb_sq, iopq, qe1, qe2, pe1, pe2;
     T ftail;          // f / (1 - f): the series tail factor, f = (1 - q)/(1 + q)
+    T ic;             // 1 / f
     int nterm;        // highest power of w
     EplTerm<T> term[EPL_MAXT + 1];
 };
@@ -382,20 +384,19 @@ RTU_HD void epl_scalars(EplC<T>& C, const double* p, bool epl) {
     C.pe1 = (T)(0.5 * c2 * icc);                    // dphi/de2 coefficient: e1/(2 c^2)
     C.pe2 = (T)(0.5 * s2 * icc);                    // -dphi/de1 coefficient: e2/(2 c^2)
     C.ftail = (T)(cc / (1.0 - cc));                 // f/(1 - f), f = c
+    C.ic = (T)icc;                                  // 1/f
 }
 
-// coefficient n >= 1 of the four sums from A_{n-1} (running), c_n, g_n and D_n
+// coefficient n >= 1 of the two sums from A_{n-1} (running), c_n and D_n
 template <typename T>
-RTU_HD void epl_term(EplTerm<T>& tm, int n, double A_prev, double c, double g, double D) {
+RTU_HD void epl_term(EplTerm<T>& tm, double A_prev, double c, double D) {
     const double A = A_prev * c;
     tm.a = (T)A;
-    tm.h = (T)((2.0 * n + 1.0) * A);
     tm.u = (T)(D * A);
-    tm.f = (T)(n * g * A_prev);
 }
 template <typename T>
 RTU_HD void epl_term0(EplTerm<T>& tm) {
-    tm.a = T(1); tm.h = T(1); tm.u = T(0); tm.f = T(0);
+    tm.a = T(1); tm.u = T(0);
 }
 
 // p = theta_E, gamma, e1, e2, x0, y0 (gamma ignored unless epl); tol = size of the
@@ -414,7 +415,7 @@ RTU_HD void epl_setup(EplC<T>& C, const double* p, bool epl, double tol) {
         const double g = -(2.0 * n - 2.0 + t) / (2.0 * n + 2.0 - t);
         const double c = f * g;
         D += 1.0 / (2.0 * n - 2.0 + t) + 1.0 / (2.0 * n + 2.0 - t);
-        epl_term(C.term[n], n, A, c, g, D);
+        epl_term(C.term[n], A, c, D);
         A *= c;
         if (fabs(A) <= tol) break;
     }
@@ -523,36 +524,28 @@ RTU_HD void epl_eval(const EplC<T>& C, bool want_t, T x, T y, EplJ<T>& J) {
     r_sqrt_inv(R2, R, iR);
     const T cre = q * xr * iR, cim = yr * iR;
     const T wre = cre * cre - cim * cim, wim = T(2) * cre * cim;
-    // the four polynomials by Horner's rule, in one loop (independent chains)
+    // S, its derivative S' and U by Horner's rule, in one loop (independent chains;
+    // the derivative's step takes S's running value before S's own step)
     const int N = C.nterm;
-    T ar = C.term[N].a, ai = T(0), hr = C.term[N].h, hi = T(0);
-    T ur = C.term[N].u, ui = T(0), fr = C.term[N].f, fi = T(0);
-    // one Horner step of the four chains at term n
-    auto step4 = [&](int n) {
+    T ar = C.term[N].a, ai = T(0), dr = T(0), di = T(0);
+    T ur = C.term[N].u, ui = T(0);
+    // one Horner step of the three chains at term n
+    auto step3 = [&](int n) {
         const EplTerm<T> tm = C.term[n];
+        const T dr2 = dr * wre - di * wim + ar;
+        di = dr * wim + di * wre + ai;
+        dr = dr2;
         const T ar2 = ar * wre - ai * wim + tm.a;
         ai = ar * wim + ai * wre;
         ar = ar2;
-        const T hr2 = hr * wre - hi * wim + tm.h;
-        hi = hr * wim + hi * wre;
-        hr = hr2;
         if (want_t) {
             const T ur2 = ur * wre - ui * wim + tm.u;
             ui = ur * wim + ui * wre;
             ur = ur2;
         }
-        const T fr2 = fr * wre - fi * wim + tm.f;
-        fi = fr * wim + fi * wre;
-        fr = fr2;
     };
-    if (sizeof(T) == 4) {
-        // float: unrolled by two (measured: the render adjoint 3% faster; not for the
-        // double and double-float types, whose larger bodies it slowed)
-#pragma unroll 2
-        for (int n = N - 1; n >= 0; --n) step4(n);
-    } else {
-        for (int n = N - 1; n >= 0; --n) step4(n);
-    }
+#pragma unroll 1
+    for (int n = N - 1; n >= 0; --n) step3(n);
     const T sre = cre * ar - cim * ai, sim = cre * ai + cim * ar;
     const T lbR = C.lnb - r_log(R);
     const T P = C.pref0 * r_exp((C.t - T(1)) * lbR);
@@ -560,6 +553,10 @@ RTU_HD void epl_eval(const EplC<T>& C, bool want_t, T x, T y, EplJ<T>& J) {
     J.are = P * sre; J.aim = P * sim;
     J.ax = C.cp * J.are - C.sp * J.aim;
     J.ay = C.sp * J.are + C.cp * J.aim;
+    // w S', then H = S + 2 w S' and F = w S' / f
+    const T vr = wre * dr - wim * di, vi = wre * di + wim * dr;
+    const T hr = ar + T(2) * vr, hi = ai + T(2) * vi;
+    const T fr = vr * C.ic, fi = vi * C.ic;
     J.hre = cre * hr - cim * hi; J.him = cre * hi + cim * hr;
     if (want_t) { J.ure = cre * ur - cim * ui; J.uim = cre * ui + cim * ur; }
     else { J.ure = T(0); J.uim = T(0); }
