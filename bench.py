@@ -46,21 +46,24 @@ L2_BYTES = 126 * 1024 * 1024
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ_RECIPE = 2032.0
 FALLBACK_HBM_GBS = 6400.0
-# algorithmic FP32 flops per supersampled ray: the EPL trace + map + interpolation of
-# one ray (about 190), its adjoint about 2.5x that
-FLOPS_FWD_RAY = 190.0
-FLOPS_ADJ_RAY = 2.5 * FLOPS_FWD_RAY
-# The two ray kernels and their algorithmic work: the forward render traces every
-# supersampled ray, the adjoint every ray inside the RTU grid.  DRAM read + write per
-# unit from one ncu capture (--set full, c2 shape, 8 mocks: 5,120,000 rays, 743,894 of
-# them in the grid), valid for the kernel sources with digest TRAFFIC_SRC_DIGEST.
+# Algorithmic FP32 flops (an FMA counts two) per ray that ends inside the RTU grid, from
+# the operation counts of the code at the c2 mocks' mean EPL series length (7.6 terms):
+# the forward trace + map + interpolation 228, its adjoint (lens value and series sums,
+# map value, slope and knot partials, bilinear slopes, lens vector-Jacobian product)
+# 516.  Rays that leave the grid's reach early, and the culled tiles' rays, are not
+# counted: the units are the in-grid rays (the N_IN_GRID statistic), for both kernels.
+FLOPS_FWD_RAY = 228.0
+FLOPS_ADJ_RAY = 516.0
+# DRAM read + write per unit from one ncu capture (--set full, c2 shape, 8 mocks:
+# 5,120,000 rays, 743,894 of them in the grid), valid for the kernel sources with digest
+# TRAFFIC_SRC_DIGEST.
 ROOF = {
-    "k_render": {"flops_per_unit": FLOPS_FWD_RAY, "units": "supersampled rays",
-                 "traffic_per_unit": (0.335360e6 + 2560) / 5120000},
+    "k_render": {"flops_per_unit": FLOPS_FWD_RAY, "units": "in-grid rays",
+                 "traffic_per_unit": (0.329984e6 + 3840) / 743894},
     "k_render_adj": {"flops_per_unit": FLOPS_ADJ_RAY, "units": "in-grid rays",
-                     "traffic_per_unit": (6.771456e6 + 50688) / 743894},
+                     "traffic_per_unit": (9.709056e6 + 156160) / 743894},
 }
-TRAFFIC_SRC_DIGEST = "8dd0852d3bf71804"
+TRAFFIC_SRC_DIGEST = "260c8ac6bd308d9e"
 KERNEL_SOURCES = ("k_render.cuh", "rtu_internal.cuh", "rtu_math.cuh", "rtu_df.cuh")
 
 
@@ -408,10 +411,14 @@ def run_ours(args):
     # the adjoint differentiates the rays inside the RTU grid (zero gradient elsewhere)
     rays_in = float(out_f64[:, rtu.STAT_N_IN_GRID].sum())
     rays = sum(m.n_rays for m in mocks)
-    units = rays if dom == "k_render" else rays_in
+    units = rays_in
     achieved = ROOF[dom]["flops_per_unit"] * units / (dom_ms / 1e3) / 1e12
     clock_mhz = clocks["sm_mhz"] or clocks["sm_max_mhz"] or SM_MAX_MHZ_RECIPE
     fp32_peak = sm_count * FP32_LANES_PER_SM * 2 * clock_mhz * 1e6 / 1e12
+    # both ray kernels against the same peak (the dominant one is the line's roofline)
+    per_kernel = {k: {"launch_ms": kern[k][1] / kern[k][0],
+                      "frac": ROOF[k]["flops_per_unit"] * units / (kern[k][1] / kern[k][0] / 1e3) / 1e12 / fp32_peak}
+                  for k in ROOF}
     # DRAM bytes from one ncu capture, per unit, scaled to this launch; null when the
     # kernel sources differ from the ones that were captured
     traffic = (ROOF[dom]["traffic_per_unit"] * units) if kernel_digest() == TRAFFIC_SRC_DIGEST else None
@@ -443,7 +450,7 @@ def run_ours(args):
                      "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
                      "traffic": traffic, "launch_ms": dom_ms, "units": ROOF[dom]["units"],
                      "units_per_launch": units, "rays_per_launch": rays, "in_grid_rays_per_launch": rays_in,
-                     "flops_per_unit": ROOF[dom]["flops_per_unit"],
+                     "flops_per_unit": ROOF[dom]["flops_per_unit"], "ray_kernels": per_kernel,
                      "peak_note": f"FP32 FMA peak from unit counts: {sm_count} SMs (device) x "
                                   f"{FP32_LANES_PER_SM} lanes x 2 x {clock_mhz:.0f} MHz (median SM clock "
                                   "sampled in the timed region)",
