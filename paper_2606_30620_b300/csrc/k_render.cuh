@@ -787,7 +787,8 @@ __device__ __forceinline__ void cell_offsets(const EvalArgs& E) {
 // near-core rays' adjoint positions go to nlist in the same order (warp u's at
 // nseg[u] on), for the adjoint's separate double-precision pass; near-core rays are
 // always deferred, so their cells come from k_compact_deferred too.
-// CMP_CTAS CTAs per evaluation (one wave); each warp takes an equal share of
+// Up to CMP_CTAS CTAs per evaluation (one wave at c2; one per 64 render warps below
+// that, so small systems launch few); each warp takes an equal share of
 // consecutive list positions (the rays cluster in the few render tiles the grid's
 // reach leaves unculled, so shares by render warp would be uneven) and walks the
 // render warps it overlaps: it finds the first with a 32-wide probe of the offsets,
@@ -817,12 +818,13 @@ __global__ void __launch_bounds__(CMP_NT) k_compact(const __grid_constant__ Batc
     const int ev = find_eval(B, blockIdx.x);
     const EvalArgs& E = B.e[ev];
     const int tile = blockIdx.x - B.tile0[ev];
+    const int ncta = B.tile0[ev + 1] - B.tile0[ev];          // this evaluation's CTAs
     const int lane = threadIdx.x & 31;
     constexpr int NWC = CMP_NT / 32;
     const int nu = E.n_cta_r * (CTA_R / 32);
     if (E.transform == RTU_TRANSFORM_LINEAR) {
         // the unsmoothed eCDF's position gradients, accumulated by k_render_adj
-        for (int i = tile * CMP_NT + threadIdx.x; i < 4 * E.n_mask; i += CMP_CTAS * CMP_NT) E.gk[i] = 0ull;
+        for (int i = tile * CMP_NT + threadIdx.x; i < 4 * E.n_mask; i += ncta * CMP_NT) E.gk[i] = 0ull;
     }
     const int cap = 32 * E.s * E.s;
     const int n_rays = E.n_img * E.n_img * E.s * E.s;
@@ -830,7 +832,7 @@ __global__ void __launch_bounds__(CMP_NT) k_compact(const __grid_constant__ Batc
     const int s2 = E.s * E.s;
     const float inv_s2 = 1.0f / (float)s2;
     const int total = max(0, min(E.useg[nu], n_rays));
-    const int nw = CMP_CTAS * NWC, w = tile * NWC + (threadIdx.x >> 5);
+    const int nw = ncta * NWC, w = tile * NWC + (threadIdx.x >> 5);
     const int share = (total + nw - 1) / nw;
     const int lo = min(total, w * share), hi = min(total, lo + share);
     if (lo >= hi) return;

@@ -656,7 +656,7 @@ int t_psf_gen(const EvalArgs& e) { return e.psf_uv ? 0 : e.n_cta_p; }
 int t_psf_sep(const EvalArgs& e) { return e.psf_uv ? e.n_cta_p : 0; }
 int t_edge(const EvalArgs& e) { return e.n_edge; }
 int t_cull_lin(const EvalArgs& e) { return is_lin(e) ? (e.n_cta_r + CULL_NT - 1) / CULL_NT : 0; }
-int t_units(const EvalArgs&) { return CMP_CTAS; }
+int t_units(const EvalArgs& e) { return std::min(CMP_CTAS, std::max(1, (e.n_cta_r * (CTA_R / 32) + 63) / 64)); }
 int t_defer(const EvalArgs& e) { return e.n_edge + 1; }
 int t_cells(const EvalArgs& e) {
     const int nc = (e.n_src - 1) * (e.n_src - 1);
