@@ -56,20 +56,20 @@ __global__ void __launch_bounds__(CTA_C, 5) k_trace_centres(const __grid_constan
     __shared__ LensK<double> L;
     __shared__ LensK<DF> Ldf;
     __shared__ double red[6][CTA_C / 32];
-    load_lensk(L, E.lensk);
-    __syncthreads();
+    __shared__ DF red_df[6][CTA_C / 32];
     // the float path traces its centre rays in double-float (about 48 bits) unless
-    // subhaloes are present; the double path in double
-    const bool use_df = !E.f64 && L.nsub == 0;
+    // subhaloes are present (and loads only that lens block); the double path in double
+    const bool use_df = !E.f64 && !(E.sub_kind && E.n_sub > 0);
     __shared__ DF pix_df;
     if (use_df) {
         load_lensk(Ldf, lensk_df_src(E.lensk));
         if (threadIdx.x == 0) pix_df = DF(E.pix);
-        __syncthreads();
+    } else {
+        load_lensk(L, E.lensk);
     }
+    __syncthreads();
     const int k = tile * CTA_C + threadIdx.x;
     const bool ok = k < E.n_mask;
-    double v[6];       // sum x, sum y, min x, max x, min y, max y of the warp (lane 0)
     if (use_df) {
         // positions and the warp reductions in double-float as well: on this part an
         // FP64 instruction holds the FP64 pipe for many cycles, and a warp tree of six
@@ -94,9 +94,24 @@ __global__ void __launch_bounds__(CTA_C, 5) k_trace_centres(const __grid_constan
                 else a[q] = a[q] < t ? t : a[q];
             }
         }
+        // the CTA's partials in double-float as well, one conversion to double each:
+        // every FP64 instruction, even with one lane active, takes a slot of the SM's
+        // FP64 pipe for the whole warp
         if ((threadIdx.x & 31) == 0)
-            for (int q = 0; q < 6; ++q) v[q] = a[q].to_double();
+            for (int q = 0; q < 6; ++q) red_df[q][threadIdx.x >> 5] = a[q];
+        __syncthreads();
+        if (threadIdx.x < 6) {
+            const int q = threadIdx.x;
+            DF r = red_df[q][0];
+            for (int i = 1; i < CTA_C / 32; ++i) {
+                const DF o = red_df[q][i];
+                r = q < 2 ? r + o : ((q & 1) == 0 ? (o < r ? o : r) : (r < o ? o : r));
+            }
+            E.cpart[tile * 8 + q] = r.to_double();
+            __threadfence();
+        }
     } else {
+        double v[6];   // sum x, sum y, min x, max x, min y, max y of the warp (lane 0)
         double bx = 0.0, by = 0.0;
         if (ok) {
             double x, y;
@@ -117,20 +132,20 @@ __global__ void __launch_bounds__(CTA_C, 5) k_trace_centres(const __grid_constan
             v[4] = fmin(v[4], __shfl_down_sync(0xffffffffu, v[4], o));
             v[5] = fmax(v[5], __shfl_down_sync(0xffffffffu, v[5], o));
         }
-    }
-    const int w = threadIdx.x >> 5;
-    if ((threadIdx.x & 31) == 0)
-        for (int q = 0; q < 6; ++q) red[q][w] = v[q];
-    __syncthreads();
-    if (threadIdx.x < 6) {
-        const int q = threadIdx.x;
-        double r = red[q][0];
-        for (int i = 1; i < CTA_C / 32; ++i) {
-            double o = red[q][i];
-            r = q < 2 ? r + o : ((q & 1) == 0 ? fmin(r, o) : fmax(r, o));
+        const int w = threadIdx.x >> 5;
+        if ((threadIdx.x & 31) == 0)
+            for (int q = 0; q < 6; ++q) red[q][w] = v[q];
+        __syncthreads();
+        if (threadIdx.x < 6) {
+            const int q = threadIdx.x;
+            double r = red[q][0];
+            for (int i = 1; i < CTA_C / 32; ++i) {
+                double o = red[q][i];
+                r = q < 2 ? r + o : ((q & 1) == 0 ? fmin(r, o) : fmax(r, o));
+            }
+            E.cpart[tile * 8 + q] = r;
+            __threadfence();
         }
-        E.cpart[tile * 8 + q] = r;
-        __threadfence();
     }
     // the last CTA of the evaluation to finish reduces the partials once (fixed order)
     __shared__ int last;
@@ -156,7 +171,7 @@ __global__ void __launch_bounds__(CTA_C) k_centre_hist(const __grid_constant__ B
     const EvalArgs& E = B.e[ev];
     const int tile = blockIdx.x - B.tile0[ev];
     __shared__ double m[6], sc[2];
-    __shared__ double red[2][CTA_C / 32];
+    __shared__ double dev[2][CTA_C];
     if (threadIdx.x < 6) m[threadIdx.x] = __ldcg(E.mom + threadIdx.x);
     __syncthreads();
     // the bin scales once per CTA (an FP64 divide each)
@@ -171,22 +186,36 @@ __global__ void __launch_bounds__(CTA_C) k_centre_hist(const __grid_constant__ B
         const int b1 = beta_bin(by, m[4], sc[1]);
         atomicAdd(E.hist + b0, w);
         atomicAdd(E.hist + HB + b1, w);
+        // the count of each bin's row of 32, so the selection reads 2 HROWS counts
+        // instead of summing the 2 HB bins
+        atomicAdd(E.hist + 2 * HB + (b0 >> 5), w);
+        atomicAdd(E.hist + 2 * HB + HROWS + (b1 >> 5), w);
         E.cbin[k] = b0;
         E.cbin[E.n_mask + k] = b1;
         d0 = (bx - m[0]) * (bx - m[0]);
         d1 = (by - m[1]) * (by - m[1]);
     }
-    for (int o = 16; o > 0; o >>= 1) {
-        d0 += __shfl_down_sync(0xffffffffu, d0, o);
-        d1 += __shfl_down_sync(0xffffffffu, d1, o);
-    }
-    if ((threadIdx.x & 31) == 0) { red[0][threadIdx.x >> 5] = d0; red[1][threadIdx.x >> 5] = d1; }
+    // the CTA's sums of squared deviations by warp 0 alone (lane l adds the rays
+    // l, l + 32, ... in order, then a shuffle tree): the SM's FP64 pipe takes one warp
+    // instruction at a time, whatever its active lanes, so a tree in every warp
+    // would cost eight times the instructions
+    dev[0][threadIdx.x] = d0;
+    dev[1][threadIdx.x] = d1;
     __syncthreads();
-    if (threadIdx.x < 2) {
-        double r = 0.0;
-        for (int i = 0; i < CTA_C / 32; ++i) r += red[threadIdx.x][i];
-        E.cpart2[tile * 2 + threadIdx.x] = r;
-        __threadfence();
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        double s0 = dev[0][lane], s1 = dev[1][lane];
+#pragma unroll
+        for (int i = 1; i < CTA_C / 32; ++i) { s0 += dev[0][lane + 32 * i]; s1 += dev[1][lane + 32 * i]; }
+        for (int o = 16; o > 0; o >>= 1) {
+            s0 += __shfl_down_sync(0xffffffffu, s0, o);
+            s1 += __shfl_down_sync(0xffffffffu, s1, o);
+        }
+        if (lane == 0) {                            // the tree's totals are in lane 0
+            E.cpart2[tile * 2] = s0;
+            E.cpart2[tile * 2 + 1] = s1;
+            __threadfence();
+        }
     }
     // the last CTA to finish: sums of squared deviations over the CTAs (lanes over
     // CTAs, fixed tree), once per evaluation
@@ -219,12 +248,27 @@ __device__ __forceinline__ void export_selection(const EvalArgs& E, int a, const
 }
 
 constexpr int SEL_NT = 1024;
-constexpr int SEL_ROWS = HB / 32;      // the histogram as rows of 32 bins (one per lane)
+constexpr int SEL_ROWS = HROWS;       // the histogram as rows of 32 bins (one per lane)
 constexpr int SEL_SMALL = SEL_CAP / (2 * MAXM);   // candidates ranked directly per target bin (48)
 constexpr int SEL_DIG = 11;            // bits per radix-refinement level
 constexpr int SEL_HB = 1 << SEL_DIG;   // digit histogram bins (2 per thread)
 static_assert(SEL_HB == 2 * SEL_NT, "two digits per thread in the refinement scan");
 static_assert(2 * SEL_HB * 4 + SEL_SMALL * 8 <= SEL_CAP * 8, "refinement scratch fits the candidate arrays");
+constexpr int SEL_CHEB = cheb_size(MAXM, MAXM - 1);   // the largest fit tables (doubles, shared memory)
+constexpr int SEL_LPT = 8;             // centre-ray bins loaded per thread at a time
+// dynamic shared memory of k_select_fit: candidates, bitmap, the fit tables
+constexpr int SEL_SMEM = SEL_CAP * 16 + HB / 8 + SEL_CHEB * 8;
+
+// 8-byte asynchronous global -> shared copy (both addresses 8-byte aligned)
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_wait() {
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 // Order-preserving 64-bit image of a double (-0 taken as +0): a < b iff key(a) < key(b).
 __device__ __forceinline__ unsigned long long order_key(double v) {
@@ -245,13 +289,14 @@ __global__ void __launch_bounds__(SEL_NT) k_select_fit(const __grid_constant__ B
     int* ci = reinterpret_cast<int*>(ck + SEL_CAP);
     unsigned* bitmap = reinterpret_cast<unsigned*>(ci + SEL_CAP);
     uint32_t* cwc = reinterpret_cast<uint32_t*>(bitmap + HB / 32);
+    double* chb = reinterpret_cast<double*>(cwc + SEL_CAP);      // [SEL_CHEB] the fit's tables
     __shared__ double mom[6];
-    __shared__ double sig[3];
+    __shared__ double sig[4];
     __shared__ int rowoff[SEL_ROWS + 1];
     __shared__ int wtot[SEL_NT / 32];
     __shared__ int t_bin[2 * MAXM], t_below[2 * MAXM], t_rank[2 * MAXM], t_slot[2 * MAXM];
-    __shared__ int d_bin[2 * MAXM], d_off[2 * MAXM + 1], d_fill[2 * MAXM], d_num[2 * MAXM];
-    __shared__ int n_d;
+    __shared__ int d_bin[2 * MAXM], d_num[2 * MAXM];
+    __shared__ int n_d, big_sh;
     __shared__ double Qs[MAXM];
     __shared__ double coef[MAXM];
     __shared__ double Xs[MAXM + 2], Ps[MAXM + 2];
@@ -261,38 +306,46 @@ __global__ void __launch_bounds__(SEL_NT) k_select_fit(const __grid_constant__ B
     const int N = E.n_mask, M = E.n_nodes, D = E.degree, K = M + 2;
     const int W = E.wtot;                            // ranks of the (weight-expanded) sample
 
-    if (tid < 6) mom[tid] = __ldcg(E.mom + tid);
-    if (tid == 0) {
-        const double sx = sqrt(__ldcg(E.mom + 6) / N), sy = sqrt(__ldcg(E.mom + 7) / N);
-        sig[0] = sx <= sy ? sx : sy;            // sigma_min, tie -> x (App. C i)
-        sig[1] = sx <= sy ? 0.0 : 1.0;
-        sig[2] = 1.0 / sig[0];
-        flag_sh = 0;
+    // the fit's tables (Chebyshev nodes, C, V, V') copied into shared memory
+    // asynchronously while the histogram is scanned
+    const int ncheb = cheb_size(M, D);
+    const bool chb_ok = ncheb <= SEL_CHEB;
+    if (chb_ok) {
+        for (int i = tid; i < ncheb; i += SEL_NT) cp_async8(chb + i, E.cheb + i);
+        cp_async_commit();
     }
+    // this axis's row counts, two per thread (scanned below)
+    static_assert(SEL_ROWS == 2 * SEL_NT, "two rows per thread");
+    const int* hrow = E.hist + 2 * HB + a * HROWS;
+    const int r0 = __ldcg(hrow + 2 * tid), r1 = __ldcg(hrow + 2 * tid + 1);
+    if (tid < 6) mom[tid] = __ldcg(E.mom + tid);
+    // the two axes' standard deviations and their inverses on two warps (FP64 divides
+    // and roots are long dependent chains on this part)
+    if (tid == 0 || tid == 32) {
+        const int q = tid >> 5;
+        const double sq = sqrt(__ldcg(E.mom + 6 + q) / N);
+        sig[q] = sq;
+        sig[2 + q] = 1.0 / sq;
+    }
+    if (tid == 64) { flag_sh = 0; big_sh = 0; }
     __syncthreads();
-    const double sigma = sig[0], isig = sig[2];
+    // sigma_min, tie -> x (App. C i); the two are positive, so their bit patterns
+    // order as they do (an integer compare: an FP64 one executed by all 32 warps
+    // would queue 32 instructions on the SM's FP64 pipe)
+    const bool sxmin = __double_as_longlong(sig[0]) <= __double_as_longlong(sig[1]);
+    const double sigma = sxmin ? sig[0] : sig[1], isig = sxmin ? sig[2] : sig[3];
     double* tr = E.trd;
     const int* hist = E.hist + a * HB;
     const double* beta = E.beta + a * N;
     const double lo = mom[2 + 2 * a];
     export_selection(E, a, hist, beta);
-    // row sums: warp w reads its 64 rows of 32 bins coalesced, 8 loads in flight
-    constexpr int RPW = SEL_ROWS / (SEL_NT / 32);
-    for (int i = 0; i < RPW; i += 8) {
-        int v[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) v[u] = hist[(wid * RPW + i + u) * 32 + lane];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int sum = __reduce_add_sync(0xffffffffu, v[u]);
-            if (lane == 0) rowoff[wid * RPW + i + u] = sum;
-        }
-    }
-    for (int i = tid; i < 2 * MAXM; i += SEL_NT) { d_fill[i] = 0; d_num[i] = 0; }
+    for (int i = tid; i < 2 * MAXM; i += SEL_NT) d_num[i] = 0;
     for (int i = tid; i < HB / 32; i += SEL_NT) bitmap[i] = 0u;
+    if (chb_ok) cp_async_wait();
     __syncthreads();
-    // exclusive scan of the row sums: two rows per thread, warp scans, warp totals
-    const int r0 = rowoff[2 * tid], r1 = rowoff[2 * tid + 1];
+    const double* cb = chb_ok ? chb : E.cheb;
+    // exclusive scan of the row counts (k_centre_hist kept them beside the bins): two
+    // rows per thread, warp scans, warp totals
     const int own = r0 + r1;
     int incl = own;
     for (int o = 1; o < 32; o <<= 1) {
@@ -325,7 +378,7 @@ __global__ void __launch_bounds__(SEL_NT) k_select_fit(const __grid_constant__ B
         if (E.transform == RTU_TRANSFORM_UNIFORM) {
             k = t == 0 ? 0 : W - 1;
         } else {
-            double h = E.cheb[cheb_u(M, D) + t / 2] * (W - 1);
+            double h = cb[cheb_u(M, D) + t / 2] * (W - 1);
             k = (int)floor(h);
             k = k < 0 ? 0 : (k > W - 1 ? W - 1 : k);
             if (t & 1) k = k + 1 > W - 1 ? W - 1 : k + 1;
@@ -382,40 +435,46 @@ __global__ void __launch_bounds__(SEL_NT) k_select_fit(const __grid_constant__ B
     for (int t = tid; t < nt; t += SEL_NT) selv[t] = lo;     // overwritten by the selection
     __syncthreads();
     const int nd = n_d;
-    // candidates of the target bins: count them per bin; a bin of at most SEL_SMALL
-    // candidates is gathered into shared memory and its targets ranked there, a larger
-    // one is resolved below by radix refinement (so the selection is exact whatever the
-    // distribution: one far outlier can squeeze most rays into a few level-1 bins)
+    // candidates of the target bins, in one pass over the centre rays: each is counted
+    // in its bin and, while the bin has at most SEL_SMALL, kept in the bin's segment of
+    // SEL_SMALL slots.  A bin of at most SEL_SMALL candidates has its targets ranked
+    // there; a larger one is resolved below by radix refinement (so the selection is
+    // exact whatever the distribution: one far outlier can squeeze most rays into a
+    // few level-1 bins).  SEL_LPT bins per thread are loaded at a time, then the
+    // positions of the hits.
+    static_assert(2 * MAXM * SEL_SMALL <= SEL_CAP, "a segment per distinct bin");
     const int* cbin = E.cbin + (size_t)a * N;    // the bins k_centre_hist used
-    for (int k = tid; k < N; k += SEL_NT) {
-        const int bn = cbin[k];
-        if (bitmap[bn >> 5] & (1u << (bn & 31))) {
-            int d = 0;
-            while (d < nd - 1 && d_bin[d] != bn) ++d;
-            atomicAdd(&d_num[d], 1);
+    for (int k0 = 0; k0 < N; k0 += SEL_NT * SEL_LPT) {
+        int bn[SEL_LPT];
+#pragma unroll
+        for (int u = 0; u < SEL_LPT; ++u) {
+            const int k = k0 + u * SEL_NT + tid;
+            bn[u] = k < N ? __ldcg(cbin + k) : -1;
         }
-    }
-    __syncthreads();
-    if (tid == 0) {
-        int off = 0;
-        for (int d = 0; d < nd; ++d) {
-            d_off[d] = off;
-            if (d_num[d] <= SEL_SMALL) off += d_num[d];
+        double bv[SEL_LPT];
+#pragma unroll
+        for (int u = 0; u < SEL_LPT; ++u) {
+            const bool hit = bn[u] >= 0 && (bitmap[bn[u] >> 5] & (1u << (bn[u] & 31)));
+            if (!hit) bn[u] = -1;
+            bv[u] = hit ? __ldcg(beta + k0 + u * SEL_NT + tid) : 0.0;
         }
-        d_off[nd] = off;
-    }
-    __syncthreads();
-    for (int k = tid; k < N; k += SEL_NT) {
-        const int bn = cbin[k];
-        if (bitmap[bn >> 5] & (1u << (bn & 31))) {
-            int d = 0;
-            while (d < nd - 1 && d_bin[d] != bn) ++d;
-            if (d_num[d] > SEL_SMALL) continue;
-            const int at = d_off[d] + atomicAdd(&d_fill[d], 1);
-            if (at < d_off[d + 1]) {
-                ck[at] = beta[k];
-                ci[at] = k;
-                cwc[at] = E.cwt ? E.cwt[k] : 1u;
+#pragma unroll
+        for (int u = 0; u < SEL_LPT; ++u) {
+            if (bn[u] < 0) continue;
+            const int k = k0 + u * SEL_NT + tid;
+            // the bin's slot (the distinct bins increase)
+            int d = 0, dh = nd - 1;
+            while (d < dh) {
+                const int mid = (d + dh) >> 1;
+                if (d_bin[mid] < bn[u]) d = mid + 1;
+                else dh = mid;
+            }
+            const int at = atomicAdd(&d_num[d], 1);
+            if (at < SEL_SMALL) {
+                const int o = d * SEL_SMALL + at;
+                ck[o] = bv[u];
+                ci[o] = k;
+                cwc[o] = E.cwt ? E.cwt[k] : 1u;
             }
         }
     }
@@ -425,8 +484,11 @@ __global__ void __launch_bounds__(SEL_NT) k_select_fit(const __grid_constant__ B
     // candidates: two per lane, each compared with all)
     for (int t = wid; t < nt; t += SEL_NT / 32) {
         const int d = t_slot[t];
-        if (d_num[d] > SEL_SMALL) continue;
-        const int o = d_off[d], cnt = d_off[d + 1] - o;
+        if (d_num[d] > SEL_SMALL) {
+            if (lane == 0) big_sh = 1;
+            continue;
+        }
+        const int o = d * SEL_SMALL, cnt = d_num[d];
         const int want = t_rank[t] - t_below[t];
         for (int c = lane; c < cnt; c += 32) {
             const double kc = ck[o + c];
@@ -450,8 +512,9 @@ __global__ void __launch_bounds__(SEL_NT) k_select_fit(const __grid_constant__ B
     // once for their key range and once for a histogram of the next digit (counts and
     // weights), keeps the digit holding the wanted rank, and stops when at most
     // SEL_SMALL candidates remain, which are ranked like the small bins.  Scratch: the
-    // candidate arrays (the small bins are done).
-    {
+    // candidate arrays (the small bins are done).  Skipped (a uniform branch) when
+    // every target bin was small.
+    if (big_sh) {
         int* hc = reinterpret_cast<int*>(ck);                 // [SEL_HB] counts
         int* hw = hc + SEL_HB;                                // [SEL_HB] weights
         double* fv = ck + SEL_HB;                             // [SEL_SMALL] final candidates
@@ -578,13 +641,6 @@ __global__ void __launch_bounds__(SEL_NT) k_select_fit(const __grid_constant__ B
             __syncthreads();
         }
     }
-    // the Chebyshev tables of the fit in shared memory (the candidates are done with)
-    const double* cb = E.cheb;
-    if (cheb_size(M, D) <= SEL_CAP) {
-        for (int i = tid; i < cheb_size(M, D); i += SEL_NT) ck[i] = E.cheb[i];
-        __syncthreads();
-        cb = ck;
-    }
     if (E.transform == RTU_TRANSFORM_UNIFORM) {
         // uniform grid: the smallest square box around the masked rays, centred on
         // each axis's range, mapped affinely onto [0, 1]^2 -- written as Hermite
@@ -603,7 +659,7 @@ __global__ void __launch_bounds__(SEL_NT) k_select_fit(const __grid_constant__ B
             tr[TR_HDR + (4 + a) * K + j] = L * isig;
         }
         if (a == 0 && tid == 0) {
-            tr[0] = mom[0]; tr[1] = mom[1]; tr[2] = sigma; tr[3] = sig[1]; tr[4] = K;
+            tr[0] = mom[0]; tr[1] = mom[1]; tr[2] = sigma; tr[3] = sxmin ? 0.0 : 1.0; tr[4] = K;
             tr[5] = r0x >= r1y ? 0.0 : 1.0; tr[6] = L;
         }
     } else {
@@ -642,34 +698,43 @@ __global__ void __launch_bounds__(SEL_NT) k_select_fit(const __grid_constant__ B
         }
         __syncthreads();
         // monotonicity guard (App. C iv): p' >= 1e-6 span per point (in parallel),
-        // strictly increasing knots (sequential in the knots, one thread)
-        double span = Xs[K - 1] - Xs[0];
-        const bool span_ok = span > 0.0;
-        if (!span_ok) span = fabs(span) + 1e-300;
-        const double floor_d = 1e-6 * span;
-        if (!span_ok && tid == 0) flag_sh |= F_NONMONO;
-        for (int j = tid; j < K; j += SEL_NT) {
-            double dp = Ps[j];
-            if (dp < floor_d) { dp = floor_d; atomicOr(&flag_sh, F_NONMONO); }
-            tr[TR_HDR + (2 + a) * K + j] = 1.0 / dp;
-        }
-        if (tid == 0) {
-            int fl = 0;
-            double prev = Xs[0];
-            tr[TR_HDR + a * K] = prev;
-            for (int j = 1; j < K; ++j) {
-                double x = Xs[j];
-                const double lim = prev + floor_d;
-                if (x < lim) { x = lim; fl |= F_NONMONO; }
-                tr[TR_HDR + a * K + j] = x;
-                prev = x;
+        // strictly increasing knots (sequential in the knots, one thread).  By warp 0
+        // alone: FP64 instructions of all 32 warps would queue on the SM's FP64 pipe.
+        if (wid == 0) {
+            double span = Xs[K - 1] - Xs[0];
+            const bool span_ok = span > 0.0;
+            if (!span_ok) span = fabs(span) + 1e-300;
+            const double floor_d = 1e-6 * span;
+            if (!span_ok && lane == 0) atomicOr(&flag_sh, F_NONMONO);
+            for (int j = lane; j < K; j += 32) {
+                double dp = Ps[j];
+                if (dp < floor_d) { dp = floor_d; atomicOr(&flag_sh, F_NONMONO); }
+                tr[TR_HDR + (2 + a) * K + j] = 1.0 / dp;
             }
-            if (fl) atomicOr(&flag_sh, fl);
+            // when no fitted knot is below its predecessor + floor (checked by one warp
+            // in parallel) all stay as fitted; else they are raised in order by one lane
+            bool low = false;
+            for (int j = 1 + lane; j < K; j += 32) low |= Xs[j] < Xs[j - 1] + floor_d;
+            if (!__any_sync(0xffffffffu, low)) {
+                for (int j = lane; j < K; j += 32) tr[TR_HDR + a * K + j] = Xs[j];
+            } else if (lane == 0) {
+                int fl = 0;
+                double prev = Xs[0];
+                tr[TR_HDR + a * K] = prev;
+                for (int j = 1; j < K; ++j) {
+                    double x = Xs[j];
+                    const double lim = prev + floor_d;
+                    if (x < lim) { x = lim; fl |= F_NONMONO; }
+                    tr[TR_HDR + a * K + j] = x;
+                    prev = x;
+                }
+                if (fl) atomicOr(&flag_sh, fl);
+            }
         }
         for (int k = tid; k <= D; k += SEL_NT) tr[TR_HDR + 8 * K + a * MAXM + k] = coef[k];
         for (int j = tid; j < M; j += SEL_NT) tr[TR_HDR + 8 * K + 2 * MAXM + a * MAXM + j] = Qs[j];
         if (a == 0 && tid == 0) {
-            tr[0] = mom[0]; tr[1] = mom[1]; tr[2] = sigma; tr[3] = sig[1]; tr[4] = K;
+            tr[0] = mom[0]; tr[1] = mom[1]; tr[2] = sigma; tr[3] = sxmin ? 0.0 : 1.0; tr[4] = K;
         }
     }
     __syncthreads();

@@ -118,7 +118,7 @@ size_t slot_layout(const rtu_system_desc& d, char* base, EvalArgs* e) {
     p = take((size_t)(z.n_cta_c_max + 2) * z.nl * 8); if (e) e->cadj = (double*)p;
     p = take((size_t)4 * MAXM * z.nl * 8);           if (e) e->jsel = (double*)p;
 
-    p = take((size_t)2 * HB * 4);                     if (e) e->hist = (int*)p;
+    p = take((size_t)2 * (HB + HROWS) * 4);           if (e) e->hist = (int*)p;
     p = take((size_t)tr_size(z.K) * 8);               if (e) e->trd = (double*)p;
     p = take((size_t)tr_size(z.K) * 4);               if (e) e->trf = (float*)p;
     p = take((size_t)4 * MAXM * 4);                   if (e) e->sel_idx = (int*)p;
@@ -306,7 +306,6 @@ const char* check_desc(const rtu_system_desc* d) {
 }
 
 std::once_flag g_attr_once;
-constexpr int SEL_SMEM = SEL_CAP * 16 + HB / 8;
 constexpr int MAX_DYN = 200 * 1024;
 
 void set_attributes() {
@@ -357,10 +356,11 @@ __global__ void __launch_bounds__(256) k_zero(const __grid_constant__ Batch B, i
     const int ev = find_eval(B, blockIdx.x);
     const EvalArgs& E = B.e[ev];
     const int tile = blockIdx.x - B.tile0[ev];
-    const int nh = 2 * HB;
+    const int nh = 2 * (HB + HROWS);
     const int ncell = (E.n_src - 1) * (E.n_src - 1);
     const int tot = nh + (with_cells ? 2 * ncell : 0);
-    for (int i = tile * 256 + threadIdx.x; i < tot; i += ZERO_TILES * 256) {
+    // tiles 1.. zero; tile 0 builds the lens blocks (a chain of FP64 latencies)
+    for (int i = (tile - 1) * 256 + threadIdx.x; tile > 0 && i < tot; i += (ZERO_TILES - 1) * 256) {
         if (i < nh) E.hist[i] = 0;
         else if (i < nh + ncell) E.ccount[i - nh] = 0;
         else E.cursor[i - nh - ncell] = 0;          // the compaction's rank cursors
@@ -371,14 +371,9 @@ __global__ void __launch_bounds__(256) k_zero(const __grid_constant__ Batch B, i
             *E.gmax = 0ull;
         }
         const int nsub = E.sub_kind ? E.n_sub : 0;
-        lens_setup_par(reinterpret_cast<LensK<double>*>(E.lensk),
-                       reinterpret_cast<LensK<float>*>(static_cast<char*>(E.lensk) + LENSK_D_BYTES), E.lens,
-                       E.profile, E.sub_kind, nsub);
-        // the double-float copy, once per call (the kernels of the FP32 path's islands
-        // load it instead of converting per CTA)
-        __syncthreads();
-        lensk_to_df(*reinterpret_cast<const LensK<double>*>(E.lensk),
-                    *reinterpret_cast<LensK<DF>*>(static_cast<char*>(E.lensk) + LENSK_DF_AT));
+        char* kb = static_cast<char*>(E.lensk);
+        lens_setup_par(reinterpret_cast<LensK<double>*>(kb), reinterpret_cast<LensK<float>*>(kb + LENSK_D_BYTES),
+                       reinterpret_cast<LensK<DF>*>(kb + LENSK_DF_AT), E.lens, E.profile, E.sub_kind, nsub);
     }
 }
 

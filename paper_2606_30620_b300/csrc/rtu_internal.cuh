@@ -6,6 +6,7 @@
 // array of per-evaluation tile counts.
 #pragma once
 #include <cuda_runtime.h>
+#include <stddef.h>
 #include <stdint.h>
 
 #include "rtu.h"
@@ -16,6 +17,7 @@ namespace rtu {
 
 constexpr int MAXB = 40;          // evaluations per launch (kernel-parameter budget)
 constexpr int HB = 65536;         // level-1 histogram bins for order statistics
+constexpr int HROWS = HB / 32;    // rows of 32 level-1 bins (their counts are kept beside the bins)
 constexpr int SEL_CAP = 6144;     // candidate keys held in shared memory by the selector
 constexpr int MAXM = 64;          // max Chebyshev nodes
 constexpr int MAX_RADIX = 12;     // max FFT stages
@@ -107,7 +109,7 @@ struct EvalArgs {
     double* cadj;      // [n_cta_c + 2][8 + 5 n_sub] centre-ray adjoint lens partials; the last
                        // two rows the selected-rank terms of each axis
     double* jsel;      // [2][2 MAXM][8 + 5 n_sub] d beta_a / d lens of each selected-rank ray
-    int* hist;         // [2][HB] level-1 histograms
+    int* hist;         // [2][HB] level-1 histograms, then [2][HB/32] their sums over rows of 32 bins
     double* trd;       // transform, double (layout in tr_* helpers)
     float* trf;        // transform, float copy
     int* sel_idx;      // [2][2 MAXM] centre-ray index at each selected rank
@@ -377,39 +379,41 @@ __device__ inline void lens_rest(LensK<T>& K, const double* lens, int profile, i
         for (int k = 0; k < 5; ++k) K.sub[h][k] = (T)lens[8 + 5 * h + k];
 }
 
-// Both lens blocks of an evaluation, built by one CTA: the series coefficients
-// c_n, c_n/f and the per-term t-derivative of log|c_n| in parallel (one thread
-// per term), the running products and sums, and the stopping index of each
-// precision (1e-16 for double, 2e-8 for float: a third of the type's unit
-// roundoff or less, as |c_n| <= f <= 1/4), by one thread.
-__device__ inline void lens_setup_par(LensK<double>* Kd, LensK<float>* Kf, const double* lens, int profile, int sub_kind,
-                               int n_sub) {
-    // Called by all threads of a CTA of at least 160.  Warps 0-2 build the series
-    // coefficients (term n by thread n - 1: the products A_n = c_1 ... c_n and the sums
-    // D_n by warp scans, synchronised among themselves by a named barrier); meanwhile
-    // one thread of warp 3 computes the double lens scalars and one of warp 4 the float
-    // ones, so the serial FP64 chains of the two run side by side.
-    __shared__ double sconst[2], wA[3], wD[3];
+// The three lens blocks of an evaluation (double, float and the double-float copy of
+// the double one), built by one CTA of at least 160 threads.  On this part FP64
+// divides, roots and logarithms are dependent chains of hundreds to thousands of
+// cycles, so the work is spread so that no thread runs more than one such chain:
+//   1. warps 0-2: the series coefficients, term n by thread n - 1 (the products
+//      A_n = c_1 ... c_n and the sums D_n by warp scans, the warps synchronised by
+//      a named barrier), written in all three types, and the stopping index of each
+//      precision (1e-16 for double, 2e-8 for float: a third of the type's unit
+//      roundoff or less, as |c_n| <= f <= 1/4); meanwhile lane 0 of warps 3-5
+//      computes one of the three independent parts of the lens-only scalars in
+//      double (one chain per warp: lanes of one warp would run them one after the
+//      other); every thread involved forms c = |(e1, e2)| (= f) itself;
+//   2. one thread per scalar writes it in the three types (the float and
+//      double-float values are the double one rounded, as a float build of the same
+//      expressions gives), and three threads the shear, core radius and subhaloes.
+__device__ inline void lens_setup_par(LensK<double>* Kd, LensK<float>* Kf, LensK<DF>* Kx, const double* lens,
+                                      int profile, int sub_kind, int n_sub) {
+    static_assert(offsetof(EplC<double>, ic) == (EPL_NSCAL - 1) * sizeof(double), "EplC scalars are contiguous");
+    static_assert(offsetof(EplC<float>, ic) == (EPL_NSCAL - 1) * sizeof(float), "EplC scalars are contiguous");
+    static_assert(offsetof(EplC<DF>, ic) == (EPL_NSCAL - 1) * sizeof(DF), "EplC scalars are contiguous");
+    __shared__ double wA[3], wD[3];
+    __shared__ EplC<double> sC;        // the double scalars (leading members only)
     __shared__ int nt_sh[2];
     const int tid = threadIdx.x;
-    if (tid == 0) {
-        // f = (1 - q)/(1 + q) with q = (1 - c)/(1 + c) is c itself
-        sconst[0] = sqrt(fmax(lens[2] * lens[2] + lens[3] * lens[3], 1e-30));
-        sconst[1] = (profile == 1 ? lens[1] : 2.0) - 1.0;
-        nt_sh[0] = EPL_MAXT;
-        nt_sh[1] = EPL_MAXT;
-    }
-    __syncthreads();
-    const double p[6] = {lens[0], lens[1], lens[2], lens[3], lens[4], lens[5]};
-    if (tid == 96) {
-        epl_scalars(Kd->C, p, profile == 1);
-        lens_rest(*Kd, lens, profile, sub_kind, n_sub);
-    } else if (tid == 128) {
-        epl_scalars(Kf->C, p, profile == 1);
-        lens_rest(*Kf, lens, profile, sub_kind, n_sub);
+    const bool epl = profile == 1;
+    if (tid >= 96 && tid < 192 && (tid & 31) == 0) {
+        const double p[6] = {lens[0], lens[1], lens[2], lens[3], lens[4], lens[5]};
+        const double cc = sqrt(fmax(p[2] * p[2] + p[3] * p[3], 1e-30));
+        epl_scalars_part(sC, p, epl, cc, (tid >> 5) - 3);
     } else if (tid < 96) {
         const int lane = tid & 31, w = tid >> 5, n = tid + 1;
-        const double f = sconst[0], t = sconst[1];
+        if (tid == 0) { nt_sh[0] = EPL_MAXT; nt_sh[1] = EPL_MAXT; }   // before the named barrier
+        // f = (1 - q)/(1 + q) with q = (1 - c)/(1 + c) is c itself
+        const double f = sqrt(fmax(lens[2] * lens[2] + lens[3] * lens[3], 1e-30));
+        const double t = (epl ? lens[1] : 2.0) - 1.0;
         const double r1 = 1.0 / (2.0 * n - 2.0 + t), r2 = 1.0 / (2.0 * n + 2.0 - t);
         const double g = -(2.0 * n - 2.0 + t) * r2;
         const double c = f * g;
@@ -427,15 +431,31 @@ __device__ inline void lens_setup_par(LensK<double>* Kd, LensK<float>* Kf, const
         if (lane == 0) Ap = w == 0 ? 1.0 : wA[0] * (w == 2 ? wA[1] : 1.0);
         epl_term(Kd->C.term[n], Ap, c, D);
         epl_term(Kf->C.term[n], Ap, c, D);
-        if (tid == 0) { epl_term0(Kd->C.term[0]); epl_term0(Kf->C.term[0]); }
+        epl_term(Kx->C.term[n], Ap, c, D);
+        if (tid == 0) { epl_term0(Kd->C.term[0]); epl_term0(Kf->C.term[0]); epl_term0(Kx->C.term[0]); }
         const double An = fabs(Ap * c);
         if (An <= 1e-16) atomicMin(&nt_sh[0], n);
         if (An <= 2e-8) atomicMin(&nt_sh[1], n);
-        asm volatile("bar.sync 1, 96;" ::: "memory");
-        if (tid == 0) {
-            Kd->C.nterm = nt_sh[0];
-            Kf->C.nterm = nt_sh[1];
-        }
+    }
+    __syncthreads();
+    if (tid < EPL_NSCAL) {
+        const double v = reinterpret_cast<const double*>(&sC)[tid];
+        reinterpret_cast<double*>(&Kd->C)[tid] = v;
+        reinterpret_cast<float*>(&Kf->C)[tid] = (float)v;
+        reinterpret_cast<DF*>(&Kx->C)[tid] = DF(v);
+    } else if (tid == 32) {
+        Kd->C.nterm = nt_sh[0];
+        Kx->C.nterm = nt_sh[0];            // the double-float copy sums as many terms as double
+        Kf->C.nterm = nt_sh[1];
+        lens_rest(*Kd, lens, profile, sub_kind, n_sub);
+    } else if (tid == 64) {
+        lens_rest(*Kf, lens, profile, sub_kind, n_sub);
+    } else if (tid == 96) {
+        // the double-float block serves the lens without subhaloes only
+        Kx->g1 = DF(lens[6]);
+        Kx->g2 = DF(lens[7]);
+        Kx->rc2 = DF(1e-4 * lens[0] * lens[0]);
+        Kx->nsub = 0; Kx->kind = sub_kind; Kx->epl = epl;
     }
 }
 
@@ -526,29 +546,6 @@ __device__ __forceinline__ void sub_vjp(const LensK<T>& K, int h, T x, T y, T gb
     nfw_deflect<D>(D(x), D(y), ks, rs, tau, xs, ys, K.kind, ax, ay);
 #pragma unroll
     for (int c = 0; c < 5; ++c) out[c] -= gbx * ax.d[c] + gby * ay.d[c];
-}
-
-// The double-float lens block of a LensK<double> (no subhaloes: the double-float
-// path serves only lenses without them), converted by the CTA's threads.
-__device__ inline void lensk_to_df(const LensK<double>& a, LensK<DF>& b) {
-    const int nt = a.C.nterm;
-    for (int i = threadIdx.x; i <= nt; i += blockDim.x) {
-        b.C.term[i].a = DF(a.C.term[i].a);
-        b.C.term[i].u = DF(a.C.term[i].u);
-    }
-    if (threadIdx.x == 0) {
-        const EplC<double>& c = a.C;
-        EplC<DF>& d = b.C;
-        d.x0 = DF(c.x0); d.y0 = DF(c.y0); d.cp = DF(c.cp); d.sp = DF(c.sp); d.q = DF(c.q); d.cc = DF(c.cc);
-        d.e1 = DF(c.e1); d.e2 = DF(c.e2); d.thE = DF(c.thE); d.sq = DF(c.sq); d.b = DF(c.b); d.t = DF(c.t);
-        d.pref0 = DF(c.pref0); d.lnb = DF(c.lnb); d.opq = DF(c.opq);
-        d.f_q = DF(c.f_q); d.tb_bq = DF(c.tb_bq); d.tb_sq = DF(c.tb_sq); d.iopq = DF(c.iopq);
-        d.qe1 = DF(c.qe1); d.qe2 = DF(c.qe2); d.pe1 = DF(c.pe1); d.pe2 = DF(c.pe2); d.ftail = DF(c.ftail);
-        d.ic = DF(c.ic);
-        d.nterm = nt;
-        b.g1 = DF(a.g1); b.g2 = DF(a.g2); b.rc2 = DF(a.rc2);
-        b.nsub = 0; b.kind = a.kind; b.epl = a.epl;
-    }
 }
 
 // the evaluation's lens blocks: LensK<double> first, then LensK<float>, then the

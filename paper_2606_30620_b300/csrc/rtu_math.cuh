@@ -346,45 +346,63 @@ struct EplC {
 // q = (1 - c)/(1 + c) gives f = (1 - q)/(1 + q) = c, 1 + q = 2/(1 + c), and the
 // position angle's cos, sin follow from cos 2 phi = e1/c, sin 2 phi = e2/c by the
 // half-angle formulas (phi = atan2(e2, e1)/2 in (-pi/2, pi/2], so cos phi >= 0 and
-// sin phi takes the sign of e2)
+// sin phi takes the sign of e2).
+// In three independent parts, so that three threads can take one chain each (the
+// caller passes c = sqrt(max(e1^2 + e2^2, 1e-30))):
+//   part 0  the frame (cos phi, sin phi), 1/f and the angle's chain factors
+//   part 1  q, sqrt q, b = theta_E sqrt q, log b and the factors of 1 + q
+//   part 2  dq/de1, dq/de2, the tail factor f/(1 - f) and (t/b) db/dtheta_E
+constexpr int EPL_NSCAL = 25;      // the leading members of EplC, x0 .. ic, all of type T
+template <typename T>
+RTU_HD void epl_scalars_part(EplC<T>& C, const double* p, bool epl, double cc, int part) {
+    const double e1 = p[2], e2 = p[3];
+    const double t = (epl ? p[1] : 2.0) - 1.0;
+    if (part == 0) {
+        const double icc = 1.0 / cc;
+        const double c2 = e1 * icc, s2 = e2 * icc;       // cos 2 phi, sin 2 phi
+        double cp, sp;
+        if (e1 == 0.0 && e2 == 0.0) {
+            cp = 1.0;                                    // a round lens: phi = atan2(0, 0)/2 = 0
+            sp = 0.0;
+        } else if (c2 >= 0.0) {
+            cp = sqrt(0.5 * (1.0 + c2));
+            sp = 0.5 * s2 / cp;
+        } else {
+            sp = sqrt(0.5 * (1.0 - c2));
+            if (s2 < 0.0) sp = -sp;
+            cp = 0.5 * fabs(s2) / fabs(sp);
+        }
+        C.x0 = (T)p[4]; C.y0 = (T)p[5]; C.cp = (T)cp; C.sp = (T)sp; C.cc = (T)cc;
+        C.e1 = (T)e1; C.e2 = (T)e2; C.thE = (T)p[0]; C.t = (T)t;
+        C.pe1 = (T)(0.5 * c2 * icc);                    // dphi/de2 coefficient: e1/(2 c^2)
+        C.pe2 = (T)(0.5 * s2 * icc);                    // -dphi/de1 coefficient: e2/(2 c^2)
+        C.ic = (T)icc;                                  // 1/f
+    } else if (part == 1) {
+        const double i1pc = 1.0 / (1.0 + cc);
+        const double q = (1.0 - cc) * i1pc;
+        const double sq = sqrt(q);
+        const double b = p[0] * sq;
+        C.q = (T)q; C.sq = (T)sq; C.b = (T)b;
+        C.pref0 = (T)(b * (1.0 + cc));                  // 2 b/(1 + q)
+        C.lnb = (T)log(b); C.opq = (T)(2.0 * i1pc);     // 1 + q
+        C.f_q = (T)(-0.5 * (1.0 + cc) * (1.0 + cc));    // df/dq = -2/(1 + q)^2
+        C.tb_bq = (T)(0.5 * t / q);                     // (t/b) db/dq, b = theta_E sqrt(q)
+        C.iopq = (T)(0.5 * (1.0 + cc));                 // 1/(1 + q)
+    } else {
+        const double icc = 1.0 / cc, i1pc = 1.0 / (1.0 + cc);
+        const double c2 = e1 * icc, s2 = e2 * icc;
+        const double q_c = -2.0 * i1pc * i1pc;          // dq/dc
+        C.qe1 = (T)(q_c * c2);                          // dq/de1 = q_c e1/c
+        C.qe2 = (T)(q_c * s2);                          // dq/de2 = q_c e2/c
+        C.ftail = (T)(cc / (1.0 - cc));                 // f/(1 - f), f = c
+        C.tb_sq = (T)(t / p[0]);                        // (t/b) db/dtheta_E
+    }
+}
+
 template <typename T>
 RTU_HD void epl_scalars(EplC<T>& C, const double* p, bool epl) {
-    const double e1 = p[2], e2 = p[3];
-    const double cc = sqrt(fmax(e1 * e1 + e2 * e2, 1e-30));
-    const double icc = 1.0 / cc;
-    const double i1pc = 1.0 / (1.0 + cc);
-    const double q = (1.0 - cc) * i1pc;
-    const double c2 = e1 * icc, s2 = e2 * icc;       // cos 2 phi, sin 2 phi
-    double cp, sp;
-    if (e1 == 0.0 && e2 == 0.0) {
-        cp = 1.0;                                    // a round lens: phi = atan2(0, 0)/2 = 0
-        sp = 0.0;
-    } else if (c2 >= 0.0) {
-        cp = sqrt(0.5 * (1.0 + c2));
-        sp = 0.5 * s2 / cp;
-    } else {
-        sp = sqrt(0.5 * (1.0 - c2));
-        if (s2 < 0.0) sp = -sp;
-        cp = 0.5 * fabs(s2) / fabs(sp);
-    }
-    const double t = (epl ? p[1] : 2.0) - 1.0;
-    const double sq = sqrt(q);
-    const double b = p[0] * sq;
-    C.x0 = (T)p[4]; C.y0 = (T)p[5]; C.cp = (T)cp; C.sp = (T)sp; C.q = (T)q; C.cc = (T)cc;
-    C.e1 = (T)e1; C.e2 = (T)e2; C.thE = (T)p[0]; C.sq = (T)sq; C.b = (T)b; C.t = (T)t;
-    C.pref0 = (T)(b * (1.0 + cc));                  // 2 b/(1 + q)
-    C.lnb = (T)log(b); C.opq = (T)(2.0 * i1pc);     // 1 + q
-    C.f_q = (T)(-0.5 * (1.0 + cc) * (1.0 + cc));    // df/dq = -2/(1 + q)^2
-    C.tb_bq = (T)(0.5 * t / q);                     // (t/b) db/dq, b = theta_E sqrt(q)
-    C.tb_sq = (T)(t / p[0]);                        // (t/b) db/dtheta_E
-    C.iopq = (T)(0.5 * (1.0 + cc));                 // 1/(1 + q)
-    const double q_c = -2.0 * i1pc * i1pc;          // dq/dc
-    C.qe1 = (T)(q_c * c2);                          // dq/de1 = q_c e1/c
-    C.qe2 = (T)(q_c * s2);                          // dq/de2 = q_c e2/c
-    C.pe1 = (T)(0.5 * c2 * icc);                    // dphi/de2 coefficient: e1/(2 c^2)
-    C.pe2 = (T)(0.5 * s2 * icc);                    // -dphi/de1 coefficient: e2/(2 c^2)
-    C.ftail = (T)(cc / (1.0 - cc));                 // f/(1 - f), f = c
-    C.ic = (T)icc;                                  // 1/f
+    const double cc = sqrt(fmax(p[2] * p[2] + p[3] * p[3], 1e-30));
+    for (int part = 0; part < 3; ++part) epl_scalars_part(C, p, epl, cc, part);
 }
 
 // coefficient n >= 1 of the two sums from A_{n-1} (running), c_n and D_n
