@@ -616,6 +616,19 @@ __global__ void __launch_bounds__(CTA_R, sizeof(T) == 4 && !LIN ? 8 : 6) k_rende
     if (E.image_out && !deferred) reinterpret_cast<T*>(E.image_out)[pixel] = val;
 }
 
+// Distance of a double-float grid coordinate from the nearest integer (a cell edge
+// or the grid boundary), in cells
+__device__ __forceinline__ float df_edge_dist(const DF& g) {
+    const float r = rintf(g.hi);
+    return fabsf((g.hi - r) + g.lo);      // g.hi - r is exact
+}
+// floor of a double-float value (hi may have rounded up onto the integer above it)
+__device__ __forceinline__ int df_floor(const DF& g) {
+    int i = (int)floorf(g.hi);
+    if ((float)i == g.hi && g.lo < 0.0f) --i;
+    return i;
+}
+
 // the deferred near-edge rays of the float path, traced and decided in double
 constexpr int EDGE_NT = 128;
 constexpr int EDGE_CTAS = 16;      // CTAs per evaluation (default; E.n_edge when tuned)
@@ -627,17 +640,26 @@ __global__ void __launch_bounds__(EDGE_NT) k_render_edge(const __grid_constant__
     __shared__ LensK<DF> Kdf;
     __shared__ double trd[TR_HDR + 4 * (MAXM + 2)];
     __shared__ double Ud[MAXM + 2];
+    __shared__ DF trx[TR_HDR + 4 * (MAXM + 2)];
+    __shared__ DF Ux[MAXM + 2];
     load_lensk(Kd, E.lensk);
     load_transform<double>(E, trd, Ud);
     __syncthreads();
     // the lens in double-float (about 48 bits) unless subhaloes are present; the
-    // CDF map and the cell decision in double
+    // Hermite map in double-float too, with the cell decided from it where the grid
+    // coordinate is farther from every cell edge than the map's double-float error
+    // bound, else (rarely) by the map in double from the same position
     const bool use_df = Kd.nsub == 0;
+    const int n = E.n_src, K = E.n_nodes + 2, s2 = E.s * E.s;
+    const bool map_df = use_df && E.transform != RTU_TRANSFORM_LINEAR;
     if (use_df) {
         load_lensk(Kdf, lensk_df_src(E.lensk));
+        if (map_df) {
+            for (int i = threadIdx.x; i < TR_HDR + 4 * K; i += EDGE_NT) trx[i] = DF(trd[i]);
+            for (int j = threadIdx.x; j < K; j += EDGE_NT) Ux[j] = DF(Ud[j]);
+        }
         __syncthreads();
     }
-    const int n = E.n_src, K = E.n_nodes + 2, s2 = E.s * E.s;
     const int cnt = min(*E.ecount, E.n_img * E.n_img * s2);
     const float* grid = reinterpret_cast<const float*>(E.src);
     float* img = reinterpret_cast<float*>(E.img);
@@ -651,19 +673,63 @@ __global__ void __launch_bounds__(EDGE_NT) k_render_edge(const __grid_constant__
         const int pixel = ray / s2, q = ray - pixel * s2;
         double xd, yd, yx, yy;
         ray_pos(E.n_img, E.pix, E.s, pixel, q, xd, yd);
+        int cell = -1, i0 = 0, j0 = 0;
+        float fxf = 0.0f, fyf = 0.0f;
+        bool decided = false;
         if (use_df) {
             DF bxf, byf;
             lens_beta_smooth<DF>(Kdf, DF(xd), DF(yd), bxf, byf);
-            rtu_coords_from_beta(E, trd, Ud, K, bxf.to_double(), byf.to_double(), yx, yy);
+            if (map_df) {
+                // the Hermite map (App. C iv) in double-float: z, its interval, the value
+                const DF isg = DF(1.0f) / trx[2];
+                const DF zx = (bxf - trx[0]) * isg, zy = (byf - trx[1]) * isg;
+                const DF* X = trx + TR_HDR;
+                const int jx = cdf_interval<DF>(X, K, zx), jy = cdf_interval<DF>(X + K, K, zy);
+                const DF gx = cdf_value<DF>(X, Ux, X + 2 * K, K, jx, zx) * DF((float)(n - 1));
+                const DF gy = cdf_value<DF>(X + K, Ux, X + 3 * K, K, jy, zy) * DF((float)(n - 1));
+                // error bound of the double-float map, in cells: 2^-36 (over 2^10 times
+                // the pair type's tested 2^-46 per operation) of the terms, scaled by
+                // |z| and a bound on the map's slope in the interval -- the knots'
+                // slopes and three times the secant (a narrow interval amplifies the
+                // error of z - X_j by 1/h); an interval too narrow to measure in float
+                // leaves the ray to the double map
+                auto slope_bound = [&](const DF* Xa, const DF* da, int j) -> float {
+                    const int k0 = j < 0 ? 0 : j;
+                    float sb = fmaxf(da[k0].hi, da[min(k0 + 1, K - 1)].hi);
+                    if (j >= 0 && j < K - 1) {
+                        const float h = (Xa[j + 1].hi - Xa[j].hi) + (Xa[j + 1].lo - Xa[j].lo);
+                        sb = h > 0.0f ? fmaxf(sb, 3.0f * (Ux[j + 1].hi - Ux[j].hi) / h) : INFINITY;
+                    }
+                    return sb;
+                };
+                const float sx = slope_bound(X, X + 2 * K, jx), sy = slope_bound(X + K, X + 3 * K, jy);
+                const float tol_x = (float)(n - 1) * 1.4551915e-11f * (1.0f + fabsf(zx.hi)) * (1.0f + sx) + 1e-12f;
+                const float tol_y = (float)(n - 1) * 1.4551915e-11f * (1.0f + fabsf(zy.hi)) * (1.0f + sy) + 1e-12f;
+                if (df_edge_dist(gx) > tol_x && df_edge_dist(gy) > tol_y) {
+                    decided = true;
+                    const DF zero(0.0f, 0.0f), top((float)(n - 1), 0.0f);
+                    if (zero < gx && gx < top && zero < gy && gy < top) {
+                        i0 = df_floor(gx);
+                        j0 = df_floor(gy);
+                        fxf = (gx.hi - (float)i0) + gx.lo;
+                        fyf = (gy.hi - (float)j0) + gy.lo;
+                        cell = j0 * (n - 1) + i0;
+                    }
+                }
+            }
+            if (!decided) rtu_coords_from_beta(E, trd, Ud, K, bxf.to_double(), byf.to_double(), yx, yy);
         } else {
             rtu_coords_d(E, Kd, trd, Ud, K, xd, yd, yx, yy);
         }
-        double fx, fy;
-        int i0, j0;
-        const int cell = cell_of<double>(yx, yy, n, fx, fy, i0, j0);
+        if (!decided) {
+            double fx, fy;
+            cell = cell_of<double>(yx, yy, n, fx, fy, i0, j0);
+            fxf = (float)fx;
+            fyf = (float)fy;
+        }
         float v = 0.0f;
         if (cell >= 0) {
-            v = bilinear_at<float, float>(grid, n, i0, j0, (float)fx, (float)fy);
+            v = bilinear_at<float, float>(grid, n, i0, j0, fxf, fyf);
             atomicAdd(E.ccount + cell, 1);
             E.cell[at] = (e0 & (STG_NEAR | STG_DEFER)) | local | ((cell + 1) << STG_SHIFT);
         } else {
@@ -676,8 +742,17 @@ __global__ void __launch_bounds__(EDGE_NT) k_render_edge(const __grid_constant__
         if (atomicSub(E.pcnt + pixel, 1) == 1) {
             const unsigned long long mask = E.pdef[pixel];
             float val = img[pixel];
-            for (int qq = 0; qq < s2; ++qq)
-                if (mask >> qq & 1ull) val += __ldcg(E.rval + (size_t)pixel * s2 + qq);
+            // the deferred values' loads issued 16 at a time, then added in order
+            const float* rv = E.rval + (size_t)pixel * s2;
+            for (int q0 = 0; q0 < s2; q0 += 16) {
+                float r[16];
+#pragma unroll
+                for (int u = 0; u < 16; ++u)
+                    r[u] = (q0 + u < s2 && (mask >> (q0 + u) & 1ull)) ? __ldcg(rv + q0 + u) : 0.0f;
+#pragma unroll
+                for (int u = 0; u < 16; ++u)
+                    if (q0 + u < s2 && (mask >> (q0 + u) & 1ull)) val += r[u];
+            }
             val = val / (float)s2;
             img[pixel] = val;
             if (E.image_out) reinterpret_cast<float*>(E.image_out)[pixel] = val;
