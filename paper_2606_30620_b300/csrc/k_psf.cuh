@@ -63,6 +63,27 @@ __device__ __forceinline__ void like_last_cta(const EvalArgs& E) {
     if (last) like_final_cta(E);
 }
 
+// The CTA's two likelihood partials (sum r^2, sum over the mask) from per-thread
+// values: a warp tree (compensated pairs for float), the warps' pairs combined in
+// order by two threads, then one conversion to double each.  (Every FP64
+// instruction takes a slot of the SM's FP64 pipe for the whole warp, however few of
+// its lanes are active, so the pairs stay in the kernel's type until the end.)  The
+// double path's pairs carry a zero low part: the same sums as adding doubles in order.
+template <typename T, int NT>
+__device__ __forceinline__ void like_cta_partials(const EvalArgs& E, int tile, T r2t, T r2mt) {
+    typedef decltype(warp_pair_sum(T(0))) P;
+    __shared__ P red[2][NT / 32];
+    const P p0 = warp_pair_sum(r2t), p1 = warp_pair_sum(r2mt);
+    if ((threadIdx.x & 31) == 0) { red[0][threadIdx.x >> 5] = p0; red[1][threadIdx.x >> 5] = p1; }
+    __syncthreads();
+    if (threadIdx.x < 2) {
+        P r = red[threadIdx.x][0];
+        for (int w = 1; w < NT / 32; ++w) pair_add(r, red[threadIdx.x][w]);
+        E.lpart[tile * 2 + threadIdx.x] = (double)r.x + (double)r.y;
+        __threadfence();
+    }
+}
+
 __device__ __forceinline__ void psf_tile_of(const EvalArgs& E, int tile, int& ti, int& tj) {
     const int nt = (E.n_img + PSF_T - 1) / PSF_T;
     tj = tile / nt;
@@ -209,7 +230,6 @@ __global__ void __launch_bounds__(PSFT_NT) k_psf_like_t(const __grid_constant__ 
     const int tile = blockIdx.x - B.tile0[ev];
     __shared__ __align__(16) float in[PsfT<KT>::W][PsfT<KT>::P];
     __shared__ __align__(16) float kw[KT * PsfT<KT>::KP];
-    __shared__ double red[2][PSFT_NT / 32];
     const int n = E.n_img;
     int ti, tj;
     psf_tile_of(E, tile, ti, tj);
@@ -239,17 +259,8 @@ __global__ void __launch_bounds__(PSFT_NT) k_psf_like_t(const __grid_constant__ 
             if (E.mask[j * n + i]) r2mf += r * r;
         }
     }
-    // per-thread float partials of 8 pixels, a compensated warp tree, then double
-    // across warps
-    const double r2 = warp_sum_lane0(r2f), r2m = warp_sum_lane0(r2mf);
-    if ((threadIdx.x & 31) == 0) { red[0][threadIdx.x >> 5] = r2; red[1][threadIdx.x >> 5] = r2m; }
-    __syncthreads();
-    if (threadIdx.x < 2) {
-        double sacc = 0.0;
-        for (int w = 0; w < PSFT_NT / 32; ++w) sacc += red[threadIdx.x][w];
-        E.lpart[tile * 2 + threadIdx.x] = sacc;
-        __threadfence();
-    }
+    // per-thread float partials of 8 pixels
+    like_cta_partials<float, PSFT_NT>(E, tile, r2f, r2mf);
     like_last_cta(E);
 }
 
@@ -304,10 +315,28 @@ __device__ __forceinline__ void psf_sep_passes(const EvalArgs& E, const T* src, 
         const T x = (T)E.psf_uv[i];
         if (i < K) u[i] = x; else v[i - K] = x;
     }
-    for (int w = threadIdx.x; w < W * W; w += PSFS_NT) {
-        const int r = w / W, q = w - r * W;
-        const int gj = j0 - c + r, gi = i0 - c + q;
-        in[r][q] = (gj >= 0 && gj < n && gi >= 0 && gi < n) ? src[gj * n + gi] : T(0);
+    // the input window with its halo: rows by warp, columns by lane (no division per
+    // element), each thread's loads issued before its stores
+    {
+        constexpr int NWS = PSFS_NT / 32, RPW = (PSFS_W + NWS - 1) / NWS;
+        static_assert(PSFS_W <= 64, "two columns per lane");
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        T val[RPW][2];
+#pragma unroll
+        for (int k = 0; k < RPW; ++k)
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {
+                const int r = wid + k * NWS, q = lane + 32 * hh;
+                const int gj = j0 - c + r, gi = i0 - c + q;
+                val[k][hh] = (r < W && q < W && gj >= 0 && gj < n && gi >= 0 && gi < n) ? src[gj * n + gi] : T(0);
+            }
+#pragma unroll
+        for (int k = 0; k < RPW; ++k)
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {
+                const int r = wid + k * NWS, q = lane + 32 * hh;
+                if (r < W && q < W) in[r][q] = val[k][hh];
+            }
     }
     __syncthreads();
     // along x: h[r][x] = sum_a v[a] in[r][x + 2c - a] (convolution) or in[r][x + a]
@@ -370,7 +399,6 @@ __global__ void __launch_bounds__(PSFS_NT) k_psf_like_sep(const __grid_constant_
     __shared__ T in[PSFS_W][PSFS_W + 1];
     __shared__ T h[PSFS_W][PSF_T + 1];
     __shared__ T u[PSF_MAXK], v[PSF_MAXK];
-    __shared__ double red[2][PSFS_NT / 32];
     const int n = E.n_img;
     int ti, tj;
     psf_tile_of(E, tile, ti, tj);
@@ -394,17 +422,8 @@ __global__ void __launch_bounds__(PSFS_NT) k_psf_like_sep(const __grid_constant_
             if (E.mask[j * n + i]) r2mt += r * r;
         }
     }
-    // per-thread partials of 4 pixels, a (compensated, for float) warp tree, then
-    // double across warps, fixed order
-    const double r2 = warp_sum_lane0(r2t), r2m = warp_sum_lane0(r2mt);
-    if ((threadIdx.x & 31) == 0) { red[0][threadIdx.x >> 5] = r2; red[1][threadIdx.x >> 5] = r2m; }
-    __syncthreads();
-    if (threadIdx.x < 2) {
-        double sacc = 0.0;
-        for (int w = 0; w < PSFS_NT / 32; ++w) sacc += red[threadIdx.x][w];
-        E.lpart[tile * 2 + threadIdx.x] = sacc;
-        __threadfence();
-    }
+    // per-thread partials of 4 pixels
+    like_cta_partials<T, PSFS_NT>(E, tile, r2t, r2mt);
     like_last_cta(E);
 }
 

@@ -867,11 +867,13 @@ __device__ __forceinline__ void cell_offsets(const EvalArgs& E) {
 // consecutive list positions (the rays cluster in the few render tiles the grid's
 // reach leaves unculled, so shares by render warp would be uneven) and walks the
 // render warps it overlaps: it finds the first with a 32-wide probe of the offsets,
-// and the near-core entries before its share in that warp with one strided count.
-// It loads up to four groups of 32 entries before it stores any and keeps their slot
-// atomics in flight together.
+// and the near-core entries before its share in that warp with one strided count;
+// the next ones from a window of 32 consecutive offsets held one per lane (a ballot,
+// no memory round trip, until the window is used up).  It loads up to CMP_G groups
+// of 32 entries before it stores any and keeps their slot atomics in flight together.
 constexpr int CMP_NT = 256;
 constexpr int CMP_CTAS = 20;
+constexpr int CMP_G = 4;
 // the largest u in [from, nu) with useg[u] <= pos (useg non-decreasing, useg[from] <= pos),
 // by a 32-ary search: the warp's lanes probe 32 evenly spaced offsets of the range
 // and keep the segment below the first one past pos (about log_32(nu) rounds)
@@ -937,33 +939,54 @@ __global__ void __launch_bounds__(CMP_NT) k_compact(const __grid_constant__ Batc
         return render_pixel(E.n_img, uu / (CTA_R / 32), (uu % (CTA_R / 32)) * 32 + lane, valid);
     };
     int pix = lane_pixel(u);
+    // the offsets window: lane l holds useg[wb + l] (useg[nu] = the total past the end)
+    // and nseg[wb + l]
+    int wb, wv, wn;
+    auto window_at = [&](int base) {
+        wb = base;
+        const int idx = min(base + lane, nu);
+        wv = E.useg[idx];
+        wn = E.nseg[idx];
+    };
+    window_at(u);
     int pos = lo;
     while (pos < hi) {
-        if (u + 1 < nu && E.useg[u + 1] <= pos) {
-            u = cmp_find_warp(E.useg, nu, u + 1, pos);
-            nat = E.nseg[u];
+        if (u + 1 - wb >= 32) window_at(u);
+        if (u + 1 < nu && __shfl_sync(0xffffffffu, wv, u + 1 - wb) <= pos) {
+            // the last render warp from u + 1 on whose offset is at most pos
+            const int from = u + 1;
+            for (;;) {
+                const unsigned past = __ballot_sync(0xffffffffu, wb + lane >= from && (wb + lane >= nu || wv > pos));
+                if (past) {
+                    u = wb + __ffs(past) - 2;
+                    break;
+                }
+                window_at(wb + 32);
+            }
+            if (u < wb || u + 1 - wb >= 32) window_at(u);   // (the answer may precede a slid window)
+            nat = __shfl_sync(0xffffffffu, wn, u - wb);
             pix = lane_pixel(u);
         }
-        const int o = E.useg[u];
-        const int end = min(hi, min(u + 1 < nu ? E.useg[u + 1] : total, o + cap));
+        const int o = __shfl_sync(0xffffffffu, wv, u - wb);
+        const int end = min(hi, min(u + 1 < nu ? __shfl_sync(0xffffffffu, wv, u + 1 - wb) : total, o + cap));
         if (end <= pos) break;          // inconsistent offsets: leave the rest unwritten
         const int* stg = E.cell + (size_t)u * cap;
-        for (int g0 = pos - o; g0 < end - o; g0 += 128) {
+        for (int g0 = pos - o; g0 < end - o; g0 += 32 * CMP_G) {
             const int gend = end - o;
-            int ent[4], cell[4], slot[4];
-            bool nr[4];
-            unsigned grp[4];
+            int ent[CMP_G], cell[CMP_G], slot[CMP_G];
+            bool nr[CMP_G];
+            unsigned grp[CMP_G];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
+            for (int j = 0; j < CMP_G; ++j) {
                 const int i = g0 + 32 * j + lane;
                 ent[j] = i < gend ? stg[i] : 0;
             }
-            // decode the four groups, then their slot atomics (one per group of lanes
+            // decode the groups, then their slot atomics (one per group of lanes
             // sharing the cell, slots by lane order inside the group; the order of the
             // records inside a cell is free: the cell sums are exact integer sums), all
-            // four in flight before any result is used
+            // in flight before any result is used
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
+            for (int j = 0; j < CMP_G; ++j) {
                 const int i = g0 + 32 * j + lane;
                 cell[j] = -1;
                 nr[j] = false;
@@ -979,7 +1002,7 @@ __global__ void __launch_bounds__(CMP_NT) k_compact(const __grid_constant__ Batc
                 if (cell[j] >= 0 && lane == __ffs(grp[j]) - 1) slot[j] = atomicAdd(E.cursor + cell[j], __popc(grp[j]));
             }
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
+            for (int j = 0; j < CMP_G; ++j) {
                 const int i = g0 + 32 * j + lane;
                 if (g0 + 32 * j >= gend) break;
                 const int leader = cell[j] >= 0 ? __ffs(grp[j]) - 1 : lane;
