@@ -232,7 +232,11 @@ __global__ void __launch_bounds__(CTA_C) k_centre_adj(const __grid_constant__ Ba
     __shared__ LensK<T> L;
     __shared__ LensK<double> Ld;
     __shared__ double hdr[4], mu[2];
-    __shared__ double red[CTA_C / 32][8];
+    // per-warp partials as (compensated, for float) pairs of the kernel's type: every
+    // FP64 instruction takes a slot of the SM's FP64 pipe for the whole warp however
+    // few lanes are active, so the conversion to double waits for the CTA's sums
+    typedef decltype(warp_pair_sum(T(0))) P;
+    __shared__ P red[CTA_C / 32][8];
     load_lensk(L, lensk_src<T>(E.lensk));
     if (sizeof(T) == 4) load_lensk(Ld, E.lensk);
     if (threadIdx.x < 4) hdr[threadIdx.x] = E.tadj[threadIdx.x];
@@ -282,7 +286,7 @@ __global__ void __launch_bounds__(CTA_C) k_centre_adj(const __grid_constant__ Ba
     double* out = E.cadj + (size_t)tile * nl;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int p = 0; p < 8; ++p) {
-        const double v = warp_sum_lane0(acc[p]);
+        const P v = warp_pair_sum(acc[p]);
         if (lane == 0) red[wid][p] = v;
     }
     // the double terms of the warps that hold a near-core ray (fixed shuffle tree)
@@ -294,23 +298,25 @@ __global__ void __launch_bounds__(CTA_C) k_centre_adj(const __grid_constant__ Ba
     }
     __syncthreads();
     if (threadIdx.x < 8) {
-        double r = 0.0;
-        for (int w = 0; w < CTA_C / 32; ++w) r += red[w][threadIdx.x] + redd[w][threadIdx.x];
-        out[threadIdx.x] = r;
+        P r = red[0][threadIdx.x];
+        for (int w = 1; w < CTA_C / 32; ++w) pair_add(r, red[w][threadIdx.x]);
+        double rd = (double)r.x + (double)r.y;
+        for (int w = 0; w < CTA_C / 32; ++w) rd += redd[w][threadIdx.x];
+        out[threadIdx.x] = rd;
     }
     for (int h = 0; h < nsub; ++h) {
         __syncthreads();
         T a5[5] = {T(0), T(0), T(0), T(0), T(0)};
         if (k < N) sub_vjp<T>(L, h, (T)xd, (T)yd, (T)gb[0], (T)gb[1], a5);
         for (int c = 0; c < 5; ++c) {
-            const double v = warp_sum_lane0(a5[c]);
+            const P v = warp_pair_sum(a5[c]);
             if (lane == 0) red[wid][c] = v;
         }
         __syncthreads();
         if (threadIdx.x < 5) {
-            double r = 0.0;
-            for (int w = 0; w < CTA_C / 32; ++w) r += red[w][threadIdx.x];
-            out[8 + 5 * h + threadIdx.x] = r;
+            P r = red[0][threadIdx.x];
+            for (int w = 1; w < CTA_C / 32; ++w) pair_add(r, red[w][threadIdx.x]);
+            out[8 + 5 * h + threadIdx.x] = (double)r.x + (double)r.y;
         }
     }
 }
