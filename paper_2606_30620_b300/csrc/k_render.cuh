@@ -1497,10 +1497,19 @@ __device__ __forceinline__ long long fix_term(float w, float gs) {
 }
 // (the 32-bit accumulation below casts this back to int: exact, |value| < 2^22)
 __device__ __forceinline__ long long fix_term(double w, double gs) { return __double2ll_rn(w * gs); }
+// The float path's integer sum as a (hi, lo) float pair on the FP32 pipe: its terms
+// are below 2^22 and a cell holds fewer than 2^26 rays, so |k| < 2^48 and
+// k = a 2^24 + b with a, b exact in float; an exact two-sum of a 2^24 and b gives
+// hi = k rounded to float and lo = the rest, both scaled by the power of two 2^-S.
+// (A conversion through double would cost an FP64 instruction per step, and the
+// SM's FP64 pipe takes one warp instruction at a time whatever the active lanes.)
 __device__ __forceinline__ float2 fix_to_pair(long long k, int S, float) {
-    const double d = (double)k * pow2_of(-S, 0.0);
-    const float hi = (float)d;
-    return make_float2(hi, (float)(d - (double)hi));
+    const float fa = (float)(int)(k >> 24) * 16777216.0f;      // exact
+    const float fb = (float)(int)(k & 0xffffff);              // exact
+    float hi, lo;
+    df_two_sum(fa, fb, hi, lo);
+    const float p = pow2_of(-S, 0.0f);
+    return make_float2(hi * p, lo * p);
 }
 __device__ __forceinline__ double2 fix_to_pair(long long k, int S, double) {
     return make_double2((double)k * pow2_of(-S, 0.0), 0.0);
