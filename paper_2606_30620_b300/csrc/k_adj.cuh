@@ -50,9 +50,10 @@ __global__ void __launch_bounds__(CDF_NT) k_cdf_adj(const __grid_constant__ Batc
     __shared__ double gXr[MAXM + 2], gpr[MAXM + 2], gc[MAXM], gQ[MAXM];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const double* tr = E.trd;
-    const double sigma = tr[2], isig = 1.0 / sigma;
+    const double sigma = tr[2];
     if (E.transform == RTU_TRANSFORM_UNIFORM) {
         if (ax != 0) return;
+        const double isig = 1.0 / sigma;
         for (int col = wid; col < NACC_FIX + 4 * K; col += CDF_NT / 32) {
             const double v = apart_col(E, col);
             if (lane == 0) tot[col] = v;
@@ -108,47 +109,53 @@ __global__ void __launch_bounds__(CDF_NT) k_cdf_adj(const __grid_constant__ Batc
     if (cstaged)
         for (int i = threadIdx.x; i < ncheb; i += CDF_NT) scheb[i] = E.cheb[i];
     const double* cheb = cstaged ? scheb : E.cheb;
-    // this axis's columns: dmu_a, dsigma (axis 0), knots X and slopes d; a warp's
-    // columns' rows loaded before any of its shuffle trees (fixed lane stride and tree)
+    // 1/sigma by one thread (an FP64 divide in every warp would queue 8 of them on
+    // the SM's FP64 pipe, which takes one warp instruction at a time)
+    __shared__ double isig_sh;
+    if (threadIdx.x == 0) isig_sh = 1.0 / sigma;
+    // this axis's columns: dmu_a, dsigma (axis 0), knots X and slopes d; each column's
+    // rows in CDF_PARTS contiguous parts, one per lane of a group of adjacent lanes
+    // (in order), the parts combined by a fixed shuffle tree -- about a third of the
+    // FP64 instructions of a lane-strided warp tree per column
+    constexpr int CDF_PARTS = 4;
     const int ncol = 2 + 2 * K;
-    constexpr int NWD = CDF_NT / 32, CPW = (2 + 2 * (MAXM + 2) + NWD - 1) / NWD;
     {
         const int rows = E.n_row_adj;
-        double v[CPW];
-#pragma unroll
-        for (int j = 0; j < CPW; ++j) {
-            const int w = wid + j * NWD;
-            v[j] = 0.0;
+        const int q = (rows + CDF_PARTS - 1) / CDF_PARTS;
+        for (int base = wid * 32; base < ncol * CDF_PARTS; base += CDF_NT) {      // warp-uniform
+            const int it = base + lane, w = it / CDF_PARTS, part = it - w * CDF_PARTS;
+            int col = 0;
+            double v = 0.0;
             if (w < ncol) {
-                const int col = w == 0 ? 8 + ax : (w == 1 ? 10 : (w < 2 + K ? NACC_FIX + ax * K + (w - 2)
-                                                                           : NACC_FIX + 2 * K + ax * K + (w - 2 - K)));
+                col = w == 0 ? 8 + ax : (w == 1 ? 10 : (w < 2 + K ? NACC_FIX + ax * K + (w - 2)
+                                                                 : NACC_FIX + 2 * K + ax * K + (w - 2 - K)));
                 const double* a = E.apart + (size_t)col * rows;
-#pragma unroll 4
-                for (int t = lane; t < rows; t += 32) v[j] += a[t];
+                const int r0 = part * q, r1 = min(rows, r0 + q);
+#pragma unroll 8
+                for (int t = r0; t < r1; ++t) v += a[t];
             }
-        }
-#pragma unroll
-        for (int j = 0; j < CPW; ++j) {
-            const int w = wid + j * NWD;
-            if (w >= ncol) break;            // warp-uniform
-            double x = v[j];
-            for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-            const int col = w == 0 ? 8 + ax : (w == 1 ? 10 : (w < 2 + K ? NACC_FIX + ax * K + (w - 2)
-                                                                       : NACC_FIX + 2 * K + ax * K + (w - 2 - K)));
-            if (lane == 0) tot[col] = x;
+            v += __shfl_xor_sync(0xffffffffu, v, 1);     // (p0 + p1), (p2 + p3)
+            v += __shfl_xor_sync(0xffffffffu, v, 2);     // then their sum
+            if (w < ncol && part == 0) tot[col] = v;
         }
     }
     __syncthreads();
+    const double isig = isig_sh;
     const double* gX = tot + NACC_FIX + ax * K;
     const double* gd = tot + NACC_FIX + 2 * K + ax * K;
     const double* Xf = sXf;      // guarded knots
     const double* Xr = sXr;      // raw knots
     const double* pr = spr;      // raw p'
     const double* sl = ssl;      // slopes 1/p'
-    double span = Xr[K - 1] - Xr[0];
-    const bool span_ok = span > 0.0;
-    if (!span_ok) span = fabs(span) + 1e-300;
-    const double floor_d = 1e-6 * span;
+    // the floor's span: formed by the threads that use it (one warp for K <= 32)
+    double span = 0.0, floor_d = 0.0;
+    bool span_ok = true;
+    if (threadIdx.x < ((K + 31) & ~31)) {
+        span = Xr[K - 1] - Xr[0];
+        span_ok = span > 0.0;
+        if (!span_ok) span = fabs(span) + 1e-300;
+        floor_d = 1e-6 * span;
+    }
     // back through the slope floor (per point) ...
     for (int j = threadIdx.x; j < K; j += CDF_NT) {
         const double gp = -gd[j] * sl[j] * sl[j];    // slope d = 1/p'
