@@ -58,6 +58,10 @@ __device__ __forceinline__ DF operator+(const DF& a, const DF& b) {
     return DF(s1, s2);
 }
 __device__ __forceinline__ DF operator-(const DF& a) { return DF(-a.hi, -a.lo); }
+// the EPL series' evaluation takes its float tail for this type (the primary
+// template, false, is in rtu_math.cuh)
+template <typename T> struct epl_pair_type;
+template <> struct epl_pair_type<DF> { static constexpr bool value = true; };
 __device__ __forceinline__ DF operator-(const DF& a, const DF& b) { return a + (-b); }
 __device__ __forceinline__ DF operator*(const DF& a, const DF& b) {
     float p, e;

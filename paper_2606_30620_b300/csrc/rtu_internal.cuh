@@ -361,7 +361,8 @@ struct LensK {
     EplC<T> C;
     T g1, g2, rc2;           // shear; squared radius of the near-core FP64 island
     T sub[MAX_SUB][5];       // kappa_s, r_s, tau, x_s, y_s
-    int nsub, kind, epl, pad_;
+    int nsub, kind, epl;
+    int nsplit;              // double-float block: the first series power summed in float
 };
 
 template <typename T>
@@ -387,7 +388,8 @@ __device__ inline void lens_rest(LensK<T>& K, const double* lens, int profile, i
 //      A_n = c_1 ... c_n and the sums D_n by warp scans, the warps synchronised by
 //      a named barrier), written in all three types, and the stopping index of each
 //      precision (1e-16 for double, 2e-8 for float: a third of the type's unit
-//      roundoff or less, as |c_n| <= f <= 1/4); meanwhile lane 0 of warps 3-5
+//      roundoff or less, as |c_n| <= f <= 1/4) and the first power the double-float
+//      evaluation sums in float (|A_n| <= 1e-9); meanwhile lane 0 of warps 3-5
 //      computes one of the three independent parts of the lens-only scalars in
 //      double (one chain per warp: lanes of one warp would run them one after the
 //      other); every thread involved forms c = |(e1, e2)| (= f) itself;
@@ -401,7 +403,7 @@ __device__ inline void lens_setup_par(LensK<double>* Kd, LensK<float>* Kf, LensK
     static_assert(offsetof(EplC<DF>, ic) == (EPL_NSCAL - 1) * sizeof(DF), "EplC scalars are contiguous");
     __shared__ double wA[3], wD[3];
     __shared__ EplC<double> sC;        // the double scalars (leading members only)
-    __shared__ int nt_sh[2];
+    __shared__ int nt_sh[3];
     const int tid = threadIdx.x;
     const bool epl = profile == 1;
     if (tid >= 96 && tid < 192 && (tid & 31) == 0) {
@@ -410,7 +412,7 @@ __device__ inline void lens_setup_par(LensK<double>* Kd, LensK<float>* Kf, LensK
         epl_scalars_part(sC, p, epl, cc, (tid >> 5) - 3);
     } else if (tid < 96) {
         const int lane = tid & 31, w = tid >> 5, n = tid + 1;
-        if (tid == 0) { nt_sh[0] = EPL_MAXT; nt_sh[1] = EPL_MAXT; }   // before the named barrier
+        if (tid == 0) { nt_sh[0] = EPL_MAXT; nt_sh[1] = EPL_MAXT; nt_sh[2] = EPL_MAXT; }   // before the named barrier
         // f = (1 - q)/(1 + q) with q = (1 - c)/(1 + c) is c itself
         const double f = sqrt(fmax(lens[2] * lens[2] + lens[3] * lens[3], 1e-30));
         const double t = (epl ? lens[1] : 2.0) - 1.0;
@@ -436,6 +438,7 @@ __device__ inline void lens_setup_par(LensK<double>* Kd, LensK<float>* Kf, LensK
         const double An = fabs(Ap * c);
         if (An <= 1e-16) atomicMin(&nt_sh[0], n);
         if (An <= 2e-8) atomicMin(&nt_sh[1], n);
+        if (An <= 1e-9) atomicMin(&nt_sh[2], n);
     }
     __syncthreads();
     if (tid < EPL_NSCAL) {
@@ -445,8 +448,11 @@ __device__ inline void lens_setup_par(LensK<double>* Kd, LensK<float>* Kf, LensK
         reinterpret_cast<DF*>(&Kx->C)[tid] = DF(v);
     } else if (tid == 32) {
         Kd->C.nterm = nt_sh[0];
-        Kx->C.nterm = nt_sh[0];            // the double-float copy sums as many terms as double
+        Kx->C.nterm = nt_sh[0];            // the double-float copy sums as many terms as double,
+        Kx->nsplit = nt_sh[2];             // those from |A_n| <= 1e-9 on in float
         Kf->C.nterm = nt_sh[1];
+        Kd->nsplit = 1 << 30;              // (no float tail)
+        Kf->nsplit = 1 << 30;
         lens_rest(*Kd, lens, profile, sub_kind, n_sub);
     } else if (tid == 64) {
         lens_rest(*Kf, lens, profile, sub_kind, n_sub);
@@ -494,7 +500,7 @@ __device__ __forceinline__ void lens_beta(const LensK<T>& K, T x, T y, T& bx, T&
 template <typename T>
 __device__ __forceinline__ void lens_beta_smooth(const LensK<T>& K, T x, T y, T& bx, T& by) {
     T ax, ay;
-    epl_alpha(K.C, x, y, ax, ay);
+    epl_alpha(K.C, x, y, ax, ay, K.nsplit);
     ax += K.g1 * x + K.g2 * y;
     ay += K.g2 * x - K.g1 * y;
     bx = x - ax;

@@ -340,6 +340,9 @@ struct EplC {
     EplTerm<T> term[EPL_MAXT + 1];
 };
 
+// whether T is the double-float pair type (specialised where that type is defined)
+template <typename T> struct epl_pair_type { static constexpr bool value = false; };
+
 // the lens-only scalars of the series (everything but the term tables), written with
 // as few divisions and roots as the algebra allows (FP64 divides, roots and
 // transcendentals are long serial chains on this part): with c = |(e1, e2)|,
@@ -495,8 +498,9 @@ RTU_HD T epl_tail_bound(const EplC<T>& C, const EplPart<T>& s) {
     return s.P * r_abs(C.term[s.m].a) * C.ftail;
 }
 
+// nsplit: for the double-float type, the first power summed in float (|A_n| <= 1e-9)
 template <typename T>
-RTU_HD void epl_alpha_finish(const EplC<T>& C, EplPart<T>& s, T& ax, T& ay) {
+RTU_HD void epl_alpha_finish(const EplC<T>& C, EplPart<T>& s, T& ax, T& ay, int nsplit = 1 << 30) {
     const T wre = s.wre, wim = s.wim;
     T pr, pi;
     if (sizeof(T) == 4) {
@@ -505,6 +509,25 @@ RTU_HD void epl_alpha_finish(const EplC<T>& C, EplPart<T>& s, T& ax, T& ay) {
         pi = T(0);
 #pragma unroll 4
         for (int n = C.nterm - 1; n >= 0; --n) {
+            const T nr = pr * wre - pi * wim + C.term[n].a;
+            pi = pr * wim + pi * wre;
+            pr = nr;
+        }
+    } else if constexpr (epl_pair_type<T>::value) {
+        // double-float: Horner's rule over the powers n >= nsplit in float (|A_n| <=
+        // 1e-9, so the float rounding of that tail is below 1e-16 of the leading
+        // term), continued in the pair type over the rest
+        const int N = C.nterm, m = nsplit < N ? nsplit : N;
+        float fr = C.term[N].a.hi, fi = 0.0f;
+        const float wr = wre.hi, wi = wim.hi;
+        for (int n = N - 1; n >= m; --n) {
+            const float nr = fr * wr - fi * wi + C.term[n].a.hi;
+            fi = fr * wi + fi * wr;
+            fr = nr;
+        }
+        pr = T(fr);
+        pi = T(fi);
+        for (int n = m - 1; n >= 0; --n) {
             const T nr = pr * wre - pi * wim + C.term[n].a;
             pi = pr * wim + pi * wre;
             pr = nr;
@@ -519,10 +542,10 @@ RTU_HD void epl_alpha_finish(const EplC<T>& C, EplPart<T>& s, T& ax, T& ay) {
 }
 
 template <typename T>
-RTU_HD void epl_alpha(const EplC<T>& C, T x, T y, T& ax, T& ay) {
+RTU_HD void epl_alpha(const EplC<T>& C, T x, T y, T& ax, T& ay, int nsplit = 1 << 30) {
     EplPart<T> s;
     epl_alpha_begin(C, x, y, 0, s);
-    epl_alpha_finish(C, s, ax, ay);
+    epl_alpha_finish(C, s, ax, ay, nsplit);
 }
 
 // Per-ray intermediates of the EPL deflection kept for the vector-Jacobian product.
