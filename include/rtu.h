@@ -330,7 +330,11 @@ rtu_status rtu_profile_timeline(char* buf, size_t bytes);
  * arithmetic).  Device buffers: x of n (op 0-2) or 2n (op 3-5) doubles, each
  * converted to a double-float (hi = x rounded to float, lo = the rest rounded);
  * y of n doubles receives hi + lo of the result: op 0 exp(x[i]), 1 log(x[i]),
- * 2 sqrt(x[i]), 3 x[2i] / x[2i+1], 4 x[2i] x[2i+1], 5 x[2i] + x[2i+1].
+ * 2 sqrt(x[i]), 3 x[2i] / x[2i+1], 4 x[2i] x[2i+1], 5 x[2i] + x[2i+1]; and the
+ * helpers of the near-edge pass's cell decision, 6 floor(x[i]) and 7 the distance of
+ * x[i] from the nearest integer (in float), and of the cell gather, 8 the float pair
+ * of the integer x[2i] (|x[2i]| < 2^48) scaled by 2^-x[2i+1] (0 <= x[2i+1] <= 122).
+ * op 8 takes 2n doubles like ops 3-5.
  * Stream-ordered; RTU_E_ARG on a bad op or null buffers. */
 rtu_status rtu_selftest_df(int32_t op, const double* x, double* y, int32_t n, void* stream);
 

@@ -1059,11 +1059,24 @@ rtu_status rtu_profile_report(char* buf, size_t bytes) {
 // ------------------------------------------------- double-float self-test
 // y[i] = f(x) of the double-float type that the FP32 path's FP64-class islands use,
 // from double inputs converted to double-float (hi = rounded x, lo = rounded rest):
-// op 0 exp, 1 log, 2 sqrt (x[i]); 3 quotient, 4 product, 5 sum (x[2i], x[2i+1]).
+// op 0 exp, 1 log, 2 sqrt (x[i]); 3 quotient, 4 product, 5 sum (x[2i], x[2i+1]);
+// the near-edge pass's cell decision helpers: 6 floor, 7 distance to the nearest
+// integer (x[i]); the cell gather's integer sums as float pairs: 8 the pair of the
+// integer x[2i] (|x| < 2^48) scaled by 2^-x[2i+1], as hi + lo.
 __global__ void __launch_bounds__(256) k_selftest_df(int op, const double* x, double* y, int n) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     DF r(0.0f, 0.0f);
+    if (op == 6 || op == 7) {
+        const DF a(x[i]);
+        y[i] = op == 6 ? (double)df_floor(a) : (double)df_edge_dist(a);
+        return;
+    }
+    if (op == 8) {
+        const float2 p = fix_to_pair((long long)x[2 * i], (int)x[2 * i + 1], 0.0f);
+        y[i] = (double)p.x + (double)p.y;
+        return;
+    }
     if (op <= 2) {
         const DF a(x[i]);
         r = op == 0 ? r_exp(a) : (op == 1 ? r_log(a) : r_sqrt(a));
@@ -1075,7 +1088,7 @@ __global__ void __launch_bounds__(256) k_selftest_df(int op, const double* x, do
 }
 
 extern "C" rtu_status rtu_selftest_df(int32_t op, const double* x, double* y, int32_t n, void* stream) {
-    if (op < 0 || op > 5) return fail(RTU_E_ARG, "rtu_selftest_df: op must be in [0, 5]");
+    if (op < 0 || op > 8) return fail(RTU_E_ARG, "rtu_selftest_df: op must be in [0, 8]");
     if (n < 0 || (n > 0 && (!x || !y))) return fail(RTU_E_ARG, "rtu_selftest_df: bad buffers");
     if (n == 0) return RTU_OK;
     k_selftest_df<<<(n + 255) / 256, 256, 0, static_cast<cudaStream_t>(stream)>>>(op, x, y, n);

@@ -496,16 +496,20 @@ def rtu_elbo_step(systems, n_samples: int, seed: int, lr: float, elbo_out=None, 
                               _stream_ptr(stream)), "rtu_elbo_step")
 
 
-DF_OPS = {"exp": 0, "log": 1, "sqrt": 2, "div": 3, "mul": 4, "add": 5}
+DF_OPS = {"exp": 0, "log": 1, "sqrt": 2, "div": 3, "mul": 4, "add": 5, "floor": 6, "edge_dist": 7, "fix_pair": 8}
+DF_BINARY = (3, 4, 5, 8)
 
 
 def rtu_selftest_df(op: str, x):
     """The double-float arithmetic of the FP32 path's islands on the device: x a float64
-    CUDA tensor ([n] for exp / log / sqrt, [n, 2] for div / mul / add); returns [n]."""
+    CUDA tensor ([n] for exp / log / sqrt / floor / edge_dist, [n, 2] for div / mul / add /
+    fix_pair); returns [n]."""
     code = DF_OPS[op]
     x = x.contiguous()
     n = x.shape[0]
-    if x.dtype != torch.float64 or not x.is_cuda or (code >= 3 and tuple(x.shape) != (n, 2)):
+    binary = code in DF_BINARY
+    if x.dtype != torch.float64 or not x.is_cuda or (binary and tuple(x.shape) != (n, 2)) or \
+            (not binary and x.dim() != 1):
         raise ValueError("x must be a float64 CUDA tensor of shape [n] or [n, 2]")
     y = torch.empty(n, dtype=torch.float64, device=x.device)
     _check(_lib.rtu_selftest_df(code, x.data_ptr(), y.data_ptr(), n, _stream_ptr(None)), "rtu_selftest_df")

@@ -75,3 +75,30 @@ def test_df_arithmetic(rtu, op):
         ref, scale = a + b, np.abs(a) + np.abs(b)
     err = np.abs(y - ref) / scale
     assert err.max() < BOUND, (err.max(), np.log2(err.max()))
+
+
+def test_df_floor_and_edge_distance(rtu):
+    """The near-edge pass decides a ray's cell from a double-float grid coordinate: its
+    floor must see the low float when the high one has rounded up onto an integer (a
+    value 7.6e-7 below 35 has hi = 35.0f), and its distance to the nearest integer
+    (a cell edge) must hold to float rounding of that distance."""
+    rng = np.random.default_rng(7)
+    ints = rng.integers(0, 256, 40000).astype(np.float64)
+    off = np.concatenate([-(10.0 ** rng.uniform(-12, -3, 20000)), 10.0 ** rng.uniform(-12, -3, 20000)])
+    x = df_exact(np.concatenate([ints + off, rng.uniform(0.0, 255.0, 40000), [35.0 - 7.6e-7, 63.0 - 1e-9, 1e-9]]))
+    fl = run(rtu, "floor", x)
+    assert np.array_equal(fl, np.floor(x)), x[fl != np.floor(x)][:5]
+    d = run(rtu, "edge_dist", x)
+    ref = np.abs(x - np.rint(x))
+    assert np.all(np.abs(d - ref) <= 2.0 ** -24 * ref + 1e-30), np.max(np.abs(d - ref) / np.maximum(ref, 1e-300))
+
+
+def test_fixed_point_pair_is_exact(rtu):
+    """The cell gather's exact integer corner sums become float pairs by an exact split
+    and two-sum: hi + lo equals the integer times 2^-S exactly for |k| < 2^48."""
+    rng = np.random.default_rng(8)
+    k = np.concatenate([rng.integers(-2 ** 47, 2 ** 47, 50000), rng.integers(-2 ** 24, 2 ** 24, 50000),
+                        [0, 1, -1, 2 ** 47 - 1, -(2 ** 47)]]).astype(np.float64)
+    S = rng.integers(0, 123, k.size).astype(np.float64)
+    y = run(rtu, "fix_pair", np.stack([k, S], axis=1))
+    assert np.array_equal(y, k * np.ldexp(1.0, -S.astype(np.int64))), (y[:3], k[:3])
