@@ -302,15 +302,17 @@ __global__ void __launch_bounds__(PSFT_NT) k_psf_adj_t(const __grid_constant__ B
 // output tile staged with its halo -- the taps v along x into a shared row buffer,
 // then the taps u along y -- K + K multiply-adds per output instead of K^2.  Each
 // thread computes 4 adjacent outputs of a pass from a sliding register window.
-// CONV: convolution (the forward model); else correlation (its adjoint).
+// CONV: convolution (the forward model); else correlation (its adjoint).  KT: the
+// tap count when known at compile time (21, 9: the loops unroll and the window's
+// shifts cost nothing), 0 for any other.
 constexpr int PSFS_NT = 256;
 constexpr int PSFS_W = PSF_T + PSF_MAXK - 1;
 
-template <typename T, bool CONV>
+template <typename T, bool CONV, int KT>
 __device__ __forceinline__ void psf_sep_passes(const EvalArgs& E, const T* src, int i0, int j0,
                                                T (*in)[PSFS_W + 1], T (*h)[PSF_T + 1], T* u, T* v, T* out4,
                                                int& ox, int& oy0) {
-    const int K = E.psf_k, c = (K - 1) / 2, n = E.n_img, W = PSF_T + 2 * c;
+    const int K = KT > 0 ? KT : E.psf_k, c = (K - 1) / 2, n = E.n_img, W = PSF_T + 2 * c;
     for (int i = threadIdx.x; i < 2 * K; i += PSFS_NT) {
         const T x = (T)E.psf_uv[i];
         if (i < K) u[i] = x; else v[i - K] = x;
@@ -346,6 +348,7 @@ __device__ __forceinline__ void psf_sep_passes(const EvalArgs& E, const T* src, 
         if (CONV) {
             const T* row = in[r] + x0 + 2 * c;          // row[u - a] for output x0 + u
             T w0 = row[0], w1 = row[1], w2 = row[2], w3 = row[3];
+#pragma unroll
             for (int a = 0; a < K; ++a) {
                 const T f = v[a];
                 a0 += f * w0; a1 += f * w1; a2 += f * w2; a3 += f * w3;
@@ -355,6 +358,7 @@ __device__ __forceinline__ void psf_sep_passes(const EvalArgs& E, const T* src, 
         } else {
             const T* row = in[r] + x0;                  // row[u + a]
             T w0 = row[0], w1 = row[1], w2 = row[2], w3 = row[3];
+#pragma unroll
             for (int a = 0; a < K; ++a) {
                 const T f = v[a];
                 a0 += f * w0; a1 += f * w1; a2 += f * w2; a3 += f * w3;
@@ -371,6 +375,7 @@ __device__ __forceinline__ void psf_sep_passes(const EvalArgs& E, const T* src, 
     if (CONV) {
         const int base = y0 + 2 * c;                    // h[y - b + 2c]
         T w0 = h[base][x], w1 = h[base + 1][x], w2 = h[base + 2][x], w3 = h[base + 3][x];
+#pragma unroll
         for (int b = 0; b < K; ++b) {
             const T f = u[b];
             a0 += f * w0; a1 += f * w1; a2 += f * w2; a3 += f * w3;
@@ -379,6 +384,7 @@ __device__ __forceinline__ void psf_sep_passes(const EvalArgs& E, const T* src, 
         }
     } else {
         T w0 = h[y0][x], w1 = h[y0 + 1][x], w2 = h[y0 + 2][x], w3 = h[y0 + 3][x];
+#pragma unroll
         for (int b = 0; b < K; ++b) {
             const T f = u[b];
             a0 += f * w0; a1 += f * w1; a2 += f * w2; a3 += f * w3;
@@ -391,7 +397,7 @@ __device__ __forceinline__ void psf_sep_passes(const EvalArgs& E, const T* src, 
     oy0 = y0;
 }
 
-template <typename T>
+template <typename T, int KT>
 __global__ void __launch_bounds__(PSFS_NT) k_psf_like_sep(const __grid_constant__ Batch B) {
     const int ev = find_eval(B, blockIdx.x);
     const EvalArgs& E = B.e[ev];
@@ -405,7 +411,7 @@ __global__ void __launch_bounds__(PSFS_NT) k_psf_like_sep(const __grid_constant_
     const int i0 = ti * PSF_T, j0 = tj * PSF_T;
     T m4[4];
     int x, y0;
-    psf_sep_passes<T, true>(E, reinterpret_cast<const T*>(E.img), i0, j0, in, h, u, v, m4, x, y0);
+    psf_sep_passes<T, true, KT>(E, reinterpret_cast<const T*>(E.img), i0, j0, in, h, u, v, m4, x, y0);
     const T isg = T(1) / T(E.sigma);
     T r2t = T(0), r2mt = T(0);
     const int i = i0 + x;
@@ -427,7 +433,7 @@ __global__ void __launch_bounds__(PSFS_NT) k_psf_like_sep(const __grid_constant_
     like_last_cta(E);
 }
 
-template <typename T>
+template <typename T, int KT>
 __global__ void __launch_bounds__(PSFS_NT) k_psf_adj_sep(const __grid_constant__ Batch B) {
     const int ev = find_eval(B, blockIdx.x);
     const EvalArgs& E = B.e[ev];
@@ -441,7 +447,7 @@ __global__ void __launch_bounds__(PSFS_NT) k_psf_adj_sep(const __grid_constant__
     const int i0 = ti * PSF_T, j0 = tj * PSF_T;
     T g4[4];
     int x, y0;
-    psf_sep_passes<T, false>(E, reinterpret_cast<const T*>(E.resid), i0, j0, in, h, u, v, g4, x, y0);
+    psf_sep_passes<T, false, KT>(E, reinterpret_cast<const T*>(E.resid), i0, j0, in, h, u, v, g4, x, y0);
     const T sc = E.dlogL ? (T)(*E.dlogL) : T(1);
     const int i = i0 + x;
     T gm = T(0);

@@ -648,7 +648,10 @@ int t_zero(const EvalArgs&) { return ZERO_TILES; }
 int t_centre(const EvalArgs& e) { return e.n_cta_c; }
 int t_adj(const EvalArgs& e) { return e.n_cta_adj; }
 int t_psf_gen(const EvalArgs& e) { return e.psf_uv ? 0 : e.n_cta_p; }
-int t_psf_sep(const EvalArgs& e) { return e.psf_uv ? e.n_cta_p : 0; }
+// rank-1 PSFs by tap count: 21 and 9 have compiled tap loops, others a runtime one
+int t_psf_sep21(const EvalArgs& e) { return e.psf_uv && e.psf_k == 21 ? e.n_cta_p : 0; }
+int t_psf_sep9(const EvalArgs& e) { return e.psf_uv && e.psf_k == 9 ? e.n_cta_p : 0; }
+int t_psf_sep_k(const EvalArgs& e) { return e.psf_uv && e.psf_k != 21 && e.psf_k != 9 ? e.n_cta_p : 0; }
 int t_edge(const EvalArgs& e) { return e.n_edge; }
 int t_cull_lin(const EvalArgs& e) { return is_lin(e) ? (e.n_cta_r + CULL_NT - 1) / CULL_NT : 0; }
 int t_units(const EvalArgs& e) { return std::min(CMP_CTAS, std::max(1, (e.n_cta_r * (CTA_R / 32) + 63) / 64)); }
@@ -751,7 +754,9 @@ rtu_status run_chunk(Batch& B, int phase, cudaStream_t st, const SideStream& ss)
         if ((r = stream_after(ss.s, st, ss.fork))) return r;
         if ((r = launch("k_compact_deferred", k_compact_deferred, B, t_defer, CMPD_NT, 0, ss.s))) return r;
         if (any_light && (r = launch("k_light_fwd", k_light_fwd<T>, B, t_light_fwd, LIGHT_FWD_NT, 0, st))) return r;
-        if ((r = launch("k_psf_like", k_psf_like_sep<T>, B, t_psf_sep, PSFS_NT, 0, st))) return r;
+        if ((r = launch("k_psf_like", k_psf_like_sep<T, 21>, B, t_psf_sep21, PSFS_NT, 0, st))) return r;
+        if ((r = launch("k_psf_like", k_psf_like_sep<T, 9>, B, t_psf_sep9, PSFS_NT, 0, st))) return r;
+        if ((r = launch("k_psf_like", k_psf_like_sep<T, 0>, B, t_psf_sep_k, PSFS_NT, 0, st))) return r;
         if (sizeof(T) == 4 && maxPsf <= 9) r = launch("k_psf_like", k_psf_like_t<9>, B, t_psf_gen, PSFT_NT, 0, st);
         else if (sizeof(T) == 4 && maxPsf <= 21) r = launch("k_psf_like", k_psf_like_t<21>, B, t_psf_gen, PSFT_NT, 0, st);
         else r = launch("k_psf_like", k_psf_like<T>, B, t_psf_gen, PSF_NT, 0, st);
@@ -761,7 +766,9 @@ rtu_status run_chunk(Batch& B, int phase, cudaStream_t st, const SideStream& ss)
     if (phase & PH_ADJOINT) {
         const size_t adj = grid_bytes + (size_t)(CTA_R / 32) * 4 * maxK * 2 * sizeof(T);
         if (adj > MAX_DYN) return fail(RTU_E_ARG, "adjoint shared memory exceeds the limit");
-        if ((r = launch("k_psf_adj", k_psf_adj_sep<T>, B, t_psf_sep, PSFS_NT, 0, st))) return r;
+        if ((r = launch("k_psf_adj", k_psf_adj_sep<T, 21>, B, t_psf_sep21, PSFS_NT, 0, st))) return r;
+        if ((r = launch("k_psf_adj", k_psf_adj_sep<T, 9>, B, t_psf_sep9, PSFS_NT, 0, st))) return r;
+        if ((r = launch("k_psf_adj", k_psf_adj_sep<T, 0>, B, t_psf_sep_k, PSFS_NT, 0, st))) return r;
         if (sizeof(T) == 4 && maxPsf <= 9) r = launch("k_psf_adj", k_psf_adj_t<9>, B, t_psf_gen, PSFT_NT, 0, st);
         else if (sizeof(T) == 4 && maxPsf <= 21) r = launch("k_psf_adj", k_psf_adj_t<21>, B, t_psf_gen, PSFT_NT, 0, st);
         else r = launch("k_psf_adj", k_psf_adj<T>, B, t_psf_gen, PSF_NT, 0, st);
