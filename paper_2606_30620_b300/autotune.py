@@ -53,12 +53,20 @@ def load(path: str = CACHE) -> dict:
     return _loaded[1]
 
 
+_memo: dict = {}
+
+
 def lookup(n_img: int, n_src: int, s: int, precision: int, path: str = CACHE):
-    """The cached launch shape of a bucket on this GPU, or None."""
+    """The cached launch shape of a bucket on this GPU, or None (memoised per bucket:
+    a serving loop looks it up for every admitted system)."""
+    key = (path, n_img, n_src, s, precision)
+    if key in _memo:
+        return _memo[key]
     if not torch.cuda.is_available():
         return None
     entry = load(path).get(gpu_name(), {}).get(bucket_key(n_img, n_src, s, precision))
-    return None if entry is None else entry["tuning"]
+    _memo[key] = None if entry is None else entry["tuning"]
+    return _memo[key]
 
 
 def _time(step, flush, steps: int) -> float:

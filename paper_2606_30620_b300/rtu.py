@@ -68,6 +68,11 @@ class Prior(ctypes.Structure):
                 ("b", ctypes.c_double), ("c", ctypes.c_double), ("d", ctypes.c_double)]
 
 
+_PRIOR_DT = np.dtype([("kind", "<i4"), ("space", "<i4"), ("a", "<f8"), ("b", "<f8"), ("c", "<f8"), ("d", "<f8")],
+                     align=True)
+assert _PRIOR_DT.itemsize == ctypes.sizeof(Prior)
+
+
 _lib.rtu_workspace_size.argtypes = [ctypes.POINTER(SystemDesc)]
 _lib.rtu_workspace_size.restype = ctypes.c_size_t
 _lib.rtu_system_create.argtypes = [ctypes.POINTER(SystemDesc), ctypes.c_void_p, ctypes.c_size_t,
@@ -181,7 +186,7 @@ class System:
     def __init__(self, data, mask, psf, sigma, pix, s_super, n_src, src_pitch, profile=RTU_SIE,
                  ps_family=RTU_PS_POWER_LAW, sub_kind=RTU_SUB_NONE, n_sub=0, precision=RTU_F32,
                  n_nodes=22, degree=21, n_slots=1, device="cuda", transform=RTU_TRANSFORM_RTU, n_light=0,
-                 weights=None, stream=None, host_staging=None, tune=True):
+                 weights=None, stream=None, host_staging=None, tune=True, alloc=None):
         """stream=None: synchronous creation (rtu_system_create).  With a torch stream
         and host (numpy) data, mask and psf: the observation travels in one pinned
         copy and the library builds the system from the host copies with uploads
@@ -189,9 +194,13 @@ class System:
         may use the system.  host_staging: a pinned uint8 tensor of at least
         staging_bytes(...) to stage that copy in (the caller keeps it untouched until
         the stream has passed the copy), else one is allocated.  tune: apply the
-        autotuner's cached launch shape for this GPU and problem bucket, if any."""
+        autotuner's cached launch shape for this GPU and problem bucket, if any.
+        alloc: a callable returning a uint8 CUDA tensor of at least the given number of
+        bytes (a caller's pool) for the workspace and, on a stream, the observation's
+        device copy, else torch allocates them; the blocks taken are in pool_blocks."""
         self.dtype = torch.float64 if precision == RTU_F64 else torch.float32
         self.device = torch.device(device)
+        self.pool_blocks = []
         on_stream = stream is not None
         if on_stream:
             if not (isinstance(data, np.ndarray) and isinstance(psf, np.ndarray) and isinstance(mask, np.ndarray)):
@@ -215,7 +224,12 @@ class System:
             if weights is not None:
                 hw = hb[(nd + nk) * tb + nm:(nd + nk) * tb + nm + 4 * nw].view(np.uint32)
                 hw[:] = np.asarray(weights).astype(np.uint32).ravel()
-            dev = torch.empty(total, dtype=torch.uint8, device=self.device)
+            if alloc is not None:
+                dev = alloc(total)
+                self.pool_blocks.append(dev)
+            else:
+                dev = torch.empty(total, dtype=torch.uint8, device=self.device)
+            dev = dev[:total]
             with torch.cuda.stream(stream):
                 dev.copy_(host, non_blocking=True)
             self._host = host          # kept until the system is closed (the copy reads it)
@@ -260,7 +274,15 @@ class System:
         nbytes = _lib.rtu_workspace_size(ctypes.byref(self.desc))
         if nbytes == 0:
             raise RTUError("invalid system description (rtu_workspace_size returned 0)")
-        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        if alloc is not None:
+            self.workspace = alloc(nbytes + 256)
+            self.pool_blocks.append(self.workspace)
+            wd = self.workspace.device
+            same_dev = wd.type == self.device.type and (self.device.index is None or wd.index == self.device.index)
+            if self.workspace.dtype != torch.uint8 or not same_dev or self.workspace.numel() < nbytes + 256:
+                raise ValueError("alloc must return a uint8 tensor on the system's device of the bytes asked for")
+        else:
+            self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
         base = self.workspace.data_ptr()
         off = (-base) % 256
         h = ctypes.c_void_p()
@@ -308,12 +330,13 @@ class System:
 
     @classmethod
     def from_mock(cls, m, precision=RTU_F32, n_slots=1, device="cuda", transform=RTU_TRANSFORM_RTU, stream=None,
-                  host_staging=None, tune=True):
+                  host_staging=None, tune=True, alloc=None):
         return cls(m.data, m.mask, m.psf, m.sigma, m.pix, m.s_super, m.n_src, m.src_pitch, m.profile,
                    m.ps_family, m.sub_kind, 0 if m.subs is None else m.subs.shape[0], precision,
                    n_slots=n_slots, device=device, transform=transform,
                    n_light=0 if getattr(m, "light", None) is None else m.light.shape[0],
-                   weights=getattr(m, "weights", None), stream=stream, host_staging=host_staging, tune=tune)
+                   weights=getattr(m, "weights", None), stream=stream, host_staging=host_staging, tune=tune,
+                   alloc=alloc)
 
     @property
     def n_sites(self) -> int:
@@ -327,10 +350,12 @@ class System:
         ns = self.n_sites
         if len(priors) != ns:
             raise ValueError(f"{ns} priors expected")
-        arr = (Prior * ns)()
-        for i, p in enumerate(priors):
-            arr[i].kind, arr[i].space = int(p[0]), int(p[1])
-            arr[i].a, arr[i].b, arr[i].c, arr[i].d = float(p[2]), float(p[3]), float(p[4]), float(p[5])
+        # the rtu_prior array from one packed record array (same layout as Prior)
+        pv = np.asarray(priors, dtype=np.float64).reshape(ns, 6)
+        rec = np.zeros(ns, dtype=_PRIOR_DT)
+        rec["kind"], rec["space"] = pv[:, 0].astype(np.int32), pv[:, 1].astype(np.int32)
+        rec["a"], rec["b"], rec["c"], rec["d"] = pv[:, 2], pv[:, 3], pv[:, 4], pv[:, 5]
+        arr = (Prior * ns).from_buffer_copy(rec.tobytes())
         fixed = np.ascontiguousarray(fixed, dtype=np.float64)
         loc = np.ascontiguousarray(loc, dtype=np.float64)
         rho = np.ascontiguousarray(rho, dtype=np.float64)

@@ -10,7 +10,9 @@ flight on separate CUDA streams, so requests that arrive while others run
 are admitted as memory and stream slots free up and their work overlaps on
 the device.  Admission uploads a system's observation, tables and guide with
 copies ordered on an admission stream that the batches' streams wait for, so
-the host never waits for the device to admit.  A request completes when the
+the host never waits for the device to admit; its workspace comes from a
+per-device pool of released workspaces (by size class), so a warm server makes
+no device allocation.  A request completes when the
 CUDA event recorded after its batch (and the copy of its ELBO into pinned host
 memory) has been reached; its latency is completion minus arrival time.
 """
@@ -86,6 +88,47 @@ def workspace_bytes(m: I.Mock, precision: int, n_samples: int) -> int:
     return int(ws) + m.n_img * m.n_img * (tb + 1) + m.psf.size * tb + 4096
 
 
+class WorkspacePool:
+    """Device workspaces of admitted systems, kept by size class (rounded up to a multiple
+    of an eighth of the power of two below the size: at most 12.5% more) and handed out again once their system is released: after a
+    warm-up, admission makes no device allocation (a stream of systems of many sizes
+    otherwise keeps fragmenting the caching allocator, and a fresh device allocation in
+    the serving loop delays every request behind it).  Blocks are never freed."""
+
+    def __init__(self, device):
+        self.device = torch.device(device)
+        self.free: dict[int, list] = {}
+        self.created = 0                  # blocks allocated so far
+
+    @staticmethod
+    def size_class(nbytes: int) -> int:
+        p = 1 << max(0, nbytes.bit_length() - 4)             # an eighth of the power of two below
+        return -(-nbytes // p) * p
+
+    def take(self, nbytes: int):
+        c = self.size_class(nbytes)
+        lst = self.free.get(c)
+        if lst:
+            return lst.pop()
+        self.created += 1
+        return torch.empty(c, dtype=torch.uint8, device=self.device)
+
+    def give(self, block):
+        self.free.setdefault(block.numel(), []).append(block)
+
+
+_POOLS: dict = {}
+
+
+def workspace_pool(device) -> WorkspacePool:
+    """The process's workspace pool of a device (shared by every server on it)."""
+    d = torch.device(device)
+    key = (d.type, d.index if d.index is not None else torch.cuda.current_device())
+    if key not in _POOLS:
+        _POOLS[key] = WorkspacePool(d)
+    return _POOLS[key]
+
+
 class PinnedRing:
     """Pinned host memory for the admission copies, handed out in FIFO order: a slice
     is reused once the event recorded after its copy has been reached (no pinned
@@ -145,6 +188,7 @@ class Server:
         self.out_dev = [torch.empty(max_batch, dtype=torch.float64, device=self.device) for _ in self.streams]
         self.out_host = [torch.empty(max_batch, dtype=torch.float64, pin_memory=True) for _ in self.streams]
         self.staging = PinnedRing(staging_bytes)
+        self.pool = workspace_pool(self.device)
 
     # ---------------------------------------------------------------- admission
     def _admit(self, req: Request, now: float) -> bool:
@@ -168,7 +212,7 @@ class Server:
         buf, span = got if isinstance(got, tuple) else (got, None)
         with torch.cuda.stream(self.admit_stream):
             s = rtu.System.from_mock(m, precision=self.precision, n_slots=self.n_samples, device=self.device,
-                                     stream=self.admit_stream, host_staging=buf)
+                                     stream=self.admit_stream, host_staging=buf, alloc=self.pool.take)
             pr, ph, loc, rho = guide_start(m)
             s.elbo_init(pr, ph, loc, rho, tag=req.system_id, stream=self.admit_stream)
         ev = torch.cuda.Event()
@@ -188,8 +232,12 @@ class Server:
             self._release(sid)
 
     def _release(self, sid: int):
+        # called once the system's last batch has completed (its event was reached),
+        # so its workspace can serve the next admission
         r = self.resident.pop(sid)
         r.system.close()
+        for block in r.system.pool_blocks:
+            self.pool.give(block)
         self.used -= r.nbytes
 
     # ----------------------------------------------------------------- batching

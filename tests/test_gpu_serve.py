@@ -65,3 +65,18 @@ def test_multi_step_requests_keep_state_on_device(serve):
     for r in reqs:
         loc, rho, t = srv.resident[r.system_id].system.elbo_state()
         assert t == 3
+
+
+def test_workspace_pool_serves_a_second_stream_without_allocating(serve):
+    """Released systems hand their workspaces back to the device's pool; the same stream
+    served again by a new server takes every workspace from it (no device allocation in
+    the serving loop), and the results stay the same bit for bit."""
+    pool = serve.workspace_pool("cuda")
+    first = small_stream(serve, 16)
+    serve.Server(budget_bytes=8 << 30, max_batch=8).run(first, realtime=False)
+    made = pool.created
+    again = small_stream(serve, 16)
+    serve.Server(budget_bytes=8 << 30, max_batch=8).run(again, realtime=False)
+    assert pool.created == made
+    for a, b in zip(first, again):
+        assert a.elbo == b.elbo, (a.rid, a.elbo, b.elbo)
