@@ -554,28 +554,34 @@ def run_autotune_report(systems, step, flush, stream, steps=50):
 def run_serving(args, dev):
     """The serving workload: a stream of lens systems (image 64-256^2, grid 32-128^2,
     2-4x rays, SIE or EPL + shear) arriving Poisson at 2000/s, one ELBO step each with
-    the state kept on the device, 120 GB admission budget.  Measured three ways on the
-    same systems: the continuous-batching server in real time (latency), the server with
-    every request queued at t = 0 (saturation throughput), and the plain per-system path.
+    the state kept on the device, 120 GB admission budget; each request carries its
+    observation and its starting guide.  Measured three ways on the same systems: the
+    continuous-batching server in real time (latency; three runs, the run with the
+    median p99 reported and every run's p50 / p99 beside it, since one host stall in a
+    2-second run moves the p99 of that run alone), the server with every request
+    queued at t = 0 (saturation throughput), and the plain per-system path.
     An untimed warm-up pass of the same stream (every request queued at t = 0) runs
     first, as the step timings run warm-up steps: it fills the device workspace pool
     that admission draws on (the serving loop then makes no device allocation); every
     system is built again from its observation when the timed runs admit it."""
     from paper_2606_30620_b300 import serve
-    import copy
     base = serve.make_stream(args.serve_n, 2000.0, seed=5000)
 
     def fresh():
-        return [serve.Request(rid=r.rid, system_id=r.system_id, mock=r.mock, arrival=r.arrival) for r in base]
+        return [serve.Request(rid=r.rid, system_id=r.system_id, mock=r.mock, arrival=r.arrival, guide=r.guide)
+                for r in base]
 
     serve.Server(budget_bytes=120 << 30, max_batch=32, n_samples=1, device=dev).run(fresh(), realtime=False)
     torch.cuda.synchronize()
-    live = serve.Server(budget_bytes=120 << 30, max_batch=32, n_samples=1, device=dev).run(fresh(), realtime=True)
+    runs = [serve.Server(budget_bytes=120 << 30, max_batch=32, n_samples=1, device=dev).run(fresh(), realtime=True)
+            for _ in range(3)]
+    live = sorted(runs, key=lambda r: r["p99_ms"])[1]
     sat = serve.Server(budget_bytes=120 << 30, max_batch=32, n_samples=1, device=dev).run(fresh(), realtime=False)
     plain = serve.serve_plain(fresh(), n_samples=1, device=dev)
     keep = ("systems", "wall_s", "systems_per_s", "p50_ms", "p99_ms", "mean_batch")
     return {"stream": f"{args.serve_n} systems, Poisson 2000/s, one ELBO step (S=1) each, 120 GB budget",
-            "open_loop": {k: live[k] for k in keep},
+            "open_loop": dict({k: live[k] for k in keep},
+                              runs_p50_p99_ms=[[round(r["p50_ms"], 2), round(r["p99_ms"], 2)] for r in runs]),
             "saturation": {k: sat[k] for k in keep},
             "plain_per_system": {k: plain[k] for k in ("systems", "wall_s", "systems_per_s")}}
 

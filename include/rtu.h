@@ -179,11 +179,19 @@ rtu_status rtu_system_create(const rtu_system_desc* desc, void* workspace, size_
                              rtu_system** out);
 /* Host copies of a system's observation inputs (each nullable): the arc mask
  * [n_img*n_img] u8, the PSF [psf_k*psf_k] real, the ray weights [n_img*n_img] u32 --
- * the same contents as the desc's device buffers. */
+ * the same contents as the desc's device buffers.  upload_bytes > 0: the library first
+ * copies upload_bytes from upload_src (host, pinned for an asynchronous copy) to
+ * upload_dst (device) on the creation stream -- one block holding the desc's device
+ * buffers, so that a caller need not order that copy itself; both pointers must then be
+ * non-null (RTU_E_ARG otherwise), and upload_src must stay unchanged until the stream
+ * has passed the copy. */
 typedef struct {
     const uint8_t* mask;
     const void* psf;
     const uint32_t* weights;
+    const void* upload_src;
+    void* upload_dst;
+    uint64_t upload_bytes;
 } rtu_host_inputs;
 
 /* rtu_system_create for a caller that holds the inputs on the host as well (e.g. a

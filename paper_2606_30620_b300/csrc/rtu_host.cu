@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -421,55 +422,84 @@ rtu_status rtu_system_create_on(const rtu_system_desc* d, const rtu_host_inputs*
     const size_t st = static_layout(*d, base, &s->cidx, &s->tw, &s->rev, &s->cheb, &cwt_buf, &uv_buf);
     // arc-mask pixel list (the CDF uses observed-pixel centres inside the mask)
     const size_t npx = (size_t)d->n_img * d->n_img;
+    const cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    cudaError_t ce = cudaSuccess;
+    // the caller's observation block first, so that the desc's buffers are filled in
+    // stream order before any kernel that reads them
+    if (hin && hin->upload_bytes) {
+        if (!hin->upload_src || !hin->upload_dst) { delete s; return fail(RTU_E_ARG, "upload block without its pointers"); }
+        if ((ce = cudaMemcpyAsync(hin->upload_dst, hin->upload_src, hin->upload_bytes, cudaMemcpyHostToDevice, cs)) !=
+            cudaSuccess) {
+            delete s;
+            return fail(RTU_E_CUDA, std::string("observation upload: ") + cudaGetErrorString(ce));
+        }
+    }
     // host copies of the mask, the PSF and the weights when the caller has them (no
     // device-to-host copy, which would wait for the device), else read back from the device
-    const cudaStream_t cs = static_cast<cudaStream_t>(stream);
-    std::vector<uint8_t> mask(npx);
-    cudaError_t ce = cudaSuccess;
-    if (hin && hin->mask) memcpy(mask.data(), hin->mask, npx);
-    else ce = cudaMemcpy(mask.data(), d->mask, npx, cudaMemcpyDeviceToHost);
-    if (ce != cudaSuccess) { delete s; return fail(RTU_E_CUDA, std::string("mask copy: ") + cudaGetErrorString(ce)); }
-    std::vector<int> idx;
-    for (size_t i = 0; i < npx; ++i) if (mask[i]) idx.push_back((int)i);
-    if (idx.size() < 2) { delete s; return fail(RTU_E_ARG, "the arc mask must hold at least 2 pixels"); }
-    s->n_mask = (int)idx.size();
+    std::vector<uint8_t> mask_copy;
+    const uint8_t* mask = hin ? hin->mask : nullptr;
+    if (!mask) {
+        mask_copy.resize(npx);
+        ce = cudaMemcpy(mask_copy.data(), d->mask, npx, cudaMemcpyDeviceToHost);
+        if (ce != cudaSuccess) { delete s; return fail(RTU_E_CUDA, std::string("mask copy: ") + cudaGetErrorString(ce)); }
+        mask = mask_copy.data();
+    }
+    // the static tables are assembled on the host with the device layout and go up in
+    // two copies; the pixel list is written straight into that image
+    std::unique_ptr<char[]> img(new char[st]);
+    int* hcidx;
+    double *htw, *hcheb;
+    int* hrev;
+    uint32_t* hcwt;
+    double* huv;
+    static_layout(*d, img.get(), &hcidx, &htw, &hrev, &hcheb, &hcwt, &huv);
+    const size_t tw_off = (size_t)(reinterpret_cast<char*>(htw) - img.get());
+    memset(img.get() + tw_off, 0, st - tw_off);        // alignment gaps of the small tables
+    size_t nm = 0;
+    for (size_t i = 0; i < npx; ++i) {                 // branch-free compaction, pixel order
+        hcidx[nm] = (int)i;
+        nm += mask[i] != 0;
+    }
+    if (nm < 2) { delete s; return fail(RTU_E_ARG, "the arc mask must hold at least 2 pixels"); }
+    s->n_mask = (int)nm;
     s->n_cta_c = (s->n_mask + CTA_C - 1) / CTA_C;
     // weighted grid: the centre rays' weights, checked, in arc-mask order
     s->cwt = nullptr;
     s->wtot = s->n_mask;
     if (d->weights) {
-        std::vector<uint32_t> w(npx), cw(idx.size());
-        if (hin && hin->weights) memcpy(w.data(), hin->weights, npx * 4);
-        else if ((ce = cudaMemcpy(w.data(), d->weights, npx * 4, cudaMemcpyDeviceToHost)) != cudaSuccess) {
-            delete s;
-            return fail(RTU_E_CUDA, std::string("weights copy: ") + cudaGetErrorString(ce));
+        std::vector<uint32_t> w_copy;
+        const uint32_t* w = hin ? hin->weights : nullptr;
+        if (!w) {
+            w_copy.resize(npx);
+            if ((ce = cudaMemcpy(w_copy.data(), d->weights, npx * 4, cudaMemcpyDeviceToHost)) != cudaSuccess) {
+                delete s;
+                return fail(RTU_E_CUDA, std::string("weights copy: ") + cudaGetErrorString(ce));
+            }
+            w = w_copy.data();
         }
         unsigned long long tot = 0;
-        for (size_t k = 0; k < idx.size(); ++k) {
-            cw[k] = w[idx[k]];
-            tot += cw[k];
-            if (cw[k] == 0) { delete s; return fail(RTU_E_ARG, "weights must be >= 1 on the arc mask"); }
+        for (size_t k = 0; k < nm; ++k) {
+            hcwt[k] = w[hcidx[k]];
+            tot += hcwt[k];
+            if (hcwt[k] == 0) { delete s; return fail(RTU_E_ARG, "weights must be >= 1 on the arc mask"); }
         }
         if (tot >= (1ull << 31)) { delete s; return fail(RTU_E_ARG, "the mask's total weight must be < 2^31"); }
-        if ((ce = cudaMemcpyAsync(cwt_buf, cw.data(), cw.size() * 4, cudaMemcpyHostToDevice, cs)) != cudaSuccess) {
-            delete s;
-            return fail(RTU_E_CUDA, std::string("weights upload: ") + cudaGetErrorString(ce));
-        }
         s->cwt = cwt_buf;
         s->wtot = (int)tot;
     }
-    std::vector<double> tw(2 * d->n_src);
     for (int m = 0; m < d->n_src; ++m) {
         const double ang = -2.0 * M_PI * m / d->n_src;
-        tw[2 * m] = std::cos(ang);
-        tw[2 * m + 1] = std::sin(ang);
+        htw[2 * m] = std::cos(ang);
+        htw[2 * m + 1] = std::sin(ang);
     }
-    std::vector<int> rev = digit_reversal(d->n_src, rad);
-    std::vector<double> cheb = chebyshev_tables(d->n_nodes, d->degree);
+    const std::vector<int> rev = digit_reversal(d->n_src, rad);
+    memcpy(hrev, rev.data(), rev.size() * 4);
+    const std::vector<double> cheb = chebyshev_tables(d->n_nodes, d->degree);
+    memcpy(hcheb, cheb.data(), cheb.size() * 8);
     // the PSF: rank 1 or not
     const int K = d->psf_k;
     const bool f64 = d->precision == RTU_F64;
-    std::vector<double> P(K * K), uv(2 * K);
+    std::vector<double> P(K * K);
     {
         std::vector<float> pf(f64 ? 0 : K * K);
         const void* hp = hin ? hin->psf : nullptr;
@@ -483,34 +513,20 @@ rtu_status rtu_system_create_on(const rtu_system_desc* d, const rtu_host_inputs*
         if (ce != cudaSuccess) { delete s; return fail(RTU_E_CUDA, std::string("psf copy: ") + cudaGetErrorString(ce)); }
         if (!f64) for (int i = 0; i < K * K; ++i) P[i] = pf[i];
     }
-    const bool sep = psf_rank1(P, K, f64, uv.data());
+    const bool sep = psf_rank1(P, K, f64, huv);
     s->psf_uv = sep ? uv_buf : nullptr;
-    {
-        // the static tables assembled on the host with the device layout, one copy
-        // (the centre weights, if any, were uploaded above)
-        std::vector<char> img(st, 0);
-        int* hcidx;
-        double *htw, *hcheb;
-        int* hrev;
-        uint32_t* hcwt;
-        double* huv;
-        static_layout(*d, img.data(), &hcidx, &htw, &hrev, &hcheb, &hcwt, &huv);
-        memcpy(hcidx, idx.data(), idx.size() * 4);
-        memcpy(htw, tw.data(), tw.size() * 8);
-        memcpy(hrev, rev.data(), rev.size() * 4);
-        memcpy(hcheb, cheb.data(), cheb.size() * 8);
-        memcpy(huv, uv.data(), uv.size() * 8);
-        const size_t tw_off = (size_t)(reinterpret_cast<char*>(htw) - img.data());
-        // the arc-mask pixel list (n_mask entries) and the FFT / Chebyshev / PSF tables; the
-        // weights region in between is written above (weighted grid) or unused
-        // stream-ordered copies from pageable memory: the driver stages the bytes before
-        // the call returns, so `img` may go out of scope; legacy stream when none is given
-        if ((ce = cudaMemcpyAsync(base, img.data(), idx.size() * 4, cudaMemcpyHostToDevice, cs)) != cudaSuccess ||
-            (ce = cudaMemcpyAsync(base + tw_off, img.data() + tw_off, st - tw_off, cudaMemcpyHostToDevice, cs)) !=
-                cudaSuccess) {
-            delete s;
-            return fail(RTU_E_CUDA, std::string("table upload: ") + cudaGetErrorString(ce));
-        }
+    // the arc-mask pixel list with, on a weighted grid, the centre weights behind it
+    // (their region starts one table further on), then the FFT / Chebyshev / PSF tables:
+    // stream-ordered copies from pageable memory, staged by the driver before the call
+    // returns, so `img` may go out of scope; legacy stream when none is given
+    const size_t cwt_off = (size_t)(reinterpret_cast<char*>(hcwt) - img.get());
+    if ((ce = cudaMemcpyAsync(base, img.get(), nm * 4, cudaMemcpyHostToDevice, cs)) != cudaSuccess ||
+        (d->weights &&
+         (ce = cudaMemcpyAsync(base + cwt_off, img.get() + cwt_off, nm * 4, cudaMemcpyHostToDevice, cs)) != cudaSuccess) ||
+        (ce = cudaMemcpyAsync(base + tw_off, img.get() + tw_off, st - tw_off, cudaMemcpyHostToDevice, cs)) !=
+            cudaSuccess) {
+        delete s;
+        return fail(RTU_E_CUDA, std::string("table upload: ") + cudaGetErrorString(ce));
     }
     const size_t per = slot_layout(*d, nullptr, nullptr);
     const size_t sper = sample_layout(*d, nullptr, nullptr);
@@ -1153,21 +1169,24 @@ rtu_status rtu_elbo_init_on(rtu_system* s, const rtu_prior* priors, const double
             return fail(RTU_E_ARG, "bounded prior needs d > c");
         if (p.kind == RTU_PRIOR_LINEAR && !(p.a >= -1.0)) return fail(RTU_E_ARG, "linear prior needs a >= -1");
     }
-    // the state region (loc, rho, Adam m and v, priors, fixed values, step, and the
-    // zeroed partials and last gradient) assembled on the host with the device layout,
-    // then one copy
-    const size_t span = (size_t)(reinterpret_cast<char*>(s->st.grad) + (size_t)2 * z.n_state * 8 -
-                                 reinterpret_cast<char*>(s->st.loc));
-    std::vector<char> img(span, 0);
-    ElboState hs;
-    state_layout(s->d, img.data(), &hs);
-    memcpy(hs.loc, loc, (size_t)z.n_state * 8);
-    memcpy(hs.rho, rho, (size_t)z.n_state * 8);
-    memcpy(hs.prior, priors, (size_t)z.n_sites * sizeof(rtu_prior));
-    memcpy(hs.fixed, fixed, (size_t)z.n_fixed * 8);
-    cudaError_t ce = cudaMemcpyAsync(s->st.loc, img.data(), span, cudaMemcpyHostToDevice,
-                                     static_cast<cudaStream_t>(stream));
-    if (ce != cudaSuccess) return fail(RTU_E_CUDA, std::string("rtu_elbo_init: ") + cudaGetErrorString(ce));
+    // the state region: loc and rho from the caller's arrays, Adam's m and v zeroed, the
+    // priors, fixed values and step from one small host image, the partials and the last
+    // gradient zeroed (two copies of the guide, one of the small image, two fills)
+    const cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    char* const sp = reinterpret_cast<char*>(s->st.prior);
+    char* const send = reinterpret_cast<char*>(s->st.part);
+    std::vector<char> img((size_t)(send - sp), 0);
+    memcpy(img.data(), priors, (size_t)z.n_sites * sizeof(rtu_prior));
+    memcpy(img.data() + (reinterpret_cast<char*>(s->st.fixed) - sp), fixed, (size_t)z.n_fixed * 8);
+    const size_t nb = (size_t)z.n_state * 8;
+    cudaError_t ce;
+    if ((ce = cudaMemcpyAsync(s->st.loc, loc, nb, cudaMemcpyHostToDevice, cs)) != cudaSuccess ||
+        (ce = cudaMemcpyAsync(s->st.rho, rho, nb, cudaMemcpyHostToDevice, cs)) != cudaSuccess ||
+        (ce = cudaMemsetAsync(s->st.m, 0, (size_t)(sp - reinterpret_cast<char*>(s->st.m)), cs)) != cudaSuccess ||
+        (ce = cudaMemcpyAsync(sp, img.data(), img.size(), cudaMemcpyHostToDevice, cs)) != cudaSuccess ||
+        (ce = cudaMemsetAsync(send, 0, (size_t)(reinterpret_cast<char*>(s->st.grad) + 2 * nb - send), cs)) !=
+            cudaSuccess)
+        return fail(RTU_E_CUDA, std::string("rtu_elbo_init: ") + cudaGetErrorString(ce));
     s->st.tag = tag;
     s->elbo_ready = true;
     return RTU_OK;

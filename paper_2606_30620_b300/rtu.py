@@ -56,7 +56,18 @@ class Eval(ctypes.Structure):
 
 
 class HostInputs(ctypes.Structure):
-    _fields_ = [("mask", ctypes.c_void_p), ("psf", ctypes.c_void_p), ("weights", ctypes.c_void_p)]
+    _fields_ = [("mask", ctypes.c_void_p), ("psf", ctypes.c_void_p), ("weights", ctypes.c_void_p),
+                ("upload_src", ctypes.c_void_p), ("upload_dst", ctypes.c_void_p), ("upload_bytes", ctypes.c_uint64)]
+
+
+def pack_priors(priors):
+    """The rtu_prior array of a sequence of (kind, space, a, b, c, d) rows, built from one
+    packed record array of the same layout."""
+    pv = np.asarray(priors, dtype=np.float64).reshape(-1, 6)
+    rec = np.zeros(pv.shape[0], dtype=_PRIOR_DT)
+    rec["kind"], rec["space"] = pv[:, 0].astype(np.int32), pv[:, 1].astype(np.int32)
+    rec["a"], rec["b"], rec["c"], rec["d"] = pv[:, 2], pv[:, 3], pv[:, 4], pv[:, 5]
+    return (Prior * pv.shape[0]).from_buffer_copy(rec.tobytes())
 
 
 class Tuning(ctypes.Structure):
@@ -230,15 +241,15 @@ class System:
             else:
                 dev = torch.empty(total, dtype=torch.uint8, device=self.device)
             dev = dev[:total]
-            with torch.cuda.stream(stream):
-                dev.copy_(host, non_blocking=True)
             self._host = host          # kept until the system is closed (the copy reads it)
             self.data = dev[:nd * tb].view(self.dtype).view(data.shape)
             self.psf = dev[nd * tb:(nd + nk) * tb].view(self.dtype).view(psf.shape)
             self.mask = dev[(nd + nk) * tb:(nd + nk) * tb + nm].view(mask.shape)
             self.weights = None if hw is None else dev[(nd + nk) * tb + nm:(nd + nk) * tb + nm + 4 * nw].view(
                 torch.int32)
-            self._host_in = HostInputs(hmask.ctypes.data, hpsf.ctypes.data, None if hw is None else hw.ctypes.data)
+            # the library copies the whole block up on the stream, before its own uploads
+            self._host_in = HostInputs(hmask.ctypes.data, hpsf.ctypes.data, None if hw is None else hw.ctypes.data,
+                                       host.data_ptr(), dev.data_ptr(), total)
         elif isinstance(data, np.ndarray) and isinstance(psf, np.ndarray):
             # host arrays: the image and the PSF travel in one copy
             npdt = np.float64 if precision == RTU_F64 else np.float32
@@ -350,12 +361,7 @@ class System:
         ns = self.n_sites
         if len(priors) != ns:
             raise ValueError(f"{ns} priors expected")
-        # the rtu_prior array from one packed record array (same layout as Prior)
-        pv = np.asarray(priors, dtype=np.float64).reshape(ns, 6)
-        rec = np.zeros(ns, dtype=_PRIOR_DT)
-        rec["kind"], rec["space"] = pv[:, 0].astype(np.int32), pv[:, 1].astype(np.int32)
-        rec["a"], rec["b"], rec["c"], rec["d"] = pv[:, 2], pv[:, 3], pv[:, 4], pv[:, 5]
-        arr = (Prior * ns).from_buffer_copy(rec.tobytes())
+        arr = priors if isinstance(priors, ctypes.Array) and priors._type_ is Prior else pack_priors(priors)
         fixed = np.ascontiguousarray(fixed, dtype=np.float64)
         loc = np.ascontiguousarray(loc, dtype=np.float64)
         rho = np.ascontiguousarray(rho, dtype=np.float64)

@@ -37,6 +37,9 @@ class Request:
     mock: I.Mock
     arrival: float                  # seconds after the stream starts
     n_steps: int = 1
+    # the starting guide the client sends, as start_guide returns it (packed priors, fixed
+    # values, loc, rho); None: built from the mock at admission (guide_start)
+    guide: tuple | None = None
     done_steps: int = 0
     finish: float | None = None
     elbo: float | None = None
@@ -63,6 +66,14 @@ def guide_start(m: I.Mock, rho0: float = -3.0):
     loc = np.concatenate([np.asarray(loc, dtype=np.float64), m.latents.ravel()])
     rho = np.full(loc.size, rho0)
     return priors, np.array(phys + light), loc, rho
+
+
+def start_guide(m: I.Mock, rho0: float = -3.0):
+    """guide_start with the priors packed for the ABI (rtu.pack_priors) and the arrays in
+    the types the library reads: what a client sends with its request."""
+    pr, ph, loc, rho = guide_start(m, rho0)
+    return (rtu.pack_priors(pr), np.ascontiguousarray(ph, dtype=np.float64),
+            np.ascontiguousarray(loc, dtype=np.float64), np.ascontiguousarray(rho, dtype=np.float64))
 
 
 def _targets(profile, sub_kind, n_sub, nps):
@@ -210,11 +221,10 @@ class Server:
         got = self.staging.take(rtu.System.staging_bytes(m.data.size, m.psf.size, self.precision,
                                                           getattr(m, "weights", None) is not None))
         buf, span = got if isinstance(got, tuple) else (got, None)
-        with torch.cuda.stream(self.admit_stream):
-            s = rtu.System.from_mock(m, precision=self.precision, n_slots=self.n_samples, device=self.device,
-                                     stream=self.admit_stream, host_staging=buf, alloc=self.pool.take)
-            pr, ph, loc, rho = guide_start(m)
-            s.elbo_init(pr, ph, loc, rho, tag=req.system_id, stream=self.admit_stream)
+        s = rtu.System.from_mock(m, precision=self.precision, n_slots=self.n_samples, device=self.device,
+                                 stream=self.admit_stream, host_staging=buf, alloc=self.pool.take)
+        pr, ph, loc, rho = req.guide if req.guide is not None else guide_start(m)
+        s.elbo_init(pr, ph, loc, rho, tag=req.system_id, stream=self.admit_stream)
         ev = torch.cuda.Event()
         ev.record(self.admit_stream)
         self.staging.commit(span, ev)
@@ -353,7 +363,11 @@ def serve_plain(requests, n_samples=1, lr=1e-3, seed=0, precision=rtu.RTU_F32, d
 
 
 def make_stream(n: int, rate_hz: float, seed: int = 5000):
-    """The serving workload: n systems, Poisson arrivals, mixed sizes and profiles."""
+    """The serving workload: n systems, Poisson arrivals, mixed sizes and profiles; each
+    request carries its observation and its starting guide."""
     times = I.poisson_arrivals(n, rate_hz, seed)
-    return [Request(rid=k, system_id=k, mock=I.config_serving_system(seed + 1 + k), arrival=float(times[k]))
-            for k in range(n)]
+    out = []
+    for k in range(n):
+        m = I.config_serving_system(seed + 1 + k)
+        out.append(Request(rid=k, system_id=k, mock=m, arrival=float(times[k]), guide=start_guide(m)))
+    return out

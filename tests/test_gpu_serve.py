@@ -80,3 +80,17 @@ def test_workspace_pool_serves_a_second_stream_without_allocating(serve):
     assert pool.created == made
     for a, b in zip(first, again):
         assert a.elbo == b.elbo, (a.rid, a.elbo, b.elbo)
+
+
+def test_requests_carrying_their_guide_match_guides_built_at_admission(serve):
+    """A request may carry its starting guide already packed (start_guide, what a client
+    sends); the server then uploads it as given: the same ELBO bit for bit as a guide
+    built from the mock at admission, and the plain path agrees."""
+    plain = small_stream(serve, 10)
+    serve.Server(budget_bytes=8 << 30, max_batch=8).run(plain, realtime=False)
+    carried = small_stream(serve, 10)
+    for r in carried:
+        r.guide = serve.start_guide(r.mock)
+    serve.Server(budget_bytes=8 << 30, max_batch=8).run(carried, realtime=True)
+    for a, b in zip(plain, carried):
+        assert a.elbo == b.elbo, (a.rid, a.elbo, b.elbo)
