@@ -59,11 +59,11 @@ FLOPS_ADJ_RAY = 516.0
 # TRAFFIC_SRC_DIGEST.
 ROOF = {
     "k_render": {"flops_per_unit": FLOPS_FWD_RAY, "units": "in-grid rays",
-                 "traffic_per_unit": (0.330240e6 + 4352) / 743894},
+                 "traffic_per_unit": (0.344576e6 + 20736) / 743894},
     "k_render_adj": {"flops_per_unit": FLOPS_ADJ_RAY, "units": "in-grid rays",
-                     "traffic_per_unit": (9.706240e6 + 156928) / 743894},
+                     "traffic_per_unit": (9.692160e6 + 144128) / 743894},
 }
-TRAFFIC_SRC_DIGEST = "31ec847b647560c9"
+TRAFFIC_SRC_DIGEST = "e7810f2f2837302b"
 KERNEL_SOURCES = ("k_render.cuh", "rtu_internal.cuh", "rtu_math.cuh", "rtu_df.cuh")
 
 
