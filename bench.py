@@ -559,7 +559,9 @@ def run_serving(args, dev):
     continuous-batching server in real time (latency; three runs, the run with the
     median p99 reported and every run's p50 / p99 beside it, since one host stall in a
     2-second run moves the p99 of that run alone), the server with every request
-    queued at t = 0 (saturation throughput), and the plain per-system path.
+    queued at t = 0 (saturation throughput), the same under a 64 MB admission budget
+    (the budget binds: admission waits for completions to free workspace), and the
+    plain per-system path.
     An untimed warm-up pass of the same stream (every request queued at t = 0) runs
     first, as the step timings run warm-up steps: it fills the device workspace pool
     that admission draws on (the serving loop then makes no device allocation); every
@@ -577,12 +579,16 @@ def run_serving(args, dev):
             for _ in range(3)]
     live = sorted(runs, key=lambda r: r["p99_ms"])[1]
     sat = serve.Server(budget_bytes=120 << 30, max_batch=32, n_samples=1, device=dev).run(fresh(), realtime=False)
+    tight = serve.Server(budget_bytes=64 << 20, max_batch=32, n_samples=1, device=dev)
+    small = tight.run(fresh(), realtime=False)
     plain = serve.serve_plain(fresh(), n_samples=1, device=dev)
     keep = ("systems", "wall_s", "systems_per_s", "p50_ms", "p99_ms", "mean_batch")
     return {"stream": f"{args.serve_n} systems, Poisson 2000/s, one ELBO step (S=1) each, 120 GB budget",
             "open_loop": dict({k: live[k] for k in keep},
                               runs_p50_p99_ms=[[round(r["p50_ms"], 2), round(r["p99_ms"], 2)] for r in runs]),
             "saturation": {k: sat[k] for k in keep},
+            "budget_64mb": dict({k: small[k] for k in keep}, peak_bytes=small["peak_bytes"],
+                                budget_bytes=64 << 20, batches=small["batches"]),
             "plain_per_system": {k: plain[k] for k in ("systems", "wall_s", "systems_per_s")}}
 
 
