@@ -473,7 +473,8 @@ def run_ours(args):
 # the NEXT variants of the hot path on the same mocks: the kernels each one adds or
 # swaps, and its whole-step throughput
 VARIANT_KERNELS = ("k_select_fit", "k_lin_sort", "k_render", "k_render_edge", "k_render_adj", "k_cdf_adj",
-                   "k_centre_adj", "k_sel_jac", "k_lin_centre_adj", "k_light_fwd", "k_light_adj")
+                   "k_centre_adj", "k_sel_jac", "k_lin_centre_adj", "k_light_fwd", "k_light_adj", "k_sub_adj",
+                   "k_render_adj_near")
 
 
 def run_variants(args, dev, mocks, flush, stream):
@@ -487,12 +488,20 @@ def run_variants(args, dev, mocks, flush, stream):
               lambda m: I.with_light(copy.copy(m), n=5, seed=3, amp=0.3), rtu.RTU_TRANSFORM_RTU),
              ("linear_ecdf", "unsmoothed linear-interpolated eCDF (App. C)",
               lambda m: m, rtu.RTU_TRANSFORM_LINEAR)]
+    # config c4 on its own mocks (8 seeds): 400^2 at 0.03"/pix, 3x3 rays, 128^2 grid,
+    # EPL + shear with 1-10 truncated NFW subhaloes, and the same systems without them
+    c4 = {sub: [I.config_c4(3000 + k, with_subs=sub) for k in range(8)] for sub in (True, False)}
+    specs += [("c4_subhaloes", "c4: 400^2, 3x3 rays, 128^2 grid, EPL + shear + 1-10 tNFW subhaloes, 8 mocks",
+               c4[True], rtu.RTU_TRANSFORM_RTU),
+              ("c4_no_subhaloes", "c4: the same 8 systems without subhaloes",
+               c4[False], rtu.RTU_TRANSFORM_RTU)]
     out = {}
     k_steps = max(1, min(args.steps, 100))
     for name, what, make, transform in specs:
-        ms_ = [make(m) for m in mocks]
+        ms_ = make if isinstance(make, list) else [make(m) for m in mocks]
         systems = [rtu.System.from_mock(m, precision=rtu.RTU_F32, device=dev, transform=transform) for m in ms_]
-        batch = rtu.Batch([rtu.Binding(s, m.lens, m.latents, m.ps, light=getattr(m, "light", None))
+        batch = rtu.Batch([rtu.Binding(s, m.lens if m.subs is None else np.concatenate([m.lens, m.subs.ravel()]),
+                                       m.latents, m.ps, light=getattr(m, "light", None))
                            for s, m in zip(systems, ms_)])
 
         def step():
@@ -520,7 +529,7 @@ def run_variants(args, dev, mocks, flush, stream):
         torch.cuda.synchronize()
         rtu.profile_enable(False)
         kern = rtu.profile_report()
-        out[name] = {"what": what, "value": len(mocks) / (ms / 1e3), "unit": "evals/s", "ms_per_step": ms,
+        out[name] = {"what": what, "value": len(ms_) / (ms / 1e3), "unit": "evals/s", "ms_per_step": ms,
                      "steps": k_steps,
                      "kernels_ms": {k: kern[k][1] / n_prof for k in VARIANT_KERNELS if k in kern}}
         del batch, systems
