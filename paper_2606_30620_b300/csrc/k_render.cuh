@@ -524,6 +524,19 @@ __global__ void __launch_bounds__(CTA_R, sizeof(T) == 4 && !LIN ? 8 : 6) k_rende
                 bx = x - (ax + shx);
                 by = y - (ay + shy);
             } else {
+                // with subhaloes: the same two-term test, the tail widened by the bound on
+                // the subhaloes' deflection; a ray that may reach the grid takes the full
+                // lens equation (the same bits as without the test)
+                EplPart<T> ps;
+                epl_alpha_begin(sh.K.C, x, y, 2, ps);
+                T ax, ay;
+                epl_alpha_of(sh.K.C, ps, ax, ay);
+                const T shx = sh.K.g1 * x + sh.K.g2 * y, shy = sh.K.g2 * x - sh.K.g1 * y;
+                const T px = (x - (ax + shx) - mux) * isg, py = (y - (ay + shy) - muy) * isg;
+                const T tail = (T(1.25) * epl_tail_bound(sh.K.C, ps) + sub_alpha_bound(sh.K) +
+                                T(1e-6) * (T(1) + r_abs(ax) + r_abs(ay) + r_abs(x) + r_abs(y))) * isg;
+                if (px < zlo[0] - tail || px > zhi[0] + tail || py < zlo[1] - tail || py > zhi[1] + tail)
+                    return -1;
                 lens_beta(sh.K, x, y, bx, by);
             }
             const T zx = (bx - mux) * isg, zy = (by - muy) * isg;

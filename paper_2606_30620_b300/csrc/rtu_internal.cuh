@@ -465,6 +465,20 @@ __device__ inline void lens_setup_par(LensK<double>* Kd, LensK<float>* Kf, LensK
     }
 }
 
+// A bound on the subhaloes' total deflection, for every ray position: a subhalo deflects
+// by 4 kappa_s r_s g(x)/x, x = r/r_s (App. A), with g the NFW projected-mass function
+// h(x) = ln(x/2) + F(x), or the truncated one, which lies below h for every tau (the
+// truncated density is the NFW one times tau^2/(tau^2 + x^2) <= 1, so it encloses less
+// projected mass).  h is increasing and sup h(x)/x = 0.3105 (at x = 1.32; h(x)/x -> 0
+// at both ends); with 0.32 taken, |alpha_h| <= 1.28 kappa_s r_s.
+constexpr double SUB_ALPHA_PER_KR = 1.28;
+template <typename T>
+__device__ __forceinline__ T sub_alpha_bound(const LensK<T>& K) {
+    T b = T(0);
+    for (int h = 0; h < K.nsub; ++h) b += r_abs(K.sub[h][0]) * r_abs(K.sub[h][1]);
+    return b * T(SUB_ALPHA_PER_KR) * T(1.001);
+}
+
 // rays near the EPL centre or a subhalo's centre / scale radius take the FP64 island
 template <typename T>
 __device__ __forceinline__ bool lens_near_core(const LensK<T>& K, T x, T y) {
@@ -683,10 +697,10 @@ __device__ inline void grid_reach(const EvalArgs& E, bool cg, float* reach) {
 // box's smallest (t > 1) or largest (t < 1) elliptical radius R -- R >= q |theta - c|,
 // and R is convex so its maximum sits at a corner -- and the shear deflection is
 // linear (extremes at the corners).  Evaluated in float from the float lens block, with
-// slack far above float rounding.  Tiles with subhaloes are never culled.
+// slack far above float rounding.  Subhaloes widen the deflection bound by
+// sub_alpha_bound, whatever their positions.
 __device__ inline bool tile_out_of_reach(const EvalArgs& E, int tile, const float* reach) {
     const LensK<float>& Kf = *reinterpret_cast<const LensK<float>*>(lensk_src<float>(E.lensk));
-    if (Kf.nsub > 0) return false;
     const int n = E.n_img, tx_n = render_tiles_x(n);
     const int ty = tile / tx_n, tx = tile - ty * tx_n;
     const int i0 = tx * RT_X, i1 = min(i0 + RT_X - 1, n - 1);
@@ -720,7 +734,7 @@ __device__ inline bool tile_out_of_reach(const EvalArgs& E, int tile, const floa
     } else {
         pmax = C.pref0 * powf(fmaxf(C.b / fmaxf(rmin, 1e-4f), fmaxf(rmax, 1e-4f) / C.b), fabsf(e));
     }
-    const float amax = pmax * (1.0f + C.ftail) * 1.001f + 1e-4f;
+    const float amax = pmax * (1.0f + C.ftail) * 1.001f + 1e-4f + sub_alpha_bound(Kf);
     const float sh_slack = 1e-5f * (fabsf(xl) + fabsf(xh) + fabsf(yl) + fabsf(yh) + 1.0f);
     // beta = theta - alpha_EPL - alpha_shear ranges per axis
     const float bxl = xl - shx_hi - amax - sh_slack, bxh = xh - shx_lo + amax + sh_slack;
