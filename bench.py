@@ -54,16 +54,16 @@ FALLBACK_HBM_GBS = 6400.0
 # counted: the units are the in-grid rays (the N_IN_GRID statistic), for both kernels.
 FLOPS_FWD_RAY = 228.0
 FLOPS_ADJ_RAY = 516.0
-# DRAM read + write per unit from one ncu capture (--set full, c2 shape, 8 mocks:
-# 5,120,000 rays, 743,894 of them in the grid), valid for the kernel sources with digest
-# TRAFFIC_SRC_DIGEST.
+# DRAM read + write per unit from one ncu capture (dram__bytes_read.sum and
+# dram__bytes_write.sum, c2 shape, 8 mocks: 5,120,000 rays, 743,894 of them in the grid),
+# valid for the kernel sources with digest TRAFFIC_SRC_DIGEST.
 ROOF = {
     "k_render": {"flops_per_unit": FLOPS_FWD_RAY, "units": "in-grid rays",
-                 "traffic_per_unit": (0.344576e6 + 20736) / 743894},
+                 "traffic_per_unit": (340992 + 9472) / 743894},
     "k_render_adj": {"flops_per_unit": FLOPS_ADJ_RAY, "units": "in-grid rays",
-                     "traffic_per_unit": (9.692160e6 + 144128) / 743894},
+                     "traffic_per_unit": (9693696 + 146176) / 743894},
 }
-TRAFFIC_SRC_DIGEST = "e7810f2f2837302b"
+TRAFFIC_SRC_DIGEST = "f312b1f1ed09a544"
 KERNEL_SOURCES = ("k_render.cuh", "rtu_internal.cuh", "rtu_math.cuh", "rtu_df.cuh")
 
 
