@@ -1417,6 +1417,7 @@ __global__ void __launch_bounds__(CTA_R, NEAR ? 1 : (sizeof(T) == 4 && !LIN ? 6 
     }
 }
 
+constexpr int SUB_GROUP = 2;
 // subhalo parameters: d logL / d(kappa_s, r_s, tau, x_s, y_s) over the compacted rays
 // with the stored d logL / d beta, same CTA tiling (and partial rows) as k_render_adj
 template <typename T>
@@ -1441,8 +1442,16 @@ __global__ void __launch_bounds__(CTA_R) k_sub_adj(const __grid_constant__ Batch
     const R2* gbuf = reinterpret_cast<const R2*>(E.gbuf);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int chunk = CTA_R * ADJ_RPT;
-    for (int h = 0; h < K.nsub; ++h) {
-        T a5[5] = {T(0), T(0), T(0), T(0), T(0)};
+    // SUB_GROUP subhaloes per pass over the ray list: each ray is read and placed once per
+    // group; every subhalo's sums still take the thread's rays in list order (the same
+    // bits as one pass per subhalo)
+    for (int h0 = 0; h0 < K.nsub; h0 += SUB_GROUP) {
+        const int hn = min(SUB_GROUP, K.nsub - h0);
+        T a5[SUB_GROUP][5];
+#pragma unroll
+        for (int j = 0; j < SUB_GROUP; ++j)
+#pragma unroll
+            for (int c = 0; c < 5; ++c) a5[j][c] = T(0);
         for (int base = tile * chunk; base < total; base += E.n_cta_adj * chunk) {
             for (int r = 0; r < ADJ_RPT; ++r) {
                 const int k = base + r * CTA_R + threadIdx.x;
@@ -1455,21 +1464,25 @@ __global__ void __launch_bounds__(CTA_R) k_sub_adj(const __grid_constant__ Batch
                 const int pj = pixel / E.n_img, pi = pixel - pj * E.n_img;
                 const T x = ray_coord(G, pi, q % s);
                 const T y = ray_coord(G, pj, q / s);
-                sub_vjp<T>(K, h, x, y, g.x, g.y, a5);
+#pragma unroll
+                for (int j = 0; j < SUB_GROUP; ++j)
+                    if (j < hn) sub_vjp<T>(K, h0 + j, x, y, g.x, g.y, a5[j]);
             }
         }
+        for (int j = 0; j < hn; ++j) {
 #pragma unroll
-        for (int c = 0; c < 5; ++c) {
-            const double v = warp_sum_lane0(a5[c]);
-            if (lane == 0) wsub[wid][c] = v;
+            for (int c = 0; c < 5; ++c) {
+                const double v = warp_sum_lane0(a5[j][c]);
+                if (lane == 0) wsub[wid][c] = v;
+            }
+            __syncthreads();
+            if (threadIdx.x < 5) {
+                double r = 0.0;
+                for (int w = 0; w < CTA_R / 32; ++w) r += wsub[w][threadIdx.x];
+                out[(NACC_FIX + 4 * Kn + 5 * (h0 + j) + threadIdx.x) * ostr] = r;
+            }
+            __syncthreads();
         }
-        __syncthreads();
-        if (threadIdx.x < 5) {
-            double r = 0.0;
-            for (int w = 0; w < CTA_R / 32; ++w) r += wsub[w][threadIdx.x];
-            out[(NACC_FIX + 4 * Kn + 5 * h + threadIdx.x) * ostr] = r;
-        }
-        __syncthreads();
     }
 }
 
