@@ -555,17 +555,32 @@ __device__ __forceinline__ void lens_beta_vjp(const LensK<T>& K, const EplJ<T>& 
     out[7] += -gbx * y - gby * x;      // d beta / d Gamma2 = (-y, -x)
 }
 
-// subhalo h: out[0..4] += dL/d(kappa_s, r_s, tau, x_s, y_s) given dL/dbeta (forward-mode duals)
+// subhalo h: out[0..4] += dL/d(kappa_s, r_s, tau, x_s, y_s) given dL/dbeta.  The
+// deflection is A (dx, dy) with A = 4 kappa_s r_s^2 g(u, tau) / r^2, u = r / r_s, so
+// every partial follows from g and its two partials in (u, tau), taken with
+// forward-mode duals: with P = G . (dx, dy), d/dkappa_s = (A / kappa_s) P,
+// d/dr_s = 4 kappa_s (2 r_s g - r g_u) / r^2 P, d/dtau = 4 kappa_s r_s^2 g_tau / r^2 P,
+// d/dx_s = -A_r (dx / r) P - A G_x (and y alike), A_r = 4 kappa_s (r_s r g_u - 2 r_s^2 g) / r^3
+// (r^2 is clamped at 1e-20 as in the deflection, with no position derivative there).
 template <typename T>
 __device__ __forceinline__ void sub_vjp(const LensK<T>& K, int h, T x, T y, T gbx, T gby, T* out) {
-    typedef Dual<T, 5> D;
-    D ks = D::seed(K.sub[h][0], 0), rs = D::seed(K.sub[h][1], 1);
-    D tau = K.kind == 2 ? D::seed(K.sub[h][2], 2) : D(K.sub[h][2]);
-    D xs = D::seed(K.sub[h][3], 3), ys = D::seed(K.sub[h][4], 4);
-    D ax, ay;
-    nfw_deflect<D>(D(x), D(y), ks, rs, tau, xs, ys, K.kind, ax, ay);
-#pragma unroll
-    for (int c = 0; c < 5; ++c) out[c] -= gbx * ax.d[c] + gby * ay.d[c];
+    typedef Dual<T, 2> D;
+    const T ks = K.sub[h][0], rs = K.sub[h][1];
+    const T dx = x - K.sub[h][3], dy = y - K.sub[h][4];
+    const T d2 = dx * dx + dy * dy;
+    const bool clamped = d2 < T(1e-20);
+    const T r = r_sqrt(clamped ? T(1e-20) : d2);
+    const D g = nfw_g<D>(D::seed(r / rs, 0), K.kind == 2 ? D::seed(K.sub[h][2], 1) : D(K.sub[h][2]), K.kind);
+    const T ir2 = T(1) / (r * r);
+    const T f = T(4) * ks * ir2;                    // 4 kappa_s / r^2
+    const T A = f * rs * rs * g.v;
+    const T P = gbx * dx + gby * dy;
+    out[0] -= T(4) * rs * rs * g.v * ir2 * P;
+    out[1] -= f * (T(2) * rs * g.v - r * g.d[0]) * P;
+    out[2] -= f * rs * rs * g.d[1] * P;
+    const T Ar = clamped ? T(0) : f * (rs * r * g.d[0] - T(2) * rs * rs * g.v) / r;
+    out[3] -= -Ar * (dx / r) * P - A * gbx;
+    out[4] -= -Ar * (dy / r) * P - A * gby;
 }
 
 // the evaluation's lens blocks: LensK<double> first, then LensK<float>, then the
