@@ -59,11 +59,11 @@ FLOPS_ADJ_RAY = 516.0
 # valid for the kernel sources with digest TRAFFIC_SRC_DIGEST.
 ROOF = {
     "k_render": {"flops_per_unit": FLOPS_FWD_RAY, "units": "in-grid rays",
-                 "traffic_per_unit": (345088 + 17408) / 743894},
+                 "traffic_per_unit": (345600 + 15616) / 743894},
     "k_render_adj": {"flops_per_unit": FLOPS_ADJ_RAY, "units": "in-grid rays",
-                     "traffic_per_unit": (9693440 + 142848) / 743894},
+                     "traffic_per_unit": (9692928 + 143104) / 743894},
 }
-TRAFFIC_SRC_DIGEST = "8fbfb93a192577f3"
+TRAFFIC_SRC_DIGEST = "e66e8e4e269de769"
 KERNEL_SOURCES = ("k_render.cuh", "rtu_internal.cuh", "rtu_math.cuh", "rtu_df.cuh")
 
 
